@@ -1,0 +1,438 @@
+/*
+ * craneplan_oracle.c -- plain, slow, FP64 CPU oracle of the stochastic B-spline path
+ * optimisation of "GPU-Accelerated Motion Planning of an Underactuated Forestry Crane
+ * in Cluttered Environments" (arXiv 2503.14160), Sec. 4.1.
+ *
+ * TEST INFRASTRUCTURE. This file is the checker the CUDA library is compared against.
+ * Only the test-suite, the package smoke check and the CPU-baseline leg of the
+ * benchmark load it; the product path never does. It shares no code, header, table
+ * or constant generator with the CUDA library.
+ *
+ * Everything is IEEE double, evaluated in the order the definitions are written.
+ * Compile with -ffp-contract=off so that x86 and Arm give identical results.
+ *
+ * What is here (paper section / reading it follows):
+ *   o_philox4x32_10     counter-based generator, Salmon et al. SC'11 (Philox4x32, 10 rounds)
+ *   o_normals           Box-Muller on Philox words: the z of Algorithm 1 step (1)
+ *   o_fk                crane chain forward kinematics (Sec. 2, Eq. FK; chain read as below)
+ *   o_sdf_cylinder      signed distance to a vertical capped cylinder (Sec. 3.1, d<0 = collision)
+ *   o_sdf_box           signed distance to an axis-aligned box (Sec. 3.1)
+ *   o_signed_distance   d(q) = min over link spheres and obstacles (Sec. 3.1), brute force
+ *   o_bspline           q(s) = sum_i P_i N_i^3(s), Cox-de Boor on a uniform knot vector (Sec. 4.1)
+ *   o_path_cost         J = J_p + w_c J_c + w_l J_l (Eq. path opt, all three sums)
+ *   o_path_cost_batch   the same for N candidates (Algorithm 1 step (2)); OpenMP over candidates
+ *   o_smooth_cost       the softplus-penalty variant of J used by the differentiable form
+ *
+ * Readings of the paper that the code depends on (the paper is silent or garbled here):
+ *   chain   slew q1 about world z; boom pitch q2 (elevation from horizontal); jib pitch q3
+ *           relative to the boom in the same vertical plane; telescope q4 extends the jib
+ *           axis; the grapple hangs plumb below the tip (passive joints at equilibrium).
+ *           e_b = (cos q2 cos q1, cos q2 sin q1, sin q2), e_j the same with q2+q3,
+ *           O = (0,0,base_z), J = O + L_b e_b, T = J + (L_j + q4) e_j.
+ *   spheres link 0: O + t e_b; link 1: J + t e_j; link 2: J + (L_j + t q4) e_j;
+ *           link 3: T - t z.  (t = the sphere's offset)
+ *   spline  n_c = K + 8 control points: P_0..P_3 = q_0, P_4..P_{K+3} = the K free points,
+ *           P_{K+4}..P_{K+7} = q_d; uniform knots t_i = i; the K+3 spans that move
+ *           ([4, K+7] in knot units) carry s in [0,1]: tau(s) = 4 + (K+3) s.
+ *   checkpoints s_k = k / n_s, n_s = (K+3) S, k = 0..n_s; the sums of Eq. path opt run
+ *           over k = 1..n_s.
+ *   r_c     r_c(q) = lambda_c * max(0, -d(q))  (the IK collision residual of Sec. 3.2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define O_MAX_SPHERES 32
+
+typedef struct {
+    double base_z;       /* height of the slew / boom pivot above the ground (m) */
+    double boom_len;     /* L_b: boom pivot to jib pivot (m) */
+    double jib_len;      /* L_j: jib pivot to the tip at zero telescope extension (m) */
+    double q_min[4];
+    double q_max[4];
+    int32_t n_spheres;
+    int32_t link[O_MAX_SPHERES];   /* 0 boom, 1 jib, 2 telescope, 3 grapple */
+    double offset[O_MAX_SPHERES];  /* t of the placement rule above */
+    double radius[O_MAX_SPHERES];
+} o_model;
+
+typedef struct {
+    int32_t n_cyl;
+    const double *cyl;   /* [n_cyl][5]: cx, cy, R, z_lo, z_hi */
+    int32_t n_box;
+    const double *box;   /* [n_box][6]: lo_x, lo_y, lo_z, hi_x, hi_y, hi_z */
+} o_scene;
+
+typedef struct {
+    int32_t K;           /* free control points (waypoints) */
+    int32_t S;           /* checkpoints per moving span */
+    double w_c, w_l;     /* weights of J_c and J_l in Eq. path opt */
+    double lambda_c;     /* scale of r_c */
+    double margin;       /* smooth form: penalty margin m (m) */
+    double beta;         /* smooth form: softplus width (m) */
+} o_cost_params;
+
+/* ------------------------------------------------------------------ Philox4x32-10 */
+
+/* One Philox4x32 round (Salmon, Moraes, Dror, Shaw, SC'11): two 32x32->64 products
+ * of words 0 and 2 with the round multipliers, the high halves xor-ed with the other
+ * words and the round key, the low halves passed through. */
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+/* Philox4x32 with 10 rounds; the key is bumped by the Weyl constants between rounds. */
+void o_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c, k);
+        k[0] += 0x9E3779B9u;
+        k[1] += 0xBB67AE85u;
+    }
+    memcpy(out, c, sizeof c);
+}
+
+void o_philox4x32_10_batch(const uint32_t *ctr, const uint32_t key[2], int64_t n, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) o_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
+/* Box-Muller (Box & Muller 1958) on two Philox words: the top 24 bits of each word give
+ * u1 = (a+1) 2^-24 in (0,1] and u2 = b 2^-24 in [0,1), both exact in binary32;
+ * z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2). */
+static void box_muller(uint32_t x0, uint32_t x1, double *z0, double *z1)
+{
+    const double u1 = ((double)(x0 >> 8) + 1.0) * 0x1p-24;
+    const double u2 = (double)(x1 >> 8) * 0x1p-24;
+    const double r = sqrt(-2.0 * log(u1));
+    const double a = 2.0 * M_PI * u2;
+    *z0 = r * cos(a);
+    *z1 = r * sin(a);
+}
+
+/* The D = 4K standard normals of candidate i at iteration t of query q (Algorithm 1 step
+ * (1)). Block j of the counter (j, i, t, q) under key (seed_lo, seed_hi) gives the four
+ * normals z[4j..4j+3] (control point j, joints 1..4). */
+void o_normals(uint64_t seed, uint32_t t, uint32_t q, int32_t i, int32_t K, double *z)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int32_t j = 0; j < K; ++j) {
+        const uint32_t ctr[4] = {(uint32_t)j, (uint32_t)i, t, q};
+        uint32_t x[4];
+        o_philox4x32_10(ctr, key, x);
+        box_muller(x[0], x[1], &z[4 * j + 0], &z[4 * j + 1]);
+        box_muller(x[2], x[3], &z[4 * j + 2], &z[4 * j + 3]);
+    }
+}
+
+void o_normals_batch(uint64_t seed, uint32_t t, uint32_t q, int32_t n, int32_t K, double *z)
+{
+    for (int32_t i = 0; i < n; ++i) o_normals(seed, t, q, i, K, z + (int64_t)i * 4 * K);
+}
+
+/* ------------------------------------------------------------------ kinematics */
+
+/* Sphere centres of the crane at configuration q (Sec. 2, Eq. FK with the chain read
+ * as in the file header). Also returns the jib pivot J and the tip T when asked. */
+void o_fk(const o_model *m, const double q[4], double *centres /* [n][3] */,
+          double *jib_pivot /* [3] or NULL */, double *tip /* [3] or NULL */)
+{
+    const double eb[3] = {cos(q[1]) * cos(q[0]), cos(q[1]) * sin(q[0]), sin(q[1])};
+    const double a = q[1] + q[2];
+    const double ej[3] = {cos(a) * cos(q[0]), cos(a) * sin(q[0]), sin(a)};
+    const double O[3] = {0.0, 0.0, m->base_z};
+    double J[3], T[3];
+    for (int c = 0; c < 3; ++c) J[c] = O[c] + m->boom_len * eb[c];
+    for (int c = 0; c < 3; ++c) T[c] = J[c] + (m->jib_len + q[3]) * ej[c];
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const double t = m->offset[s];
+        double *p = centres + 3 * s;
+        switch (m->link[s]) {
+        case 0: for (int c = 0; c < 3; ++c) p[c] = O[c] + t * eb[c]; break;
+        case 1: for (int c = 0; c < 3; ++c) p[c] = J[c] + t * ej[c]; break;
+        case 2: for (int c = 0; c < 3; ++c) p[c] = J[c] + (m->jib_len + t * q[3]) * ej[c]; break;
+        default:
+            p[0] = T[0];
+            p[1] = T[1];
+            p[2] = T[2] - t;
+            break;
+        }
+    }
+    if (jib_pivot) memcpy(jib_pivot, J, sizeof J);
+    if (tip) memcpy(tip, T, sizeof T);
+}
+
+/* ------------------------------------------------------------------ signed distances */
+
+/* Exact signed distance from point p to the vertical capped cylinder {rho <= R,
+ * z_lo <= z <= z_hi}: the standard two-component form, with a = rho - R (radial) and
+ * b = max(z_lo - z, z - z_hi) (axial): min(max(a, b), 0) + |(max(a,0), max(b,0))|. */
+double o_sdf_cylinder(const double p[3], const double *cyl /* cx, cy, R, z_lo, z_hi */)
+{
+    const double rho = hypot(p[0] - cyl[0], p[1] - cyl[1]);
+    const double a = rho - cyl[2];
+    const double b = fmax(cyl[3] - p[2], p[2] - cyl[4]);
+    return fmin(fmax(a, b), 0.0) + hypot(fmax(a, 0.0), fmax(b, 0.0));
+}
+
+/* Exact signed distance from p to the axis-aligned box [lo, hi]: with centre c and
+ * half-extent h, q_i = |p_i - c_i| - h_i, d = |max(q, 0)| + min(max_i q_i, 0). */
+double o_sdf_box(const double p[3], const double *box /* lo[3], hi[3] */)
+{
+    double qv[3], outside = 0.0, inner = -HUGE_VAL;
+    for (int c = 0; c < 3; ++c) {
+        const double centre = 0.5 * (box[c] + box[3 + c]);
+        const double half = 0.5 * (box[3 + c] - box[c]);
+        qv[c] = fabs(p[c] - centre) - half;
+        outside += fmax(qv[c], 0.0) * fmax(qv[c], 0.0);
+        inner = fmax(inner, qv[c]);
+    }
+    return sqrt(outside) + fmin(inner, 0.0);
+}
+
+/* d(q): minimum over all link spheres and all obstacles of (obstacle SDF at the
+ * sphere centre) - (sphere radius); d < 0 means collision (Sec. 3.1). +inf when the
+ * scene is empty. Brute force over every pair. */
+double o_signed_distance(const o_model *m, const o_scene *sc, const double q[4])
+{
+    double centres[3 * O_MAX_SPHERES];
+    o_fk(m, q, centres, NULL, NULL);
+    double d = HUGE_VAL;
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const double *p = centres + 3 * s;
+        for (int o = 0; o < sc->n_cyl; ++o)
+            d = fmin(d, o_sdf_cylinder(p, sc->cyl + 5 * o) - m->radius[s]);
+        for (int o = 0; o < sc->n_box; ++o)
+            d = fmin(d, o_sdf_box(p, sc->box + 6 * o) - m->radius[s]);
+    }
+    return d;
+}
+
+void o_signed_distance_batch(const o_model *m, const o_scene *sc, const double *q, int64_t n,
+                             double *d)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) d[i] = o_signed_distance(m, sc, q + 4 * i);
+}
+
+/* ------------------------------------------------------------------ B-spline */
+
+/* All cubic basis functions N_{i,3}(tau), i = 0..n_c-1, on the uniform knots t_i = i
+ * (i = 0..n_c+3), by the Cox-de Boor recursion written out degree by degree:
+ *   N_{i,0}(tau) = 1 if t_i <= tau < t_{i+1}, else 0
+ *   N_{i,p}(tau) = (tau - t_i)/(t_{i+p} - t_i) N_{i,p-1}(tau)
+ *                + (t_{i+p+1} - tau)/(t_{i+p+1} - t_{i+1}) N_{i+1,p-1}(tau). */
+void o_bspline_basis(int32_t n_c, double tau, double *basis /* [n_c] */)
+{
+    const int n_knots = n_c + 4;
+    double N[64 + 4];
+    for (int i = 0; i < n_knots - 1; ++i) {
+        const double ti = (double)i, ti1 = (double)(i + 1);
+        N[i] = (ti <= tau && tau < ti1) ? 1.0 : 0.0;
+    }
+    for (int p = 1; p <= 3; ++p) {
+        for (int i = 0; i < n_knots - 1 - p; ++i) {
+            const double ti = (double)i, tip = (double)(i + p);
+            const double ti1 = (double)(i + 1), tip1 = (double)(i + p + 1);
+            N[i] = (tau - ti) / (tip - ti) * N[i] + (tip1 - tau) / (tip1 - ti1) * N[i + 1];
+        }
+    }
+    for (int i = 0; i < n_c; ++i) basis[i] = N[i];
+}
+
+/* q(tau) = sum_i P_i N_{i,3}(tau) for control points P[n_c][4]. */
+void o_bspline(const double *P, int32_t n_c, double tau, double q[4])
+{
+    double basis[64];
+    o_bspline_basis(n_c, tau, basis);
+    for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+        for (int i = 0; i < n_c; ++i) acc += P[4 * i + c] * basis[i];
+        q[c] = acc;
+    }
+}
+
+/* The n_c = K + 8 control points of a candidate: four copies of q_0, the K free points
+ * xi[K][4], four copies of q_d (Sec. 4.1, end-point clamping). */
+static void assemble_control_points(int32_t K, const double *xi, const double q0[4],
+                                    const double qd[4], double *P)
+{
+    for (int i = 0; i < 4; ++i) memcpy(P + 4 * i, q0, 4 * sizeof(double));
+    memcpy(P + 16, xi, (size_t)K * 4 * sizeof(double));
+    for (int i = 0; i < 4; ++i) memcpy(P + 4 * (K + 4 + i), qd, 4 * sizeof(double));
+}
+
+/* Path parameter of checkpoint k: s_k = k / n_s, mapped onto the moving spans. */
+static double checkpoint_tau(int32_t K, int32_t S, int64_t k)
+{
+    const int64_t n_s = (int64_t)(K + 3) * S;
+    const double s = (double)k / (double)n_s;
+    return 4.0 + (double)(K + 3) * s;
+}
+
+/* ------------------------------------------------------------------ path cost */
+
+typedef struct {
+    double J, Jp, Jc, Jl;  /* total and the three terms of Eq. path opt */
+    double length;         /* sum_k |q(s_k) - q(s_{k-1})|, the path length that is reported */
+    int32_t flag;          /* 1 when d(q(s_k)) < 0 at some k = 1..n_s */
+    int32_t n_flagged;     /* how many checkpoints are in collision */
+} o_cost;
+
+/* Eq. path opt for one candidate. d_out (optional, [n_s + 1]) receives d(q(s_k)). */
+void o_path_cost(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                 const double *xi /* [K][4] */, const double q0[4], const double qd[4],
+                 o_cost *out, double *d_out)
+{
+    const int32_t K = cp->K, n_c = K + 8;
+    const int64_t n_s = (int64_t)(K + 3) * cp->S;
+    double P[4 * 72];
+    assemble_control_points(K, xi, q0, qd, P);
+    double q_prev[4];
+    o_bspline(P, n_c, checkpoint_tau(K, cp->S, 0), q_prev);
+    if (d_out) d_out[0] = o_signed_distance(m, sc, q_prev);
+    double Jp = 0.0, Jc = 0.0, Jl = 0.0, len = 0.0;
+    int32_t flag = 0, n_flagged = 0;
+    for (int64_t k = 1; k <= n_s; ++k) {
+        double q[4];
+        o_bspline(P, n_c, checkpoint_tau(K, cp->S, k), q);
+        double step2 = 0.0;
+        for (int c = 0; c < 4; ++c) step2 += (q[c] - q_prev[c]) * (q[c] - q_prev[c]);
+        Jp += step2;
+        len += sqrt(step2);
+        const double d = o_signed_distance(m, sc, q);
+        if (d_out) d_out[k] = d;
+        Jc += cp->lambda_c * fmax(0.0, -d);
+        if (d < 0.0) {
+            flag = 1;
+            ++n_flagged;
+        }
+        for (int c = 0; c < 4; ++c) {
+            const double hi = fmax(0.0, q[c] - m->q_max[c]);
+            const double lo = fmax(0.0, m->q_min[c] - q[c]);
+            Jl += hi * hi + lo * lo;
+        }
+        memcpy(q_prev, q, sizeof q);
+    }
+    out->Jp = Jp;
+    out->Jc = Jc;
+    out->Jl = Jl;
+    out->J = Jp + cp->w_c * Jc + cp->w_l * Jl;
+    out->length = len;
+    out->flag = flag;
+    out->n_flagged = n_flagged;
+}
+
+/* Algorithm 1 step (2) for n candidates xi[n][K][4]. d_out (optional) is [n][n_s+1]. */
+void o_path_cost_batch(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                       const double *xi, int64_t n, const double q0[4], const double qd[4],
+                       o_cost *out, double *d_out)
+{
+    const int64_t n_s = (int64_t)(cp->K + 3) * cp->S;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i)
+        o_path_cost(m, sc, cp, xi + i * 4 * cp->K, q0, qd, out + i,
+                    d_out ? d_out + i * (n_s + 1) : NULL);
+}
+
+/* ------------------------------------------------------------------ smooth form */
+
+/* softplus(x) = ln(1 + e^x), evaluated without overflow. */
+static double softplus(double x)
+{
+    return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x));
+}
+
+/* Smooth collision penalty at configuration q: lambda_c times the sum over every
+ * sphere-obstacle pair of beta * softplus((margin - sd) / beta), sd the pair's signed
+ * distance. It replaces max(0, -d) by a C-infinity surrogate so that the cost has a
+ * gradient everywhere. */
+double o_smooth_penalty(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                        const double q[4])
+{
+    double centres[3 * O_MAX_SPHERES];
+    o_fk(m, q, centres, NULL, NULL);
+    double acc = 0.0;
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const double *p = centres + 3 * s;
+        for (int o = 0; o < sc->n_cyl; ++o) {
+            const double sd = o_sdf_cylinder(p, sc->cyl + 5 * o) - m->radius[s];
+            acc += cp->beta * softplus((cp->margin - sd) / cp->beta);
+        }
+        for (int o = 0; o < sc->n_box; ++o) {
+            const double sd = o_sdf_box(p, sc->box + 6 * o) - m->radius[s];
+            acc += cp->beta * softplus((cp->margin - sd) / cp->beta);
+        }
+    }
+    return cp->lambda_c * acc;
+}
+
+/* J_smooth = J_p + w_c sum_k smooth_penalty(q(s_k)) + w_l J_l, k = 1..n_s. */
+double o_smooth_cost(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                     const double *xi, const double q0[4], const double qd[4])
+{
+    const int32_t K = cp->K, n_c = K + 8;
+    const int64_t n_s = (int64_t)(K + 3) * cp->S;
+    double P[4 * 72];
+    assemble_control_points(K, xi, q0, qd, P);
+    double q_prev[4];
+    o_bspline(P, n_c, checkpoint_tau(K, cp->S, 0), q_prev);
+    double Jp = 0.0, Jc = 0.0, Jl = 0.0;
+    for (int64_t k = 1; k <= n_s; ++k) {
+        double q[4];
+        o_bspline(P, n_c, checkpoint_tau(K, cp->S, k), q);
+        for (int c = 0; c < 4; ++c) Jp += (q[c] - q_prev[c]) * (q[c] - q_prev[c]);
+        Jc += o_smooth_penalty(m, sc, cp, q);
+        for (int c = 0; c < 4; ++c) {
+            const double hi = fmax(0.0, q[c] - m->q_max[c]);
+            const double lo = fmax(0.0, m->q_min[c] - q[c]);
+            Jl += hi * hi + lo * lo;
+        }
+        memcpy(q_prev, q, sizeof q);
+    }
+    return Jp + cp->w_c * Jc + cp->w_l * Jl;
+}
+
+void o_smooth_cost_batch(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                         const double *xi, int64_t n, const double q0[4], const double qd[4],
+                         double *J)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i) J[i] = o_smooth_cost(m, sc, cp, xi + i * 4 * cp->K, q0, qd);
+}
+
+/* ------------------------------------------------------------------ threads */
+
+void o_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int32_t o_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
