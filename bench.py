@@ -1,0 +1,338 @@
+"""Benchmark of the stochastic B-spline path optimisation on one GB300 per rank.
+
+A step is one whole plan: the T iterations of Algorithm 1 (sample, evaluate, rank,
+update; arXiv 2503.14160 Sec. 4.1) for one query, then the evaluation of the mean path.
+Workload: the single large query (N = 4096 candidates, K = 16 waypoints, S = 64 checkpoints
+per span, 500 trees in a 2-10 m annulus, 100 iterations), synthetic and seeded.
+
+Metric: candidate paths evaluated per second = N * T / (time per plan), plus ms per plan.
+  value  device time of the plan on the planner's stream (CUDA events), inputs resident
+  e2e    wall time through the C ABI with host buffers: scene and end points copied in,
+         control points and statistics copied out, every step
+
+--impl reference times the FP64 CPU oracle (the checker) on the host cores on a bounded
+sample of the same workload. Under torchrun every rank runs an independent replica
+(its own query, Philox query word = rank); value sums the ranks' candidates over the
+slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate paths evaluated/sec & ms per plan on 1 GB300 vs FP64 CPU oracle"
+UNIT = "candidate paths/s"
+WORKLOAD = "single_large"
+PEAK_SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FLOPS_PER_PAIR = 5          # 2 sub, 1 mul, 1 fma per sphere-obstacle pair
+FLOPS_PER_CHECKPOINT = 140  # spline 32, kinematics ~80, length 12, limits 16
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def select_endpoints_gpu(cp, planner, crane, seed, query):
+    """Start/goal by the rule of the workload, using the library's d(q) kernel."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+
+    def dist(q):
+        qt = torch.from_numpy(np.ascontiguousarray(q, np.float32)).cuda()
+        d = torch.zeros(q.shape[0], dtype=torch.float32, device="cuda")
+        cp.cp_signed_distance(planner.handle, qt, q.shape[0], d)
+        return d.cpu().numpy().astype(np.float64)
+
+    q0, qd, ok, _ = workloads.select_endpoints(crane, dist, seed=seed, query=query)
+    return q0, qd, ok
+
+
+def flush_l2(buf):
+    buf.add_(1.0)   # a write of a buffer larger than the 129 MB L2
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2503_14160_gb300 import build, craneplan as cp, workloads
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    cp.load()
+    wl = workloads.WORKLOADS[args.workload]
+    iters = args.iterations or wl.iterations
+    crane = workloads.forestry_crane()
+    scene = workloads.make_scene(wl)
+    params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank)
+    planner = cp.Planner(crane, scene, params)
+    h = planner.handle
+    q0, qd, ok = select_endpoints_gpu(cp, planner, crane, wl.seed, rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    # warm-up plans
+    for _ in range(args.warmup):
+        cp.cp_set_endpoints(h, q0, qd)
+        cp.cp_plan(h, iters, K=wl.n_waypoints)
+    torch.cuda.synchronize()
+
+    # device-timed plans (inputs resident): events around each plan, L2 flushed between
+    times = []
+    launches0 = cp.cp_launch_count()
+    cp.cp_set_timing(h, True)
+    stats = None
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush_l2(flush)
+            start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            cp.cp_set_endpoints(h, q0, qd)
+            _, stats = cp.cp_plan(h, iters, K=None)
+            end.record(stream)
+            end.synchronize()
+            times.append(start.elapsed_time(end))
+        torch.cuda.synchronize()
+        barrier()
+    launches = cp.cp_launch_count() - launches0
+    timing = cp.cp_get_timing(h)
+    cp.cp_set_timing(h, False)
+
+    # end-to-end through the C ABI with host buffers, wall clock
+    e2e_times = []
+    for _ in range(args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        cp.cp_set_scene(h, planner.scene)
+        cp.cp_set_endpoints(h, q0, qd)
+        ctrl, st = cp.cp_plan(h, iters, K=wl.n_waypoints)
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+    barrier()
+
+    ms = float(np.mean(times))
+    ms_e2e = float(np.mean(e2e_times))
+    if ws > 1:
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    units = wl.n_candidates * iters * ws
+    value = units / (ms / 1e3)
+
+    # roofline of the evaluation kernel (FK + collision + cost)
+    n_s = wl.n_checkpoints
+    pairs = len(crane.spheres) * (scene.n_cyl + scene.n_box)
+    flops_per_candidate = n_s * (pairs * FLOPS_PER_PAIR + FLOPS_PER_CHECKPOINT)
+    # each plan launches the kernel T times on N candidates and once on the mean path
+    flops_per_launch = (wl.n_candidates * iters + 1) * flops_per_candidate / (iters + 1)
+    eval_ms = timing["eval_ms"] / max(timing["eval_launches"], 1)
+    achieved = flops_per_launch / (eval_ms / 1e3) / 1e12
+    peak = PEAK_SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    clk = clocks.summary()
+
+    if rank == 0:
+        bi = scene.n_cyl * 40 + scene.n_box * 48 + 64
+        bo = (wl.n_waypoints + 8) * 32 + 6 * 8 + 4
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded crane-and-forest scene; paper environments unavailable)",
+            "config": {"workload": "%s: N=%d K=%d S=%d cylinders=%d iterations=%d per plan"
+                                   % (wl.name, wl.n_candidates, wl.n_waypoints, wl.substeps,
+                                      scene.n_cyl, iters),
+                       "step": "one plan", "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed between steps (256 MB write)",
+                       "endpoints_ok": bool(ok)},
+            "ms_per_plan": ms,
+            "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "ms_per_plan": ms_e2e,
+                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "kernel": "k_eval", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                         "frac_at_observed_clock": (achieved / (peak * clk["sm_mhz"] / 2070.0)
+                                                    if clk.get("sm_mhz") else None),
+                         "traffic": None, "eval_ms_per_launch": eval_ms,
+                         "eval_launches": timing["eval_launches"]},
+            "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
+                                  for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},
+            "plan_result": {"J": stats["J"], "length": stats["length"], "flag": stats["flag"]},
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl, crane, scene, q0, qd, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    planner.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, crane, scene, q0, qd, seconds, max_batches=None):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample: candidate
+    evaluations (step (2), which dominates a plan) of the same workload, in batches until
+    `seconds` have passed; value in candidate paths per second."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    from paper_2503_14160_gb300 import workloads
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    problem = oracle.Problem(crane, scene, oracle.CostParams(K=wl.n_waypoints, S=wl.substeps))
+    batch = 4 * cores
+    xi = workloads.random_candidates(q0, qd, wl.n_waypoints, batch, seed=123).astype(np.float64)
+    done, t0, batches = 0, time.perf_counter(), 0
+    while True:
+        oracle.evaluate(problem, xi, q0, qd)
+        done += batch
+        batches += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_batches and batches >= max_batches):
+            break
+    return {"value": done / el, "unit": UNIT, "cores": int(oracle.get_threads()),
+            "kind": "oracle", "seconds": el,
+            "sample": "%d candidate evaluations (K=%d, S=%d, %d cylinders, FP64, OpenMP over "
+                      "candidates) of the %s workload" % (done, wl.n_waypoints, wl.substeps,
+                                                          scene.n_cyl, wl.name)}
+
+
+def run_reference(args):
+    from paper_2503_14160_gb300 import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    wl = workloads.WORKLOADS[args.workload]
+    iters = args.iterations or wl.iterations
+    crane = workloads.forestry_crane()
+    scene = workloads.make_scene(wl)
+    with open(os.path.join(ROOT, "tests", "golden", "endpoints.json")) as f:
+        e = json.load(f)["workloads"][wl.name]
+    q0, qd = np.array(e["q0"]), np.array(e["qd"])
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(wl, crane, scene, q0, qd, args.cpu_seconds / 4, max_batches=1)
+        if i >= args.warmup:
+            per_step.append(r)
+    value = float(np.mean([r["value"] for r in per_step]))
+    ms_per_plan = wl.n_candidates * iters / value * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean([r["seconds"] for r in per_step])) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded crane-and-forest scene)", "impl": "reference",
+            "config": {"workload": "%s: N=%d K=%d S=%d cylinders=%d iterations=%d per plan"
+                                   % (wl.name, wl.n_candidates, wl.n_waypoints, wl.substeps,
+                                      scene.n_cyl, iters),
+                       "step": "a bounded sample: one batch of candidate evaluations"},
+            "ms_per_plan_extrapolated": ms_per_plan,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": per_step[0]["cores"],
+                             "kind": "oracle", "sample": per_step[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--iterations", type=int, default=0, help="override iterations per plan")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

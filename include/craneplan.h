@@ -1,0 +1,246 @@
+/*
+ * craneplan.h -- C ABI of the GB300 (sm_103a) library for the stochastic B-spline path
+ * optimisation of a forestry crane (arXiv 2503.14160, Sec. 4.1, Algorithm 1).
+ *
+ * One planning query searches joint space for a short, collision-free path from q_0 to
+ * q_d. The path is a cubic B-spline whose K free control points ("waypoints") are drawn
+ * each iteration from N(mu, sigma^2 C) (Algorithm 1 step (1)); every candidate is scored
+ * with J = J_p + w_c J_c + w_l J_l over n_s = (K+3) S checkpoints (Eq. path opt; step
+ * (2)); the candidates are ranked (step (3)); the nu best get log-rank weights (step (4));
+ * and mu and C are replaced by the weighted mean and covariance of those elites (steps
+ * (5)-(6)).
+ *
+ * Conventions for every entry point:
+ *  - Return value: CP_OK (0) on success, a negative cp_status on failure; then
+ *    cp_last_error() (thread-local) describes the failure. No call aborts the process.
+ *  - "d_" pointers are CUDA device pointers owned by the caller; "h_" pointers and
+ *    struct pointers are host memory owned by the caller. The library keeps no caller
+ *    pointer after a call returns.
+ *  - All device work of a planner is ordered on the stream given to cp_plan_init (a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream). Calls that take
+ *    device pointers only enqueue work and return before it completes; calls that take
+ *    "h_" outputs synchronise that stream.
+ *  - Layouts: a candidate is K control points of 4 joints (q1 slew [rad], q2 boom pitch
+ *    [rad], q3 jib pitch [rad], q4 telescope [m]), stored point-major as float[K][4]
+ *    (one float4 per point); a population is float[N][K][4]. Means and covariances are
+ *    double, flattened point-major: index 4*point + joint, D = 4K.
+ *  - The library allocates device memory only in cp_plan_init (its workspace) and frees
+ *    it in cp_destroy.
+ */
+#ifndef CRANEPLAN_H
+#define CRANEPLAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CP_MAX_SPHERES 16
+#define CP_MAX_WAYPOINTS 32
+#define CP_VERSION 1
+
+typedef enum cp_status {
+    CP_OK = 0,
+    CP_ERR_ARG = -1,      /* an argument is out of range or NULL where it may not be */
+    CP_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    CP_ERR_TIMEOUT = -3,  /* a bounded device-side wait gave up */
+    CP_ERR_STATE = -4,    /* the planner is not ready for this call (e.g. no end points) */
+    CP_ERR_OOM = -5,      /* device allocation failed */
+    CP_ERR_NUMERIC = -6   /* the covariance lost positive definiteness */
+} cp_status;
+
+/* One link-bounding sphere (Sec. 3.1 collision geometry, here spheres on the links).
+ * Its centre, with O the slew/boom pivot, J the jib pivot, T the tip, e_b and e_j the
+ * boom and jib directions and t = offset:
+ *   link 0 (boom)      O + t e_b
+ *   link 1 (jib)       J + t e_j
+ *   link 2 (telescope) J + (jib_len + t q4) e_j
+ *   link 3 (grapple)   T - t z      (the grapple hangs plumb below the tip) */
+typedef struct cp_sphere {
+    int32_t link;
+    double offset;   /* m */
+    double radius;   /* m, > 0 */
+} cp_sphere;
+
+/* The actuated crane chain (Sec. 2, Eq. FK): slew q1 about world z at the origin; boom
+ * pivot at height base_z; boom pitch q2 measured from horizontal; jib pitch q3 relative
+ * to the boom in the same vertical plane; telescope q4 extends the jib axis.
+ *   e_b = (cos q2 cos q1, cos q2 sin q1, sin q2),  e_j = same with q2 + q3,
+ *   O = (0, 0, base_z),  J = O + boom_len e_b,  T = J + (jib_len + q4) e_j.
+ * q_min/q_max are the joint limits used by J_l (Eq. path opt); the kinematics use the
+ * raw, unclamped q. */
+typedef struct cp_model {
+    double base_z;
+    double boom_len;
+    double jib_len;
+    double q_min[4];
+    double q_max[4];
+    int32_t n_spheres;                    /* 1..CP_MAX_SPHERES */
+    cp_sphere spheres[CP_MAX_SPHERES];
+} cp_model;
+
+/* Vertical capped cylinder {(x-cx)^2 + (y-cy)^2 <= radius^2, z_lo <= z <= z_hi}. */
+typedef struct cp_cylinder {
+    double cx, cy, radius, z_lo, z_hi;
+} cp_cylinder;
+
+/* Axis-aligned box [lo, hi]. */
+typedef struct cp_box {
+    double lo[3];
+    double hi[3];
+} cp_box;
+
+/* Obstacle scene in HOST memory. The signed distance d(q) of Sec. 3.1 is the minimum
+ * over link spheres and obstacles of (obstacle signed distance at the sphere centre)
+ * minus the sphere radius; d < 0 is a collision. */
+typedef struct cp_scene {
+    int32_t n_cyl;
+    const cp_cylinder *cyl;
+    int32_t n_box;
+    const cp_box *box;
+} cp_scene;
+
+/* Search parameters of Algorithm 1 and of the cost (Eq. path opt). */
+typedef struct cp_params {
+    int32_t n_candidates;   /* lambda = N, the population size, >= 2 */
+    int32_t n_waypoints;    /* K free control points, 1..CP_MAX_WAYPOINTS */
+    int32_t substeps;       /* S checkpoints per moving spline span; n_s = (K+3) S */
+    int32_t n_elites;       /* nu; 0 selects floor(N/2) */
+    double w_c;             /* weight of J_c */
+    double w_l;             /* weight of J_l */
+    double lambda_c;        /* r_c(q) = lambda_c max(0, -d(q)) */
+    double sigma;           /* step size: samples are N(mu, sigma^2 C) */
+    double eps;             /* covariance regulariser eps I of step (6) */
+    double init_std_frac;   /* C_0 = diag((init_std_frac (q_max - q_min))^2) */
+    uint64_t seed;          /* Philox key */
+    uint32_t query;         /* fourth Philox counter word (query id) */
+    int32_t max_cylinders;  /* capacity of the scene buffers (cp_set_scene); 0 = scene's */
+    int32_t max_boxes;
+} cp_params;
+
+/* Cost terms of the final mean path and the state of a finished plan. */
+typedef struct cp_plan_stats {
+    double J, Jp, Jc, Jl;   /* cost of the final mean path and its three terms */
+    double length;          /* sum_k |q(s_k) - q(s_{k-1})| of the final mean path */
+    int32_t flag;           /* 1 when the final mean path collides at some checkpoint */
+    int32_t n_flagged;      /* checkpoints of the final mean path in collision */
+    int32_t iterations;     /* iterations run by this call */
+    int32_t iteration;      /* the planner's iteration counter after the call */
+    double best_J;          /* lowest candidate cost of the last iteration */
+} cp_plan_stats;
+
+/* Accumulated device time per stage while timing is on (CUDA events on the planner's
+ * stream around each stage's launches). */
+typedef struct cp_timing {
+    double eval_ms;   int64_t eval_launches;    /* FK + collision + cost kernel only */
+    double sample_ms; int64_t sample_launches;
+    double factor_ms; int64_t factor_launches;
+    double update_ms; int64_t update_launches;  /* rank, weights, mean, covariance */
+} cp_timing;
+
+typedef struct cp_planner cp_planner;
+
+/* Description of the last failure on this thread ("" when none). */
+const char *cp_last_error(void);
+
+/* CP_VERSION of the loaded library. */
+int32_t cp_version(void);
+
+/* Number of kernels this library has launched in this process (all planners). */
+int64_t cp_launch_count(void);
+
+/* Create a planner on the current CUDA device: validates the model, scene and parameters,
+ * allocates the device workspace for N candidates, stages the scene (host -> device) and
+ * tabulates the spline basis. End points must be set with cp_set_endpoints before
+ * sampling or planning. On failure *out is NULL and nothing stays allocated.
+ * Errors: CP_ERR_ARG (invalid input), CP_ERR_OOM, CP_ERR_CUDA. */
+int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *params,
+                 void *stream, cp_planner **out);
+
+/* Release the workspace (synchronises the planner's stream first). NULL is ignored. */
+void cp_destroy(cp_planner *p);
+
+/* Replace the obstacle scene (host memory, copied to the device on the planner's
+ * stream). Capacities are those given at init. Errors: CP_ERR_ARG, CP_ERR_CUDA. */
+int cp_set_scene(cp_planner *p, const cp_scene *scene);
+
+/* Set start q_0 and goal q_d (host, 4 doubles each) and reset the search: mu <- the K
+ * interior points evenly spaced on the segment q_0 -> q_d (Sec. 4.1 initial guess),
+ * C <- diag((init_std_frac (q_max - q_min))^2), iteration counter <- 0, and factor
+ * sigma^2 C. Errors: CP_ERR_ARG, CP_ERR_CUDA. */
+int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4]);
+
+/* Algorithm 1 step (1): d_xi[i] = mu + L z_i for i < N, L L^T = sigma^2 C, z_i the D
+ * standard normals of Philox4x32-10 at counter (block j, candidate i, iteration `iter`,
+ * query) under key seed, through Box-Muller (block j gives z[4j..4j+3]). d_xi is
+ * float[N][K][4] on the device. Errors: CP_ERR_STATE (no end points), CP_ERR_ARG. */
+int cp_sample(cp_planner *p, int32_t iter, float *d_xi);
+
+/* Algorithm 1 step (2): the cost of Eq. path opt for n candidates d_xi (float[n][K][4],
+ * n <= N). Outputs (device; all but d_J may be NULL):
+ *   d_J              double[n]       J = J_p + w_c J_c + w_l J_l
+ *   d_flag           uint8[n]        1 when d(q(s_k)) < 0 at some checkpoint k = 1..n_s
+ *   d_terms          double[n][5]    J_p, J_c, J_l, path length, checkpoints in collision
+ *   d_substep_flags  uint32[n][W]    W = ceil(n_s / 32); bit b of word w is checkpoint
+ *                                    k = 32 w + b + 1 in collision
+ *   d_pen            float[n][n_s]   max(0, -d(q(s_k))) at k = 1..n_s
+ * Errors: CP_ERR_STATE (no end points), CP_ERR_ARG. */
+int cp_evaluate(cp_planner *p, const float *d_xi, int32_t n, double *d_J, uint8_t *d_flag,
+                double *d_terms, uint32_t *d_substep_flags, float *d_pen);
+
+/* Algorithm 1 steps (3)-(6) for the N candidates d_xi with costs d_J (double[N], NaN
+ * ranks last, ties go to the lower index): mu <- sum_j w_j xi_(j),
+ * C <- sum_j w_j (xi_(j) - mu)(xi_(j) - mu)^T + eps I with the new mu, then factor
+ * sigma^2 C for the next sample and advance the iteration counter.
+ * Errors: CP_ERR_STATE, CP_ERR_ARG, CP_ERR_NUMERIC (reported by the next host-synchronising call). */
+int cp_update(cp_planner *p, const double *d_J, const float *d_xi);
+
+/* Synchronise the planner's stream and report a device-side failure of earlier
+ * asynchronous calls (CP_ERR_NUMERIC for a non-positive-definite covariance met by the
+ * factorisation, CP_ERR_TIMEOUT for a bounded wait that gave up); the report is cleared. */
+int cp_synchronize(cp_planner *p);
+
+/* Run `iters` iterations of Algorithm 1 (sample, evaluate, update) from the current
+ * state, then evaluate the mean path. h_ctrl (host, may be NULL) receives the K+8
+ * control points of the result, double[K+8][4]: four copies of q_0, mu, four copies of
+ * q_d. stats (host, may be NULL) receives the cost terms of the mean path.
+ * Synchronises the planner's stream. Errors: CP_ERR_STATE, CP_ERR_ARG, CP_ERR_CUDA,
+ * CP_ERR_NUMERIC. */
+int cp_plan(cp_planner *p, int32_t iters, double *h_ctrl, cp_plan_stats *stats);
+
+/* Sec. 3.1 signed distance d(q) (float, device) for n configurations d_q (float[n][4],
+ * device); +inf for an empty scene. Errors: CP_ERR_ARG. */
+int cp_signed_distance(cp_planner *p, const float *d_q, int32_t n, float *d_d);
+
+/* Copy the current mean (double[D]) and covariance (double[D][D]) to device buffers
+ * (either may be NULL). */
+int cp_get_distribution(const cp_planner *p, double *d_mu, double *d_C);
+
+/* Replace mean and covariance from device buffers, set the iteration counter to `iter`
+ * and factor sigma^2 C (a checkpoint restore: with the same seed the remaining
+ * iterations repeat bit for bit). Errors: CP_ERR_STATE (no end points), CP_ERR_ARG. */
+int cp_set_distribution(cp_planner *p, const double *d_mu, const double *d_C, int32_t iter);
+
+/* Copy the current Cholesky factor L (double[D][D], lower, L L^T = sigma^2 C). */
+int cp_get_factor(const cp_planner *p, double *d_L);
+
+/* Copy the candidate indices of the last update in rank order (int32[nu]). */
+int cp_get_elites(const cp_planner *p, int32_t *d_idx);
+
+/* Philox4x32-10 (Salmon et al., SC'11) of n counters d_ctr (uint32[n][4], device) under
+ * key = (uint32)seed, (uint32)(seed >> 32); d_out is uint32[n][4]. `stream` as above. */
+int cp_philox4x32_10(const uint32_t *d_ctr, uint64_t key, int64_t n, uint32_t *d_out,
+                     void *stream);
+
+/* Turn per-stage timing on (1) or off (0); turning it on clears the accumulators. */
+int cp_set_timing(cp_planner *p, int32_t on);
+
+/* Synchronise the planner's stream and return the accumulated stage times. */
+int cp_get_timing(cp_planner *p, cp_timing *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRANEPLAN_H */

@@ -1,0 +1,327 @@
+"""Python binding of the craneplan C ABI (include/craneplan.h): argument marshalling only.
+
+Every function keeps the name of the C entry point it calls. Device buffers are passed as
+torch CUDA tensors (their data pointers); host buffers as numpy arrays or sequences. The
+CUDA library must have been built (``paper_2503_14160_gb300.build.build()``); there is no
+fallback: importing this module without the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+CP_MAX_SPHERES = 16
+CP_MAX_WAYPOINTS = 32
+
+STATUS = {0: "CP_OK", -1: "CP_ERR_ARG", -2: "CP_ERR_CUDA", -3: "CP_ERR_TIMEOUT",
+          -4: "CP_ERR_STATE", -5: "CP_ERR_OOM", -6: "CP_ERR_NUMERIC"}
+
+
+class CranePlanError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+class cp_sphere(ctypes.Structure):
+    _fields_ = [("link", ctypes.c_int32), ("offset", ctypes.c_double), ("radius", ctypes.c_double)]
+
+
+class cp_model(ctypes.Structure):
+    _fields_ = [("base_z", ctypes.c_double), ("boom_len", ctypes.c_double),
+                ("jib_len", ctypes.c_double), ("q_min", ctypes.c_double * 4),
+                ("q_max", ctypes.c_double * 4), ("n_spheres", ctypes.c_int32),
+                ("spheres", cp_sphere * CP_MAX_SPHERES)]
+
+
+class cp_cylinder(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("radius", ctypes.c_double),
+                ("z_lo", ctypes.c_double), ("z_hi", ctypes.c_double)]
+
+
+class cp_box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class cp_scene(ctypes.Structure):
+    _fields_ = [("n_cyl", ctypes.c_int32), ("cyl", ctypes.c_void_p),
+                ("n_box", ctypes.c_int32), ("box", ctypes.c_void_p)]
+
+
+class cp_params(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("n_waypoints", ctypes.c_int32),
+                ("substeps", ctypes.c_int32), ("n_elites", ctypes.c_int32),
+                ("w_c", ctypes.c_double), ("w_l", ctypes.c_double),
+                ("lambda_c", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("eps", ctypes.c_double), ("init_std_frac", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("query", ctypes.c_uint32),
+                ("max_cylinders", ctypes.c_int32), ("max_boxes", ctypes.c_int32)]
+
+
+class cp_plan_stats(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("Jp", ctypes.c_double), ("Jc", ctypes.c_double),
+                ("Jl", ctypes.c_double), ("length", ctypes.c_double),
+                ("flag", ctypes.c_int32), ("n_flagged", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("iteration", ctypes.c_int32),
+                ("best_J", ctypes.c_double)]
+
+
+class cp_timing(ctypes.Structure):
+    _fields_ = [("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64),
+                ("sample_ms", ctypes.c_double), ("sample_launches", ctypes.c_int64),
+                ("factor_ms", ctypes.c_double), ("factor_launches", ctypes.c_int64),
+                ("update_ms", ctypes.c_double), ("update_launches", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "cp_last_error": (ctypes.c_char_p, []),
+    "cp_version": (ctypes.c_int32, []),
+    "cp_launch_count": (ctypes.c_int64, []),
+    "cp_plan_init": (ctypes.c_int, [ctypes.POINTER(cp_model), ctypes.POINTER(cp_scene),
+                                    ctypes.POINTER(cp_params), _P, ctypes.POINTER(_P)]),
+    "cp_destroy": (None, [_P]),
+    "cp_set_scene": (ctypes.c_int, [_P, ctypes.POINTER(cp_scene)]),
+    "cp_set_endpoints": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "cp_sample": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "cp_evaluate": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "cp_update": (ctypes.c_int, [_P, _P, _P]),
+    "cp_synchronize": (ctypes.c_int, [_P]),
+    "cp_plan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(cp_plan_stats)]),
+    "cp_signed_distance": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "cp_get_distribution": (ctypes.c_int, [_P, _P, _P]),
+    "cp_set_distribution": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+    "cp_get_factor": (ctypes.c_int, [_P, _P]),
+    "cp_get_elites": (ctypes.c_int, [_P, _P]),
+    "cp_philox4x32_10": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P]),
+    "cp_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cp_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(cp_timing)]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libcraneplan.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libcraneplan.so is not built (%s); run "
+                           "paper_2503_14160_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise CranePlanError(rc, load().cp_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _c4(v) -> ctypes.Array:
+    a = np.ascontiguousarray(v, dtype=np.float64).reshape(4)
+    return (ctypes.c_double * 4)(*a.tolist())
+
+
+# --------------------------------------------------------------------------- marshalling
+
+def make_model(crane) -> cp_model:
+    """cp_model from a workloads.CraneModel."""
+    m = cp_model()
+    m.base_z, m.boom_len, m.jib_len = crane.base_z, crane.boom_len, crane.jib_len
+    for j in range(4):
+        m.q_min[j], m.q_max[j] = crane.q_min[j], crane.q_max[j]
+    if len(crane.spheres) > CP_MAX_SPHERES:
+        raise ValueError("at most %d spheres" % CP_MAX_SPHERES)
+    m.n_spheres = len(crane.spheres)
+    for s, sp in enumerate(crane.spheres):
+        m.spheres[s] = cp_sphere(sp.link, sp.offset, sp.radius)
+    return m
+
+
+class HostScene:
+    """cp_scene over host arrays (keeps them alive)."""
+
+    def __init__(self, cylinders, boxes):
+        cyl = np.ascontiguousarray(cylinders, dtype=np.float64).reshape(-1, 5)
+        box = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 6)
+        self.cyl, self.box = cyl, box
+        self.c = cp_scene(cyl.shape[0], cyl.ctypes.data if cyl.shape[0] else None,
+                          box.shape[0], box.ctypes.data if box.shape[0] else None)
+
+    @classmethod
+    def from_scene(cls, scene) -> "HostScene":
+        return cls(scene.cylinders, scene.boxes)
+
+
+def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
+                w_l: float = 100.0, lambda_c: float = 1.0, sigma: float = 1.0,
+                eps: float = 1e-8, init_std_frac: float = 0.1, seed: int = 0, query: int = 0,
+                max_cylinders: int = 0, max_boxes: int = 0) -> cp_params:
+    return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
+                     query, max_cylinders, max_boxes)
+
+
+# --------------------------------------------------------------------------- entry points
+
+def cp_last_error() -> str:
+    return load().cp_last_error().decode()
+
+
+def cp_version() -> int:
+    return int(load().cp_version())
+
+
+def cp_launch_count() -> int:
+    return int(load().cp_launch_count())
+
+
+def cp_plan_init(model: cp_model, scene: HostScene, params: cp_params, stream=None) -> int:
+    """Returns the planner handle (an opaque pointer as int)."""
+    out = _P()
+    _check(load().cp_plan_init(ctypes.byref(model), ctypes.byref(scene.c), ctypes.byref(params),
+                               _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def cp_destroy(p: int) -> None:
+    load().cp_destroy(p)
+
+
+def cp_set_scene(p: int, scene: HostScene) -> None:
+    _check(load().cp_set_scene(p, ctypes.byref(scene.c)))
+
+
+def cp_set_endpoints(p: int, q0, qd) -> None:
+    _check(load().cp_set_endpoints(p, _c4(q0), _c4(qd)))
+
+
+def cp_sample(p: int, it: int, xi) -> None:
+    _check(load().cp_sample(p, int(it), _ptr(xi)))
+
+
+def cp_evaluate(p: int, xi, n: int, J, flag=None, terms=None, substep_flags=None,
+                pen=None) -> None:
+    _check(load().cp_evaluate(p, _ptr(xi), int(n), _ptr(J), _ptr(flag), _ptr(terms),
+                              _ptr(substep_flags), _ptr(pen)))
+
+
+def cp_update(p: int, J, xi) -> None:
+    _check(load().cp_update(p, _ptr(J), _ptr(xi)))
+
+
+def cp_synchronize(p: int) -> None:
+    _check(load().cp_synchronize(p))
+
+
+def cp_plan(p: int, iters: int, K: Optional[int] = None):
+    """Returns (control points double[K+8][4] or None, stats dict)."""
+    stats = cp_plan_stats()
+    ctrl = np.zeros((K + 8, 4)) if K is not None else None
+    cptr = ctrl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if ctrl is not None else None
+    _check(load().cp_plan(p, int(iters), cptr, ctypes.byref(stats)))
+    return ctrl, {f: getattr(stats, f) for f, _ in cp_plan_stats._fields_}
+
+
+def cp_signed_distance(p: int, q, n: int, d) -> None:
+    _check(load().cp_signed_distance(p, _ptr(q), int(n), _ptr(d)))
+
+
+def cp_get_distribution(p: int, mu=None, C=None) -> None:
+    _check(load().cp_get_distribution(p, _ptr(mu), _ptr(C)))
+
+
+def cp_set_distribution(p: int, mu, C, it: int) -> None:
+    _check(load().cp_set_distribution(p, _ptr(mu), _ptr(C), int(it)))
+
+
+def cp_get_factor(p: int, L) -> None:
+    _check(load().cp_get_factor(p, _ptr(L)))
+
+
+def cp_get_elites(p: int, idx) -> None:
+    _check(load().cp_get_elites(p, _ptr(idx)))
+
+
+def cp_philox4x32_10(ctr, key: int, n: int, out, stream=None) -> None:
+    _check(load().cp_philox4x32_10(_ptr(ctr), int(key), int(n), _ptr(out), _stream(stream)))
+
+
+def cp_set_timing(p: int, on: bool) -> None:
+    _check(load().cp_set_timing(p, 1 if on else 0))
+
+
+def cp_get_timing(p: int) -> dict:
+    t = cp_timing()
+    _check(load().cp_get_timing(p, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in cp_timing._fields_}
+
+
+class Planner:
+    """Owns one planner handle and the host scene it was created from."""
+
+    def __init__(self, crane, scene, params: cp_params, stream=None):
+        self.model = make_model(crane)
+        self.scene = HostScene.from_scene(scene)
+        self.params = params
+        self.N, self.K, self.S = params.n_candidates, params.n_waypoints, params.substeps
+        self.D = 4 * self.K
+        self.n_s = (self.K + 3) * self.S
+        self.nu = params.n_elites if params.n_elites > 0 else self.N // 2
+        self.handle = cp_plan_init(self.model, self.scene, params, stream)
+
+    def close(self):
+        if self.handle:
+            cp_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

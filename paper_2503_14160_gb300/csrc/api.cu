@@ -1,0 +1,685 @@
+// C ABI of the craneplan library (declared in include/craneplan.h): validation, the
+// planner's device workspace, and the order of the kernel launches of Algorithm 1
+// (arXiv 2503.14160, Sec. 4.1). All arithmetic of the method runs in the kernels; host
+// code here only checks arguments, copies inputs and results, and sequences launches.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cp_internal.cuh"
+
+namespace cp {
+
+namespace {
+thread_local char g_err[512] = "";
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? CP_ERR_OOM : CP_ERR_CUDA;
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace cp
+
+using namespace cp;
+
+namespace {
+
+enum Stage { ST_EVAL = 0, ST_SAMPLE = 1, ST_FACTOR = 2, ST_UPDATE = 3, ST_COUNT = 4 };
+
+struct Timer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[ST_COUNT];
+    cudaEvent_t open = nullptr;
+
+    int begin(cudaStream_t st)
+    {
+        if (!on) return CP_OK;
+        cudaEvent_t e;
+        int rc = take(&e);
+        if (rc != CP_OK) return rc;
+        CP_CUDA(cudaEventRecord(e, st));
+        open = e;
+        return CP_OK;
+    }
+    int end(Stage s, cudaStream_t st)
+    {
+        if (!on) return CP_OK;
+        cudaEvent_t e;
+        int rc = take(&e);
+        if (rc != CP_OK) return rc;
+        CP_CUDA(cudaEventRecord(e, st));
+        spans[s].emplace_back(open, e);
+        return CP_OK;
+    }
+    int take(cudaEvent_t *e)
+    {
+        if (used == pool.size()) {
+            cudaEvent_t ev;
+            CP_CUDA(cudaEventCreate(&ev));
+            pool.push_back(ev);
+        }
+        *e = pool[used++];
+        return CP_OK;
+    }
+    void clear()
+    {
+        used = 0;
+        for (auto &s : spans) s.clear();
+    }
+    void destroy()
+    {
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+        clear();
+    }
+};
+
+// Bump allocator over one device allocation (256-byte aligned pieces).
+struct Layout {
+    size_t bytes = 0;
+    template <typename T>
+    size_t take(size_t count)
+    {
+        const size_t off = bytes;
+        bytes += (count * sizeof(T) + 255) & ~(size_t)255;
+        return off;
+    }
+};
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+struct cp_planner {
+    cudaStream_t st = nullptr;
+    int device = 0, num_sms = 1;
+    cp_params prm{};
+    int N = 0, K = 0, S = 0, D = 0, n_s = 0, chunks = 0, nu = 0, n_mean_chunks = 0;
+    int cap_cyl = 0, cap_box = 0;
+    ModelDev mdev{};
+    SceneDev sdev{};
+    char *base = nullptr;
+    // workspace pieces
+    cp_cylinder *cyl_in = nullptr;
+    cp_box *box_in = nullptr;
+    float4 *cyl_filt = nullptr, *cyl_exact = nullptr, *box_c = nullptr, *box_h = nullptr;
+    float4 *basis = nullptr;
+    double *consts = nullptr;   // q0[4], qd[4], q_min[4], q_max[4]
+    double *mu = nullptr, *C = nullptr, *L = nullptr;
+    float *Lt = nullptr;
+    float *xi = nullptr;
+    double *J = nullptr, *terms = nullptr;
+    uint8_t *flag = nullptr;
+    float4 *partial = nullptr;
+    uint32_t *flagword = nullptr;
+    int *rank = nullptr, *elite = nullptr;
+    float *elites = nullptr;
+    double *w = nullptr, *mean_part = nullptr, *cov_part = nullptr;
+    double *best = nullptr;
+    uint32_t *status = nullptr;
+    double *ctrl = nullptr;
+    float *mean_xi = nullptr;
+    double *mean_J = nullptr, *mean_terms = nullptr;
+    uint8_t *mean_flag = nullptr;
+    bool have_endpoints = false;
+    float4 q0f{}, qdf{};
+    int iteration = 0;
+    Timer timer;
+};
+
+namespace {
+
+int validate_model(const cp_model *m)
+{
+    if (!m) return set_error("model is NULL"), CP_ERR_ARG;
+    if (m->n_spheres < 1 || m->n_spheres > CP_MAX_SPHERES)
+        return set_error("n_spheres %d outside 1..%d", m->n_spheres, CP_MAX_SPHERES), CP_ERR_ARG;
+    if (!is_finite(m->base_z) || !is_finite(m->boom_len) || !is_finite(m->jib_len))
+        return set_error("model lengths must be finite"), CP_ERR_ARG;
+    for (int j = 0; j < 4; ++j)
+        if (!is_finite(m->q_min[j]) || !is_finite(m->q_max[j]) || !(m->q_min[j] < m->q_max[j]))
+            return set_error("joint %d limits must be finite with q_min < q_max", j), CP_ERR_ARG;
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const cp_sphere &sp = m->spheres[s];
+        if (sp.link < 0 || sp.link > 3) return set_error("sphere %d: link %d outside 0..3", s, sp.link), CP_ERR_ARG;
+        if (!is_finite(sp.offset) || !(sp.radius > 0.0) || !is_finite(sp.radius))
+            return set_error("sphere %d: offset must be finite and radius > 0", s), CP_ERR_ARG;
+    }
+    return CP_OK;
+}
+
+int validate_scene(const cp_scene *sc)
+{
+    if (!sc) return set_error("scene is NULL"), CP_ERR_ARG;
+    if (sc->n_cyl < 0 || sc->n_box < 0) return set_error("negative obstacle count"), CP_ERR_ARG;
+    if (sc->n_cyl > 0 && !sc->cyl) return set_error("scene.cyl is NULL"), CP_ERR_ARG;
+    if (sc->n_box > 0 && !sc->box) return set_error("scene.box is NULL"), CP_ERR_ARG;
+    for (int i = 0; i < sc->n_cyl; ++i) {
+        const cp_cylinder &c = sc->cyl[i];
+        if (!is_finite(c.cx) || !is_finite(c.cy) || !is_finite(c.z_lo) || !is_finite(c.z_hi) ||
+            !(c.radius > 0.0) || !is_finite(c.radius) || !(c.z_lo <= c.z_hi))
+            return set_error("cylinder %d is invalid (radius > 0, z_lo <= z_hi, finite)", i), CP_ERR_ARG;
+    }
+    for (int i = 0; i < sc->n_box; ++i) {
+        const cp_box &b = sc->box[i];
+        for (int c = 0; c < 3; ++c)
+            if (!is_finite(b.lo[c]) || !is_finite(b.hi[c]) || !(b.lo[c] <= b.hi[c]))
+                return set_error("box %d is invalid (finite, lo <= hi)", i), CP_ERR_ARG;
+    }
+    return CP_OK;
+}
+
+int validate_params(const cp_params *p)
+{
+    if (!p) return set_error("params is NULL"), CP_ERR_ARG;
+    if (p->n_candidates < 2 || p->n_candidates > (1 << 22))
+        return set_error("n_candidates %d outside 2..%d", p->n_candidates, 1 << 22), CP_ERR_ARG;
+    if (p->n_waypoints < 1 || p->n_waypoints > CP_MAX_WAYPOINTS)
+        return set_error("n_waypoints %d outside 1..%d", p->n_waypoints, CP_MAX_WAYPOINTS), CP_ERR_ARG;
+    if (p->substeps < 1 || p->substeps > 4096)
+        return set_error("substeps %d outside 1..4096", p->substeps), CP_ERR_ARG;
+    if (p->n_elites < 0 || p->n_elites > p->n_candidates)
+        return set_error("n_elites %d outside 0..n_candidates", p->n_elites), CP_ERR_ARG;
+    if (!(p->sigma > 0.0) || !is_finite(p->sigma)) return set_error("sigma must be > 0"), CP_ERR_ARG;
+    if (!(p->eps >= 0.0) || !is_finite(p->eps)) return set_error("eps must be >= 0"), CP_ERR_ARG;
+    if (!(p->init_std_frac > 0.0) || !is_finite(p->init_std_frac))
+        return set_error("init_std_frac must be > 0"), CP_ERR_ARG;
+    if (!(p->w_c >= 0.0) || !(p->w_l >= 0.0) || !(p->lambda_c >= 0.0) || !is_finite(p->w_c) ||
+        !is_finite(p->w_l) || !is_finite(p->lambda_c))
+        return set_error("cost weights must be finite and >= 0"), CP_ERR_ARG;
+    if (p->max_cylinders < 0 || p->max_boxes < 0) return set_error("negative capacity"), CP_ERR_ARG;
+    const int64_t n_s = (int64_t)(p->n_waypoints + 3) * p->substeps;
+    if ((int64_t)p->n_candidates * ((n_s + 31) / 32) > 0x7FFFFFFF)
+        return set_error("n_candidates * ceil(n_s / 32) exceeds 2^31 - 1"), CP_ERR_ARG;
+    return CP_OK;
+}
+
+ModelDev make_model(const cp_model *m)
+{
+    ModelDev d{};
+    d.base_z = (float)m->base_z;
+    for (int j = 0; j < 4; ++j) {
+        d.q_min[j] = (float)m->q_min[j];
+        d.q_max[j] = (float)m->q_max[j];
+    }
+    d.n_spheres = m->n_spheres;
+    float r_max = 0.f;
+    for (int s = 0; s < kMaxSpheres; ++s) {
+        SphereLin l{0.f, 0.f, 0.f, 0.f, -1e30f};   // padding: never the nearest pair
+        if (s < m->n_spheres) {
+            const cp_sphere &sp = m->spheres[s];
+            const float t = (float)sp.offset, Lb = (float)m->boom_len, Lj = (float)m->jib_len;
+            switch (sp.link) {
+            case 0: l = {t, 0.f, 0.f, 0.f, 0.f}; break;
+            case 1: l = {Lb, t, 0.f, 0.f, 0.f}; break;
+            case 2: l = {Lb, Lj, t, 0.f, 0.f}; break;
+            default: l = {Lb, Lj, 1.f, t, 0.f}; break;
+            }
+            l.radius = (float)sp.radius;
+            if (l.radius > r_max) r_max = l.radius;
+        }
+        d.sph[s] = l;
+    }
+    d.r_max = r_max;
+    return d;
+}
+
+int stage_scene(cp_planner *p, const cp_scene *sc)
+{
+    if (sc->n_cyl > p->cap_cyl || sc->n_box > p->cap_box)
+        return set_error("scene (%d cylinders, %d boxes) exceeds the capacity (%d, %d) set at init",
+                         sc->n_cyl, sc->n_box, p->cap_cyl, p->cap_box), CP_ERR_ARG;
+    if (sc->n_cyl > 0)
+        CP_CUDA(cudaMemcpyAsync(p->cyl_in, sc->cyl, sizeof(cp_cylinder) * sc->n_cyl,
+                                cudaMemcpyHostToDevice, p->st));
+    if (sc->n_box > 0)
+        CP_CUDA(cudaMemcpyAsync(p->box_in, sc->box, sizeof(cp_box) * sc->n_box,
+                                cudaMemcpyHostToDevice, p->st));
+    int rc = launch_prepare_scene(p->cyl_in, sc->n_cyl, p->box_in, sc->n_box, p->mdev.r_max,
+                                  p->cyl_filt, p->cyl_exact, p->box_c, p->box_h, p->st);
+    if (rc != CP_OK) return rc;
+    p->sdev.n_cyl = sc->n_cyl;
+    p->sdev.n_box = sc->n_box;
+    return CP_OK;
+}
+
+int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_flag,
+             double *d_terms, uint32_t *d_words, float *d_pen)
+{
+    EvalArgs a{};
+    a.xi = (const float4 *)d_xi;
+    a.n = n;
+    a.K = p->K;
+    a.S = p->S;
+    a.n_s = p->n_s;
+    a.chunks = p->chunks;
+    a.q0 = p->q0f;
+    a.qd = p->qdf;
+    a.basis = p->basis;
+    a.partial = p->partial;
+    a.flagword = p->flagword;
+    a.pen_out = d_pen;
+    int rc = p->timer.begin(p->st);
+    if (rc != CP_OK) return rc;
+    rc = launch_eval(p->mdev, p->sdev, a, p->num_sms, p->st);
+    if (rc != CP_OK) return rc;
+    rc = p->timer.end(ST_EVAL, p->st);
+    if (rc != CP_OK) return rc;
+    return launch_eval_finalize(p->partial, p->flagword, n, p->chunks, p->prm.w_c, p->prm.w_l,
+                                p->prm.lambda_c, d_J, d_flag, d_terms, d_words, p->st);
+}
+
+int run_factor(cp_planner *p)
+{
+    int rc = p->timer.begin(p->st);
+    if (rc != CP_OK) return rc;
+    rc = launch_factor(p->C, p->prm.sigma * p->prm.sigma, p->D, p->L, p->Lt, p->status, p->st);
+    if (rc != CP_OK) return rc;
+    return p->timer.end(ST_FACTOR, p->st);
+}
+
+int run_sample(cp_planner *p, int iter, float *d_xi)
+{
+    int rc = p->timer.begin(p->st);
+    if (rc != CP_OK) return rc;
+    rc = launch_sample(p->mu, p->Lt, p->N, p->K, p->prm.seed, (uint32_t)iter, p->prm.query, d_xi,
+                       p->st);
+    if (rc != CP_OK) return rc;
+    return p->timer.end(ST_SAMPLE, p->st);
+}
+
+int run_update(cp_planner *p, const double *d_J, const float *d_xi)
+{
+    int rc = p->timer.begin(p->st);
+    if (rc != CP_OK) return rc;
+    CP_CUDA(cudaMemsetAsync(p->rank, 0, sizeof(int) * p->N, p->st));
+    if ((rc = launch_rank(d_J, p->N, p->nu, p->rank, p->st)) != CP_OK) return rc;
+    if ((rc = launch_scatter(p->rank, d_J, d_xi, p->N, p->nu, p->D, p->elite, p->elites, p->best,
+                             p->st)) != CP_OK)
+        return rc;
+    if ((rc = launch_mean(p->elites, p->w, p->nu, p->D, p->mean_part, p->mu, p->st)) != CP_OK)
+        return rc;
+    if ((rc = launch_cov(p->elites, p->w, p->mu, p->nu, p->D, p->prm.eps, p->cov_part, p->C,
+                         p->st)) != CP_OK)
+        return rc;
+    if ((rc = p->timer.end(ST_UPDATE, p->st)) != CP_OK) return rc;
+    if ((rc = run_factor(p)) != CP_OK) return rc;
+    p->iteration += 1;
+    return CP_OK;
+}
+
+int check_status(cp_planner *p)
+{
+    uint32_t s = 0;
+    CP_CUDA(cudaMemcpyAsync(&s, p->status, sizeof s, cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaStreamSynchronize(p->st));
+    if (s & DEV_ERR_NOT_PD) {
+        CP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(uint32_t), p->st));
+        return set_error("the covariance is not positive definite (Cholesky pivot <= 0)"), CP_ERR_NUMERIC;
+    }
+    if (s & DEV_ERR_TIMEOUT) {
+        CP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(uint32_t), p->st));
+        return set_error("a bounded device wait gave up"), CP_ERR_TIMEOUT;
+    }
+    return CP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cp_last_error(void) { return g_err; }
+
+int32_t cp_version(void) { return CP_VERSION; }
+
+int64_t cp_launch_count(void) { return g_launches.load(); }
+
+int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *params,
+                 void *stream, cp_planner **out)
+{
+    g_err[0] = 0;
+    if (!out) return set_error("out is NULL"), CP_ERR_ARG;
+    *out = nullptr;
+    int rc;
+    if ((rc = validate_model(model)) != CP_OK) return rc;
+    if ((rc = validate_scene(scene)) != CP_OK) return rc;
+    if ((rc = validate_params(params)) != CP_OK) return rc;
+
+    cp_planner *p = new (std::nothrow) cp_planner();
+    if (!p) return set_error("host allocation failed"), CP_ERR_OOM;
+    p->st = (cudaStream_t)stream;
+    p->prm = *params;
+    p->N = params->n_candidates;
+    p->K = params->n_waypoints;
+    p->S = params->substeps;
+    p->D = 4 * p->K;
+    p->n_s = (p->K + 3) * p->S;
+    p->chunks = (p->n_s + 31) / 32;
+    p->nu = params->n_elites > 0 ? params->n_elites : p->N / 2;
+    if (p->nu < 1) p->nu = 1;
+    p->n_mean_chunks = (p->nu + update_chunk_size() - 1) / update_chunk_size();
+    p->cap_cyl = params->max_cylinders > scene->n_cyl ? params->max_cylinders : scene->n_cyl;
+    p->cap_box = params->max_boxes > scene->n_box ? params->max_boxes : scene->n_box;
+    p->mdev = make_model(model);
+
+    auto fail = [&](int code) {
+        if (p->base) cudaFree(p->base);
+        delete p;
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice"));
+    e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    int smem_optin = 0;
+    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    const size_t eval_smem = eval_smem_bytes(p->cap_cyl, p->cap_box, p->S);
+    if (eval_smem > (size_t)smem_optin) {
+        set_error("scene capacity (%d cylinders, %d boxes) needs %zu B of shared memory; the "
+                  "device allows %d B per block", p->cap_cyl, p->cap_box, eval_smem, smem_optin);
+        return fail(CP_ERR_ARG);
+    }
+    if ((rc = eval_configure(eval_smem > 48 * 1024 ? eval_smem : 48 * 1024)) != CP_OK) return fail(rc);
+    if ((rc = factor_configure()) != CP_OK) return fail(rc);
+    if ((rc = sample_configure()) != CP_OK) return fail(rc);
+
+    const size_t N = p->N, D = p->D, nu = p->nu, ch = p->chunks, mc = p->n_mean_chunks;
+    Layout L;
+    const size_t o_cyl_in = L.take<cp_cylinder>(p->cap_cyl + 1);
+    const size_t o_box_in = L.take<cp_box>(p->cap_box + 1);
+    const size_t o_filt = L.take<float4>(p->cap_cyl + 1);
+    const size_t o_exact = L.take<float4>(p->cap_cyl + 1);
+    const size_t o_bc = L.take<float4>(p->cap_box + 1);
+    const size_t o_bh = L.take<float4>(p->cap_box + 1);
+    const size_t o_basis = L.take<float4>(2 * (size_t)p->S);
+    const size_t o_consts = L.take<double>(16);
+    const size_t o_mu = L.take<double>(D);
+    const size_t o_C = L.take<double>(D * D);
+    const size_t o_L = L.take<double>(D * D);
+    const size_t o_Lt = L.take<float>(D * D);
+    const size_t o_xi = L.take<float>(N * D);
+    const size_t o_J = L.take<double>(N);
+    const size_t o_terms = L.take<double>(N * 5);
+    const size_t o_flag = L.take<uint8_t>(N);
+    const size_t o_partial = L.take<float4>(N * ch);
+    const size_t o_flagword = L.take<uint32_t>(N * ch);
+    const size_t o_rank = L.take<int>(N);
+    const size_t o_elite = L.take<int>(nu);
+    const size_t o_elites = L.take<float>(nu * D);
+    const size_t o_w = L.take<double>(nu);
+    const size_t o_mean_part = L.take<double>(mc * D);
+    const size_t o_cov_part = L.take<double>(mc * D * D);
+    const size_t o_best = L.take<double>(1);
+    const size_t o_status = L.take<uint32_t>(1);
+    const size_t o_ctrl = L.take<double>(4 * ((size_t)p->K + 8));
+    const size_t o_mean_xi = L.take<float>(D);
+    const size_t o_mean_J = L.take<double>(1);
+    const size_t o_mean_terms = L.take<double>(5);
+    const size_t o_mean_flag = L.take<uint8_t>(1);
+    e = cudaMalloc((void **)&p->base, L.bytes);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(workspace)"));
+    char *b = p->base;
+    p->cyl_in = (cp_cylinder *)(b + o_cyl_in);
+    p->box_in = (cp_box *)(b + o_box_in);
+    p->cyl_filt = (float4 *)(b + o_filt);
+    p->cyl_exact = (float4 *)(b + o_exact);
+    p->box_c = (float4 *)(b + o_bc);
+    p->box_h = (float4 *)(b + o_bh);
+    p->basis = (float4 *)(b + o_basis);
+    p->consts = (double *)(b + o_consts);
+    p->mu = (double *)(b + o_mu);
+    p->C = (double *)(b + o_C);
+    p->L = (double *)(b + o_L);
+    p->Lt = (float *)(b + o_Lt);
+    p->xi = (float *)(b + o_xi);
+    p->J = (double *)(b + o_J);
+    p->terms = (double *)(b + o_terms);
+    p->flag = (uint8_t *)(b + o_flag);
+    p->partial = (float4 *)(b + o_partial);
+    p->flagword = (uint32_t *)(b + o_flagword);
+    p->rank = (int *)(b + o_rank);
+    p->elite = (int *)(b + o_elite);
+    p->elites = (float *)(b + o_elites);
+    p->w = (double *)(b + o_w);
+    p->mean_part = (double *)(b + o_mean_part);
+    p->cov_part = (double *)(b + o_cov_part);
+    p->best = (double *)(b + o_best);
+    p->status = (uint32_t *)(b + o_status);
+    p->ctrl = (double *)(b + o_ctrl);
+    p->mean_xi = (float *)(b + o_mean_xi);
+    p->mean_J = (double *)(b + o_mean_J);
+    p->mean_terms = (double *)(b + o_mean_terms);
+    p->mean_flag = (uint8_t *)(b + o_mean_flag);
+    p->sdev.cyl_filt = p->cyl_filt;
+    p->sdev.cyl_exact = p->cyl_exact;
+    p->sdev.box_c = p->box_c;
+    p->sdev.box_h = p->box_h;
+
+    e = cudaMemsetAsync(p->base, 0, L.bytes, p->st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(workspace)"));
+    double lim[8];
+    for (int j = 0; j < 4; ++j) {
+        lim[j] = model->q_min[j];
+        lim[4 + j] = model->q_max[j];
+    }
+    e = cudaMemcpyAsync(p->consts + 8, lim, sizeof lim, cudaMemcpyHostToDevice, p->st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpyAsync(limits)"));
+    if ((rc = stage_scene(p, scene)) != CP_OK) return fail(rc);
+    if ((rc = launch_basis_table(p->S, p->basis, p->st)) != CP_OK) return fail(rc);
+    if ((rc = launch_weights(p->nu, p->w, p->st)) != CP_OK) return fail(rc);
+    e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamSynchronize(init)"));
+    *out = p;
+    return CP_OK;
+}
+
+void cp_destroy(cp_planner *p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(p->st);
+    p->timer.destroy();
+    if (p->base) cudaFree(p->base);
+    delete p;
+}
+
+int cp_set_scene(cp_planner *p, const cp_scene *scene)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    int rc = validate_scene(scene);
+    if (rc != CP_OK) return rc;
+    return stage_scene(p, scene);
+}
+
+int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4])
+{
+    if (!p || !h_q0 || !h_qd) return set_error("NULL argument"), CP_ERR_ARG;
+    for (int j = 0; j < 4; ++j)
+        if (!is_finite(h_q0[j]) || !is_finite(h_qd[j])) return set_error("end points must be finite"), CP_ERR_ARG;
+    double ends[8];
+    memcpy(ends, h_q0, 4 * sizeof(double));
+    memcpy(ends + 4, h_qd, 4 * sizeof(double));
+    CP_CUDA(cudaMemcpyAsync(p->consts, ends, sizeof ends, cudaMemcpyHostToDevice, p->st));
+    p->q0f = make_float4((float)h_q0[0], (float)h_q0[1], (float)h_q0[2], (float)h_q0[3]);
+    p->qdf = make_float4((float)h_qd[0], (float)h_qd[1], (float)h_qd[2], (float)h_qd[3]);
+    int rc = launch_init_distribution(p->consts, p->consts + 4, p->consts + 8, p->consts + 12, p->K,
+                                      p->prm.init_std_frac, p->mu, p->C, p->st);
+    if (rc != CP_OK) return rc;
+    p->iteration = 0;
+    p->have_endpoints = true;
+    return run_factor(p);
+}
+
+int cp_sample(cp_planner *p, int32_t iter, float *d_xi)
+{
+    if (!p || !d_xi) return set_error("NULL argument"), CP_ERR_ARG;
+    if (iter < 0) return set_error("iteration must be >= 0"), CP_ERR_ARG;
+    if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
+    return run_sample(p, iter, d_xi);
+}
+
+int cp_evaluate(cp_planner *p, const float *d_xi, int32_t n, double *d_J, uint8_t *d_flag,
+                double *d_terms, uint32_t *d_substep_flags, float *d_pen)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (n < 0 || n > p->N) return set_error("n = %d outside 0..N = %d", n, p->N), CP_ERR_ARG;
+    if (n > 0 && (!d_xi || !d_J)) return set_error("d_xi and d_J are required"), CP_ERR_ARG;
+    if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
+    if (n == 0) return CP_OK;
+    return run_eval(p, d_xi, n, d_J, d_flag, d_terms, d_substep_flags, d_pen);
+}
+
+int cp_update(cp_planner *p, const double *d_J, const float *d_xi)
+{
+    if (!p || !d_J || !d_xi) return set_error("NULL argument"), CP_ERR_ARG;
+    if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
+    return run_update(p, d_J, d_xi);
+}
+
+int cp_plan(cp_planner *p, int32_t iters, double *h_ctrl, cp_plan_stats *stats)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (iters < 0) return set_error("iters must be >= 0"), CP_ERR_ARG;
+    if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
+    int rc;
+    for (int it = 0; it < iters; ++it) {
+        if ((rc = run_sample(p, p->iteration, p->xi)) != CP_OK) return rc;
+        if ((rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr)) != CP_OK) return rc;
+        if ((rc = run_update(p, p->J, p->xi)) != CP_OK) return rc;
+    }
+    if ((rc = launch_mean_to_candidate(p->mu, p->D, p->mean_xi, p->st)) != CP_OK) return rc;
+    if ((rc = run_eval(p, p->mean_xi, 1, p->mean_J, p->mean_flag, p->mean_terms, nullptr, nullptr)) != CP_OK)
+        return rc;
+    if ((rc = launch_control_points(p->consts, p->consts + 4, p->mu, p->K, p->ctrl, p->st)) != CP_OK)
+        return rc;
+    double host[8];
+    CP_CUDA(cudaMemcpyAsync(host, p->mean_J, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaMemcpyAsync(host + 1, p->mean_terms, 5 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaMemcpyAsync(host + 6, p->best, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    if (h_ctrl)
+        CP_CUDA(cudaMemcpyAsync(h_ctrl, p->ctrl, sizeof(double) * 4 * (p->K + 8),
+                                cudaMemcpyDeviceToHost, p->st));
+    if ((rc = check_status(p)) != CP_OK) return rc;   // synchronises
+    if (stats) {
+        stats->J = host[0];
+        stats->Jp = host[1];
+        stats->Jc = host[2];
+        stats->Jl = host[3];
+        stats->length = host[4];
+        stats->n_flagged = (int32_t)host[5];
+        stats->flag = stats->n_flagged > 0;
+        stats->iterations = iters;
+        stats->iteration = p->iteration;
+        stats->best_J = host[6];
+    }
+    return CP_OK;
+}
+
+int cp_signed_distance(cp_planner *p, const float *d_q, int32_t n, float *d_d)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (n < 0 || (n > 0 && (!d_q || !d_d))) return set_error("invalid arguments"), CP_ERR_ARG;
+    return launch_signed_distance(p->mdev, p->sdev, d_q, n, d_d, p->st);
+}
+
+int cp_get_distribution(const cp_planner *p, double *d_mu, double *d_C)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (d_mu) CP_CUDA(cudaMemcpyAsync(d_mu, p->mu, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
+    if (d_C)
+        CP_CUDA(cudaMemcpyAsync(d_C, p->C, sizeof(double) * p->D * p->D, cudaMemcpyDeviceToDevice, p->st));
+    return CP_OK;
+}
+
+int cp_set_distribution(cp_planner *p, const double *d_mu, const double *d_C, int32_t iter)
+{
+    if (!p || !d_mu || !d_C) return set_error("NULL argument"), CP_ERR_ARG;
+    if (iter < 0) return set_error("iteration must be >= 0"), CP_ERR_ARG;
+    if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
+    CP_CUDA(cudaMemcpyAsync(p->mu, d_mu, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
+    CP_CUDA(cudaMemcpyAsync(p->C, d_C, sizeof(double) * p->D * p->D, cudaMemcpyDeviceToDevice, p->st));
+    p->iteration = iter;
+    return run_factor(p);
+}
+
+int cp_get_factor(const cp_planner *p, double *d_L)
+{
+    if (!p || !d_L) return set_error("NULL argument"), CP_ERR_ARG;
+    CP_CUDA(cudaMemcpyAsync(d_L, p->L, sizeof(double) * p->D * p->D, cudaMemcpyDeviceToDevice, p->st));
+    return CP_OK;
+}
+
+int cp_get_elites(const cp_planner *p, int32_t *d_idx)
+{
+    if (!p || !d_idx) return set_error("NULL argument"), CP_ERR_ARG;
+    CP_CUDA(cudaMemcpyAsync(d_idx, p->elite, sizeof(int32_t) * p->nu, cudaMemcpyDeviceToDevice, p->st));
+    return CP_OK;
+}
+
+int cp_philox4x32_10(const uint32_t *d_ctr, uint64_t key, int64_t n, uint32_t *d_out, void *stream)
+{
+    if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return set_error("invalid arguments"), CP_ERR_ARG;
+    return launch_philox(d_ctr, (uint32_t)key, (uint32_t)(key >> 32), n, d_out, (cudaStream_t)stream);
+}
+
+int cp_set_timing(cp_planner *p, int32_t on)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    CP_CUDA(cudaStreamSynchronize(p->st));
+    p->timer.clear();
+    p->timer.on = on != 0;
+    return CP_OK;
+}
+
+int cp_get_timing(cp_planner *p, cp_timing *out)
+{
+    if (!p || !out) return set_error("NULL argument"), CP_ERR_ARG;
+    CP_CUDA(cudaStreamSynchronize(p->st));
+    double ms[ST_COUNT] = {0, 0, 0, 0};
+    int64_t cnt[ST_COUNT] = {0, 0, 0, 0};
+    for (int s = 0; s < ST_COUNT; ++s) {
+        for (auto &pr : p->timer.spans[s]) {
+            float t = 0.f;
+            CP_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+            ms[s] += t;
+            cnt[s] += 1;
+        }
+    }
+    out->eval_ms = ms[ST_EVAL];
+    out->eval_launches = cnt[ST_EVAL];
+    out->sample_ms = ms[ST_SAMPLE];
+    out->sample_launches = cnt[ST_SAMPLE];
+    out->factor_ms = ms[ST_FACTOR];
+    out->factor_launches = cnt[ST_FACTOR];
+    out->update_ms = ms[ST_UPDATE];
+    out->update_launches = cnt[ST_UPDATE];
+    p->timer.clear();
+    return CP_OK;
+}
+
+int cp_synchronize(cp_planner *p)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    return check_status(p);
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal declarations of the craneplan CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/craneplan.h"
+
+namespace cp {
+
+// ------------------------------------------------------------------ error plumbing
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+void count_launch();
+
+#define CP_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::cp::cuda_fail(e_, #call);  \
+    } while (0)
+
+#define CP_LAUNCHED(what)                                          \
+    do {                                                           \
+        ::cp::count_launch();                                      \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return ::cp::cuda_fail(e_, what);   \
+    } while (0)
+
+// Status word written by kernels (0 = fine). Bits:
+enum : uint32_t {
+    DEV_ERR_TIMEOUT = 1u,      // a bounded wait gave up
+    DEV_ERR_NOT_PD = 2u,       // Cholesky met a non-positive pivot
+};
+
+// ------------------------------------------------------------------ geometry records
+
+// Sphere placement in the linear form used by the kernels:
+//   centre = O + alpha e_b + (beta + gamma q4) e_j - delta z
+struct SphereLin {
+    float alpha, beta, gamma, delta, radius;
+};
+
+constexpr int kMaxSpheres = CP_MAX_SPHERES;
+
+struct ModelDev {
+    float base_z;
+    float q_min[4], q_max[4];
+    int n_spheres;
+    float r_max;                       // largest sphere radius (filter bound)
+    SphereLin sph[kMaxSpheres];
+};
+
+// Cylinder records in device memory (float32):
+//   filt[o]  = {cx, cy, W, 0}, W = cx^2 + cy^2 - (R + r_max)^2 (rounded from fp64)
+//   exact[o] = {R, z_lo, z_hi, 0}
+// Box records: centre {cx, cy, cz, 0} and half extent {hx, hy, hz, 0}.
+struct SceneDev {
+    const float4 *cyl_filt;
+    const float4 *cyl_exact;
+    int n_cyl;
+    const float4 *box_c;
+    const float4 *box_h;
+    int n_box;
+};
+
+// Margin of the fast 2-D cylinder filter, in m^2: a pair reaches the exact distance test
+// when (rho^2 - (R + r_max)^2), evaluated in float32 in expanded form, is below it. The
+// rounding error of that form for a pair within reach of the crane is below 3e-4 m^2.
+constexpr float kFilterMargin = 2.0e-3f;
+
+// ------------------------------------------------------------------ launchers
+
+struct EvalArgs {
+    const float4 *xi;           // [n][K]
+    int n, K, S, n_s, chunks;   // chunks = ceil(n_s / 32)
+    float4 q0, qd;
+    const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
+    float4 *partial;            // [n][chunks] {J_p, sum pen, J_l, length} (float)
+    uint32_t *flagword;         // [n][chunks]
+    float *pen_out;             // optional [n][n_s]
+};
+
+int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
+                cudaStream_t st);
+int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n, int chunks,
+                         double w_c, double w_l, double lambda_c, double *J, uint8_t *flag,
+                         double *terms, uint32_t *substep_flags, cudaStream_t st);
+int launch_signed_distance(const ModelDev &m, const SceneDev &sc, const float *q, int n,
+                           float *d, cudaStream_t st);
+size_t eval_smem_bytes(int n_cyl, int n_box, int S);
+int eval_configure(size_t smem_bytes);
+
+int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d_box_in,
+                         int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact,
+                         float4 *box_c, float4 *box_h, cudaStream_t st);
+int launch_basis_table(int S, float4 *basis, cudaStream_t st);
+int launch_init_distribution(const double *q0, const double *qd, const double *q_min,
+                             const double *q_max, int K, double init_std_frac, double *mu,
+                             double *C, cudaStream_t st);
+int launch_mean_to_candidate(const double *mu, int D, float *xi, cudaStream_t st);
+int launch_control_points(const double *q0, const double *qd, const double *mu, int K,
+                          double *ctrl, cudaStream_t st);
+
+int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out,
+                  cudaStream_t st);
+int launch_factor(const double *C, double sigma2, int D, double *L, float *Lt_f,
+                  uint32_t *status, cudaStream_t st);
+int factor_configure();
+int launch_sample(const double *mu, const float *Lt_f, int N, int K, uint64_t seed,
+                  uint32_t iter, uint32_t query, float *xi, cudaStream_t st);
+int sample_configure();
+
+int launch_weights(int nu, double *w, cudaStream_t st);
+int launch_rank(const double *J, int N, int nu, int *rank, cudaStream_t st);
+int launch_scatter(const int *rank, const double *J, const float *xi, int N, int nu, int D,
+                   int *elite, float *elites, double *best_J, cudaStream_t st);
+int launch_mean(const float *elites, const double *w, int nu, int D, double *partial,
+                double *mu, cudaStream_t st);
+int launch_cov(const float *elites, const double *w, const double *mu, int nu, int D,
+               double eps, double *partial, double *C, cudaStream_t st);
+int update_chunk_size();
+
+}  // namespace cp

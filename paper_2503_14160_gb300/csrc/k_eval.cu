@@ -1,0 +1,313 @@
+// Algorithm 1 step (2) on the GPU: for every candidate path, the cubic B-spline at the
+// n_s checkpoints, the crane kinematics, the link-sphere vs obstacle signed distance and
+// the three cost terms of Eq. path opt (arXiv 2503.14160, Sec. 4.1; d(q) of Sec. 3.1).
+//
+// Work decomposition: a work unit is (candidate, chunk of 32 consecutive checkpoints); a
+// warp takes one unit at a time, one checkpoint per lane, so the 32 lanes of a warp read
+// the same one or two spline spans (float4 control points, broadcast loads). All
+// obstacles are staged once per CTA in shared memory. Per checkpoint and link sphere the
+// obstacle loop is a 2-FMA power test against every cylinder; only pairs that pass it
+// (sphere within reach of the cylinder) take the exact capped-cylinder distance. Per
+// unit, lane values are reduced with warp shuffles (FP32) into one partial per unit; a
+// second kernel sums each candidate's partials in a fixed order in FP64.
+#include <math_constants.h>
+
+#include "cp_internal.cuh"
+
+namespace cp {
+namespace {
+
+constexpr int kEvalThreads = 256;
+
+__device__ __forceinline__ float sdf_cylinder(float x, float y, float z, float cx, float cy,
+                                              float4 e /* R, z_lo, z_hi */)
+{
+    const float dx = x - cx, dy = y - cy;
+    const float rho = sqrtf(fmaf(dx, dx, dy * dy));
+    const float a = rho - e.x;
+    const float b = fmaxf(e.y - z, z - e.z);
+    const float ap = fmaxf(a, 0.f), bp = fmaxf(b, 0.f);
+    return fminf(fmaxf(a, b), 0.f) + sqrtf(fmaf(ap, ap, bp * bp));
+}
+
+__device__ __forceinline__ float sdf_box(float x, float y, float z, float4 c, float4 h)
+{
+    const float qx = fabsf(x - c.x) - h.x;
+    const float qy = fabsf(y - c.y) - h.y;
+    const float qz = fabsf(z - c.z) - h.z;
+    const float px = fmaxf(qx, 0.f), py = fmaxf(qy, 0.f), pz = fmaxf(qz, 0.f);
+    return sqrtf(fmaf(px, px, fmaf(py, py, pz * pz))) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+}
+
+// Sphere centres at configuration q (chain of Sec. 2 in the linear placement form).
+template <int NSPH>
+__device__ __forceinline__ void crane_fk(const ModelDev &m, float4 q, float *x, float *y,
+                                         float *z)
+{
+    float s1, c1, s2, c2, s23, c23;
+    sincosf(q.x, &s1, &c1);
+    sincosf(q.y, &s2, &c2);
+    sincosf(q.y + q.z, &s23, &c23);
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s) {
+        const SphereLin sp = m.sph[s];
+        const float b = fmaf(sp.gamma, q.w, sp.beta);
+        const float h = fmaf(sp.alpha, c2, b * c23);
+        x[s] = c1 * h;
+        y[s] = s1 * h;
+        z[s] = m.base_z + fmaf(sp.alpha, s2, fmaf(b, s23, -sp.delta));
+    }
+}
+
+__device__ __forceinline__ float4 combine4(float4 w, float4 p0, float4 p1, float4 p2, float4 p3)
+{
+    float4 r;
+    r.x = fmaf(w.x, p0.x, fmaf(w.y, p1.x, fmaf(w.z, p2.x, w.w * p3.x)));
+    r.y = fmaf(w.x, p0.y, fmaf(w.y, p1.y, fmaf(w.z, p2.y, w.w * p3.y)));
+    r.z = fmaf(w.x, p0.z, fmaf(w.y, p1.z, fmaf(w.z, p2.z, w.w * p3.z)));
+    r.w = fmaf(w.x, p0.w, fmaf(w.y, p1.w, fmaf(w.z, p2.w, w.w * p3.w)));
+    return r;
+}
+
+__device__ __forceinline__ float limit_excess(float v, float lo, float hi)
+{
+    const float a = fmaxf(0.f, v - hi), b = fmaxf(0.f, lo - v);
+    return fmaf(a, a, b * b);
+}
+
+template <int NSPH>
+__global__ void __launch_bounds__(kEvalThreads)
+k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
+{
+    extern __shared__ __align__(16) float4 smem[];
+    float4 *s_filt = smem;
+    float4 *s_exact = s_filt + sc.n_cyl;
+    float4 *s_bc = s_exact + sc.n_cyl;
+    float4 *s_bh = s_bc + sc.n_box;
+    float4 *s_basis = s_bh + sc.n_box;
+    for (int i = threadIdx.x; i < sc.n_cyl; i += blockDim.x) {
+        s_filt[i] = sc.cyl_filt[i];
+        s_exact[i] = sc.cyl_exact[i];
+    }
+    for (int i = threadIdx.x; i < sc.n_box; i += blockDim.x) {
+        s_bc[i] = sc.box_c[i];
+        s_bh[i] = sc.box_h[i];
+    }
+    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x) s_basis[i] = a.basis[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int units = a.n * a.chunks;
+
+    for (int u = warp; u < units; u += n_warps) {
+        const int cand = u / a.chunks;
+        const int chunk = u - cand * a.chunks;
+        const int k = chunk * 32 + lane + 1;          // checkpoint index, 1..n_s
+        const bool valid = k <= a.n_s;
+        const int kc = valid ? k : a.n_s;
+        const int span = (kc - 1) / a.S;              // moving span - 1, 0..K+2
+        const int mstep = kc - span * a.S;            // 1..S within the span
+
+        // control points P_{span+1..span+4} of [q0 x4, xi (K), qd x4]
+        const float4 *xi = a.xi + (size_t)cand * a.K;
+        float4 P[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int g = span + 1 + i;
+            P[i] = g < 4 ? a.q0 : (g >= a.K + 4 ? a.qd : __ldg(xi + (g - 4)));
+        }
+        const float4 bw = s_basis[2 * (mstep - 1)];
+        const float4 dbw = s_basis[2 * (mstep - 1) + 1];
+        const float4 q = combine4(bw, P[0], P[1], P[2], P[3]);
+        const float4 dq = combine4(dbw, P[0], P[1], P[2], P[3]);   // q(s_k) - q(s_{k-1})
+
+        const float jp = fmaf(dq.x, dq.x, fmaf(dq.y, dq.y, fmaf(dq.z, dq.z, dq.w * dq.w)));
+        const float len = sqrtf(jp);
+        const float jl = limit_excess(q.x, m.q_min[0], m.q_max[0]) +
+                         limit_excess(q.y, m.q_min[1], m.q_max[1]) +
+                         limit_excess(q.z, m.q_min[2], m.q_max[2]) +
+                         limit_excess(q.w, m.q_min[3], m.q_max[3]);
+
+        float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH];
+        crane_fk<NSPH>(m, q, X, Y, Z);
+#pragma unroll
+        for (int s = 0; s < NSPH; ++s) {
+            T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
+            X[s] *= -2.f;   // exact; -0.5 X recovers x
+            Y[s] *= -2.f;
+        }
+
+        float dmin = CUDART_INF_F;
+        for (int o = 0; o < sc.n_cyl; ++o) {
+            const float4 f = s_filt[o];
+#pragma unroll
+            for (int s = 0; s < NSPH; ++s) {
+                // rho^2 - (R + r_max)^2 - x^2 - y^2 in expanded form (2 FMA)
+                const float g = fmaf(X[s], f.x, fmaf(Y[s], f.y, f.z));
+                if (g < T[s]) {
+                    const float d = sdf_cylinder(-0.5f * X[s], -0.5f * Y[s], Z[s], f.x, f.y,
+                                                 s_exact[o]) - m.sph[s].radius;
+                    dmin = fminf(dmin, d);
+                }
+            }
+        }
+        for (int o = 0; o < sc.n_box; ++o) {
+            const float4 c = s_bc[o], h = s_bh[o];
+#pragma unroll
+            for (int s = 0; s < NSPH; ++s)
+                dmin = fminf(dmin, sdf_box(-0.5f * X[s], -0.5f * Y[s], Z[s], c, h) -
+                                       m.sph[s].radius);
+        }
+
+        const float pen = fmaxf(0.f, -dmin);
+        const bool hit = valid && (dmin < 0.f);
+        float v0 = valid ? jp : 0.f, v1 = valid ? pen : 0.f;
+        float v2 = valid ? jl : 0.f, v3 = valid ? len : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+            v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+            v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+            v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) {
+            a.partial[u] = make_float4(v0, v1, v2, v3);
+            a.flagword[u] = word;
+        }
+        if (a.pen_out != nullptr && valid) a.pen_out[(size_t)cand * a.n_s + (k - 1)] = pen;
+    }
+}
+
+__global__ void k_eval_finalize(const float4 *__restrict__ partial,
+                                const uint32_t *__restrict__ flagword, int n, int chunks,
+                                double w_c, double w_l, double lambda_c, double *J,
+                                uint8_t *flag, double *terms, uint32_t *substep_flags)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double jp = 0.0, jc = 0.0, jl = 0.0, len = 0.0;
+    int n_flagged = 0;
+    for (int c = 0; c < chunks; ++c) {
+        const float4 v = partial[(size_t)i * chunks + c];
+        const uint32_t w = flagword[(size_t)i * chunks + c];
+        jp += (double)v.x;
+        jc += (double)v.y;
+        jl += (double)v.z;
+        len += (double)v.w;
+        n_flagged += __popc(w);
+        if (substep_flags != nullptr) substep_flags[(size_t)i * chunks + c] = w;
+    }
+    jc *= lambda_c;
+    J[i] = jp + w_c * jc + w_l * jl;
+    if (flag != nullptr) flag[i] = n_flagged > 0 ? 1 : 0;
+    if (terms != nullptr) {
+        double *t = terms + (size_t)i * 5;
+        t[0] = jp;
+        t[1] = jc;
+        t[2] = jl;
+        t[3] = len;
+        t[4] = (double)n_flagged;
+    }
+}
+
+// d(q) for single configurations: every pair, exact distances (no filter).
+template <int NSPH>
+__global__ void k_signed_distance(const ModelDev m, const SceneDev sc, const float *q, int n,
+                                  float *d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 qi = make_float4(q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]);
+    float x[NSPH], y[NSPH], z[NSPH];
+    crane_fk<NSPH>(m, qi, x, y, z);
+    float dmin = CUDART_INF_F;
+    for (int o = 0; o < sc.n_cyl; ++o) {
+        const float4 f = sc.cyl_filt[o], e = sc.cyl_exact[o];
+#pragma unroll
+        for (int s = 0; s < NSPH; ++s)
+            dmin = fminf(dmin, sdf_cylinder(x[s], y[s], z[s], f.x, f.y, e) - m.sph[s].radius);
+    }
+    for (int o = 0; o < sc.n_box; ++o) {
+        const float4 c = sc.box_c[o], h = sc.box_h[o];
+#pragma unroll
+        for (int s = 0; s < NSPH; ++s)
+            dmin = fminf(dmin, sdf_box(x[s], y[s], z[s], c, h) - m.sph[s].radius);
+    }
+    d[i] = dmin;
+}
+
+template <int NSPH>
+int eval_grid(size_t smem, int num_sms, int units)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<NSPH>,
+                                                                  kEvalThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int warps_per_block = kEvalThreads / 32;
+    const int needed = (units + warps_per_block - 1) / warps_per_block;
+    int grid = num_sms * per_sm;
+    if (grid > needed) grid = needed;
+    return grid < 1 ? 1 : grid;
+}
+
+}  // namespace
+
+size_t eval_smem_bytes(int n_cyl, int n_box, int S)
+{
+    return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S);
+}
+
+int eval_configure(size_t smem_bytes)
+{
+    CP_CUDA(cudaFuncSetAttribute(k_eval<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes));
+    CP_CUDA(cudaFuncSetAttribute(k_eval<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes));
+    return CP_OK;
+}
+
+int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
+                cudaStream_t st)
+{
+    const int units = a.n * a.chunks;
+    if (units == 0) return CP_OK;
+    const size_t smem = eval_smem_bytes(sc.n_cyl, sc.n_box, a.S);
+    if (m.n_spheres == 12) {
+        k_eval<12><<<eval_grid<12>(smem, num_sms, units), kEvalThreads, smem, st>>>(m, sc, a);
+    } else {
+        k_eval<16><<<eval_grid<16>(smem, num_sms, units), kEvalThreads, smem, st>>>(m, sc, a);
+    }
+    CP_LAUNCHED("k_eval");
+    return CP_OK;
+}
+
+int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n, int chunks,
+                         double w_c, double w_l, double lambda_c, double *J, uint8_t *flag,
+                         double *terms, uint32_t *substep_flags, cudaStream_t st)
+{
+    if (n == 0) return CP_OK;
+    const int threads = 128;
+    k_eval_finalize<<<(n + threads - 1) / threads, threads, 0, st>>>(
+        partial, flagword, n, chunks, w_c, w_l, lambda_c, J, flag, terms, substep_flags);
+    CP_LAUNCHED("k_eval_finalize");
+    return CP_OK;
+}
+
+int launch_signed_distance(const ModelDev &m, const SceneDev &sc, const float *q, int n,
+                           float *d, cudaStream_t st)
+{
+    if (n == 0) return CP_OK;
+    const int threads = 128;
+    const int blocks = (n + threads - 1) / threads;
+    if (m.n_spheres == 12)
+        k_signed_distance<12><<<blocks, threads, 0, st>>>(m, sc, q, n, d);
+    else
+        k_signed_distance<16><<<blocks, threads, 0, st>>>(m, sc, q, n, d);
+    CP_LAUNCHED("k_signed_distance");
+    return CP_OK;
+}
+
+}  // namespace cp

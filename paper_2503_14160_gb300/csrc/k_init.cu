@@ -1,0 +1,143 @@
+// Set-up kernels: obstacle records for the evaluation kernel, the uniform cubic B-spline
+// basis table, the initial sampling distribution (Sec. 4.1: linear interpolation with
+// evenly spaced interior control points) and small format conversions.
+#include "cp_internal.cuh"
+
+namespace cp {
+namespace {
+
+__global__ void k_prepare_scene(const cp_cylinder *__restrict__ cyl, int n_cyl,
+                                const cp_box *__restrict__ box, int n_box, float r_max,
+                                float4 *cyl_filt, float4 *cyl_exact, float4 *box_c,
+                                float4 *box_h)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_cyl) {
+        const cp_cylinder c = cyl[i];
+        const double reach = c.radius + (double)r_max;
+        const double W = c.cx * c.cx + c.cy * c.cy - reach * reach;
+        cyl_filt[i] = make_float4((float)c.cx, (float)c.cy, (float)W, 0.f);
+        cyl_exact[i] = make_float4((float)c.radius, (float)c.z_lo, (float)c.z_hi, 0.f);
+    }
+    if (i < n_box) {
+        const cp_box b = box[i];
+        box_c[i] = make_float4((float)(0.5 * (b.lo[0] + b.hi[0])), (float)(0.5 * (b.lo[1] + b.hi[1])),
+                               (float)(0.5 * (b.lo[2] + b.hi[2])), 0.f);
+        box_h[i] = make_float4((float)(0.5 * (b.hi[0] - b.lo[0])), (float)(0.5 * (b.hi[1] - b.lo[1])),
+                               (float)(0.5 * (b.hi[2] - b.lo[2])), 0.f);
+    }
+}
+
+// Uniform cubic B-spline basis on one span at u in [0, 1] (basis-matrix form):
+//   b0 = (1-u)^3 / 6, b1 = (3u^3 - 6u^2 + 4) / 6, b2 = (-3u^3 + 3u^2 + 3u + 1) / 6, b3 = u^3 / 6
+__device__ void cubic_basis(double u, double b[4])
+{
+    const double v = 1.0 - u;
+    b[0] = v * v * v / 6.0;
+    b[1] = (3.0 * u * u * u - 6.0 * u * u + 4.0) / 6.0;
+    b[2] = (-3.0 * u * u * u + 3.0 * u * u + 3.0 * u + 1.0) / 6.0;
+    b[3] = u * u * u / 6.0;
+}
+
+// basis[2(m-1)] = b(m/S), basis[2(m-1)+1] = b(m/S) - b((m-1)/S), m = 1..S, differences
+// taken in FP64 before rounding so that increments keep their relative accuracy.
+__global__ void k_basis_table(int S, float4 *basis)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (m > S) return;
+    double b[4], b0[4];
+    cubic_basis((double)m / (double)S, b);
+    cubic_basis((double)(m - 1) / (double)S, b0);
+    basis[2 * (m - 1)] = make_float4((float)b[0], (float)b[1], (float)b[2], (float)b[3]);
+    basis[2 * (m - 1) + 1] = make_float4((float)(b[0] - b0[0]), (float)(b[1] - b0[1]),
+                                         (float)(b[2] - b0[2]), (float)(b[3] - b0[3]));
+}
+
+// mu[4f + c] = q0[c] + (f+1)/(K+1) (qd[c] - q0[c]); C = diag((frac (q_max - q_min))^2).
+__global__ void k_init_distribution(const double *q0, const double *qd, const double *q_min,
+                                    const double *q_max, int K, double frac, double *mu,
+                                    double *C)
+{
+    const int D = 4 * K;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < D * D;
+         idx += gridDim.x * blockDim.x) {
+        const int r = idx / D, c = idx - r * D;
+        double v = 0.0;
+        if (r == c) {
+            const int j = r & 3;
+            const double sd = frac * (q_max[j] - q_min[j]);
+            v = sd * sd;
+        }
+        C[idx] = v;
+        if (idx < D) {
+            const int f = idx >> 2, j = idx & 3;
+            mu[idx] = q0[j] + (double)(f + 1) / (double)(K + 1) * (qd[j] - q0[j]);
+        }
+    }
+}
+
+__global__ void k_mean_to_candidate(const double *mu, int D, float *xi)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < D) xi[r] = (float)mu[r];
+}
+
+__global__ void k_control_points(const double *q0, const double *qd, const double *mu, int K,
+                                 double *ctrl)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // 0 .. 4(K+8)-1
+    if (idx >= 4 * (K + 8)) return;
+    const int point = idx >> 2, j = idx & 3;
+    ctrl[idx] = point < 4 ? q0[j] : (point >= K + 4 ? qd[j] : mu[4 * (point - 4) + j]);
+}
+
+}  // namespace
+
+int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d_box_in,
+                         int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact,
+                         float4 *box_c, float4 *box_h, cudaStream_t st)
+{
+    const int n = n_cyl > n_box ? n_cyl : n_box;
+    if (n == 0) return CP_OK;
+    k_prepare_scene<<<(n + 127) / 128, 128, 0, st>>>(d_cyl_in, n_cyl, d_box_in, n_box, r_max,
+                                                     cyl_filt, cyl_exact, box_c, box_h);
+    CP_LAUNCHED("k_prepare_scene");
+    return CP_OK;
+}
+
+int launch_basis_table(int S, float4 *basis, cudaStream_t st)
+{
+    k_basis_table<<<(S + 127) / 128, 128, 0, st>>>(S, basis);
+    CP_LAUNCHED("k_basis_table");
+    return CP_OK;
+}
+
+int launch_init_distribution(const double *q0, const double *qd, const double *q_min,
+                             const double *q_max, int K, double init_std_frac, double *mu,
+                             double *C, cudaStream_t st)
+{
+    const int D = 4 * K;
+    const int threads = 256;
+    const int blocks = (D * D + threads - 1) / threads;
+    k_init_distribution<<<blocks, threads, 0, st>>>(q0, qd, q_min, q_max, K, init_std_frac, mu, C);
+    CP_LAUNCHED("k_init_distribution");
+    return CP_OK;
+}
+
+int launch_mean_to_candidate(const double *mu, int D, float *xi, cudaStream_t st)
+{
+    k_mean_to_candidate<<<1, 128, 0, st>>>(mu, D, xi);
+    CP_LAUNCHED("k_mean_to_candidate");
+    return CP_OK;
+}
+
+int launch_control_points(const double *q0, const double *qd, const double *mu, int K,
+                          double *ctrl, cudaStream_t st)
+{
+    const int n = 4 * (K + 8);
+    k_control_points<<<(n + 127) / 128, 128, 0, st>>>(q0, qd, mu, K, ctrl);
+    CP_LAUNCHED("k_control_points");
+    return CP_OK;
+}
+
+}  // namespace cp

@@ -1,0 +1,184 @@
+// Algorithm 1 step (1): xi_i ~ N(mu, sigma^2 C) (arXiv 2503.14160, Sec. 4.1).
+//   k_factor  L L^T = sigma^2 C, FP64 right-looking Cholesky in one CTA (D <= 128)
+//   k_sample  z_i from Philox4x32-10 (Salmon et al., SC'11) + Box-Muller, xi_i = mu + L z_i
+// The counter of candidate i, block j, iteration t, query q is (j, i, t, q); the key is
+// the 64-bit seed split into two words. Block j gives the normals z[4j..4j+3].
+#include "cp_internal.cuh"
+
+namespace cp {
+namespace {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kWeyl0;
+        k1 += kWeyl1;
+    }
+    return c;
+}
+
+// Box-Muller on the top 24 bits of two words: u1 in (0, 1], u2 in [0, 1), both exact.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    const float u1 = (float)((a >> 8) + 1u) * 0x1p-24f;
+    const float u2 = (float)(b >> 8) * 0x1p-24f;
+    const float r = sqrtf(-2.f * logf(u1));
+    float s, c;
+    sincospif(2.f * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+__global__ void k_philox(const uint4 *__restrict__ ctr, uint32_t k0, uint32_t k1, int64_t n,
+                         uint4 *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+constexpr int kFactorThreads = 1024;
+
+// One CTA; A = sigma^2 C in shared memory (D^2 doubles). Column k: pivot sqrt, scale the
+// column below it, then rank-1 update of the trailing lower triangle. Outputs L (double,
+// row-major, upper part zero) and its FP32 transpose Lt[c][r] = L[r][c] for the sampler.
+__global__ void __launch_bounds__(kFactorThreads)
+k_factor(const double *__restrict__ C, double sigma2, int D, double *L, float *Lt,
+         uint32_t *status)
+{
+    extern __shared__ double A[];
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+    for (int idx = tid; idx < D * D; idx += blockDim.x) A[idx] = sigma2 * C[idx];
+    __syncthreads();
+    for (int k = 0; k < D; ++k) {
+        if (tid == 0) {
+            double akk = A[k * D + k];
+            if (!(akk > 0.0)) {
+                bad = 1;
+                akk = 1.0;
+            }
+            A[k * D + k] = sqrt(akk);
+        }
+        __syncthreads();
+        const double piv = A[k * D + k];
+        for (int i = k + 1 + tid; i < D; i += blockDim.x) A[i * D + k] /= piv;
+        __syncthreads();
+        const int T = D - k - 1;
+        for (int idx = tid; idx < T * T; idx += blockDim.x) {
+            const int i = k + 1 + idx / T, j = k + 1 + idx % T;
+            if (j <= i) A[i * D + j] -= A[i * D + k] * A[j * D + k];
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int r = idx / D, c = idx - r * D;
+        const double v = c <= r ? A[idx] : 0.0;
+        L[idx] = v;
+        Lt[c * D + r] = (float)v;
+    }
+    if (tid == 0 && bad) atomicOr(status, DEV_ERR_NOT_PD);
+}
+
+constexpr int kSampleThreads = 256;
+
+// One candidate per warp at a time; Lt (FP32, column-major) in shared memory, the D
+// normals of the candidate in a per-warp shared buffer; lane l writes rows l, l+32, ...
+__global__ void __launch_bounds__(kSampleThreads)
+k_sample(const double *__restrict__ mu, const float *__restrict__ Lt, int N, int K,
+         uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *xi)
+{
+    extern __shared__ float sm[];
+    const int D = 4 * K;
+    float *sL = sm;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sZ = sm + D * D + wib * D;
+    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) sL[idx] = Lt[idx];
+    __syncthreads();
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int i = warp; i < N; i += n_warps) {
+        for (int j = lane; j < K; j += 32) {
+            const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)i, iter, query), k0, k1);
+            float z0, z1, z2, z3;
+            box_muller(x.x, x.y, z0, z1);
+            box_muller(x.z, x.w, z2, z3);
+            sZ[4 * j + 0] = z0;
+            sZ[4 * j + 1] = z1;
+            sZ[4 * j + 2] = z2;
+            sZ[4 * j + 3] = z3;
+        }
+        __syncwarp();
+        for (int r = lane; r < D; r += 32) {
+            float acc = 0.f;
+            for (int c = 0; c < D; ++c) acc = fmaf(sL[c * D + r], sZ[c], acc);
+            xi[(size_t)i * D + r] = (float)(mu[r] + (double)acc);
+        }
+        __syncwarp();
+    }
+}
+
+size_t sample_smem(int K) { return sizeof(float) * ((size_t)16 * K * K + (kSampleThreads / 32) * 4 * K); }
+
+}  // namespace
+
+int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out,
+                  cudaStream_t st)
+{
+    if (n == 0) return CP_OK;
+    const int threads = 256;
+    const int64_t blocks = (n + threads - 1) / threads;
+    k_philox<<<(unsigned)blocks, threads, 0, st>>>((const uint4 *)ctr, k0, k1, n, (uint4 *)out);
+    CP_LAUNCHED("k_philox");
+    return CP_OK;
+}
+
+int factor_configure()
+{
+    const int max_smem = (int)(sizeof(double) * 4 * CP_MAX_WAYPOINTS * 4 * CP_MAX_WAYPOINTS);
+    CP_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    return CP_OK;
+}
+
+int launch_factor(const double *C, double sigma2, int D, double *L, float *Lt_f,
+                  uint32_t *status, cudaStream_t st)
+{
+    const size_t smem = sizeof(double) * (size_t)D * D;
+    k_factor<<<1, kFactorThreads, smem, st>>>(C, sigma2, D, L, Lt_f, status);
+    CP_LAUNCHED("k_factor");
+    return CP_OK;
+}
+
+int sample_configure()
+{
+    CP_CUDA(cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sample_smem(CP_MAX_WAYPOINTS)));
+    return CP_OK;
+}
+
+int launch_sample(const double *mu, const float *Lt_f, int N, int K, uint64_t seed,
+                  uint32_t iter, uint32_t query, float *xi, cudaStream_t st)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    CP_CUDA(cudaGetDevice(&dev));
+    CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = sample_smem(K);
+    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample, kSampleThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int warps = kSampleThreads / 32;
+    int blocks = (N + warps - 1) / warps;
+    if (blocks > sms * per_sm) blocks = sms * per_sm;
+    k_sample<<<blocks, kSampleThreads, smem, st>>>(mu, Lt_f, N, K, (uint32_t)seed,
+                                                   (uint32_t)(seed >> 32), iter, query, xi);
+    CP_LAUNCHED("k_sample");
+    return CP_OK;
+}
+
+}  // namespace cp

@@ -1,0 +1,186 @@
+"""GPU parity of Algorithm 1 steps (1), (3)-(6) and of the whole loop against the FP64
+oracle: sampling (same Philox words, normals to float32 rounding), the Cholesky factor,
+the ranking (exact), the weighted mean and covariance (FP64, 1e-12 relative), and plans
+(path length within 1e-3 relative)."""
+import numpy as np
+import pytest
+
+from helpers import Setup, endpoints
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2503_14160_gb300 import build, craneplan
+    build.build()
+    craneplan.load()
+    return craneplan
+
+
+@pytest.fixture(scope="module")
+def crane():
+    from paper_2503_14160_gb300 import workloads
+    return workloads.forestry_crane()
+
+
+def _spd(D, seed, scale=0.05):
+    g = np.random.default_rng(seed)
+    A = g.normal(size=(D, D))
+    return scale * (A @ A.T / D + 0.2 * np.eye(D)), g.normal(size=D)
+
+
+@pytest.mark.parametrize("N,K,it", [(96, 4, 0), (257, 8, 7), (64, 32, 123)])
+def test_sample_and_factor(lib, crane, N, K, it):
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    s = Setup(crane, workloads.empty_scene(), N=N, K=K, S=4, seed=77, sigma=0.8)
+    try:
+        D = 4 * K
+        C, mu = _spd(D, seed=K)
+        lib.cp_set_endpoints(s.h, np.zeros(4), np.ones(4))
+        lib.cp_set_distribution(s.h, torch.from_numpy(mu).cuda(), torch.from_numpy(C).cuda(), it)
+        Lg = torch.zeros(D, D, dtype=torch.float64, device="cuda")
+        lib.cp_get_factor(s.h, Lg)
+        xi = torch.zeros(N, K, 4, device="cuda")
+        lib.cp_sample(s.h, it, xi)
+        lib.cp_synchronize(s.h)
+        L = s.oracle.factor(C, 0.8)
+        np.testing.assert_allclose(Lg.cpu().numpy(), L, rtol=1e-12, atol=1e-15)
+        z = s.oracle.normals(77, it, 0, N, K)
+        want = mu[None, :] + z @ L.T
+        got = xi.cpu().numpy().reshape(N, D).astype(np.float64)
+        # float32 rounding bound: the result, and a D-term float32 dot product of L and z
+        bound = EPS32 * np.abs(want) + (D + 8) * EPS32 * (np.abs(z) @ np.abs(L).T) + 1e-30
+        assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("N,K,nu,ties", [(300, 4, 150, 30), (4096, 16, 0, 0), (77, 2, 1, 5),
+                                         (65536, 32, 0, 100)])
+def test_update_matches_oracle(lib, crane, N, K, nu, ties):
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    s = Setup(crane, workloads.empty_scene(), N=N, K=K, S=2, n_elites=nu, eps=1e-8)
+    try:
+        J = workloads.random_costs(N, seed=N, ties=ties)
+        J[[1, N // 3]] = np.nan
+        g = np.random.default_rng(N)
+        xi = (g.normal(size=(N, K, 4)) * 0.3 + 1.0).astype(np.float32)
+        lib.cp_set_endpoints(s.h, np.zeros(4), np.ones(4))
+        Jt = torch.from_numpy(J).cuda()
+        xt = torch.from_numpy(xi).cuda()
+        lib.cp_update(s.h, Jt, xt)
+        D = 4 * K
+        mu = torch.zeros(D, dtype=torch.float64, device="cuda")
+        C = torch.zeros(D, D, dtype=torch.float64, device="cuda")
+        el = torch.zeros(s.nu, dtype=torch.int32, device="cuda")
+        Lg = torch.zeros(D, D, dtype=torch.float64, device="cuda")
+        lib.cp_get_distribution(s.h, mu, C)
+        lib.cp_get_elites(s.h, el)
+        lib.cp_get_factor(s.h, Lg)
+        lib.cp_synchronize(s.h)
+        order = s.oracle.rank(J)
+        np.testing.assert_array_equal(el.cpu().numpy(), order[:s.nu])
+        mu_o, C_o = s.oracle.update(xi.astype(np.float64), J, s.nu, 1e-8)
+        np.testing.assert_allclose(mu.cpu().numpy(), mu_o, rtol=1e-12, atol=1e-15)
+        Cg = C.cpu().numpy()
+        np.testing.assert_allclose(Cg, C_o, rtol=1e-11, atol=1e-14 * np.abs(C_o).max())
+        np.testing.assert_allclose(Lg.cpu().numpy(), np.linalg.cholesky(Cg), rtol=1e-11,
+                                   atol=1e-14)
+    finally:
+        s.close()
+
+
+def test_update_single_elite(lib, crane):
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    s = Setup(crane, workloads.empty_scene(), N=10, K=2, S=2, n_elites=1, eps=1e-8)
+    try:
+        J = np.linspace(3.0, 1.0, 10)
+        xi = np.random.default_rng(1).normal(size=(10, 2, 4)).astype(np.float32)
+        lib.cp_set_endpoints(s.h, np.zeros(4), np.ones(4))
+        lib.cp_update(s.h, torch.from_numpy(J).cuda(), torch.from_numpy(xi).cuda())
+        mu = torch.zeros(8, dtype=torch.float64, device="cuda")
+        C = torch.zeros(8, 8, dtype=torch.float64, device="cuda")
+        lib.cp_get_distribution(s.h, mu, C)
+        lib.cp_synchronize(s.h)
+        np.testing.assert_array_equal(mu.cpu().numpy(), xi[9].reshape(-1).astype(np.float64))
+        np.testing.assert_allclose(C.cpu().numpy(), 1e-8 * np.eye(8), atol=1e-22)
+    finally:
+        s.close()
+
+
+def _plan_gpu(lib, s, q0, qd, iters):
+    lib.cp_set_endpoints(s.h, q0, qd)
+    ctrl, stats = lib.cp_plan(s.h, iters, K=s.K)
+    return ctrl, stats
+
+
+def test_plan_free_space(lib, crane):
+    """No obstacles: the GPU plan, like the oracle's, converges to the straight segment."""
+    from paper_2503_14160_gb300 import workloads
+    q0 = np.array([2.0, 0.1, -2.0, 0.3])
+    qd = np.array([-1.5, 1.0, -0.5, 2.2])
+    s = Setup(crane, workloads.empty_scene(), N=128, K=6, S=16, seed=3)
+    try:
+        ctrl, st = _plan_gpu(lib, s, q0, qd, 150)
+        res = s.oracle.plan(s.problem, s.sp, q0, qd, 150)
+        assert st["length"] == pytest.approx(np.linalg.norm(qd - q0), rel=1e-3)
+        assert st["length"] == pytest.approx(res.final.length[0], rel=1e-3)
+        assert st["Jp"] == pytest.approx(res.final.Jp[0], rel=1e-3)
+        assert st["flag"] == 0 and st["Jl"] == 0.0
+        np.testing.assert_array_equal(ctrl[:4], np.tile(q0, (4, 1)))
+        np.testing.assert_array_equal(ctrl[-4:], np.tile(qd, (4, 1)))
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plan_small_forest_matches_oracle(lib, crane, seed):
+    """The plain single query (N=256, K=8, S=32, 20 trees, 50 iterations): the converged
+    path length matches the oracle's within 1e-3 relative."""
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("single_small")
+    s = Setup(crane, workloads.make_scene(workloads.WORKLOADS["single_small"]), N=256, K=8,
+              S=32, seed=seed)
+    try:
+        ctrl, st = _plan_gpu(lib, s, q0, qd, 50)
+        res = s.oracle.plan(s.problem, s.sp, q0, qd, 50)
+        print("seed", seed, "gpu", st["length"], st["J"], st["flag"], "oracle",
+              res.final.length[0], res.final.J[0], res.final.flag[0])
+        assert st["length"] == pytest.approx(res.final.length[0], rel=1e-3)
+        assert st["flag"] == res.final.flag[0]
+    finally:
+        s.close()
+
+
+def test_plan_deterministic_and_resumable(lib, crane):
+    """Same seed, same result bit for bit; a restored (mu, C, t) repeats the remaining
+    iterations exactly."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("single_small")
+    s = Setup(crane, workloads.make_scene(workloads.WORKLOADS["single_small"]), N=256, K=8,
+              S=32, seed=5)
+    try:
+        a, _ = _plan_gpu(lib, s, q0, qd, 20)
+        b, _ = _plan_gpu(lib, s, q0, qd, 20)
+        np.testing.assert_array_equal(a, b)
+        lib.cp_set_endpoints(s.h, q0, qd)
+        lib.cp_plan(s.h, 10, K=8)
+        mu = torch.zeros(32, dtype=torch.float64, device="cuda")
+        C = torch.zeros(32, 32, dtype=torch.float64, device="cuda")
+        lib.cp_get_distribution(s.h, mu, C)
+        c1, st1 = lib.cp_plan(s.h, 10, K=8)
+        np.testing.assert_array_equal(c1, a)
+        lib.cp_set_endpoints(s.h, q0, qd)
+        lib.cp_set_distribution(s.h, mu, C, 10)
+        c2, st2 = lib.cp_plan(s.h, 10, K=8)
+        np.testing.assert_array_equal(c2, a)
+        assert st2["iteration"] == 20
+    finally:
+        s.close()
