@@ -109,6 +109,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+EVAL_SOURCE = os.path.join(ROOT, "paper_2503_14160_gb300", "csrc", "k_eval.cu")
+EVAL_PROFILE = os.path.join(ROOT, "profiles", "k_eval_single_large.md")
+
+
+def eval_source_sha1():
+    import hashlib
+    with open(EVAL_SOURCE, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def traffic_per_launch():
+    """DRAM bytes (read + write) per launch of the evaluation kernel from the committed ncu
+    summary, or None when that summary was taken from a different kernel source."""
+    try:
+        text = open(EVAL_PROFILE).read()
+    except OSError:
+        return None
+    sha, traffic = None, None
+    for line in text.splitlines():
+        if line.startswith("source sha1:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram bytes per launch:"):
+            traffic = float(line.split(":", 1)[1].split()[0])
+    return traffic if sha == eval_source_sha1() else None
+
+
 def select_endpoints_gpu(cp, planner, crane, seed, query):
     """Start/goal by the rule of the workload, using the library's d(q) kernel."""
     import torch
@@ -209,10 +235,10 @@ def run_ours(args):
     n_s = wl.n_checkpoints
     pairs = len(crane.spheres) * (scene.n_cyl + scene.n_box)
     flops_per_candidate = n_s * (pairs * FLOPS_PER_PAIR + FLOPS_PER_CHECKPOINT)
-    # each plan launches the kernel T times on N candidates and once on the mean path
-    flops_per_launch = (wl.n_candidates * iters + 1) * flops_per_candidate / (iters + 1)
+    # per plan the kernel runs T times on N candidates and once on the mean path
+    flops_timed = args.steps * (wl.n_candidates * iters + 1) * flops_per_candidate
     eval_ms = timing["eval_ms"] / max(timing["eval_launches"], 1)
-    achieved = flops_per_launch / (eval_ms / 1e3) / 1e12
+    achieved = flops_timed / (timing["eval_ms"] / 1e3) / 1e12
     peak = PEAK_SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
     clk = clocks.summary()
 
@@ -239,7 +265,7 @@ def run_ours(args):
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                          "frac_at_observed_clock": (achieved / (peak * clk["sm_mhz"] / 2070.0)
                                                     if clk.get("sm_mhz") else None),
-                         "traffic": None, "eval_ms_per_launch": eval_ms,
+                         "traffic": traffic_per_launch(), "eval_ms_per_launch": eval_ms,
                          "eval_launches": timing["eval_launches"]},
             "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
                                   for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},

@@ -42,17 +42,23 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libcraneplan.so if it is missing or older than its sources."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, defines=(), lib_path=None) -> str:
+    """Compile and link libcraneplan.so if it is missing or older than its sources.
+
+    `defines` (e.g. ["CP_EVAL_MIN_BLOCKS=2"]) and `lib_path` build a variant elsewhere."""
+    lib = lib_path or LIB
+    if not force and not defines and lib_path is None and not _stale():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    out_dir = os.path.dirname(os.path.abspath(lib))
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
-    objs = [os.path.join(OUT_DIR, s.replace(".cu", ".o")) for s in SOURCES]
+    tag = "" if not defines else "_" + "_".join(d.replace("=", "") for d in defines)
+    objs = [os.path.join(out_dir, s.replace(".cu", tag + ".o")) for s in SOURCES]
+    dflags = ["-D" + d for d in defines]
 
     def compile_one(src_obj):
         src, obj = src_obj
-        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose)
+        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose) + dflags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
@@ -60,15 +66,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         logs = list(ex.map(compile_one, zip(SOURCES, objs)))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         print("".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -376,7 +376,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->chunks = (p->n_s + 31) / 32;
     p->nu = params->n_elites > 0 ? params->n_elites : p->N / 2;
     if (p->nu < 1) p->nu = 1;
-    p->n_mean_chunks = (p->nu + update_chunk_size() - 1) / update_chunk_size();
+    p->n_mean_chunks = update_chunks(p->nu);
     p->cap_cyl = params->max_cylinders > scene->n_cyl ? params->max_cylinders : scene->n_cyl;
     p->cap_box = params->max_boxes > scene->n_box ? params->max_boxes : scene->n_box;
     p->mdev = make_model(model);
@@ -402,6 +402,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     if ((rc = eval_configure(eval_smem > 48 * 1024 ? eval_smem : 48 * 1024)) != CP_OK) return fail(rc);
     if ((rc = factor_configure()) != CP_OK) return fail(rc);
     if ((rc = sample_configure()) != CP_OK) return fail(rc);
+    if ((rc = update_configure()) != CP_OK) return fail(rc);
 
     const size_t N = p->N, D = p->D, nu = p->nu, ch = p->chunks, mc = p->n_mean_chunks;
     Layout L;

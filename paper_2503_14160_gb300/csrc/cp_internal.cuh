@@ -76,8 +76,8 @@ struct EvalArgs {
     int n, K, S, n_s, chunks;   // chunks = ceil(n_s / 32)
     float4 q0, qd;
     const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
-    float4 *partial;            // [n][chunks] {J_p, sum pen, J_l, length} (float)
-    uint32_t *flagword;         // [n][chunks]
+    float4 *partial;            // [chunks][n] {J_p, sum pen, J_l, length} (float)
+    uint32_t *flagword;         // [chunks][n]
     float *pen_out;             // optional [n][n_s]
 };
 
@@ -119,6 +119,7 @@ int launch_mean(const float *elites, const double *w, int nu, int D, double *par
                 double *mu, cudaStream_t st);
 int launch_cov(const float *elites, const double *w, const double *mu, int nu, int D,
                double eps, double *partial, double *C, cudaStream_t st);
-int update_chunk_size();
+int update_chunks(int nu);
+int update_configure();
 
 }  // namespace cp

@@ -18,6 +18,11 @@ namespace cp {
 namespace {
 
 constexpr int kEvalThreads = 256;
+#ifndef CP_EVAL_MIN_BLOCKS
+#define CP_EVAL_MIN_BLOCKS 3   // CTAs of 8 warps resident per SM (3: at most 85 registers)
+#endif
+constexpr int kEvalMinBlocks = CP_EVAL_MIN_BLOCKS;
+constexpr int kObstaclesPerBranch = 2;   // obstacles tested between two branches
 
 __device__ __forceinline__ float sdf_cylinder(float x, float y, float z, float cx, float cy,
                                               float4 e /* R, z_lo, z_hi */)
@@ -75,10 +80,69 @@ __device__ __forceinline__ float limit_excess(float v, float lo, float hi)
     return fmaf(a, a, b * b);
 }
 
+// 1 when g[s] < t[s] for some s of the 12 (one compare per pair, each folding the
+// running predicate in with setp's boolean OR; one select at the end).
+// 1 when g[s] < t[s] for some s of the 12: one chain of compares, each folding the
+// running predicate in with setp's boolean OR, and one select at the end.
+__device__ __forceinline__ uint32_t any_below12(const float2 *g, const float *t)
+{
+    uint32_t r;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.lt.f32 p, %1, %13;\n\t"
+        "setp.lt.or.f32 p, %2, %14, p;\n\t"
+        "setp.lt.or.f32 p, %3, %15, p;\n\t"
+        "setp.lt.or.f32 p, %4, %16, p;\n\t"
+        "setp.lt.or.f32 p, %5, %17, p;\n\t"
+        "setp.lt.or.f32 p, %6, %18, p;\n\t"
+        "setp.lt.or.f32 p, %7, %19, p;\n\t"
+        "setp.lt.or.f32 p, %8, %20, p;\n\t"
+        "setp.lt.or.f32 p, %9, %21, p;\n\t"
+        "setp.lt.or.f32 p, %10, %22, p;\n\t"
+        "setp.lt.or.f32 p, %11, %23, p;\n\t"
+        "setp.lt.or.f32 p, %12, %24, p;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "f"(g[0].x), "f"(g[0].y), "f"(g[1].x), "f"(g[1].y), "f"(g[2].x), "f"(g[2].y),
+          "f"(g[3].x), "f"(g[3].y), "f"(g[4].x), "f"(g[4].y), "f"(g[5].x), "f"(g[5].y),
+          "f"(t[0]), "f"(t[1]), "f"(t[2]), "f"(t[3]), "f"(t[4]), "f"(t[5]),
+          "f"(t[6]), "f"(t[7]), "f"(t[8]), "f"(t[9]), "f"(t[10]), "f"(t[11]));
+    return r;
+}
+
 template <int NSPH>
-__global__ void __launch_bounds__(kEvalThreads)
+__device__ __forceinline__ uint32_t any_below(const float2 *g, const float *t)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int q = 0; q < NSPH / 12; ++q) r |= any_below12(g + 6 * q, t + 12 * q);
+#pragma unroll
+    for (int s = 12 * (NSPH / 12); s < NSPH; s += 2)
+        r |= (uint32_t)((g[s / 2].x < t[s]) | (g[s / 2].y < t[s + 1]));
+    return r;
+}
+
+// Exact signed distance of every sphere whose filter test passes against one cylinder
+// (f = {cx, cy, W}, e = {R, z_lo, z_hi}); +inf when none passes.
+template <int NSPH>
+__device__ __forceinline__ float exact_cylinders(const ModelDev &m, const float *X, const float *Y,
+                                              const float *Z, const float *T, float4 f, float4 e)
+{
+    float d = CUDART_INF_F;
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s) {
+        const float g = fmaf(X[s], f.x, fmaf(Y[s], f.y, f.z));
+        if (g < T[s])
+            d = fminf(d, sdf_cylinder(-0.5f * X[s], -0.5f * Y[s], Z[s], f.x, f.y, e) - m.sph[s].radius);
+    }
+    return d;
+}
+
+template <int NSPH>
+__global__ void __launch_bounds__(kEvalThreads, kEvalMinBlocks)
 k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
 {
+    // Shared memory: per cylinder the filter record {cx, cy, W, 0} and the exact record
+    // {R, z_lo, z_hi, 0}; per box its centre and half extent; the spline basis table.
     extern __shared__ __align__(16) float4 smem[];
     float4 *s_filt = smem;
     float4 *s_exact = s_filt + sc.n_cyl;
@@ -130,6 +194,8 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
                          limit_excess(q.z, m.q_min[2], m.q_max[2]) +
                          limit_excess(q.w, m.q_min[3], m.q_max[3]);
 
+        // Sphere centres; per sphere the filter threshold T = margin - (x^2 + y^2) and the
+        // scaled coordinates (-2x, -2y), kept in pairs for packed FP32x2 FMAs.
         float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH];
         crane_fk<NSPH>(m, q, X, Y, Z);
 #pragma unroll
@@ -138,20 +204,48 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
             X[s] *= -2.f;   // exact; -0.5 X recovers x
             Y[s] *= -2.f;
         }
+        float2 X2[NSPH / 2], Y2[NSPH / 2];
+#pragma unroll
+        for (int p = 0; p < NSPH / 2; ++p) {
+            X2[p] = make_float2(X[2 * p], X[2 * p + 1]);
+            Y2[p] = make_float2(Y[2 * p], Y[2 * p + 1]);
+        }
 
         float dmin = CUDART_INF_F;
-        for (int o = 0; o < sc.n_cyl; ++o) {
-            const float4 f = s_filt[o];
+        // Two obstacles per step: 2 x NSPH power tests rho^2 - (R + r_max)^2 < margin in
+        // expanded form (-2x cx - 2y cy + W vs. margin - x^2 - y^2), two packed FMAs per
+        // sphere pair; the hit predicates accumulate without branches. Only when a test
+        // passes does the lane take the exact capped-cylinder distance.
+        constexpr int OB = kObstaclesPerBranch;
+        int o = 0;
+        for (; o + OB <= sc.n_cyl; o += OB) {
+            float4 fo[OB];      // {cx, cy, W, 0} of each obstacle, for the exact path
+            uint32_t hit[OB];
+            uint32_t any = 0;
 #pragma unroll
-            for (int s = 0; s < NSPH; ++s) {
-                // rho^2 - (R + r_max)^2 - x^2 - y^2 in expanded form (2 FMA)
-                const float g = fmaf(X[s], f.x, fmaf(Y[s], f.y, f.z));
-                if (g < T[s]) {
-                    const float d = sdf_cylinder(-0.5f * X[s], -0.5f * Y[s], Z[s], f.x, f.y,
-                                                 s_exact[o]) - m.sph[s].radius;
-                    dmin = fminf(dmin, d);
-                }
+            for (int b = 0; b < OB; ++b) {
+                const float4 f = s_filt[o + b];
+                const float2 cx2 = make_float2(f.x, f.x), cy2 = make_float2(f.y, f.y);
+                const float2 w2 = make_float2(f.z, f.z);
+                fo[b] = f;
+                float2 g[NSPH / 2];
+#pragma unroll
+                for (int p = 0; p < NSPH / 2; ++p) g[p] = __ffma2_rn(X2[p], cx2, __ffma2_rn(Y2[p], cy2, w2));
+                hit[b] = any_below<NSPH>(g, T);
+                any |= hit[b];
             }
+            if (any) {
+#pragma unroll
+                for (int b = 0; b < OB; ++b)
+                    if (hit[b]) dmin = fminf(dmin, exact_cylinders<NSPH>(m, X, Y, Z, T, fo[b], s_exact[o + b]));
+            }
+        }
+        for (; o < sc.n_cyl; ++o) {
+            const float4 f0 = s_filt[o];
+            bool hit0 = false;
+#pragma unroll
+            for (int s = 0; s < NSPH; ++s) hit0 |= fmaf(X[s], f0.x, fmaf(Y[s], f0.y, f0.z)) < T[s];
+            if (hit0) dmin = fminf(dmin, exact_cylinders<NSPH>(m, X, Y, Z, T, f0, s_exact[o]));
         }
         for (int o = 0; o < sc.n_box; ++o) {
             const float4 c = s_bc[o], h = s_bh[o];
@@ -173,26 +267,29 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
             v3 += __shfl_xor_sync(0xffffffffu, v3, off);
         }
         const uint32_t word = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) {
-            a.partial[u] = make_float4(v0, v1, v2, v3);
-            a.flagword[u] = word;
+        if (lane == 0) {   // chunk-major, so the finalize reads coalesce
+            a.partial[(size_t)chunk * a.n + cand] = make_float4(v0, v1, v2, v3);
+            a.flagword[(size_t)chunk * a.n + cand] = word;
         }
         if (a.pen_out != nullptr && valid) a.pen_out[(size_t)cand * a.n_s + (k - 1)] = pen;
     }
 }
 
+// One warp per candidate: lanes take the candidate's chunks (lane, lane + 32, ...), sum
+// them in FP64, and a fixed shuffle tree combines the lanes (deterministic order).
 __global__ void k_eval_finalize(const float4 *__restrict__ partial,
                                 const uint32_t *__restrict__ flagword, int n, int chunks,
                                 double w_c, double w_l, double lambda_c, double *J,
                                 uint8_t *flag, double *terms, uint32_t *substep_flags)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
     double jp = 0.0, jc = 0.0, jl = 0.0, len = 0.0;
     int n_flagged = 0;
-    for (int c = 0; c < chunks; ++c) {
-        const float4 v = partial[(size_t)i * chunks + c];
-        const uint32_t w = flagword[(size_t)i * chunks + c];
+    for (int c = lane; c < chunks; c += 32) {
+        const float4 v = partial[(size_t)c * n + i];
+        const uint32_t w = flagword[(size_t)c * n + i];
         jp += (double)v.x;
         jc += (double)v.y;
         jl += (double)v.z;
@@ -200,6 +297,15 @@ __global__ void k_eval_finalize(const float4 *__restrict__ partial,
         n_flagged += __popc(w);
         if (substep_flags != nullptr) substep_flags[(size_t)i * chunks + c] = w;
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        jp += __shfl_xor_sync(0xffffffffu, jp, off);
+        jc += __shfl_xor_sync(0xffffffffu, jc, off);
+        jl += __shfl_xor_sync(0xffffffffu, jl, off);
+        len += __shfl_xor_sync(0xffffffffu, len, off);
+        n_flagged += __shfl_xor_sync(0xffffffffu, n_flagged, off);
+    }
+    if (lane != 0) return;
     jc *= lambda_c;
     J[i] = jp + w_c * jc + w_l * jl;
     if (flag != nullptr) flag[i] = n_flagged > 0 ? 1 : 0;
@@ -289,8 +395,8 @@ int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n,
                          double *terms, uint32_t *substep_flags, cudaStream_t st)
 {
     if (n == 0) return CP_OK;
-    const int threads = 128;
-    k_eval_finalize<<<(n + threads - 1) / threads, threads, 0, st>>>(
+    const int threads = 256;
+    k_eval_finalize<<<(n * 32 + threads - 1) / threads, threads, 0, st>>>(
         partial, flagword, n, chunks, w_c, w_l, lambda_c, J, flag, terms, substep_flags);
     CP_LAUNCHED("k_eval_finalize");
     return CP_OK;

@@ -45,45 +45,85 @@ __global__ void k_philox(const uint4 *__restrict__ ctr, uint32_t k0, uint32_t k1
 
 constexpr int kFactorThreads = 1024;
 
-// One CTA; A = sigma^2 C in shared memory (D^2 doubles). Column k: pivot sqrt, scale the
-// column below it, then rank-1 update of the trailing lower triangle. Outputs L (double,
-// row-major, upper part zero) and its FP32 transpose Lt[c][r] = L[r][c] for the sampler.
+// 1/sqrt(a) for a > 0: a float seed refined by two Newton-Raphson steps
+// y <- y (3 - a y^2) / 2 in FP64 (quadratic convergence: 24 -> 48 -> 96 bits). On a part
+// with a narrow FP64 pipe this short chain is much faster than a library square root and
+// division on the critical path of every column.
+__device__ __forceinline__ double rsqrt_newton(double a)
+{
+    double y = (double)rsqrtf((float)a);
+    const double h = 0.5 * a;
+    y = y * fma(-h * y, y, 1.5);
+    y = y * fma(-h * y, y, 1.5);
+    return y;
+}
+
+// One CTA, right-looking Cholesky of A = sigma^2 C in shared memory (row stride D + 1).
+// Column k: with inv = 1/sqrt(a_kk), every trailing entry k < j <= i takes
+// a_ij -= a_ik a_jk inv^2, and the thread that updates a_{k+1,k+1} also computes the next
+// pivot's inv into the other slot of a double buffer, so one barrier per column suffices.
+// Column k of L is l_ik = a_ik inv. Outputs L (double, row-major, upper part zero) and its
+// FP32 transpose Lt[c][r] = L[r][c] for the sampler. A pivot that is not positive raises
+// DEV_ERR_NOT_PD (and is replaced by 1 so that the kernel finishes).
 __global__ void __launch_bounds__(kFactorThreads)
 k_factor(const double *__restrict__ C, double sigma2, int D, double *L, float *Lt,
          uint32_t *status)
 {
     extern __shared__ double A[];
+    __shared__ double s_inv[2];
     __shared__ int bad;
+    const int ld = D + 1;
     const int tid = threadIdx.x;
-    if (tid == 0) bad = 0;
-    for (int idx = tid; idx < D * D; idx += blockDim.x) A[idx] = sigma2 * C[idx];
+    for (int idx = tid; idx < D * D; idx += blockDim.x) {
+        const int r = idx / D, c = idx - r * D;
+        A[r * ld + c] = sigma2 * C[idx];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        bad = 0;
+        double a = A[0];
+        if (!(a > 0.0)) {
+            bad = 1;
+            a = 1.0;
+            A[0] = a;
+        }
+        s_inv[0] = rsqrt_newton(a);
+    }
     __syncthreads();
     for (int k = 0; k < D; ++k) {
-        if (tid == 0) {
-            double akk = A[k * D + k];
-            if (!(akk > 0.0)) {
-                bad = 1;
-                akk = 1.0;
-            }
-            A[k * D + k] = sqrt(akk);
-        }
-        __syncthreads();
-        const double piv = A[k * D + k];
-        for (int i = k + 1 + tid; i < D; i += blockDim.x) A[i * D + k] /= piv;
-        __syncthreads();
+        const double inv = s_inv[k & 1];
+        const double inv2 = inv * inv;
         const int T = D - k - 1;
         for (int idx = tid; idx < T * T; idx += blockDim.x) {
-            const int i = k + 1 + idx / T, j = k + 1 + idx % T;
-            if (j <= i) A[i * D + j] -= A[i * D + k] * A[j * D + k];
+            const int ii = idx / T, jj = idx - ii * T;
+            if (jj <= ii) {
+                const int i = k + 1 + ii, j = k + 1 + jj;
+                double v = A[i * ld + j] - A[i * ld + k] * A[j * ld + k] * inv2;
+                if (ii == 0) {   // the next pivot
+                    if (!(v > 0.0)) {
+                        bad = 1;
+                        v = 1.0;
+                    }
+                    s_inv[(k + 1) & 1] = rsqrt_newton(v);
+                }
+                A[i * ld + j] = v;
+            }
         }
         __syncthreads();
+        for (int i = k + tid; i < D; i += blockDim.x) {
+            const double l = A[i * ld + k] * inv;
+            L[i * D + k] = l;
+            Lt[k * D + i] = (float)l;
+        }
     }
     for (int idx = tid; idx < D * D; idx += blockDim.x) {
         const int r = idx / D, c = idx - r * D;
-        const double v = c <= r ? A[idx] : 0.0;
-        L[idx] = v;
-        Lt[c * D + r] = (float)v;
+        if (c > r) {
+            L[idx] = 0.0;
+            Lt[c * D + r] = 0.f;
+        }
     }
+    __syncthreads();
     if (tid == 0 && bad) atomicOr(status, DEV_ERR_NOT_PD);
 }
 
@@ -142,7 +182,8 @@ int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint
 
 int factor_configure()
 {
-    const int max_smem = (int)(sizeof(double) * 4 * CP_MAX_WAYPOINTS * 4 * CP_MAX_WAYPOINTS);
+    const int Dm = 4 * CP_MAX_WAYPOINTS;
+    const int max_smem = (int)(sizeof(double) * Dm * (Dm + 1));
     CP_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     return CP_OK;
 }
@@ -150,7 +191,7 @@ int factor_configure()
 int launch_factor(const double *C, double sigma2, int D, double *L, float *Lt_f,
                   uint32_t *status, cudaStream_t st)
 {
-    const size_t smem = sizeof(double) * (size_t)D * D;
+    const size_t smem = sizeof(double) * (size_t)D * (D + 1);
     k_factor<<<1, kFactorThreads, smem, st>>>(C, sigma2, D, L, Lt_f, status);
     CP_LAUNCHED("k_factor");
     return CP_OK;

@@ -13,7 +13,8 @@
 namespace cp {
 namespace {
 
-constexpr int kChunk = 128;         // elites per partial
+constexpr int kChunk = 32;          // elites staged at a time
+constexpr int kMaxChunks = 512;     // bound on the partial buffers
 constexpr int kRankThreads = 256;
 constexpr int kRankSplit = 256;     // j-range per grid row of k_rank_count
 
@@ -83,35 +84,60 @@ __global__ void k_scatter(const int *__restrict__ rank, const double *__restrict
     for (int c = lane; c < D; c += 32) elites[(size_t)r * D + c] = xi[(size_t)warp * D + c];
 }
 
-// Chunk p of kChunk elites: partial[p][c] = sum_{j in chunk} w_j elites[j][c].
-__global__ void k_mean_partial(const float *__restrict__ elites, const double *__restrict__ w,
-                               int nu, int D, double *partial)
+// Chunk p (elites [p per, (p+1) per)): partial[p][c] = sum_j w_j elites[j][c], staged
+// kChunk rows at a time in shared memory with coalesced loads; thread c sums in elite order.
+__global__ void __launch_bounds__(128)
+k_mean_partial(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D,
+               int per, double *partial)
 {
+    __shared__ float s_rows[kChunk * 4 * CP_MAX_WAYPOINTS];
     const int p = blockIdx.x, c = threadIdx.x;
-    if (c >= D) return;
-    const int j0 = p * kChunk, j1 = min(nu, j0 + kChunk);
+    const int j_end = min(nu, (p + 1) * per);
     double acc = 0.0;
-    for (int j = j0; j < j1; ++j) acc += w[j] * (double)elites[(size_t)j * D + c];
-    partial[(size_t)p * D + c] = acc;
+    for (int j0 = p * per; j0 < j_end; j0 += kChunk) {
+        const int cnt = min(j_end - j0, kChunk);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < cnt * D; idx += blockDim.x)
+            s_rows[idx] = elites[(size_t)j0 * D + idx];
+        __syncthreads();
+        if (c < D)
+            for (int j = 0; j < cnt; ++j) acc += w[j0 + j] * (double)s_rows[j * D + c];
+    }
+    if (c < D) partial[(size_t)p * D + c] = acc;
+}
+
+// Fixed-order sum of n partials with eight loads in flight (the grouping is fixed, so the
+// result does not depend on scheduling).
+__device__ __forceinline__ double sum_partials(const double *__restrict__ p, size_t stride, int n)
+{
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int q = 0;
+    for (; q + 8 <= n; q += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] += p[(size_t)(q + u) * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        if (q + u < n) a[u] += p[(size_t)(q + u) * stride];
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 __global__ void k_mean_combine(const double *__restrict__ partial, int n_chunks, int D, double *mu)
 {
     const int c = threadIdx.x;
     if (c >= D) return;
-    double acc = 0.0;
-    for (int p = 0; p < n_chunks; ++p) acc += partial[(size_t)p * D + c];
-    mu[c] = acc;
+    mu[c] = sum_partials(partial + c, (size_t)D, n_chunks);
 }
 
 // Block (tile t of the lower triangle of 16x16 tiles, chunk p): one output per thread.
+// The chunk's deviations y_j = xi_(j) - mu are staged kChunk elites at a time, the tile's
+// rows scaled by w_j, so each term costs one FP64 FMA.
 __global__ void __launch_bounds__(256)
 k_cov_partial(const float *__restrict__ elites, const double *__restrict__ w,
-              const double *__restrict__ mu, int nu, int D, double *partial)
+              const double *__restrict__ mu, int nu, int D, int per, double *partial)
 {
-    __shared__ double yr[kChunk][16];
-    __shared__ double yc[kChunk][16];
-    __shared__ double ws[kChunk];
+    __shared__ double wyr[kChunk][17];
+    __shared__ double yc[kChunk][17];
     // tile index -> (tile row tr >= tile col tc)
     int t = blockIdx.x, tr = 0;
     while (t > tr) {
@@ -120,18 +146,22 @@ k_cov_partial(const float *__restrict__ elites, const double *__restrict__ w,
     }
     const int tc = t;
     const int p = blockIdx.y;
-    const int j0 = p * kChunk, cnt = min(nu - j0, kChunk);
-    for (int idx = threadIdx.x; idx < cnt * 16; idx += blockDim.x) {
-        const int j = idx >> 4, k = idx & 15;
-        const int r = tr * 16 + k, c = tc * 16 + k;
-        yr[j][k] = r < D ? (double)elites[(size_t)(j0 + j) * D + r] - mu[r] : 0.0;
-        yc[j][k] = c < D ? (double)elites[(size_t)(j0 + j) * D + c] - mu[c] : 0.0;
-    }
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) ws[j] = w[j0 + j];
-    __syncthreads();
     const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+    const int j_end = min(nu, (p + 1) * per);
     double acc = 0.0;
-    for (int j = 0; j < cnt; ++j) acc += ws[j] * yr[j][a] * yc[j][b];
+    for (int j0 = p * per; j0 < j_end; j0 += kChunk) {
+        const int cnt = min(j_end - j0, kChunk);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < cnt * 16; idx += blockDim.x) {
+            const int j = idx >> 4, k = idx & 15;
+            const int r = tr * 16 + k, c = tc * 16 + k;
+            const double wj = w[j0 + j];
+            wyr[j][k] = r < D ? wj * ((double)elites[(size_t)(j0 + j) * D + r] - mu[r]) : 0.0;
+            yc[j][k] = c < D ? (double)elites[(size_t)(j0 + j) * D + c] - mu[c] : 0.0;
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) acc = fma(wyr[j][a], yc[j][b], acc);
+    }
     const int r = tr * 16 + a, c = tc * 16 + b;
     if (r < D && c < D) partial[((size_t)p * D + r) * D + c] = acc;
 }
@@ -143,15 +173,28 @@ __global__ void k_cov_combine(const double *__restrict__ partial, int n_chunks, 
     if (idx >= D * D) return;
     int r = idx / D, c = idx - r * D;
     const int lr = r >= c ? r : c, lc = r >= c ? c : r;     // lower-triangle source
-    double acc = 0.0;
-    for (int p = 0; p < n_chunks; ++p) acc += partial[((size_t)p * D + lr) * D + lc];
+    double acc = sum_partials(partial + (size_t)lr * D + lc, (size_t)D * D, n_chunks);
     if (r == c) acc += eps;
     C[idx] = acc;
 }
 
 }  // namespace
 
-int update_chunk_size() { return kChunk; }
+// Number of partials (chunks of elites) the update uses for nu elites, and elites per chunk.
+int update_chunks(int nu)
+{
+    const int n = (nu + kChunk - 1) / kChunk;
+    return n < kMaxChunks ? n : kMaxChunks;
+}
+
+static int per_chunk(int nu)
+{
+    const int n = update_chunks(nu);
+    const int per = (nu + n - 1) / n;
+    return (per + kChunk - 1) / kChunk * kChunk;
+}
+
+int update_configure() { return CP_OK; }
 
 int launch_weights(int nu, double *w, cudaStream_t st)
 {
@@ -183,8 +226,9 @@ int launch_scatter(const int *rank, const double *J, const float *xi, int N, int
 int launch_mean(const float *elites, const double *w, int nu, int D, double *partial,
                 double *mu, cudaStream_t st)
 {
-    const int n_chunks = (nu + kChunk - 1) / kChunk;
-    k_mean_partial<<<n_chunks, 128, 0, st>>>(elites, w, nu, D, partial);
+    const int per = per_chunk(nu);
+    const int n_chunks = (nu + per - 1) / per;
+    k_mean_partial<<<n_chunks, 128, 0, st>>>(elites, w, nu, D, per, partial);
     CP_LAUNCHED("k_mean_partial");
     k_mean_combine<<<1, 128, 0, st>>>(partial, n_chunks, D, mu);
     CP_LAUNCHED("k_mean_combine");
@@ -194,10 +238,11 @@ int launch_mean(const float *elites, const double *w, int nu, int D, double *par
 int launch_cov(const float *elites, const double *w, const double *mu, int nu, int D,
                double eps, double *partial, double *C, cudaStream_t st)
 {
-    const int n_chunks = (nu + kChunk - 1) / kChunk;
+    const int per = per_chunk(nu);
+    const int n_chunks = (nu + per - 1) / per;
     const int tiles = (D + 15) / 16;
     dim3 grid(tiles * (tiles + 1) / 2, n_chunks);
-    k_cov_partial<<<grid, 256, 0, st>>>(elites, w, mu, nu, D, partial);
+    k_cov_partial<<<grid, 256, 0, st>>>(elites, w, mu, nu, D, per, partial);
     CP_LAUNCHED("k_cov_partial");
     k_cov_combine<<<(D * D + 255) / 256, 256, 0, st>>>(partial, n_chunks, D, eps, C);
     CP_LAUNCHED("k_cov_combine");

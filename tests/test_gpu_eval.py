@@ -75,7 +75,9 @@ def test_evaluate_small_forest(lib, crane, K, S, n):
     try:
         xi = workloads.random_candidates(q0, qd, K, n, seed=K * 100 + S)
         g, o = check_eval(s, xi, q0, qd)
-        assert o.flag.sum() > 0 and (o.flag == 0).sum() > 0 or n < 8
+        d = o.d[:, 1:]
+        if n >= 8:   # both sides of contact are exercised
+            assert (d < 0).any() and (d > 0).any()
     finally:
         s.close()
 
