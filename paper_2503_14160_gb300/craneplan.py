@@ -101,6 +101,12 @@ _SIGS = {
     "cp_get_factor": (ctypes.c_int, [_P, _P]),
     "cp_get_elites": (ctypes.c_int, [_P, _P]),
     "cp_philox4x32_10": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P]),
+    "cp_evaluate_static": (ctypes.c_int, [ctypes.POINTER(cp_model), _P, ctypes.c_int32, _P,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), _P, ctypes.c_int32,
+                                          _P, _P, _P, _P]),
     "cp_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cp_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(cp_timing)]),
 }
@@ -284,6 +290,17 @@ def cp_get_elites(p: int, idx) -> None:
 
 def cp_philox4x32_10(ctr, key: int, n: int, out, stream=None) -> None:
     _check(load().cp_philox4x32_10(_ptr(ctr), int(key), int(n), _ptr(out), _stream(stream)))
+
+
+def cp_evaluate_static(model: cp_model, cyl, n_cyl: int, box, n_box: int, K: int, S: int,
+                       w_c: float, w_l: float, lambda_c: float, q0, qd, xi, n: int, J,
+                       flag=None, terms=None, stream=None) -> None:
+    """Evaluation without device allocation (fixed library scratch). cyl is a CUDA float64
+    tensor [n_cyl][5] (cx, cy, R, z_lo, z_hi), box a CUDA float64 tensor [n_box][6]."""
+    _check(load().cp_evaluate_static(ctypes.byref(model), _ptr(cyl), int(n_cyl), _ptr(box),
+                                     int(n_box), int(K), int(S), float(w_c), float(w_l),
+                                     float(lambda_c), _c4(q0), _c4(qd), _ptr(xi), int(n),
+                                     _ptr(J), _ptr(flag), _ptr(terms), _stream(stream)))
 
 
 def cp_set_timing(p: int, on: bool) -> None:

@@ -146,7 +146,7 @@ struct cp_planner {
     Timer timer;
 };
 
-namespace {
+namespace cp {
 
 int validate_model(const cp_model *m)
 {
@@ -166,6 +166,40 @@ int validate_model(const cp_model *m)
     }
     return CP_OK;
 }
+
+ModelDev make_model(const cp_model *m)
+{
+    ModelDev d{};
+    d.base_z = (float)m->base_z;
+    for (int j = 0; j < 4; ++j) {
+        d.q_min[j] = (float)m->q_min[j];
+        d.q_max[j] = (float)m->q_max[j];
+    }
+    d.n_spheres = m->n_spheres;
+    float r_max = 0.f;
+    for (int s = 0; s < kMaxSpheres; ++s) {
+        SphereLin l{0.f, 0.f, 0.f, 0.f, -1e30f};   // padding: never the nearest pair
+        if (s < m->n_spheres) {
+            const cp_sphere &sp = m->spheres[s];
+            const float t = (float)sp.offset, Lb = (float)m->boom_len, Lj = (float)m->jib_len;
+            switch (sp.link) {
+            case 0: l = {t, 0.f, 0.f, 0.f, 0.f}; break;
+            case 1: l = {Lb, t, 0.f, 0.f, 0.f}; break;
+            case 2: l = {Lb, Lj, t, 0.f, 0.f}; break;
+            default: l = {Lb, Lj, 1.f, t, 0.f}; break;
+            }
+            l.radius = (float)sp.radius;
+            if (l.radius > r_max) r_max = l.radius;
+        }
+        d.sph[s] = l;
+    }
+    d.r_max = r_max;
+    return d;
+}
+
+}  // namespace cp
+
+namespace {
 
 int validate_scene(const cp_scene *sc)
 {
@@ -211,36 +245,6 @@ int validate_params(const cp_params *p)
     if ((int64_t)p->n_candidates * ((n_s + 31) / 32) > 0x7FFFFFFF)
         return set_error("n_candidates * ceil(n_s / 32) exceeds 2^31 - 1"), CP_ERR_ARG;
     return CP_OK;
-}
-
-ModelDev make_model(const cp_model *m)
-{
-    ModelDev d{};
-    d.base_z = (float)m->base_z;
-    for (int j = 0; j < 4; ++j) {
-        d.q_min[j] = (float)m->q_min[j];
-        d.q_max[j] = (float)m->q_max[j];
-    }
-    d.n_spheres = m->n_spheres;
-    float r_max = 0.f;
-    for (int s = 0; s < kMaxSpheres; ++s) {
-        SphereLin l{0.f, 0.f, 0.f, 0.f, -1e30f};   // padding: never the nearest pair
-        if (s < m->n_spheres) {
-            const cp_sphere &sp = m->spheres[s];
-            const float t = (float)sp.offset, Lb = (float)m->boom_len, Lj = (float)m->jib_len;
-            switch (sp.link) {
-            case 0: l = {t, 0.f, 0.f, 0.f, 0.f}; break;
-            case 1: l = {Lb, t, 0.f, 0.f, 0.f}; break;
-            case 2: l = {Lb, Lj, t, 0.f, 0.f}; break;
-            default: l = {Lb, Lj, 1.f, t, 0.f}; break;
-            }
-            l.radius = (float)sp.radius;
-            if (l.radius > r_max) r_max = l.radius;
-        }
-        d.sph[s] = l;
-    }
-    d.r_max = r_max;
-    return d;
 }
 
 int stage_scene(cp_planner *p, const cp_scene *sc)

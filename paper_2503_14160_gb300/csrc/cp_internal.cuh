@@ -69,6 +69,9 @@ struct SceneDev {
 // rounding error of that form for a pair within reach of the crane is below 3e-4 m^2.
 constexpr float kFilterMargin = 2.0e-3f;
 
+int validate_model(const cp_model *m);
+ModelDev make_model(const cp_model *m);
+
 // ------------------------------------------------------------------ launchers
 
 struct EvalArgs {
@@ -90,6 +93,7 @@ int launch_signed_distance(const ModelDev &m, const SceneDev &sc, const float *q
                            float *d, cudaStream_t st);
 size_t eval_smem_bytes(int n_cyl, int n_box, int S);
 int eval_configure(size_t smem_bytes);
+int eval_ensure_smem(size_t smem_bytes);
 
 int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d_box_in,
                          int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact,

@@ -375,6 +375,21 @@ int eval_configure(size_t smem_bytes)
     return CP_OK;
 }
 
+// Raise (never lower) the dynamic shared-memory limit of the evaluation kernels.
+int eval_ensure_smem(size_t smem_bytes)
+{
+    cudaFuncAttributes at12{}, at16{};
+    CP_CUDA(cudaFuncGetAttributes(&at12, k_eval<12>));
+    CP_CUDA(cudaFuncGetAttributes(&at16, k_eval<16>));
+    if ((size_t)at12.maxDynamicSharedSizeBytes < smem_bytes)
+        CP_CUDA(cudaFuncSetAttribute(k_eval<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_bytes));
+    if ((size_t)at16.maxDynamicSharedSizeBytes < smem_bytes)
+        CP_CUDA(cudaFuncSetAttribute(k_eval<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_bytes));
+    return CP_OK;
+}
+
 int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
                 cudaStream_t st)
 {
