@@ -169,7 +169,8 @@ def run_ours(args):
     iters = args.iterations or wl.iterations
     crane = workloads.forestry_crane()
     scene = workloads.make_scene(wl)
-    params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank)
+    params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank,
+                            grid_cell=wl.grid_cell)
     planner = cp.Planner(crane, scene, params)
     h = planner.handle
     q0, qd, ok = select_endpoints_gpu(cp, planner, crane, wl.seed, rank)
@@ -260,13 +261,16 @@ def run_ours(args):
             "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "ms_per_plan": ms_e2e,
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "kernel": "k_eval", "achieved": achieved,
+            "roofline": None if wl.grid_cell > 0 else
+                        {"bound": "alu", "kernel": "k_eval", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                          "frac_at_observed_clock": (achieved / (peak * clk["sm_mhz"] / 2070.0)
                                                     if clk.get("sm_mhz") else None),
                          "traffic": traffic_per_launch(), "eval_ms_per_launch": eval_ms,
                          "eval_launches": timing["eval_launches"]},
+            "eval_kernel": {"name": "k_eval_grid" if wl.grid_cell > 0 else "k_eval",
+                            "ms_per_launch": eval_ms, "launches": timing["eval_launches"]},
             "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
                                   for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},
             "plan_result": {"J": stats["J"], "length": stats["length"], "flag": stats["flag"]},

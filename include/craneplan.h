@@ -117,6 +117,11 @@ typedef struct cp_params {
     uint32_t query;         /* fourth Philox counter word (query id) */
     int32_t max_cylinders;  /* capacity of the scene buffers (cp_set_scene); 0 = scene's */
     int32_t max_boxes;
+    double grid_cell;       /* > 0: evaluate through a uniform 2-D obstacle grid with cells of
+                               this side (m); 0: every sphere against every obstacle */
+    double grid_half_extent;/* half side of the square grid window centred on the base (m);
+                               0 = boom_len + jib_len + max|q4 limit| + 4 */
+    int64_t max_grid_items; /* capacity of the cell lists; 0 = bound of the initial scene */
 } cp_params;
 
 /* Cost terms of the final mean path and the state of a finished plan. */

@@ -60,7 +60,9 @@ class cp_params(ctypes.Structure):
                 ("lambda_c", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("eps", ctypes.c_double), ("init_std_frac", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("query", ctypes.c_uint32),
-                ("max_cylinders", ctypes.c_int32), ("max_boxes", ctypes.c_int32)]
+                ("max_cylinders", ctypes.c_int32), ("max_boxes", ctypes.c_int32),
+                ("grid_cell", ctypes.c_double), ("grid_half_extent", ctypes.c_double),
+                ("max_grid_items", ctypes.c_int64)]
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -202,9 +204,11 @@ class HostScene:
 def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 w_l: float = 100.0, lambda_c: float = 1.0, sigma: float = 1.0,
                 eps: float = 1e-8, init_std_frac: float = 0.1, seed: int = 0, query: int = 0,
-                max_cylinders: int = 0, max_boxes: int = 0) -> cp_params:
+                max_cylinders: int = 0, max_boxes: int = 0, grid_cell: float = 0.0,
+                grid_half_extent: float = 0.0, max_grid_items: int = 0) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
-                     query, max_cylinders, max_boxes)
+                     query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
+                     max_grid_items)
 
 
 # --------------------------------------------------------------------------- entry points

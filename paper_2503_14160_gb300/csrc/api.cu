@@ -140,6 +140,11 @@ struct cp_planner {
     float *mean_xi = nullptr;
     double *mean_J = nullptr, *mean_terms = nullptr;
     uint8_t *mean_flag = nullptr;
+    bool use_grid = false;
+    GridDev gdev{};
+    int64_t grid_cap = 0;
+    int *grid_count = nullptr, *grid_cursor = nullptr, *grid_start = nullptr;
+    int *grid_items = nullptr, *grid_outside = nullptr, *grid_counters = nullptr;
     bool have_endpoints = false;
     float4 q0f{}, qdf{};
     int iteration = 0;
@@ -241,6 +246,9 @@ int validate_params(const cp_params *p)
         !is_finite(p->w_l) || !is_finite(p->lambda_c))
         return set_error("cost weights must be finite and >= 0"), CP_ERR_ARG;
     if (p->max_cylinders < 0 || p->max_boxes < 0) return set_error("negative capacity"), CP_ERR_ARG;
+    if (!(p->grid_cell >= 0.0) || !is_finite(p->grid_cell) || !(p->grid_half_extent >= 0.0) ||
+        !is_finite(p->grid_half_extent) || p->max_grid_items < 0)
+        return set_error("grid_cell, grid_half_extent and max_grid_items must be >= 0"), CP_ERR_ARG;
     const int64_t n_s = (int64_t)(p->n_waypoints + 3) * p->substeps;
     if ((int64_t)p->n_candidates * ((n_s + 31) / 32) > 0x7FFFFFFF)
         return set_error("n_candidates * ceil(n_s / 32) exceeds 2^31 - 1"), CP_ERR_ARG;
@@ -263,6 +271,15 @@ int stage_scene(cp_planner *p, const cp_scene *sc)
     if (rc != CP_OK) return rc;
     p->sdev.n_cyl = sc->n_cyl;
     p->sdev.n_box = sc->n_box;
+    if (p->use_grid) {
+        const int64_t need = grid_items_bound(sc, p->mdev.r_max, p->prm.grid_cell);
+        if (need > p->grid_cap)
+            return set_error("scene may need %lld grid entries; capacity %lld (max_grid_items)",
+                             (long long)need, (long long)p->grid_cap), CP_ERR_ARG;
+        rc = launch_grid_build(p->sdev, p->gdev, p->mdev.r_max, p->grid_count, p->grid_cursor,
+                               p->grid_start, p->grid_items, p->grid_outside, p->grid_counters, p->st);
+        if (rc != CP_OK) return rc;
+    }
     return CP_OK;
 }
 
@@ -284,7 +301,8 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.pen_out = d_pen;
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
-    rc = launch_eval(p->mdev, p->sdev, a, p->num_sms, p->st);
+    rc = p->use_grid ? launch_eval_grid(p->mdev, p->sdev, p->gdev, a, p->num_sms, p->st)
+                     : launch_eval(p->mdev, p->sdev, a, p->num_sms, p->st);
     if (rc != CP_OK) return rc;
     rc = p->timer.end(ST_EVAL, p->st);
     if (rc != CP_OK) return rc;
@@ -397,7 +415,30 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     int smem_optin = 0;
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
-    const size_t eval_smem = eval_smem_bytes(p->cap_cyl, p->cap_box, p->S);
+    p->use_grid = params->grid_cell > 0.0;
+    int64_t cells = 0;
+    if (p->use_grid) {
+        const double h = params->grid_cell;
+        double W = params->grid_half_extent;
+        if (W <= 0.0)
+            W = model->boom_len + model->jib_len +
+                std::fmax(std::fabs(model->q_min[3]), std::fabs(model->q_max[3])) + 4.0;
+        const int64_t n_axis = (int64_t)std::ceil(2.0 * W / h);
+        if (n_axis < 1 || n_axis * n_axis > (1 << 22)) {
+            set_error("grid of %lld x %lld cells is outside 1..2^22 cells", (long long)n_axis,
+                      (long long)n_axis);
+            return fail(CP_ERR_ARG);
+        }
+        cells = n_axis * n_axis;
+        p->gdev.x0 = (float)(-0.5 * n_axis * h);
+        p->gdev.y0 = p->gdev.x0;
+        p->gdev.inv_h = (float)(1.0 / h);
+        p->gdev.nx = p->gdev.ny = (int)n_axis;
+        p->grid_cap = params->max_grid_items > 0 ? params->max_grid_items
+                                                 : grid_items_bound(scene, p->mdev.r_max, h);
+        if (p->grid_cap < 1) p->grid_cap = 1;
+    }
+    const size_t eval_smem = p->use_grid ? 0 : eval_smem_bytes(p->cap_cyl, p->cap_box, p->S);
     if (eval_smem > (size_t)smem_optin) {
         set_error("scene capacity (%d cylinders, %d boxes) needs %zu B of shared memory; the "
                   "device allows %d B per block", p->cap_cyl, p->cap_box, eval_smem, smem_optin);
@@ -441,6 +482,12 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_mean_J = L.take<double>(1);
     const size_t o_mean_terms = L.take<double>(5);
     const size_t o_mean_flag = L.take<uint8_t>(1);
+    const size_t o_grid_count = L.take<int>((size_t)cells + 1);
+    const size_t o_grid_cursor = L.take<int>((size_t)cells + 1);
+    const size_t o_grid_start = L.take<int>((size_t)cells + 1);
+    const size_t o_grid_items = L.take<int>(p->use_grid ? (size_t)p->grid_cap : 1);
+    const size_t o_grid_outside = L.take<int>((size_t)p->cap_cyl + p->cap_box + 1);
+    const size_t o_grid_counters = L.take<int>(2);
     e = cudaMalloc((void **)&p->base, L.bytes);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(workspace)"));
     char *b = p->base;
@@ -475,6 +522,16 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mean_J = (double *)(b + o_mean_J);
     p->mean_terms = (double *)(b + o_mean_terms);
     p->mean_flag = (uint8_t *)(b + o_mean_flag);
+    p->grid_count = (int *)(b + o_grid_count);
+    p->grid_cursor = (int *)(b + o_grid_cursor);
+    p->grid_start = (int *)(b + o_grid_start);
+    p->grid_items = (int *)(b + o_grid_items);
+    p->grid_outside = (int *)(b + o_grid_outside);
+    p->grid_counters = (int *)(b + o_grid_counters);
+    p->gdev.cell_start = p->grid_start;
+    p->gdev.items = p->grid_items;
+    p->gdev.outside = p->grid_outside;
+    p->gdev.n_outside = p->grid_counters;
     p->sdev.cyl_filt = p->cyl_filt;
     p->sdev.cyl_exact = p->cyl_exact;
     p->sdev.box_c = p->box_c;

@@ -64,6 +64,17 @@ struct SceneDev {
     int n_box;
 };
 
+// Uniform grid of obstacle ids over a square window (cells h x h, nx x ny).
+struct GridDev {
+    float x0, y0;            // window corner
+    float inv_h;
+    int nx, ny;
+    const int *cell_start;   // [nx ny + 1]
+    const int *items;        // obstacle ids: < n_cyl cylinder, else box (id - n_cyl)
+    const int *outside;      // ids whose dilated footprint leaves the window
+    const int *n_outside;    // [1]
+};
+
 // Margin of the fast 2-D cylinder filter, in m^2: a pair reaches the exact distance test
 // when (rho^2 - (R + r_max)^2), evaluated in float32 in expanded form, is below it. The
 // rounding error of that form for a pair within reach of the crane is below 3e-4 m^2.
@@ -94,6 +105,12 @@ int launch_signed_distance(const ModelDev &m, const SceneDev &sc, const float *q
 size_t eval_smem_bytes(int n_cyl, int n_box, int S);
 int eval_configure(size_t smem_bytes);
 int eval_ensure_smem(size_t smem_bytes);
+
+int64_t grid_items_bound(const cp_scene *sc, double r_max, double h);
+int launch_grid_build(const SceneDev &sc, const GridDev &g, float r_max, int *count, int *cursor,
+                      int *start, int *items, int *outside, int *counters, cudaStream_t st);
+int launch_eval_grid(const ModelDev &m, const SceneDev &sc, const GridDev &g, const EvalArgs &a,
+                     int num_sms, cudaStream_t st);
 
 int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d_box_in,
                          int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact,

@@ -1,0 +1,131 @@
+// Device code shared by the evaluation kernels (brute-force and grid): signed distances,
+// crane kinematics, the spline at one checkpoint and the per-unit reduction.
+#pragma once
+
+#include <math_constants.h>
+
+#include "cp_internal.cuh"
+
+namespace cp {
+
+static __device__ __forceinline__ float sdf_cylinder(float x, float y, float z, float cx, float cy,
+                                              float4 e /* R, z_lo, z_hi */)
+{
+    const float dx = x - cx, dy = y - cy;
+    const float rho = sqrtf(fmaf(dx, dx, dy * dy));
+    const float a = rho - e.x;
+    const float b = fmaxf(e.y - z, z - e.z);
+    const float ap = fmaxf(a, 0.f), bp = fmaxf(b, 0.f);
+    return fminf(fmaxf(a, b), 0.f) + sqrtf(fmaf(ap, ap, bp * bp));
+}
+
+static __device__ __forceinline__ float sdf_box(float x, float y, float z, float4 c, float4 h)
+{
+    const float qx = fabsf(x - c.x) - h.x;
+    const float qy = fabsf(y - c.y) - h.y;
+    const float qz = fabsf(z - c.z) - h.z;
+    const float px = fmaxf(qx, 0.f), py = fmaxf(qy, 0.f), pz = fmaxf(qz, 0.f);
+    return sqrtf(fmaf(px, px, fmaf(py, py, pz * pz))) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+}
+
+// Sphere centres at configuration q (chain of Sec. 2 in the linear placement form).
+template <int NSPH>
+static __device__ __forceinline__ void crane_fk(const ModelDev &m, float4 q, float *x, float *y,
+                                         float *z)
+{
+    float s1, c1, s2, c2, s23, c23;
+    sincosf(q.x, &s1, &c1);
+    sincosf(q.y, &s2, &c2);
+    sincosf(q.y + q.z, &s23, &c23);
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s) {
+        const SphereLin sp = m.sph[s];
+        const float b = fmaf(sp.gamma, q.w, sp.beta);
+        const float h = fmaf(sp.alpha, c2, b * c23);
+        x[s] = c1 * h;
+        y[s] = s1 * h;
+        z[s] = m.base_z + fmaf(sp.alpha, s2, fmaf(b, s23, -sp.delta));
+    }
+}
+
+static __device__ __forceinline__ float4 combine4(float4 w, float4 p0, float4 p1, float4 p2, float4 p3)
+{
+    float4 r;
+    r.x = fmaf(w.x, p0.x, fmaf(w.y, p1.x, fmaf(w.z, p2.x, w.w * p3.x)));
+    r.y = fmaf(w.x, p0.y, fmaf(w.y, p1.y, fmaf(w.z, p2.y, w.w * p3.y)));
+    r.z = fmaf(w.x, p0.z, fmaf(w.y, p1.z, fmaf(w.z, p2.z, w.w * p3.z)));
+    r.w = fmaf(w.x, p0.w, fmaf(w.y, p1.w, fmaf(w.z, p2.w, w.w * p3.w)));
+    return r;
+}
+
+static __device__ __forceinline__ float limit_excess(float v, float lo, float hi)
+{
+    const float a = fmaxf(0.f, v - hi), b = fmaxf(0.f, lo - v);
+    return fmaf(a, a, b * b);
+}
+
+// Per lane: the checkpoint k = 32 chunk + lane + 1 of candidate `cand`, its configuration
+// q(s_k), the squared and plain length of the increment q(s_k) - q(s_{k-1}) and the
+// joint-limit excess (Eq. path opt). Lanes past n_s evaluate the last checkpoint and are
+// marked invalid.
+struct Checkpoint {
+    float4 q;
+    float jp, len, jl;
+    int k;
+    bool valid;
+};
+
+static __device__ __forceinline__ Checkpoint checkpoint_setup(const ModelDev &m, const EvalArgs &a,
+                                                              const float4 *s_basis, int cand,
+                                                              int chunk, int lane)
+{
+    Checkpoint c;
+    c.k = chunk * 32 + lane + 1;
+    c.valid = c.k <= a.n_s;
+    const int kc = c.valid ? c.k : a.n_s;
+    const int span = (kc - 1) / a.S;              // moving span - 1, 0..K+2
+    const int mstep = kc - span * a.S;            // 1..S within the span
+    // control points P_{span+1..span+4} of [q0 x4, xi (K), qd x4]
+    const float4 *xi = a.xi + (size_t)cand * a.K;
+    float4 P[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int g = span + 1 + i;
+        P[i] = g < 4 ? a.q0 : (g >= a.K + 4 ? a.qd : __ldg(xi + (g - 4)));
+    }
+    const float4 bw = s_basis[2 * (mstep - 1)];
+    const float4 dbw = s_basis[2 * (mstep - 1) + 1];
+    c.q = combine4(bw, P[0], P[1], P[2], P[3]);
+    const float4 dq = combine4(dbw, P[0], P[1], P[2], P[3]);   // q(s_k) - q(s_{k-1})
+    c.jp = fmaf(dq.x, dq.x, fmaf(dq.y, dq.y, fmaf(dq.z, dq.z, dq.w * dq.w)));
+    c.len = sqrtf(c.jp);
+    c.jl = limit_excess(c.q.x, m.q_min[0], m.q_max[0]) + limit_excess(c.q.y, m.q_min[1], m.q_max[1]) +
+           limit_excess(c.q.z, m.q_min[2], m.q_max[2]) + limit_excess(c.q.w, m.q_min[3], m.q_max[3]);
+    return c;
+}
+
+// Warp-shuffle sums (FP32) of the unit's lanes and the ballot of collision flags, written
+// chunk-major by lane 0; the per-checkpoint penalty goes to pen_out when asked.
+static __device__ __forceinline__ void unit_epilogue(const EvalArgs &a, const Checkpoint &c, float dmin,
+                                                     int cand, int chunk, int lane)
+{
+    const float pen = fmaxf(0.f, -dmin);
+    const bool hit = c.valid && (dmin < 0.f);
+    float v0 = c.valid ? c.jp : 0.f, v1 = c.valid ? pen : 0.f;
+    float v2 = c.valid ? c.jl : 0.f, v3 = c.valid ? c.len : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+        v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) {   // chunk-major, so the finalize reads coalesce
+        a.partial[(size_t)chunk * a.n + cand] = make_float4(v0, v1, v2, v3);
+        a.flagword[(size_t)chunk * a.n + cand] = word;
+    }
+    if (a.pen_out != nullptr && c.valid) a.pen_out[(size_t)cand * a.n_s + (c.k - 1)] = pen;
+}
+
+}  // namespace cp

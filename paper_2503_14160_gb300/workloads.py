@@ -191,6 +191,7 @@ class Workload:
     rad_lo: float
     rad_hi: float
     spacing: float = 0.0        # >0: Poisson-disc placement
+    grid_cell: float = 0.0      # >0: evaluate through a uniform obstacle grid of this cell
     n_box: int = 0
     box_r_in: float = 2.0
     box_r_out: float = 12.0
@@ -211,7 +212,7 @@ WORKLOADS: Dict[str, Workload] = {
     # Dense forest: 5000 trees (Poisson disc >= 0.8 m, 2-50 m annulus) + 50 boxes;
     # N=65536, K=32, S=128, 200 iterations.
     "dense_forest": Workload("dense_forest", 65536, 32, 128, 200, 5000, 2.0, 50.0, 0.1, 0.5,
-                             spacing=0.8, n_box=50),
+                             spacing=0.8, n_box=50, grid_cell=0.5),
     # Differentiable form: 1000 trees in a 2-14 m annulus; N=16384, K=32, S=64.
     "differentiable": Workload("differentiable", 16384, 32, 64, 0, 1000, 2.0, 14.0, 0.1, 0.4),
 }

@@ -155,6 +155,38 @@ def test_evaluate_single_large_full_size(lib, crane):
         s.close()
 
 
+@pytest.mark.parametrize("half,cell", [(0.0, 0.5), (5.0, 0.5), (0.0, 0.23)])
+def test_evaluate_grid_dense_forest(lib, crane, half, cell):
+    """The uniform-grid evaluation on the dense forest (5000 cylinders + 50 boxes) against
+    the oracle's brute force: default window, a 10 m window (spheres beyond it use the list
+    of obstacles that leave the window) and an odd cell size."""
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("dense_forest")
+    s = Setup(crane, workloads.make_scene(workloads.WORKLOADS["dense_forest"]), N=64, K=6,
+              S=16, grid_cell=cell, grid_half_extent=half)
+    try:
+        xi = workloads.random_candidates(q0, qd, 6, 64, seed=17)
+        g, o = check_eval(s, xi, q0, qd)
+        assert (o.d[:, 1:] < 0).any() and (o.d[:, 1:] > 0).any()
+    finally:
+        s.close()
+
+
+def test_evaluate_grid_dense_forest_full_size(lib, crane):
+    """The dense forest at its full size (N=65536, K=32, S=128) in one launch; the oracle
+    checks 8 candidates spread over the population."""
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("dense_forest")
+    s = Setup(crane, workloads.make_scene(workloads.WORKLOADS["dense_forest"]), N=65536, K=32,
+              S=128, grid_cell=0.5)
+    try:
+        xi = workloads.random_candidates(q0, qd, 32, 65536, seed=23, spread=(0.3, 0.15, 0.2, 0.3))
+        idx = np.array([0, 31, 32, 20000, 40000, 65503, 65504, 65535])
+        check_eval(s, xi, q0, qd, idx)
+    finally:
+        s.close()
+
+
 def test_signed_distance(lib, crane):
     """d(q) for configurations inside and beyond the joint limits."""
     import torch
