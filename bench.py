@@ -284,6 +284,96 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_differentiable(args):
+    """The differentiable form: adjoint of the smooth cost for N candidates (gradients/s),
+    and 10 gradient-descent polish steps on the 64 best candidates of a sampled population."""
+    import torch
+    from paper_2503_14160_gb300 import build, craneplan as cp, workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    cp.load()
+    wl = workloads.WORKLOADS["differentiable"]
+    crane = workloads.forestry_crane()
+    scene = workloads.make_scene(wl)
+    params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed)
+    planner = cp.Planner(crane, scene, params)
+    h = planner.handle
+    q0, qd, ok = select_endpoints_gpu(cp, planner, crane, wl.seed, rank)
+    cp.cp_set_endpoints(h, q0, qd)
+    N, K = wl.n_candidates, wl.n_waypoints
+    xi = torch.zeros(N, K, 4, device="cuda")
+    J = torch.zeros(N, dtype=torch.float64, device="cuda")
+    dxi = torch.zeros_like(xi)
+    cp.cp_sample(h, 0, xi)
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        cp.cp_smooth_cost_grad(h, xi, N, None, J, dxi)
+    times = []
+    l0 = cp.cp_launch_count()
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cp.cp_smooth_cost_grad(h, xi, N, None, J, dxi)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+    launches = cp.cp_launch_count() - l0
+    ms = float(np.mean(times))
+    # polish: 64 best of the population, 10 steps, alpha = 1e-3
+    cp.cp_evaluate(h, xi, N, J)
+    best = xi[torch.argsort(J)[:64]].contiguous()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    cp.cp_polish(h, best, 64, 10, 1e-3)
+    b.record(stream)
+    b.synchronize()
+    polish_ms = a.elapsed_time(b)
+    # end to end: candidates copied in from pinned host memory, gradients copied out
+    host_xi = xi.cpu().pin_memory()
+    host_g = torch.empty_like(host_xi).pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xi.copy_(host_xi, non_blocking=True)
+        cp.cp_smooth_cost_grad(h, xi, N, None, J, dxi)
+        host_g.copy_(dxi, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    line = {"metric": "candidate gradients/sec (adjoint of the smooth path cost)",
+            "value": N / (ms / 1e3), "unit": "gradients/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded crane-and-forest scene)",
+            "config": {"workload": "differentiable: N=%d K=%d S=%d cylinders=%d, softplus margin "
+                                   "0.05 m" % (N, K, wl.substeps, scene.n_cyl),
+                       "step": "one adjoint launch over all candidates",
+                       "l2": "flushed between steps (256 MB write)"},
+            "polish_ms": polish_ms, "polish": "64 best candidates x 10 steps, alpha 1e-3",
+            "e2e": {"value": N / (float(np.mean(e2e)) / 1e3), "unit": "gradients/s",
+                    "h2d_bytes_per_step": N * K * 16, "d2h_bytes_per_step": N * K * 16},
+            "gpu_launches": launches, "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        import oracle
+        oracle.set_threads(os.cpu_count() or 1)
+        pb = oracle.Problem(crane, scene, oracle.CostParams(K=K, S=wl.substeps))
+        x = xi[:2 * (os.cpu_count() or 1)].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.smooth_grad(pb, x, q0, qd)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": x.shape[0] / el, "unit": "gradients/s",
+                                "cores": oracle.get_threads(), "kind": "oracle",
+                                "sample": "%d analytic FP64 gradients" % x.shape[0]}
+    print(json.dumps(line), flush=True)
+    planner.close()
+
+
 def cpu_baseline(wl, crane, scene, q0, qd, seconds, max_batches=None):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample: candidate
     evaluations (step (2), which dominates a plan) of the same workload, in batches until
@@ -360,6 +450,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "differentiable":
+        run_differentiable(args)
     else:
         run_ours(args)
 

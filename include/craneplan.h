@@ -122,6 +122,8 @@ typedef struct cp_params {
     double grid_half_extent;/* half side of the square grid window centred on the base (m);
                                0 = boom_len + jib_len + max|q4 limit| + 4 */
     int64_t max_grid_items; /* capacity of the cell lists; 0 = bound of the initial scene */
+    double smooth_margin;   /* differentiable form: softplus margin m (m); 0 selects 0.05 */
+    double smooth_beta;     /* differentiable form: softplus width beta (m); 0 selects 0.01 */
 } cp_params;
 
 /* Cost terms of the final mean path and the state of a finished plan. */
@@ -237,6 +239,26 @@ int cp_get_elites(const cp_planner *p, int32_t *d_idx);
  * key = (uint32)seed, (uint32)(seed >> 32); d_out is uint32[n][4]. `stream` as above. */
 int cp_philox4x32_10(const uint32_t *d_ctr, uint64_t key, int64_t n, uint32_t *d_out,
                      void *stream);
+
+/* Differentiable form of the cost (the smooth surrogate of Eq. path opt used for gradient
+ * polish): J_s = J_p + w_c lambda_c sum_k sum_{sphere, obstacle} beta softplus((m - sd) / beta)
+ * + w_l J_l, with sd the pair's signed distance (Sec. 3.1), m = smooth_margin and
+ * beta = smooth_beta. Pairs with sd > m + 30 beta are skipped (each would add less than
+ * 1e-13 beta). d_xi is float[n][K][4] (n <= N); d_J receives double[n].
+ * Errors: CP_ERR_STATE (no end points), CP_ERR_ARG. */
+int cp_smooth_cost(cp_planner *p, const float *d_xi, int32_t n, double *d_J);
+
+/* Adjoint of cp_smooth_cost: d_dxi[i] = gJ[i] * dJ_s(xi_i)/dxi_i (float[n][K][4]), with
+ * d_gJ double[n] (NULL: all ones); d_J (may be NULL) receives J_s as in cp_smooth_cost. The
+ * forward pass is recomputed per checkpoint (no tape in memory); per-candidate sums are
+ * taken in a fixed order, so results are deterministic. Errors as cp_smooth_cost. */
+int cp_smooth_cost_grad(cp_planner *p, const float *d_xi, int32_t n, const double *d_gJ,
+                        double *d_J, float *d_dxi);
+
+/* Gradient polish: `steps` plain gradient-descent steps xi <- xi - alpha dJ_s/dxi on the n
+ * candidates d_xi (float[n][K][4], updated in place), e.g. the best candidates of a plan
+ * before they are handed to a trajectory optimiser. Errors as cp_smooth_cost. */
+int cp_polish(cp_planner *p, float *d_xi, int32_t n, int32_t steps, double alpha);
 
 /* Size of the fixed device scratch behind cp_evaluate_static (bytes, per GPU). */
 #define CP_STATIC_SCRATCH_BYTES (32u << 20)

@@ -22,6 +22,7 @@
  *   o_path_cost         J = J_p + w_c J_c + w_l J_l (Eq. path opt, all three sums)
  *   o_path_cost_batch   the same for N candidates (Algorithm 1 step (2)); OpenMP over candidates
  *   o_smooth_cost       the softplus-penalty variant of J used by the differentiable form
+ *   o_smooth_grad       its analytic gradient with respect to the K free control points
  *
  * Readings of the paper that the code depends on (the paper is silent or garbled here):
  *   chain   slew q1 about world z; boom pitch q2 (elevation from horizontal); jib pitch q3
@@ -415,6 +416,181 @@ void o_smooth_cost_batch(const o_model *m, const o_scene *sc, const o_cost_param
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i) J[i] = o_smooth_cost(m, sc, cp, xi + i * 4 * cp->K, q0, qd);
+}
+
+/* ------------------------------------------------------------------ gradient */
+
+/* Jacobian of every sphere centre with respect to q: jac[s][c][j] = d centre_s[c] / d q_j,
+ * from the chain of o_fk (each link point is a sum of terms in e_b, e_j and z). */
+static void fk_jacobian(const o_model *m, const double q[4], double *jac /* [n][3][4] */)
+{
+    const double c1 = cos(q[0]), s1 = sin(q[0]);
+    const double c2 = cos(q[1]), s2 = sin(q[1]);
+    const double a = q[1] + q[2];
+    const double c23 = cos(a), s23 = sin(a);
+    /* e_b and its derivatives by q1, q2; e_j and its derivatives by q1, q2 (= by q3) */
+    const double eb[3] = {c2 * c1, c2 * s1, s2};
+    const double deb1[3] = {-c2 * s1, c2 * c1, 0.0};
+    const double deb2[3] = {-s2 * c1, -s2 * s1, c2};
+    const double ej[3] = {c23 * c1, c23 * s1, s23};
+    const double dej1[3] = {-c23 * s1, c23 * c1, 0.0};
+    const double dej2[3] = {-s23 * c1, -s23 * s1, c23};
+    (void)eb;
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const double t = m->offset[s];
+        double A = 0.0, B = 0.0, G = 0.0;   /* centre = O + A e_b + (B + G q4) e_j + ... */
+        switch (m->link[s]) {
+        case 0: A = t; break;
+        case 1: A = m->boom_len; B = t; break;
+        case 2: A = m->boom_len; B = m->jib_len; G = t; break;
+        default: A = m->boom_len; B = m->jib_len; G = 1.0; break;
+        }
+        const double L = B + G * q[3];
+        double *J = jac + 12 * s;
+        for (int c = 0; c < 3; ++c) {
+            J[4 * c + 0] = A * deb1[c] + L * dej1[c];
+            J[4 * c + 1] = A * deb2[c] + L * dej2[c];
+            J[4 * c + 2] = L * dej2[c];
+            J[4 * c + 3] = G * ej[c];
+        }
+    }
+}
+
+/* Gradient of the capped-cylinder SDF at p (the SDF is piecewise smooth: radial on the
+ * side, axial on the caps, along (a, b) off the rim; inside, the nearer face). */
+static void sdf_cylinder_grad(const double p[3], const double *cyl, double g[3])
+{
+    const double dx = p[0] - cyl[0], dy = p[1] - cyl[1];
+    const double rho = hypot(dx, dy);
+    const double a = rho - cyl[2];
+    const double up = p[2] - cyl[4], down = cyl[3] - p[2];
+    const double b = fmax(down, up);
+    const double sz = up >= down ? 1.0 : -1.0;
+    const double ux = rho > 0.0 ? dx / rho : 0.0, uy = rho > 0.0 ? dy / rho : 0.0;
+    if (a > 0.0 && b > 0.0) {
+        const double h = hypot(a, b);
+        g[0] = a / h * ux;
+        g[1] = a / h * uy;
+        g[2] = b / h * sz;
+    } else if (a >= b) {
+        g[0] = ux;
+        g[1] = uy;
+        g[2] = 0.0;
+    } else {
+        g[0] = 0.0;
+        g[1] = 0.0;
+        g[2] = sz;
+    }
+}
+
+/* Gradient of the box SDF at p: outside, along the clamped offset; inside, the face of the
+ * largest q_i. */
+static void sdf_box_grad(const double p[3], const double *box, double g[3])
+{
+    double qv[3], sg[3], out = 0.0;
+    int imax = 0;
+    for (int c = 0; c < 3; ++c) {
+        const double centre = 0.5 * (box[c] + box[3 + c]);
+        const double half = 0.5 * (box[3 + c] - box[c]);
+        sg[c] = p[c] >= centre ? 1.0 : -1.0;
+        qv[c] = fabs(p[c] - centre) - half;
+        out += fmax(qv[c], 0.0) * fmax(qv[c], 0.0);
+        if (qv[c] > qv[imax]) imax = c;
+    }
+    if (out > 0.0) {
+        const double n = sqrt(out);
+        for (int c = 0; c < 3; ++c) g[c] = fmax(qv[c], 0.0) / n * sg[c];
+    } else {
+        for (int c = 0; c < 3; ++c) g[c] = c == imax ? sg[c] : 0.0;
+    }
+}
+
+/* logistic(x) = d softplus / dx */
+static double logistic(double x)
+{
+    return x >= 0.0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x));
+}
+
+/* d/dq of the smooth collision penalty at q (4 values). */
+static void smooth_penalty_grad(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                                const double q[4], double g[4])
+{
+    double centres[3 * O_MAX_SPHERES], jac[12 * O_MAX_SPHERES];
+    o_fk(m, q, centres, NULL, NULL);
+    fk_jacobian(m, q, jac);
+    for (int j = 0; j < 4; ++j) g[j] = 0.0;
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const double *p = centres + 3 * s;
+        double dp[3] = {0.0, 0.0, 0.0};   /* d penalty / d centre */
+        for (int o = 0; o < sc->n_cyl; ++o) {
+            const double sd = o_sdf_cylinder(p, sc->cyl + 5 * o) - m->radius[s];
+            const double w = -logistic((cp->margin - sd) / cp->beta);
+            double gs[3];
+            sdf_cylinder_grad(p, sc->cyl + 5 * o, gs);
+            for (int c = 0; c < 3; ++c) dp[c] += w * gs[c];
+        }
+        for (int o = 0; o < sc->n_box; ++o) {
+            const double sd = o_sdf_box(p, sc->box + 6 * o) - m->radius[s];
+            const double w = -logistic((cp->margin - sd) / cp->beta);
+            double gs[3];
+            sdf_box_grad(p, sc->box + 6 * o, gs);
+            for (int c = 0; c < 3; ++c) dp[c] += w * gs[c];
+        }
+        const double *J = jac + 12 * s;
+        for (int j = 0; j < 4; ++j)
+            for (int c = 0; c < 3; ++c) g[j] += cp->lambda_c * dp[c] * J[4 * c + j];
+    }
+}
+
+/* Gradient of J_smooth (o_smooth_cost) with respect to the K free control points xi[K][4].
+ * q(s_k) = sum_i N_i(tau_k) P_i is linear in the control points, so with r_k = dJ/dq(s_k),
+ * dJ/dxi_f = sum_k r_k N_{4+f}(tau_k), where
+ *   r_k = 2 (q_k - q_{k-1}) [k >= 1] - 2 (q_{k+1} - q_k) [k < n_s]
+ *       + w_c d(penalty)/dq (q_k) + w_l d(J_l terms)/dq (q_k)   [k >= 1]. */
+void o_smooth_grad(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                   const double *xi, const double q0[4], const double qd[4], double *grad)
+{
+    const int32_t K = cp->K, n_c = K + 8;
+    const int64_t n_s = (int64_t)(K + 3) * cp->S;
+    double P[4 * 72];
+    assemble_control_points(K, xi, q0, qd, P);
+    double *Q = (double *)malloc(sizeof(double) * 4 * (size_t)(n_s + 1));
+    for (int64_t k = 0; k <= n_s; ++k) o_bspline(P, n_c, checkpoint_tau(K, cp->S, k), Q + 4 * k);
+    for (int i = 0; i < 4 * K; ++i) grad[i] = 0.0;
+    for (int64_t k = 0; k <= n_s; ++k) {
+        const double *q = Q + 4 * k;
+        double r[4] = {0.0, 0.0, 0.0, 0.0};
+        if (k >= 1)
+            for (int c = 0; c < 4; ++c) r[c] += 2.0 * (q[c] - Q[4 * (k - 1) + c]);
+        if (k < n_s)
+            for (int c = 0; c < 4; ++c) r[c] -= 2.0 * (Q[4 * (k + 1) + c] - q[c]);
+        if (k >= 1) {
+            double gp[4];
+            smooth_penalty_grad(m, sc, cp, q, gp);
+            for (int c = 0; c < 4; ++c) {
+                const double hi = fmax(0.0, q[c] - m->q_max[c]);
+                const double lo = fmax(0.0, m->q_min[c] - q[c]);
+                r[c] += cp->w_c * gp[c] + cp->w_l * 2.0 * (hi - lo);
+            }
+        }
+        double basis[64];
+        o_bspline_basis(n_c, checkpoint_tau(K, cp->S, k), basis);
+        for (int f = 0; f < K; ++f) {
+            const double b = basis[4 + f];
+            if (b != 0.0)
+                for (int c = 0; c < 4; ++c) grad[4 * f + c] += r[c] * b;
+        }
+    }
+    free(Q);
+}
+
+void o_smooth_grad_batch(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                         const double *xi, int64_t n, const double q0[4], const double qd[4],
+                         double *grad)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i)
+        o_smooth_grad(m, sc, cp, xi + i * 4 * cp->K, q0, qd, grad + i * 4 * cp->K);
 }
 
 /* ------------------------------------------------------------------ threads */

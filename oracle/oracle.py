@@ -95,6 +95,9 @@ def lib():
         L.o_smooth_cost_batch.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Scene),
                                           ctypes.POINTER(_CostParams), dp, ctypes.c_int64,
                                           dp, dp, dp]
+        L.o_smooth_grad_batch.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Scene),
+                                          ctypes.POINTER(_CostParams), dp, ctypes.c_int64,
+                                          dp, dp, dp]
         L.o_set_threads.argtypes = [ctypes.c_int32]
         L.o_get_threads.restype = ctypes.c_int32
         _lib = L
@@ -259,6 +262,25 @@ def smooth_cost(problem: Problem, xi, q0, qd) -> np.ndarray:
                               ctypes.byref(problem.cp), _dp(xi), xi.shape[0], _dp(_c64(q0)),
                               _dp(_c64(qd)), _dp(J))
     return J
+
+
+def smooth_grad(problem: Problem, xi, q0, qd) -> np.ndarray:
+    """Analytic gradient of smooth_cost with respect to xi[n][K][4]."""
+    K = problem.cost.K
+    xi = _c64(xi).reshape(-1, K, 4)
+    g = np.zeros_like(xi)
+    lib().o_smooth_grad_batch(ctypes.byref(problem.model), ctypes.byref(problem.scene),
+                              ctypes.byref(problem.cp), _dp(xi), xi.shape[0], _dp(_c64(q0)),
+                              _dp(_c64(qd)), _dp(g))
+    return g
+
+
+def polish(problem: Problem, xi, q0, qd, steps: int, alpha: float) -> np.ndarray:
+    """Plain gradient descent on the smooth cost, xi <- xi - alpha grad, `steps` times."""
+    x = _c64(xi).reshape(-1, problem.cost.K, 4).copy()
+    for _ in range(steps):
+        x = x - alpha * smooth_grad(problem, x, q0, qd)
+    return x
 
 
 # --------------------------------------------------------------------------- Algorithm 1

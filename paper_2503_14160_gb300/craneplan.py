@@ -62,7 +62,8 @@ class cp_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("query", ctypes.c_uint32),
                 ("max_cylinders", ctypes.c_int32), ("max_boxes", ctypes.c_int32),
                 ("grid_cell", ctypes.c_double), ("grid_half_extent", ctypes.c_double),
-                ("max_grid_items", ctypes.c_int64)]
+                ("max_grid_items", ctypes.c_int64), ("smooth_margin", ctypes.c_double),
+                ("smooth_beta", ctypes.c_double)]
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -109,6 +110,9 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), _P, ctypes.c_int32,
                                           _P, _P, _P, _P]),
+    "cp_smooth_cost": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "cp_smooth_cost_grad": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
+    "cp_polish": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
     "cp_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cp_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(cp_timing)]),
 }
@@ -205,10 +209,11 @@ def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 w_l: float = 100.0, lambda_c: float = 1.0, sigma: float = 1.0,
                 eps: float = 1e-8, init_std_frac: float = 0.1, seed: int = 0, query: int = 0,
                 max_cylinders: int = 0, max_boxes: int = 0, grid_cell: float = 0.0,
-                grid_half_extent: float = 0.0, max_grid_items: int = 0) -> cp_params:
+                grid_half_extent: float = 0.0, max_grid_items: int = 0,
+                smooth_margin: float = 0.05, smooth_beta: float = 0.01) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
                      query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
-                     max_grid_items)
+                     max_grid_items, smooth_margin, smooth_beta)
 
 
 # --------------------------------------------------------------------------- entry points
@@ -305,6 +310,18 @@ def cp_evaluate_static(model: cp_model, cyl, n_cyl: int, box, n_box: int, K: int
                                      int(n_box), int(K), int(S), float(w_c), float(w_l),
                                      float(lambda_c), _c4(q0), _c4(qd), _ptr(xi), int(n),
                                      _ptr(J), _ptr(flag), _ptr(terms), _stream(stream)))
+
+
+def cp_smooth_cost(p: int, xi, n: int, J) -> None:
+    _check(load().cp_smooth_cost(p, _ptr(xi), int(n), _ptr(J)))
+
+
+def cp_smooth_cost_grad(p: int, xi, n: int, gJ, J, dxi) -> None:
+    _check(load().cp_smooth_cost_grad(p, _ptr(xi), int(n), _ptr(gJ), _ptr(J), _ptr(dxi)))
+
+
+def cp_polish(p: int, xi, n: int, steps: int, alpha: float) -> None:
+    _check(load().cp_polish(p, _ptr(xi), int(n), int(steps), float(alpha)))
 
 
 def cp_set_timing(p: int, on: bool) -> None:

@@ -140,6 +140,8 @@ struct cp_planner {
     float *mean_xi = nullptr;
     double *mean_J = nullptr, *mean_terms = nullptr;
     uint8_t *mean_flag = nullptr;
+    float *grad = nullptr;      // [N][D] gradient buffer for polish
+    int smem_optin = 0;
     bool use_grid = false;
     GridDev gdev{};
     int64_t grid_cap = 0;
@@ -247,8 +249,9 @@ int validate_params(const cp_params *p)
         return set_error("cost weights must be finite and >= 0"), CP_ERR_ARG;
     if (p->max_cylinders < 0 || p->max_boxes < 0) return set_error("negative capacity"), CP_ERR_ARG;
     if (!(p->grid_cell >= 0.0) || !is_finite(p->grid_cell) || !(p->grid_half_extent >= 0.0) ||
-        !is_finite(p->grid_half_extent) || p->max_grid_items < 0)
-        return set_error("grid_cell, grid_half_extent and max_grid_items must be >= 0"), CP_ERR_ARG;
+        !is_finite(p->grid_half_extent) || p->max_grid_items < 0 || !(p->smooth_margin >= 0.0) ||
+        !is_finite(p->smooth_margin) || !(p->smooth_beta >= 0.0) || !is_finite(p->smooth_beta))
+        return set_error("grid and smooth-penalty parameters must be finite and >= 0"), CP_ERR_ARG;
     const int64_t n_s = (int64_t)(p->n_waypoints + 3) * p->substeps;
     if ((int64_t)p->n_candidates * ((n_s + 31) / 32) > 0x7FFFFFFF)
         return set_error("n_candidates * ceil(n_s / 32) exceeds 2^31 - 1"), CP_ERR_ARG;
@@ -390,6 +393,8 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     if (!p) return set_error("host allocation failed"), CP_ERR_OOM;
     p->st = (cudaStream_t)stream;
     p->prm = *params;
+    if (p->prm.smooth_margin == 0.0) p->prm.smooth_margin = 0.05;
+    if (p->prm.smooth_beta == 0.0) p->prm.smooth_beta = 0.01;
     p->N = params->n_candidates;
     p->K = params->n_waypoints;
     p->S = params->substeps;
@@ -414,6 +419,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
     int smem_optin = 0;
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    p->smem_optin = smem_optin;
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
     p->use_grid = params->grid_cell > 0.0;
     int64_t cells = 0;
@@ -488,6 +494,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_grid_items = L.take<int>(p->use_grid ? (size_t)p->grid_cap : 1);
     const size_t o_grid_outside = L.take<int>((size_t)p->cap_cyl + p->cap_box + 1);
     const size_t o_grid_counters = L.take<int>(2);
+    const size_t o_grad = L.take<float>(N * D);
     e = cudaMalloc((void **)&p->base, L.bytes);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(workspace)"));
     char *b = p->base;
@@ -522,6 +529,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mean_J = (double *)(b + o_mean_J);
     p->mean_terms = (double *)(b + o_mean_terms);
     p->mean_flag = (uint8_t *)(b + o_mean_flag);
+    p->grad = (float *)(b + o_grad);
     p->grid_count = (int *)(b + o_grid_count);
     p->grid_cursor = (int *)(b + o_grid_cursor);
     p->grid_start = (int *)(b + o_grid_start);
@@ -652,6 +660,55 @@ int cp_plan(cp_planner *p, int32_t iters, double *h_ctrl, cp_plan_stats *stats)
         stats->iterations = iters;
         stats->iteration = p->iteration;
         stats->best_J = host[6];
+    }
+    return CP_OK;
+}
+
+static int smooth_check(cp_planner *p, int n, const void *xi)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (n < 0 || n > p->N) return set_error("n = %d outside 0..N = %d", n, p->N), CP_ERR_ARG;
+    if (n > 0 && !xi) return set_error("d_xi is NULL"), CP_ERR_ARG;
+    if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
+    const size_t smem = smooth_smem_bytes(p->sdev.n_cyl, p->sdev.n_box, p->S, p->K);
+    if (smem > (size_t)p->smem_optin)
+        return set_error("the smooth cost stages %zu B of obstacles per block; the device allows "
+                         "%d B", smem, p->smem_optin), CP_ERR_ARG;
+    return CP_OK;
+}
+
+static int run_smooth(cp_planner *p, const float *xi, int n, const double *gJ, double *J, float *dxi)
+{
+    return launch_smooth(p->mdev, p->sdev, xi, n, p->K, p->S, p->q0f, p->qdf, p->basis,
+                         p->prm.smooth_margin, p->prm.smooth_beta, p->prm.w_c * p->prm.lambda_c,
+                         p->prm.w_l, gJ, J, dxi, p->num_sms, p->st);
+}
+
+int cp_smooth_cost(cp_planner *p, const float *d_xi, int32_t n, double *d_J)
+{
+    int rc = smooth_check(p, n, d_xi);
+    if (rc != CP_OK) return rc;
+    if (n > 0 && !d_J) return set_error("d_J is NULL"), CP_ERR_ARG;
+    return run_smooth(p, d_xi, n, nullptr, d_J, nullptr);
+}
+
+int cp_smooth_cost_grad(cp_planner *p, const float *d_xi, int32_t n, const double *d_gJ,
+                        double *d_J, float *d_dxi)
+{
+    int rc = smooth_check(p, n, d_xi);
+    if (rc != CP_OK) return rc;
+    if (n > 0 && !d_dxi) return set_error("d_dxi is NULL"), CP_ERR_ARG;
+    return run_smooth(p, d_xi, n, d_gJ, d_J, d_dxi);
+}
+
+int cp_polish(cp_planner *p, float *d_xi, int32_t n, int32_t steps, double alpha)
+{
+    int rc = smooth_check(p, n, d_xi);
+    if (rc != CP_OK) return rc;
+    if (steps < 0 || !is_finite(alpha)) return set_error("steps >= 0 and finite alpha"), CP_ERR_ARG;
+    for (int s = 0; s < steps; ++s) {
+        if ((rc = run_smooth(p, d_xi, n, nullptr, nullptr, p->grad)) != CP_OK) return rc;
+        if ((rc = launch_axpy(d_xi, p->grad, alpha, (int64_t)n * p->D, p->st)) != CP_OK) return rc;
     }
     return CP_OK;
 }

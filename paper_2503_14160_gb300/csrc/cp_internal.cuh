@@ -112,6 +112,13 @@ int launch_grid_build(const SceneDev &sc, const GridDev &g, float r_max, int *co
 int launch_eval_grid(const ModelDev &m, const SceneDev &sc, const GridDev &g, const EvalArgs &a,
                      int num_sms, cudaStream_t st);
 
+size_t smooth_smem_bytes(int n_cyl, int n_box, int S, int K);
+int launch_smooth(const ModelDev &m, const SceneDev &sc, const float *xi, int n, int K, int S,
+                  float4 q0, float4 qd, const float4 *basis, double margin, double beta,
+                  double wc_lc, double w_l, const double *gJ, double *J, float *dxi, int num_sms,
+                  cudaStream_t st);
+int launch_axpy(float *x, const float *y, double alpha, int64_t n, cudaStream_t st);
+
 int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d_box_in,
                          int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact,
                          float4 *box_c, float4 *box_h, cudaStream_t st);

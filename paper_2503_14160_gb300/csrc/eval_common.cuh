@@ -64,6 +64,45 @@ static __device__ __forceinline__ float limit_excess(float v, float lo, float hi
     return fmaf(a, a, b * b);
 }
 
+// 1 when g[s] < t[s] for some s of the 12: one chain of compares, each folding the
+// running predicate in with setp's boolean OR, and one select at the end.
+static __device__ __forceinline__ uint32_t any_below12(const float2 *g, const float *t)
+{
+    uint32_t r;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.lt.f32 p, %1, %13;\n\t"
+        "setp.lt.or.f32 p, %2, %14, p;\n\t"
+        "setp.lt.or.f32 p, %3, %15, p;\n\t"
+        "setp.lt.or.f32 p, %4, %16, p;\n\t"
+        "setp.lt.or.f32 p, %5, %17, p;\n\t"
+        "setp.lt.or.f32 p, %6, %18, p;\n\t"
+        "setp.lt.or.f32 p, %7, %19, p;\n\t"
+        "setp.lt.or.f32 p, %8, %20, p;\n\t"
+        "setp.lt.or.f32 p, %9, %21, p;\n\t"
+        "setp.lt.or.f32 p, %10, %22, p;\n\t"
+        "setp.lt.or.f32 p, %11, %23, p;\n\t"
+        "setp.lt.or.f32 p, %12, %24, p;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "f"(g[0].x), "f"(g[0].y), "f"(g[1].x), "f"(g[1].y), "f"(g[2].x), "f"(g[2].y),
+          "f"(g[3].x), "f"(g[3].y), "f"(g[4].x), "f"(g[4].y), "f"(g[5].x), "f"(g[5].y),
+          "f"(t[0]), "f"(t[1]), "f"(t[2]), "f"(t[3]), "f"(t[4]), "f"(t[5]),
+          "f"(t[6]), "f"(t[7]), "f"(t[8]), "f"(t[9]), "f"(t[10]), "f"(t[11]));
+    return r;
+}
+
+template <int NSPH>
+static __device__ __forceinline__ uint32_t any_below(const float2 *g, const float *t)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int q = 0; q < NSPH / 12; ++q) r |= any_below12(g + 6 * q, t + 12 * q);
+#pragma unroll
+    for (int s = 12 * (NSPH / 12); s < NSPH; s += 2)
+        r |= (uint32_t)((g[s / 2].x < t[s]) | (g[s / 2].y < t[s + 1]));
+    return r;
+}
+
 // Per lane: the checkpoint k = 32 chunk + lane + 1 of candidate `cand`, its configuration
 // q(s_k), the squared and plain length of the increment q(s_k) - q(s_{k-1}) and the
 // joint-limit excess (Eq. path opt). Lanes past n_s evaluate the last checkpoint and are

@@ -1,0 +1,330 @@
+// Differentiable form of the cost and its adjoint (the smooth surrogate of Eq. path opt,
+// arXiv 2503.14160 Sec. 4.1, used to polish candidates before trajectory optimisation):
+//   J_s = sum_k |q(s_k) - q(s_{k-1})|^2 + w_c lambda_c sum_k sum_pairs beta softplus((m - sd)/beta)
+//         + w_l sum_k sum_j (max(0, q - q_max)^2 + max(0, q_min - q)^2)
+// q(s_k) is linear in the control points, so with r_k = dJ/dq(s_k) the gradient is
+//   dJ/dP_g = sum_k [2 (q_k - q_{k-1}) (b_g(s_k) - b_g(s_{k-1})) + r_k^pen b_g(s_k)],
+// r_k^pen chaining the softplus derivative through the signed-distance gradient and the
+// kinematic Jacobian. One warp per candidate walks its checkpoints 32 at a time (one per
+// lane), recomputing the forward pass (no tape); the per-control-point sums of a chunk are
+// reduced in a fixed lane order into a per-warp accumulator, so results are deterministic.
+#include "eval_common.cuh"
+
+namespace cp {
+namespace {
+
+constexpr int kSmoothThreads = 256;     // 8 warps, one candidate per warp
+constexpr float kSmoothCut = 30.f;      // pairs with sd > m + 30 beta are skipped
+
+struct SmoothArgs {
+    const float4 *xi;
+    int n, K, S, n_s, chunks;
+    float4 q0, qd;
+    const float4 *basis;     // [S][2] as in EvalArgs
+    float margin, beta;      // softplus margin m and width beta
+    float wc_lc, w_l;        // w_c lambda_c and w_l
+    const double *gJ;        // [n] or nullptr (ones)
+    double *J;               // [n] or nullptr
+    float *dxi;              // [n][K][4] or nullptr
+};
+
+__device__ __forceinline__ float softplus_f(float x)
+{
+    return x > 0.f ? x + log1pf(expf(-x)) : log1pf(expf(x));
+}
+
+__device__ __forceinline__ float logistic_f(float x)
+{
+    return x >= 0.f ? 1.f / (1.f + expf(-x)) : expf(x) / (1.f + expf(x));
+}
+
+// Gradient of the capped-cylinder SDF: radial on the side, axial on the caps, along (a, b)
+// off the rim; inside, the nearer face.
+__device__ __forceinline__ float3 sdf_cylinder_grad(float x, float y, float z, float cx, float cy,
+                                                    float4 e)
+{
+    const float dx = x - cx, dy = y - cy;
+    const float rho = sqrtf(fmaf(dx, dx, dy * dy));
+    const float a = rho - e.x;
+    const float up = z - e.z, down = e.y - z;
+    const float b = fmaxf(down, up);
+    const float sz = up >= down ? 1.f : -1.f;
+    const float ux = rho > 0.f ? dx / rho : 0.f, uy = rho > 0.f ? dy / rho : 0.f;
+    if (a > 0.f && b > 0.f) {
+        const float h = sqrtf(fmaf(a, a, b * b));
+        return make_float3(a / h * ux, a / h * uy, b / h * sz);
+    }
+    if (a >= b) return make_float3(ux, uy, 0.f);
+    return make_float3(0.f, 0.f, sz);
+}
+
+// Gradient of the box SDF: outside, along the clamped offset; inside, the face of the
+// largest component.
+__device__ __forceinline__ float3 sdf_box_grad(float x, float y, float z, float4 c, float4 h)
+{
+    const float sx = x >= c.x ? 1.f : -1.f, sy = y >= c.y ? 1.f : -1.f, sz = z >= c.z ? 1.f : -1.f;
+    const float qx = fabsf(x - c.x) - h.x, qy = fabsf(y - c.y) - h.y, qz = fabsf(z - c.z) - h.z;
+    const float px = fmaxf(qx, 0.f), py = fmaxf(qy, 0.f), pz = fmaxf(qz, 0.f);
+    const float out = fmaf(px, px, fmaf(py, py, pz * pz));
+    if (out > 0.f) {
+        const float inv = rsqrtf(out);
+        return make_float3(px * inv * sx, py * inv * sy, pz * inv * sz);
+    }
+    if (qx >= qy && qx >= qz) return make_float3(sx, 0.f, 0.f);
+    if (qy >= qz) return make_float3(0.f, sy, 0.f);
+    return make_float3(0.f, 0.f, sz);
+}
+
+// Softplus term of one pair and (GRAD) its contribution to d penalty / d centre.
+template <bool GRAD>
+__device__ __forceinline__ void pair_term(float sd, float3 grad_sdf, float m, float beta,
+                                          float &pen, float3 &dp)
+{
+    const float x = (m - sd) / beta;
+    pen = fmaf(beta, softplus_f(x), pen);
+    if (GRAD) {
+        const float w = -logistic_f(x);
+        dp.x = fmaf(w, grad_sdf.x, dp.x);
+        dp.y = fmaf(w, grad_sdf.y, dp.y);
+        dp.z = fmaf(w, grad_sdf.z, dp.z);
+    }
+}
+
+template <int NSPH, bool GRAD>
+__global__ void __launch_bounds__(kSmoothThreads)
+k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
+{
+    extern __shared__ __align__(16) float4 smem[];
+    float4 *s_filt = smem;                      // {cx, cy, W_s, 0}
+    float4 *s_exact = s_filt + sc.n_cyl;        // {R, z_lo, z_hi, 0}
+    float4 *s_bc = s_exact + sc.n_cyl;
+    float4 *s_bh = s_bc + sc.n_box;
+    float4 *s_basis = s_bh + sc.n_box;
+    float *s_warp = reinterpret_cast<float *>(s_basis + 2 * a.S);
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per_warp = 32 * 16 + 32 + 4 * a.K;
+    float *s_contrib = s_warp + wib * per_warp;              // [32][4 control points][4]
+    int *s_span = reinterpret_cast<int *>(s_contrib + 32 * 16);
+    float *s_acc = s_contrib + 32 * 16 + 32;                 // [K][4]
+    const double reach = (double)m.r_max + (double)a.margin + (double)kSmoothCut * a.beta;
+    for (int i = threadIdx.x; i < sc.n_cyl; i += blockDim.x) {
+        const float4 f = sc.cyl_filt[i], e = sc.cyl_exact[i];
+        const double R = (double)e.x + reach;
+        const double W = (double)f.x * f.x + (double)f.y * f.y - R * R;
+        s_filt[i] = make_float4(f.x, f.y, (float)W, 0.f);
+        s_exact[i] = e;
+    }
+    for (int i = threadIdx.x; i < sc.n_box; i += blockDim.x) {
+        s_bc[i] = sc.box_c[i];
+        s_bh[i] = sc.box_h[i];
+    }
+    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x) s_basis[i] = a.basis[i];
+    __syncthreads();
+
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int cand = warp; cand < a.n; cand += n_warps) {
+        if (GRAD)
+            for (int t = lane; t < 4 * a.K; t += 32) s_acc[t] = 0.f;
+        double J = 0.0;
+        const float4 *xi = a.xi + (size_t)cand * a.K;
+        for (int chunk = 0; chunk < a.chunks; ++chunk) {
+            const int k = chunk * 32 + lane + 1;
+            const bool valid = k <= a.n_s;
+            const int kc = valid ? k : a.n_s;
+            const int span = (kc - 1) / a.S;
+            const int mstep = kc - span * a.S;
+            float4 P[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int g = span + 1 + i;
+                P[i] = g < 4 ? a.q0 : (g >= a.K + 4 ? a.qd : __ldg(xi + (g - 4)));
+            }
+            const float4 bw = s_basis[2 * (mstep - 1)], dbw = s_basis[2 * (mstep - 1) + 1];
+            const float4 q = combine4(bw, P[0], P[1], P[2], P[3]);
+            const float4 dq = combine4(dbw, P[0], P[1], P[2], P[3]);
+            const float jp = fmaf(dq.x, dq.x, fmaf(dq.y, dq.y, fmaf(dq.z, dq.z, dq.w * dq.w)));
+            const float jl = limit_excess(q.x, m.q_min[0], m.q_max[0]) + limit_excess(q.y, m.q_min[1], m.q_max[1]) +
+                             limit_excess(q.z, m.q_min[2], m.q_max[2]) + limit_excess(q.w, m.q_min[3], m.q_max[3]);
+
+            float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH];
+            crane_fk<NSPH>(m, q, X, Y, Z);
+            float3 dp[NSPH];
+#pragma unroll
+            for (int s = 0; s < NSPH; ++s) {
+                T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
+                dp[s] = make_float3(0.f, 0.f, 0.f);
+            }
+            float pen = 0.f;
+            for (int o = 0; o < sc.n_cyl; ++o) {
+                const float4 f = s_filt[o];
+                float2 g[NSPH / 2];
+#pragma unroll
+                for (int p = 0; p < NSPH / 2; ++p) {
+                    const float2 x2 = make_float2(-2.f * X[2 * p], -2.f * X[2 * p + 1]);
+                    const float2 y2 = make_float2(-2.f * Y[2 * p], -2.f * Y[2 * p + 1]);
+                    g[p] = __ffma2_rn(x2, make_float2(f.x, f.x),
+                                      __ffma2_rn(y2, make_float2(f.y, f.y), make_float2(f.z, f.z)));
+                }
+                if (any_below<NSPH>(g, T)) {
+                    const float4 e = s_exact[o];
+#pragma unroll
+                    for (int s = 0; s < NSPH; ++s) {
+                        const float gs = (s & 1) ? g[s / 2].y : g[s / 2].x;
+                        if (gs < T[s]) {
+                            const float sd = sdf_cylinder(X[s], Y[s], Z[s], f.x, f.y, e) - m.sph[s].radius;
+                            const float3 gr = GRAD ? sdf_cylinder_grad(X[s], Y[s], Z[s], f.x, f.y, e)
+                                                   : make_float3(0.f, 0.f, 0.f);
+                            pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, dp[s]);
+                        }
+                    }
+                }
+            }
+            for (int o = 0; o < sc.n_box; ++o) {
+                const float4 c = s_bc[o], h = s_bh[o];
+#pragma unroll
+                for (int s = 0; s < NSPH; ++s) {
+                    const float sd = sdf_box(X[s], Y[s], Z[s], c, h) - m.sph[s].radius;
+                    if (sd < a.margin + kSmoothCut * a.beta) {
+                        const float3 gr = GRAD ? sdf_box_grad(X[s], Y[s], Z[s], c, h)
+                                               : make_float3(0.f, 0.f, 0.f);
+                        pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, dp[s]);
+                    }
+                }
+            }
+
+            float v = valid ? jp + a.wc_lc * pen + a.w_l * jl : 0.f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            J += (double)v;   // every lane holds the same sum; lane 0 writes it
+
+            if (GRAD) {
+                // r = d(terms at s_k)/dq: penalty through the kinematic Jacobian, and limits
+                float s1, c1, s2, c2, s23, c23;
+                sincosf(q.x, &s1, &c1);
+                sincosf(q.y, &s2, &c2);
+                sincosf(q.y + q.z, &s23, &c23);
+                float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+#pragma unroll
+                for (int s = 0; s < NSPH; ++s) {
+                    const SphereLin sp = m.sph[s];
+                    const float L = fmaf(sp.gamma, q.w, sp.beta);
+                    const float u = fmaf(sp.alpha, s2, L * s23);     // d h / d q2 = -u
+                    const float hz = fmaf(sp.alpha, c2, L * c23);    // horizontal reach
+                    const float3 d = dp[s];
+                    r0 += fmaf(-d.x, Y[s], d.y * X[s]);
+                    r1 += fmaf(d.x, -c1 * u, fmaf(d.y, -s1 * u, d.z * hz));
+                    r2 += L * fmaf(d.x, -c1 * s23, fmaf(d.y, -s1 * s23, d.z * c23));
+                    r3 += sp.gamma * fmaf(d.x, c1 * c23, fmaf(d.y, s1 * c23, d.z * s23));
+                }
+                const float4 lim2 = make_float4(
+                    2.f * (fmaxf(0.f, q.x - m.q_max[0]) - fmaxf(0.f, m.q_min[0] - q.x)),
+                    2.f * (fmaxf(0.f, q.y - m.q_max[1]) - fmaxf(0.f, m.q_min[1] - q.y)),
+                    2.f * (fmaxf(0.f, q.z - m.q_max[2]) - fmaxf(0.f, m.q_min[2] - q.z)),
+                    2.f * (fmaxf(0.f, q.w - m.q_max[3]) - fmaxf(0.f, m.q_min[3] - q.w)));
+                const float4 r = make_float4(fmaf(a.wc_lc, r0, a.w_l * lim2.x), fmaf(a.wc_lc, r1, a.w_l * lim2.y),
+                                             fmaf(a.wc_lc, r2, a.w_l * lim2.z), fmaf(a.wc_lc, r3, a.w_l * lim2.w));
+                // contribution to control point span+1+i: 2 dq db_i + r b_i
+                const float bi[4] = {bw.x, bw.y, bw.z, bw.w}, dbi[4] = {dbw.x, dbw.y, dbw.z, dbw.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float wd = valid ? 2.f * dbi[i] : 0.f, wb = valid ? bi[i] : 0.f;
+                    s_contrib[lane * 16 + 4 * i + 0] = fmaf(wd, dq.x, wb * r.x);
+                    s_contrib[lane * 16 + 4 * i + 1] = fmaf(wd, dq.y, wb * r.y);
+                    s_contrib[lane * 16 + 4 * i + 2] = fmaf(wd, dq.z, wb * r.z);
+                    s_contrib[lane * 16 + 4 * i + 3] = fmaf(wd, dq.w, wb * r.w);
+                }
+                s_span[lane] = span;
+                __syncwarp();
+                // fixed-order sums over the lanes for every (control point, joint) touched
+                const int g_lo = s_span[0] + 1, g_hi = s_span[31] + 4;
+                for (int t = lane; t < 4 * (g_hi - g_lo + 1); t += 32) {
+                    const int G = g_lo + (t >> 2), j = t & 3;
+                    float acc = 0.f;
+                    for (int l = 0; l < 32; ++l) {
+                        const int i = G - s_span[l] - 1;
+                        if (i >= 0 && i < 4) acc += s_contrib[l * 16 + 4 * i + j];
+                    }
+                    if (G >= 4 && G < a.K + 4) s_acc[(G - 4) * 4 + j] += acc;
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0 && a.J != nullptr) a.J[cand] = J;
+        if (GRAD) {
+            const float gj = a.gJ != nullptr ? (float)a.gJ[cand] : 1.f;
+            for (int t = lane; t < 4 * a.K; t += 32) a.dxi[(size_t)cand * 4 * a.K + t] = gj * s_acc[t];
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void k_axpy(float *x, const float *y, float alpha, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = fmaf(-alpha, y[i], x[i]);
+}
+
+size_t smooth_smem(int n_cyl, int n_box, int S, int K)
+{
+    return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S) +
+           sizeof(float) * (kSmoothThreads / 32) * (size_t)(32 * 16 + 32 + 4 * K);
+}
+
+template <bool GRAD>
+int launch_smooth_t(const ModelDev &m, const SceneDev &sc, const SmoothArgs &a, int num_sms,
+                    cudaStream_t st)
+{
+    const size_t smem = smooth_smem(sc.n_cyl, sc.n_box, a.S, a.K);
+    auto kern = m.n_spheres == 12 ? k_smooth<12, GRAD> : k_smooth<16, GRAD>;
+    CP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmoothThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int grid = (a.n + kSmoothThreads / 32 - 1) / (kSmoothThreads / 32);
+    if (grid > num_sms * per_sm) grid = num_sms * per_sm;
+    kern<<<grid, kSmoothThreads, smem, st>>>(m, sc, a);
+    CP_LAUNCHED("k_smooth");
+    return CP_OK;
+}
+
+}  // namespace
+
+size_t smooth_smem_bytes(int n_cyl, int n_box, int S, int K) { return smooth_smem(n_cyl, n_box, S, K); }
+
+int launch_smooth(const ModelDev &m, const SceneDev &sc, const float *xi, int n, int K, int S,
+                  float4 q0, float4 qd, const float4 *basis, double margin, double beta,
+                  double wc_lc, double w_l, const double *gJ, double *J, float *dxi, int num_sms,
+                  cudaStream_t st)
+{
+    if (n == 0) return CP_OK;
+    SmoothArgs a{};
+    a.xi = (const float4 *)xi;
+    a.n = n;
+    a.K = K;
+    a.S = S;
+    a.n_s = (K + 3) * S;
+    a.chunks = (a.n_s + 31) / 32;
+    a.q0 = q0;
+    a.qd = qd;
+    a.basis = basis;
+    a.margin = (float)margin;
+    a.beta = (float)beta;
+    a.wc_lc = (float)wc_lc;
+    a.w_l = (float)w_l;
+    a.gJ = gJ;
+    a.J = J;
+    a.dxi = dxi;
+    return dxi != nullptr ? launch_smooth_t<true>(m, sc, a, num_sms, st)
+                          : launch_smooth_t<false>(m, sc, a, num_sms, st);
+}
+
+int launch_axpy(float *x, const float *y, double alpha, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return CP_OK;
+    k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, (float)alpha, n);
+    CP_LAUNCHED("k_axpy");
+    return CP_OK;
+}
+
+}  // namespace cp
