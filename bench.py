@@ -374,6 +374,79 @@ def run_differentiable(args):
     planner.close()
 
 
+def run_batch(args):
+    """The batched serving form: 64 queries of uneven size (N ~ U[1024, 16384], K ~ U[8, 32],
+    M ~ U[50, 3000] cylinders, S = 64, 100 iterations) planned by one graph launch, against the
+    same queries planned one after another with cp_plan. Launch shapes per size bucket come
+    from the autotuner."""
+    import torch
+    from paper_2503_14160_gb300 import autotune, build, craneplan as cp, workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    cp.load()
+    crane = workloads.forestry_crane()
+    model = cp.make_model(crane)
+    S, T = 64, args.iterations or 100
+    queries = workloads.batch_queries(64, seed=rank)
+    tuner = autotune.Autotuner()
+    t_tune = time.perf_counter()
+    cfgs = [tuner.best(crane, bq.n_candidates, bq.n_waypoints, S, bq.n_cyl) for bq in queries]
+    t_tune = time.perf_counter() - t_tune
+    scenes, params, q0s, qds = [], [], [], []
+    for q, (bq, cfg) in enumerate(zip(queries, cfgs)):
+        sc = workloads.batch_scene(bq, seed=rank, q=q)
+        with cp.Planner(crane, sc, cp.make_params(64, bq.n_waypoints, S)) as tmp:
+            q0, qd, _ = select_endpoints_gpu(cp, tmp, crane, rank, q)
+        scenes.append(cp.HostScene.from_scene(sc))
+        params.append(cp.make_params(bq.n_candidates, bq.n_waypoints, S, seed=rank, query=q, **cfg))
+        q0s.append(q0)
+        qds.append(qd)
+    t0 = time.perf_counter()
+    b = cp.cp_batch_init(model, scenes, params, q0s, qds, T)
+    t_init = time.perf_counter() - t0
+    units = sum(bq.n_candidates for bq in queries) * T
+    for _ in range(args.warmup):
+        cp.cp_batch_run(b, 64)
+    batch_ms = []
+    l0 = cp.cp_launch_count()
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = cp.cp_batch_run(b, 64)
+            batch_ms.append((time.perf_counter() - t0) * 1e3)
+    launches = cp.cp_launch_count() - l0
+    seq_ms = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in range(64):
+            p = cp.cp_batch_planner(b, q)
+            cp.cp_set_endpoints(p, q0s[q], qds[q])
+            cp.cp_plan(p, T)
+        seq_ms.append((time.perf_counter() - t0) * 1e3)
+    ms, ms_seq = float(np.mean(batch_ms)), float(np.mean(seq_ms))
+    grid_q = sum(1 for c in cfgs if c["grid_cell"] > 0)
+    line = {"metric": "candidate paths evaluated/sec, 64-query batch (one CUDA graph) vs sequential",
+            "value": units / (ms / 1e3), "unit": "candidate paths/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded crane-and-forest scenes)",
+            "config": {"workload": "64 queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
+                                   "S=64, %d iterations" % T, "step": "one batch (all queries)"},
+            "sequential": {"value": units / (ms_seq / 1e3), "ms_per_batch": ms_seq},
+            "speedup_vs_sequential": ms_seq / ms,
+            "graph_record_and_instantiate_s": t_init, "autotune_s": t_tune,
+            "queries_on_grid": grid_q,
+            "collision_free": sum(1 for _, st in res if st["flag"] == 0),
+            "gpu_launches": launches, "clocks": clocks.summary(),
+            "e2e": {"value": units / (ms / 1e3), "unit": "candidate paths/s",
+                    "h2d_bytes_per_step": 64 * 64, "d2h_bytes_per_step": 64 * 8 * 168}}
+    print(json.dumps(line), flush=True)
+    cp.cp_batch_destroy(b)
+
+
 def cpu_baseline(wl, crane, scene, q0, qd, seconds, max_batches=None):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample: candidate
     evaluations (step (2), which dominates a plan) of the same workload, in batches until
@@ -452,6 +525,8 @@ def main():
         run_reference(args)
     elif args.workload == "differentiable":
         run_differentiable(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -124,6 +124,8 @@ typedef struct cp_params {
     int64_t max_grid_items; /* capacity of the cell lists; 0 = bound of the initial scene */
     double smooth_margin;   /* differentiable form: softplus margin m (m); 0 selects 0.05 */
     double smooth_beta;     /* differentiable form: softplus width beta (m); 0 selects 0.01 */
+    int32_t eval_ctas_per_sm; /* launch shape of the evaluation kernel: CTAs per SM of its
+                                 persistent grid (0: as many as fit) */
 } cp_params;
 
 /* Cost terms of the final mean path and the state of a finished plan. */
@@ -259,6 +261,51 @@ int cp_smooth_cost_grad(cp_planner *p, const float *d_xi, int32_t n, const doubl
  * candidates d_xi (float[n][K][4], updated in place), e.g. the best candidates of a plan
  * before they are handed to a trajectory optimiser. Errors as cp_smooth_cost. */
 int cp_polish(cp_planner *p, float *d_xi, int32_t n, int32_t steps, double alpha);
+
+/* ------------------------------------------------------------------ batched form */
+
+/* One planning query of a batch: its obstacle scene (host memory, copied at
+ * cp_batch_init), its search parameters (sizes may differ between queries) and its start and
+ * goal configurations. */
+typedef struct cp_query {
+    cp_scene scene;
+    cp_params params;
+    double q0[4];
+    double qd[4];
+} cp_query;
+
+/* Result of one query: the control points of the final mean path (the first (K+8)*4
+ * entries, four copies of q0, the K waypoints, four copies of qd) and its cost terms. */
+typedef struct cp_batch_result {
+    cp_plan_stats stats;
+    double ctrl[(CP_MAX_WAYPOINTS + 8) * 4];
+} cp_batch_result;
+
+typedef struct cp_batch cp_batch;
+
+/* Batched serving form of Algorithm 1: nq independent queries planned concurrently for
+ * `iters` iterations each. Creates one planner and one stream per query, then records every
+ * query's whole plan (end points in, initial distribution, the iterations, the mean path's
+ * evaluation, results out) as one CUDA graph whose branches run concurrently, so that small
+ * queries fill the GPU around large ones. Allocation happens here only. Errors: as
+ * cp_plan_init (for the first query that fails), CP_ERR_CUDA. */
+int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, int32_t iters,
+                  cp_batch **out);
+
+/* Change the start and goal of query q for the next cp_batch_run (host values). */
+int cp_batch_set_endpoints(cp_batch *b, int32_t q, const double h_q0[4], const double h_qd[4]);
+
+/* Run every query once: one launch of the recorded graph, then wait for it. results (host,
+ * nq entries, may be NULL) receives each query's result. Errors: CP_ERR_NUMERIC when a
+ * query's covariance lost positive definiteness, CP_ERR_CUDA. */
+int cp_batch_run(cp_batch *b, cp_batch_result *results);
+
+/* The planner behind query q (owned by the batch), e.g. to plan that query alone with
+ * cp_plan; do not use it while cp_batch_run is running. NULL when q is out of range. */
+cp_planner *cp_batch_planner(cp_batch *b, int32_t q);
+
+/* Release the batch, its planners, streams and graph. NULL is ignored. */
+void cp_batch_destroy(cp_batch *b);
 
 /* Size of the fixed device scratch behind cp_evaluate_static (bytes, per GPU). */
 #define CP_STATIC_SCRATCH_BYTES (32u << 20)

@@ -63,7 +63,7 @@ class cp_params(ctypes.Structure):
                 ("max_cylinders", ctypes.c_int32), ("max_boxes", ctypes.c_int32),
                 ("grid_cell", ctypes.c_double), ("grid_half_extent", ctypes.c_double),
                 ("max_grid_items", ctypes.c_int64), ("smooth_margin", ctypes.c_double),
-                ("smooth_beta", ctypes.c_double)]
+                ("smooth_beta", ctypes.c_double), ("eval_ctas_per_sm", ctypes.c_int32)]
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -72,6 +72,15 @@ class cp_plan_stats(ctypes.Structure):
                 ("flag", ctypes.c_int32), ("n_flagged", ctypes.c_int32),
                 ("iterations", ctypes.c_int32), ("iteration", ctypes.c_int32),
                 ("best_J", ctypes.c_double)]
+
+
+class cp_query(ctypes.Structure):
+    _fields_ = [("scene", cp_scene), ("params", cp_params), ("q0", ctypes.c_double * 4),
+                ("qd", ctypes.c_double * 4)]
+
+
+class cp_batch_result(ctypes.Structure):
+    _fields_ = [("stats", cp_plan_stats), ("ctrl", ctypes.c_double * ((CP_MAX_WAYPOINTS + 8) * 4))]
 
 
 class cp_timing(ctypes.Structure):
@@ -113,6 +122,13 @@ _SIGS = {
     "cp_smooth_cost": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "cp_smooth_cost_grad": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
     "cp_polish": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
+    "cp_batch_init": (ctypes.c_int, [ctypes.POINTER(cp_model), ctypes.POINTER(cp_query),
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "cp_batch_set_endpoints": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]),
+    "cp_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(cp_batch_result)]),
+    "cp_batch_planner": (_P, [_P, ctypes.c_int32]),
+    "cp_batch_destroy": (None, [_P]),
     "cp_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cp_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(cp_timing)]),
 }
@@ -210,10 +226,11 @@ def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 eps: float = 1e-8, init_std_frac: float = 0.1, seed: int = 0, query: int = 0,
                 max_cylinders: int = 0, max_boxes: int = 0, grid_cell: float = 0.0,
                 grid_half_extent: float = 0.0, max_grid_items: int = 0,
-                smooth_margin: float = 0.05, smooth_beta: float = 0.01) -> cp_params:
+                smooth_margin: float = 0.05, smooth_beta: float = 0.01,
+                eval_ctas_per_sm: int = 0) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
                      query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
-                     max_grid_items, smooth_margin, smooth_beta)
+                     max_grid_items, smooth_margin, smooth_beta, eval_ctas_per_sm)
 
 
 # --------------------------------------------------------------------------- entry points
@@ -322,6 +339,47 @@ def cp_smooth_cost_grad(p: int, xi, n: int, gJ, J, dxi) -> None:
 
 def cp_polish(p: int, xi, n: int, steps: int, alpha: float) -> None:
     _check(load().cp_polish(p, _ptr(xi), int(n), int(steps), float(alpha)))
+
+
+def cp_batch_init(model: cp_model, scenes, params, q0s, qds, iters: int) -> int:
+    """scenes: HostScene per query; params: cp_params per query; returns the batch handle."""
+    nq = len(scenes)
+    qs = (cp_query * nq)()
+    for i in range(nq):
+        qs[i].scene = scenes[i].c
+        qs[i].params = params[i]
+        qs[i].q0 = _c4(q0s[i])
+        qs[i].qd = _c4(qds[i])
+    out = _P()
+    _check(load().cp_batch_init(ctypes.byref(model), qs, nq, int(iters), ctypes.byref(out)))
+    return out.value
+
+
+def cp_batch_set_endpoints(b: int, q: int, q0, qd) -> None:
+    _check(load().cp_batch_set_endpoints(b, int(q), _c4(q0), _c4(qd)))
+
+
+def cp_batch_run(b: int, nq: int, K=None):
+    """Runs the batch; returns [(ctrl [K+8][4] or None, stats dict)] per query."""
+    res = (cp_batch_result * nq)()
+    _check(load().cp_batch_run(b, res))
+    out = []
+    for i in range(nq):
+        st = {f: getattr(res[i].stats, f) for f, _ in cp_plan_stats._fields_}
+        ctrl = None
+        if K is not None:
+            k = K[i]
+            ctrl = np.ctypeslib.as_array(res[i].ctrl)[: 4 * (k + 8)].reshape(k + 8, 4).copy()
+        out.append((ctrl, st))
+    return out
+
+
+def cp_batch_planner(b: int, q: int) -> int:
+    return load().cp_batch_planner(b, int(q))
+
+
+def cp_batch_destroy(b: int) -> None:
+    load().cp_batch_destroy(b)
 
 
 def cp_set_timing(p: int, on: bool) -> None:

@@ -141,6 +141,7 @@ struct cp_planner {
     double *mean_J = nullptr, *mean_terms = nullptr;
     uint8_t *mean_flag = nullptr;
     float *grad = nullptr;      // [N][D] gradient buffer for polish
+    float4 *ends_f = nullptr;   // [2] {q0, qd} in float, written with the end points
     int smem_optin = 0;
     bool use_grid = false;
     GridDev gdev{};
@@ -248,6 +249,7 @@ int validate_params(const cp_params *p)
         !is_finite(p->w_l) || !is_finite(p->lambda_c))
         return set_error("cost weights must be finite and >= 0"), CP_ERR_ARG;
     if (p->max_cylinders < 0 || p->max_boxes < 0) return set_error("negative capacity"), CP_ERR_ARG;
+    if (p->eval_ctas_per_sm < 0) return set_error("eval_ctas_per_sm must be >= 0"), CP_ERR_ARG;
     if (!(p->grid_cell >= 0.0) || !is_finite(p->grid_cell) || !(p->grid_half_extent >= 0.0) ||
         !is_finite(p->grid_half_extent) || p->max_grid_items < 0 || !(p->smooth_margin >= 0.0) ||
         !is_finite(p->smooth_margin) || !(p->smooth_beta >= 0.0) || !is_finite(p->smooth_beta))
@@ -298,6 +300,8 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.chunks = p->chunks;
     a.q0 = p->q0f;
     a.qd = p->qdf;
+    a.ends = p->ends_f;
+    a.ctas_per_sm = p->prm.eval_ctas_per_sm;
     a.basis = p->basis;
     a.partial = p->partial;
     a.flagword = p->flagword;
@@ -495,6 +499,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_grid_outside = L.take<int>((size_t)p->cap_cyl + p->cap_box + 1);
     const size_t o_grid_counters = L.take<int>(2);
     const size_t o_grad = L.take<float>(N * D);
+    const size_t o_ends_f = L.take<float4>(2);
     e = cudaMalloc((void **)&p->base, L.bytes);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(workspace)"));
     char *b = p->base;
@@ -530,6 +535,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mean_terms = (double *)(b + o_mean_terms);
     p->mean_flag = (uint8_t *)(b + o_mean_flag);
     p->grad = (float *)(b + o_grad);
+    p->ends_f = (float4 *)(b + o_ends_f);
     p->grid_count = (int *)(b + o_grid_count);
     p->grid_cursor = (int *)(b + o_grid_cursor);
     p->grid_start = (int *)(b + o_grid_start);
@@ -592,7 +598,7 @@ int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4])
     p->q0f = make_float4((float)h_q0[0], (float)h_q0[1], (float)h_q0[2], (float)h_q0[3]);
     p->qdf = make_float4((float)h_qd[0], (float)h_qd[1], (float)h_qd[2], (float)h_qd[3]);
     int rc = launch_init_distribution(p->consts, p->consts + 4, p->consts + 8, p->consts + 12, p->K,
-                                      p->prm.init_std_frac, p->mu, p->C, p->st);
+                                      p->prm.init_std_frac, p->mu, p->C, p->ends_f, p->st);
     if (rc != CP_OK) return rc;
     p->iteration = 0;
     p->have_endpoints = true;
@@ -799,6 +805,209 @@ int cp_synchronize(cp_planner *p)
 {
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     return check_status(p);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched form
+
+struct cp_batch {
+    int nq = 0, iters = 0;
+    cudaStream_t origin = nullptr;
+    std::vector<cp_planner *> planners;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    double *h_in = nullptr;       // pinned [nq][8]: q0, qd
+    double *h_out = nullptr;      // pinned [nq][kOutStride]
+    uint32_t *h_status = nullptr; // pinned [nq]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int kOutStride = 8 + (CP_MAX_WAYPOINTS + 8) * 4;   // J, terms[5], best, pad, ctrl
+
+// The device work of one query's plan on its planner's stream, with host inputs and outputs
+// in pinned memory (recorded into the batch graph).
+int record_plan(cp_planner *p, int iters, const double *h_in, double *h_out, uint32_t *h_status)
+{
+    int rc;
+    CP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(uint32_t), p->st));
+    CP_CUDA(cudaMemcpyAsync(p->consts, h_in, 8 * sizeof(double), cudaMemcpyHostToDevice, p->st));
+    if ((rc = launch_init_distribution(p->consts, p->consts + 4, p->consts + 8, p->consts + 12, p->K,
+                                       p->prm.init_std_frac, p->mu, p->C, p->ends_f, p->st)) != CP_OK)
+        return rc;
+    if ((rc = run_factor(p)) != CP_OK) return rc;
+    for (int t = 0; t < iters; ++t) {
+        if ((rc = run_sample(p, t, p->xi)) != CP_OK) return rc;
+        if ((rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr)) != CP_OK) return rc;
+        if ((rc = run_update(p, p->J, p->xi)) != CP_OK) return rc;
+    }
+    if ((rc = launch_mean_to_candidate(p->mu, p->D, p->mean_xi, p->st)) != CP_OK) return rc;
+    if ((rc = run_eval(p, p->mean_xi, 1, p->mean_J, p->mean_flag, p->mean_terms, nullptr, nullptr)) != CP_OK)
+        return rc;
+    if ((rc = launch_control_points(p->consts, p->consts + 4, p->mu, p->K, p->ctrl, p->st)) != CP_OK)
+        return rc;
+    CP_CUDA(cudaMemcpyAsync(h_out, p->mean_J, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaMemcpyAsync(h_out + 1, p->mean_terms, 5 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaMemcpyAsync(h_out + 6, p->best, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaMemcpyAsync(h_out + 8, p->ctrl, sizeof(double) * 4 * (p->K + 8), cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaMemcpyAsync(h_status, p->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, p->st));
+    return CP_OK;
+}
+
+void batch_free(cp_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto *p : b->planners) cp_destroy(p);
+    for (auto e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->h_in) cudaFreeHost(b->h_in);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, int32_t iters,
+                  cp_batch **out)
+{
+    g_err[0] = 0;
+    if (!out) return set_error("out is NULL"), CP_ERR_ARG;
+    *out = nullptr;
+    if (!queries || nq < 1 || nq > 4096) return set_error("nq = %d outside 1..4096", nq), CP_ERR_ARG;
+    if (iters < 0) return set_error("iters must be >= 0"), CP_ERR_ARG;
+    for (int q = 0; q < nq; ++q)
+        for (int j = 0; j < 4; ++j)
+            if (!is_finite(queries[q].q0[j]) || !is_finite(queries[q].qd[j]))
+                return set_error("query %d: end points must be finite", q), CP_ERR_ARG;
+    cp_batch *b = new (std::nothrow) cp_batch();
+    if (!b) return set_error("host allocation failed"), CP_ERR_OOM;
+    b->nq = nq;
+    b->iters = iters;
+    auto fail = [&](int code) {
+        batch_free(b);
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
+    if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaEventCreate"));
+    if ((e = cudaMallocHost((void **)&b->h_in, sizeof(double) * 8 * nq)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&b->h_out, sizeof(double) * kOutStride * nq)) != cudaSuccess ||
+        (e = cudaMallocHost((void **)&b->h_status, sizeof(uint32_t) * nq)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaMallocHost"));
+    for (int q = 0; q < nq; ++q) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
+        b->streams.push_back(st);
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaEventCreate"));
+        b->joins.push_back(ev);
+        cp_planner *p = nullptr;
+        const int rc = cp_plan_init(model, &queries[q].scene, &queries[q].params, st, &p);
+        if (rc != CP_OK) {
+            char msg[512];
+            snprintf(msg, sizeof msg, "query %d: %s", q, g_err);
+            set_error("%s", msg);
+            return fail(rc);
+        }
+        b->planners.push_back(p);
+        p->have_endpoints = true;
+        memcpy(b->h_in + 8 * q, queries[q].q0, 4 * sizeof(double));
+        memcpy(b->h_in + 8 * q + 4, queries[q].qd, 4 * sizeof(double));
+    }
+    // record every query's plan as one graph with a branch per query
+    if ((e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaStreamBeginCapture"));
+    int rc = CP_OK;
+    e = cudaEventRecord(b->fork, b->origin);
+    for (int q = 0; q < nq && e == cudaSuccess && rc == CP_OK; ++q) {
+        if ((e = cudaStreamWaitEvent(b->streams[q], b->fork, 0)) != cudaSuccess) break;
+        rc = record_plan(b->planners[q], iters, b->h_in + 8 * q, b->h_out + kOutStride * q,
+                         b->h_status + q);
+        if (rc != CP_OK) break;
+        if ((e = cudaEventRecord(b->joins[q], b->streams[q])) != cudaSuccess) break;
+        e = cudaStreamWaitEvent(b->origin, b->joins[q], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(b->origin, &graph);
+    b->graph = graph;
+    if (rc != CP_OK) return fail(rc);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "recording the batch graph"));
+    if (e_end != cudaSuccess) return fail(cuda_fail(e_end, "cudaStreamEndCapture"));
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaGraphInstantiate"));
+    *out = b;
+    return CP_OK;
+}
+
+int cp_batch_set_endpoints(cp_batch *b, int32_t q, const double h_q0[4], const double h_qd[4])
+{
+    if (!b || !h_q0 || !h_qd || q < 0 || q >= b->nq) return set_error("invalid arguments"), CP_ERR_ARG;
+    for (int j = 0; j < 4; ++j)
+        if (!is_finite(h_q0[j]) || !is_finite(h_qd[j])) return set_error("end points must be finite"), CP_ERR_ARG;
+    CP_CUDA(cudaStreamSynchronize(b->origin));   // the graph may be reading the inputs
+    memcpy(b->h_in + 8 * q, h_q0, 4 * sizeof(double));
+    memcpy(b->h_in + 8 * q + 4, h_qd, 4 * sizeof(double));
+    return CP_OK;
+}
+
+int cp_batch_run(cp_batch *b, cp_batch_result *results)
+{
+    if (!b) return set_error("batch is NULL"), CP_ERR_ARG;
+    CP_CUDA(cudaGraphLaunch(b->exec, b->origin));
+    count_launch();
+    CP_CUDA(cudaStreamSynchronize(b->origin));
+    int rc = CP_OK;
+    for (int q = 0; q < b->nq; ++q) {
+        const double *o = b->h_out + kOutStride * q;
+        if (results) {
+            cp_batch_result &r = results[q];
+            memset(&r, 0, sizeof r);
+            r.stats.J = o[0];
+            r.stats.Jp = o[1];
+            r.stats.Jc = o[2];
+            r.stats.Jl = o[3];
+            r.stats.length = o[4];
+            r.stats.n_flagged = (int32_t)o[5];
+            r.stats.flag = r.stats.n_flagged > 0;
+            r.stats.iterations = b->iters;
+            r.stats.iteration = b->iters;
+            r.stats.best_J = o[6];
+            memcpy(r.ctrl, o + 8, sizeof(double) * 4 * (b->planners[q]->K + 8));
+        }
+        if (b->h_status[q] != 0 && rc == CP_OK) {
+            set_error("query %d: the covariance is not positive definite", q);
+            rc = CP_ERR_NUMERIC;
+        }
+    }
+    return rc;
+}
+
+cp_planner *cp_batch_planner(cp_batch *b, int32_t q)
+{
+    if (!b || q < 0 || q >= b->nq) return nullptr;
+    return b->planners[q];
+}
+
+void cp_batch_destroy(cp_batch *b)
+{
+    if (!b) return;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    batch_free(b);
 }
 
 }  // extern "C"

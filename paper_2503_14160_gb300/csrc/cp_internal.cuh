@@ -88,7 +88,9 @@ ModelDev make_model(const cp_model *m);
 struct EvalArgs {
     const float4 *xi;           // [n][K]
     int n, K, S, n_s, chunks;   // chunks = ceil(n_s / 32)
-    float4 q0, qd;
+    float4 q0, qd;              // end points, used when `ends` is null
+    const float4 *ends;         // optional device copy {q0, qd}, read at run time
+    int ctas_per_sm;            // persistent-grid CTAs per SM (0: as many as fit)
     const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
     float4 *partial;            // [chunks][n] {J_p, sum pen, J_l, length} (float)
     uint32_t *flagword;         // [chunks][n]
@@ -125,7 +127,7 @@ int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d
 int launch_basis_table(int S, float4 *basis, cudaStream_t st);
 int launch_init_distribution(const double *q0, const double *qd, const double *q_min,
                              const double *q_max, int K, double init_std_frac, double *mu,
-                             double *C, cudaStream_t st);
+                             double *C, float4 *ends_f, cudaStream_t st);
 int launch_mean_to_candidate(const double *mu, int D, float *xi, cudaStream_t st);
 int launch_control_points(const double *q0, const double *qd, const double *mu, int K,
                           double *ctrl, cudaStream_t st);

@@ -126,11 +126,13 @@ static __device__ __forceinline__ Checkpoint checkpoint_setup(const ModelDev &m,
     const int mstep = kc - span * a.S;            // 1..S within the span
     // control points P_{span+1..span+4} of [q0 x4, xi (K), qd x4]
     const float4 *xi = a.xi + (size_t)cand * a.K;
+    const float4 q0 = a.ends != nullptr ? __ldg(a.ends) : a.q0;
+    const float4 qd = a.ends != nullptr ? __ldg(a.ends + 1) : a.qd;
     float4 P[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int g = span + 1 + i;
-        P[i] = g < 4 ? a.q0 : (g >= a.K + 4 ? a.qd : __ldg(xi + (g - 4)));
+        P[i] = g < 4 ? q0 : (g >= a.K + 4 ? qd : __ldg(xi + (g - 4)));
     }
     const float4 bw = s_basis[2 * (mstep - 1)];
     const float4 dbw = s_basis[2 * (mstep - 1) + 1];

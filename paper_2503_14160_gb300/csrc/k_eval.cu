@@ -207,12 +207,13 @@ __global__ void k_signed_distance(const ModelDev m, const SceneDev sc, const flo
 }
 
 template <int NSPH>
-int eval_grid(size_t smem, int num_sms, int units)
+int eval_grid(size_t smem, int num_sms, int units, int ctas_per_sm)
 {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<NSPH>,
                                                                   kEvalThreads, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const int warps_per_block = kEvalThreads / 32;
     const int needed = (units + warps_per_block - 1) / warps_per_block;
     int grid = num_sms * per_sm;
@@ -258,9 +259,9 @@ int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int nu
     if (units == 0) return CP_OK;
     const size_t smem = eval_smem_bytes(sc.n_cyl, sc.n_box, a.S);
     if (m.n_spheres == 12) {
-        k_eval<12><<<eval_grid<12>(smem, num_sms, units), kEvalThreads, smem, st>>>(m, sc, a);
+        k_eval<12><<<eval_grid<12>(smem, num_sms, units, a.ctas_per_sm), kEvalThreads, smem, st>>>(m, sc, a);
     } else {
-        k_eval<16><<<eval_grid<16>(smem, num_sms, units), kEvalThreads, smem, st>>>(m, sc, a);
+        k_eval<16><<<eval_grid<16>(smem, num_sms, units, a.ctas_per_sm), kEvalThreads, smem, st>>>(m, sc, a);
     }
     CP_LAUNCHED("k_eval");
     return CP_OK;

@@ -220,6 +220,7 @@ int launch_eval_grid(const ModelDev &m, const SceneDev &sc, const GridDev &g, co
     else
         CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_grid<16>, kGridThreads, smem));
     if (per_sm < 1) per_sm = 1;
+    if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
     const int needed = (units + kGridThreads / 32 - 1) / (kGridThreads / 32);
     int grid = num_sms * per_sm;
     if (grid > needed) grid = needed;

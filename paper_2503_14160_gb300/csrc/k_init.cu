@@ -56,9 +56,13 @@ __global__ void k_basis_table(int S, float4 *basis)
 // mu[4f + c] = q0[c] + (f+1)/(K+1) (qd[c] - q0[c]); C = diag((frac (q_max - q_min))^2).
 __global__ void k_init_distribution(const double *q0, const double *qd, const double *q_min,
                                     const double *q_max, int K, double frac, double *mu,
-                                    double *C)
+                                    double *C, float4 *ends_f)
 {
     const int D = 4 * K;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ends_f != nullptr) {
+        ends_f[0] = make_float4((float)q0[0], (float)q0[1], (float)q0[2], (float)q0[3]);
+        ends_f[1] = make_float4((float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]);
+    }
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < D * D;
          idx += gridDim.x * blockDim.x) {
         const int r = idx / D, c = idx - r * D;
@@ -114,12 +118,13 @@ int launch_basis_table(int S, float4 *basis, cudaStream_t st)
 
 int launch_init_distribution(const double *q0, const double *qd, const double *q_min,
                              const double *q_max, int K, double init_std_frac, double *mu,
-                             double *C, cudaStream_t st)
+                             double *C, float4 *ends_f, cudaStream_t st)
 {
     const int D = 4 * K;
     const int threads = 256;
     const int blocks = (D * D + threads - 1) / threads;
-    k_init_distribution<<<blocks, threads, 0, st>>>(q0, qd, q_min, q_max, K, init_std_frac, mu, C);
+    k_init_distribution<<<blocks, threads, 0, st>>>(q0, qd, q_min, q_max, K, init_std_frac, mu, C,
+                                                    ends_f);
     CP_LAUNCHED("k_init_distribution");
     return CP_OK;
 }

@@ -218,6 +218,35 @@ WORKLOADS: Dict[str, Workload] = {
 }
 
 
+@dataclasses.dataclass(frozen=True)
+class BatchQuery:
+    n_candidates: int
+    n_waypoints: int
+    n_cyl: int
+    r_out: float
+
+
+def batch_queries(nq: int = 64, seed: int = 0, n_lo: int = 1024, n_hi: int = 16384,
+                  k_lo: int = 8, k_hi: int = 32, m_lo: int = 50, m_hi: int = 3000,
+                  density: float = 1.66) -> List[BatchQuery]:
+    """Uneven query sizes of the batched serving form: N, K and the cylinder count uniform
+    in their ranges; each scene fills an annulus 2..r_out at the given trees per m^2,
+    r_out = sqrt(4 + M / (density pi))."""
+    g = rng(seed, STREAM_QUERY_SIZES)
+    out = []
+    for _ in range(nq):
+        N = int(g.integers(n_lo, n_hi + 1))
+        K = int(g.integers(k_lo, k_hi + 1))
+        M = int(g.integers(m_lo, m_hi + 1))
+        out.append(BatchQuery(N, K, M, math.sqrt(4.0 + M / (density * math.pi))))
+    return out
+
+
+def batch_scene(bq: BatchQuery, seed: int, q: int) -> Scene:
+    g = rng(seed, STREAM_SCENE, 1000 + q)
+    return Scene(annulus_cylinders(g, bq.n_cyl, 2.0, bq.r_out, 0.1, 0.4), np.zeros((0, 6)))
+
+
 def make_scene(w: Workload) -> Scene:
     g = rng(w.seed, STREAM_SCENE)
     if w.spacing > 0.0:
