@@ -42,30 +42,35 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, defines=(), lib_path=None) -> str:
+def build(force: bool = False, verbose: bool = False, defines=(), lib_path=None,
+          src_dir=None) -> str:
     """Compile and link libcraneplan.so if it is missing or older than its sources.
 
-    `defines` (e.g. ["CP_EVAL_MIN_BLOCKS=2"]) and `lib_path` build a variant elsewhere."""
+    `defines` (e.g. ["CP_EVAL_MIN_BLOCKS=2"]), `lib_path` and `src_dir` (a copy of csrc/)
+    build a variant elsewhere."""
     lib = lib_path or LIB
-    if not force and not defines and lib_path is None and not _stale():
+    csrc = src_dir or CSRC
+    if not force and not defines and lib_path is None and src_dir is None and not _stale():
         return LIB
     out_dir = os.path.dirname(os.path.abspath(lib))
     os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     tag = "" if not defines else "_" + "_".join(d.replace("=", "") for d in defines)
-    objs = [os.path.join(out_dir, s.replace(".cu", tag + ".o")) for s in SOURCES]
+    objs = [os.path.join(out_dir, s.replace(".cu", tag + ".o")) for s in SOURCES
+            if os.path.exists(os.path.join(csrc, s))]
     dflags = ["-D" + d for d in defines]
 
     def compile_one(src_obj):
         src, obj = src_obj
-        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(verbose) + dflags
+        cmd = [cc, "-c", os.path.join(csrc, src), "-o", obj] + _flags(verbose) + dflags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
         return r.stdout + r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        logs = list(ex.map(compile_one, zip(SOURCES, objs)))
+    srcs = [s for s in SOURCES if os.path.exists(os.path.join(csrc, s))]
+    with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        logs = list(ex.map(compile_one, zip(srcs, objs)))
     tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

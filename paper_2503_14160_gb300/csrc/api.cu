@@ -147,7 +147,8 @@ struct cp_planner {
     GridDev gdev{};
     int64_t grid_cap = 0;
     int *grid_count = nullptr, *grid_cursor = nullptr, *grid_start = nullptr;
-    int *grid_items = nullptr, *grid_outside = nullptr, *grid_counters = nullptr;
+    float4 *grid_items = nullptr, *grid_outside = nullptr;
+    int *grid_counters = nullptr;
     bool have_endpoints = false;
     float4 q0f{}, qdf{};
     int iteration = 0;
@@ -495,8 +496,8 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_grid_count = L.take<int>((size_t)cells + 1);
     const size_t o_grid_cursor = L.take<int>((size_t)cells + 1);
     const size_t o_grid_start = L.take<int>((size_t)cells + 1);
-    const size_t o_grid_items = L.take<int>(p->use_grid ? (size_t)p->grid_cap : 1);
-    const size_t o_grid_outside = L.take<int>((size_t)p->cap_cyl + p->cap_box + 1);
+    const size_t o_grid_items = L.take<float4>(p->use_grid ? (size_t)p->grid_cap : 1);
+    const size_t o_grid_outside = L.take<float4>((size_t)p->cap_cyl + p->cap_box + 1);
     const size_t o_grid_counters = L.take<int>(2);
     const size_t o_grad = L.take<float>(N * D);
     const size_t o_ends_f = L.take<float4>(2);
@@ -539,8 +540,8 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->grid_count = (int *)(b + o_grid_count);
     p->grid_cursor = (int *)(b + o_grid_cursor);
     p->grid_start = (int *)(b + o_grid_start);
-    p->grid_items = (int *)(b + o_grid_items);
-    p->grid_outside = (int *)(b + o_grid_outside);
+    p->grid_items = (float4 *)(b + o_grid_items);
+    p->grid_outside = (float4 *)(b + o_grid_outside);
     p->grid_counters = (int *)(b + o_grid_counters);
     p->gdev.cell_start = p->grid_start;
     p->gdev.items = p->grid_items;

@@ -70,8 +70,8 @@ struct GridDev {
     float inv_h;
     int nx, ny;
     const int *cell_start;   // [nx ny + 1]
-    const int *items;        // obstacle ids: < n_cyl cylinder, else box (id - n_cyl)
-    const int *outside;      // ids whose dilated footprint leaves the window
+    const float4 *items;     // records {cx, cy, W, id}; id < n_cyl cylinder, else box n_cyl + b
+    const float4 *outside;   // records of obstacles whose dilated footprint leaves the window
     const int *n_outside;    // [1]
 };
 
@@ -110,7 +110,7 @@ int eval_ensure_smem(size_t smem_bytes);
 
 int64_t grid_items_bound(const cp_scene *sc, double r_max, double h);
 int launch_grid_build(const SceneDev &sc, const GridDev &g, float r_max, int *count, int *cursor,
-                      int *start, int *items, int *outside, int *counters, cudaStream_t st);
+                      int *start, float4 *items, float4 *outside, int *counters, cudaStream_t st);
 int launch_eval_grid(const ModelDev &m, const SceneDev &sc, const GridDev &g, const EvalArgs &a,
                      int num_sms, cudaStream_t st);
 

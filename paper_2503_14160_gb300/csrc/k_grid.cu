@@ -1,5 +1,7 @@
 // Uniform 2-D grid of the obstacles for large scenes, and the evaluation kernel that
 // queries it (Algorithm 1 step (2), d(q) of Sec. 3.1, arXiv 2503.14160).
+// Cell entries are filter records {cx, cy, W, id}: one load per entry, the same 2-FMA
+// reach test as the brute-force kernel, and the exact distance only within reach.
 //
 // The grid covers a square window centred on the crane base with cells of side h. Every
 // obstacle goes into every cell that its footprint, dilated by the largest sphere radius
@@ -16,6 +18,9 @@ namespace cp {
 namespace {
 
 constexpr int kGridThreads = 256;
+#ifndef CP_GRID_MIN_BLOCKS
+#define CP_GRID_MIN_BLOCKS 4   // CTAs of 8 warps resident per SM (at most 64 registers)
+#endif
 constexpr float kGridPad = 1e-3f;   // m; covers float rounding of the cell index
 
 // Dilated footprint [x0, x1] x [y0, y1] of obstacle id (cylinders first, then boxes).
@@ -92,50 +97,44 @@ __global__ void __launch_bounds__(1024) k_grid_scan(const int *count, int n, int
     if (t == 1023) start[n] = part[1023];
 }
 
-__global__ void k_grid_fill(const SceneDev sc, const GridDev g, float r, int *cursor, int *items,
-                            int *outside, int *outside_cursor)
+// Cell entries are records {cx, cy, W, id}: a cylinder's filter record (W as in the
+// brute-force kernel) with its id in the last word; boxes carry W = -huge so that the
+// filter always passes them on to the exact distance.
+__device__ __forceinline__ float4 grid_record(const SceneDev &sc, int id)
+{
+    if (id < sc.n_cyl) {
+        const float4 f = sc.cyl_filt[id];
+        return make_float4(f.x, f.y, f.z, __int_as_float(id));
+    }
+    return make_float4(0.f, 0.f, -3.0e38f, __int_as_float(id));
+}
+
+__global__ void k_grid_fill(const SceneDev sc, const GridDev g, float r, int *cursor, float4 *items,
+                            float4 *outside, int *outside_cursor)
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= sc.n_cyl + sc.n_box) return;
     float x0, x1, y0, y1;
     footprint(sc, r, id, x0, x1, y0, y1);
+    const float4 rec = grid_record(sc, id);
     int ix0, ix1, iy0, iy1;
-    if (cell_range(g, x0, x1, y0, y1, ix0, ix1, iy0, iy1)) outside[atomicAdd(outside_cursor, 1)] = id;
+    if (cell_range(g, x0, x1, y0, y1, ix0, ix1, iy0, iy1)) outside[atomicAdd(outside_cursor, 1)] = rec;
     for (int iy = iy0; iy <= iy1; ++iy)
-        for (int ix = ix0; ix <= ix1; ++ix) items[atomicAdd(cursor + iy * g.nx + ix, 1)] = id;
+        for (int ix = ix0; ix <= ix1; ++ix) items[atomicAdd(cursor + iy * g.nx + ix, 1)] = rec;
 }
 
-// Signed distance of sphere (x, y, z, r) to obstacle id.
-__device__ __forceinline__ float obstacle_distance(const SceneDev &sc, int id, float x, float y,
-                                                   float z, float r)
+// Signed distance of sphere (x, y, z, r) to the obstacle of a cell record.
+__device__ __forceinline__ float record_distance(const SceneDev &sc, float4 rec, float x, float y,
+                                                 float z, float r)
 {
-    if (id < sc.n_cyl) {
-        const float4 f = __ldg(sc.cyl_filt + id), e = __ldg(sc.cyl_exact + id);
-        return sdf_cylinder(x, y, z, f.x, f.y, e) - r;
-    }
+    const int id = __float_as_int(rec.w);
+    if (id < sc.n_cyl) return sdf_cylinder(x, y, z, rec.x, rec.y, __ldg(sc.cyl_exact + id)) - r;
     const float4 c = __ldg(sc.box_c + id - sc.n_cyl), h = __ldg(sc.box_h + id - sc.n_cyl);
     return sdf_box(x, y, z, c, h) - r;
 }
 
-// The cell list holding (x, y), or the list of obstacles that leave the window.
-__device__ __forceinline__ void cell_list(const GridDev &g, float x, float y, int &b, int &e,
-                                          const int *&list)
-{
-    const float fx = (x - g.x0) * g.inv_h, fy = (y - g.y0) * g.inv_h;
-    if (fx >= 0.f && fy >= 0.f && fx < (float)g.nx && fy < (float)g.ny) {
-        const int cell = (int)fy * g.nx + (int)fx;
-        b = __ldg(g.cell_start + cell);
-        e = __ldg(g.cell_start + cell + 1);
-        list = g.items;
-    } else {
-        b = 0;
-        e = __ldg(g.n_outside);
-        list = g.outside;
-    }
-}
-
 template <int NSPH>
-__global__ void __launch_bounds__(kGridThreads)
+__global__ void __launch_bounds__(kGridThreads, CP_GRID_MIN_BLOCKS)
 k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs a)
 {
     extern __shared__ __align__(16) float4 s_basis[];
@@ -151,15 +150,40 @@ k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
         float X[NSPH], Y[NSPH], Z[NSPH];
         crane_fk<NSPH>(m, c.q, X, Y, Z);
-        float dmin = CUDART_INF_F;
+        // Per sphere: the entry range of its cell (looked up for all spheres first, so the
+        // loads are in flight together) and its query record. The sphere loop below is kept
+        // rolled, reading these small per-thread arrays, so that one copy of the entry loop
+        // serves all spheres (unrolled, the code outgrows the instruction cache).
+        float4 qs[NSPH];   // {-2x, -2y, margin - x^2 - y^2, z}
+        int2 range[NSPH];
 #pragma unroll
         for (int s = 0; s < NSPH; ++s) {
-            int b, e;
-            const int *list;
-            cell_list(g, X[s], Y[s], b, e, list);
-            const float r = m.sph[s].radius;
-            for (int it = b; it < e; ++it)
-                dmin = fminf(dmin, obstacle_distance(sc, __ldg(list + it), X[s], Y[s], Z[s], r));
+            const float fx = (X[s] - g.x0) * g.inv_h, fy = (Y[s] - g.y0) * g.inv_h;
+            if (fx >= 0.f && fy >= 0.f && fx < (float)g.nx && fy < (float)g.ny) {
+                const int cell = (int)fy * g.nx + (int)fx;
+                range[s] = make_int2(__ldg(g.cell_start + cell), __ldg(g.cell_start + cell + 1));
+            } else {
+                range[s] = make_int2(-1, 0);   // outside the window
+            }
+            qs[s] = make_float4(-2.f * X[s], -2.f * Y[s], kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]), Z[s]);
+        }
+        float dmin = CUDART_INF_F;
+#pragma unroll 1
+        for (int s = 0; s < m.n_spheres; ++s) {
+            const float4 sq = qs[s];
+            const float xs = -0.5f * sq.x, ys = -0.5f * sq.y, r = m.sph[s].radius;
+            const float4 *list = g.items;
+            int it = range[s].x, end = range[s].y;
+            if (it < 0) {
+                list = g.outside;
+                it = 0;
+                end = __ldg(g.n_outside);
+            }
+            for (; it < end; ++it) {
+                const float4 rec = __ldg(list + it);
+                if (fmaf(sq.x, rec.x, fmaf(sq.y, rec.y, rec.z)) < sq.z)   // within reach (2-D)
+                    dmin = fminf(dmin, record_distance(sc, rec, xs, ys, sq.w, r));
+            }
         }
         unit_epilogue(a, c, dmin, cand, chunk, lane);
     }
@@ -188,7 +212,8 @@ int64_t grid_items_bound(const cp_scene *sc, double r_max, double h)
 }
 
 int launch_grid_build(const SceneDev &sc, const GridDev &g, float r_max, int *count, int *cursor,
-                      int *start, int *items, int *outside, int *counters /* [2] */, cudaStream_t st)
+                      int *start, float4 *items, float4 *outside, int *counters /* [2] */,
+                      cudaStream_t st)
 {
     const int n_obs = sc.n_cyl + sc.n_box;
     const int cells = g.nx * g.ny;
