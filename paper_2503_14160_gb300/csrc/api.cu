@@ -142,6 +142,8 @@ struct cp_planner {
     uint8_t *mean_flag = nullptr;
     float *grad = nullptr;      // [N][D] gradient buffer for polish
     float4 *ends_f = nullptr;   // [2] {q0, qd} in float, written with the end points
+    float *smooth_part_g = nullptr;   // partial gradients when few candidates share the GPU
+    double *smooth_part_J = nullptr;
     int smem_optin = 0;
     bool use_grid = false;
     GridDev gdev{};
@@ -501,6 +503,9 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_grid_counters = L.take<int>(2);
     const size_t o_grad = L.take<float>(N * D);
     const size_t o_ends_f = L.take<float4>(2);
+    const size_t units_max = (size_t)smooth_partial_units(p->num_sms);
+    const size_t o_sp_g = L.take<float>(units_max * D);
+    const size_t o_sp_J = L.take<double>(units_max);
     e = cudaMalloc((void **)&p->base, L.bytes);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(workspace)"));
     char *b = p->base;
@@ -537,6 +542,8 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mean_flag = (uint8_t *)(b + o_mean_flag);
     p->grad = (float *)(b + o_grad);
     p->ends_f = (float4 *)(b + o_ends_f);
+    p->smooth_part_g = (float *)(b + o_sp_g);
+    p->smooth_part_J = (double *)(b + o_sp_J);
     p->grid_count = (int *)(b + o_grid_count);
     p->grid_cursor = (int *)(b + o_grid_cursor);
     p->grid_start = (int *)(b + o_grid_start);
@@ -688,7 +695,8 @@ static int run_smooth(cp_planner *p, const float *xi, int n, const double *gJ, d
 {
     return launch_smooth(p->mdev, p->sdev, xi, n, p->K, p->S, p->q0f, p->qdf, p->basis,
                          p->prm.smooth_margin, p->prm.smooth_beta, p->prm.w_c * p->prm.lambda_c,
-                         p->prm.w_l, gJ, J, dxi, p->num_sms, p->st);
+                         p->prm.w_l, gJ, J, dxi, p->smooth_part_g, p->smooth_part_J, p->num_sms,
+                         p->st);
 }
 
 int cp_smooth_cost(cp_planner *p, const float *d_xi, int32_t n, double *d_J)

@@ -26,6 +26,10 @@ struct SmoothArgs {
     const double *gJ;        // [n] or nullptr (ones)
     double *J;               // [n] or nullptr
     float *dxi;              // [n][K][4] or nullptr
+    int groups;              // warps per candidate (chunk groups); > 1 writes partials
+    int chunks_per_group;
+    float *part_g;           // [n groups][4K] when groups > 1
+    double *part_J;          // [n groups] when groups > 1
 };
 
 __device__ __forceinline__ float softplus_f(float x)
@@ -123,12 +127,17 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
 
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int cand = warp; cand < a.n; cand += n_warps) {
+    // A unit is (candidate, group of consecutive chunks); with few candidates several
+    // warps share one candidate and write partial sums that k_smooth_reduce combines.
+    for (int unit = warp; unit < a.n * a.groups; unit += n_warps) {
+        const int cand = unit / a.groups, group = unit - cand * a.groups;
+        const int c_begin = group * a.chunks_per_group;
+        const int c_end = min(a.chunks, c_begin + a.chunks_per_group);
         if (GRAD)
             for (int t = lane; t < 4 * a.K; t += 32) s_acc[t] = 0.f;
         double J = 0.0;
         const float4 *xi = a.xi + (size_t)cand * a.K;
-        for (int chunk = 0; chunk < a.chunks; ++chunk) {
+        for (int chunk = c_begin; chunk < c_end; ++chunk) {
             const int k = chunk * 32 + lane + 1;
             const bool valid = k <= a.n_s;
             const int kc = valid ? k : a.n_s;
@@ -149,31 +158,39 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
 
             float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH];
             crane_fk<NSPH>(m, q, X, Y, Z);
+            // Registers feed the unrolled filter; the per-thread arrays below (local memory)
+            // feed the rolled exact path, so that one copy of the distance, gradient and
+            // softplus code serves every sphere (unrolled it outgrows the instruction cache).
+            float4 sph[NSPH];   // {x, y, z, T}
             float3 dp[NSPH];
 #pragma unroll
             for (int s = 0; s < NSPH; ++s) {
                 T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
+                sph[s] = make_float4(X[s], Y[s], Z[s], T[s]);
                 dp[s] = make_float3(0.f, 0.f, 0.f);
+            }
+            float2 X2[NSPH / 2], Y2[NSPH / 2];
+#pragma unroll
+            for (int p = 0; p < NSPH / 2; ++p) {
+                X2[p] = make_float2(-2.f * X[2 * p], -2.f * X[2 * p + 1]);
+                Y2[p] = make_float2(-2.f * Y[2 * p], -2.f * Y[2 * p + 1]);
             }
             float pen = 0.f;
             for (int o = 0; o < sc.n_cyl; ++o) {
                 const float4 f = s_filt[o];
                 float2 g[NSPH / 2];
 #pragma unroll
-                for (int p = 0; p < NSPH / 2; ++p) {
-                    const float2 x2 = make_float2(-2.f * X[2 * p], -2.f * X[2 * p + 1]);
-                    const float2 y2 = make_float2(-2.f * Y[2 * p], -2.f * Y[2 * p + 1]);
-                    g[p] = __ffma2_rn(x2, make_float2(f.x, f.x),
-                                      __ffma2_rn(y2, make_float2(f.y, f.y), make_float2(f.z, f.z)));
-                }
+                for (int p = 0; p < NSPH / 2; ++p)
+                    g[p] = __ffma2_rn(X2[p], make_float2(f.x, f.x),
+                                      __ffma2_rn(Y2[p], make_float2(f.y, f.y), make_float2(f.z, f.z)));
                 if (any_below<NSPH>(g, T)) {
                     const float4 e = s_exact[o];
-#pragma unroll
-                    for (int s = 0; s < NSPH; ++s) {
-                        const float gs = (s & 1) ? g[s / 2].y : g[s / 2].x;
-                        if (gs < T[s]) {
-                            const float sd = sdf_cylinder(X[s], Y[s], Z[s], f.x, f.y, e) - m.sph[s].radius;
-                            const float3 gr = GRAD ? sdf_cylinder_grad(X[s], Y[s], Z[s], f.x, f.y, e)
+#pragma unroll 1
+                    for (int s = 0; s < m.n_spheres; ++s) {
+                        const float4 c = sph[s];
+                        if (fmaf(-2.f * c.x, f.x, fmaf(-2.f * c.y, f.y, f.z)) < c.w) {
+                            const float sd = sdf_cylinder(c.x, c.y, c.z, f.x, f.y, e) - m.sph[s].radius;
+                            const float3 gr = GRAD ? sdf_cylinder_grad(c.x, c.y, c.z, f.x, f.y, e)
                                                    : make_float3(0.f, 0.f, 0.f);
                             pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, dp[s]);
                         }
@@ -181,12 +198,13 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                 }
             }
             for (int o = 0; o < sc.n_box; ++o) {
-                const float4 c = s_bc[o], h = s_bh[o];
-#pragma unroll
-                for (int s = 0; s < NSPH; ++s) {
-                    const float sd = sdf_box(X[s], Y[s], Z[s], c, h) - m.sph[s].radius;
+                const float4 cb = s_bc[o], hb = s_bh[o];
+#pragma unroll 1
+                for (int s = 0; s < m.n_spheres; ++s) {
+                    const float4 c = sph[s];
+                    const float sd = sdf_box(c.x, c.y, c.z, cb, hb) - m.sph[s].radius;
                     if (sd < a.margin + kSmoothCut * a.beta) {
-                        const float3 gr = GRAD ? sdf_box_grad(X[s], Y[s], Z[s], c, h)
+                        const float3 gr = GRAD ? sdf_box_grad(c.x, c.y, c.z, cb, hb)
                                                : make_float3(0.f, 0.f, 0.f);
                         pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, dp[s]);
                     }
@@ -250,12 +268,39 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                 __syncwarp();
             }
         }
-        if (lane == 0 && a.J != nullptr) a.J[cand] = J;
-        if (GRAD) {
-            const float gj = a.gJ != nullptr ? (float)a.gJ[cand] : 1.f;
-            for (int t = lane; t < 4 * a.K; t += 32) a.dxi[(size_t)cand * 4 * a.K + t] = gj * s_acc[t];
-            __syncwarp();
+        if (a.groups == 1) {
+            if (lane == 0 && a.J != nullptr) a.J[cand] = J;
+            if (GRAD) {
+                const float gj = a.gJ != nullptr ? (float)a.gJ[cand] : 1.f;
+                for (int t = lane; t < 4 * a.K; t += 32) a.dxi[(size_t)cand * 4 * a.K + t] = gj * s_acc[t];
+            }
+        } else {
+            if (lane == 0) a.part_J[unit] = J;
+            if (GRAD)
+                for (int t = lane; t < 4 * a.K; t += 32) a.part_g[(size_t)unit * 4 * a.K + t] = s_acc[t];
         }
+        __syncwarp();
+    }
+}
+
+// Sums the groups' partials of each candidate in group order (one warp per candidate).
+__global__ void k_smooth_reduce(int n, int groups, int K, const double *part_J, const float *part_g,
+                                const double *gJ, double *J, float *dxi)
+{
+    const int cand = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (cand >= n) return;
+    if (lane == 0 && J != nullptr) {
+        double acc = 0.0;
+        for (int g = 0; g < groups; ++g) acc += part_J[(size_t)cand * groups + g];
+        J[cand] = acc;
+    }
+    if (dxi == nullptr) return;
+    const float gj = gJ != nullptr ? (float)gJ[cand] : 1.f;
+    for (int t = lane; t < 4 * K; t += 32) {
+        float acc = 0.f;
+        for (int g = 0; g < groups; ++g) acc += part_g[((size_t)cand * groups + g) * 4 * K + t];
+        dxi[(size_t)cand * 4 * K + t] = gj * acc;
     }
 }
 
@@ -281,10 +326,16 @@ int launch_smooth_t(const ModelDev &m, const SceneDev &sc, const SmoothArgs &a, 
     int per_sm = 0;
     CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmoothThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    int grid = (a.n + kSmoothThreads / 32 - 1) / (kSmoothThreads / 32);
+    const int units = a.n * a.groups;
+    int grid = (units + kSmoothThreads / 32 - 1) / (kSmoothThreads / 32);
     if (grid > num_sms * per_sm) grid = num_sms * per_sm;
     kern<<<grid, kSmoothThreads, smem, st>>>(m, sc, a);
     CP_LAUNCHED("k_smooth");
+    if (a.groups > 1) {
+        k_smooth_reduce<<<(a.n * 32 + 255) / 256, 256, 0, st>>>(a.n, a.groups, a.K, a.part_J, a.part_g,
+                                                                a.gJ, a.J, a.dxi);
+        CP_LAUNCHED("k_smooth_reduce");
+    }
     return CP_OK;
 }
 
@@ -292,10 +343,22 @@ int launch_smooth_t(const ModelDev &m, const SceneDev &sc, const SmoothArgs &a, 
 
 size_t smooth_smem_bytes(int n_cyl, int n_box, int S, int K) { return smooth_smem(n_cyl, n_box, S, K); }
 
+// Chunk groups per candidate: enough units for about 32 warps per SM when candidates are
+// few, at most the number of chunks; the partial buffers hold smooth_partial_units() units.
+int smooth_groups(int n, int chunks, int num_sms)
+{
+    const int target = 32 * num_sms;
+    if (n <= 0 || n >= target) return 1;
+    int g = (target + n - 1) / n;
+    return g < chunks ? g : chunks;
+}
+
+int64_t smooth_partial_units(int num_sms) { return 2 * 32 * (int64_t)num_sms; }
+
 int launch_smooth(const ModelDev &m, const SceneDev &sc, const float *xi, int n, int K, int S,
                   float4 q0, float4 qd, const float4 *basis, double margin, double beta,
-                  double wc_lc, double w_l, const double *gJ, double *J, float *dxi, int num_sms,
-                  cudaStream_t st)
+                  double wc_lc, double w_l, const double *gJ, double *J, float *dxi, float *part_g,
+                  double *part_J, int num_sms, cudaStream_t st)
 {
     if (n == 0) return CP_OK;
     SmoothArgs a{};
@@ -315,6 +378,11 @@ int launch_smooth(const ModelDev &m, const SceneDev &sc, const float *xi, int n,
     a.gJ = gJ;
     a.J = J;
     a.dxi = dxi;
+    a.groups = smooth_groups(n, a.chunks, num_sms);
+    a.chunks_per_group = (a.chunks + a.groups - 1) / a.groups;
+    a.groups = (a.chunks + a.chunks_per_group - 1) / a.chunks_per_group;   // no empty group
+    a.part_g = part_g;
+    a.part_J = part_J;
     return dxi != nullptr ? launch_smooth_t<true>(m, sc, a, num_sms, st)
                           : launch_smooth_t<false>(m, sc, a, num_sms, st);
 }
