@@ -126,6 +126,9 @@ typedef struct cp_params {
     double smooth_beta;     /* differentiable form: softplus width beta (m); 0 selects 0.01 */
     int32_t eval_ctas_per_sm; /* launch shape of the evaluation kernel: CTAs per SM of its
                                  persistent grid (0: as many as fit) */
+    int32_t debug_withhold_staging; /* test hook, 0 in use: 1 makes the brute-force
+                                 evaluation issue no shared-memory staging copy, so that its
+                                 bounded wait runs out and CP_ERR_TIMEOUT is reported */
 } cp_params;
 
 /* Cost terms of the final mean path and the state of a finished plan. */

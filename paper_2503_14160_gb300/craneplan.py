@@ -63,7 +63,8 @@ class cp_params(ctypes.Structure):
                 ("max_cylinders", ctypes.c_int32), ("max_boxes", ctypes.c_int32),
                 ("grid_cell", ctypes.c_double), ("grid_half_extent", ctypes.c_double),
                 ("max_grid_items", ctypes.c_int64), ("smooth_margin", ctypes.c_double),
-                ("smooth_beta", ctypes.c_double), ("eval_ctas_per_sm", ctypes.c_int32)]
+                ("smooth_beta", ctypes.c_double), ("eval_ctas_per_sm", ctypes.c_int32),
+                ("debug_withhold_staging", ctypes.c_int32)]
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -227,10 +228,11 @@ def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 max_cylinders: int = 0, max_boxes: int = 0, grid_cell: float = 0.0,
                 grid_half_extent: float = 0.0, max_grid_items: int = 0,
                 smooth_margin: float = 0.05, smooth_beta: float = 0.01,
-                eval_ctas_per_sm: int = 0) -> cp_params:
+                eval_ctas_per_sm: int = 0, debug_withhold_staging: int = 0) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
                      query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
-                     max_grid_items, smooth_margin, smooth_beta, eval_ctas_per_sm)
+                     max_grid_items, smooth_margin, smooth_beta, eval_ctas_per_sm,
+                     debug_withhold_staging)
 
 
 # --------------------------------------------------------------------------- entry points

@@ -142,6 +142,8 @@ struct cp_planner {
     uint8_t *mean_flag = nullptr;
     float *grad = nullptr;      // [N][D] gradient buffer for polish
     float4 *ends_f = nullptr;   // [2] {q0, qd} in float, written with the end points
+    unsigned long long *rkey_a = nullptr, *rkey_b = nullptr;   // radix sort scratch
+    int *rval_a = nullptr, *rval_b = nullptr, *rhist = nullptr;
     float *smooth_part_g = nullptr;   // partial gradients when few candidates share the GPU
     double *smooth_part_J = nullptr;
     int smem_optin = 0;
@@ -305,6 +307,8 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.qd = p->qdf;
     a.ends = p->ends_f;
     a.ctas_per_sm = p->prm.eval_ctas_per_sm;
+    a.withhold_staging = p->prm.debug_withhold_staging;
+    a.status = p->status;
     a.basis = p->basis;
     a.partial = p->partial;
     a.flagword = p->flagword;
@@ -343,11 +347,20 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
 {
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
-    CP_CUDA(cudaMemsetAsync(p->rank, 0, sizeof(int) * p->N, p->st));
-    if ((rc = launch_rank(d_J, p->N, p->nu, p->rank, p->st)) != CP_OK) return rc;
-    if ((rc = launch_scatter(p->rank, d_J, d_xi, p->N, p->nu, p->D, p->elite, p->elites, p->best,
-                             p->st)) != CP_OK)
-        return rc;
+    if (p->N >= kRadixMinN) {
+        if ((rc = launch_radix_rank(d_J, p->N, p->rkey_a, p->rkey_b, p->rval_a, p->rval_b, p->rhist,
+                                    p->st)) != CP_OK)
+            return rc;
+        if ((rc = launch_gather_elites(p->rval_a, d_J, d_xi, p->nu, p->D, p->elite, p->elites, p->best,
+                                       p->st)) != CP_OK)
+            return rc;
+    } else {
+        CP_CUDA(cudaMemsetAsync(p->rank, 0, sizeof(int) * p->N, p->st));
+        if ((rc = launch_rank(d_J, p->N, p->nu, p->rank, p->st)) != CP_OK) return rc;
+        if ((rc = launch_scatter(p->rank, d_J, d_xi, p->N, p->nu, p->D, p->elite, p->elites, p->best,
+                                 p->st)) != CP_OK)
+            return rc;
+    }
     if ((rc = launch_mean(p->elites, p->w, p->nu, p->D, p->mean_part, p->mu, p->st)) != CP_OK)
         return rc;
     if ((rc = launch_cov(p->elites, p->w, p->mu, p->nu, p->D, p->prm.eps, p->cov_part, p->C,
@@ -506,6 +519,12 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t units_max = (size_t)smooth_partial_units(p->num_sms);
     const size_t o_sp_g = L.take<float>(units_max * D);
     const size_t o_sp_J = L.take<double>(units_max);
+    const bool radix = p->N >= kRadixMinN;
+    const size_t o_rka = L.take<unsigned long long>(radix ? N : 1);
+    const size_t o_rkb = L.take<unsigned long long>(radix ? N : 1);
+    const size_t o_rva = L.take<int>(radix ? N : 1);
+    const size_t o_rvb = L.take<int>(radix ? N : 1);
+    const size_t o_rh = L.take<int>(radix ? 256 * (size_t)radix_tiles(p->N) : 1);
     e = cudaMalloc((void **)&p->base, L.bytes);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(workspace)"));
     char *b = p->base;
@@ -542,6 +561,11 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mean_flag = (uint8_t *)(b + o_mean_flag);
     p->grad = (float *)(b + o_grad);
     p->ends_f = (float4 *)(b + o_ends_f);
+    p->rkey_a = (unsigned long long *)(b + o_rka);
+    p->rkey_b = (unsigned long long *)(b + o_rkb);
+    p->rval_a = (int *)(b + o_rva);
+    p->rval_b = (int *)(b + o_rvb);
+    p->rhist = (int *)(b + o_rh);
     p->smooth_part_g = (float *)(b + o_sp_g);
     p->smooth_part_J = (double *)(b + o_sp_J);
     p->grid_count = (int *)(b + o_grid_count);

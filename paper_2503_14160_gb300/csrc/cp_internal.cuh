@@ -91,6 +91,8 @@ struct EvalArgs {
     float4 q0, qd;              // end points, used when `ends` is null
     const float4 *ends;         // optional device copy {q0, qd}, read at run time
     int ctas_per_sm;            // persistent-grid CTAs per SM (0: as many as fit)
+    int withhold_staging;       // test hook: issue no staging copy, so its wait runs out
+    uint32_t *status;           // device status word (DEV_ERR_*) or null
     const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
     float4 *partial;            // [chunks][n] {J_p, sum pen, J_l, length} (float)
     uint32_t *flagword;         // [chunks][n]
@@ -151,6 +153,12 @@ int launch_mean(const float *elites, const double *w, int nu, int D, double *par
 int launch_cov(const float *elites, const double *w, const double *mu, int nu, int D,
                double eps, double *partial, double *C, cudaStream_t st);
 int update_chunks(int nu);
+int radix_tiles(int N);
+int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,
+                      int *val_a, int *val_b, int *hist, cudaStream_t st);
+int launch_gather_elites(const int *sorted, const double *J, const float *xi, int nu, int D,
+                         int *elite, float *elites, double *best_J, cudaStream_t st);
+constexpr int kRadixMinN = 8193;   // the radix sort ranks populations above 8192
 int update_configure();
 
 }  // namespace cp

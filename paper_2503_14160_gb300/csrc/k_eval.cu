@@ -5,7 +5,8 @@
 // Work decomposition: a work unit is (candidate, chunk of 32 consecutive checkpoints); a
 // warp takes one unit at a time, one checkpoint per lane, so the 32 lanes of a warp read
 // the same one or two spline spans (float4 control points, broadcast loads). All
-// obstacles are staged once per CTA in shared memory. Per checkpoint and link sphere the
+// obstacles are staged once per CTA in shared memory by bulk copies (TMA, no multicast)
+// completing on an mbarrier with a bounded wait. Per checkpoint and link sphere the
 // obstacle loop is a 2-FMA power test against every cylinder; only pairs that pass it
 // (sphere within reach of the cylinder) take the exact capped-cylinder distance. Per
 // unit, lane values are reduced with warp shuffles (FP32) into one partial per unit; a
@@ -21,6 +22,72 @@ constexpr int kEvalThreads = 256;
 #endif
 constexpr int kEvalMinBlocks = CP_EVAL_MIN_BLOCKS;
 constexpr int kObstaclesPerBranch = 2;   // obstacles tested between two branches
+constexpr long long kStagingWaitCycles = 2000000000ll;   // about one second at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Bulk copy (TMA, no multicast) of `bytes` from global memory into this CTA's shared
+// memory; both addresses 16-byte aligned, bytes a multiple of 16. Completes on `bar`.
+__device__ __forceinline__ void bulk_copy_to_smem(void *dst, const void *src, uint32_t bytes,
+                                                  uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbarrier_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Stages the obstacle records, box records and spline table into shared memory with bulk
+// copies completing on one mbarrier. Every thread waits at most kStagingWaitCycles; when
+// the wait runs out in any thread the CTA records DEV_ERR_TIMEOUT and returns false (a
+// uniform decision). `withhold` issues no copy, so that the wait runs out on purpose (the
+// test of this path); nothing is then in flight when the CTA leaves.
+__device__ __noinline__ bool stage_bulk(uint64_t *bar, float4 *s_filt, float4 *s_exact, float4 *s_bc,
+                           float4 *s_bh, float4 *s_basis, const SceneDev &sc, const EvalArgs &a)
+{
+    const uint32_t b_cyl = 16u * (uint32_t)sc.n_cyl, b_box = 16u * (uint32_t)sc.n_box;
+    const uint32_t b_basis = 32u * (uint32_t)a.S;
+    const uint32_t total = 2 * b_cyl + 2 * b_box + b_basis;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(smem_u32(bar)), "r"(total) : "memory");
+        if (!a.withhold_staging) {
+            if (b_cyl) {
+                bulk_copy_to_smem(s_filt, sc.cyl_filt, b_cyl, bar);
+                bulk_copy_to_smem(s_exact, sc.cyl_exact, b_cyl, bar);
+            }
+            if (b_box) {
+                bulk_copy_to_smem(s_bc, sc.box_c, b_box, bar);
+                bulk_copy_to_smem(s_bh, sc.box_h, b_box, bar);
+            }
+            bulk_copy_to_smem(s_basis, a.basis, b_basis, bar);
+        }
+    }
+    const long long t0 = clock64();
+    bool done = mbarrier_try_wait(bar, 0);
+    while (!done && clock64() - t0 < kStagingWaitCycles) done = mbarrier_try_wait(bar, 0);
+    if (__syncthreads_or(!done)) {
+        if (threadIdx.x == 0 && a.status != nullptr) atomicOr(a.status, DEV_ERR_TIMEOUT);
+        return false;
+    }
+    return true;
+}
 
 // Exact signed distance of every sphere whose filter test passes against one cylinder
 // (f = {cx, cy, W}, e = {R, z_lo, z_hi}); +inf when none passes.
@@ -50,16 +117,8 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
     float4 *s_bc = s_exact + sc.n_cyl;
     float4 *s_bh = s_bc + sc.n_box;
     float4 *s_basis = s_bh + sc.n_box;
-    for (int i = threadIdx.x; i < sc.n_cyl; i += blockDim.x) {
-        s_filt[i] = sc.cyl_filt[i];
-        s_exact[i] = sc.cyl_exact[i];
-    }
-    for (int i = threadIdx.x; i < sc.n_box; i += blockDim.x) {
-        s_bc[i] = sc.box_c[i];
-        s_bh[i] = sc.box_h[i];
-    }
-    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x) s_basis[i] = a.basis[i];
-    __syncthreads();
+    __shared__ __align__(8) uint64_t staging_bar;
+    if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, sc, a)) return;
 
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);

@@ -4,6 +4,7 @@
 //                    (J ascending, NaN as +inf, ties by index): an all-pairs count, split
 //                    over the grid's y dimension and summed with integer atomics
 //   k_scatter        elite list in rank order, the elite rows gathered contiguously
+//   k_radix_*        for large N instead: a stable LSD radix sort of the keys (8 x 8 bits)
 //   k_mean_partial / k_mean_combine   mu = sum_j w_j xi_(j), FP64, fixed order
 //   k_cov_partial / k_cov_combine     C = sum_j w_j (xi_(j) - mu)(xi_(j) - mu)^T + eps I,
 //                    FP64, about the new mean, 16x16 output tiles x chunks of elites,
@@ -178,7 +179,159 @@ __global__ void k_cov_combine(const double *__restrict__ partial, int n_chunks, 
     C[idx] = acc;
 }
 
+// ---------------------------------------------------------------- LSD radix sort (large N)
+// Stable ascending sort of (key, index) by the order-preserving 64-bit keys: eight passes of
+// 8-bit digits; tiles of kRadixTile consecutive elements; per pass a tile histogram, an
+// exclusive scan in (digit, tile) order, and a stable scatter (ranks inside a warp from
+// __match_any_sync, across warps and rounds from per-digit prefixes).
+constexpr int kRadixTile = 1024;
+constexpr int kRadixThreads = 256;
+
+__global__ void k_radix_init(const double *__restrict__ J, int N, unsigned long long *key, int *val)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        key[i] = order_key(J[i]);
+        val[i] = i;
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_hist(const unsigned long long *__restrict__ key, int N, int shift, int tiles, int *hist)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int b = blockIdx.x * kRadixTile, e = min(N, b + kRadixTile);
+    for (int i = b + threadIdx.x; i < e; i += kRadixThreads)
+        atomicAdd(&h[(int)((key[i] >> shift) & 255ull)], 1);
+    __syncthreads();
+    hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];   // digit-major
+}
+
+// Exclusive scan of n = 256 * tiles counts in place (one CTA).
+__global__ void __launch_bounds__(1024) k_radix_scan(int *a, int n)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int b = t * per, e = min(n, b + per);
+    int acc = 0;
+    for (int i = b; i < e; ++i) acc += a[i];
+    part[t] = acc;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = t > 0 ? part[t - 1] : 0;
+    for (int i = b; i < e; ++i) {
+        const int c = a[i];
+        a[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_scatter(const unsigned long long *__restrict__ key_in, const int *__restrict__ val_in, int N,
+                int shift, int tiles, const int *__restrict__ offsets, unsigned long long *key_out,
+                int *val_out)
+{
+    __shared__ int run[256];            // elements of each digit placed by earlier rounds
+    __shared__ int wcount[8][256];      // per-warp digit counts of the current round
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    run[threadIdx.x] = offsets[threadIdx.x * tiles + blockIdx.x];
+    const int b = blockIdx.x * kRadixTile, e = min(N, b + kRadixTile);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = b; r < e; r += kRadixThreads) {
+        for (int w = 0; w < 8; ++w) wcount[w][threadIdx.x] = 0;
+        __syncthreads();
+        const int i = r + threadIdx.x;
+        const bool valid = i < e;
+        unsigned long long k = 0;
+        int v = 0, d = 256 + lane;      // invalid lanes get digits no valid lane has
+        if (valid) {
+            k = key_in[i];
+            v = val_in[i];
+            d = (int)((k >> shift) & 255ull);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int in_warp = __popc(peers & lt);
+        if (valid && in_warp == 0) wcount[warp][d] = __popc(peers);
+        __syncthreads();
+        int before = 0;                 // same digit in earlier warps of this round
+        if (valid)
+            for (int w = 0; w < warp; ++w) before += wcount[w][d];
+        if (valid) {
+            const int pos = run[d] + before + in_warp;
+            key_out[pos] = k;
+            val_out[pos] = v;
+        }
+        __syncthreads();
+        int total = 0;
+        for (int w = 0; w < 8; ++w) total += wcount[w][threadIdx.x];
+        run[threadIdx.x] += total;
+        __syncthreads();
+    }
+}
+
+// Elite list and rows from the sorted indices; rank 0 also records its cost.
+__global__ void k_gather_elites(const int *__restrict__ sorted, const double *__restrict__ J,
+                                const float *__restrict__ xi, int nu, int D, int *elite,
+                                float *elites, double *best_J)
+{
+    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nu) return;
+    const int i = sorted[r];
+    if (lane == 0) {
+        elite[r] = i;
+        if (r == 0 && best_J != nullptr) *best_J = J[i];
+    }
+    for (int c = lane; c < D; c += 32) elites[(size_t)r * D + c] = xi[(size_t)i * D + c];
+}
+
 }  // namespace
+
+int radix_tiles(int N) { return (N + kRadixTile - 1) / kRadixTile; }
+
+// Sorted candidate order by (J, index) into `sorted` (N ints); scratch: two key buffers of
+// N, one value buffer of N, hist of 256 * radix_tiles(N) ints.
+int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,
+                      int *val_a, int *val_b, int *hist, cudaStream_t st)
+{
+    const int tiles = radix_tiles(N);
+    k_radix_init<<<(N + 255) / 256, 256, 0, st>>>(J, N, key_a, val_a);
+    CP_LAUNCHED("k_radix_init");
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        k_radix_hist<<<tiles, kRadixThreads, 0, st>>>(key_a, N, shift, tiles, hist);
+        CP_LAUNCHED("k_radix_hist");
+        k_radix_scan<<<1, 1024, 0, st>>>(hist, 256 * tiles);
+        CP_LAUNCHED("k_radix_scan");
+        k_radix_scatter<<<tiles, kRadixThreads, 0, st>>>(key_a, val_a, N, shift, tiles, hist, key_b, val_b);
+        CP_LAUNCHED("k_radix_scatter");
+        unsigned long long *tk = key_a;
+        key_a = key_b;
+        key_b = tk;
+        int *tv = val_a;
+        val_a = val_b;
+        val_b = tv;
+    }
+    return CP_OK;   // after an even number of passes the result is back in val_a
+}
+
+int launch_gather_elites(const int *sorted, const double *J, const float *xi, int nu, int D,
+                         int *elite, float *elites, double *best_J, cudaStream_t st)
+{
+    const int threads = 256;
+    k_gather_elites<<<(nu * 32 + threads - 1) / threads, threads, 0, st>>>(sorted, J, xi, nu, D, elite,
+                                                                          elites, best_J);
+    CP_LAUNCHED("k_gather_elites");
+    return CP_OK;
+}
 
 // Number of partials (chunks of elites) the update uses for nu elites, and elites per chunk.
 int update_chunks(int nu)

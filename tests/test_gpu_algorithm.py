@@ -60,7 +60,7 @@ def test_sample_and_factor(lib, crane, N, K, it):
 
 
 @pytest.mark.parametrize("N,K,nu,ties", [(300, 4, 150, 30), (4096, 16, 0, 0), (77, 2, 1, 5),
-                                         (65536, 32, 0, 100)])
+                                         (8193, 8, 8000, 200), (65536, 32, 0, 100)])
 def test_update_matches_oracle(lib, crane, N, K, nu, ties):
     import torch
     from paper_2503_14160_gb300 import workloads
@@ -91,6 +91,29 @@ def test_update_matches_oracle(lib, crane, N, K, nu, ties):
         np.testing.assert_allclose(Cg, C_o, rtol=1e-11, atol=1e-14 * np.abs(C_o).max())
         np.testing.assert_allclose(Lg.cpu().numpy(), np.linalg.cholesky(Cg), rtol=1e-11,
                                    atol=1e-14)
+    finally:
+        s.close()
+
+
+def test_rank_large_population_edge_values(lib, crane):
+    """The radix ranking used for large populations on the values that stress an
+    order-preserving key: negative costs, -0 against +0, +-inf, NaN (after +inf in index
+    order), long runs of ties; every candidate is an elite so the whole order is checked."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    N, K = 9001, 1
+    s = Setup(crane, workloads.empty_scene(), N=N, K=K, S=2, n_elites=N, eps=1e-8)
+    try:
+        g = np.random.default_rng(7)
+        J = g.choice([-3.5, -0.0, 0.0, 1e-300, -1e-300, 2.0, np.inf, -np.inf, np.nan], size=N)
+        J[::7] = g.normal(size=len(J[::7])) * 1e3
+        xi = g.normal(size=(N, K, 4)).astype(np.float32)
+        lib.cp_set_endpoints(s.h, np.zeros(4), np.ones(4))
+        lib.cp_update(s.h, torch.from_numpy(J).cuda(), torch.from_numpy(xi).cuda())
+        el = torch.zeros(N, dtype=torch.int32, device="cuda")
+        lib.cp_get_elites(s.h, el)
+        lib.cp_synchronize(s.h)
+        np.testing.assert_array_equal(el.cpu().numpy(), s.oracle.rank(J))
     finally:
         s.close()
 

@@ -225,3 +225,37 @@ def test_philox_bits(lib):
         lib.cp_philox4x32_10(c, key, ctr.shape[0], out)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), want)
+
+
+def test_staging_wait_runs_out_and_reports(lib, crane):
+    """Failure detection without a fault: the evaluation kernel is told to issue no staging
+    copy, so its bounded mbarrier wait runs out (about a second); the CTAs record the
+    timeout and leave with nothing in flight, the host reads CP_ERR_TIMEOUT, and the context
+    stays usable for the next planner."""
+    import time
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("single_small")
+    scene = _scene("single_small")
+    xi = workloads.random_candidates(q0, qd, 4, 32, seed=2)
+    model = lib.make_model(crane)
+    params = lib.make_params(32, 4, 8, debug_withhold_staging=1)
+    bad = lib.Planner(crane, scene, params)
+    try:
+        lib.cp_set_endpoints(bad.handle, q0, qd)
+        x = torch.from_numpy(xi).cuda()
+        J = torch.zeros(32, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        lib.cp_evaluate(bad.handle, x, 32, J)
+        with pytest.raises(lib.CranePlanError) as e:
+            lib.cp_synchronize(bad.handle)
+        assert e.value.status == -3
+        assert time.perf_counter() - t0 < 30.0
+        lib.cp_synchronize(bad.handle)          # the report is cleared once read
+    finally:
+        bad.close()
+    s = Setup(crane, scene, N=32, K=4, S=8)
+    try:
+        check_eval(s, xi, q0, qd)               # the device keeps working
+    finally:
+        s.close()
