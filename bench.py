@@ -36,6 +36,38 @@ PEAK_SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FLOPS_PER_PAIR = 5          # 2 sub, 1 mul, 1 fma per sphere-obstacle pair
 FLOPS_PER_CHECKPOINT = 140  # spline 32, kinematics ~80, length 12, limits 16
+FLOPS_FRAME_PER_SPHERE = 6  # broad phase: the sphere centre in the unit's frame (2 mul, 2 fma)
+FLOPS_PER_BROAD_TEST = 10   # broad phase: one obstacle against a unit's box
+FP32_PEAK_TFLOPS = PEAK_SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+
+
+def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, broadphase, sm_mhz):
+    """Algorithmic FP32 work of the evaluation launches in `timing` over their device time.
+
+    Per checkpoint FLOPS_PER_CHECKPOINT (spline, kinematics, length, limits); per sphere and
+    obstacle whose pair test runs FLOPS_PER_PAIR, for all 32 lanes of a unit. Exhaustive:
+    every obstacle of every unit is tested. Broad phase: every (unit, obstacle) takes one
+    box test, each checkpoint places its spheres in the unit frame, and only the counted
+    survivors take pair tests."""
+    units = timing["eval_units"]
+    tests = timing["eval_obstacle_tests"]
+    if units <= 0 or tests < 0 or timing["eval_ms"] <= 0:
+        return None
+    flops = candidates * n_s * FLOPS_PER_CHECKPOINT + tests * 32 * n_spheres * FLOPS_PER_PAIR
+    if broadphase:
+        flops += candidates * n_s * n_spheres * FLOPS_FRAME_PER_SPHERE
+        flops += units * n_obstacles * FLOPS_PER_BROAD_TEST
+    achieved = flops / (timing["eval_ms"] / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "k_eval" + (" (broad phase)" if broadphase else " (exhaustive)"),
+            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "frac_at_observed_clock": (achieved / (FP32_PEAK_TFLOPS * sm_mhz / 2070.0)
+                                       if sm_mhz else None),
+            "eval_ms_per_launch": timing["eval_ms"] / max(timing["eval_launches"], 1),
+            "eval_launches": timing["eval_launches"],
+            "pair_tests_per_checkpoint": tests * 32 * n_spheres / max(candidates * n_s, 1),
+            "pair_tests_exhaustive_per_checkpoint": n_spheres * n_obstacles}
 
 
 def dist_env():
@@ -170,7 +202,7 @@ def run_ours(args):
     crane = workloads.forestry_crane()
     scene = workloads.make_scene(wl)
     params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank,
-                            grid_cell=wl.grid_cell)
+                            grid_cell=wl.grid_cell, eval_exhaustive=int(args.exhaustive))
     planner = cp.Planner(crane, scene, params)
     h = planner.handle
     q0, qd, ok = select_endpoints_gpu(cp, planner, crane, wl.seed, rank)
@@ -232,16 +264,21 @@ def run_ours(args):
     units = wl.n_candidates * iters * ws
     value = units / (ms / 1e3)
 
-    # roofline of the evaluation kernel (FK + collision + cost)
+    # roofline of the evaluation kernel (FK + collision + cost); per plan the kernel runs
+    # T times on N candidates and once on the mean path
     n_s = wl.n_checkpoints
-    pairs = len(crane.spheres) * (scene.n_cyl + scene.n_box)
-    flops_per_candidate = n_s * (pairs * FLOPS_PER_PAIR + FLOPS_PER_CHECKPOINT)
-    # per plan the kernel runs T times on N candidates and once on the mean path
-    flops_timed = args.steps * (wl.n_candidates * iters + 1) * flops_per_candidate
     eval_ms = timing["eval_ms"] / max(timing["eval_launches"], 1)
-    achieved = flops_timed / (timing["eval_ms"] / 1e3) / 1e12
-    peak = PEAK_SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
     clk = clocks.summary()
+    candidates = args.steps * (wl.n_candidates * iters + 1)
+    roofline = None
+    roofline_exhaustive = None
+    if wl.grid_cell <= 0:
+        roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
+                                 candidates, not args.exhaustive, clk.get("sm_mhz"))
+        roofline["traffic"] = traffic_per_launch()
+        if not args.exhaustive:
+            roofline_exhaustive = exhaustive_roofline(cp, crane, scene, wl, q0, qd,
+                                                      clk.get("sm_mhz"))
 
     if rank == 0:
         bi = scene.n_cyl * 40 + scene.n_box * 48 + 64
@@ -261,14 +298,8 @@ def run_ours(args):
             "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "ms_per_plan": ms_e2e,
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
             "gpu_launches": launches,
-            "roofline": None if wl.grid_cell > 0 else
-                        {"bound": "alu", "kernel": "k_eval", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                         "frac_at_observed_clock": (achieved / (peak * clk["sm_mhz"] / 2070.0)
-                                                    if clk.get("sm_mhz") else None),
-                         "traffic": traffic_per_launch(), "eval_ms_per_launch": eval_ms,
-                         "eval_launches": timing["eval_launches"]},
+            "roofline": roofline,
+            "roofline_exhaustive": roofline_exhaustive,
             "eval_kernel": {"name": "k_eval_grid" if wl.grid_cell > 0 else "k_eval",
                             "ms_per_launch": eval_ms, "launches": timing["eval_launches"]},
             "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
@@ -282,6 +313,32 @@ def run_ours(args):
     planner.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def exhaustive_roofline(cp, crane, scene, wl, q0, qd, sm_mhz, iterations=10):
+    """The exhaustive form of the evaluation (every sphere against every obstacle) timed on
+    the same query for a few iterations, for comparison with the broad phase."""
+    import torch
+    params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed,
+                            eval_exhaustive=1)
+    planner = cp.Planner(crane, scene, params)
+    try:
+        h = planner.handle
+        cp.cp_set_endpoints(h, q0, qd)
+        cp.cp_plan(h, 2, K=None)
+        torch.cuda.synchronize()
+        cp.cp_set_timing(h, True)
+        cp.cp_set_endpoints(h, q0, qd)
+        cp.cp_plan(h, iterations, K=None)
+        t = cp.cp_get_timing(h)
+        cp.cp_set_timing(h, False)
+    finally:
+        planner.close()
+    r = eval_roofline(t, len(crane.spheres), scene.n_cyl + scene.n_box, wl.n_checkpoints,
+                      wl.n_candidates * iterations + 1, False, sm_mhz)
+    if r is not None:
+        r["iterations"] = iterations
+    return r
 
 
 def run_differentiable(args):
@@ -520,6 +577,8 @@ def main():
     ap.add_argument("--iterations", type=int, default=0, help="override iterations per plan")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--exhaustive", action="store_true",
+                    help="evaluate every sphere against every obstacle (no broad phase)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -129,6 +129,11 @@ typedef struct cp_params {
     int32_t debug_withhold_staging; /* test hook, 0 in use: 1 makes the brute-force
                                  evaluation issue no shared-memory staging copy, so that its
                                  bounded wait runs out and CP_ERR_TIMEOUT is reported */
+    int32_t eval_exhaustive; /* 1: test every sphere against every obstacle; 0 (default): a
+                                broad phase first drops, per 32 checkpoints of a candidate,
+                                the obstacles out of reach of all their spheres. Both give
+                                the same results bit for bit; only the time differs. Not
+                                used by the grid form (grid_cell > 0). */
 } cp_params;
 
 /* Cost terms of the final mean path and the state of a finished plan. */
@@ -143,12 +148,17 @@ typedef struct cp_plan_stats {
 } cp_plan_stats;
 
 /* Accumulated device time per stage while timing is on (CUDA events on the planner's
- * stream around each stage's launches). */
+ * stream around each stage's launches), and the work the evaluation kernel did. */
 typedef struct cp_timing {
     double eval_ms;   int64_t eval_launches;    /* FK + collision + cost kernel only */
     double sample_ms; int64_t sample_launches;
     double factor_ms; int64_t factor_launches;
     double update_ms; int64_t update_launches;  /* rank, weights, mean, covariance */
+    int64_t eval_units;           /* work units evaluated: candidates x ceil(n_s / 32) */
+    int64_t eval_obstacle_tests;  /* (unit, obstacle) pairs whose per-sphere test ran:
+                                     the broad-phase survivors, or every obstacle of every
+                                     unit in the exhaustive form (counted on the device
+                                     for the broad phase; -1 for the grid form) */
 } cp_timing;
 
 typedef struct cp_planner cp_planner;

@@ -64,7 +64,7 @@ class cp_params(ctypes.Structure):
                 ("grid_cell", ctypes.c_double), ("grid_half_extent", ctypes.c_double),
                 ("max_grid_items", ctypes.c_int64), ("smooth_margin", ctypes.c_double),
                 ("smooth_beta", ctypes.c_double), ("eval_ctas_per_sm", ctypes.c_int32),
-                ("debug_withhold_staging", ctypes.c_int32)]
+                ("debug_withhold_staging", ctypes.c_int32), ("eval_exhaustive", ctypes.c_int32)]
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -88,7 +88,8 @@ class cp_timing(ctypes.Structure):
     _fields_ = [("eval_ms", ctypes.c_double), ("eval_launches", ctypes.c_int64),
                 ("sample_ms", ctypes.c_double), ("sample_launches", ctypes.c_int64),
                 ("factor_ms", ctypes.c_double), ("factor_launches", ctypes.c_int64),
-                ("update_ms", ctypes.c_double), ("update_launches", ctypes.c_int64)]
+                ("update_ms", ctypes.c_double), ("update_launches", ctypes.c_int64),
+                ("eval_units", ctypes.c_int64), ("eval_obstacle_tests", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -228,11 +229,12 @@ def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 max_cylinders: int = 0, max_boxes: int = 0, grid_cell: float = 0.0,
                 grid_half_extent: float = 0.0, max_grid_items: int = 0,
                 smooth_margin: float = 0.05, smooth_beta: float = 0.01,
-                eval_ctas_per_sm: int = 0, debug_withhold_staging: int = 0) -> cp_params:
+                eval_ctas_per_sm: int = 0, debug_withhold_staging: int = 0,
+                eval_exhaustive: int = 0) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
                      query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
                      max_grid_items, smooth_margin, smooth_beta, eval_ctas_per_sm,
-                     debug_withhold_staging)
+                     debug_withhold_staging, eval_exhaustive)
 
 
 # --------------------------------------------------------------------------- entry points

@@ -49,6 +49,8 @@ struct Timer {
     size_t used = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[ST_COUNT];
     cudaEvent_t open = nullptr;
+    int64_t units = 0, tests = 0;   // evaluation work while on (tests: exhaustive form)
+    bool grid = false;
 
     int begin(cudaStream_t st)
     {
@@ -84,6 +86,8 @@ struct Timer {
     {
         used = 0;
         for (auto &s : spans) s.clear();
+        units = tests = 0;
+        grid = false;
     }
     void destroy()
     {
@@ -142,6 +146,7 @@ struct cp_planner {
     uint8_t *mean_flag = nullptr;
     float *grad = nullptr;      // [N][D] gradient buffer for polish
     float4 *ends_f = nullptr;   // [2] {q0, qd} in float, written with the end points
+    unsigned long long *work = nullptr;   // broad-phase survivor count while timing
     unsigned long long *rkey_a = nullptr, *rkey_b = nullptr;   // radix sort scratch
     int *rval_a = nullptr, *rval_b = nullptr, *rhist = nullptr;
     float *smooth_part_g = nullptr;   // partial gradients when few candidates share the GPU
@@ -255,6 +260,8 @@ int validate_params(const cp_params *p)
         return set_error("cost weights must be finite and >= 0"), CP_ERR_ARG;
     if (p->max_cylinders < 0 || p->max_boxes < 0) return set_error("negative capacity"), CP_ERR_ARG;
     if (p->eval_ctas_per_sm < 0) return set_error("eval_ctas_per_sm must be >= 0"), CP_ERR_ARG;
+    if (p->eval_exhaustive != 0 && p->eval_exhaustive != 1)
+        return set_error("eval_exhaustive must be 0 or 1"), CP_ERR_ARG;
     if (!(p->grid_cell >= 0.0) || !is_finite(p->grid_cell) || !(p->grid_half_extent >= 0.0) ||
         !is_finite(p->grid_half_extent) || p->max_grid_items < 0 || !(p->smooth_margin >= 0.0) ||
         !is_finite(p->smooth_margin) || !(p->smooth_beta >= 0.0) || !is_finite(p->smooth_beta))
@@ -308,6 +315,13 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.ends = p->ends_f;
     a.ctas_per_sm = p->prm.eval_ctas_per_sm;
     a.withhold_staging = p->prm.debug_withhold_staging;
+    a.broadphase = p->prm.eval_exhaustive ? 0 : 1;
+    a.work = p->timer.on ? p->work : nullptr;
+    if (p->timer.on) {
+        p->timer.units += (int64_t)n * p->chunks;
+        if (p->use_grid) p->timer.grid = true;
+        else if (!a.broadphase) p->timer.tests += (int64_t)n * p->chunks * (p->sdev.n_cyl + p->sdev.n_box);
+    }
     a.status = p->status;
     a.basis = p->basis;
     a.partial = p->partial;
@@ -519,6 +533,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t units_max = (size_t)smooth_partial_units(p->num_sms);
     const size_t o_sp_g = L.take<float>(units_max * D);
     const size_t o_sp_J = L.take<double>(units_max);
+    const size_t o_work = L.take<unsigned long long>(1);
     const bool radix = p->N >= kRadixMinN;
     const size_t o_rka = L.take<unsigned long long>(radix ? N : 1);
     const size_t o_rkb = L.take<unsigned long long>(radix ? N : 1);
@@ -561,6 +576,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mean_flag = (uint8_t *)(b + o_mean_flag);
     p->grad = (float *)(b + o_grad);
     p->ends_f = (float4 *)(b + o_ends_f);
+    p->work = (unsigned long long *)(b + o_work);
     p->rkey_a = (unsigned long long *)(b + o_rka);
     p->rkey_b = (unsigned long long *)(b + o_rkb);
     p->rval_a = (int *)(b + o_rva);
@@ -805,6 +821,8 @@ int cp_set_timing(cp_planner *p, int32_t on)
     CP_CUDA(cudaStreamSynchronize(p->st));
     p->timer.clear();
     p->timer.on = on != 0;
+    CP_CUDA(cudaMemsetAsync(p->work, 0, sizeof(unsigned long long), p->st));
+    CP_CUDA(cudaStreamSynchronize(p->st));
     return CP_OK;
 }
 
@@ -830,7 +848,13 @@ int cp_get_timing(cp_planner *p, cp_timing *out)
     out->factor_launches = cnt[ST_FACTOR];
     out->update_ms = ms[ST_UPDATE];
     out->update_launches = cnt[ST_UPDATE];
+    unsigned long long survivors = 0;
+    CP_CUDA(cudaMemcpy(&survivors, p->work, sizeof(survivors), cudaMemcpyDeviceToHost));
+    out->eval_units = p->timer.units;
+    out->eval_obstacle_tests = p->timer.grid ? -1 : p->timer.tests + (int64_t)survivors;
     p->timer.clear();
+    CP_CUDA(cudaMemsetAsync(p->work, 0, sizeof(unsigned long long), p->st));
+    CP_CUDA(cudaStreamSynchronize(p->st));
     return CP_OK;
 }
 

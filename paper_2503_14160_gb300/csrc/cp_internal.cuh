@@ -92,6 +92,8 @@ struct EvalArgs {
     const float4 *ends;         // optional device copy {q0, qd}, read at run time
     int ctas_per_sm;            // persistent-grid CTAs per SM (0: as many as fit)
     int withhold_staging;       // test hook: issue no staging copy, so its wait runs out
+    int broadphase;             // 1: per-unit broad phase before the per-sphere filter
+    unsigned long long *work;   // optional: += obstacle tests that passed the broad phase
     uint32_t *status;           // device status word (DEV_ERR_*) or null
     const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
     float4 *partial;            // [chunks][n] {J_p, sum pen, J_l, length} (float)

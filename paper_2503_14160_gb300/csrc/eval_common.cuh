@@ -31,10 +31,15 @@ static __device__ __forceinline__ float sdf_box(float x, float y, float z, float
 // Sphere centres at configuration q (chain of Sec. 2 in the linear placement form).
 template <int NSPH>
 static __device__ __forceinline__ void crane_fk(const ModelDev &m, float4 q, float *x, float *y,
-                                         float *z)
+                                         float *z, float *sin_slew = nullptr,
+                                         float *cos_slew = nullptr)
 {
     float s1, c1, s2, c2, s23, c23;
     sincosf(q.x, &s1, &c1);
+    if (sin_slew != nullptr) {
+        *sin_slew = s1;
+        *cos_slew = c1;
+    }
     sincosf(q.y, &s2, &c2);
     sincosf(q.y + q.z, &s23, &c23);
 #pragma unroll

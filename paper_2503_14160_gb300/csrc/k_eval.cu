@@ -105,7 +105,60 @@ __device__ __forceinline__ float exact_cylinders(const ModelDev &m, const float 
     return d;
 }
 
+// Broad phase of one work unit (32 checkpoints of one candidate): the unit's sphere
+// centres are bounded by a box in a frame turned to the slew angle of lane 16, taken as
+// the sine and cosine its kinematics computed (any near-unit vector would do; the same one
+// maps spheres and obstacles). All spheres of one configuration lie on the vertical plane at
+// its slew angle, so the box is long and thin. An obstacle whose centre lies farther than
+// its reach (the `w` of its record) from that box cannot pass the per-sphere filter for any
+// lane; the reach carries 1 cm of slack over the filter's own bound, far above the FP32
+// rounding of either test.
+struct UnitFrame {
+    float c0, s0;     // frame axes
+    float uc, uh;     // box centre and half extent along the slew direction
+    float vc, vh;     // and across it
+};
+
 template <int NSPH>
+__device__ __forceinline__ UnitFrame unit_frame(float sin_slew, float cos_slew, const float *X,
+                                                const float *Y)
+{
+    UnitFrame f;
+    f.s0 = __shfl_sync(0xffffffffu, sin_slew, 16);
+    f.c0 = __shfl_sync(0xffffffffu, cos_slew, 16);
+    float umin = CUDART_INF_F, umax = -CUDART_INF_F, vmin = CUDART_INF_F, vmax = -CUDART_INF_F;
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s) {
+        const float u = fmaf(f.c0, X[s], f.s0 * Y[s]);
+        const float v = fmaf(f.c0, Y[s], -f.s0 * X[s]);
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, off));
+        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, off));
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+    }
+    f.uc = 0.5f * (umin + umax);
+    f.uh = 0.5f * (umax - umin);
+    f.vc = 0.5f * (vmin + vmax);
+    f.vh = 0.5f * (vmax - vmin);
+    return f;
+}
+
+// True when the obstacle record r = {cx, cy, ., reach} may come within reach of the unit.
+__device__ __forceinline__ bool unit_near(const UnitFrame &f, float4 r)
+{
+    const float u = fmaf(f.c0, r.x, f.s0 * r.y);
+    const float v = fmaf(f.c0, r.y, -f.s0 * r.x);
+    return (fabsf(u - f.uc) <= f.uh + r.w) & (fabsf(v - f.vc) <= f.vh + r.w);
+}
+
+template <int NSPH, bool CULL>
 __global__ void __launch_bounds__(kEvalThreads, kEvalMinBlocks)
 k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
 {
@@ -124,6 +177,7 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     const int units = a.n * a.chunks;
+    uint32_t tested = 0;   // broad-phase survivors of this warp's units
 
     for (int u = warp; u < units; u += n_warps) {
         const int cand = u / a.chunks;
@@ -133,7 +187,14 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
         // Sphere centres; per sphere the filter threshold T = margin - (x^2 + y^2) and the
         // scaled coordinates (-2x, -2y), kept in pairs for packed FP32x2 FMAs.
         float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH];
-        crane_fk<NSPH>(m, c.q, X, Y, Z);
+        UnitFrame fr;
+        if constexpr (CULL) {
+            float sin_slew, cos_slew;
+            crane_fk<NSPH>(m, c.q, X, Y, Z, &sin_slew, &cos_slew);
+            fr = unit_frame<NSPH>(sin_slew, cos_slew, X, Y);
+        } else {
+            crane_fk<NSPH>(m, c.q, X, Y, Z);
+        }
 #pragma unroll
         for (int s = 0; s < NSPH; ++s) {
             T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
@@ -148,6 +209,41 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
         }
 
         float dmin = CUDART_INF_F;
+        if constexpr (CULL) {
+            // Broad phase: each lane tests one obstacle of 32 against the unit's box; the
+            // warp then runs the per-sphere filter on the survivors only (a uniform loop).
+            for (int base = 0; base < sc.n_cyl; base += 32) {
+                const int o = base + lane;
+                uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, s_filt[o]));
+                tested += __popc(mask);
+                while (mask) {
+                    const int ob = base + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const float4 f = s_filt[ob];
+                    const float2 cx2 = make_float2(f.x, f.x), cy2 = make_float2(f.y, f.y);
+                    const float2 w2 = make_float2(f.z, f.z);
+                    float2 g[NSPH / 2];
+#pragma unroll
+                    for (int p = 0; p < NSPH / 2; ++p) g[p] = __ffma2_rn(X2[p], cx2, __ffma2_rn(Y2[p], cy2, w2));
+                    if (any_below<NSPH>(g, T)) dmin = fminf(dmin, exact_cylinders<NSPH>(m, X, Y, Z, T, f, s_exact[ob]));
+                }
+            }
+            for (int base = 0; base < sc.n_box; base += 32) {
+                const int o = base + lane;
+                uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_box && unit_near(fr, s_bc[o]));
+                tested += __popc(mask);
+                while (mask) {
+                    const int ob = base + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const float4 bc = s_bc[ob], bh = s_bh[ob];
+#pragma unroll
+                    for (int s = 0; s < NSPH; ++s)
+                        dmin = fminf(dmin, sdf_box(-0.5f * X[s], -0.5f * Y[s], Z[s], bc, bh) - m.sph[s].radius);
+                }
+            }
+            unit_epilogue(a, c, dmin, cand, chunk, lane);
+            continue;
+        }
         // Two obstacles per step: 2 x NSPH power tests rho^2 - (R + r_max)^2 < margin in
         // expanded form (-2x cx - 2y cy + W vs. margin - x^2 - y^2), two packed FMAs per
         // sphere pair; the hit predicates accumulate without branches. Only when a test
@@ -193,6 +289,7 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
 
         unit_epilogue(a, c, dmin, cand, chunk, lane);
     }
+    if (CULL && a.work != nullptr && lane == 0 && tested != 0) atomicAdd(a.work, (unsigned long long)tested);
 }
 
 // One warp per candidate: lanes take the candidate's chunks (lane, lane + 32, ...), sum
@@ -265,11 +362,11 @@ __global__ void k_signed_distance(const ModelDev m, const SceneDev sc, const flo
     d[i] = dmin;
 }
 
-template <int NSPH>
+template <int NSPH, bool CULL>
 int eval_grid(size_t smem, int num_sms, int units, int ctas_per_sm)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<NSPH>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<NSPH, CULL>,
                                                                   kEvalThreads, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
@@ -287,28 +384,26 @@ size_t eval_smem_bytes(int n_cyl, int n_box, int S)
     return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S);
 }
 
-int eval_configure(size_t smem_bytes)
+template <typename F>
+int raise_smem(F *fn, size_t smem_bytes)
 {
-    CP_CUDA(cudaFuncSetAttribute(k_eval<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes));
-    CP_CUDA(cudaFuncSetAttribute(k_eval<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes));
+    cudaFuncAttributes at{};
+    CP_CUDA(cudaFuncGetAttributes(&at, fn));
+    if ((size_t)at.maxDynamicSharedSizeBytes < smem_bytes)
+        CP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
     return CP_OK;
 }
+
+int eval_configure(size_t smem_bytes) { return eval_ensure_smem(smem_bytes); }
 
 // Raise (never lower) the dynamic shared-memory limit of the evaluation kernels.
 int eval_ensure_smem(size_t smem_bytes)
 {
-    cudaFuncAttributes at12{}, at16{};
-    CP_CUDA(cudaFuncGetAttributes(&at12, k_eval<12>));
-    CP_CUDA(cudaFuncGetAttributes(&at16, k_eval<16>));
-    if ((size_t)at12.maxDynamicSharedSizeBytes < smem_bytes)
-        CP_CUDA(cudaFuncSetAttribute(k_eval<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_bytes));
-    if ((size_t)at16.maxDynamicSharedSizeBytes < smem_bytes)
-        CP_CUDA(cudaFuncSetAttribute(k_eval<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_bytes));
-    return CP_OK;
+    int rc;
+    if ((rc = raise_smem(k_eval<12, false>, smem_bytes)) != CP_OK) return rc;
+    if ((rc = raise_smem(k_eval<16, false>, smem_bytes)) != CP_OK) return rc;
+    if ((rc = raise_smem(k_eval<12, true>, smem_bytes)) != CP_OK) return rc;
+    return raise_smem(k_eval<16, true>, smem_bytes);
 }
 
 int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
@@ -317,10 +412,17 @@ int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int nu
     const int units = a.n * a.chunks;
     if (units == 0) return CP_OK;
     const size_t smem = eval_smem_bytes(sc.n_cyl, sc.n_box, a.S);
+    const int cpsm = a.ctas_per_sm;
     if (m.n_spheres == 12) {
-        k_eval<12><<<eval_grid<12>(smem, num_sms, units, a.ctas_per_sm), kEvalThreads, smem, st>>>(m, sc, a);
+        if (a.broadphase)
+            k_eval<12, true><<<eval_grid<12, true>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
+        else
+            k_eval<12, false><<<eval_grid<12, false>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
     } else {
-        k_eval<16><<<eval_grid<16>(smem, num_sms, units, a.ctas_per_sm), kEvalThreads, smem, st>>>(m, sc, a);
+        if (a.broadphase)
+            k_eval<16, true><<<eval_grid<16, true>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
+        else
+            k_eval<16, false><<<eval_grid<16, false>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
     }
     CP_LAUNCHED("k_eval");
     return CP_OK;

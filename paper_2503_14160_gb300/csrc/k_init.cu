@@ -16,13 +16,18 @@ __global__ void k_prepare_scene(const cp_cylinder *__restrict__ cyl, int n_cyl,
         const cp_cylinder c = cyl[i];
         const double reach = c.radius + (double)r_max;
         const double W = c.cx * c.cx + c.cy * c.cy - reach * reach;
-        cyl_filt[i] = make_float4((float)c.cx, (float)c.cy, (float)W, 0.f);
+        // w: broad-phase reach, the filter's bound sqrt(reach^2 + margin) with slack
+        const double cull = sqrt(reach * reach + 0.01) + 0.01;
+        cyl_filt[i] = make_float4((float)c.cx, (float)c.cy, (float)W, (float)cull);
         cyl_exact[i] = make_float4((float)c.radius, (float)c.z_lo, (float)c.z_hi, 0.f);
     }
     if (i < n_box) {
         const cp_box b = box[i];
+        // w: broad-phase reach, the half diagonal of the footprint plus a sphere, with slack
+        const double hx = 0.5 * (b.hi[0] - b.lo[0]), hy = 0.5 * (b.hi[1] - b.lo[1]);
+        const double cull = sqrt(hx * hx + hy * hy) + (double)r_max + 0.01;
         box_c[i] = make_float4((float)(0.5 * (b.lo[0] + b.hi[0])), (float)(0.5 * (b.lo[1] + b.hi[1])),
-                               (float)(0.5 * (b.lo[2] + b.hi[2])), 0.f);
+                               (float)(0.5 * (b.lo[2] + b.hi[2])), (float)cull);
         box_h[i] = make_float4((float)(0.5 * (b.hi[0] - b.lo[0])), (float)(0.5 * (b.hi[1] - b.lo[1])),
                                (float)(0.5 * (b.hi[2] - b.lo[2])), 0.f);
     }

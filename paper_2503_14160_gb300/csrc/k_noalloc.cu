@@ -116,6 +116,7 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     a.chunks = chunks;
     a.q0 = make_float4((float)h_q0[0], (float)h_q0[1], (float)h_q0[2], (float)h_q0[3]);
     a.qd = make_float4((float)h_qd[0], (float)h_qd[1], (float)h_qd[2], (float)h_qd[3]);
+    a.broadphase = 1;
     a.basis = basis;
     a.partial = (float4 *)(base + o_partial);
     a.flagword = (uint32_t *)(base + o_words);

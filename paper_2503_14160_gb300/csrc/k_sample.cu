@@ -1,5 +1,5 @@
 // Algorithm 1 step (1): xi_i ~ N(mu, sigma^2 C) (arXiv 2503.14160, Sec. 4.1).
-//   k_factor  L L^T = sigma^2 C, FP64 right-looking Cholesky in one CTA (D <= 128)
+//   k_factor  L L^T = sigma^2 C, FP64 right-looking Cholesky (L D L^T form) in one CTA, D <= 128
 //   k_sample  z_i from Philox4x32-10 (Salmon et al., SC'11) + Box-Muller, xi_i = mu + L z_i
 // The counter of candidate i, block j, iteration t, query q is (j, i, t, q); the key is
 // the 64-bit seed split into two words. Block j gives the normals z[4j..4j+3].
@@ -44,39 +44,65 @@ __global__ void k_philox(const uint4 *__restrict__ ctr, uint32_t k0, uint32_t k1
 }
 
 constexpr int kFactorThreads = 1024;
+constexpr int kFactorMaxD = 4 * CP_MAX_WAYPOINTS;
 
-// 1/sqrt(a) for a > 0: a float seed refined by two Newton-Raphson steps
-// y <- y (3 - a y^2) / 2 in FP64 (quadratic convergence: 24 -> 48 -> 96 bits). On a part
-// with a narrow FP64 pipe this short chain is much faster than a library square root and
-// division on the critical path of every column.
+// 1/a and 1/sqrt(a) for a > 0: a float seed refined by two Newton-Raphson steps in FP64
+// (quadratic convergence: 23 -> 46 -> 92 bits). On a part with a narrow FP64 pipe these
+// short chains are much faster than a library division or square root. Arguments whose
+// float conversion is not a normal number take the IEEE operations instead.
+__device__ __forceinline__ double recip_newton(double a)
+{
+    const float af = (float)a;
+    if (!(af > 1e-30f && af < 1e30f)) return 1.0 / a;
+    double y = (double)__frcp_rn(af);
+    y = fma(y, fma(-a, y, 1.0), y);
+    y = fma(y, fma(-a, y, 1.0), y);
+    return y;
+}
+
 __device__ __forceinline__ double rsqrt_newton(double a)
 {
-    double y = (double)rsqrtf((float)a);
+    const float af = (float)a;
+    if (!(af > 1e-30f && af < 1e30f)) return 1.0 / sqrt(a);
+    double y = (double)rsqrtf(af);
     const double h = 0.5 * a;
     y = y * fma(-h * y, y, 1.5);
     y = y * fma(-h * y, y, 1.5);
     return y;
 }
 
-// One CTA, right-looking Cholesky of A = sigma^2 C in shared memory (row stride D + 1).
-// Column k: with inv = 1/sqrt(a_kk), every trailing entry k < j <= i takes
-// a_ij -= a_ik a_jk inv^2, and the thread that updates a_{k+1,k+1} also computes the next
-// pivot's inv into the other slot of a double buffer, so one barrier per column suffices.
-// Column k of L is l_ik = a_ik inv. Outputs L (double, row-major, upper part zero) and its
-// FP32 transpose Lt[c][r] = L[r][c] for the sampler. A pivot that is not positive raises
+// (ii, jj), 0 <= jj <= ii, of the e-th entry of a lower triangle stored row by row.
+__device__ __forceinline__ void tri_index(int e, int &ii, int &jj)
+{
+    int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    if ((r + 1) * (r + 2) / 2 <= e) ++r;
+    if (r * (r + 1) / 2 > e) --r;
+    ii = r;
+    jj = e - r * (r + 1) / 2;
+}
+
+// One CTA, right-looking Cholesky of A = sigma^2 C in shared memory (row stride D + 1) in
+// the unscaled (L D L^T) form: step k takes t_i = a_ik / a_kk for the rows below the pivot,
+// then a_ij -= t_i a_jk over the trailing lower triangle, one FMA per entry and every lane
+// busy. The thread that updates a_{k+1,k+1} also forms the next pivot's reciprocal (double
+// buffered), so the pivot chain is one FMA and a short Newton chain per column. At the end
+// column k holds a_ik = l_ik sqrt(a_kk), so l_ik = a_ik / sqrt(a_kk) with the D square
+// roots taken together. Outputs L (double, row-major, upper part zero) and its FP32
+// transpose Lt[c][r] = L[r][c] for the sampler. A pivot that is not positive raises
 // DEV_ERR_NOT_PD (and is replaced by 1 so that the kernel finishes).
 __global__ void __launch_bounds__(kFactorThreads)
 k_factor(const double *__restrict__ C, double sigma2, int D, double *L, float *Lt,
          uint32_t *status)
 {
     extern __shared__ double A[];
-    __shared__ double s_inv[2];
+    __shared__ double s_d[2];
+    __shared__ double s_t[kFactorMaxD];
     __shared__ int bad;
     const int ld = D + 1;
     const int tid = threadIdx.x;
     for (int idx = tid; idx < D * D; idx += blockDim.x) {
         const int r = idx / D, c = idx - r * D;
-        A[r * ld + c] = sigma2 * C[idx];
+        if (c <= r) A[r * ld + c] = sigma2 * C[idx];
     }
     __syncthreads();
     if (tid == 0) {
@@ -87,41 +113,38 @@ k_factor(const double *__restrict__ C, double sigma2, int D, double *L, float *L
             a = 1.0;
             A[0] = a;
         }
-        s_inv[0] = rsqrt_newton(a);
+        s_d[0] = recip_newton(a);
     }
     __syncthreads();
-    for (int k = 0; k < D; ++k) {
-        const double inv = s_inv[k & 1];
-        const double inv2 = inv * inv;
+    for (int k = 0; k + 1 < D; ++k) {
         const int T = D - k - 1;
-        for (int idx = tid; idx < T * T; idx += blockDim.x) {
-            const int ii = idx / T, jj = idx - ii * T;
-            if (jj <= ii) {
-                const int i = k + 1 + ii, j = k + 1 + jj;
-                double v = A[i * ld + j] - A[i * ld + k] * A[j * ld + k] * inv2;
-                if (ii == 0) {   // the next pivot
-                    if (!(v > 0.0)) {
-                        bad = 1;
-                        v = 1.0;
-                    }
-                    s_inv[(k + 1) & 1] = rsqrt_newton(v);
+        const double d = s_d[k & 1];
+        for (int i = tid; i < T; i += blockDim.x) s_t[i] = A[(k + 1 + i) * ld + k] * d;
+        __syncthreads();
+        const int E = T * (T + 1) / 2;
+        for (int e = tid; e < E; e += blockDim.x) {
+            int ii, jj;
+            tri_index(e, ii, jj);
+            const int i = k + 1 + ii, j = k + 1 + jj;
+            double v = fma(-s_t[ii], A[j * ld + k], A[i * ld + j]);
+            if (e == 0) {   // the next pivot
+                if (!(v > 0.0)) {
+                    bad = 1;
+                    v = 1.0;
                 }
-                A[i * ld + j] = v;
+                s_d[(k + 1) & 1] = recip_newton(v);
             }
+            A[i * ld + j] = v;
         }
         __syncthreads();
-        for (int i = k + tid; i < D; i += blockDim.x) {
-            const double l = A[i * ld + k] * inv;
-            L[i * D + k] = l;
-            Lt[k * D + i] = (float)l;
-        }
     }
+    for (int k = tid; k < D; k += blockDim.x) s_t[k] = rsqrt_newton(A[k * ld + k]);
+    __syncthreads();
     for (int idx = tid; idx < D * D; idx += blockDim.x) {
         const int r = idx / D, c = idx - r * D;
-        if (c > r) {
-            L[idx] = 0.0;
-            Lt[c * D + r] = 0.f;
-        }
+        const double l = c <= r ? A[r * ld + c] * s_t[c] : 0.0;
+        L[idx] = l;
+        Lt[c * D + r] = (float)l;
     }
     __syncthreads();
     if (tid == 0 && bad) atomicOr(status, DEV_ERR_NOT_PD);

@@ -187,6 +187,74 @@ def test_evaluate_grid_dense_forest_full_size(lib, crane):
         s.close()
 
 
+@pytest.mark.parametrize("name,n_cyl,K,S,n,spread", [
+    ("single_small", None, 8, 32, 256, (0.6, 0.3, 0.4, 0.5)),
+    ("single_large", None, 16, 64, 512, (0.6, 0.3, 0.4, 0.5)),
+    ("single_large", None, 5, 7, 45, (3.0, 1.0, 1.5, 2.0)),     # far outside the limits
+    ("dense_forest", 300, 4, 16, 64, (0.6, 0.3, 0.4, 0.5)),     # cylinders and boxes
+    ("dense_forest", None, 6, 16, 40, (0.6, 0.3, 0.4, 0.5)),    # 5000 cylinders, no grid
+])
+def test_broadphase_matches_exhaustive_bitwise(lib, crane, name, n_cyl, K, S, n, spread):
+    """The broad phase only drops obstacles that no sphere of the 32 checkpoints can reach,
+    so the default evaluation and the exhaustive one (every sphere against every obstacle)
+    give the same penalties, flags, terms and costs bit for bit."""
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints(name)
+    scene = _scene(name, n_cyl=n_cyl)
+    xi = workloads.random_candidates(q0, qd, K, n, seed=K * 7 + n, spread=spread)
+    out = []
+    for exhaustive in (0, 1):
+        s = Setup(crane, scene, N=n, K=K, S=S, exhaustive=exhaustive)
+        try:
+            out.append(s.evaluate(xi, q0, qd))
+        finally:
+            s.close()
+    for key in ("J", "flag", "terms", "words", "pen"):
+        np.testing.assert_array_equal(out[0][key], out[1][key], err_msg=key)
+    assert out[0]["flag"].any()
+
+
+def test_work_counters(lib, crane):
+    """While timing is on the planner reports the evaluation work: units, and obstacle
+    tests (every obstacle of every unit when exhaustive, the counted broad-phase survivors
+    otherwise, a small fraction of them on the 500-tree scene)."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("single_large")
+    scene = _scene("single_large")
+    n, K, S = 256, 16, 64
+    xi = torch.from_numpy(workloads.random_candidates(q0, qd, K, n, seed=4)).cuda()
+    J = torch.zeros(n, dtype=torch.float64, device="cuda")
+    chunks = ((K + 3) * S + 31) // 32
+    got = []
+    for exhaustive in (1, 0):
+        s = Setup(crane, scene, N=n, K=K, S=S, exhaustive=exhaustive)
+        try:
+            lib.cp_set_endpoints(s.h, q0, qd)
+            lib.cp_set_timing(s.h, True)
+            lib.cp_evaluate(s.h, xi, n, J)
+            lib.cp_evaluate(s.h, xi, n, J)
+            t = lib.cp_get_timing(s.h)
+            lib.cp_set_timing(s.h, False)
+        finally:
+            s.close()
+        assert t["eval_launches"] == 2 and t["eval_units"] == 2 * n * chunks
+        got.append(t["eval_obstacle_tests"])
+    assert got[0] == 2 * n * chunks * scene.n_cyl
+    assert 0 < got[1] < got[0] // 10
+
+
+def test_exhaustive_matches_oracle(lib, crane):
+    """The exhaustive evaluation against the oracle directly (boxes and cylinders)."""
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("dense_forest")
+    s = Setup(crane, _scene("dense_forest", n_cyl=200), N=48, K=5, S=12, exhaustive=1)
+    try:
+        check_eval(s, workloads.random_candidates(q0, qd, 5, 48, seed=8), q0, qd)
+    finally:
+        s.close()
+
+
 def test_signed_distance(lib, crane):
     """d(q) for configurations inside and beyond the joint limits."""
     import torch
