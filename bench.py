@@ -182,6 +182,24 @@ def select_endpoints_gpu(cp, planner, crane, seed, query):
     return q0, qd, ok
 
 
+def max_over_ranks(values, device):
+    """Each value's maximum over the ranks of the process group (the slowest replica);
+    the values themselves on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(units_per_rank, world_size, ms_slowest):
+    """Whole-job throughput of independent replicas: every rank's units over the slowest
+    rank's time."""
+    return units_per_rank * world_size / (ms_slowest / 1e3)
+
+
 def flush_l2(buf):
     buf.add_(1.0)   # a write of a buffer larger than the 129 MB L2
 
@@ -255,14 +273,9 @@ def run_ours(args):
         e2e_times.append((time.perf_counter() - t0) * 1e3)
     barrier()
 
-    ms = float(np.mean(times))
-    ms_e2e = float(np.mean(e2e_times))
-    if ws > 1:
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    ms, ms_e2e = max_over_ranks([float(np.mean(times)), float(np.mean(e2e_times))], "cuda")
     units = wl.n_candidates * iters * ws
-    value = units / (ms / 1e3)
+    value = job_throughput(wl.n_candidates * iters, ws, ms)
 
     # roofline of the evaluation kernel (FK + collision + cost); per plan the kernel runs
     # T times on N candidates and once on the mean path
