@@ -375,10 +375,8 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
                                  p->st)) != CP_OK)
             return rc;
     }
-    if ((rc = launch_mean(p->elites, p->w, p->nu, p->D, p->mean_part, p->mu, p->st)) != CP_OK)
-        return rc;
-    if ((rc = launch_cov(p->elites, p->w, p->mu, p->nu, p->D, p->prm.eps, p->cov_part, p->C,
-                         p->st)) != CP_OK)
+    if ((rc = launch_moments(p->elites, p->w, p->nu, p->D, p->prm.eps, p->cov_part, p->mean_part,
+                             p->mu, p->C, p->st)) != CP_OK)
         return rc;
     if ((rc = p->timer.end(ST_UPDATE, p->st)) != CP_OK) return rc;
     if ((rc = run_factor(p)) != CP_OK) return rc;

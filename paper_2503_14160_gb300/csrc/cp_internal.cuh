@@ -80,6 +80,17 @@ struct GridDev {
 // rounding error of that form for a pair within reach of the crane is below 3e-4 m^2.
 constexpr float kFilterMargin = 2.0e-3f;
 
+// (ii, jj), 0 <= jj <= ii, of the e-th entry of a lower triangle stored row by row.
+static __device__ __forceinline__ void tri_index(int e, int &ii, int &jj)
+{
+    int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    if ((r + 1) * (r + 2) / 2 <= e) ++r;
+    if (r * (r + 1) / 2 > e) --r;
+    ii = r;
+    jj = e - r * (r + 1) / 2;
+}
+
+
 int validate_model(const cp_model *m);
 ModelDev make_model(const cp_model *m);
 
@@ -96,8 +107,8 @@ struct EvalArgs {
     unsigned long long *work;   // optional: += obstacle tests that passed the broad phase
     uint32_t *status;           // device status word (DEV_ERR_*) or null
     const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
-    float4 *partial;            // [chunks][n] {J_p, sum pen, J_l, length} (float)
-    uint32_t *flagword;         // [chunks][n]
+    float4 *partial;            // [n][chunks] {J_p, sum pen, J_l, length} (float)
+    uint32_t *flagword;         // [n][chunks]
     float *pen_out;             // optional [n][n_s]
 };
 
@@ -150,10 +161,8 @@ int launch_weights(int nu, double *w, cudaStream_t st);
 int launch_rank(const double *J, int N, int nu, int *rank, cudaStream_t st);
 int launch_scatter(const int *rank, const double *J, const float *xi, int N, int nu, int D,
                    int *elite, float *elites, double *best_J, cudaStream_t st);
-int launch_mean(const float *elites, const double *w, int nu, int D, double *partial,
-                double *mu, cudaStream_t st);
-int launch_cov(const float *elites, const double *w, const double *mu, int nu, int D,
-               double eps, double *partial, double *C, cudaStream_t st);
+int launch_moments(const float *elites, const double *w, int nu, int D, double eps,
+                   double *s2p, double *s1p, double *mu, double *C, cudaStream_t st);
 int update_chunks(int nu);
 int radix_tiles(int N);
 int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,

@@ -151,7 +151,7 @@ static __device__ __forceinline__ Checkpoint checkpoint_setup(const ModelDev &m,
 }
 
 // Warp-shuffle sums (FP32) of the unit's lanes and the ballot of collision flags, written
-// chunk-major by lane 0; the per-checkpoint penalty goes to pen_out when asked.
+// by lane 0 ([candidate][chunk]); the per-checkpoint penalty goes to pen_out when asked.
 static __device__ __forceinline__ void unit_epilogue(const EvalArgs &a, const Checkpoint &c, float dmin,
                                                      int cand, int chunk, int lane)
 {
@@ -167,9 +167,9 @@ static __device__ __forceinline__ void unit_epilogue(const EvalArgs &a, const Ch
         v3 += __shfl_xor_sync(0xffffffffu, v3, off);
     }
     const uint32_t word = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) {   // chunk-major, so the finalize reads coalesce
-        a.partial[(size_t)chunk * a.n + cand] = make_float4(v0, v1, v2, v3);
-        a.flagword[(size_t)chunk * a.n + cand] = word;
+    if (lane == 0) {   // candidate-major: the finalize warp of a candidate reads its row
+        a.partial[(size_t)cand * a.chunks + chunk] = make_float4(v0, v1, v2, v3);
+        a.flagword[(size_t)cand * a.chunks + chunk] = word;
     }
     if (a.pen_out != nullptr && c.valid) a.pen_out[(size_t)cand * a.n_s + (c.k - 1)] = pen;
 }

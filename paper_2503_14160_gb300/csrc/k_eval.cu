@@ -305,8 +305,8 @@ __global__ void k_eval_finalize(const float4 *__restrict__ partial,
     double jp = 0.0, jc = 0.0, jl = 0.0, len = 0.0;
     int n_flagged = 0;
     for (int c = lane; c < chunks; c += 32) {
-        const float4 v = partial[(size_t)c * n + i];
-        const uint32_t w = flagword[(size_t)c * n + i];
+        const float4 v = partial[(size_t)i * chunks + c];
+        const uint32_t w = flagword[(size_t)i * chunks + c];
         jp += (double)v.x;
         jc += (double)v.y;
         jl += (double)v.z;

@@ -71,22 +71,14 @@ __device__ __forceinline__ double rsqrt_newton(double a)
     return y;
 }
 
-// (ii, jj), 0 <= jj <= ii, of the e-th entry of a lower triangle stored row by row.
-__device__ __forceinline__ void tri_index(int e, int &ii, int &jj)
-{
-    int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-    if ((r + 1) * (r + 2) / 2 <= e) ++r;
-    if (r * (r + 1) / 2 > e) --r;
-    ii = r;
-    jj = e - r * (r + 1) / 2;
-}
-
 // One CTA, right-looking Cholesky of A = sigma^2 C in shared memory (row stride D + 1) in
 // the unscaled (L D L^T) form: step k takes t_i = a_ik / a_kk for the rows below the pivot,
 // then a_ij -= t_i a_jk over the trailing lower triangle, one FMA per entry and every lane
-// busy. The thread that updates a_{k+1,k+1} also forms the next pivot's reciprocal (double
-// buffered), so the pivot chain is one FMA and a short Newton chain per column. At the end
-// column k holds a_ik = l_ik sqrt(a_kk), so l_ik = a_ik / sqrt(a_kk) with the D square
+// busy. The next pivot's reciprocal is the critical chain of every column; the FP64 pipe is
+// narrow, so that chain runs alone on one scheduler: warps are dealt to the SM's four
+// schedulers round robin, warp 0 computes a_{k+1,k+1} and its reciprocal (double
+// buffered), and the bulk update runs on the warps of the other three schedulers. At the
+// end column k holds a_ik = l_ik sqrt(a_kk), so l_ik = a_ik / sqrt(a_kk) with the D square
 // roots taken together. Outputs L (double, row-major, upper part zero) and its FP32
 // transpose Lt[c][r] = L[r][c] for the sampler. A pivot that is not positive raises
 // DEV_ERR_NOT_PD (and is replaced by 1 so that the kernel finishes).
@@ -100,6 +92,10 @@ k_factor(const double *__restrict__ C, double sigma2, int D, double *L, float *L
     __shared__ int bad;
     const int ld = D + 1;
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const bool worker = (warp & 3) != 0;
+    const int wtid = ((warp >> 2) * 3 + (warp & 3) - 1) * 32 + lane;   // 0 .. 3/4 blockDim - 1
+    const int wcount = (int)blockDim.x / 4 * 3;
     for (int idx = tid; idx < D * D; idx += blockDim.x) {
         const int r = idx / D, c = idx - r * D;
         if (c <= r) A[r * ld + c] = sigma2 * C[idx];
@@ -119,22 +115,26 @@ k_factor(const double *__restrict__ C, double sigma2, int D, double *L, float *L
     for (int k = 0; k + 1 < D; ++k) {
         const int T = D - k - 1;
         const double d = s_d[k & 1];
-        for (int i = tid; i < T; i += blockDim.x) s_t[i] = A[(k + 1 + i) * ld + k] * d;
+        if (worker)
+            for (int i = wtid; i < T; i += wcount) s_t[i] = A[(k + 1 + i) * ld + k] * d;
         __syncthreads();
-        const int E = T * (T + 1) / 2;
-        for (int e = tid; e < E; e += blockDim.x) {
-            int ii, jj;
-            tri_index(e, ii, jj);
-            const int i = k + 1 + ii, j = k + 1 + jj;
-            double v = fma(-s_t[ii], A[j * ld + k], A[i * ld + j]);
-            if (e == 0) {   // the next pivot
-                if (!(v > 0.0)) {
-                    bad = 1;
-                    v = 1.0;
-                }
-                s_d[(k + 1) & 1] = recip_newton(v);
+        if (worker) {
+            const int E = T * (T + 1) / 2;
+            for (int e = wtid + 1; e < E; e += wcount) {   // entry 0 is the pivot
+                int ii, jj;
+                tri_index(e, ii, jj);
+                const int i = k + 1 + ii, j = k + 1 + jj;
+                A[i * ld + j] = fma(-s_t[ii], A[j * ld + k], A[i * ld + j]);
             }
-            A[i * ld + j] = v;
+        } else if (tid == 0) {
+            const int i = k + 1;
+            double v = fma(-(A[i * ld + k] * d), A[i * ld + k], A[i * ld + i]);
+            if (!(v > 0.0)) {
+                bad = 1;
+                v = 1.0;
+            }
+            A[i * ld + i] = v;
+            s_d[(k + 1) & 1] = recip_newton(v);
         }
         __syncthreads();
     }

@@ -5,10 +5,10 @@
 //                    over the grid's y dimension and summed with integer atomics
 //   k_scatter        elite list in rank order, the elite rows gathered contiguously
 //   k_radix_*        for large N instead: a stable LSD radix sort of the keys (8 x 8 bits)
-//   k_mean_partial / k_mean_combine   mu = sum_j w_j xi_(j), FP64, fixed order
-//   k_cov_partial / k_cov_combine     C = sum_j w_j (xi_(j) - mu)(xi_(j) - mu)^T + eps I,
-//                    FP64, about the new mean, 16x16 output tiles x chunks of elites,
-//                    chunk partials summed in chunk order (deterministic)
+//   k_moments_partial / k_moments_combine   mu = sum_j w_j xi_(j) and
+//                    C = sum_j w_j (xi_(j) - mu)(xi_(j) - mu)^T + eps I (about the new
+//                    mean) in one FP64 pass about the best elite, 16x16 output tiles x
+//                    chunks of elites, chunk partials summed in a fixed order (deterministic)
 #include "cp_internal.cuh"
 
 namespace cp {
@@ -85,62 +85,23 @@ __global__ void k_scatter(const int *__restrict__ rank, const double *__restrict
     for (int c = lane; c < D; c += 32) elites[(size_t)r * D + c] = xi[(size_t)warp * D + c];
 }
 
-// Chunk p (elites [p per, (p+1) per)): partial[p][c] = sum_j w_j elites[j][c], staged
-// kChunk rows at a time in shared memory with coalesced loads; thread c sums in elite order.
-__global__ void __launch_bounds__(128)
-k_mean_partial(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D,
-               int per, double *partial)
-{
-    __shared__ float s_rows[kChunk * 4 * CP_MAX_WAYPOINTS];
-    const int p = blockIdx.x, c = threadIdx.x;
-    const int j_end = min(nu, (p + 1) * per);
-    double acc = 0.0;
-    for (int j0 = p * per; j0 < j_end; j0 += kChunk) {
-        const int cnt = min(j_end - j0, kChunk);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < cnt * D; idx += blockDim.x)
-            s_rows[idx] = elites[(size_t)j0 * D + idx];
-        __syncthreads();
-        if (c < D)
-            for (int j = 0; j < cnt; ++j) acc += w[j0 + j] * (double)s_rows[j * D + c];
-    }
-    if (c < D) partial[(size_t)p * D + c] = acc;
-}
-
-// Fixed-order sum of n partials with eight loads in flight (the grouping is fixed, so the
-// result does not depend on scheduling).
-__device__ __forceinline__ double sum_partials(const double *__restrict__ p, size_t stride, int n)
-{
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int q = 0;
-    for (; q + 8 <= n; q += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] += p[(size_t)(q + u) * stride];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-        if (q + u < n) a[u] += p[(size_t)(q + u) * stride];
-    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-}
-
-__global__ void k_mean_combine(const double *__restrict__ partial, int n_chunks, int D, double *mu)
-{
-    const int c = threadIdx.x;
-    if (c >= D) return;
-    mu[c] = sum_partials(partial + c, (size_t)D, n_chunks);
-}
-
-// Block (tile t of the lower triangle of 16x16 tiles, chunk p): one output per thread.
-// The chunk's deviations y_j = xi_(j) - mu are staged kChunk elites at a time, the tile's
-// rows scaled by w_j, so each term costs one FP64 FMA.
+// Steps (5)-(6) in one pass over the elites, about the best elite m0 = xi_(1): with
+// y_j = xi_(j) - m0 (exact in FP64 for the FP32 rows), S1 = sum_j w_j y_j and
+// S2 = sum_j w_j y_j y_j^T give mu = m0 + S1 and, since the weights sum to one,
+// C = sum_j w_j (xi_(j) - mu)(xi_(j) - mu)^T + eps I = S2 - S1 S1^T + eps I. The best elite
+// lies within the spread of the elites, so S1 S1^T is of the size of C and the subtraction
+// loses no more than a few FP64 roundings.
+//
+// Block (tile t of the lower triangle of 16x16 tiles, chunk p of kChunk-row groups): one
+// S2 entry per thread, and S1 of the tile's rows on diagonal tiles. Partials are stored
+// entry-major ([entry][chunk]) so that the combine reads them with coalesced loads.
 __global__ void __launch_bounds__(256)
-k_cov_partial(const float *__restrict__ elites, const double *__restrict__ w,
-              const double *__restrict__ mu, int nu, int D, int per, double *partial)
+k_moments_partial(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D,
+                  int per, int n_chunks, double *s2p, double *s1p)
 {
     __shared__ double wyr[kChunk][17];
     __shared__ double yc[kChunk][17];
-    // tile index -> (tile row tr >= tile col tc)
-    int t = blockIdx.x, tr = 0;
+    int t = blockIdx.x, tr = 0;   // tile index -> (tile row tr >= tile col tc)
     while (t > tr) {
         t -= tr + 1;
         ++tr;
@@ -148,35 +109,62 @@ k_cov_partial(const float *__restrict__ elites, const double *__restrict__ w,
     const int tc = t;
     const int p = blockIdx.y;
     const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+    const bool diag = tr == tc;
     const int j_end = min(nu, (p + 1) * per);
-    double acc = 0.0;
+    double acc = 0.0, acc1 = 0.0;
     for (int j0 = p * per; j0 < j_end; j0 += kChunk) {
         const int cnt = min(j_end - j0, kChunk);
         __syncthreads();
         for (int idx = threadIdx.x; idx < cnt * 16; idx += blockDim.x) {
             const int j = idx >> 4, k = idx & 15;
             const int r = tr * 16 + k, c = tc * 16 + k;
-            const double wj = w[j0 + j];
-            wyr[j][k] = r < D ? wj * ((double)elites[(size_t)(j0 + j) * D + r] - mu[r]) : 0.0;
-            yc[j][k] = c < D ? (double)elites[(size_t)(j0 + j) * D + c] - mu[c] : 0.0;
+            const float *row = elites + (size_t)(j0 + j) * D;
+            wyr[j][k] = r < D ? w[j0 + j] * ((double)row[r] - (double)elites[r]) : 0.0;
+            yc[j][k] = c < D ? (double)row[c] - (double)elites[c] : 0.0;
         }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) acc = fma(wyr[j][a], yc[j][b], acc);
+        if (diag && b == 0)
+            for (int j = 0; j < cnt; ++j) acc1 += wyr[j][a];
     }
     const int r = tr * 16 + a, c = tc * 16 + b;
-    if (r < D && c < D) partial[((size_t)p * D + r) * D + c] = acc;
+    if (r < D && c <= r) s2p[((size_t)r * D + c) * n_chunks + p] = acc;
+    if (diag && b == 0 && r < D) s1p[(size_t)r * n_chunks + p] = acc1;
 }
 
-__global__ void k_cov_combine(const double *__restrict__ partial, int n_chunks, int D, double eps,
-                              double *C)
+// Sum of n values at stride 1, lane-strided and then by a fixed shuffle tree (every lane
+// gets the same result; the order does not depend on scheduling).
+__device__ __forceinline__ double warp_sum(const double *__restrict__ v, int n, int lane)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= D * D) return;
-    int r = idx / D, c = idx - r * D;
-    const int lr = r >= c ? r : c, lc = r >= c ? c : r;     // lower-triangle source
-    double acc = sum_partials(partial + (size_t)lr * D + lc, (size_t)D * D, n_chunks);
-    if (r == c) acc += eps;
-    C[idx] = acc;
+    double s = 0.0;
+    for (int q = lane; q < n; q += 32) s += v[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+}
+
+// One warp per lower-triangle entry (r >= c): C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c];
+// on the diagonal also mu_r = m0_r + S1_r.
+__global__ void k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1p,
+                                  int n_chunks, int D, double eps, const float *__restrict__ elites,
+                                  double *mu, double *C)
+{
+    const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= D * (D + 1) / 2) return;
+    int r, c;
+    tri_index(e, r, c);
+    const double s2 = warp_sum(s2p + ((size_t)r * D + c) * n_chunks, n_chunks, lane);
+    const double sr = warp_sum(s1p + (size_t)r * n_chunks, n_chunks, lane);
+    const double sc = warp_sum(s1p + (size_t)c * n_chunks, n_chunks, lane);
+    if (lane != 0) return;
+    double v = fma(-sr, sc, s2);
+    if (r == c) {
+        v += eps;
+        mu[r] = (double)elites[r] + sr;
+    }
+    C[(size_t)r * D + c] = v;
+    C[(size_t)c * D + r] = v;
 }
 
 // ---------------------------------------------------------------- LSD radix sort (large N)
@@ -376,29 +364,19 @@ int launch_scatter(const int *rank, const double *J, const float *xi, int N, int
     return CP_OK;
 }
 
-int launch_mean(const float *elites, const double *w, int nu, int D, double *partial,
-                double *mu, cudaStream_t st)
-{
-    const int per = per_chunk(nu);
-    const int n_chunks = (nu + per - 1) / per;
-    k_mean_partial<<<n_chunks, 128, 0, st>>>(elites, w, nu, D, per, partial);
-    CP_LAUNCHED("k_mean_partial");
-    k_mean_combine<<<1, 128, 0, st>>>(partial, n_chunks, D, mu);
-    CP_LAUNCHED("k_mean_combine");
-    return CP_OK;
-}
-
-int launch_cov(const float *elites, const double *w, const double *mu, int nu, int D,
-               double eps, double *partial, double *C, cudaStream_t st)
+int launch_moments(const float *elites, const double *w, int nu, int D, double eps,
+                   double *s2p, double *s1p, double *mu, double *C, cudaStream_t st)
 {
     const int per = per_chunk(nu);
     const int n_chunks = (nu + per - 1) / per;
     const int tiles = (D + 15) / 16;
     dim3 grid(tiles * (tiles + 1) / 2, n_chunks);
-    k_cov_partial<<<grid, 256, 0, st>>>(elites, w, mu, nu, D, per, partial);
-    CP_LAUNCHED("k_cov_partial");
-    k_cov_combine<<<(D * D + 255) / 256, 256, 0, st>>>(partial, n_chunks, D, eps, C);
-    CP_LAUNCHED("k_cov_combine");
+    k_moments_partial<<<grid, 256, 0, st>>>(elites, w, nu, D, per, n_chunks, s2p, s1p);
+    CP_LAUNCHED("k_moments_partial");
+    const int entries = D * (D + 1) / 2;
+    k_moments_combine<<<(entries * 32 + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, eps, elites,
+                                                                  mu, C);
+    CP_LAUNCHED("k_moments_combine");
     return CP_OK;
 }
 
