@@ -28,28 +28,38 @@ static __device__ __forceinline__ float sdf_box(float x, float y, float z, float
     return sqrtf(fmaf(px, px, fmaf(py, py, pz * pz))) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
 }
 
-// Sphere centres at configuration q (chain of Sec. 2 in the linear placement form).
+// Sphere centres at configuration q (chain of Sec. 2 in the linear placement form), in
+// polar form: every centre is (c1 h, s1 h, z) with (c1, s1) the cosine and sine of the slew
+// angle and h the signed horizontal distance from the slew axis.
 template <int NSPH>
-static __device__ __forceinline__ void crane_fk(const ModelDev &m, float4 q, float *x, float *y,
-                                         float *z, float *sin_slew = nullptr,
-                                         float *cos_slew = nullptr)
+static __device__ __forceinline__ void crane_fk_polar(const ModelDev &m, float4 q, float *h, float *z,
+                                               float &s1, float &c1)
 {
-    float s1, c1, s2, c2, s23, c23;
+    float s2, c2, s23, c23;
     sincosf(q.x, &s1, &c1);
-    if (sin_slew != nullptr) {
-        *sin_slew = s1;
-        *cos_slew = c1;
-    }
     sincosf(q.y, &s2, &c2);
     sincosf(q.y + q.z, &s23, &c23);
 #pragma unroll
     for (int s = 0; s < NSPH; ++s) {
         const SphereLin sp = m.sph[s];
         const float b = fmaf(sp.gamma, q.w, sp.beta);
-        const float h = fmaf(sp.alpha, c2, b * c23);
-        x[s] = c1 * h;
-        y[s] = s1 * h;
+        h[s] = fmaf(sp.alpha, c2, b * c23);
         z[s] = m.base_z + fmaf(sp.alpha, s2, fmaf(b, s23, -sp.delta));
+    }
+}
+
+// The same centres in Cartesian form, x = c1 h and y = s1 h.
+template <int NSPH>
+static __device__ __forceinline__ void crane_fk(const ModelDev &m, float4 q, float *x, float *y,
+                                         float *z)
+{
+    float s1, c1;
+    crane_fk_polar<NSPH>(m, q, x, z, s1, c1);
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s) {
+        const float h = x[s];
+        x[s] = __fmul_rn(c1, h);   // rounded products: the broad-phase form takes the same
+        y[s] = __fmul_rn(s1, h);
     }
 }
 

@@ -21,6 +21,10 @@ constexpr int kEvalThreads = 256;
 #define CP_EVAL_MIN_BLOCKS 3   // CTAs of 8 warps resident per SM (3: at most 85 registers)
 #endif
 constexpr int kEvalMinBlocks = CP_EVAL_MIN_BLOCKS;
+#ifndef CP_EVAL_BROAD_MIN_BLOCKS
+#define CP_EVAL_BROAD_MIN_BLOCKS 4   // broad-phase form: at most 64 registers
+#endif
+constexpr int kEvalBroadMinBlocks = CP_EVAL_BROAD_MIN_BLOCKS;
 constexpr int kObstaclesPerBranch = 2;   // obstacles tested between two branches
 constexpr long long kStagingWaitCycles = 2000000000ll;   // about one second at 2 GHz
 
@@ -105,14 +109,14 @@ __device__ __forceinline__ float exact_cylinders(const ModelDev &m, const float 
     return d;
 }
 
-// Broad phase of one work unit (32 checkpoints of one candidate): the unit's sphere
-// centres are bounded by a box in a frame turned to the slew angle of lane 16, taken as
-// the sine and cosine its kinematics computed (any near-unit vector would do; the same one
-// maps spheres and obstacles). All spheres of one configuration lie on the vertical plane at
-// its slew angle, so the box is long and thin. An obstacle whose centre lies farther than
-// its reach (the `w` of its record) from that box cannot pass the per-sphere filter for any
-// lane; the reach carries 1 cm of slack over the filter's own bound, far above the FP32
-// rounding of either test.
+// Broad phase of one work unit (32 checkpoints of one candidate). All spheres of one
+// configuration lie on the vertical plane at its slew angle, at signed horizontal distances
+// h from the slew axis. The unit's centres are bounded by a box in a frame turned to the
+// slew angle of lane 16: a sphere at h on the plane at angle phi has frame coordinates
+// h (cos, sin)(phi - phi_16), so the box follows from each lane's smallest and largest h.
+// An obstacle whose centre lies farther than its reach (the `w` of its record) from that
+// box cannot pass the per-sphere filter for any lane; the reach carries 1 cm of slack over
+// the filter's own bound, far above the FP32 rounding of either test.
 struct UnitFrame {
     float c0, s0;     // frame axes
     float uc, uh;     // box centre and half extent along the slew direction
@@ -120,22 +124,20 @@ struct UnitFrame {
 };
 
 template <int NSPH>
-__device__ __forceinline__ UnitFrame unit_frame(float sin_slew, float cos_slew, const float *X,
-                                                const float *Y)
+__device__ __forceinline__ UnitFrame unit_frame(float s1, float c1, const float *H)
 {
     UnitFrame f;
-    f.s0 = __shfl_sync(0xffffffffu, sin_slew, 16);
-    f.c0 = __shfl_sync(0xffffffffu, cos_slew, 16);
-    float umin = CUDART_INF_F, umax = -CUDART_INF_F, vmin = CUDART_INF_F, vmax = -CUDART_INF_F;
+    f.s0 = __shfl_sync(0xffffffffu, s1, 16);
+    f.c0 = __shfl_sync(0xffffffffu, c1, 16);
+    float hmin = H[0], hmax = H[0];
 #pragma unroll
-    for (int s = 0; s < NSPH; ++s) {
-        const float u = fmaf(f.c0, X[s], f.s0 * Y[s]);
-        const float v = fmaf(f.c0, Y[s], -f.s0 * X[s]);
-        umin = fminf(umin, u);
-        umax = fmaxf(umax, u);
-        vmin = fminf(vmin, v);
-        vmax = fmaxf(vmax, v);
+    for (int s = 1; s < NSPH; ++s) {
+        hmin = fminf(hmin, H[s]);
+        hmax = fmaxf(hmax, H[s]);
     }
+    const float cd = fmaf(f.c0, c1, f.s0 * s1), sd = fmaf(f.c0, s1, -f.s0 * c1);
+    float umin = fminf(hmin * cd, hmax * cd), umax = fmaxf(hmin * cd, hmax * cd);
+    float vmin = fminf(hmin * sd, hmax * sd), vmax = fmaxf(hmin * sd, hmax * sd);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, off));
@@ -158,12 +160,38 @@ __device__ __forceinline__ bool unit_near(const UnitFrame &f, float4 r)
     return (fabsf(u - f.uc) <= f.uh + r.w) & (fabsf(v - f.vc) <= f.vh + r.w);
 }
 
-template <int NSPH, bool CULL>
-__global__ void __launch_bounds__(kEvalThreads, kEvalMinBlocks)
-k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
+// Exact distance of every sphere whose polar filter passes against one cylinder: with the
+// obstacle centre at p along the lane's plane and q across it, sphere s passes when
+// (h_s - p)^2 < (R + r_max)^2 + margin - q^2 = rhs. The distance itself is taken from the
+// Cartesian centre (c1 h, s1 h, z), rounded products (no contraction into the distance's
+// differences), the same values the exhaustive form uses.
+template <int NSPH>
+__device__ __forceinline__ float exact_polar(const ModelDev &m, const float *H, const float *Z,
+                                             float c1, float s1, float p, float rhs, float4 f,
+                                             float4 e)
 {
-    // Shared memory: per cylinder the filter record {cx, cy, W, 0} and the exact record
-    // {R, z_lo, z_hi, 0}; per box its centre and half extent; the spline basis table.
+    float d = CUDART_INF_F;
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s) {
+        const float dh = H[s] - p;
+        if (fmaf(dh, dh, -rhs) < 0.f)
+            d = fminf(d, sdf_cylinder(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], f.x, f.y, e) -
+                             m.sph[s].radius);
+    }
+    return d;
+}
+
+// The evaluation with the broad phase (the default form). Per unit: the checkpoints and
+// the kinematics in polar form, the unit box, then rounds of 32 obstacles: each lane tests
+// one obstacle against the box, and the warp takes the survivors one by one (a uniform
+// loop) through the per-sphere polar filter, two packed FP32x2 operations per sphere pair,
+// and the exact distance where it passes. Boxes take the same broad phase and then the
+// exact distance for every sphere. Its distances are those of the exhaustive form for
+// every pair that can be in contact, so both forms give the same results bit for bit.
+template <int NSPH>
+__global__ void __launch_bounds__(kEvalThreads, kEvalBroadMinBlocks)
+k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
+{
     extern __shared__ __align__(16) float4 smem[];
     float4 *s_filt = smem;
     float4 *s_exact = s_filt + sc.n_cyl;
@@ -178,6 +206,81 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     const int units = a.n * a.chunks;
     uint32_t tested = 0;   // broad-phase survivors of this warp's units
+    const float zero[NSPH] = {};
+
+    for (int u = warp; u < units; u += n_warps) {
+        const int cand = u / a.chunks;
+        const int chunk = u - cand * a.chunks;
+        const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
+        float H[NSPH], Z[NSPH], s1, c1;
+        crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
+        const UnitFrame fr = unit_frame<NSPH>(s1, c1, H);
+        float2 H2[NSPH / 2];
+#pragma unroll
+        for (int q = 0; q < NSPH / 2; ++q) H2[q] = make_float2(H[2 * q], H[2 * q + 1]);
+
+        float dmin = CUDART_INF_F;
+        for (int base = 0; base < sc.n_cyl; base += 32) {
+            const int o = base + lane;
+            uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, s_filt[o]));
+            tested += __popc(mask);
+            while (mask) {
+                const int ob = base + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float4 f = s_filt[ob], e = s_exact[ob];
+                const float p = fmaf(c1, f.x, s1 * f.y);
+                const float q = fmaf(c1, f.y, -(s1 * f.x));
+                const float rhs = fmaf(-q, q, e.w);
+                const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
+                float2 t[NSPH / 2];
+#pragma unroll
+                for (int k = 0; k < NSPH / 2; ++k) {
+                    const float2 dh = __fadd2_rn(H2[k], mp2);
+                    t[k] = __ffma2_rn(dh, dh, mr2);
+                }
+                if (any_below<NSPH>(t, zero))
+                    dmin = fminf(dmin, exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e));
+            }
+        }
+        for (int base = 0; base < sc.n_box; base += 32) {
+            const int o = base + lane;
+            uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_box && unit_near(fr, s_bc[o]));
+            tested += __popc(mask);
+            while (mask) {
+                const int ob = base + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float4 bc = s_bc[ob], bh = s_bh[ob];
+#pragma unroll
+                for (int s = 0; s < NSPH; ++s)
+                    dmin = fminf(dmin, sdf_box(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], bc, bh) -
+                                           m.sph[s].radius);
+            }
+        }
+        unit_epilogue(a, c, dmin, cand, chunk, lane);
+    }
+    if (a.work != nullptr && lane == 0 && tested != 0) atomicAdd(a.work, (unsigned long long)tested);
+}
+
+// The exhaustive evaluation: every sphere against every obstacle.
+template <int NSPH>
+__global__ void __launch_bounds__(kEvalThreads, kEvalMinBlocks)
+k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
+{
+    // Shared memory: per cylinder the filter record {cx, cy, W, reach} and the exact record
+    // {R, z_lo, z_hi, bound}; per box its centre and half extent; the spline basis table.
+    extern __shared__ __align__(16) float4 smem[];
+    float4 *s_filt = smem;
+    float4 *s_exact = s_filt + sc.n_cyl;
+    float4 *s_bc = s_exact + sc.n_cyl;
+    float4 *s_bh = s_bc + sc.n_box;
+    float4 *s_basis = s_bh + sc.n_box;
+    __shared__ __align__(8) uint64_t staging_bar;
+    if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, sc, a)) return;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int units = a.n * a.chunks;
 
     for (int u = warp; u < units; u += n_warps) {
         const int cand = u / a.chunks;
@@ -187,14 +290,7 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
         // Sphere centres; per sphere the filter threshold T = margin - (x^2 + y^2) and the
         // scaled coordinates (-2x, -2y), kept in pairs for packed FP32x2 FMAs.
         float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH];
-        UnitFrame fr;
-        if constexpr (CULL) {
-            float sin_slew, cos_slew;
-            crane_fk<NSPH>(m, c.q, X, Y, Z, &sin_slew, &cos_slew);
-            fr = unit_frame<NSPH>(sin_slew, cos_slew, X, Y);
-        } else {
-            crane_fk<NSPH>(m, c.q, X, Y, Z);
-        }
+        crane_fk<NSPH>(m, c.q, X, Y, Z);
 #pragma unroll
         for (int s = 0; s < NSPH; ++s) {
             T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
@@ -209,41 +305,6 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
         }
 
         float dmin = CUDART_INF_F;
-        if constexpr (CULL) {
-            // Broad phase: each lane tests one obstacle of 32 against the unit's box; the
-            // warp then runs the per-sphere filter on the survivors only (a uniform loop).
-            for (int base = 0; base < sc.n_cyl; base += 32) {
-                const int o = base + lane;
-                uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, s_filt[o]));
-                tested += __popc(mask);
-                while (mask) {
-                    const int ob = base + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const float4 f = s_filt[ob];
-                    const float2 cx2 = make_float2(f.x, f.x), cy2 = make_float2(f.y, f.y);
-                    const float2 w2 = make_float2(f.z, f.z);
-                    float2 g[NSPH / 2];
-#pragma unroll
-                    for (int p = 0; p < NSPH / 2; ++p) g[p] = __ffma2_rn(X2[p], cx2, __ffma2_rn(Y2[p], cy2, w2));
-                    if (any_below<NSPH>(g, T)) dmin = fminf(dmin, exact_cylinders<NSPH>(m, X, Y, Z, T, f, s_exact[ob]));
-                }
-            }
-            for (int base = 0; base < sc.n_box; base += 32) {
-                const int o = base + lane;
-                uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_box && unit_near(fr, s_bc[o]));
-                tested += __popc(mask);
-                while (mask) {
-                    const int ob = base + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const float4 bc = s_bc[ob], bh = s_bh[ob];
-#pragma unroll
-                    for (int s = 0; s < NSPH; ++s)
-                        dmin = fminf(dmin, sdf_box(-0.5f * X[s], -0.5f * Y[s], Z[s], bc, bh) - m.sph[s].radius);
-                }
-            }
-            unit_epilogue(a, c, dmin, cand, chunk, lane);
-            continue;
-        }
         // Two obstacles per step: 2 x NSPH power tests rho^2 - (R + r_max)^2 < margin in
         // expanded form (-2x cx - 2y cy + W vs. margin - x^2 - y^2), two packed FMAs per
         // sphere pair; the hit predicates accumulate without branches. Only when a test
@@ -289,8 +350,8 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
 
         unit_epilogue(a, c, dmin, cand, chunk, lane);
     }
-    if (CULL && a.work != nullptr && lane == 0 && tested != 0) atomicAdd(a.work, (unsigned long long)tested);
 }
+
 
 // One warp per candidate: lanes take the candidate's chunks (lane, lane + 32, ...), sum
 // them in FP64, and a fixed shuffle tree combines the lanes (deterministic order).
@@ -362,12 +423,11 @@ __global__ void k_signed_distance(const ModelDev m, const SceneDev sc, const flo
     d[i] = dmin;
 }
 
-template <int NSPH, bool CULL>
-int eval_grid(size_t smem, int num_sms, int units, int ctas_per_sm)
+template <typename F>
+int eval_grid(F *kernel, size_t smem, int num_sms, int units, int ctas_per_sm)
 {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<NSPH, CULL>,
-                                                                  kEvalThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kEvalThreads, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const int warps_per_block = kEvalThreads / 32;
@@ -400,10 +460,10 @@ int eval_configure(size_t smem_bytes) { return eval_ensure_smem(smem_bytes); }
 int eval_ensure_smem(size_t smem_bytes)
 {
     int rc;
-    if ((rc = raise_smem(k_eval<12, false>, smem_bytes)) != CP_OK) return rc;
-    if ((rc = raise_smem(k_eval<16, false>, smem_bytes)) != CP_OK) return rc;
-    if ((rc = raise_smem(k_eval<12, true>, smem_bytes)) != CP_OK) return rc;
-    return raise_smem(k_eval<16, true>, smem_bytes);
+    if ((rc = raise_smem(k_eval<12>, smem_bytes)) != CP_OK) return rc;
+    if ((rc = raise_smem(k_eval<16>, smem_bytes)) != CP_OK) return rc;
+    if ((rc = raise_smem(k_eval_broad<12>, smem_bytes)) != CP_OK) return rc;
+    return raise_smem(k_eval_broad<16>, smem_bytes);
 }
 
 int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
@@ -415,14 +475,14 @@ int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int nu
     const int cpsm = a.ctas_per_sm;
     if (m.n_spheres == 12) {
         if (a.broadphase)
-            k_eval<12, true><<<eval_grid<12, true>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
+            k_eval_broad<12><<<eval_grid(k_eval_broad<12>, smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
         else
-            k_eval<12, false><<<eval_grid<12, false>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
+            k_eval<12><<<eval_grid(k_eval<12>, smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
     } else {
         if (a.broadphase)
-            k_eval<16, true><<<eval_grid<16, true>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
+            k_eval_broad<16><<<eval_grid(k_eval_broad<16>, smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
         else
-            k_eval<16, false><<<eval_grid<16, false>(smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
+            k_eval<16><<<eval_grid(k_eval<16>, smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
     }
     CP_LAUNCHED("k_eval");
     return CP_OK;

@@ -19,7 +19,9 @@ __global__ void k_prepare_scene(const cp_cylinder *__restrict__ cyl, int n_cyl,
         // w: broad-phase reach, the filter's bound sqrt(reach^2 + margin) with slack
         const double cull = sqrt(reach * reach + 0.01) + 0.01;
         cyl_filt[i] = make_float4((float)c.cx, (float)c.cy, (float)W, (float)cull);
-        cyl_exact[i] = make_float4((float)c.radius, (float)c.z_lo, (float)c.z_hi, 0.f);
+        // w: (R + r_max)^2 plus the filter margin, the bound of the filter in polar form
+        cyl_exact[i] = make_float4((float)c.radius, (float)c.z_lo, (float)c.z_hi,
+                                   (float)(reach * reach + (double)kFilterMargin));
     }
     if (i < n_box) {
         const cp_box b = box[i];
