@@ -141,14 +141,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-EVAL_SOURCE = os.path.join(ROOT, "paper_2503_14160_gb300", "csrc", "k_eval.cu")
-EVAL_PROFILE = os.path.join(ROOT, "profiles", "k_eval_single_large.md")
+EVAL_SOURCES = [os.path.join(ROOT, "paper_2503_14160_gb300", "csrc", f)
+                for f in ("k_eval.cu", "eval_common.cuh", "cp_internal.cuh")]
+EVAL_PROFILE = os.path.join(ROOT, "profiles", "k_eval_broad_single_large.md")
 
 
 def eval_source_sha1():
+    """SHA-1 over the sources of the evaluation kernel (the key of its committed profile)."""
     import hashlib
-    with open(EVAL_SOURCE, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+    h = hashlib.sha1()
+    for path in EVAL_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def traffic_per_launch():
