@@ -294,6 +294,9 @@ def run_ours(args):
         roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
                                  candidates, not args.exhaustive, clk.get("sm_mhz"))
         roofline["traffic"] = traffic_per_launch()
+        peaks = cp.cp_alu_peaks()
+        roofline["measured_fma_peaks"] = peaks
+        roofline["frac_of_measured_fp32"] = roofline["achieved"] / peaks["fp32_tflops"]
         if not args.exhaustive:
             roofline_exhaustive = exhaustive_roofline(cp, crane, scene, wl, q0, qd,
                                                       clk.get("sm_mhz"))

@@ -169,7 +169,8 @@ const char *cp_last_error(void);
 /* CP_VERSION of the loaded library. */
 int32_t cp_version(void);
 
-/* Number of kernels this library has launched in this process (all planners). */
+/* Number of kernels this library has launched in this process (all planners); a replay of a
+ * batch graph counts the kernels recorded in it. */
 int64_t cp_launch_count(void);
 
 /* Create a planner on the current CUDA device: validates the model, scene and parameters,
@@ -351,6 +352,13 @@ int cp_set_timing(cp_planner *p, int32_t on);
 
 /* Synchronise the planner's stream and return the accumulated stage times. */
 int cp_get_timing(cp_planner *p, cp_timing *out);
+
+/* Measured throughput of the FP32 and the FP64 FMA pipes of the current device (TFLOP/s,
+ * an FMA counted as 2 flops): compute-only kernels of eight independent FMA chains per
+ * thread, eight CTAs of 256 threads per SM, the faster of two timed launches after one
+ * warm-up. The paper has no counterpart; these are the denominators of the reported FP32
+ * and FP64 utilisation. Takes a few milliseconds; allocates and frees a small buffer. */
+int cp_alu_peaks(double *fp32_tflops, double *fp64_tflops);
 
 #ifdef __cplusplus
 }

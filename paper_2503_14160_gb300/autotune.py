@@ -1,8 +1,8 @@
 """Launch-shape autotuner for the evaluation kernel.
 
-For a problem size it times cp_evaluate under each candidate configuration (brute force
-with 1, 2 or 3 CTAs per SM; uniform grid with 0.5 m or 1.0 m cells) on a synthetic
-population and keeps the fastest. Results are cached in a JSON file keyed by device name,
+For a problem size it times cp_evaluate under each candidate configuration (the broad-phase
+form with as many CTAs per SM as fit or with 2; the exhaustive form; the uniform grid with
+0.5 m or 1.0 m cells) on a synthetic population and keeps the fastest. Results are cached in a JSON file keyed by device name,
 K, S and power-of-two buckets of the candidate and cylinder counts, so a batch of uneven
 queries tunes each bucket once.
 """
@@ -17,9 +17,9 @@ from . import craneplan as cp
 from . import workloads
 
 CONFIGS = [
-    {"grid_cell": 0.0, "eval_ctas_per_sm": 3},
+    {"grid_cell": 0.0, "eval_ctas_per_sm": 0},
     {"grid_cell": 0.0, "eval_ctas_per_sm": 2},
-    {"grid_cell": 0.0, "eval_ctas_per_sm": 1},
+    {"grid_cell": 0.0, "eval_ctas_per_sm": 0, "eval_exhaustive": 1},
     {"grid_cell": 0.5, "eval_ctas_per_sm": 0},
     {"grid_cell": 1.0, "eval_ctas_per_sm": 0},
 ]

@@ -133,6 +133,7 @@ _SIGS = {
     "cp_batch_destroy": (None, [_P]),
     "cp_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cp_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(cp_timing)]),
+    "cp_alu_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -394,6 +395,13 @@ def cp_get_timing(p: int) -> dict:
     t = cp_timing()
     _check(load().cp_get_timing(p, ctypes.byref(t)))
     return {f: getattr(t, f) for f, _ in cp_timing._fields_}
+
+
+def cp_alu_peaks() -> dict:
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    _check(load().cp_alu_peaks(ctypes.byref(f32), ctypes.byref(f64)))
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
 
 
 class Planner:

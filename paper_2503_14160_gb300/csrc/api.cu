@@ -878,6 +878,7 @@ struct cp_batch {
     uint32_t *h_status = nullptr; // pinned [nq]
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int64_t kernel_nodes = 0;     // kernels recorded into the graph
 };
 
 namespace {
@@ -988,6 +989,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     if ((e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaStreamBeginCapture"));
     int rc = CP_OK;
+    const int64_t launches_before = g_launches.load();
     e = cudaEventRecord(b->fork, b->origin);
     for (int q = 0; q < nq && e == cudaSuccess && rc == CP_OK; ++q) {
         if ((e = cudaStreamWaitEvent(b->streams[q], b->fork, 0)) != cudaSuccess) break;
@@ -1000,6 +1002,8 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     cudaGraph_t graph = nullptr;
     const cudaError_t e_end = cudaStreamEndCapture(b->origin, &graph);
     b->graph = graph;
+    b->kernel_nodes = g_launches.load() - launches_before;   // recorded, not run
+    g_launches.fetch_sub(b->kernel_nodes);
     if (rc != CP_OK) return fail(rc);
     if (e != cudaSuccess) return fail(cuda_fail(e, "recording the batch graph"));
     if (e_end != cudaSuccess) return fail(cuda_fail(e_end, "cudaStreamEndCapture"));
@@ -1024,7 +1028,7 @@ int cp_batch_run(cp_batch *b, cp_batch_result *results)
 {
     if (!b) return set_error("batch is NULL"), CP_ERR_ARG;
     CP_CUDA(cudaGraphLaunch(b->exec, b->origin));
-    count_launch();
+    g_launches.fetch_add(b->kernel_nodes, std::memory_order_relaxed);
     CP_CUDA(cudaStreamSynchronize(b->origin));
     int rc = CP_OK;
     for (int q = 0; q < b->nq; ++q) {

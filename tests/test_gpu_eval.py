@@ -327,3 +327,11 @@ def test_staging_wait_runs_out_and_reports(lib, crane):
         check_eval(s, xi, q0, qd)               # the device keeps working
     finally:
         s.close()
+
+
+def test_alu_peak_probes(lib):
+    """The FMA-pipe probes return plausible rates: FP32 within the part's nominal
+    152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s, FP64 well below it."""
+    p = lib.cp_alu_peaks()
+    assert 10.0 < p["fp32_tflops"] < 81.0
+    assert 0.05 < p["fp64_tflops"] < p["fp32_tflops"]
