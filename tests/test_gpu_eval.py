@@ -196,8 +196,9 @@ def test_evaluate_grid_dense_forest_full_size(lib, crane):
 ])
 def test_broadphase_matches_exhaustive_bitwise(lib, crane, name, n_cyl, K, S, n, spread):
     """The broad phase only drops obstacles that no sphere of the 32 checkpoints can reach,
-    so the default evaluation and the exhaustive one (every sphere against every obstacle)
-    give the same penalties, flags, terms and costs bit for bit."""
+    and it takes the same exact distances, so the default evaluation and the exhaustive one
+    (every sphere against every obstacle) give the same penalties, flags, terms and costs
+    bit for bit."""
     from paper_2503_14160_gb300 import workloads
     q0, qd = endpoints(name)
     scene = _scene(name, n_cyl=n_cyl)
@@ -212,6 +213,24 @@ def test_broadphase_matches_exhaustive_bitwise(lib, crane, name, n_cyl, K, S, n,
     for key in ("J", "flag", "terms", "words", "pen"):
         np.testing.assert_array_equal(out[0][key], out[1][key], err_msg=key)
     assert out[0]["flag"].any()
+
+
+def test_evaluate_spheres_of_unequal_radius(lib, crane):
+    """A model whose spheres differ in radius (the filter bound uses the largest); checked
+    against the oracle."""
+    import dataclasses
+    from paper_2503_14160_gb300 import workloads
+    spheres = tuple(dataclasses.replace(sp, radius=0.25 + 0.02 * (i % 3))
+                    for i, sp in enumerate(crane.spheres))
+    model = dataclasses.replace(crane, spheres=spheres)
+    q0, qd = endpoints("single_small")
+    s = Setup(model, _scene("single_small"), N=64, K=6, S=20)
+    try:
+        xi = workloads.random_candidates(q0, qd, 6, 64, seed=31)
+        g, o = check_eval(s, xi, q0, qd)
+        assert (o.d[:, 1:] < 0).any()
+    finally:
+        s.close()
 
 
 def test_work_counters(lib, crane):
