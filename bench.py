@@ -38,27 +38,32 @@ FLOPS_PER_PAIR = 5          # 2 sub, 1 mul, 1 fma per sphere-obstacle pair
 FLOPS_PER_CHECKPOINT = 140  # spline 32, kinematics ~80, length 12, limits 16
 FLOPS_FRAME_PER_SPHERE = 6  # broad phase: the sphere centre in the unit's frame (2 mul, 2 fma)
 FLOPS_PER_BROAD_TEST = 10   # broad phase: one obstacle against a unit's box
+FLOPS_GRID_PER_SPHERE = 4   # grid: the cell of a sphere centre (2 sub, 2 mul)
 FP32_PEAK_TFLOPS = PEAK_SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
 
 
-def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, broadphase, sm_mhz):
+def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, form, sm_mhz):
     """Algorithmic FP32 work of the evaluation launches in `timing` over their device time.
 
     Per checkpoint FLOPS_PER_CHECKPOINT (spline, kinematics, length, limits); per sphere and
-    obstacle whose pair test runs FLOPS_PER_PAIR, for all 32 lanes of a unit. Exhaustive:
-    every obstacle of every unit is tested. Broad phase: every (unit, obstacle) takes one
-    box test, each checkpoint places its spheres in the unit frame, and only the counted
-    survivors take pair tests."""
+    obstacle whose pair test runs FLOPS_PER_PAIR. form "exhaustive": every obstacle of every
+    unit is tested. "broad": every (unit, obstacle) takes one box test, each checkpoint
+    places its spheres in the unit frame, and only the counted survivors take pair tests.
+    "grid": each sphere finds its cell (FLOPS_GRID_PER_SPHERE) and the counted cell entries
+    take pair tests."""
     units = timing["eval_units"]
-    tests = timing["eval_obstacle_tests"]
-    if units <= 0 or tests < 0 or timing["eval_ms"] <= 0:
+    pairs = timing["eval_pair_tests"]
+    if units <= 0 or pairs < 0 or timing["eval_ms"] <= 0:
         return None
-    flops = candidates * n_s * FLOPS_PER_CHECKPOINT + tests * 32 * n_spheres * FLOPS_PER_PAIR
-    if broadphase:
+    flops = candidates * n_s * FLOPS_PER_CHECKPOINT + pairs * FLOPS_PER_PAIR
+    if form == "broad":
         flops += candidates * n_s * n_spheres * FLOPS_FRAME_PER_SPHERE
         flops += units * n_obstacles * FLOPS_PER_BROAD_TEST
+    elif form == "grid":
+        flops += candidates * n_s * n_spheres * FLOPS_GRID_PER_SPHERE
     achieved = flops / (timing["eval_ms"] / 1e3) / 1e12
-    return {"bound": "alu", "kernel": "k_eval" + (" (broad phase)" if broadphase else " (exhaustive)"),
+    kernel = {"broad": "k_eval_broad", "exhaustive": "k_eval", "grid": "k_eval_grid"}[form]
+    return {"bound": "alu", "kernel": kernel,
             "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
@@ -66,7 +71,7 @@ def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, broadphase, s
                                        if sm_mhz else None),
             "eval_ms_per_launch": timing["eval_ms"] / max(timing["eval_launches"], 1),
             "eval_launches": timing["eval_launches"],
-            "pair_tests_per_checkpoint": tests * 32 * n_spheres / max(candidates * n_s, 1),
+            "pair_tests_per_checkpoint": pairs / max(candidates * n_s, 1),
             "pair_tests_exhaustive_per_checkpoint": n_spheres * n_obstacles}
 
 
@@ -288,15 +293,16 @@ def run_ours(args):
     eval_ms = timing["eval_ms"] / max(timing["eval_launches"], 1)
     clk = clocks.summary()
     candidates = args.steps * (wl.n_candidates * iters + 1)
-    roofline = None
     roofline_exhaustive = None
-    if wl.grid_cell <= 0:
-        roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
-                                 candidates, not args.exhaustive, clk.get("sm_mhz"))
-        roofline["traffic"] = traffic_per_launch()
+    form = "grid" if wl.grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
+    roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
+                             candidates, form, clk.get("sm_mhz"))
+    if roofline is not None:
+        roofline["traffic"] = traffic_per_launch() if form == "broad" else None
         peaks = cp.cp_alu_peaks()
         roofline["measured_fma_peaks"] = peaks
         roofline["frac_of_measured_fp32"] = roofline["achieved"] / peaks["fp32_tflops"]
+    if wl.grid_cell <= 0:
         if not args.exhaustive:
             roofline_exhaustive = exhaustive_roofline(cp, crane, scene, wl, q0, qd,
                                                       clk.get("sm_mhz"))
@@ -321,7 +327,8 @@ def run_ours(args):
             "gpu_launches": launches,
             "roofline": roofline,
             "roofline_exhaustive": roofline_exhaustive,
-            "eval_kernel": {"name": "k_eval_grid" if wl.grid_cell > 0 else "k_eval",
+            "eval_kernel": {"name": {"broad": "k_eval_broad", "exhaustive": "k_eval",
+                                     "grid": "k_eval_grid"}[form],
                             "ms_per_launch": eval_ms, "launches": timing["eval_launches"]},
             "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
                                   for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},
@@ -356,7 +363,7 @@ def exhaustive_roofline(cp, crane, scene, wl, q0, qd, sm_mhz, iterations=10):
     finally:
         planner.close()
     r = eval_roofline(t, len(crane.spheres), scene.n_cyl + scene.n_box, wl.n_checkpoints,
-                      wl.n_candidates * iterations + 1, False, sm_mhz)
+                      wl.n_candidates * iterations + 1, "exhaustive", sm_mhz)
     if r is not None:
         r["iterations"] = iterations
     return r

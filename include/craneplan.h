@@ -159,6 +159,9 @@ typedef struct cp_timing {
                                      the broad-phase survivors, or every obstacle of every
                                      unit in the exhaustive form (counted on the device
                                      for the broad phase; -1 for the grid form) */
+    int64_t eval_pair_tests;      /* (checkpoint lane, sphere, obstacle) filter tests run:
+                                     counted on the device for the grid form (cell entries
+                                     visited), 32 x spheres x eval_obstacle_tests otherwise */
 } cp_timing;
 
 typedef struct cp_planner cp_planner;

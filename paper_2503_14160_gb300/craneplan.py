@@ -89,7 +89,8 @@ class cp_timing(ctypes.Structure):
                 ("sample_ms", ctypes.c_double), ("sample_launches", ctypes.c_int64),
                 ("factor_ms", ctypes.c_double), ("factor_launches", ctypes.c_int64),
                 ("update_ms", ctypes.c_double), ("update_launches", ctypes.c_int64),
-                ("eval_units", ctypes.c_int64), ("eval_obstacle_tests", ctypes.c_int64)]
+                ("eval_units", ctypes.c_int64), ("eval_obstacle_tests", ctypes.c_int64),
+                ("eval_pair_tests", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p

@@ -850,6 +850,8 @@ int cp_get_timing(cp_planner *p, cp_timing *out)
     CP_CUDA(cudaMemcpy(&survivors, p->work, sizeof(survivors), cudaMemcpyDeviceToHost));
     out->eval_units = p->timer.units;
     out->eval_obstacle_tests = p->timer.grid ? -1 : p->timer.tests + (int64_t)survivors;
+    out->eval_pair_tests = p->timer.grid ? (int64_t)survivors
+                                         : out->eval_obstacle_tests * 32 * p->mdev.n_spheres;
     p->timer.clear();
     CP_CUDA(cudaMemsetAsync(p->work, 0, sizeof(unsigned long long), p->st));
     CP_CUDA(cudaStreamSynchronize(p->st));

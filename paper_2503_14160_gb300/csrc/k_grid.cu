@@ -144,6 +144,7 @@ k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     const int units = a.n * a.chunks;
+    uint32_t tested = 0;   // cell entries this lane visited
     for (int u = warp; u < units; u += n_warps) {
         const int cand = u / a.chunks;
         const int chunk = u - cand * a.chunks;
@@ -179,6 +180,7 @@ k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs
                 it = 0;
                 end = __ldg(g.n_outside);
             }
+            tested += (uint32_t)(end - it);
             for (; it < end; ++it) {
                 const float4 rec = __ldg(list + it);
                 if (fmaf(sq.x, rec.x, fmaf(sq.y, rec.y, rec.z)) < sq.z)   // within reach (2-D)
@@ -186,6 +188,10 @@ k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs
             }
         }
         unit_epilogue(a, c, dmin, cand, chunk, lane);
+    }
+    if (a.work != nullptr) {
+        const uint32_t warp_tested = __reduce_add_sync(0xffffffffu, tested);
+        if (lane == 0 && warp_tested != 0) atomicAdd(a.work, (unsigned long long)warp_tested);
     }
 }
 

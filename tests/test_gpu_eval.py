@@ -258,9 +258,22 @@ def test_work_counters(lib, crane):
         finally:
             s.close()
         assert t["eval_launches"] == 2 and t["eval_units"] == 2 * n * chunks
+        assert t["eval_pair_tests"] == 32 * 12 * t["eval_obstacle_tests"]
         got.append(t["eval_obstacle_tests"])
     assert got[0] == 2 * n * chunks * scene.n_cyl
     assert 0 < got[1] < got[0] // 10
+    # grid form: cell entries visited, a small fraction of the exhaustive pair tests
+    s = Setup(crane, scene, N=n, K=K, S=S, grid_cell=0.5)
+    try:
+        lib.cp_set_endpoints(s.h, q0, qd)
+        lib.cp_set_timing(s.h, True)
+        lib.cp_evaluate(s.h, xi, n, J)
+        t = lib.cp_get_timing(s.h)
+        lib.cp_set_timing(s.h, False)
+    finally:
+        s.close()
+    assert t["eval_obstacle_tests"] == -1
+    assert 0 < t["eval_pair_tests"] < 32 * 12 * got[0] // 20
 
 
 def test_exhaustive_matches_oracle(lib, crane):
