@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "cp_internal.cuh"
@@ -126,6 +127,8 @@ struct cp_planner {
     cp_cylinder *cyl_in = nullptr;
     cp_box *box_in = nullptr;
     float4 *cyl_filt = nullptr, *cyl_exact = nullptr, *box_c = nullptr, *box_h = nullptr;
+    float4 *cyl_group = nullptr;
+    std::vector<cp_cylinder> cyl_sorted;   // host copy of the scene in staging order
     float4 *basis = nullptr;
     double *consts = nullptr;   // q0[4], qd[4], q_min[4], q_max[4]
     double *mu = nullptr, *C = nullptr, *L = nullptr;
@@ -272,19 +275,59 @@ int validate_params(const cp_params *p)
     return CP_OK;
 }
 
+// Cylinders sorted by the Z-order (Morton) code of their centres on a 65536 x 65536 lattice
+// over the scene's bounding box; ties keep the caller's order.
+void morton_order(const cp_cylinder *cyl, int n, std::vector<cp_cylinder> &out)
+{
+    double x0 = cyl[0].cx, x1 = x0, y0 = cyl[0].cy, y1 = y0;
+    for (int i = 1; i < n; ++i) {
+        x0 = std::min(x0, cyl[i].cx);
+        x1 = std::max(x1, cyl[i].cx);
+        y0 = std::min(y0, cyl[i].cy);
+        y1 = std::max(y1, cyl[i].cy);
+    }
+    const double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0.0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0.0;
+    auto spread = [](uint32_t v) {   // bits of v to the even positions
+        uint64_t x = v & 0xFFFFu;
+        x = (x | (x << 8)) & 0x00FF00FFu;
+        x = (x | (x << 4)) & 0x0F0F0F0Fu;
+        x = (x | (x << 2)) & 0x33333333u;
+        x = (x | (x << 1)) & 0x55555555u;
+        return (uint32_t)x;
+    };
+    std::vector<std::pair<uint32_t, int>> key((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const uint32_t qx = (uint32_t)((cyl[i].cx - x0) * sx), qy = (uint32_t)((cyl[i].cy - y0) * sy);
+        key[i] = {spread(qx) | (spread(qy) << 1), i};
+    }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<uint32_t, int> &a, const std::pair<uint32_t, int> &b) {
+                         return a.first < b.first;
+                     });
+    out.resize((size_t)n);
+    for (int i = 0; i < n; ++i) out[i] = cyl[key[i].second];
+}
+
 int stage_scene(cp_planner *p, const cp_scene *sc)
 {
     if (sc->n_cyl > p->cap_cyl || sc->n_box > p->cap_box)
         return set_error("scene (%d cylinders, %d boxes) exceeds the capacity (%d, %d) set at init",
                          sc->n_cyl, sc->n_box, p->cap_cyl, p->cap_box), CP_ERR_ARG;
-    if (sc->n_cyl > 0)
-        CP_CUDA(cudaMemcpyAsync(p->cyl_in, sc->cyl, sizeof(cp_cylinder) * sc->n_cyl,
+    if (sc->n_cyl > 0) {
+        // staged in Z order of the centres, so that the groups of kGroup consecutive cylinders
+        // are compact (every kernel takes a minimum or a sum over all of them; the order only
+        // changes which obstacles share a group)
+        morton_order(sc->cyl, sc->n_cyl, p->cyl_sorted);
+        CP_CUDA(cudaMemcpyAsync(p->cyl_in, p->cyl_sorted.data(), sizeof(cp_cylinder) * sc->n_cyl,
                                 cudaMemcpyHostToDevice, p->st));
+        CP_CUDA(cudaStreamSynchronize(p->st));   // the host copy may change on the next call
+    }
     if (sc->n_box > 0)
         CP_CUDA(cudaMemcpyAsync(p->box_in, sc->box, sizeof(cp_box) * sc->n_box,
                                 cudaMemcpyHostToDevice, p->st));
     int rc = launch_prepare_scene(p->cyl_in, sc->n_cyl, p->box_in, sc->n_box, p->mdev.r_max,
-                                  p->cyl_filt, p->cyl_exact, p->box_c, p->box_h, p->st);
+                                  p->cyl_filt, p->cyl_exact, p->cyl_group, p->box_c, p->box_h,
+                                  p->st);
     if (rc != CP_OK) return rc;
     p->sdev.n_cyl = sc->n_cyl;
     p->sdev.n_box = sc->n_box;
@@ -493,6 +536,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_box_in = L.take<cp_box>(p->cap_box + 1);
     const size_t o_filt = L.take<float4>(p->cap_cyl + 1);
     const size_t o_exact = L.take<float4>(p->cap_cyl + 1);
+    const size_t o_group = L.take<float4>(n_groups(p->cap_cyl) + 1);
     const size_t o_bc = L.take<float4>(p->cap_box + 1);
     const size_t o_bh = L.take<float4>(p->cap_box + 1);
     const size_t o_basis = L.take<float4>(2 * (size_t)p->S);
@@ -544,6 +588,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->cyl_in = (cp_cylinder *)(b + o_cyl_in);
     p->box_in = (cp_box *)(b + o_box_in);
     p->cyl_filt = (float4 *)(b + o_filt);
+    p->cyl_group = (float4 *)(b + o_group);
     p->cyl_exact = (float4 *)(b + o_exact);
     p->box_c = (float4 *)(b + o_bc);
     p->box_h = (float4 *)(b + o_bh);
@@ -593,6 +638,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->gdev.outside = p->grid_outside;
     p->gdev.n_outside = p->grid_counters;
     p->sdev.cyl_filt = p->cyl_filt;
+    p->sdev.cyl_group = p->cyl_group;
     p->sdev.cyl_exact = p->cyl_exact;
     p->sdev.box_c = p->box_c;
     p->sdev.box_h = p->box_h;

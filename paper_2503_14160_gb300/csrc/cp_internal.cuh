@@ -62,7 +62,12 @@ struct SceneDev {
     const float4 *box_c;
     const float4 *box_h;
     int n_box;
+    const float4 *cyl_group;   // [n_groups(n_cyl)] {gx, gy, 0, radius}: circle that holds every
+                               // member's reach (kGroup consecutive cylinders per group)
 };
+
+constexpr int kGroup = 8;    // cylinders per broad-phase group
+__host__ __device__ inline int n_groups(int n_cyl) { return (n_cyl + kGroup - 1) / kGroup; }
 
 // Uniform grid of obstacle ids over a square window (cells h x h, nx x ny).
 struct GridDev {
@@ -138,7 +143,7 @@ int64_t smooth_partial_units(int num_sms);
 int launch_axpy(float *x, const float *y, double alpha, int64_t n, cudaStream_t st);
 
 int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d_box_in,
-                         int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact,
+                         int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact, float4 *cyl_group,
                          float4 *box_c, float4 *box_h, cudaStream_t st);
 int launch_basis_table(int S, float4 *basis, cudaStream_t st);
 int launch_init_distribution(const double *q0, const double *qd, const double *q_min,

@@ -52,17 +52,18 @@ __device__ __forceinline__ bool mbarrier_try_wait(uint64_t *bar, uint32_t parity
     return ok != 0;
 }
 
-// Stages the obstacle records, box records and spline table into shared memory with bulk
+// Stages the obstacle records, box records, spline table and cylinder groups into shared memory with bulk
 // copies completing on one mbarrier. Every thread waits at most kStagingWaitCycles; when
 // the wait runs out in any thread the CTA records DEV_ERR_TIMEOUT and returns false (a
 // uniform decision). `withhold` issues no copy, so that the wait runs out on purpose (the
 // test of this path); nothing is then in flight when the CTA leaves.
 __device__ __noinline__ bool stage_bulk(uint64_t *bar, float4 *s_filt, float4 *s_exact, float4 *s_bc,
-                           float4 *s_bh, float4 *s_basis, const SceneDev &sc, const EvalArgs &a)
+                           float4 *s_bh, float4 *s_basis, float4 *s_group, const SceneDev &sc,
+                           const EvalArgs &a)
 {
     const uint32_t b_cyl = 16u * (uint32_t)sc.n_cyl, b_box = 16u * (uint32_t)sc.n_box;
-    const uint32_t b_basis = 32u * (uint32_t)a.S;
-    const uint32_t total = 2 * b_cyl + 2 * b_box + b_basis;
+    const uint32_t b_basis = 32u * (uint32_t)a.S, b_group = 16u * (uint32_t)n_groups(sc.n_cyl);
+    const uint32_t total = 2 * b_cyl + 2 * b_box + b_basis + b_group;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -75,6 +76,7 @@ __device__ __noinline__ bool stage_bulk(uint64_t *bar, float4 *s_filt, float4 *s
             if (b_cyl) {
                 bulk_copy_to_smem(s_filt, sc.cyl_filt, b_cyl, bar);
                 bulk_copy_to_smem(s_exact, sc.cyl_exact, b_cyl, bar);
+                bulk_copy_to_smem(s_group, sc.cyl_group, b_group, bar);
             }
             if (b_box) {
                 bulk_copy_to_smem(s_bc, sc.box_c, b_box, bar);
@@ -198,8 +200,9 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
     float4 *s_bc = s_exact + sc.n_cyl;
     float4 *s_bh = s_bc + sc.n_box;
     float4 *s_basis = s_bh + sc.n_box;
+    float4 *s_group = s_basis + 2 * a.S;
     __shared__ __align__(8) uint64_t staging_bar;
-    if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, sc, a)) return;
+    if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, s_group, sc, a)) return;
 
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -220,12 +223,24 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
         for (int q = 0; q < NSPH / 2; ++q) H2[q] = make_float2(H[2 * q], H[2 * q + 1]);
 
         float dmin = CUDART_INF_F;
-        for (int base = 0; base < sc.n_cyl; base += 32) {
-            const int o = base + lane;
-            uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, s_filt[o]));
+        const int n_grp = n_groups(sc.n_cyl);
+        for (int gbase = 0; gbase < n_grp; gbase += 32) {
+            // groups whose circle meets the unit box, then their members four groups at a
+            // time: lane l takes member l % 8 of the (l / 8)-th remaining group
+            uint32_t gmask = __ballot_sync(0xffffffffu, gbase + lane < n_grp && unit_near(fr, s_group[gbase + lane]));
+            while (gmask) {
+                uint32_t g = gmask;
+                const int slot = lane >> 3;
+                g = slot >= 1 ? g & (g - 1) : g;
+                g = slot >= 2 ? g & (g - 1) : g;
+                g = slot >= 3 ? g & (g - 1) : g;
+                const int o = g ? (gbase + __ffs(g) - 1) * kGroup + (lane & (kGroup - 1)) : sc.n_cyl;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) gmask &= gmask - 1;
+                uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, s_filt[o]));
             tested += __popc(mask);
             while (mask) {
-                const int ob = base + __ffs(mask) - 1;
+                const int ob = __shfl_sync(0xffffffffu, o, __ffs(mask) - 1);
                 mask &= mask - 1;
                 const float4 f = s_filt[ob], e = s_exact[ob];
                 const float p = fmaf(c1, f.x, s1 * f.y);
@@ -240,6 +255,7 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
                 }
                 if (any_below<NSPH>(t, zero))
                     dmin = fminf(dmin, exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e));
+            }
             }
         }
         for (int base = 0; base < sc.n_box; base += 32) {
@@ -274,8 +290,9 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
     float4 *s_bc = s_exact + sc.n_cyl;
     float4 *s_bh = s_bc + sc.n_box;
     float4 *s_basis = s_bh + sc.n_box;
+    float4 *s_group = s_basis + 2 * a.S;
     __shared__ __align__(8) uint64_t staging_bar;
-    if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, sc, a)) return;
+    if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, s_group, sc, a)) return;
 
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -353,47 +370,52 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
 }
 
 
-// One warp per candidate: lanes take the candidate's chunks (lane, lane + 32, ...), sum
-// them in FP64, and a fixed shuffle tree combines the lanes (deterministic order).
+// Four lanes per candidate: lane g of the group sums the candidate's chunks g, g + 4, ...
+// in FP64, and two shuffle steps combine the four (a fixed order, so results are
+// deterministic). The group's lanes read neighbouring chunk records of one row.
+constexpr int kFinalizeLanes = 4;
+
 __global__ void k_eval_finalize(const float4 *__restrict__ partial,
                                 const uint32_t *__restrict__ flagword, int n, int chunks,
                                 double w_c, double w_l, double lambda_c, double *J,
                                 uint8_t *flag, double *terms, uint32_t *substep_flags)
 {
-    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / kFinalizeLanes, g = t % kFinalizeLanes;
+    const bool active = i < n;
     double jp = 0.0, jc = 0.0, jl = 0.0, len = 0.0;
     int n_flagged = 0;
-    for (int c = lane; c < chunks; c += 32) {
-        const float4 v = partial[(size_t)i * chunks + c];
-        const uint32_t w = flagword[(size_t)i * chunks + c];
-        jp += (double)v.x;
-        jc += (double)v.y;
-        jl += (double)v.z;
-        len += (double)v.w;
-        n_flagged += __popc(w);
-        if (substep_flags != nullptr) substep_flags[(size_t)i * chunks + c] = w;
+    if (active) {
+        for (int c = g; c < chunks; c += kFinalizeLanes) {
+            const float4 v = partial[(size_t)i * chunks + c];
+            const uint32_t w = flagword[(size_t)i * chunks + c];
+            jp += (double)v.x;
+            jc += (double)v.y;
+            jl += (double)v.z;
+            len += (double)v.w;
+            n_flagged += __popc(w);
+            if (substep_flags != nullptr) substep_flags[(size_t)i * chunks + c] = w;
+        }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 1; off < kFinalizeLanes; off <<= 1) {   // every lane of the warp takes part
         jp += __shfl_xor_sync(0xffffffffu, jp, off);
         jc += __shfl_xor_sync(0xffffffffu, jc, off);
         jl += __shfl_xor_sync(0xffffffffu, jl, off);
         len += __shfl_xor_sync(0xffffffffu, len, off);
         n_flagged += __shfl_xor_sync(0xffffffffu, n_flagged, off);
     }
-    if (lane != 0) return;
+    if (!active || g != 0) return;
     jc *= lambda_c;
     J[i] = jp + w_c * jc + w_l * jl;
     if (flag != nullptr) flag[i] = n_flagged > 0 ? 1 : 0;
     if (terms != nullptr) {
-        double *t = terms + (size_t)i * 5;
-        t[0] = jp;
-        t[1] = jc;
-        t[2] = jl;
-        t[3] = len;
-        t[4] = (double)n_flagged;
+        double *tm = terms + (size_t)i * 5;
+        tm[0] = jp;
+        tm[1] = jc;
+        tm[2] = jl;
+        tm[3] = len;
+        tm[4] = (double)n_flagged;
     }
 }
 
@@ -441,7 +463,8 @@ int eval_grid(F *kernel, size_t smem, int num_sms, int units, int ctas_per_sm)
 
 size_t eval_smem_bytes(int n_cyl, int n_box, int S)
 {
-    return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S);
+    return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S +
+                             (size_t)n_groups(n_cyl));
 }
 
 template <typename F>
@@ -494,7 +517,7 @@ int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n,
 {
     if (n == 0) return CP_OK;
     const int threads = 256;
-    k_eval_finalize<<<(n * 32 + threads - 1) / threads, threads, 0, st>>>(
+    k_eval_finalize<<<(n * kFinalizeLanes + threads - 1) / threads, threads, 0, st>>>(
         partial, flagword, n, chunks, w_c, w_l, lambda_c, J, flag, terms, substep_flags);
     CP_LAUNCHED("k_eval_finalize");
     return CP_OK;

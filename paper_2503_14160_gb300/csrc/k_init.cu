@@ -35,6 +35,33 @@ __global__ void k_prepare_scene(const cp_cylinder *__restrict__ cyl, int n_cyl,
     }
 }
 
+// Group g of kGroup consecutive cylinders: a circle {gx, gy, 0, radius} that holds the reach
+// disk of every member (centre plus its broad-phase reach w), so that an obstacle box test
+// that passes for a member passes for its group. The centre is the middle of the members'
+// bounding box; the radius is taken in FP64 and padded by 1e-5 m plus 1e-6 of the centre's
+// distance from the origin, far above the FP32 rounding of the rotated coordinates.
+__global__ void k_prepare_groups(const float4 *__restrict__ cyl_filt, int n_cyl, float4 *group)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_groups(n_cyl)) return;
+    const int b = g * kGroup, e = min(n_cyl, b + kGroup);
+    float x0 = cyl_filt[b].x, x1 = x0, y0 = cyl_filt[b].y, y1 = y0;
+    for (int i = b + 1; i < e; ++i) {
+        x0 = fminf(x0, cyl_filt[i].x);
+        x1 = fmaxf(x1, cyl_filt[i].x);
+        y0 = fminf(y0, cyl_filt[i].y);
+        y1 = fmaxf(y1, cyl_filt[i].y);
+    }
+    const float gx = 0.5f * (x0 + x1), gy = 0.5f * (y0 + y1);
+    double r = 0.0;
+    for (int i = b; i < e; ++i) {
+        const double dx = (double)cyl_filt[i].x - gx, dy = (double)cyl_filt[i].y - gy;
+        r = fmax(r, sqrt(dx * dx + dy * dy) + (double)cyl_filt[i].w);
+    }
+    r += 1e-5 + 1e-6 * sqrt((double)gx * gx + (double)gy * gy);
+    group[g] = make_float4(gx, gy, 0.f, (float)(r * (1.0 + 1e-6)));
+}
+
 // Uniform cubic B-spline basis on one span at u in [0, 1] (basis-matrix form):
 //   b0 = (1-u)^3 / 6, b1 = (3u^3 - 6u^2 + 4) / 6, b2 = (-3u^3 + 3u^2 + 3u + 1) / 6, b3 = u^3 / 6
 __device__ void cubic_basis(double u, double b[4])
@@ -105,7 +132,7 @@ __global__ void k_control_points(const double *q0, const double *qd, const doubl
 }  // namespace
 
 int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d_box_in,
-                         int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact,
+                         int n_box, float r_max, float4 *cyl_filt, float4 *cyl_exact, float4 *cyl_group,
                          float4 *box_c, float4 *box_h, cudaStream_t st)
 {
     const int n = n_cyl > n_box ? n_cyl : n_box;
@@ -113,6 +140,10 @@ int launch_prepare_scene(const cp_cylinder *d_cyl_in, int n_cyl, const cp_box *d
     k_prepare_scene<<<(n + 127) / 128, 128, 0, st>>>(d_cyl_in, n_cyl, d_box_in, n_box, r_max,
                                                      cyl_filt, cyl_exact, box_c, box_h);
     CP_LAUNCHED("k_prepare_scene");
+    if (n_cyl > 0) {
+        k_prepare_groups<<<(n_groups(n_cyl) + 127) / 128, 128, 0, st>>>(cyl_filt, n_cyl, cyl_group);
+        CP_LAUNCHED("k_prepare_groups");
+    }
     return CP_OK;
 }
 

@@ -75,7 +75,8 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     // scratch layout: cylinder records, box records, basis table, partials, words
     const size_t o_filt = 0;
     const size_t o_exact = o_filt + align256(sizeof(float4) * (size_t)n_cyl);
-    const size_t o_bc = o_exact + align256(sizeof(float4) * (size_t)n_cyl);
+    const size_t o_group = o_exact + align256(sizeof(float4) * (size_t)n_cyl);
+    const size_t o_bc = o_group + align256(sizeof(float4) * (size_t)n_groups(n_cyl));
     const size_t o_bh = o_bc + align256(sizeof(float4) * (size_t)n_box);
     const size_t o_basis = o_bh + align256(sizeof(float4) * (size_t)n_box);
     const size_t o_partial = o_basis + align256(sizeof(float4) * 2 * (size_t)S);
@@ -98,15 +99,17 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     unsigned char *base = nullptr;
     if ((rc = scratch_address(&base)) != CP_OK) return rc;
     float4 *filt = (float4 *)(base + o_filt), *exact = (float4 *)(base + o_exact);
+    float4 *group = (float4 *)(base + o_group);
     float4 *bc = (float4 *)(base + o_bc), *bh = (float4 *)(base + o_bh);
     float4 *basis = (float4 *)(base + o_basis);
     const cudaStream_t st = (cudaStream_t)stream;
 
     const ModelDev m = make_model(model);
-    if ((rc = launch_prepare_scene(d_cyl, n_cyl, d_box, n_box, m.r_max, filt, exact, bc, bh, st)) != CP_OK)
+    if ((rc = launch_prepare_scene(d_cyl, n_cyl, d_box, n_box, m.r_max, filt, exact, group, bc, bh, st)) !=
+        CP_OK)
         return rc;
     if ((rc = launch_basis_table(S, basis, st)) != CP_OK) return rc;
-    SceneDev sc{filt, exact, n_cyl, bc, bh, n_box};
+    SceneDev sc{filt, exact, n_cyl, bc, bh, n_box, group};
     EvalArgs a{};
     a.xi = (const float4 *)d_xi;
     a.n = n;
