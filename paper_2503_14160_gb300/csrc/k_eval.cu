@@ -111,57 +111,6 @@ __device__ __forceinline__ float exact_cylinders(const ModelDev &m, const float 
     return d;
 }
 
-// Broad phase of one work unit (32 checkpoints of one candidate). All spheres of one
-// configuration lie on the vertical plane at its slew angle, at signed horizontal distances
-// h from the slew axis. The unit's centres are bounded by a box in a frame turned to the
-// slew angle of lane 16: a sphere at h on the plane at angle phi has frame coordinates
-// h (cos, sin)(phi - phi_16), so the box follows from each lane's smallest and largest h.
-// An obstacle whose centre lies farther than its reach (the `w` of its record) from that
-// box cannot pass the per-sphere filter for any lane; the reach carries 1 cm of slack over
-// the filter's own bound, far above the FP32 rounding of either test.
-struct UnitFrame {
-    float c0, s0;     // frame axes
-    float uc, uh;     // box centre and half extent along the slew direction
-    float vc, vh;     // and across it
-};
-
-template <int NSPH>
-__device__ __forceinline__ UnitFrame unit_frame(float s1, float c1, const float *H)
-{
-    UnitFrame f;
-    f.s0 = __shfl_sync(0xffffffffu, s1, 16);
-    f.c0 = __shfl_sync(0xffffffffu, c1, 16);
-    float hmin = H[0], hmax = H[0];
-#pragma unroll
-    for (int s = 1; s < NSPH; ++s) {
-        hmin = fminf(hmin, H[s]);
-        hmax = fmaxf(hmax, H[s]);
-    }
-    const float cd = fmaf(f.c0, c1, f.s0 * s1), sd = fmaf(f.c0, s1, -f.s0 * c1);
-    float umin = fminf(hmin * cd, hmax * cd), umax = fmaxf(hmin * cd, hmax * cd);
-    float vmin = fminf(hmin * sd, hmax * sd), vmax = fmaxf(hmin * sd, hmax * sd);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, off));
-        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, off));
-        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
-    }
-    f.uc = 0.5f * (umin + umax);
-    f.uh = 0.5f * (umax - umin);
-    f.vc = 0.5f * (vmin + vmax);
-    f.vh = 0.5f * (vmax - vmin);
-    return f;
-}
-
-// True when the obstacle record r = {cx, cy, ., reach} may come within reach of the unit.
-__device__ __forceinline__ bool unit_near(const UnitFrame &f, float4 r)
-{
-    const float u = fmaf(f.c0, r.x, f.s0 * r.y);
-    const float v = fmaf(f.c0, r.y, -f.s0 * r.x);
-    return (fabsf(u - f.uc) <= f.uh + r.w) & (fabsf(v - f.vc) <= f.vh + r.w);
-}
-
 // Exact distance of every sphere whose polar filter passes against one cylinder: with the
 // obstacle centre at p along the lane's plane and q across it, sphere s passes when
 // (h_s - p)^2 < (R + r_max)^2 + margin - q^2 = rhs. The distance itself is taken from the

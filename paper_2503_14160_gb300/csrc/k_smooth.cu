@@ -99,12 +99,13 @@ __global__ void __launch_bounds__(kSmoothThreads)
 k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
 {
     extern __shared__ __align__(16) float4 smem[];
-    float4 *s_filt = smem;                      // {cx, cy, W_s, 0}
+    float4 *s_filt = smem;                      // {cx, cy, W_s, reach}
     float4 *s_exact = s_filt + sc.n_cyl;        // {R, z_lo, z_hi, 0}
     float4 *s_bc = s_exact + sc.n_cyl;
     float4 *s_bh = s_bc + sc.n_box;
     float4 *s_basis = s_bh + sc.n_box;
-    float *s_warp = reinterpret_cast<float *>(s_basis + 2 * a.S);
+    float4 *s_group = s_basis + 2 * a.S;
+    float *s_warp = reinterpret_cast<float *>(s_group + n_groups(sc.n_cyl));
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per_warp = 32 * 16 + 32 + 4 * a.K;
     float *s_contrib = s_warp + wib * per_warp;              // [32][4 control points][4]
@@ -115,9 +116,10 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
         const float4 f = sc.cyl_filt[i], e = sc.cyl_exact[i];
         const double R = (double)e.x + reach;
         const double W = (double)f.x * f.x + (double)f.y * f.y - R * R;
-        s_filt[i] = make_float4(f.x, f.y, (float)W, 0.f);
+        s_filt[i] = make_float4(f.x, f.y, (float)W, f.w);   // w: broad-phase reach
         s_exact[i] = e;
     }
+    for (int i = threadIdx.x; i < n_groups(sc.n_cyl); i += blockDim.x) s_group[i] = sc.cyl_group[i];
     for (int i = threadIdx.x; i < sc.n_box; i += blockDim.x) {
         s_bc[i] = sc.box_c[i];
         s_bh[i] = sc.box_h[i];
@@ -156,8 +158,18 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
             const float jl = limit_excess(q.x, m.q_min[0], m.q_max[0]) + limit_excess(q.y, m.q_min[1], m.q_max[1]) +
                              limit_excess(q.z, m.q_min[2], m.q_max[2]) + limit_excess(q.w, m.q_min[3], m.q_max[3]);
 
-            float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH];
-            crane_fk<NSPH>(m, q, X, Y, Z);
+            float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH], s1, c1;
+            crane_fk_polar<NSPH>(m, q, X, Z, s1, c1);
+            // broad phase of the chunk: the box of its spheres in the slew frame, dilated by
+            // the softplus range m + cut beta beyond the obstacles' contact reach
+            const UnitFrame fr = unit_frame<NSPH>(s1, c1, X);
+            const float extra = a.margin + kSmoothCut * a.beta;
+#pragma unroll
+            for (int s = 0; s < NSPH; ++s) {
+                const float h = X[s];
+                X[s] = __fmul_rn(c1, h);
+                Y[s] = __fmul_rn(s1, h);
+            }
             // Registers feed the unrolled filter; the per-thread arrays below (local memory)
             // feed the rolled exact path, so that one copy of the distance, gradient and
             // softplus code serves every sphere (unrolled it outgrows the instruction cache).
@@ -176,7 +188,23 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                 Y2[p] = make_float2(-2.f * Y[2 * p], -2.f * Y[2 * p + 1]);
             }
             float pen = 0.f;
-            for (int o = 0; o < sc.n_cyl; ++o) {
+            const int n_grp = n_groups(sc.n_cyl);
+            for (int gbase = 0; gbase < n_grp; gbase += 32) {
+                uint32_t gmask = __ballot_sync(0xffffffffu, gbase + lane < n_grp &&
+                                                                unit_near(fr, s_group[gbase + lane], extra));
+                while (gmask) {
+                    uint32_t gg = gmask;
+                    const int slot = lane >> 3;
+                    gg = slot >= 1 ? gg & (gg - 1) : gg;
+                    gg = slot >= 2 ? gg & (gg - 1) : gg;
+                    gg = slot >= 3 ? gg & (gg - 1) : gg;
+                    const int oc = gg ? (gbase + __ffs(gg) - 1) * kGroup + (lane & (kGroup - 1)) : sc.n_cyl;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) gmask &= gmask - 1;
+                    uint32_t omask = __ballot_sync(0xffffffffu, oc < sc.n_cyl && unit_near(fr, s_filt[oc], extra));
+                    while (omask) {
+                const int o = __shfl_sync(0xffffffffu, oc, __ffs(omask) - 1);
+                omask &= omask - 1;
                 const float4 f = s_filt[o];
                 float2 g[NSPH / 2];
 #pragma unroll
@@ -196,8 +224,15 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                         }
                     }
                 }
+                    }
+                }
             }
-            for (int o = 0; o < sc.n_box; ++o) {
+            for (int bbase = 0; bbase < sc.n_box; bbase += 32) {
+                uint32_t bmask = __ballot_sync(0xffffffffu, bbase + lane < sc.n_box &&
+                                                                unit_near(fr, s_bc[bbase + lane], extra));
+                while (bmask) {
+                const int o = bbase + __ffs(bmask) - 1;
+                bmask &= bmask - 1;
                 const float4 cb = s_bc[o], hb = s_bh[o];
 #pragma unroll 1
                 for (int s = 0; s < m.n_spheres; ++s) {
@@ -208,6 +243,7 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                                                : make_float3(0.f, 0.f, 0.f);
                         pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, dp[s]);
                     }
+                }
                 }
             }
 
@@ -312,7 +348,8 @@ __global__ void k_axpy(float *x, const float *y, float alpha, int64_t n)
 
 size_t smooth_smem(int n_cyl, int n_box, int S, int K)
 {
-    return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S) +
+    return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S +
+                             (size_t)n_groups(n_cyl)) +
            sizeof(float) * (kSmoothThreads / 32) * (size_t)(32 * 16 + 32 + 4 * K);
 }
 
