@@ -137,44 +137,51 @@ template <int NSPH>
 __global__ void __launch_bounds__(kGridThreads, CP_GRID_MIN_BLOCKS)
 k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs a)
 {
+    // Shared memory: the spline table, then per warp, sphere and lane the record
+    // {h, z, first entry, end entry} of the sphere's cell (h its signed horizontal distance
+    // from the slew axis), read by the rolled sphere loop.
     extern __shared__ __align__(16) float4 s_basis[];
+    float4 *s_sph = s_basis + 2 * a.S;
     for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x) s_basis[i] = a.basis[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+    float4 *my_sph = s_sph + (threadIdx.x >> 5) * NSPH * 32 + lane;
     const int units = a.n * a.chunks;
     uint32_t tested = 0;   // cell entries this lane visited
     for (int u = warp; u < units; u += n_warps) {
         const int cand = u / a.chunks;
         const int chunk = u - cand * a.chunks;
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
-        float X[NSPH], Y[NSPH], Z[NSPH];
-        crane_fk<NSPH>(m, c.q, X, Y, Z);
-        // Per sphere: the entry range of its cell (looked up for all spheres first, so the
-        // loads are in flight together) and its query record. The sphere loop below is kept
-        // rolled, reading these small per-thread arrays, so that one copy of the entry loop
-        // serves all spheres (unrolled, the code outgrows the instruction cache).
-        float4 qs[NSPH];   // {-2x, -2y, margin - x^2 - y^2, z}
-        int2 range[NSPH];
+        float H[NSPH], Z[NSPH], s1, c1;
+        crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
+        // Per sphere the entry range of its cell, looked up for all spheres first so that the
+        // loads are in flight together, and kept with h and z in shared memory: the sphere
+        // loop below stays rolled (one copy of the entry loop serves all spheres; unrolled,
+        // the code outgrows the instruction cache) without per-thread local arrays.
 #pragma unroll
         for (int s = 0; s < NSPH; ++s) {
-            const float fx = (X[s] - g.x0) * g.inv_h, fy = (Y[s] - g.y0) * g.inv_h;
+            const float x = __fmul_rn(c1, H[s]), y = __fmul_rn(s1, H[s]);
+            const float fx = (x - g.x0) * g.inv_h, fy = (y - g.y0) * g.inv_h;
+            int first = -1, end = 0;   // -1: outside the window
             if (fx >= 0.f && fy >= 0.f && fx < (float)g.nx && fy < (float)g.ny) {
                 const int cell = (int)fy * g.nx + (int)fx;
-                range[s] = make_int2(__ldg(g.cell_start + cell), __ldg(g.cell_start + cell + 1));
-            } else {
-                range[s] = make_int2(-1, 0);   // outside the window
+                first = __ldg(g.cell_start + cell);
+                end = __ldg(g.cell_start + cell + 1);
             }
-            qs[s] = make_float4(-2.f * X[s], -2.f * Y[s], kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]), Z[s]);
+            my_sph[s * 32] = make_float4(H[s], Z[s], __int_as_float(first), __int_as_float(end));
         }
+        __syncwarp();
         float dmin = CUDART_INF_F;
 #pragma unroll 1
         for (int s = 0; s < m.n_spheres; ++s) {
-            const float4 sq = qs[s];
-            const float xs = -0.5f * sq.x, ys = -0.5f * sq.y, r = m.sph[s].radius;
+            const float4 sp = my_sph[s * 32];
+            const float xs = __fmul_rn(c1, sp.x), ys = __fmul_rn(s1, sp.x);
+            const float qx = -2.f * xs, qy = -2.f * ys, T = kFilterMargin - fmaf(xs, xs, ys * ys);
+            const float r = m.sph[s].radius;
             const float4 *list = g.items;
-            int it = range[s].x, end = range[s].y;
+            int it = __float_as_int(sp.z), end = __float_as_int(sp.w);
             if (it < 0) {
                 list = g.outside;
                 it = 0;
@@ -183,16 +190,28 @@ k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs
             tested += (uint32_t)(end - it);
             for (; it < end; ++it) {
                 const float4 rec = __ldg(list + it);
-                if (fmaf(sq.x, rec.x, fmaf(sq.y, rec.y, rec.z)) < sq.z)   // within reach (2-D)
-                    dmin = fminf(dmin, record_distance(sc, rec, xs, ys, sq.w, r));
+                if (fmaf(qx, rec.x, fmaf(qy, rec.y, rec.z)) < T)   // within reach (2-D)
+                    dmin = fminf(dmin, record_distance(sc, rec, xs, ys, sp.y, r));
             }
         }
+        __syncwarp();
         unit_epilogue(a, c, dmin, cand, chunk, lane);
     }
     if (a.work != nullptr) {
         const uint32_t warp_tested = __reduce_add_sync(0xffffffffu, tested);
         if (lane == 0 && warp_tested != 0) atomicAdd(a.work, (unsigned long long)warp_tested);
     }
+}
+
+// Raise (never lower) the dynamic shared-memory limit of a grid kernel.
+template <typename F>
+cudaError_t raise_grid_smem(F *fn, size_t smem)
+{
+    cudaFuncAttributes at{};
+    cudaError_t e = cudaFuncGetAttributes(&at, fn);
+    if (e == cudaSuccess && (size_t)at.maxDynamicSharedSizeBytes < smem)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
 }
 
 }  // namespace
@@ -244,12 +263,16 @@ int launch_eval_grid(const ModelDev &m, const SceneDev &sc, const GridDev &g, co
 {
     const int units = a.n * a.chunks;
     if (units == 0) return CP_OK;
-    const size_t smem = sizeof(float4) * 2 * (size_t)a.S;
+    const int nsph = m.n_spheres == 12 ? 12 : 16;
+    const size_t smem = sizeof(float4) * (2 * (size_t)a.S + (size_t)(kGridThreads / 32) * nsph * 32);
     int per_sm = 0;
-    if (m.n_spheres == 12)
+    if (m.n_spheres == 12) {
+        CP_CUDA(raise_grid_smem(k_eval_grid<12>, smem));
         CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_grid<12>, kGridThreads, smem));
-    else
+    } else {
+        CP_CUDA(raise_grid_smem(k_eval_grid<16>, smem));
         CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_grid<16>, kGridThreads, smem));
+    }
     if (per_sm < 1) per_sm = 1;
     if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
     const int needed = (units + kGridThreads / 32 - 1) / (kGridThreads / 32);
