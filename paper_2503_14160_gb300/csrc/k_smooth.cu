@@ -13,7 +13,7 @@
 namespace cp {
 namespace {
 
-constexpr int kSmoothThreads = 256;     // 8 warps, one candidate per warp
+constexpr int kSmoothMaxThreads = 512;  // up to 16 warps per CTA, one candidate per warp
 constexpr float kSmoothCut = 30.f;      // pairs with sd > m + 30 beta are skipped
 
 struct SmoothArgs {
@@ -94,8 +94,13 @@ __device__ __forceinline__ void pair_term(float sd, float3 grad_sdf, float m, fl
     }
 }
 
+// Shared floats of one warp: the lane sums of the gradient ([32][4 control points][4]),
+// the lanes' spans, the candidate's accumulator [K][4], and per sphere and lane h, z and the
+// three components of d penalty / d centre.
+__host__ __device__ inline int smooth_warp_floats(int K, int nsph) { return 32 * 16 + 32 + 4 * K + 5 * nsph * 32; }
+
 template <int NSPH, bool GRAD>
-__global__ void __launch_bounds__(kSmoothThreads)
+__global__ void __launch_bounds__(kSmoothMaxThreads)
 k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
 {
     extern __shared__ __align__(16) float4 smem[];
@@ -107,10 +112,13 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
     float4 *s_group = s_basis + 2 * a.S;
     float *s_warp = reinterpret_cast<float *>(s_group + n_groups(sc.n_cyl));
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per_warp = 32 * 16 + 32 + 4 * a.K;
+    const int per_warp = smooth_warp_floats(a.K, NSPH);
     float *s_contrib = s_warp + wib * per_warp;              // [32][4 control points][4]
     int *s_span = reinterpret_cast<int *>(s_contrib + 32 * 16);
     float *s_acc = s_contrib + 32 * 16 + 32;                 // [K][4]
+    // per sphere s the lane's entries sit at [s * 32 + lane] (no bank conflicts)
+    float *s_h = s_acc + 4 * a.K + lane;
+    float *s_z = s_h + NSPH * 32, *s_dx = s_z + NSPH * 32, *s_dy = s_dx + NSPH * 32, *s_dz = s_dy + NSPH * 32;
     const double reach = (double)m.r_max + (double)a.margin + (double)kSmoothCut * a.beta;
     for (int i = threadIdx.x; i < sc.n_cyl; i += blockDim.x) {
         const float4 f = sc.cyl_filt[i], e = sc.cyl_exact[i];
@@ -167,20 +175,20 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
 #pragma unroll
             for (int s = 0; s < NSPH; ++s) {
                 const float h = X[s];
+                s_h[s * 32] = h;
+                s_z[s * 32] = Z[s];
+                s_dx[s * 32] = 0.f;
+                s_dy[s * 32] = 0.f;
+                s_dz[s * 32] = 0.f;
                 X[s] = __fmul_rn(c1, h);
                 Y[s] = __fmul_rn(s1, h);
             }
-            // Registers feed the unrolled filter; the per-thread arrays below (local memory)
-            // feed the rolled exact path, so that one copy of the distance, gradient and
-            // softplus code serves every sphere (unrolled it outgrows the instruction cache).
-            float4 sph[NSPH];   // {x, y, z, T}
-            float3 dp[NSPH];
+            // Registers feed the unrolled filter; the shared per-lane entries (h, z, d pen / d
+            // centre) feed the rolled exact path, so that one copy of the distance, gradient
+            // and softplus code serves every sphere (unrolled it outgrows the instruction
+            // cache) without per-thread local arrays.
 #pragma unroll
-            for (int s = 0; s < NSPH; ++s) {
-                T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
-                sph[s] = make_float4(X[s], Y[s], Z[s], T[s]);
-                dp[s] = make_float3(0.f, 0.f, 0.f);
-            }
+            for (int s = 0; s < NSPH; ++s) T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
             float2 X2[NSPH / 2], Y2[NSPH / 2];
 #pragma unroll
             for (int p = 0; p < NSPH / 2; ++p) {
@@ -215,12 +223,22 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                     const float4 e = s_exact[o];
 #pragma unroll 1
                     for (int s = 0; s < m.n_spheres; ++s) {
-                        const float4 c = sph[s];
-                        if (fmaf(-2.f * c.x, f.x, fmaf(-2.f * c.y, f.y, f.z)) < c.w) {
-                            const float sd = sdf_cylinder(c.x, c.y, c.z, f.x, f.y, e) - m.sph[s].radius;
-                            const float3 gr = GRAD ? sdf_cylinder_grad(c.x, c.y, c.z, f.x, f.y, e)
+                        const float h = s_h[s * 32];
+                        const float cx = __fmul_rn(c1, h), cy = __fmul_rn(s1, h);
+                        const float cw = kFilterMargin - fmaf(cx, cx, cy * cy);
+                        if (fmaf(-2.f * cx, f.x, fmaf(-2.f * cy, f.y, f.z)) < cw) {
+                            const float cz = s_z[s * 32];
+                            const float sd = sdf_cylinder(cx, cy, cz, f.x, f.y, e) - m.sph[s].radius;
+                            const float3 gr = GRAD ? sdf_cylinder_grad(cx, cy, cz, f.x, f.y, e)
                                                    : make_float3(0.f, 0.f, 0.f);
-                            pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, dp[s]);
+                            float3 d = make_float3(0.f, 0.f, 0.f);
+                            if (GRAD) d = make_float3(s_dx[s * 32], s_dy[s * 32], s_dz[s * 32]);
+                            pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, d);
+                            if (GRAD) {
+                                s_dx[s * 32] = d.x;
+                                s_dy[s * 32] = d.y;
+                                s_dz[s * 32] = d.z;
+                            }
                         }
                     }
                 }
@@ -236,12 +254,20 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                 const float4 cb = s_bc[o], hb = s_bh[o];
 #pragma unroll 1
                 for (int s = 0; s < m.n_spheres; ++s) {
-                    const float4 c = sph[s];
-                    const float sd = sdf_box(c.x, c.y, c.z, cb, hb) - m.sph[s].radius;
+                    const float h = s_h[s * 32];
+                    const float cx = __fmul_rn(c1, h), cy = __fmul_rn(s1, h), cz = s_z[s * 32];
+                    const float sd = sdf_box(cx, cy, cz, cb, hb) - m.sph[s].radius;
                     if (sd < a.margin + kSmoothCut * a.beta) {
-                        const float3 gr = GRAD ? sdf_box_grad(c.x, c.y, c.z, cb, hb)
+                        const float3 gr = GRAD ? sdf_box_grad(cx, cy, cz, cb, hb)
                                                : make_float3(0.f, 0.f, 0.f);
-                        pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, dp[s]);
+                        float3 d = make_float3(0.f, 0.f, 0.f);
+                        if (GRAD) d = make_float3(s_dx[s * 32], s_dy[s * 32], s_dz[s * 32]);
+                        pair_term<GRAD>(sd, gr, a.margin, a.beta, pen, d);
+                        if (GRAD) {
+                            s_dx[s * 32] = d.x;
+                            s_dy[s * 32] = d.y;
+                            s_dz[s * 32] = d.z;
+                        }
                     }
                 }
                 }
@@ -265,7 +291,7 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                     const float L = fmaf(sp.gamma, q.w, sp.beta);
                     const float u = fmaf(sp.alpha, s2, L * s23);     // d h / d q2 = -u
                     const float hz = fmaf(sp.alpha, c2, L * c23);    // horizontal reach
-                    const float3 d = dp[s];
+                    const float3 d = make_float3(s_dx[s * 32], s_dy[s * 32], s_dz[s * 32]);
                     r0 += fmaf(-d.x, Y[s], d.y * X[s]);
                     r1 += fmaf(d.x, -c1 * u, fmaf(d.y, -s1 * u, d.z * hz));
                     r2 += L * fmaf(d.x, -c1 * s23, fmaf(d.y, -s1 * s23, d.z * c23));
@@ -346,27 +372,36 @@ __global__ void k_axpy(float *x, const float *y, float alpha, int64_t n)
     if (i < n) x[i] = fmaf(-alpha, y[i], x[i]);
 }
 
-size_t smooth_smem(int n_cyl, int n_box, int S, int K)
+size_t smooth_smem(int n_cyl, int n_box, int S, int K, int nsph, int threads)
 {
     return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S +
                              (size_t)n_groups(n_cyl)) +
-           sizeof(float) * (kSmoothThreads / 32) * (size_t)(32 * 16 + 32 + 4 * K);
+           sizeof(float) * (size_t)(threads / 32) * (size_t)smooth_warp_floats(K, nsph);
 }
 
 template <bool GRAD>
 int launch_smooth_t(const ModelDev &m, const SceneDev &sc, const SmoothArgs &a, int num_sms,
                     cudaStream_t st)
 {
-    const size_t smem = smooth_smem(sc.n_cyl, sc.n_box, a.S, a.K);
+    const int nsph = m.n_spheres == 12 ? 12 : 16;
+    int dev = 0, optin = 0;
+    CP_CUDA(cudaGetDevice(&dev));
+    CP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    // the largest CTA (512, 256 or 128 threads) whose shared memory fits: the obstacle
+    // tables are staged once per CTA, so larger CTAs leave room for more warps per SM
+    int threads = kSmoothMaxThreads;
+    while (threads > 128 && smooth_smem(sc.n_cyl, sc.n_box, a.S, a.K, nsph, threads) > (size_t)optin)
+        threads /= 2;
+    const size_t smem = smooth_smem(sc.n_cyl, sc.n_box, a.S, a.K, nsph, threads);
     auto kern = m.n_spheres == 12 ? k_smooth<12, GRAD> : k_smooth<16, GRAD>;
     CP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmoothThreads, smem));
+    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) per_sm = 1;
     const int units = a.n * a.groups;
-    int grid = (units + kSmoothThreads / 32 - 1) / (kSmoothThreads / 32);
+    int grid = (units + threads / 32 - 1) / (threads / 32);
     if (grid > num_sms * per_sm) grid = num_sms * per_sm;
-    kern<<<grid, kSmoothThreads, smem, st>>>(m, sc, a);
+    kern<<<grid, threads, smem, st>>>(m, sc, a);
     CP_LAUNCHED("k_smooth");
     if (a.groups > 1) {
         k_smooth_reduce<<<(a.n * 32 + 255) / 256, 256, 0, st>>>(a.n, a.groups, a.K, a.part_J, a.part_g,
@@ -378,7 +413,8 @@ int launch_smooth_t(const ModelDev &m, const SceneDev &sc, const SmoothArgs &a, 
 
 }  // namespace
 
-size_t smooth_smem_bytes(int n_cyl, int n_box, int S, int K) { return smooth_smem(n_cyl, n_box, S, K); }
+// Shared memory of the smallest launch (128 threads, 16 spheres): the scene fits if this does.
+size_t smooth_smem_bytes(int n_cyl, int n_box, int S, int K) { return smooth_smem(n_cyl, n_box, S, K, 16, 128); }
 
 // Chunk groups per candidate: enough units for about 32 warps per SM when candidates are
 // few, at most the number of chunks; the partial buffers hold smooth_partial_units() units.
