@@ -301,12 +301,14 @@ def run_ours(args):
     clk = clocks.summary()
     candidates = args.steps * (wl.n_candidates * iters + 1)
     roofline_exhaustive = None
+    peaks_fp64 = None
     form = "grid" if wl.grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
     roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
                              candidates, form, clk.get("sm_mhz"))
     if roofline is not None:
         roofline["traffic"] = traffic_per_launch() if form == "broad" else None
         peaks = cp.cp_alu_peaks()
+        peaks_fp64 = peaks["fp64_tflops"]
         roofline["measured_fma_peaks"] = peaks
         roofline["frac_of_measured_fp32"] = roofline["achieved"] / peaks["fp32_tflops"]
     if wl.grid_cell <= 0:
@@ -339,6 +341,7 @@ def run_ours(args):
                             "ms_per_launch": eval_ms, "launches": timing["eval_launches"]},
             "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
                                   for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},
+            "fp64_stages": fp64_stages(timing, wl, peaks_fp64),
             "plan_result": {"J": stats["J"], "length": stats["length"], "flag": stats["flag"]},
             "clocks": clk,
         }
@@ -348,6 +351,27 @@ def run_ours(args):
     planner.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def fp64_stages(timing, wl, fp64_peak):
+    """The FP64 stages against the measured FP64 FMA rate: the Cholesky factor (D^3/3 FMAs per
+    iteration) and the update (nu D(D+1)/2 FMAs for the covariance plus nu D for the mean),
+    FMA = 2 flops."""
+    if not fp64_peak or timing["factor_launches"] <= 0 or timing["update_launches"] <= 0:
+        return None
+    D = 4 * wl.n_waypoints
+    nu = wl.n_candidates // 2
+    f_factor = 2.0 * D ** 3 / 3.0
+    f_update = 2.0 * (nu * D * (D + 1) / 2.0 + nu * D)
+    ms_f = timing["factor_ms"] / timing["factor_launches"]
+    ms_u = timing["update_ms"] / timing["update_launches"]
+    out = {}
+    for name, fl, ms in (("factor", f_factor, ms_f), ("update", f_update, ms_u)):
+        achieved = fl / (ms / 1e3) / 1e12
+        out[name] = {"bound": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "peak_basis": "cp_alu_peaks (measured FP64 FMA rate)",
+                     "us_per_call": ms * 1e3}
+    return out
 
 
 def exhaustive_roofline(cp, crane, scene, wl, q0, qd, sm_mhz, iterations=10):
@@ -535,8 +559,36 @@ def run_batch(args):
             "gpu_launches": launches, "clocks": clocks.summary(),
             "e2e": {"value": units / (ms / 1e3), "unit": "candidate paths/s",
                     "h2d_bytes_per_step": 64 * 64, "d2h_bytes_per_step": 64 * 8 * 168}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(crane, queries, q0s, qds, rank, S, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     cp.cp_batch_destroy(b)
+
+
+def batch_cpu_baseline(crane, queries, q0s, qds, seed, S, seconds):
+    """The FP64 oracle on a bounded sample of the batch: candidate evaluations of every
+    eighth query in turn (each with its own scene and sizes) until `seconds` have passed."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    from paper_2503_14160_gb300 import workloads
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    done, t0, picked = 0, time.perf_counter(), list(range(0, len(queries), 8))
+    while True:
+        for q in picked:
+            bq = queries[q]
+            sc = workloads.batch_scene(bq, seed=seed, q=q)
+            problem = oracle.Problem(crane, sc, oracle.CostParams(K=bq.n_waypoints, S=S))
+            xi = workloads.random_candidates(q0s[q], qds[q], bq.n_waypoints, 2 * cores, seed=q)
+            oracle.evaluate(problem, xi.astype(np.float64), q0s[q], qds[q])
+            done += xi.shape[0]
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": "candidate paths/s", "cores": int(oracle.get_threads()),
+            "kind": "oracle", "seconds": el,
+            "sample": "%d candidate evaluations (FP64, OpenMP over candidates) of queries %s of "
+                      "the batch, each with its own scene and sizes" % (done, picked)}
 
 
 def cpu_baseline(wl, crane, scene, q0, qd, seconds, max_batches=None):
