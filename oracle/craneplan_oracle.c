@@ -23,6 +23,7 @@
  *   o_path_cost_batch   the same for N candidates (Algorithm 1 step (2)); OpenMP over candidates
  *   o_smooth_cost       the softplus-penalty variant of J used by the differentiable form
  *   o_smooth_grad       its analytic gradient with respect to the K free control points
+ *   o_ik_residual       residual and Jacobian of the collision-free IK (Sec. 3.2, Eq. IK opt)
  *
  * Readings of the paper that the code depends on (the paper is silent or garbled here):
  *   chain   slew q1 about world z; boom pitch q2 (elevation from horizontal); jib pitch q3
@@ -591,6 +592,68 @@ void o_smooth_grad_batch(const o_model *m, const o_scene *sc, const o_cost_param
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < n; ++i)
         o_smooth_grad(m, sc, cp, xi + i * 4 * cp->K, q0, qd, grad + i * 4 * cp->K);
+}
+
+/* ------------------------------------------------------------------ collision-free IK */
+
+/* Residual of the collision-free IK of Sec. 3.2 (Eq. IK opt) at q for the target
+ * (x, y, z, psi) and its Jacobian with respect to q (jac[5][4], may be NULL):
+ *   r[0..2] = p_g - p_d, with p_g = T - (0, 0, grapple_len) the grapple centre (plumb);
+ *   r[3]    = lambda_q Log(R_d^T R_g): the grapple hangs plumb, so R_g = Rz(q1) and the log
+ *             map has one component, the angle q1 - psi wrapped to [-pi, pi];
+ *   r[4]    = lambda_c max(0, -d(q));
+ *   r_e     = 0 identically (the passive joints are at their equilibrium by the chain's
+ *             reading), so it is not a row.
+ * d/dq of r[4] is -lambda_c times the gradient of the pair that attains d(q) (the first
+ * minimum in the order spheres, then cylinders, then boxes) when d < 0, else 0. */
+void o_ik_residual(const o_model *m, const o_scene *sc, const double q[4], const double target[4],
+                   double lambda_q, double lambda_c, double grapple_len, double r[5], double *jac)
+{
+    double centres[3 * O_MAX_SPHERES], T[3];
+    o_fk(m, q, centres, NULL, T);
+    r[0] = T[0] - target[0];
+    r[1] = T[1] - target[1];
+    r[2] = T[2] - grapple_len - target[2];
+    r[3] = lambda_q * remainder(q[0] - target[3], 2.0 * M_PI);
+    double d = HUGE_VAL;
+    int s_min = -1, o_min = -1;   /* o_min >= n_cyl: box o_min - n_cyl */
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const double *p = centres + 3 * s;
+        for (int o = 0; o < sc->n_cyl; ++o) {
+            const double v = o_sdf_cylinder(p, sc->cyl + 5 * o) - m->radius[s];
+            if (v < d) { d = v; s_min = s; o_min = o; }
+        }
+        for (int o = 0; o < sc->n_box; ++o) {
+            const double v = o_sdf_box(p, sc->box + 6 * o) - m->radius[s];
+            if (v < d) { d = v; s_min = s; o_min = sc->n_cyl + o; }
+        }
+    }
+    r[4] = lambda_c * fmax(0.0, -d);
+    if (!jac) return;
+    double sj[12 * O_MAX_SPHERES];
+    fk_jacobian(m, q, sj);
+    /* the tip T is the link-3 point at offset 0: O + L_b e_b + (L_j + q4) e_j */
+    const double c1 = cos(q[0]), s1 = sin(q[0]), c2 = cos(q[1]), s2 = sin(q[1]);
+    const double c23 = cos(q[1] + q[2]), s23 = sin(q[1] + q[2]);
+    const double Lb = m->boom_len, L = m->jib_len + q[3];
+    const double dT[3][4] = {
+        {-s1 * (Lb * c2 + L * c23), -c1 * (Lb * s2 + L * s23), -c1 * L * s23, c1 * c23},
+        {c1 * (Lb * c2 + L * c23), -s1 * (Lb * s2 + L * s23), -s1 * L * s23, s1 * c23},
+        {0.0, Lb * c2 + L * c23, L * c23, s23}};
+    for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 4; ++j) jac[4 * c + j] = dT[c][j];
+    jac[12] = lambda_q;
+    jac[13] = jac[14] = jac[15] = 0.0;
+    for (int j = 0; j < 4; ++j) jac[16 + j] = 0.0;
+    if (d < 0.0 && s_min >= 0) {
+        double g[3];
+        const double *p = centres + 3 * s_min;
+        if (o_min < sc->n_cyl) sdf_cylinder_grad(p, sc->cyl + 5 * o_min, g);
+        else sdf_box_grad(p, sc->box + 6 * (o_min - sc->n_cyl), g);
+        const double *J = sj + 12 * s_min;
+        for (int j = 0; j < 4; ++j)
+            jac[16 + j] = -lambda_c * (g[0] * J[j] + g[1] * J[4 + j] + g[2] * J[8 + j]);
+    }
 }
 
 /* ------------------------------------------------------------------ threads */

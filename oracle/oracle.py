@@ -17,6 +17,10 @@ written here with numpy, one function per step, in the paper's order and notatio
   update             steps (5) and (6): mu <- sum_j w_j x_(j);
                      C <- sum_j w_j (x_(j) - mu)(x_(j) - mu)^T + eps I  (new mu)
   plan               the loop of Algorithm 1 for a fixed number of iterations
+  ik_residual        the residual of the collision-free IK (Sec. 3.2, Eq. IK opt) and its
+                     Jacobian, through the C oracle
+  ik_solve           damped Gauss-Newton (Levenberg-Marquardt) on Eq. IK opt from one start
+  ik_solve_best      the best of several Philox starting points
 
 Readings where the paper is silent: sigma = 1; C_0 = diag((0.1 (q_max - q_min))^2) per
 free control point; nu = floor(N/2); eps = 1e-8; w_c = w_l = 100; lambda_c = 1; the
@@ -98,6 +102,8 @@ def lib():
         L.o_smooth_grad_batch.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Scene),
                                           ctypes.POINTER(_CostParams), dp, ctypes.c_int64,
                                           dp, dp, dp]
+        L.o_ik_residual.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Scene), dp, dp,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
         L.o_set_threads.argtypes = [ctypes.c_int32]
         L.o_get_threads.restype = ctypes.c_int32
         _lib = L
@@ -382,3 +388,82 @@ def plan(problem: Problem, sp: SearchParams, q0, qd, iterations: int,
     mean_J.append(float(final.J[0]))
     P = np.concatenate([np.tile(q0, (4, 1)), mu.reshape(sp.K, 4), np.tile(qd, (4, 1))])
     return PlanResult(mu.reshape(sp.K, 4), C, P, np.asarray(best), np.asarray(mean_J), final)
+
+
+# --------------------------------------------------------------------------- collision-free IK
+
+@dataclasses.dataclass
+class IKParams:
+    """Scales of the residual of Eq. IK opt (Sec. 3.2) and the solver's settings."""
+    lambda_q: float = 1.0       # m per rad of yaw error
+    lambda_c: float = 1.0       # scale of r_c = lambda_c max(0, -d)
+    grapple_len: float = 1.0    # the grapple centre hangs this far below the tip (m)
+    mu0: float = 1e-3           # initial damping
+    seed: int = 0               # Philox key of the starting points
+
+
+IK_TAG = 0x494B5354             # third Philox counter word of the IK starting points
+
+
+def ik_residual(problem: Problem, q, target, ik: IKParams, jacobian: bool = True):
+    """r (5) and, if asked, dr/dq (5 x 4) of Eq. IK opt at q for target (x, y, z, psi)."""
+    r = np.zeros(5)
+    J = np.zeros((5, 4)) if jacobian else None
+    lib().o_ik_residual(ctypes.byref(problem.model), ctypes.byref(problem.scene), _dp(_c64(q)),
+                        _dp(_c64(target)), ik.lambda_q, ik.lambda_c, ik.grapple_len, _dp(r),
+                        _dp(J) if J is not None else None)
+    return r, J
+
+
+def ik_start(problem: Problem, ik: IKParams, target_index: int, restart: int, query: int = 0):
+    """Starting configuration `restart` of target `target_index`: four uniforms from one
+    Philox4x32-10 block (counter (restart, target, tag, query), key = seed), top 24 bits of
+    each word, spread over the joint limits."""
+    ctr = np.array([[restart, target_index, IK_TAG, query]], dtype=np.uint32)
+    key = (int(ik.seed) & 0xFFFFFFFF, (int(ik.seed) >> 32) & 0xFFFFFFFF)
+    w = philox4x32_10(ctr, key)[0]
+    u = (w >> 8).astype(np.float64) * 2.0 ** -24
+    lo = np.array(problem.model_py.q_min, dtype=np.float64)
+    hi = np.array(problem.model_py.q_max, dtype=np.float64)
+    return lo + u * (hi - lo)
+
+
+def ik_solve(problem: Problem, target, q_start, iters: int, ik: IKParams):
+    """Damped Gauss-Newton (Levenberg-Marquardt) on Eq. IK opt from q_start, the steps in
+    order: H = J^T J, g = J^T r; solve (H + mu (diag H + 1e-6)) s = -g; q' = clip(q + s)
+    to the joint limits; accept q' when |r(q')|^2 < |r(q)|^2 (then mu /= 3, floor 1e-12),
+    else mu *= 4 (cap 1e12). Returns (q, |r|^2, history of |r|^2 after each iteration)."""
+    lo = np.array(problem.model_py.q_min, dtype=np.float64)
+    hi = np.array(problem.model_py.q_max, dtype=np.float64)
+    q = np.clip(_c64(q_start), lo, hi)
+    mu = ik.mu0
+    r, J = ik_residual(problem, q, target, ik)
+    f = float(r @ r)
+    hist = []
+    for _ in range(iters):
+        H = J.T @ J
+        g = J.T @ r
+        A = H + mu * np.diag(np.diag(H) + 1e-6)
+        step = -np.linalg.solve(A, g)
+        q_new = np.clip(q + step, lo, hi)
+        r_new, J_new = ik_residual(problem, q_new, target, ik)
+        f_new = float(r_new @ r_new)
+        if f_new < f:
+            q, r, J, f = q_new, r_new, J_new, f_new
+            mu = max(mu / 3.0, 1e-12)
+        else:
+            mu = min(mu * 4.0, 1e12)
+        hist.append(f)
+    return q, f, hist
+
+
+def ik_solve_best(problem: Problem, target, target_index: int, restarts: int, iters: int,
+                  ik: IKParams, query: int = 0):
+    """The best of `restarts` solves from the Philox starting points (lowest |r|^2, ties to
+    the lower restart index): (q, |r|^2, restart)."""
+    best = None
+    for s in range(restarts):
+        q, f, _ = ik_solve(problem, target, ik_start(problem, ik, target_index, s, query), iters, ik)
+        if best is None or f < best[1]:
+            best = (q, f, s)
+    return best
