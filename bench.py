@@ -490,6 +490,199 @@ def run_differentiable(args):
     planner.close()
 
 
+IK_TARGETS, IK_RESTARTS, IK_ITERS = 16384, 8, 50
+IK_FLOPS_PER_EVAL = 150     # kinematics of 12 spheres and the tip, residual, Jacobian rows
+IK_FLOPS_PER_OBSTACLE = 4   # plane test of one obstacle (fma, mul, square, compare)
+IK_FLOPS_PER_SOLVE = 200    # J^T J, J^T r, damping, 4x4 Cholesky and two substitutions
+
+
+def ik_flops(n_obstacles, restarts, iters):
+    """FP32 operations of one target's solve, counting the evaluations (iters + 1 per
+    start) and the damped solves (iters per start); the distances of the pairs that pass
+    the plane test are left out, so this is a lower bound."""
+    per_eval = IK_FLOPS_PER_EVAL + IK_FLOPS_PER_OBSTACLE * n_obstacles
+    return restarts * ((iters + 1) * per_eval + iters * IK_FLOPS_PER_SOLVE)
+
+
+def ik_oracle_sample(crane, scene, targets, restarts, iters, seconds, seed):
+    """The FP64 oracle's IK (best of `restarts` Levenberg-Marquardt solves) on the targets
+    in turn until `seconds` have passed; solves per second."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    pb = oracle.Problem(crane, scene, oracle.CostParams(K=1, S=1))
+    oik = oracle.IKParams(seed=seed)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.ik_solve_best(pb, targets[done % targets.shape[0]], done % targets.shape[0],
+                             restarts, iters, oik)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": "IK solves/s", "cores": 1, "kind": "oracle",
+            "seconds": el,
+            "sample": "%d FP64 IK solves (%d starts x %d LM iterations, %d cylinders), "
+                      "one thread" % (done, restarts, iters, scene.n_cyl)}
+
+
+def ik_config(scene):
+    return {"workload": "ik: %d grasp poses (grapple centre of a collision-free configuration, "
+                        "clearance 0.05 m, height -0.5..1.5 m, yaw = slew) among %d trees, "
+                        "%d starts x %d LM iterations each"
+                        % (IK_TARGETS, scene.n_cyl, IK_RESTARTS, IK_ITERS),
+            "step": "one cp_ik launch over all targets",
+            "l2": "flushed between steps (256 MB write)"}
+
+
+def ik_targets_gpu(cp, h, crane, n, seed, grapple_len=1.0):
+    """Grasp poses drawn with the library's own distance and kinematics."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+
+    def tips(q):
+        qt = torch.from_numpy(np.ascontiguousarray(q, np.float32)).cuda()
+        t = torch.zeros(q.shape[0], 3, device="cuda")
+        cp.cp_forward_kinematics(h, qt, q.shape[0], None, t)
+        return qt, t
+
+    def accept(q):
+        qt, t = tips(q)
+        d = torch.zeros(q.shape[0], device="cuda")
+        cp.cp_signed_distance(h, qt, q.shape[0], d)
+        zg = t[:, 2] - grapple_len
+        ok = (d > workloads.GRASP_CLEARANCE) & (zg > workloads.GRASP_Z[0]) & (zg < workloads.GRASP_Z[1])
+        return ok.cpu().numpy()
+
+    q = workloads.grasp_configurations(crane, accept, n, seed=seed)
+    _, t = tips(q)
+    t = t.cpu().numpy().astype(np.float64)
+    return np.column_stack([t[:, 0], t[:, 1], t[:, 2] - grapple_len, q[:, 0]])
+
+
+def ik_targets_oracle(crane, scene, n, seed, grapple_len=1.0):
+    """The same draw with the oracle's distance and kinematics (reference arm)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    from paper_2503_14160_gb300 import workloads
+    pb = oracle.Problem(crane, scene, oracle.CostParams(K=1, S=1))
+
+    def accept(q):
+        zg = oracle.fk_tips(pb, q)[:, 2] - grapple_len
+        return ((oracle.signed_distance(pb, q) > workloads.GRASP_CLEARANCE)
+                & (zg > workloads.GRASP_Z[0]) & (zg < workloads.GRASP_Z[1]))
+
+    q = workloads.grasp_configurations(crane, accept, n, seed=seed)
+    T = oracle.fk_tips(pb, q)
+    return np.column_stack([T[:, 0], T[:, 1], T[:, 2] - grapple_len, q[:, 0]])
+
+
+def run_ik(args):
+    """Batched collision-free IK (Sec. 3.2): IK solves per second for a batch of grasp poses."""
+    import torch
+    from paper_2503_14160_gb300 import build, craneplan as cp, workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    cp.load()
+    crane = workloads.forestry_crane()
+    scene = workloads.make_scene(workloads.WORKLOADS[workloads.IK_SCENE])
+    planner = cp.Planner(crane, scene, cp.make_params(64, 2, 2))
+    h = planner.handle
+    n, iters = IK_TARGETS, args.iterations or IK_ITERS
+    ik = cp.make_ik_params(seed=rank, query=rank, restarts=IK_RESTARTS, iters=iters)
+    targets_np = ik_targets_gpu(cp, h, crane, n, seed=rank)
+    targets = torch.from_numpy(targets_np.astype(np.float32)).cuda()
+    q = torch.zeros(n, 4, device="cuda")
+    f = torch.zeros(n, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        cp.cp_ik(h, targets, n, ik, q, f)
+    torch.cuda.synchronize()
+    times = []
+    l0 = cp.cp_launch_count()
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cp.cp_ik(h, targets, n, ik, q, f)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+    launches = cp.cp_launch_count() - l0
+    ms = float(np.mean(times))
+    fv = f.cpu().numpy()
+    # end to end: targets in from pinned host memory, configurations and costs out
+    host_t = targets.cpu().pin_memory()
+    host_q = torch.empty_like(q, device="cpu").pin_memory()
+    host_f = torch.empty_like(f, device="cpu").pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        targets.copy_(host_t, non_blocking=True)
+        cp.cp_ik(h, targets, n, ik, q, f)
+        host_q.copy_(q, non_blocking=True)
+        host_f.copy_(f, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    peaks = cp.cp_alu_peaks()
+    flops = n * ik_flops(scene.n_cyl + scene.n_box, IK_RESTARTS, iters)
+    achieved = flops / (ms / 1e3) / 1e12
+    line = {"metric": "collision-free IK solves/sec (Sec. 3.2), batched",
+            "value": n / (ms / 1e3), "unit": "IK solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded grasp poses in the crane-and-forest scene)",
+            "config": ik_config(scene),
+            "solved_fraction": float(np.mean(fv < 1e-6)),
+            "median_residual_sq": float(np.median(fv)),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"],
+                         "unit": "TFLOP/s", "frac": achieved / peaks["fp32_tflops"],
+                         "traffic": None,
+                         "peak_source": "FP32 FMA rate measured by cp_alu_peaks on this GPU",
+                         "kernel": "k_ik<12>",
+                         "flops_note": "lower bound: kinematics, plane tests and 4x4 solves; "
+                                       "pair distances of surviving obstacles not counted"},
+            "e2e": {"value": n / (float(np.mean(e2e)) / 1e3), "unit": "IK solves/s",
+                    "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 20},
+            "gpu_launches": launches, "clocks": clocks.summary()}
+    if not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = ik_oracle_sample(crane, scene, targets_np, IK_RESTARTS, iters,
+                                                args.cpu_seconds, rank)
+    print(json.dumps(line), flush=True)
+    planner.close()
+
+
+def run_ik_reference(args):
+    from paper_2503_14160_gb300 import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    crane = workloads.forestry_crane()
+    scene = workloads.make_scene(workloads.WORKLOADS[workloads.IK_SCENE])
+    iters = args.iterations or IK_ITERS
+    targets = ik_targets_oracle(crane, scene, 256, seed=0)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        r = ik_oracle_sample(crane, scene, targets, IK_RESTARTS, iters, args.cpu_seconds / 4, 0)
+        if i >= args.warmup:
+            per_step.append(r)
+    value = float(np.mean([r["value"] for r in per_step]))
+    line = {"metric": "collision-free IK solves/sec (Sec. 3.2), batched", "value": value,
+            "unit": "IK solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean([r["seconds"] for r in per_step])) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded grasp poses in the crane-and-forest scene)",
+            "impl": "reference", "config": ik_config(scene),
+            "cpu_baseline": {"value": value, "unit": "IK solves/s", "cores": 1, "kind": "oracle",
+                             "sample": per_step[0]["sample"]},
+            "e2e": {"value": value, "unit": "IK solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """The batched serving form: 64 queries of uneven size (N ~ U[1024, 16384], K ~ U[8, 32],
     M ~ U[50, 3000] cylinders, S = 64, 100 iterations) planned by one graph launch, against the
@@ -667,8 +860,12 @@ def main():
     ap.add_argument("--exhaustive", action="store_true",
                     help="evaluate every sphere against every obstacle (no broad phase)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload == "ik":
+        run_ik_reference(args)
+    elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ik":
+        run_ik(args)
     elif args.workload == "differentiable":
         run_differentiable(args)
     elif args.workload == "batch":

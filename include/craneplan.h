@@ -239,6 +239,54 @@ int cp_plan(cp_planner *p, int32_t iters, double *h_ctrl, cp_plan_stats *stats);
  * device); +inf for an empty scene. Errors: CP_ERR_ARG. */
 int cp_signed_distance(cp_planner *p, const float *d_q, int32_t n, float *d_d);
 
+/* Forward kinematics of Sec. 2 (Eq. FK) for n configurations d_q (float[n][4], device,
+ * 16-byte aligned): the link-sphere centres d_centres (float[n][n_spheres][3], or NULL) by
+ * the placement rule of cp_model, and the tip T = O + boom_len e_b + (jib_len + q4) e_j
+ * (float[n][3], or NULL); the grapple centre hangs plumb below T. FP32, asynchronous on
+ * the planner's stream. Errors: CP_ERR_ARG (n < 0, NULL or misaligned d_q). */
+int cp_forward_kinematics(cp_planner *p, const float *d_q, int32_t n, float *d_centres, float *d_tip);
+
+/* Collision-free inverse kinematics of Sec. 3.2 (Eq. IK opt), batched: for each target
+ * pose (x, y, z, psi) the configuration q that minimises |r(q)|^2 with
+ *   r[0..2] = p_g(q) - (x, y, z)      p_g = the grapple centre, grapple_len below the tip
+ *                                     (the passive joints hang plumb at equilibrium, so the
+ *                                     equilibrium residual r_e is zero and not a row);
+ *   r[3]    = lambda_q * wrap(q1 - psi)  the grapple's orientation is Rz(q1), so the SO(3)
+ *                                     log of R_d^T R_g is the yaw error wrapped to [-pi, pi];
+ *   r[4]    = lambda_c * max(0, -d(q))  d(q) the signed distance of Sec. 3.1.
+ * Solver: damped Gauss-Newton (Levenberg-Marquardt): solve (H + mu (diag H + 1e-6)) s = -g
+ * with H = J^T J and g = J^T r, clip q + s to the joint limits, accept when |r|^2
+ * decreases (mu / 3, floor 1e-12), else mu * 4 (cap 1e12); `iters` iterations from each of
+ * `restarts` starting points, the best (lowest |r|^2, the lower start on ties) kept. Start
+ * k of target t is four uniforms of one Philox4x32-10 block, counter (k, t, 0x494B5354,
+ * query), key = seed, top 24 bits of each word spread over the joint limits; with
+ * d_q_init non-NULL start 0 is d_q_init[t] instead (a warm start). Arithmetic is FP32.
+ * Arguments (device pointers, row-major, owned by the caller; d_targets, d_q_init and d_q
+ * 16-byte aligned, each row read or written as one 16-byte word):
+ *   d_targets   float[n][4]   x, y, z (m) and psi (rad)
+ *   d_q_init    float[n][4]   or NULL
+ *   d_q         float[n][4]   result
+ *   d_f         float[n]      |r(q)|^2 at the result
+ *   d_restart   int32[n]      or NULL: the start that won
+ *   d_r         float[n][5]   or NULL: r at the result
+ * A NaN target gives a NaN |r|^2 (ranked last among the starts). Asynchronous on the
+ * planner's stream. Errors: CP_ERR_ARG (n < 0, restarts outside 1..CP_IK_MAX_RESTARTS,
+ * iters < 0, a negative scale or grapple length, mu0 <= 0, NULL or misaligned buffers). */
+#define CP_IK_MAX_RESTARTS 1024
+typedef struct cp_ik_params {
+    double lambda_q;      /* m per rad of yaw error */
+    double lambda_c;      /* scale of the collision residual */
+    double grapple_len;   /* tip to grapple centre (m) */
+    double mu0;           /* initial damping */
+    uint64_t seed;        /* Philox key of the starting points */
+    uint32_t query;       /* fourth Philox counter word: separates batches */
+    int32_t restarts;
+    int32_t iters;
+} cp_ik_params;
+
+int cp_ik(cp_planner *p, const float *d_targets, int32_t n, const cp_ik_params *ik,
+          const float *d_q_init, float *d_q, float *d_f, int32_t *d_restart, float *d_r);
+
 /* Copy the current mean (double[D]) and covariance (double[D][D]) to device buffers
  * (either may be NULL). */
 int cp_get_distribution(const cp_planner *p, double *d_mu, double *d_C);

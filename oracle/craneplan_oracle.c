@@ -24,6 +24,7 @@
  *   o_smooth_cost       the softplus-penalty variant of J used by the differentiable form
  *   o_smooth_grad       its analytic gradient with respect to the K free control points
  *   o_ik_residual       residual and Jacobian of the collision-free IK (Sec. 3.2, Eq. IK opt)
+ *   o_fk_tip_batch      the tip of o_fk for many configurations
  *
  * Readings of the paper that the code depends on (the paper is silent or garbled here):
  *   chain   slew q1 about world z; boom pitch q2 (elevation from horizontal); jib pitch q3
@@ -224,6 +225,13 @@ double o_signed_distance(const o_model *m, const o_scene *sc, const double q[4])
             d = fmin(d, o_sdf_box(p, sc->box + 6 * o) - m->radius[s]);
     }
     return d;
+}
+
+/* Tips T of n configurations (o_fk, one after another): tips[n][3]. */
+void o_fk_tip_batch(const o_model *m, const double *q, int64_t n, double *tips)
+{
+    double centres[3 * O_MAX_SPHERES];
+    for (int64_t i = 0; i < n; ++i) o_fk(m, q + 4 * i, centres, NULL, tips + 3 * i);
 }
 
 void o_signed_distance_batch(const o_model *m, const o_scene *sc, const double *q, int64_t n,

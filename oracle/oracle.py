@@ -85,6 +85,7 @@ def lib():
         L.o_normals_batch.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_int32, ctypes.c_int32, dp]
         L.o_fk.argtypes = [ctypes.POINTER(_Model), dp, dp, dp, dp]
+        L.o_fk_tip_batch.argtypes = [ctypes.POINTER(_Model), dp, ctypes.c_int64, dp]
         L.o_sdf_cylinder.argtypes = [dp, dp]
         L.o_sdf_cylinder.restype = ctypes.c_double
         L.o_sdf_box.argtypes = [dp, dp]
@@ -200,6 +201,14 @@ def fk(problem: Problem, q) -> tuple:
     T = np.zeros(3)
     lib().o_fk(ctypes.byref(problem.model), _dp(q), _dp(c), _dp(J), _dp(T))
     return c, J, T
+
+
+def fk_tips(problem: Problem, q) -> np.ndarray:
+    """Tips T[n][3] of configurations q[n][4] (the T of fk, batched)."""
+    q = _c64(q).reshape(-1, 4)
+    T = np.zeros((q.shape[0], 3))
+    lib().o_fk_tip_batch(ctypes.byref(problem.model), _dp(q), q.shape[0], _dp(T))
+    return T
 
 
 def sdf_cylinder(p, cyl) -> float:

@@ -93,6 +93,15 @@ class cp_timing(ctypes.Structure):
                 ("eval_pair_tests", ctypes.c_int64)]
 
 
+class cp_ik_params(ctypes.Structure):
+    _fields_ = [("lambda_q", ctypes.c_double), ("lambda_c", ctypes.c_double),
+                ("grapple_len", ctypes.c_double), ("mu0", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("query", ctypes.c_uint32),
+                ("restarts", ctypes.c_int32), ("iters", ctypes.c_int32)]
+
+
+CP_IK_MAX_RESTARTS = 1024
+
 _P = ctypes.c_void_p
 _SIGS = {
     "cp_last_error": (ctypes.c_char_p, []),
@@ -111,6 +120,9 @@ _SIGS = {
     "cp_plan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(cp_plan_stats)]),
     "cp_signed_distance": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "cp_forward_kinematics": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "cp_ik": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(cp_ik_params), _P, _P, _P,
+                             _P, _P]),
     "cp_get_distribution": (ctypes.c_int, [_P, _P, _P]),
     "cp_set_distribution": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     "cp_get_factor": (ctypes.c_int, [_P, _P]),
@@ -302,6 +314,22 @@ def cp_plan(p: int, iters: int, K: Optional[int] = None):
 
 def cp_signed_distance(p: int, q, n: int, d) -> None:
     _check(load().cp_signed_distance(p, _ptr(q), int(n), _ptr(d)))
+
+
+def cp_forward_kinematics(p: int, q, n: int, centres=None, tip=None) -> None:
+    _check(load().cp_forward_kinematics(p, _ptr(q), int(n), _ptr(centres), _ptr(tip)))
+
+
+def make_ik_params(lambda_q: float = 1.0, lambda_c: float = 1.0, grapple_len: float = 1.0,
+                   mu0: float = 1e-3, seed: int = 0, query: int = 0, restarts: int = 8,
+                   iters: int = 50) -> cp_ik_params:
+    return cp_ik_params(lambda_q, lambda_c, grapple_len, mu0, seed, query, restarts, iters)
+
+
+def cp_ik(p: int, targets, n: int, ik: cp_ik_params, q, f, q_init=None, restart=None,
+          r=None) -> None:
+    _check(load().cp_ik(p, _ptr(targets), int(n), ctypes.byref(ik), _ptr(q_init), _ptr(q),
+                        _ptr(f), _ptr(restart), _ptr(r)))
 
 
 def cp_get_distribution(p: int, mu=None, C=None) -> None:

@@ -215,6 +215,8 @@ ModelDev make_model(const cp_model *m)
         d.sph[s] = l;
     }
     d.r_max = r_max;
+    d.boom_len = (float)m->boom_len;
+    d.jib_len = (float)m->jib_len;
     return d;
 }
 
@@ -817,6 +819,32 @@ int cp_signed_distance(cp_planner *p, const float *d_q, int32_t n, float *d_d)
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     if (n < 0 || (n > 0 && (!d_q || !d_d))) return set_error("invalid arguments"), CP_ERR_ARG;
     return launch_signed_distance(p->mdev, p->sdev, d_q, n, d_d, p->st);
+}
+
+int cp_forward_kinematics(cp_planner *p, const float *d_q, int32_t n, float *d_centres, float *d_tip)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (n < 0 || (n > 0 && !d_q)) return set_error("invalid arguments"), CP_ERR_ARG;
+    if ((uintptr_t)d_q & 15u) return set_error("d_q must be 16-byte aligned"), CP_ERR_ARG;
+    return launch_forward_kinematics(p->mdev, d_q, n, d_centres, d_tip, p->st);
+}
+
+int cp_ik(cp_planner *p, const float *d_targets, int32_t n, const cp_ik_params *ik,
+          const float *d_q_init, float *d_q, float *d_f, int32_t *d_restart, float *d_r)
+{
+    if (!p || !ik) return set_error("NULL argument"), CP_ERR_ARG;
+    if (n < 0 || (n > 0 && (!d_targets || !d_q || !d_f))) return set_error("invalid arguments"), CP_ERR_ARG;
+    if (ik->restarts < 1 || ik->restarts > CP_IK_MAX_RESTARTS)
+        return set_error("restarts must be in 1..%d", CP_IK_MAX_RESTARTS), CP_ERR_ARG;
+    if (ik->iters < 0) return set_error("iters must be >= 0"), CP_ERR_ARG;
+    if (((uintptr_t)d_targets | (uintptr_t)d_q_init | (uintptr_t)d_q) & 15u)
+        return set_error("d_targets, d_q_init and d_q must be 16-byte aligned"), CP_ERR_ARG;
+    if (!(ik->lambda_q >= 0.0) || !(ik->lambda_c >= 0.0) || !(ik->grapple_len >= 0.0) || !(ik->mu0 > 0.0) ||
+        !is_finite(ik->lambda_q) || !is_finite(ik->lambda_c) || !is_finite(ik->grapple_len) || !is_finite(ik->mu0))
+        return set_error("IK scales must be finite and >= 0, mu0 > 0"), CP_ERR_ARG;
+    return launch_ik(p->mdev, p->sdev, d_targets, d_q_init, n, ik->restarts, ik->iters, (float)ik->lambda_q,
+                     (float)ik->lambda_c, (float)ik->grapple_len, (float)ik->mu0, ik->seed, ik->query, d_q, d_f,
+                     d_restart, d_r, p->st);
 }
 
 int cp_get_distribution(const cp_planner *p, double *d_mu, double *d_C)

@@ -49,6 +49,7 @@ struct ModelDev {
     int n_spheres;
     float r_max;                       // largest sphere radius (filter bound)
     SphereLin sph[kMaxSpheres];
+    float boom_len, jib_len;           // L_b and L_j: the tip is O + L_b e_b + (L_j + q4) e_j
 };
 
 // Cylinder records in device memory (float32):
@@ -124,6 +125,12 @@ int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n,
                          double *terms, uint32_t *substep_flags, cudaStream_t st);
 int launch_signed_distance(const ModelDev &m, const SceneDev &sc, const float *q, int n,
                            float *d, cudaStream_t st);
+int launch_ik(const ModelDev &m, const SceneDev &sc, const float *targets, const float *q_init, int n,
+              int restarts, int iters, float lambda_q, float lambda_c, float grapple_len, float mu0,
+              uint64_t seed, uint32_t query, float *q_out, float *f_out, int *restart_out, float *r_out,
+              cudaStream_t st);
+int launch_forward_kinematics(const ModelDev &m, const float *q, int n, float *centres, float *tip,
+                              cudaStream_t st);
 size_t eval_smem_bytes(int n_cyl, int n_box, int S);
 int eval_configure(size_t smem_bytes);
 int eval_ensure_smem(size_t smem_bytes);

@@ -39,6 +39,43 @@ static __device__ __forceinline__ float sdf_box(float x, float y, float z, float
     return sqrt_sfu(fmaf(px, px, fmaf(py, py, pz * pz))) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
 }
 
+// Gradient of the capped-cylinder SDF: radial on the side, axial on the caps, along (a, b)
+// off the rim; inside, the nearer face.
+static __device__ __forceinline__ float3 sdf_cylinder_grad(float x, float y, float z, float cx, float cy,
+                                                    float4 e)
+{
+    const float dx = x - cx, dy = y - cy;
+    const float rho = sqrtf(fmaf(dx, dx, dy * dy));
+    const float a = rho - e.x;
+    const float up = z - e.z, down = e.y - z;
+    const float b = fmaxf(down, up);
+    const float sz = up >= down ? 1.f : -1.f;
+    const float ux = rho > 0.f ? dx / rho : 0.f, uy = rho > 0.f ? dy / rho : 0.f;
+    if (a > 0.f && b > 0.f) {
+        const float h = sqrtf(fmaf(a, a, b * b));
+        return make_float3(a / h * ux, a / h * uy, b / h * sz);
+    }
+    if (a >= b) return make_float3(ux, uy, 0.f);
+    return make_float3(0.f, 0.f, sz);
+}
+
+// Gradient of the box SDF: outside, along the clamped offset; inside, the face of the
+// largest component.
+static __device__ __forceinline__ float3 sdf_box_grad(float x, float y, float z, float4 c, float4 h)
+{
+    const float sx = x >= c.x ? 1.f : -1.f, sy = y >= c.y ? 1.f : -1.f, sz = z >= c.z ? 1.f : -1.f;
+    const float qx = fabsf(x - c.x) - h.x, qy = fabsf(y - c.y) - h.y, qz = fabsf(z - c.z) - h.z;
+    const float px = fmaxf(qx, 0.f), py = fmaxf(qy, 0.f), pz = fmaxf(qz, 0.f);
+    const float out = fmaf(px, px, fmaf(py, py, pz * pz));
+    if (out > 0.f) {
+        const float inv = rsqrtf(out);
+        return make_float3(px * inv * sx, py * inv * sy, pz * inv * sz);
+    }
+    if (qx >= qy && qx >= qz) return make_float3(sx, 0.f, 0.f);
+    if (qy >= qz) return make_float3(0.f, sy, 0.f);
+    return make_float3(0.f, 0.f, sz);
+}
+
 // Sphere centres at configuration q (chain of Sec. 2 in the linear placement form), in
 // polar form: every centre is (c1 h, s1 h, z) with (c1, s1) the cosine and sine of the slew
 // angle and h the signed horizontal distance from the slew axis.

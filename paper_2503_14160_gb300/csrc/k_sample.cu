@@ -4,25 +4,10 @@
 // The counter of candidate i, block j, iteration t, query q is (j, i, t, q); the key is
 // the 64-bit seed split into two words. Block j gives the normals z[4j..4j+3].
 #include "cp_internal.cuh"
+#include "philox.cuh"
 
 namespace cp {
 namespace {
-
-constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
-constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
-
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
-        const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += kWeyl0;
-        k1 += kWeyl1;
-    }
-    return c;
-}
 
 // Box-Muller on the top 24 bits of two words: u1 in (0, 1], u2 in [0, 1), both exact.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)

@@ -1,0 +1,27 @@
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based generator of the
+// sampling step and of the IK starting points: ten rounds, each multiplying words 0 and 2
+// by the round constants, xor-ing the high halves with the other words and the round key,
+// the key bumped by the Weyl constants between rounds.
+#pragma once
+
+#include <cstdint>
+
+namespace cp {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+
+static __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kWeyl0;
+        k1 += kWeyl1;
+    }
+    return c;
+}
+
+}  // namespace cp

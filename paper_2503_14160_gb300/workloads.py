@@ -24,6 +24,7 @@ STREAM_SCENE = 1
 STREAM_ENDPOINTS = 2
 STREAM_QUERY_SIZES = 3
 STREAM_TEST = 7
+STREAM_IK_TARGETS = 4
 
 
 def rng(seed: int, stream: int, *extra: int) -> np.random.Generator:
@@ -294,6 +295,34 @@ def select_endpoints(model: CraneModel, distance: Callable[[np.ndarray], np.ndar
         return found[0], found[1], True, draws
     best.sort(key=lambda t: -t[0])
     return best[0][1], best[1][1], False, draws
+
+
+# Grasp poses for the batched IK: the grapple centre of a collision-free configuration
+# (clearance GRASP_CLEARANCE) at a height in GRASP_Z (logs on the ground and on a low pile),
+# yaw equal to the slew angle, in the sparse single-query stand (20 trees).
+IK_SCENE = "single_small"
+GRASP_CLEARANCE = 0.05
+GRASP_Z = (-0.5, 1.5)
+
+
+def grasp_configurations(model: CraneModel, accept: Callable[[np.ndarray], np.ndarray], n: int,
+                         seed: int = 0, batch: int = 65536, max_draws: int = 8_000_000) -> np.ndarray:
+    """The first n draws (in draw order) of configurations uniform in the joint limits that
+    `accept` admits; `accept` maps q[m][4] to bool[m] and is the caller's (the grasp rule
+    above: distance and grapple height, evaluated by whichever implementation the caller
+    trusts). float64 [n][4]; raises when fewer than n qualify within max_draws."""
+    g = rng(seed, STREAM_IK_TARGETS)
+    found: List[np.ndarray] = []
+    have, draws = 0, 0
+    while have < n and draws < max_draws:
+        q = uniform_configurations(model, g, batch)
+        ok = np.asarray(accept(q), dtype=bool)
+        found.append(q[ok][: n - have])
+        have += found[-1].shape[0]
+        draws += batch
+    if have < n:
+        raise RuntimeError("only %d of %d grasp configurations in %d draws" % (have, n, draws))
+    return np.concatenate(found, axis=0)
 
 
 # --------------------------------------------------------------------------- test buffers
