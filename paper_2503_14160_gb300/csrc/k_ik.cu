@@ -5,26 +5,27 @@
 // joints' equilibrium residual is zero by the chain's reading. Damped Gauss-Newton
 // (Levenberg-Marquardt) from several starting points per target, the best kept.
 //
-// One CTA per target, one warp per starting point (up to 8 warps; more starts loop over
-// the warps). Each evaluation of r and its Jacobian
-// takes the kinematics on every lane and spreads the obstacles over the lanes for d(q) and
-// its attaining pair; the 4x4 damped normal equations are solved by every lane (a Cholesky
-// in FP32, identical on all lanes), so the warp stays converged. The best start of each
-// target is chosen through shared memory at the end; a NaN cost (a NaN target) ranks as
-// +inf there, so every lane agrees on the choice.
+// One thread per (target, start): the lanes of a warp take the starts of one to 32 targets
+// (a group of G lanes per target, G the power of two >= min(starts, 32); more starts loop
+// over the group's lanes), so a warp instruction advances up to 32 solves. Each thread
+// scans the obstacles in the same order (the loads are warp-wide broadcasts) and evaluates
+// sphere distances only for obstacles that pass a plane test. The best start of a target
+// is found by shuffles within its group; a NaN cost (a NaN target) ranks as +inf there.
 #include "eval_common.cuh"
 #include "philox.cuh"
 
 namespace cp {
 namespace {
 
-constexpr int kIKMaxWarps = 8;             // warps per target; more starts loop
+constexpr int kIKThreads = 128;
+constexpr int kIKMinBlocks = 7;            // 28 warps per SM: 72 registers a thread
 constexpr uint32_t kIKTag = 0x494B5354u;   // third Philox counter word of the starting points
 
 struct IKArgs {
     const float4 *targets;   // [n] {x, y, z, psi}
     const float4 *q_init;    // [n] or null: start of restart 0
     int n, restarts, iters;
+    int group;               // lanes per target (power of two, <= 32)
     float lambda_q, lambda_c, grapple_len, mu0;
     uint32_t k0, k1, query;
     float4 *q_out;           // [n]
@@ -33,114 +34,172 @@ struct IKArgs {
     float *r_out;            // [n][5] or null: residual at q_out
 };
 
+// One evaluation in the form the step needs: the residual, |r|^2 and the normal equations
+// H = J^T J (upper triangle, row-major: 00 01 02 03 11 12 13 22 23 33) and g = J^T r.
 struct Eval {
     float r[5];
-    float J[5][4];
     float f;
+    float H[10];
+    float g[4];
 };
 
-// The most negative sphere-obstacle distance and its pair, spread over the warp's lanes;
-// the pair key is s (n_cyl + n_box) + o (cylinders first), the lower key kept on ties.
-// Only negative distances enter the residual, so an obstacle whose axis (cylinder) or
-// bounding circle (box) lies farther from the crane's vertical plane than it can reach a
-// sphere is skipped: every centre is (c1 h, s1 h, z), at squared horizontal distance
-// (h - u)^2 + v^2 from a point whose plane coordinates are (u, v), so v^2 above
-// (R + r_max)^2 (plus the filter margin) leaves every pair at a distance >= 0. When no pair
-// is negative d is returned as +inf.
-template <int NSPH>
-__device__ __forceinline__ void warp_distance(const ModelDev &m, const SceneDev &sc, float s1, float c1,
-                                              const float *x, const float *y, const float *z, int lane,
-                                              float &d, int &key)
+// H += j^T j, g += j^T rk for one residual row j.
+__device__ __forceinline__ void add_row(Eval &ev, float j0, float j1, float j2, float j3, float rk)
 {
-    const int n_obs = sc.n_cyl + sc.n_box;
-    d = CUDART_INF_F;
-    key = 0x7fffffff;
-    for (int o = lane; o < sc.n_cyl; o += 32) {
-        const float4 f = __ldg(sc.cyl_filt + o), e = __ldg(sc.cyl_exact + o);
-        const float v = fmaf(-s1, f.x, c1 * f.y);
-        if (v * v >= e.w) continue;
-#pragma unroll
-        for (int s = 0; s < NSPH; ++s) {
-            const float t = sdf_cylinder(x[s], y[s], z[s], f.x, f.y, e) - m.sph[s].radius;
-            const int k = s * n_obs + o;
-            if (t < d || (t == d && k < key)) {
-                d = t;
-                key = k;
-            }
-        }
-    }
-    for (int b = lane; b < sc.n_box; b += 32) {
-        const float4 c = __ldg(sc.box_c + b), h = __ldg(sc.box_h + b);
-        const float v = fmaf(-s1, c.x, c1 * c.y);
-        if (fabsf(v) >= c.w) continue;
-#pragma unroll
-        for (int s = 0; s < NSPH; ++s) {
-            const float t = sdf_box(x[s], y[s], z[s], c, h) - m.sph[s].radius;
-            const int k = s * n_obs + sc.n_cyl + b;
-            if (t < d || (t == d && k < key)) {
-                d = t;
-                key = k;
-            }
-        }
-    }
-    if (!(d < 0.f)) {
-        d = CUDART_INF_F;
-        key = 0x7fffffff;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float d2 = __shfl_xor_sync(0xffffffffu, d, off);
-        const int k2 = __shfl_xor_sync(0xffffffffu, key, off);
-        if (d2 < d || (d2 == d && k2 < key)) {
-            d = d2;
-            key = k2;
-        }
-    }
+    ev.H[0] = fmaf(j0, j0, ev.H[0]);
+    ev.H[1] = fmaf(j0, j1, ev.H[1]);
+    ev.H[2] = fmaf(j0, j2, ev.H[2]);
+    ev.H[3] = fmaf(j0, j3, ev.H[3]);
+    ev.H[4] = fmaf(j1, j1, ev.H[4]);
+    ev.H[5] = fmaf(j1, j2, ev.H[5]);
+    ev.H[6] = fmaf(j1, j3, ev.H[6]);
+    ev.H[7] = fmaf(j2, j2, ev.H[7]);
+    ev.H[8] = fmaf(j2, j3, ev.H[8]);
+    ev.H[9] = fmaf(j3, j3, ev.H[9]);
+    ev.g[0] = fmaf(j0, rk, ev.g[0]);
+    ev.g[1] = fmaf(j1, rk, ev.g[1]);
+    ev.g[2] = fmaf(j2, rk, ev.g[2]);
+    ev.g[3] = fmaf(j3, rk, ev.g[3]);
 }
 
-// r(q) and dr/dq for the target; every lane returns the same values.
-template <int NSPH>
-__device__ __forceinline__ void evaluate(const ModelDev &m, const SceneDev &sc, const IKArgs &a, float4 q,
-                                         float4 tg, int lane, Eval &ev)
+// x - 2 pi round(x / 2 pi), the remainder of x by 2 pi in [-pi, pi]; 2 pi is split into a
+// float head and tail (Cody and Waite) so that n 2 pi is subtracted to ~1e-7 rad for the
+// small n met here (|x| within a few turns).
+__device__ __forceinline__ float wrap_angle(float x)
 {
-    float H[NSPH], Z[NSPH], s1, c1;
-    crane_fk_polar<NSPH>(m, q, H, Z, s1, c1);
-    float X[NSPH], Y[NSPH];
+    const float n = rintf(x * 0.159154943091895336f);
+    return fmaf(-n, -1.74845553e-7f, fmaf(-n, 6.28318548202514648f, x));
+}
+
+// Kinematic quantities of one configuration shared by the residual and the Jacobian.
+struct Pose {
+    float s1, c1, s2, c2, s23, c23, q4;
+};
+
+// Shared-memory records of a CTA: the sphere table, and per thread the sphere centres of
+// the configuration being evaluated (h and z of sphere s at [s][thread]), so that the
+// obstacle loop reads them instead of holding them in registers.
+template <int NSPH>
+struct IKShared {
+    SphereLin sph[NSPH];
+    float h[NSPH][kIKThreads];
+    float z[NSPH][kIKThreads];
+};
+
+// Centre of sphere s at the pose, in polar form (h along the slew direction, z).
+__device__ __forceinline__ void sphere_polar(const ModelDev &m, const Pose &p, int s, float &h, float &z, float &L)
+{
+    const SphereLin sp = m.sph[s];
+    L = fmaf(sp.gamma, p.q4, sp.beta);
+    h = fmaf(sp.alpha, p.c2, L * p.c23);
+    z = m.base_z + fmaf(sp.alpha, p.s2, fmaf(L, p.s23, -sp.delta));
+}
+
+// The most negative sphere-obstacle distance and its pair (key s (n_cyl + n_box) + o,
+// cylinders first, the lower key kept on ties). Only negative distances enter the
+// residual, so pairs that cannot be negative are skipped. Every centre is (c1 h, s1 h, z):
+// at squared horizontal distance (h - u)^2 + v^2 from a point with plane coordinates
+// (u, v) (u along the slew direction, v across). A cylinder is skipped when v^2 is above
+// (R + r_max)^2 plus the filter margin (its bound .w) or u lies beyond the spheres' range
+// of h by more than its reach (a bound above R + r_max); a sphere of a kept cylinder when
+// (h - u)^2 + v^2 is above the same bound. A box is skipped when its footprint circle
+// (radius .w, which includes r_max) is that far from the plane or the range. Every skipped
+// pair has a distance >= 0. d = +inf when no pair is negative.
+template <int NSPH>
+__device__ __forceinline__ void scan_distance(const ModelDev &m, const SceneDev &sc, const Pose &p,
+                                              IKShared<NSPH> &sm, float &d, int &key)
+{
+    const int n_obs = sc.n_cyl + sc.n_box;
+    const int tid = threadIdx.x;
+    float h_lo = CUDART_INF_F, h_hi = -CUDART_INF_F;
 #pragma unroll
     for (int s = 0; s < NSPH; ++s) {
-        X[s] = __fmul_rn(c1, H[s]);
-        Y[s] = __fmul_rn(s1, H[s]);
+        float h, z, L;
+        sphere_polar(m, p, s, h, z, L);
+        sm.h[s][tid] = h;
+        sm.z[s][tid] = z;
+        h_lo = fminf(h_lo, h);
+        h_hi = fmaxf(h_hi, h);
     }
-    float s2, c2, s23, c23;
-    sincosf(q.y, &s2, &c2);
-    sincosf(q.y + q.z, &s23, &c23);
+    d = 0.f;
+    key = 0x7fffffff;
+    for (int o = 0; o < sc.n_cyl; ++o) {
+        const float4 f = __ldg(sc.cyl_filt + o), e = __ldg(sc.cyl_exact + o);
+        const float u = fmaf(p.c1, f.x, p.s1 * f.y), v = fmaf(-p.s1, f.x, p.c1 * f.y);
+        if (v * v >= e.w || u < h_lo - f.w || u > h_hi + f.w) continue;
+#pragma unroll 1
+        for (int s = 0; s < NSPH; ++s) {
+            const float h = sm.h[s][tid];
+            const float dx = h - u;
+            if (fmaf(dx, dx, v * v) >= e.w) continue;
+            const float t = sdf_cylinder(__fmul_rn(p.c1, h), __fmul_rn(p.s1, h), sm.z[s][tid], f.x, f.y, e) -
+                            sm.sph[s].radius;
+            const int k = s * n_obs + o;
+            if (t < d || (t == d && d < 0.f && k < key)) {
+                d = t;
+                key = k;
+            }
+        }
+    }
+    for (int b = 0; b < sc.n_box; ++b) {
+        const float4 c = __ldg(sc.box_c + b), hb = __ldg(sc.box_h + b);
+        const float u = fmaf(p.c1, c.x, p.s1 * c.y), v = fmaf(-p.s1, c.x, p.c1 * c.y);
+        if (fabsf(v) >= c.w || u < h_lo - c.w || u > h_hi + c.w) continue;
+#pragma unroll 1
+        for (int s = 0; s < NSPH; ++s) {
+            const float h = sm.h[s][tid];
+            const float t = sdf_box(__fmul_rn(p.c1, h), __fmul_rn(p.s1, h), sm.z[s][tid], c, hb) - sm.sph[s].radius;
+            const int k = s * n_obs + sc.n_cyl + b;
+            if (t < d || (t == d && d < 0.f && k < key)) {
+                d = t;
+                key = k;
+            }
+        }
+    }
+    if (key == 0x7fffffff) d = CUDART_INF_F;
+}
+
+// r(q) and dr/dq for the target.
+template <int NSPH>
+__device__ __forceinline__ void evaluate(const ModelDev &m, const SceneDev &sc, const IKArgs &a, float4 q,
+                                         float4 tg, IKShared<NSPH> &sm, Eval &ev)
+{
+    Pose p;
+    sincosf(q.x, &p.s1, &p.c1);
+    sincosf(q.y, &p.s2, &p.c2);
+    sincosf(q.y + q.z, &p.s23, &p.c23);
+    p.q4 = q.w;
     // the tip: boom L_b along e_b, (L_j + q4) along e_j
     const float Lb = m.boom_len, Lt = m.jib_len + q.w;
-    const float ht = fmaf(Lb, c2, Lt * c23), zt = m.base_z + fmaf(Lb, s2, Lt * s23);
-    ev.r[0] = c1 * ht - tg.x;
-    ev.r[1] = s1 * ht - tg.y;
+    const float ht = fmaf(Lb, p.c2, Lt * p.c23), zt = m.base_z + fmaf(Lb, p.s2, Lt * p.s23);
+    // explicit fused forms: every instance of this function rounds the residual alike
+    ev.r[0] = fmaf(p.c1, ht, -tg.x);
+    ev.r[1] = fmaf(p.s1, ht, -tg.y);
     ev.r[2] = zt - a.grapple_len - tg.z;
-    ev.r[3] = a.lambda_q * remainderf(q.x - tg.w, 6.28318530717958648f);
+    ev.r[3] = a.lambda_q * wrap_angle(q.x - tg.w);
     float d;
     int key;
-    warp_distance<NSPH>(m, sc, s1, c1, X, Y, Z, lane, d, key);
+    scan_distance<NSPH>(m, sc, p, sm, d, key);
     ev.r[4] = a.lambda_c * fmaxf(0.f, -d);
-    // Jacobian: tip rows, yaw row, collision row (gradient of the attaining pair)
-    const float dh2 = -fmaf(Lb, s2, Lt * s23), dh3 = -Lt * s23, dh4 = c23;
-    const float dz2 = fmaf(Lb, c2, Lt * c23), dz3 = Lt * c23, dz4 = s23;
-    ev.J[0][0] = -s1 * ht; ev.J[0][1] = c1 * dh2; ev.J[0][2] = c1 * dh3; ev.J[0][3] = c1 * dh4;
-    ev.J[1][0] = c1 * ht;  ev.J[1][1] = s1 * dh2; ev.J[1][2] = s1 * dh3; ev.J[1][3] = s1 * dh4;
-    ev.J[2][0] = 0.f;      ev.J[2][1] = dz2;      ev.J[2][2] = dz3;      ev.J[2][3] = dz4;
-    ev.J[3][0] = a.lambda_q; ev.J[3][1] = 0.f; ev.J[3][2] = 0.f; ev.J[3][3] = 0.f;
-    ev.J[4][0] = ev.J[4][1] = ev.J[4][2] = ev.J[4][3] = 0.f;
+    // Jacobian rows (tip, yaw, collision: the gradient of the attaining pair) folded into
+    // the normal equations as they are formed
+#pragma unroll
+    for (int i = 0; i < 10; ++i) ev.H[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ev.g[i] = 0.f;
+    const float dh2 = -fmaf(Lb, p.s2, Lt * p.s23), dh3 = -Lt * p.s23, dh4 = p.c23;
+    const float dz2 = fmaf(Lb, p.c2, Lt * p.c23), dz3 = Lt * p.c23, dz4 = p.s23;
+    add_row(ev, -p.s1 * ht, p.c1 * dh2, p.c1 * dh3, p.c1 * dh4, ev.r[0]);
+    add_row(ev, p.c1 * ht, p.s1 * dh2, p.s1 * dh3, p.s1 * dh4, ev.r[1]);
+    add_row(ev, 0.f, dz2, dz3, dz4, ev.r[2]);
+    add_row(ev, a.lambda_q, 0.f, 0.f, 0.f, ev.r[3]);
     if (d < 0.f) {
         const int n_obs = sc.n_cyl + sc.n_box;
         const int s = key / n_obs, o = key - s * n_obs;
-        const SphereLin sp = m.sph[s];
-        const float L = fmaf(sp.gamma, q.w, sp.beta);
-        const float h = fmaf(sp.alpha, c2, L * c23);
-        const float px = __fmul_rn(c1, h), py = __fmul_rn(s1, h);
-        const float pz = m.base_z + fmaf(sp.alpha, s2, fmaf(L, s23, -sp.delta));
+        const SphereLin sp = sm.sph[s];
+        const float h = sm.h[s][threadIdx.x], pz = sm.z[s][threadIdx.x];
+        const float L = fmaf(sp.gamma, p.q4, sp.beta);
+        const float px = __fmul_rn(p.c1, h), py = __fmul_rn(p.s1, h);
         float3 g;
         if (o < sc.n_cyl) {
             const float4 f = __ldg(sc.cyl_filt + o), e = __ldg(sc.cyl_exact + o);
@@ -148,13 +207,13 @@ __device__ __forceinline__ void evaluate(const ModelDev &m, const SceneDev &sc, 
         } else {
             g = sdf_box_grad(px, py, pz, __ldg(sc.box_c + o - sc.n_cyl), __ldg(sc.box_h + o - sc.n_cyl));
         }
-        const float ph2 = -fmaf(sp.alpha, s2, L * s23), ph3 = -L * s23, ph4 = sp.gamma * c23;
-        const float pz2 = fmaf(sp.alpha, c2, L * c23), pz3 = L * c23, pz4 = sp.gamma * s23;
+        const float ph2 = -fmaf(sp.alpha, p.s2, L * p.s23), ph3 = -L * p.s23, ph4 = sp.gamma * p.c23;
+        const float pz2 = fmaf(sp.alpha, p.c2, L * p.c23), pz3 = L * p.c23, pz4 = sp.gamma * p.s23;
+        // d(centre)/dq: slew turns (x, y) = (c1 h, s1 h); the others move h and z
+        const float gh = fmaf(g.x, p.c1, g.y * p.s1);   // gradient along the slew direction
         const float k = -a.lambda_c;
-        ev.J[4][0] = k * (g.x * (-s1 * h) + g.y * (c1 * h));
-        ev.J[4][1] = k * (g.x * c1 * ph2 + g.y * s1 * ph2 + g.z * pz2);
-        ev.J[4][2] = k * (g.x * c1 * ph3 + g.y * s1 * ph3 + g.z * pz3);
-        ev.J[4][3] = k * (g.x * c1 * ph4 + g.y * s1 * ph4 + g.z * pz4);
+        add_row(ev, k * h * fmaf(-g.x, p.s1, g.y * p.c1), k * fmaf(gh, ph2, g.z * pz2),
+                k * fmaf(gh, ph3, g.z * pz3), k * fmaf(gh, ph4, g.z * pz4), ev.r[4]);
     }
     float f = 0.f;
 #pragma unroll
@@ -168,58 +227,29 @@ __device__ __forceinline__ float4 clamp_q(const ModelDev &m, float4 q)
                        fminf(fmaxf(q.z, m.q_min[2]), m.q_max[2]), fminf(fmaxf(q.w, m.q_min[3]), m.q_max[3]));
 }
 
-// Solves (H + mu (diag H + 1e-6)) s = -g for the 4x4 symmetric H by Cholesky.
+// Solves (H + mu (diag H + 1e-6)) s = -g by Cholesky, L L^T with the reciprocal pivots
+// from the hardware reciprocal square root (within 2 ulp) so that no division is needed.
 __device__ __forceinline__ float4 damped_step(const Eval &ev, float mu)
 {
-    float A[4][4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float g = 0.f;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) g = fmaf(ev.J[k][i], ev.r[k], g);
-        b[i] = -g;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float h = 0.f;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) h = fmaf(ev.J[k][i], ev.J[k][j], h);
-            A[i][j] = h;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) A[i][i] = fmaf(mu, A[i][i] + 1e-6f, A[i][i]);
-    // A = L L^T in place (lower), then forward and back substitution
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float dj = A[j][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) dj = fmaf(-A[j][k], A[j][k], dj);
-        dj = sqrtf(fmaxf(dj, 1e-30f));
-        A[j][j] = dj;
-#pragma unroll
-        for (int i = j + 1; i < 4; ++i) {
-            float v = A[i][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) v = fmaf(-A[i][k], A[j][k], v);
-            A[i][j] = v / dj;
-        }
-    }
-    float y[4], x[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float v = b[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) v = fmaf(-A[i][k], y[k], v);
-        y[i] = v / A[i][i];
-    }
-#pragma unroll
-    for (int i = 3; i >= 0; --i) {
-        float v = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 4; ++k) v = fmaf(-A[k][i], x[k], v);
-        x[i] = v / A[i][i];
-    }
-    return make_float4(x[0], x[1], x[2], x[3]);
+    const float a00 = fmaf(mu, ev.H[0] + 1e-6f, ev.H[0]), a11 = fmaf(mu, ev.H[4] + 1e-6f, ev.H[4]);
+    const float a22 = fmaf(mu, ev.H[7] + 1e-6f, ev.H[7]), a33 = fmaf(mu, ev.H[9] + 1e-6f, ev.H[9]);
+    const float i0 = rsqrtf(fmaxf(a00, 1e-30f));
+    const float l10 = ev.H[1] * i0, l20 = ev.H[2] * i0, l30 = ev.H[3] * i0;
+    const float i1 = rsqrtf(fmaxf(fmaf(-l10, l10, a11), 1e-30f));
+    const float l21 = fmaf(-l20, l10, ev.H[5]) * i1, l31 = fmaf(-l30, l10, ev.H[6]) * i1;
+    const float i2 = rsqrtf(fmaxf(fmaf(-l21, l21, fmaf(-l20, l20, a22)), 1e-30f));
+    const float l32 = fmaf(-l31, l21, fmaf(-l30, l20, ev.H[8])) * i2;
+    const float i3 = rsqrtf(fmaxf(fmaf(-l32, l32, fmaf(-l31, l31, fmaf(-l30, l30, a33))), 1e-30f));
+    // L y = -g, then L^T x = y
+    const float y0 = -ev.g[0] * i0;
+    const float y1 = fmaf(-l10, y0, -ev.g[1]) * i1;
+    const float y2 = fmaf(-l21, y1, fmaf(-l20, y0, -ev.g[2])) * i2;
+    const float y3 = fmaf(-l32, y2, fmaf(-l31, y1, fmaf(-l30, y0, -ev.g[3]))) * i3;
+    const float x3 = y3 * i3;
+    const float x2 = fmaf(-l32, x3, y2) * i2;
+    const float x1 = fmaf(-l31, x3, fmaf(-l21, x2, y1)) * i1;
+    const float x0 = fmaf(-l30, x3, fmaf(-l20, x2, fmaf(-l10, x1, y0))) * i0;
+    return make_float4(x0, x1, x2, x3);
 }
 
 __device__ __forceinline__ float rank_cost(float f) { return f == f ? f : CUDART_INF_F; }
@@ -235,32 +265,39 @@ __device__ __forceinline__ float4 ik_start(const ModelDev &m, const IKArgs &a, i
                        fmaf(u2, m.q_max[2] - m.q_min[2], m.q_min[2]), fmaf(u3, m.q_max[3] - m.q_min[3], m.q_min[3]));
 }
 
-// One CTA per target; warp w solves the starts w, w + warps, ... and keeps its best (the
-// lowest |r|^2, the lower start on ties).
+// Thread (target t, lane j of its group) solves the starts j, j + G, ... of t and keeps
+// its best (the lowest |r|^2, the lower start on ties); the group then agrees on the best.
 template <int NSPH>
-__global__ void __launch_bounds__(kIKMaxWarps * 32)
+__global__ void __launch_bounds__(kIKThreads, kIKMinBlocks)
 k_ik(const ModelDev m, const SceneDev sc, const IKArgs a)
 {
-    __shared__ float s_f[kIKMaxWarps];
-    __shared__ int s_k[kIKMaxWarps];
-    __shared__ float4 s_q[kIKMaxWarps];
-    __shared__ float s_r[kIKMaxWarps][5];
-    const int t = blockIdx.x;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    __shared__ IKShared<NSPH> sm;
+    if (threadIdx.x < NSPH) sm.sph[threadIdx.x] = m.sph[threadIdx.x];
+    __syncthreads();
+    const int G = a.group;
+    const long long gid = (long long)blockIdx.x * kIKThreads + threadIdx.x;
+    const int j = threadIdx.x & (G - 1);
+    const bool live = gid / G < a.n;
+    const int t = live ? (int)(gid / G) : a.n - 1;
     const float4 tg = a.targets[t];
     float best_f = CUDART_INF_F;
     int best_k = -1;
     float4 best_q = make_float4(0.f, 0.f, 0.f, 0.f);
-    float best_r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     Eval ev, en;
-    for (int k = w; k < a.restarts; k += warps) {
+    for (int k = j; k < a.restarts; k += G) {
         float4 q = clamp_q(m, ik_start<NSPH>(m, a, t, k));
         float mu = a.mu0;
-        evaluate<NSPH>(m, sc, a, q, tg, lane, ev);
+        evaluate<NSPH>(m, sc, a, q, tg, sm, ev);
         for (int it = 0; it < a.iters; ++it) {
             const float4 st = damped_step(ev, mu);
             const float4 qn = clamp_q(m, make_float4(q.x + st.x, q.y + st.y, q.z + st.z, q.w + st.w));
-            evaluate<NSPH>(m, sc, a, qn, tg, lane, en);
+            if (qn.x == q.x && qn.y == q.y && qn.z == q.z && qn.w == q.w) {
+                // the step vanished in rounding: the trial is q itself, whose cost is not
+                // below its own, so the step is rejected without evaluating it again
+                mu = fminf(mu * 4.f, 1e12f);
+                continue;
+            }
+            evaluate<NSPH>(m, sc, a, qn, tg, sm, en);
             if (en.f < ev.f) {
                 q = qn;
                 ev = en;
@@ -273,38 +310,33 @@ k_ik(const ModelDev m, const SceneDev sc, const IKArgs a)
             best_f = ev.f;
             best_k = k;
             best_q = q;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) best_r[i] = ev.r[i];
         }
     }
-    if (lane == 0) {
-        s_f[w] = best_f;
-        s_k[w] = best_k;
-        s_q[w] = best_q;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) s_r[w][i] = best_r[i];
+    // best over the group: (f, start) in lexicographic order; lanes without a start rank last
+    float fr = best_k >= 0 ? rank_cost(best_f) : CUDART_INF_F;
+    int kr = best_k >= 0 ? best_k : 0x7fffffff;
+    for (int off = G >> 1; off > 0; off >>= 1) {
+        const float f2 = __shfl_xor_sync(0xffffffffu, fr, off);
+        const int k2 = __shfl_xor_sync(0xffffffffu, kr, off);
+        if (f2 < fr || (f2 == fr && k2 < kr)) {
+            fr = f2;
+            kr = k2;
+        }
     }
-    __syncthreads();
-    if (w == 0) {
-        // best over the warps: (f, start) in lexicographic order
-        float f = lane < warps ? rank_cost(s_f[lane]) : CUDART_INF_F;
-        int k = lane < warps ? s_k[lane] : 0x7fffffff;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float f2 = __shfl_xor_sync(0xffffffffu, f, off);
-            const int k2 = __shfl_xor_sync(0xffffffffu, k, off);
-            if (f2 < f || (f2 == f && k2 < k)) {
-                f = f2;
-                k = k2;
-            }
-        }
-        if (lane == 0) {
-            const int wb = k % warps;   // the warp that solved start k
-            a.q_out[t] = s_q[wb];
-            a.f_out[t] = s_f[wb];
-            if (a.restart_out != nullptr) a.restart_out[t] = k;
-        }
-        if (a.r_out != nullptr && lane < 5) a.r_out[(size_t)t * 5 + lane] = s_r[k % warps][lane];
+    const int owner = ((int)threadIdx.x & 31 & ~(G - 1)) | (kr & (G - 1));   // the lane that solved start kr
+    const float4 qb = make_float4(__shfl_sync(0xffffffffu, best_q.x, owner), __shfl_sync(0xffffffffu, best_q.y, owner),
+                                  __shfl_sync(0xffffffffu, best_q.z, owner), __shfl_sync(0xffffffffu, best_q.w, owner));
+    const float fb = __shfl_sync(0xffffffffu, best_f, owner);
+    if (live && j == 0) {
+        a.q_out[t] = qb;
+        a.f_out[t] = fb;
+        if (a.restart_out != nullptr) a.restart_out[t] = kr;
+    }
+    if (a.r_out != nullptr) {
+        // the residual at the answer, evaluated once more (the same arithmetic as the solve)
+        evaluate<NSPH>(m, sc, a, qb, tg, sm, en);
+        if (live && j == 0)
+            for (int i = 0; i < 5; ++i) a.r_out[(size_t)t * 5 + i] = en.r[i];
     }
 }
 
@@ -368,11 +400,14 @@ int launch_ik(const ModelDev &m, const SceneDev &sc, const float *targets, const
     a.f_out = f_out;
     a.restart_out = restart_out;
     a.r_out = r_out;
-    const int threads = 32 * (restarts < kIKMaxWarps ? restarts : kIKMaxWarps);
+    int G = 1;
+    while (G < restarts && G < 32) G <<= 1;
+    a.group = G;
+    const long long blocks = ((long long)n * G + kIKThreads - 1) / kIKThreads;
     if (m.n_spheres == 12)
-        k_ik<12><<<n, threads, 0, st>>>(m, sc, a);
+        k_ik<12><<<(unsigned)blocks, kIKThreads, 0, st>>>(m, sc, a);
     else
-        k_ik<16><<<n, threads, 0, st>>>(m, sc, a);
+        k_ik<16><<<(unsigned)blocks, kIKThreads, 0, st>>>(m, sc, a);
     CP_LAUNCHED("k_ik");
     return CP_OK;
 }
