@@ -19,6 +19,8 @@ namespace {
 
 constexpr int kIKThreads = 128;
 constexpr int kIKMinBlocks = 7;            // 28 warps per SM: 72 registers a thread
+constexpr int kIKStagedObstacles = 1024;   // up to this many obstacles, plane-test records in
+                                           // shared memory (16 KB; 7 CTAs fit an SM)
 constexpr uint32_t kIKTag = 0x494B5354u;   // third Philox counter word of the starting points
 
 struct IKArgs {
@@ -105,9 +107,9 @@ __device__ __forceinline__ void sphere_polar(const ModelDev &m, const Pose &p, i
 // (h - u)^2 + v^2 is above the same bound. A box is skipped when its footprint circle
 // (radius .w, which includes r_max) is that far from the plane or the range. Every skipped
 // pair has a distance >= 0. d = +inf when no pair is negative.
-template <int NSPH>
+template <int NSPH, bool STAGED>
 __device__ __forceinline__ void scan_distance(const ModelDev &m, const SceneDev &sc, const Pose &p,
-                                              IKShared<NSPH> &sm, float &d, int &key)
+                                              IKShared<NSPH> &sm, const float4 *s_obs, float &d, int &key)
 {
     const int n_obs = sc.n_cyl + sc.n_box;
     const int tid = threadIdx.x;
@@ -124,9 +126,20 @@ __device__ __forceinline__ void scan_distance(const ModelDev &m, const SceneDev 
     d = 0.f;
     key = 0x7fffffff;
     for (int o = 0; o < sc.n_cyl; ++o) {
-        const float4 f = __ldg(sc.cyl_filt + o), e = __ldg(sc.cyl_exact + o);
+        // plane test on {cx, cy, reach, (R + r_max)^2 + margin}; the exact record on a pass
+        float4 f;
+        if (STAGED) {
+            f = s_obs[o];
+        } else {
+            f = __ldg(sc.cyl_filt + o);
+            f.z = __ldg(&sc.cyl_exact[o].w);
+            const float r = f.w;
+            f.w = f.z;
+            f.z = r;
+        }
         const float u = fmaf(p.c1, f.x, p.s1 * f.y), v = fmaf(-p.s1, f.x, p.c1 * f.y);
-        if (v * v >= e.w || u < h_lo - f.w || u > h_hi + f.w) continue;
+        if (v * v >= f.w || u < h_lo - f.z || u > h_hi + f.z) continue;
+        const float4 e = __ldg(sc.cyl_exact + o);
 #pragma unroll 1
         for (int s = 0; s < NSPH; ++s) {
             const float h = sm.h[s][tid];
@@ -142,9 +155,10 @@ __device__ __forceinline__ void scan_distance(const ModelDev &m, const SceneDev 
         }
     }
     for (int b = 0; b < sc.n_box; ++b) {
+        const float4 cb = STAGED ? s_obs[sc.n_cyl + b] : __ldg(sc.box_c + b);
+        const float u = fmaf(p.c1, cb.x, p.s1 * cb.y), v = fmaf(-p.s1, cb.x, p.c1 * cb.y);
+        if (fabsf(v) >= cb.w || u < h_lo - cb.w || u > h_hi + cb.w) continue;
         const float4 c = __ldg(sc.box_c + b), hb = __ldg(sc.box_h + b);
-        const float u = fmaf(p.c1, c.x, p.s1 * c.y), v = fmaf(-p.s1, c.x, p.c1 * c.y);
-        if (fabsf(v) >= c.w || u < h_lo - c.w || u > h_hi + c.w) continue;
 #pragma unroll 1
         for (int s = 0; s < NSPH; ++s) {
             const float h = sm.h[s][tid];
@@ -160,9 +174,9 @@ __device__ __forceinline__ void scan_distance(const ModelDev &m, const SceneDev 
 }
 
 // r(q) and dr/dq for the target.
-template <int NSPH>
+template <int NSPH, bool STAGED>
 __device__ __forceinline__ void evaluate(const ModelDev &m, const SceneDev &sc, const IKArgs &a, float4 q,
-                                         float4 tg, IKShared<NSPH> &sm, Eval &ev)
+                                         float4 tg, IKShared<NSPH> &sm, const float4 *s_obs, Eval &ev)
 {
     Pose p;
     sincosf(q.x, &p.s1, &p.c1);
@@ -179,7 +193,7 @@ __device__ __forceinline__ void evaluate(const ModelDev &m, const SceneDev &sc, 
     ev.r[3] = a.lambda_q * wrap_angle(q.x - tg.w);
     float d;
     int key;
-    scan_distance<NSPH>(m, sc, p, sm, d, key);
+    scan_distance<NSPH, STAGED>(m, sc, p, sm, s_obs, d, key);
     ev.r[4] = a.lambda_c * fmaxf(0.f, -d);
     // Jacobian rows (tip, yaw, collision: the gradient of the attaining pair) folded into
     // the normal equations as they are formed
@@ -267,12 +281,20 @@ __device__ __forceinline__ float4 ik_start(const ModelDev &m, const IKArgs &a, i
 
 // Thread (target t, lane j of its group) solves the starts j, j + G, ... of t and keeps
 // its best (the lowest |r|^2, the lower start on ties); the group then agrees on the best.
-template <int NSPH>
+template <int NSPH, bool STAGED>
 __global__ void __launch_bounds__(kIKThreads, kIKMinBlocks)
 k_ik(const ModelDev m, const SceneDev sc, const IKArgs a)
 {
     __shared__ IKShared<NSPH> sm;
+    extern __shared__ float4 s_obs[];   // STAGED: the plane-test records of every obstacle
     if (threadIdx.x < NSPH) sm.sph[threadIdx.x] = m.sph[threadIdx.x];
+    if (STAGED) {
+        for (int o = threadIdx.x; o < sc.n_cyl; o += kIKThreads) {
+            const float4 f = sc.cyl_filt[o];
+            s_obs[o] = make_float4(f.x, f.y, f.w, sc.cyl_exact[o].w);
+        }
+        for (int b = threadIdx.x; b < sc.n_box; b += kIKThreads) s_obs[sc.n_cyl + b] = sc.box_c[b];
+    }
     __syncthreads();
     const int G = a.group;
     const long long gid = (long long)blockIdx.x * kIKThreads + threadIdx.x;
@@ -287,7 +309,7 @@ k_ik(const ModelDev m, const SceneDev sc, const IKArgs a)
     for (int k = j; k < a.restarts; k += G) {
         float4 q = clamp_q(m, ik_start<NSPH>(m, a, t, k));
         float mu = a.mu0;
-        evaluate<NSPH>(m, sc, a, q, tg, sm, ev);
+        evaluate<NSPH, STAGED>(m, sc, a, q, tg, sm, s_obs, ev);
         for (int it = 0; it < a.iters; ++it) {
             const float4 st = damped_step(ev, mu);
             const float4 qn = clamp_q(m, make_float4(q.x + st.x, q.y + st.y, q.z + st.z, q.w + st.w));
@@ -297,7 +319,7 @@ k_ik(const ModelDev m, const SceneDev sc, const IKArgs a)
                 mu = fminf(mu * 4.f, 1e12f);
                 continue;
             }
-            evaluate<NSPH>(m, sc, a, qn, tg, sm, en);
+            evaluate<NSPH, STAGED>(m, sc, a, qn, tg, sm, s_obs, en);
             if (en.f < ev.f) {
                 q = qn;
                 ev = en;
@@ -334,7 +356,7 @@ k_ik(const ModelDev m, const SceneDev sc, const IKArgs a)
     }
     if (a.r_out != nullptr) {
         // the residual at the answer, evaluated once more (the same arithmetic as the solve)
-        evaluate<NSPH>(m, sc, a, qb, tg, sm, en);
+        evaluate<NSPH, STAGED>(m, sc, a, qb, tg, sm, s_obs, en);
         if (live && j == 0)
             for (int i = 0; i < 5; ++i) a.r_out[(size_t)t * 5 + i] = en.r[i];
     }
@@ -404,10 +426,16 @@ int launch_ik(const ModelDev &m, const SceneDev &sc, const float *targets, const
     while (G < restarts && G < 32) G <<= 1;
     a.group = G;
     const long long blocks = ((long long)n * G + kIKThreads - 1) / kIKThreads;
-    if (m.n_spheres == 12)
-        k_ik<12><<<(unsigned)blocks, kIKThreads, 0, st>>>(m, sc, a);
-    else
-        k_ik<16><<<(unsigned)blocks, kIKThreads, 0, st>>>(m, sc, a);
+    const int n_obs = sc.n_cyl + sc.n_box;
+    const bool staged = n_obs <= kIKStagedObstacles;
+    const size_t smem = staged ? sizeof(float4) * (size_t)n_obs : 0;
+    if (m.n_spheres == 12) {
+        if (staged) k_ik<12, true><<<(unsigned)blocks, kIKThreads, smem, st>>>(m, sc, a);
+        else k_ik<12, false><<<(unsigned)blocks, kIKThreads, 0, st>>>(m, sc, a);
+    } else {
+        if (staged) k_ik<16, true><<<(unsigned)blocks, kIKThreads, smem, st>>>(m, sc, a);
+        else k_ik<16, false><<<(unsigned)blocks, kIKThreads, 0, st>>>(m, sc, a);
+    }
     CP_LAUNCHED("k_ik");
     return CP_OK;
 }
