@@ -491,9 +491,9 @@ def run_differentiable(args):
 
 
 IK_TARGETS, IK_RESTARTS, IK_ITERS = 16384, 8, 50
-IK_FLOPS_PER_EVAL = 150     # kinematics of 12 spheres and the tip, residual, Jacobian rows
-IK_FLOPS_PER_OBSTACLE = 4   # plane test of one obstacle (fma, mul, square, compare)
-IK_FLOPS_PER_SOLVE = 200    # J^T J, J^T r, damping, 4x4 Cholesky and two substitutions
+IK_FLOPS_PER_EVAL = 150     # kinematics of 12 spheres and the tip, the residual
+IK_FLOPS_PER_OBSTACLE = 4   # plane test of one obstacle (part of its 2 fma + 3 mul)
+IK_FLOPS_PER_SOLVE = 200    # Jacobian rows, J^T J, J^T r, damping, 4x4 Cholesky, substitutions
 
 
 def ik_flops(n_obstacles, restarts, iters):
