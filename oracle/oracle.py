@@ -17,6 +17,9 @@ written here with numpy, one function per step, in the paper's order and notatio
   update             steps (5) and (6): mu <- sum_j w_j x_(j);
                      C <- sum_j w_j (x_(j) - mu)(x_(j) - mu)^T + eps I  (new mu)
   plan               the loop of Algorithm 1 for a fixed number of iterations
+  update_cmaes       the CMA-ES update the method is modelled on (step size and evolution
+                     paths, rank-one and rank-mu covariance about the old mean), a variant
+                     of steps (5) and (6)
   ik_residual        the residual of the collision-free IK (Sec. 3.2, Eq. IK opt) and its
                      Jacobian, through the C oracle
   ik_solve           damped Gauss-Newton (Levenberg-Marquardt) on Eq. IK opt from one start
@@ -366,6 +369,86 @@ def update(xi: np.ndarray, J: np.ndarray, nu: int, eps: float):
     Y = elites - mu[None, :]
     C = (Y * w[:, None]).T @ Y + eps * np.eye(D)
     return mu, C
+
+
+# --------------------------------------------------------------------------- CMA-ES variant
+
+@dataclasses.dataclass
+class CMAState:
+    """State of the CMA-ES update (the variant the paper's method is modelled on): mean,
+    covariance, global step size sigma, the two evolution paths, and the iterations done."""
+    mu: np.ndarray
+    C: np.ndarray
+    sigma: float
+    p_sigma: np.ndarray
+    p_c: np.ndarray
+    t: int = 0
+
+
+@dataclasses.dataclass
+class CMAConstants:
+    mu_eff: float
+    c_sigma: float
+    d_sigma: float
+    c_c: float
+    c_1: float
+    c_mu: float
+    chi_n: float
+
+
+def cma_constants(D: int, w: np.ndarray) -> CMAConstants:
+    """Default learning rates of CMA-ES for dimension D and positive recombination weights
+    w (Hansen, "The CMA Evolution Strategy: A Tutorial", 2016, Table 1), and the expected
+    norm of a D-dimensional standard normal vector (its series approximation)."""
+    mu_eff = 1.0 / float(np.sum(w * w))
+    c_sigma = (mu_eff + 2.0) / (D + mu_eff + 5.0)
+    d_sigma = 1.0 + 2.0 * max(0.0, math.sqrt((mu_eff - 1.0) / (D + 1.0)) - 1.0) + c_sigma
+    c_c = (4.0 + mu_eff / D) / (D + 4.0 + 2.0 * mu_eff / D)
+    c_1 = 2.0 / ((D + 1.3) ** 2 + mu_eff)
+    c_mu = min(1.0 - c_1, 2.0 * (mu_eff - 2.0 + 1.0 / mu_eff) / ((D + 2.0) ** 2 + mu_eff))
+    chi_n = math.sqrt(D) * (1.0 - 1.0 / (4.0 * D) + 1.0 / (21.0 * D * D))
+    return CMAConstants(mu_eff, c_sigma, d_sigma, c_c, c_1, c_mu, chi_n)
+
+
+def cma_init(mu: np.ndarray, C: np.ndarray, sigma: float) -> CMAState:
+    D = mu.shape[0]
+    return CMAState(_c64(mu).copy(), _c64(C).copy(), float(sigma), np.zeros(D), np.zeros(D), 0)
+
+
+def update_cmaes(state: CMAState, xi: np.ndarray, J: np.ndarray, nu: int) -> CMAState:
+    """CMA-ES update in place of steps (5) and (6), with the same selection and weights
+    (steps (3) and (4)), in the order of the tutorial:
+      mean      m' = sum_j w_j x_(j)
+      steps     y_j = (x_(j) - m) / sigma          (about the OLD mean)
+      p_sigma   (1 - c_s) p_sigma + sqrt(c_s (2 - c_s) mu_eff) L_C^-1 (m' - m) / sigma
+      h_sigma   1 if |p_sigma| / sqrt(1 - (1 - c_s)^(2 (t + 1))) < (1.4 + 2 / (D + 1)) chi_n
+      p_c       (1 - c_c) p_c + h_sigma sqrt(c_c (2 - c_c) mu_eff) (m' - m) / sigma
+      C'        (1 + c_1 (1 - h_sigma) c_c (2 - c_c) - c_1 - c_mu) C + c_1 p_c p_c^T
+                + c_mu sum_j w_j y_j y_j^T
+      sigma'    sigma exp((c_s / d_s) (|p_sigma| / chi_n - 1))
+    C^-1/2 of the tutorial is taken as L_C^-1 with L_C the Cholesky factor of C: both map
+    N(0, C) to N(0, I), which is all the path's length statistics rely on."""
+    D = state.mu.shape[0]
+    X = _c64(xi).reshape(-1, D)
+    order = rank(J)
+    elites = X[order[:nu]]
+    w = log_rank_weights(nu)
+    k = cma_constants(D, w)
+    m, sigma = state.mu, state.sigma
+    m_new = w @ elites
+    Y = (elites - m[None, :]) / sigma
+    L_C = np.linalg.cholesky(state.C)
+    shift = (m_new - m) / sigma
+    z = np.linalg.solve(L_C, shift)
+    p_sigma = (1.0 - k.c_sigma) * state.p_sigma + math.sqrt(k.c_sigma * (2.0 - k.c_sigma) * k.mu_eff) * z
+    norm = float(np.linalg.norm(p_sigma))
+    h = 1.0 if norm / math.sqrt(1.0 - (1.0 - k.c_sigma) ** (2 * (state.t + 1))) < (1.4 + 2.0 / (D + 1)) * k.chi_n else 0.0
+    p_c = (1.0 - k.c_c) * state.p_c + h * math.sqrt(k.c_c * (2.0 - k.c_c) * k.mu_eff) * shift
+    delta_h = (1.0 - h) * k.c_c * (2.0 - k.c_c)
+    C = ((1.0 + k.c_1 * delta_h - k.c_1 - k.c_mu) * state.C + k.c_1 * np.outer(p_c, p_c)
+         + k.c_mu * (Y * w[:, None]).T @ Y)
+    sigma_new = sigma * math.exp((k.c_sigma / k.d_sigma) * (norm / k.chi_n - 1.0))
+    return CMAState(m_new, C, sigma_new, p_sigma, p_c, state.t + 1)
 
 
 @dataclasses.dataclass
