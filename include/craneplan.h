@@ -134,7 +134,16 @@ typedef struct cp_params {
                                 the obstacles out of reach of all their spheres. Both give
                                 the same results bit for bit; only the time differs. Not
                                 used by the grid form (grid_cell > 0). */
+    int32_t update_rule;    /* steps (5)-(6): CP_UPDATE_PAPER (0) as Algorithm 1 prints them
+                               (covariance about the new mean plus eps I, sigma fixed), or
+                               CP_UPDATE_CMAES (1), the CMA-ES update the method is modelled
+                               on: a cumulated step-size path adapts sigma, and C takes a
+                               rank-one (evolution path) and a rank-mu (elites about the OLD
+                               mean) update with the default learning rates; no eps. */
 } cp_params;
+
+#define CP_UPDATE_PAPER 0
+#define CP_UPDATE_CMAES 1
 
 /* Cost terms of the final mean path and the state of a finished plan. */
 typedef struct cp_plan_stats {
@@ -295,6 +304,14 @@ int cp_get_distribution(const cp_planner *p, double *d_mu, double *d_C);
  * and factor sigma^2 C (a checkpoint restore: with the same seed the remaining
  * iterations repeat bit for bit). Errors: CP_ERR_STATE (no end points), CP_ERR_ARG. */
 int cp_set_distribution(cp_planner *p, const double *d_mu, const double *d_C, int32_t iter);
+
+/* State of the CMA-ES update rule beyond (mu, C): double[1 + 2D] = {sigma, p_sigma[D],
+ * p_c[D]} (device buffers). cp_set_endpoints resets it to {params.sigma, 0, 0};
+ * cp_set_cma_state replaces it and factors sigma^2 C again (with cp_set_distribution it
+ * restores a checkpoint of the CMA-ES rule). Under CP_UPDATE_PAPER the state holds the
+ * fixed sigma and zero paths. Errors: CP_ERR_ARG, CP_ERR_STATE (no end points). */
+int cp_get_cma_state(const cp_planner *p, double *d_state);
+int cp_set_cma_state(cp_planner *p, const double *d_state);
 
 /* Copy the current Cholesky factor L (double[D][D], lower, L L^T = sigma^2 C). */
 int cp_get_factor(const cp_planner *p, double *d_L);

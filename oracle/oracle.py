@@ -462,17 +462,23 @@ class PlanResult:
 
 
 def plan(problem: Problem, sp: SearchParams, q0, qd, iterations: int,
-         callback=None) -> PlanResult:
-    """Algorithm 1 for a fixed number of iterations, starting from init_distribution."""
+         callback=None, rule: str = "paper") -> PlanResult:
+    """Algorithm 1 for a fixed number of iterations, starting from init_distribution;
+    rule "cmaes" takes update_cmaes (sigma adapted) in place of steps (5)-(6)."""
     q0, qd = _c64(q0), _c64(qd)
     m = problem.model_py
     mu, C = init_distribution(q0, qd, sp.K, m.q_min, m.q_max, sp.init_std_frac)
+    st = cma_init(mu, C, sp.sigma)
     best, mean_J = [], []
     for t in range(iterations):
-        L = factor(C, sp.sigma)
-        xi = sample(mu, L, sp.seed, t, sp.query, sp.N, sp.K)
+        L = factor(st.C if rule == "cmaes" else C, st.sigma if rule == "cmaes" else sp.sigma)
+        xi = sample(st.mu if rule == "cmaes" else mu, L, sp.seed, t, sp.query, sp.N, sp.K)
         J = evaluate(problem, xi, q0, qd).J
-        mu, C = update(xi, J, sp.n_elites, sp.eps)
+        if rule == "cmaes":
+            st = update_cmaes(st, xi, J, sp.n_elites)
+            mu, C = st.mu, st.C
+        else:
+            mu, C = update(xi, J, sp.n_elites, sp.eps)
         best.append(float(np.nanmin(J)))
         if callback is not None:
             callback(t, mu, C, J)

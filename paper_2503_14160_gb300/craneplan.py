@@ -64,7 +64,12 @@ class cp_params(ctypes.Structure):
                 ("grid_cell", ctypes.c_double), ("grid_half_extent", ctypes.c_double),
                 ("max_grid_items", ctypes.c_int64), ("smooth_margin", ctypes.c_double),
                 ("smooth_beta", ctypes.c_double), ("eval_ctas_per_sm", ctypes.c_int32),
-                ("debug_withhold_staging", ctypes.c_int32), ("eval_exhaustive", ctypes.c_int32)]
+                ("debug_withhold_staging", ctypes.c_int32), ("eval_exhaustive", ctypes.c_int32),
+                ("update_rule", ctypes.c_int32)]
+
+
+CP_UPDATE_PAPER = 0
+CP_UPDATE_CMAES = 1
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -126,6 +131,8 @@ _SIGS = {
     "cp_get_distribution": (ctypes.c_int, [_P, _P, _P]),
     "cp_set_distribution": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     "cp_get_factor": (ctypes.c_int, [_P, _P]),
+    "cp_get_cma_state": (ctypes.c_int, [_P, _P]),
+    "cp_set_cma_state": (ctypes.c_int, [_P, _P]),
     "cp_get_elites": (ctypes.c_int, [_P, _P]),
     "cp_philox4x32_10": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P]),
     "cp_evaluate_static": (ctypes.c_int, [ctypes.POINTER(cp_model), _P, ctypes.c_int32, _P,
@@ -244,11 +251,11 @@ def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 grid_half_extent: float = 0.0, max_grid_items: int = 0,
                 smooth_margin: float = 0.05, smooth_beta: float = 0.01,
                 eval_ctas_per_sm: int = 0, debug_withhold_staging: int = 0,
-                eval_exhaustive: int = 0) -> cp_params:
+                eval_exhaustive: int = 0, update_rule: int = CP_UPDATE_PAPER) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
                      query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
                      max_grid_items, smooth_margin, smooth_beta, eval_ctas_per_sm,
-                     debug_withhold_staging, eval_exhaustive)
+                     debug_withhold_staging, eval_exhaustive, update_rule)
 
 
 # --------------------------------------------------------------------------- entry points
@@ -342,6 +349,14 @@ def cp_set_distribution(p: int, mu, C, it: int) -> None:
 
 def cp_get_factor(p: int, L) -> None:
     _check(load().cp_get_factor(p, _ptr(L)))
+
+
+def cp_get_cma_state(p: int, state) -> None:
+    _check(load().cp_get_cma_state(p, _ptr(state)))
+
+
+def cp_set_cma_state(p: int, state) -> None:
+    _check(load().cp_set_cma_state(p, _ptr(state)))
 
 
 def cp_get_elites(p: int, idx) -> None:

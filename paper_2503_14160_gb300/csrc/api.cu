@@ -152,6 +152,9 @@ struct cp_planner {
     unsigned long long *work = nullptr;   // broad-phase survivor count while timing
     unsigned long long *rkey_a = nullptr, *rkey_b = nullptr;   // radix sort scratch
     int *rval_a = nullptr, *rval_b = nullptr, *rhist = nullptr;
+    double *cma = nullptr;      // CMA-ES rule: {sigma, sigma before the update, h_sigma, |p_sigma|}
+    double *p_sigma = nullptr, *p_c = nullptr, *mu_prev = nullptr;
+    CmaConsts cmak{};
     float *smooth_part_g = nullptr;   // partial gradients when few candidates share the GPU
     double *smooth_part_J = nullptr;
     int smem_optin = 0;
@@ -186,6 +189,26 @@ int validate_model(const cp_model *m)
             return set_error("sphere %d: offset must be finite and radius > 0", s), CP_ERR_ARG;
     }
     return CP_OK;
+}
+
+CmaConsts cma_consts(int D, int nu)
+{
+    // the log-rank weights of step (4), as k_weights forms them
+    std::vector<double> w(nu);
+    double sum = 0.0;
+    for (int j = 0; j < nu; ++j) sum += (w[j] = std::log(nu + 0.5) - std::log(j + 1.0));
+    double s2 = 0.0;
+    for (int j = 0; j < nu; ++j) s2 += (w[j] / sum) * (w[j] / sum);
+    CmaConsts k{};
+    const double n = D;
+    k.mu_eff = 1.0 / s2;
+    k.c_sigma = (k.mu_eff + 2.0) / (n + k.mu_eff + 5.0);
+    k.d_sigma = 1.0 + 2.0 * std::max(0.0, std::sqrt((k.mu_eff - 1.0) / (n + 1.0)) - 1.0) + k.c_sigma;
+    k.c_c = (4.0 + k.mu_eff / n) / (n + 4.0 + 2.0 * k.mu_eff / n);
+    k.c_1 = 2.0 / ((n + 1.3) * (n + 1.3) + k.mu_eff);
+    k.c_mu = std::min(1.0 - k.c_1, 2.0 * (k.mu_eff - 2.0 + 1.0 / k.mu_eff) / ((n + 2.0) * (n + 2.0) + k.mu_eff));
+    k.chi_n = std::sqrt(n) * (1.0 - 1.0 / (4.0 * n) + 1.0 / (21.0 * n * n));
+    return k;
 }
 
 ModelDev make_model(const cp_model *m)
@@ -267,6 +290,8 @@ int validate_params(const cp_params *p)
     if (p->eval_ctas_per_sm < 0) return set_error("eval_ctas_per_sm must be >= 0"), CP_ERR_ARG;
     if (p->eval_exhaustive != 0 && p->eval_exhaustive != 1)
         return set_error("eval_exhaustive must be 0 or 1"), CP_ERR_ARG;
+    if (p->update_rule != CP_UPDATE_PAPER && p->update_rule != CP_UPDATE_CMAES)
+        return set_error("update_rule must be CP_UPDATE_PAPER or CP_UPDATE_CMAES"), CP_ERR_ARG;
     if (!(p->grid_cell >= 0.0) || !is_finite(p->grid_cell) || !(p->grid_half_extent >= 0.0) ||
         !is_finite(p->grid_half_extent) || p->max_grid_items < 0 || !(p->smooth_margin >= 0.0) ||
         !is_finite(p->smooth_margin) || !(p->smooth_beta >= 0.0) || !is_finite(p->smooth_beta))
@@ -387,7 +412,8 @@ int run_factor(cp_planner *p)
 {
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
-    rc = launch_factor(p->C, p->prm.sigma * p->prm.sigma, p->D, p->L, p->Lt, p->status, p->st);
+    rc = launch_factor(p->C, p->prm.sigma * p->prm.sigma, p->prm.update_rule == CP_UPDATE_CMAES ? p->cma : nullptr,
+                       p->D, p->L, p->Lt, p->status, p->st);
     if (rc != CP_OK) return rc;
     return p->timer.end(ST_FACTOR, p->st);
 }
@@ -420,9 +446,16 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
                                  p->st)) != CP_OK)
             return rc;
     }
-    if ((rc = launch_moments(p->elites, p->w, p->nu, p->D, p->prm.eps, p->cov_part, p->mean_part,
-                             p->mu, p->C, p->st)) != CP_OK)
+    if (p->prm.update_rule == CP_UPDATE_CMAES) {
+        CP_CUDA(cudaMemcpyAsync(p->mu_prev, p->mu, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
+        if ((rc = launch_cma_update(p->elites, p->w, p->nu, p->D, p->mu_prev, p->L, p->cmak, p->iteration,
+                                    p->cov_part, p->mean_part, p->mu, p->C, p->p_sigma, p->p_c, p->cma,
+                                    p->st)) != CP_OK)
+            return rc;
+    } else if ((rc = launch_moments(p->elites, p->w, p->nu, p->D, p->prm.eps, p->cov_part, p->mean_part,
+                                    p->mu, p->C, p->st)) != CP_OK) {
         return rc;
+    }
     if ((rc = p->timer.end(ST_UPDATE, p->st)) != CP_OK) return rc;
     if ((rc = run_factor(p)) != CP_OK) return rc;
     p->iteration += 1;
@@ -578,6 +611,10 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_sp_g = L.take<float>(units_max * D);
     const size_t o_sp_J = L.take<double>(units_max);
     const size_t o_work = L.take<unsigned long long>(1);
+    const size_t o_cma = L.take<double>(4);
+    const size_t o_psig = L.take<double>(D);
+    const size_t o_pc = L.take<double>(D);
+    const size_t o_mu_prev = L.take<double>(D);
     const bool radix = p->N >= kRadixMinN;
     const size_t o_rka = L.take<unsigned long long>(radix ? N : 1);
     const size_t o_rkb = L.take<unsigned long long>(radix ? N : 1);
@@ -622,6 +659,11 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->grad = (float *)(b + o_grad);
     p->ends_f = (float4 *)(b + o_ends_f);
     p->work = (unsigned long long *)(b + o_work);
+    p->cma = (double *)(b + o_cma);
+    p->p_sigma = (double *)(b + o_psig);
+    p->p_c = (double *)(b + o_pc);
+    p->mu_prev = (double *)(b + o_mu_prev);
+    p->cmak = cma_consts(p->D, p->nu);
     p->rkey_a = (unsigned long long *)(b + o_rka);
     p->rkey_b = (unsigned long long *)(b + o_rkb);
     p->rval_a = (int *)(b + o_rva);
@@ -694,6 +736,7 @@ int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4])
     int rc = launch_init_distribution(p->consts, p->consts + 4, p->consts + 8, p->consts + 12, p->K,
                                       p->prm.init_std_frac, p->mu, p->C, p->ends_f, p->st);
     if (rc != CP_OK) return rc;
+    if ((rc = launch_cma_reset(p->prm.sigma, p->D, p->cma, p->p_sigma, p->p_c, p->st)) != CP_OK) return rc;
     p->iteration = 0;
     p->have_endpoints = true;
     return run_factor(p);
@@ -874,6 +917,25 @@ int cp_get_factor(const cp_planner *p, double *d_L)
     return CP_OK;
 }
 
+int cp_get_cma_state(const cp_planner *p, double *d_state)
+{
+    if (!p || !d_state) return set_error("NULL argument"), CP_ERR_ARG;
+    CP_CUDA(cudaMemcpyAsync(d_state, p->cma, sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    CP_CUDA(cudaMemcpyAsync(d_state + 1, p->p_sigma, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
+    CP_CUDA(cudaMemcpyAsync(d_state + 1 + p->D, p->p_c, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
+    return CP_OK;
+}
+
+int cp_set_cma_state(cp_planner *p, const double *d_state)
+{
+    if (!p || !d_state) return set_error("NULL argument"), CP_ERR_ARG;
+    if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
+    CP_CUDA(cudaMemcpyAsync(p->cma, d_state, sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    CP_CUDA(cudaMemcpyAsync(p->p_sigma, d_state + 1, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
+    CP_CUDA(cudaMemcpyAsync(p->p_c, d_state + 1 + p->D, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
+    return run_factor(p);
+}
+
 int cp_get_elites(const cp_planner *p, int32_t *d_idx)
 {
     if (!p || !d_idx) return set_error("NULL argument"), CP_ERR_ARG;
@@ -971,6 +1033,8 @@ int record_plan(cp_planner *p, int iters, const double *h_in, double *h_out, uin
     if ((rc = launch_init_distribution(p->consts, p->consts + 4, p->consts + 8, p->consts + 12, p->K,
                                        p->prm.init_std_frac, p->mu, p->C, p->ends_f, p->st)) != CP_OK)
         return rc;
+    if ((rc = launch_cma_reset(p->prm.sigma, p->D, p->cma, p->p_sigma, p->p_c, p->st)) != CP_OK) return rc;
+    p->iteration = 0;
     if ((rc = run_factor(p)) != CP_OK) return rc;
     for (int t = 0; t < iters; ++t) {
         if ((rc = run_sample(p, t, p->xi)) != CP_OK) return rc;

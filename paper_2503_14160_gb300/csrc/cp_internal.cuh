@@ -162,8 +162,8 @@ int launch_control_points(const double *q0, const double *qd, const double *mu, 
 
 int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out,
                   cudaStream_t st);
-int launch_factor(const double *C, double sigma2, int D, double *L, float *Lt_f,
-                  uint32_t *status, cudaStream_t st);
+int launch_factor(const double *C, double sigma2, const double *sigma_dev, int D, double *L,
+                  float *Lt_f, uint32_t *status, cudaStream_t st);
 int factor_configure();
 int launch_sample(const double *mu, const float *Lt_f, int N, int K, uint64_t seed,
                   uint32_t iter, uint32_t query, float *xi, cudaStream_t st);
@@ -175,6 +175,17 @@ int launch_scatter(const int *rank, const double *J, const float *xi, int N, int
                    int *elite, float *elites, double *best_J, cudaStream_t st);
 int launch_moments(const float *elites, const double *w, int nu, int D, double eps,
                    double *s2p, double *s1p, double *mu, double *C, cudaStream_t st);
+
+// Learning rates of the CMA-ES update (Hansen, "The CMA Evolution Strategy: A Tutorial",
+// default parameters) for dimension D and the log-rank weights of nu elites.
+struct CmaConsts {
+    double mu_eff, c_sigma, d_sigma, c_c, c_1, c_mu, chi_n;
+};
+CmaConsts cma_consts(int D, int nu);
+int launch_cma_reset(double sigma0, int D, double *cma, double *p_sigma, double *p_c, cudaStream_t st);
+int launch_cma_update(const float *elites, const double *w, int nu, int D, const double *mu_prev,
+                      const double *L, const CmaConsts &k, int t, double *s2p, double *s1p, double *mu,
+                      double *C, double *p_sigma, double *p_c, double *cma, cudaStream_t st);
 int update_chunks(int nu);
 int radix_tiles(int N);
 int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,

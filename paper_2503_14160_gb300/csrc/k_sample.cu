@@ -68,9 +68,10 @@ __device__ __forceinline__ double rsqrt_newton(double a)
 // transpose Lt[c][r] = L[r][c] for the sampler. A pivot that is not positive raises
 // DEV_ERR_NOT_PD (and is replaced by 1 so that the kernel finishes).
 __global__ void __launch_bounds__(kFactorThreads)
-k_factor(const double *__restrict__ C, double sigma2, int D, double *L, float *Lt,
-         uint32_t *status)
+k_factor(const double *__restrict__ C, double sigma2, const double *__restrict__ sigma_dev, int D, double *L,
+         float *Lt, uint32_t *status)
 {
+    if (sigma_dev != nullptr) sigma2 = sigma_dev[0] * sigma_dev[0];   // the step size kept on the device
     extern __shared__ double A[];
     __shared__ double s_d[2];
     __shared__ double s_t[kFactorMaxD];
@@ -196,11 +197,11 @@ int factor_configure()
     return CP_OK;
 }
 
-int launch_factor(const double *C, double sigma2, int D, double *L, float *Lt_f,
-                  uint32_t *status, cudaStream_t st)
+int launch_factor(const double *C, double sigma2, const double *sigma_dev, int D, double *L,
+                  float *Lt_f, uint32_t *status, cudaStream_t st)
 {
     const size_t smem = sizeof(double) * (size_t)D * (D + 1);
-    k_factor<<<1, kFactorThreads, smem, st>>>(C, sigma2, D, L, Lt_f, status);
+    k_factor<<<1, kFactorThreads, smem, st>>>(C, sigma2, sigma_dev, D, L, Lt_f, status);
     CP_LAUNCHED("k_factor");
     return CP_OK;
 }

@@ -281,6 +281,112 @@ __global__ void k_gather_elites(const int *__restrict__ sorted, const double *__
     for (int c = lane; c < D; c += 32) elites[(size_t)r * D + c] = xi[(size_t)i * D + c];
 }
 
+// ---------------------------------------------------------------- CMA-ES update rule
+// The update of the CMA-ES tutorial (Hansen 2016) in place of steps (5)-(6), from the same
+// per-chunk moments about the best elite x_(1): S1 = sum_j w_j y_j, S2 = sum_j w_j y_j y_j^T,
+// y_j = x_(j) - x_(1). State cma[4] = {sigma, sigma before the update, h_sigma, |p_sigma|}.
+constexpr int kCmaThreads = 4 * CP_MAX_WAYPOINTS;   // one thread per coordinate, D <= 128
+
+__global__ void k_cma_reset(double sigma0, int D, double *cma, double *p_sigma, double *p_c)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < D) {
+        p_sigma[i] = 0.0;
+        p_c[i] = 0.0;
+    }
+    if (i == 0) {
+        cma[0] = sigma0;
+        cma[1] = sigma0;
+        cma[2] = 1.0;
+        cma[3] = 0.0;
+    }
+}
+
+// One CTA: the new mean m' = x_(1) + S1, the mean shift m' - m, z = L^-1 (m' - m) by forward
+// substitution with the current factor L (L L^T = sigma^2 C, so z = L_C^-1 (m' - m) / sigma
+// with L_C the Cholesky factor of C), the step-size path and its length, h_sigma, the
+// covariance path, and sigma'.
+__global__ void __launch_bounds__(kCmaThreads)
+k_cma_paths(const double *__restrict__ s1p, int n_chunks, int D, const float *__restrict__ elites,
+            const double *__restrict__ mu_prev, const double *__restrict__ L, CmaConsts k, int t,
+            double *mu, double *p_sigma, double *p_c, double *cma)
+{
+    __shared__ double s_b[kCmaThreads];
+    __shared__ double s_z;
+    __shared__ double s_red[kCmaThreads / 32];
+    const int r = threadIdx.x;
+    double shift = 0.0;
+    if (r < D) {
+        double s1 = 0.0;
+        for (int c = 0; c < n_chunks; ++c) s1 += s1p[(size_t)r * n_chunks + c];
+        const double m_new = (double)elites[r] + s1;
+        shift = m_new - mu_prev[r];
+        mu[r] = m_new;
+        s_b[r] = shift;
+    }
+    __syncthreads();
+    double z = 0.0;
+    for (int j = 0; j < D; ++j) {
+        if (r == j) {
+            z = s_b[j] / L[(size_t)j * D + j];
+            s_z = z;
+        }
+        __syncthreads();
+        if (r > j && r < D) s_b[r] = fma(-L[(size_t)r * D + j], s_z, s_b[r]);
+        __syncthreads();
+    }
+    const double sigma = cma[0];
+    double ps = 0.0;
+    if (r < D) {
+        ps = fma(1.0 - k.c_sigma, p_sigma[r], sqrt(k.c_sigma * (2.0 - k.c_sigma) * k.mu_eff) * z);
+        p_sigma[r] = ps;
+    }
+    double v = ps * ps;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((r & 31) == 0) s_red[r >> 5] = v;
+    __syncthreads();
+    double n2 = 0.0;
+    for (int w = 0; w < kCmaThreads / 32; ++w) n2 += s_red[w];
+    const double norm = sqrt(n2);
+    const double h = norm / sqrt(1.0 - pow(1.0 - k.c_sigma, 2.0 * (t + 1)))
+                     < (1.4 + 2.0 / (D + 1)) * k.chi_n ? 1.0 : 0.0;
+    if (r < D) p_c[r] = fma(1.0 - k.c_c, p_c[r], h * sqrt(k.c_c * (2.0 - k.c_c) * k.mu_eff) * (shift / sigma));
+    if (r == 0) {
+        cma[1] = sigma;
+        cma[2] = h;
+        cma[3] = norm;
+        cma[0] = sigma * exp((k.c_sigma / k.d_sigma) * (norm / k.chi_n - 1.0));
+    }
+}
+
+// One warp per lower-triangle entry: the elites' weighted scatter about the OLD mean m from
+// the moments about x_(1) (with d = x_(1) - m and weights summing to one:
+// S2 + S1 d^T + d S1^T + d d^T), then C' = a C + c_1 p_c p_c^T + c_mu scatter / sigma^2 with
+// a = 1 + c_1 (1 - h_sigma) c_c (2 - c_c) - c_1 - c_mu.
+__global__ void k_cma_cov(const double *__restrict__ s2p, const double *__restrict__ s1p, int n_chunks,
+                          int D, const float *__restrict__ elites, const double *__restrict__ mu_prev,
+                          const double *__restrict__ p_c, const double *__restrict__ cma, CmaConsts k,
+                          double *C)
+{
+    const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= D * (D + 1) / 2) return;
+    int r, c;
+    tri_index(e, r, c);
+    const double s2 = warp_sum(s2p + ((size_t)r * D + c) * n_chunks, n_chunks, lane);
+    const double sr = warp_sum(s1p + (size_t)r * n_chunks, n_chunks, lane);
+    const double sc = warp_sum(s1p + (size_t)c * n_chunks, n_chunks, lane);
+    if (lane != 0) return;
+    const double dr = (double)elites[r] - mu_prev[r], dc = (double)elites[c] - mu_prev[c];
+    const double scatter = fma(dr, dc, fma(dr, sc, fma(sr, dc, s2)));
+    const double sig = cma[1], h = cma[2];
+    const double a = 1.0 + k.c_1 * (1.0 - h) * k.c_c * (2.0 - k.c_c) - k.c_1 - k.c_mu;
+    const double v = fma(a, C[(size_t)r * D + c], fma(k.c_1 * p_c[r], p_c[c], k.c_mu * scatter / (sig * sig)));
+    C[(size_t)r * D + c] = v;
+    C[(size_t)c * D + r] = v;
+}
+
 }  // namespace
 
 int radix_tiles(int N) { return (N + kRadixTile - 1) / kRadixTile; }
@@ -361,6 +467,34 @@ int launch_scatter(const int *rank, const double *J, const float *xi, int N, int
     const int blocks = (N * 32 + threads - 1) / threads;
     k_scatter<<<blocks, threads, 0, st>>>(rank, J, xi, N, nu, D, elite, elites, best_J);
     CP_LAUNCHED("k_scatter");
+    return CP_OK;
+}
+
+int launch_cma_reset(double sigma0, int D, double *cma, double *p_sigma, double *p_c, cudaStream_t st)
+{
+    k_cma_reset<<<(D + 127) / 128, 128, 0, st>>>(sigma0, D, cma, p_sigma, p_c);
+    CP_LAUNCHED("k_cma_reset");
+    return CP_OK;
+}
+
+// CMA-ES update: mu_prev must hold the mean before the update; mu, C, p_sigma, p_c and cma
+// are updated in place (L is the factor of sigma^2 C before the update).
+int launch_cma_update(const float *elites, const double *w, int nu, int D, const double *mu_prev,
+                      const double *L, const CmaConsts &k, int t, double *s2p, double *s1p, double *mu,
+                      double *C, double *p_sigma, double *p_c, double *cma, cudaStream_t st)
+{
+    const int per = per_chunk(nu);
+    const int n_chunks = (nu + per - 1) / per;
+    const int tiles = (D + 15) / 16;
+    dim3 grid(tiles * (tiles + 1) / 2, n_chunks);
+    k_moments_partial<<<grid, 256, 0, st>>>(elites, w, nu, D, per, n_chunks, s2p, s1p);
+    CP_LAUNCHED("k_moments_partial");
+    k_cma_paths<<<1, kCmaThreads, 0, st>>>(s1p, n_chunks, D, elites, mu_prev, L, k, t, mu, p_sigma, p_c, cma);
+    CP_LAUNCHED("k_cma_paths");
+    const int entries = D * (D + 1) / 2;
+    k_cma_cov<<<(entries * 32 + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, elites, mu_prev, p_c, cma,
+                                                          k, C);
+    CP_LAUNCHED("k_cma_cov");
     return CP_OK;
 }
 

@@ -48,7 +48,7 @@ class Setup:
 
     def __init__(self, crane, scene, N, K, S, seed=0, n_elites=0, w_c=100.0, w_l=100.0,
                  lambda_c=1.0, eps=1e-8, sigma=1.0, grid_cell=0.0, grid_half_extent=0.0,
-                 exhaustive=0):
+                 exhaustive=0, update_rule=0):
         import torch
         import oracle
         from paper_2503_14160_gb300 import craneplan as cp
@@ -60,7 +60,7 @@ class Setup:
         params = cp.make_params(N, K, S, n_elites=n_elites, w_c=w_c, w_l=w_l,
                                 lambda_c=lambda_c, eps=eps, sigma=sigma, seed=seed,
                                 grid_cell=grid_cell, grid_half_extent=grid_half_extent,
-                                eval_exhaustive=exhaustive)
+                                eval_exhaustive=exhaustive, update_rule=update_rule)
         self.planner = cp.Planner(crane, scene, params)
         self.nu = self.planner.nu
         self.problem = oracle.Problem(crane, scene, oracle.CostParams(K=K, S=S, w_c=w_c, w_l=w_l,
