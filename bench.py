@@ -152,12 +152,18 @@ EVAL_PROFILE = os.path.join(ROOT, "profiles", "k_eval_broad_single_large.md")
 
 
 def eval_source_sha1():
-    """SHA-1 over the sources of the evaluation kernel (the key of its committed profile)."""
+    """SHA-1 over the sources of the evaluation kernel (the key of its committed profile):
+    k_eval.cu and eval_common.cuh whole, and cp_internal.cuh up to its first launcher
+    declaration (the device records the kernel reads; the host-side declarations after it
+    do not change the kernel)."""
     import hashlib
     h = hashlib.sha1()
     for path in EVAL_SOURCES:
         with open(path, "rb") as f:
-            h.update(f.read())
+            data = f.read()
+        if path.endswith("cp_internal.cuh"):
+            data = data[:data.index(b"int launch_eval(")]
+        h.update(data)
     return h.hexdigest()
 
 
@@ -230,7 +236,8 @@ def run_ours(args):
     crane = workloads.forestry_crane()
     scene = workloads.make_scene(wl)
     params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank,
-                            grid_cell=wl.grid_cell, eval_exhaustive=int(args.exhaustive))
+                            grid_cell=wl.grid_cell, eval_exhaustive=int(args.exhaustive),
+                            update_rule=cp.CP_UPDATE_CMAES if args.update_rule == "cmaes" else cp.CP_UPDATE_PAPER)
     planner = cp.Planner(crane, scene, params)
     h = planner.handle
     q0, qd, ok = select_endpoints_gpu(cp, planner, crane, wl.seed, rank)
@@ -329,7 +336,7 @@ def run_ours(args):
                                       scene.n_cyl, iters),
                        "step": "one plan", "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "flushed between steps (256 MB write)",
-                       "endpoints_ok": bool(ok)},
+                       "endpoints_ok": bool(ok), "update_rule": args.update_rule},
             "ms_per_plan": ms,
             "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "ms_per_plan": ms_e2e,
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
@@ -857,6 +864,8 @@ def main():
     ap.add_argument("--iterations", type=int, default=0, help="override iterations per plan")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--update-rule", default="paper", choices=["paper", "cmaes"],
+                    help="steps (5)-(6) as Algorithm 1 prints them, or the CMA-ES update")
     ap.add_argument("--exhaustive", action="store_true",
                     help="evaluate every sphere against every obstacle (no broad phase)")
     args = ap.parse_args()

@@ -305,16 +305,23 @@ __global__ void k_cma_reset(double sigma0, int D, double *cma, double *p_sigma, 
 // One CTA: the new mean m' = x_(1) + S1, the mean shift m' - m, z = L^-1 (m' - m) by forward
 // substitution with the current factor L (L L^T = sigma^2 C, so z = L_C^-1 (m' - m) / sigma
 // with L_C the Cholesky factor of C), the step-size path and its length, h_sigma, the
-// covariance path, and sigma'.
+// covariance path, and sigma'. L is staged in shared memory (row stride D + 1); warp 0
+// runs the substitution column by column, lane l holding rows l, l + 32, l + 64, l + 96,
+// each new z_j passed by a shuffle, so the dependent chain has no block barrier.
 __global__ void __launch_bounds__(kCmaThreads)
 k_cma_paths(const double *__restrict__ s1p, int n_chunks, int D, const float *__restrict__ elites,
             const double *__restrict__ mu_prev, const double *__restrict__ L, CmaConsts k, int t,
             double *mu, double *p_sigma, double *p_c, double *cma)
 {
+    extern __shared__ double s_L[];   // [D][D + 1]
     __shared__ double s_b[kCmaThreads];
-    __shared__ double s_z;
     __shared__ double s_red[kCmaThreads / 32];
-    const int r = threadIdx.x;
+    const int r = threadIdx.x, lane = r & 31;
+    const int ld = D + 1;
+    for (int idx = r; idx < D * D; idx += kCmaThreads) {
+        const int i = idx / D, j = idx - i * D;
+        if (j <= i) s_L[i * ld + j] = L[idx];
+    }
     double shift = 0.0;
     if (r < D) {
         double s1 = 0.0;
@@ -325,16 +332,31 @@ k_cma_paths(const double *__restrict__ s1p, int n_chunks, int D, const float *__
         s_b[r] = shift;
     }
     __syncthreads();
-    double z = 0.0;
-    for (int j = 0; j < D; ++j) {
-        if (r == j) {
-            z = s_b[j] / L[(size_t)j * D + j];
-            s_z = z;
+    if (r < 32) {
+        double b[4], rinv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = lane + 32 * i;
+            b[i] = row < D ? s_b[row] : 0.0;
+            rinv[i] = row < D ? 1.0 / s_L[row * ld + row] : 0.0;
         }
-        __syncthreads();
-        if (r > j && r < D) s_b[r] = fma(-L[(size_t)r * D + j], s_z, s_b[r]);
-        __syncthreads();
+#pragma unroll
+        for (int slot = 0; slot < 4; ++slot) {
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = slot * 32 + jj;
+                if (j >= D) break;
+                const double zj = __shfl_sync(0xffffffffu, b[slot] * rinv[slot], jj);
+                if (lane == jj) s_b[j] = zj;   // z_j replaces b_j
+#pragma unroll
+                for (int i = slot; i < 4; ++i) {
+                    const int row = lane + 32 * i;
+                    if (row > j && row < D) b[i] = fma(-s_L[row * ld + j], zj, b[i]);
+                }
+            }
+        }
     }
+    __syncthreads();
+    const double z = r < D ? s_b[r] : 0.0;
     const double sigma = cma[0];
     double ps = 0.0;
     if (r < D) {
@@ -344,7 +366,7 @@ k_cma_paths(const double *__restrict__ s1p, int n_chunks, int D, const float *__
     double v = ps * ps;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if ((r & 31) == 0) s_red[r >> 5] = v;
+    if (lane == 0) s_red[r >> 5] = v;
     __syncthreads();
     double n2 = 0.0;
     for (int w = 0; w < kCmaThreads / 32; ++w) n2 += s_red[w];
@@ -441,7 +463,13 @@ static int per_chunk(int nu)
     return (per + kChunk - 1) / kChunk * kChunk;
 }
 
-int update_configure() { return CP_OK; }
+int update_configure()
+{
+    const int Dm = 4 * CP_MAX_WAYPOINTS;
+    CP_CUDA(cudaFuncSetAttribute(k_cma_paths, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double) * Dm * (Dm + 1))));
+    return CP_OK;
+}
 
 int launch_weights(int nu, double *w, cudaStream_t st)
 {
@@ -489,7 +517,8 @@ int launch_cma_update(const float *elites, const double *w, int nu, int D, const
     dim3 grid(tiles * (tiles + 1) / 2, n_chunks);
     k_moments_partial<<<grid, 256, 0, st>>>(elites, w, nu, D, per, n_chunks, s2p, s1p);
     CP_LAUNCHED("k_moments_partial");
-    k_cma_paths<<<1, kCmaThreads, 0, st>>>(s1p, n_chunks, D, elites, mu_prev, L, k, t, mu, p_sigma, p_c, cma);
+    const size_t smem = sizeof(double) * (size_t)D * (D + 1);
+    k_cma_paths<<<1, kCmaThreads, smem, st>>>(s1p, n_chunks, D, elites, mu_prev, L, k, t, mu, p_sigma, p_c, cma);
     CP_LAUNCHED("k_cma_paths");
     const int entries = D * (D + 1) / 2;
     k_cma_cov<<<(entries * 32 + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, elites, mu_prev, p_c, cma,
