@@ -358,6 +358,17 @@ int stage_scene(cp_planner *p, const cp_scene *sc)
     if (rc != CP_OK) return rc;
     p->sdev.n_cyl = sc->n_cyl;
     p->sdev.n_box = sc->n_box;
+    double zlo = 1e30, zhi = -1e30;
+    for (int i = 0; i < sc->n_cyl; ++i) {
+        zlo = std::min(zlo, sc->cyl[i].z_lo);
+        zhi = std::max(zhi, sc->cyl[i].z_hi);
+    }
+    for (int i = 0; i < sc->n_box; ++i) {
+        zlo = std::min(zlo, sc->box[i].lo[2]);
+        zhi = std::max(zhi, sc->box[i].hi[2]);
+    }
+    p->sdev.z_lo_all = (float)zlo;
+    p->sdev.z_hi_all = (float)zhi;
     if (p->use_grid) {
         const int64_t need = grid_items_bound(sc, p->mdev.r_max, p->prm.grid_cell);
         if (need > p->grid_cap)

@@ -65,7 +65,14 @@ struct SceneDev {
     int n_box;
     const float4 *cyl_group;   // [n_groups(n_cyl)] {gx, gy, 0, radius}: circle that holds every
                                // member's reach (kGroup consecutive cylinders per group)
+    float z_lo_all = -1e30f;   // lowest z_lo and highest z_hi over all obstacles (unbounded
+    float z_hi_all = 1e30f;    // where the caller does not know them)
 };
+
+// Vertical gate of the collision tests: only penetration counts, so a sphere whose centre
+// lies below an obstacle's z_lo or above its z_hi by more than r_max (plus 1 mm, far above
+// the FP32 rounding of z) cannot penetrate it and needs no distance.
+constexpr float kZGate = 1e-3f;
 
 constexpr int kGroup = 8;    // cylinders per broad-phase group
 __host__ __device__ inline int n_groups(int n_cyl) { return (n_cyl + kGroup - 1) / kGroup; }

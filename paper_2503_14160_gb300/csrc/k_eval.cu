@@ -95,17 +95,18 @@ __device__ __noinline__ bool stage_bulk(uint64_t *bar, float4 *s_filt, float4 *s
     return true;
 }
 
-// Exact signed distance of every sphere whose filter test passes against one cylinder
-// (f = {cx, cy, W}, e = {R, z_lo, z_hi}); +inf when none passes.
+// Exact signed distance of every sphere whose filter test and vertical gate pass against
+// one cylinder (f = {cx, cy, W}, e = {R, z_lo, z_hi}); +inf when none passes.
 template <int NSPH>
 __device__ __forceinline__ float exact_cylinders(const ModelDev &m, const float *X, const float *Y,
                                               const float *Z, const float *T, float4 f, float4 e)
 {
     float d = CUDART_INF_F;
+    const float zlo = e.y - m.r_max - kZGate, zhi = e.z + m.r_max + kZGate;
 #pragma unroll
     for (int s = 0; s < NSPH; ++s) {
         const float g = fmaf(X[s], f.x, fmaf(Y[s], f.y, f.z));
-        if (g < T[s])
+        if (g < T[s] && Z[s] > zlo && Z[s] < zhi)
             d = fminf(d, sdf_cylinder(-0.5f * X[s], -0.5f * Y[s], Z[s], f.x, f.y, e) - m.sph[s].radius);
     }
     return d;
@@ -113,7 +114,8 @@ __device__ __forceinline__ float exact_cylinders(const ModelDev &m, const float 
 
 // Exact distance of every sphere whose polar filter passes against one cylinder: with the
 // obstacle centre at p along the lane's plane and q across it, sphere s passes when
-// (h_s - p)^2 < (R + r_max)^2 + margin - q^2 = rhs. The distance itself is taken from the
+// (h_s - p)^2 < (R + r_max)^2 + margin - q^2 = rhs and its centre is within the cylinder's
+// height range widened by r_max and the gate. The distance itself is taken from the
 // Cartesian centre (c1 h, s1 h, z), rounded products (no contraction into the distance's
 // differences), the same values the exhaustive form uses.
 template <int NSPH>
@@ -122,10 +124,11 @@ __device__ __forceinline__ float exact_polar(const ModelDev &m, const float *H, 
                                              float4 e)
 {
     float d = CUDART_INF_F;
+    const float zlo = e.y - m.r_max - kZGate, zhi = e.z + m.r_max + kZGate;
 #pragma unroll
     for (int s = 0; s < NSPH; ++s) {
         const float dh = H[s] - p;
-        if (fmaf(dh, dh, -rhs) < 0.f)
+        if (fmaf(dh, dh, -rhs) < 0.f && Z[s] > zlo && Z[s] < zhi)
             d = fminf(d, sdf_cylinder(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], f.x, f.y, e) -
                              m.sph[s].radius);
     }
@@ -196,11 +199,19 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
                 const float q = fmaf(c1, f.y, -(s1 * f.x));
                 const float rhs = fmaf(-q, q, e.w);
                 const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
+                // per sphere pair: the polar filter, and the vertical gate as
+                // (z - z_mid)^2 < (half height + r_max + gate)^2; a sphere passes when both
+                // are negative, i.e. when their maximum is
+                const float zmid = 0.5f * (e.y + e.z), zh = fmaf(0.5f, e.z - e.y, m.r_max + kZGate);
+                const float2 mz2 = make_float2(-zmid, -zmid), mzh2 = make_float2(-zh * zh, -zh * zh);
                 float2 t[NSPH / 2];
 #pragma unroll
                 for (int k = 0; k < NSPH / 2; ++k) {
                     const float2 dh = __fadd2_rn(H2[k], mp2);
-                    t[k] = __ffma2_rn(dh, dh, mr2);
+                    const float2 th = __ffma2_rn(dh, dh, mr2);
+                    const float2 dz = __fadd2_rn(make_float2(Z[2 * k], Z[2 * k + 1]), mz2);
+                    const float2 tz = __ffma2_rn(dz, dz, mzh2);
+                    t[k] = make_float2(fmaxf(th.x, tz.x), fmaxf(th.y, tz.y));
                 }
                 if (any_below<NSPH>(t, zero))
                     dmin = fminf(dmin, exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e));

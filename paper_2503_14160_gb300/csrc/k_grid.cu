@@ -128,7 +128,11 @@ __device__ __forceinline__ float record_distance(const SceneDev &sc, float4 rec,
                                                  float z, float r)
 {
     const int id = __float_as_int(rec.w);
-    if (id < sc.n_cyl) return sdf_cylinder(x, y, z, rec.x, rec.y, __ldg(sc.cyl_exact + id)) - r;
+    if (id < sc.n_cyl) {
+        const float4 e = __ldg(sc.cyl_exact + id);
+        if (z < e.y - r - kZGate || z > e.z + r + kZGate) return CUDART_INF_F;   // cannot penetrate
+        return sdf_cylinder(x, y, z, rec.x, rec.y, e) - r;
+    }
     const float4 c = __ldg(sc.box_c + id - sc.n_cyl), h = __ldg(sc.box_h + id - sc.n_cyl);
     return sdf_box(x, y, z, c, h) - r;
 }
@@ -187,6 +191,7 @@ k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs
                 it = 0;
                 end = __ldg(g.n_outside);
             }
+            if (sp.y < sc.z_lo_all - r - kZGate || sp.y > sc.z_hi_all + r + kZGate) end = it;   // above or below every obstacle
             tested += (uint32_t)(end - it);
             for (; it < end; ++it) {
                 const float4 rec = __ldg(list + it);
