@@ -111,7 +111,9 @@ k_moments_partial(const float *__restrict__ elites, const double *__restrict__ w
     const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
     const bool diag = tr == tc;
     const int j_end = min(nu, (p + 1) * per);
-    double acc = 0.0, acc1 = 0.0;
+    // four interleaved accumulators: a dependent FP64 FMA waits tens of cycles, so one
+    // running sum would leave the FP64 pipe idle between its steps
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, acc1 = 0.0;
     for (int j0 = p * per; j0 < j_end; j0 += kChunk) {
         const int cnt = min(j_end - j0, kChunk);
         __syncthreads();
@@ -123,12 +125,19 @@ k_moments_partial(const float *__restrict__ elites, const double *__restrict__ w
             yc[j][k] = c < D ? (double)row[c] - (double)elites[c] : 0.0;
         }
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) acc = fma(wyr[j][a], yc[j][b], acc);
+        int j = 0;
+        for (; j + 3 < cnt; j += 4) {
+            a0 = fma(wyr[j][a], yc[j][b], a0);
+            a1 = fma(wyr[j + 1][a], yc[j + 1][b], a1);
+            a2 = fma(wyr[j + 2][a], yc[j + 2][b], a2);
+            a3 = fma(wyr[j + 3][a], yc[j + 3][b], a3);
+        }
+        for (; j < cnt; ++j) a0 = fma(wyr[j][a], yc[j][b], a0);
         if (diag && b == 0)
             for (int j = 0; j < cnt; ++j) acc1 += wyr[j][a];
     }
     const int r = tr * 16 + a, c = tc * 16 + b;
-    if (r < D && c <= r) s2p[((size_t)r * D + c) * n_chunks + p] = acc;
+    if (r < D && c <= r) s2p[((size_t)r * D + c) * n_chunks + p] = (a0 + a1) + (a2 + a3);
     if (diag && b == 0 && r < D) s1p[(size_t)r * n_chunks + p] = acc1;
 }
 
