@@ -209,6 +209,25 @@ static __device__ __forceinline__ UnitFrame unit_frame(float s1, float c1, const
     return f;
 }
 
+// The unit box of unit_frame over the spheres whose centre height lies in (zlo, zhi), the
+// band in which some obstacle can be penetrated at all; a lane with no such sphere adds
+// its first sphere (a larger box is still a bound).
+template <int NSPH>
+static __device__ __forceinline__ UnitFrame unit_frame_band(float s1, float c1, const float *H, const float *Z,
+                                                            float zlo, float zhi)
+{
+    float hmin = CUDART_INF_F, hmax = -CUDART_INF_F;
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s) {
+        const bool in = Z[s] > zlo && Z[s] < zhi;
+        hmin = in ? fminf(hmin, H[s]) : hmin;
+        hmax = in ? fmaxf(hmax, H[s]) : hmax;
+    }
+    if (hmin > hmax) hmin = hmax = H[0];
+    const float hb[2] = {hmin, hmax};
+    return unit_frame<2>(s1, c1, hb);
+}
+
 // True when the obstacle record r = {cx, cy, ., reach} may come within reach (plus
 // `extra`, a further dilation for longer-range terms) of the unit.
 static __device__ __forceinline__ bool unit_near(const UnitFrame &f, float4 r, float extra = 0.f)

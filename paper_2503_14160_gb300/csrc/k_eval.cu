@@ -169,10 +169,16 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
         float H[NSPH], Z[NSPH], s1, c1;
         crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
-        const UnitFrame fr = unit_frame<NSPH>(s1, c1, H);
+        // Spheres above or below every obstacle by more than r_max (the vertical gate over
+        // the whole scene) can penetrate nothing: they leave the unit box, and their packed
+        // h is pushed far away so that no polar filter passes them.
+        const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
+        const UnitFrame fr = unit_frame_band<NSPH>(s1, c1, H, Z, zlo, zhi);
         float2 H2[NSPH / 2];
 #pragma unroll
-        for (int q = 0; q < NSPH / 2; ++q) H2[q] = make_float2(H[2 * q], H[2 * q + 1]);
+        for (int q = 0; q < NSPH / 2; ++q)
+            H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
+                                Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
 
         float dmin = CUDART_INF_F;
         const int n_grp = n_groups(sc.n_cyl);
@@ -199,19 +205,11 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
                 const float q = fmaf(c1, f.y, -(s1 * f.x));
                 const float rhs = fmaf(-q, q, e.w);
                 const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
-                // per sphere pair: the polar filter, and the vertical gate as
-                // (z - z_mid)^2 < (half height + r_max + gate)^2; a sphere passes when both
-                // are negative, i.e. when their maximum is
-                const float zmid = 0.5f * (e.y + e.z), zh = fmaf(0.5f, e.z - e.y, m.r_max + kZGate);
-                const float2 mz2 = make_float2(-zmid, -zmid), mzh2 = make_float2(-zh * zh, -zh * zh);
                 float2 t[NSPH / 2];
 #pragma unroll
                 for (int k = 0; k < NSPH / 2; ++k) {
                     const float2 dh = __fadd2_rn(H2[k], mp2);
-                    const float2 th = __ffma2_rn(dh, dh, mr2);
-                    const float2 dz = __fadd2_rn(make_float2(Z[2 * k], Z[2 * k + 1]), mz2);
-                    const float2 tz = __ffma2_rn(dz, dz, mzh2);
-                    t[k] = make_float2(fmaxf(th.x, tz.x), fmaxf(th.y, tz.y));
+                    t[k] = __ffma2_rn(dh, dh, mr2);
                 }
                 if (any_below<NSPH>(t, zero))
                     dmin = fminf(dmin, exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e));
