@@ -229,6 +229,9 @@ def run_ours(args):
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    # a stream of our own: cp_plan records its iterations as a CUDA graph there (the legacy
+    # default stream cannot be captured); every event below sits on this stream
+    torch.cuda.set_stream(torch.cuda.Stream())
     build.build()
     cp.load()
     wl = workloads.WORKLOADS[args.workload]

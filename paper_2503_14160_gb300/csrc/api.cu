@@ -168,6 +168,14 @@ struct cp_planner {
     float4 q0f{}, qdf{};
     int iteration = 0;
     Timer timer;
+    // cp_plan's iterations recorded as one CUDA graph (launch gaps between the small
+    // dependent kernels vanish); valid for one start iteration, count, scene and end points
+    cudaGraphExec_t plan_exec = nullptr;
+    int plan_start = -1, plan_iters = -1;
+    float4 plan_q0{}, plan_qd{};
+    SceneDev plan_sdev{};
+    GridDev plan_gdev{};
+    int64_t plan_nodes = 0;   // kernels in the recorded graph
 };
 
 namespace cp {
@@ -721,6 +729,7 @@ void cp_destroy(cp_planner *p)
     if (!p) return;
     cudaStreamSynchronize(p->st);
     p->timer.destroy();
+    if (p->plan_exec) cudaGraphExecDestroy(p->plan_exec);
     if (p->base) cudaFree(p->base);
     delete p;
 }
@@ -779,16 +788,94 @@ int cp_update(cp_planner *p, const double *d_J, const float *d_xi)
     return run_update(p, d_J, d_xi);
 }
 
+bool same_scene(const SceneDev &a, const SceneDev &b)
+{
+    return a.cyl_filt == b.cyl_filt && a.cyl_exact == b.cyl_exact && a.n_cyl == b.n_cyl && a.box_c == b.box_c &&
+           a.box_h == b.box_h && a.n_box == b.n_box && a.cyl_group == b.cyl_group &&
+           memcmp(&a.z_lo_all, &b.z_lo_all, sizeof(float)) == 0 && memcmp(&a.z_hi_all, &b.z_hi_all, sizeof(float)) == 0;
+}
+
+bool same_grid(const GridDev &a, const GridDev &b)
+{
+    return memcmp(&a.x0, &b.x0, sizeof(float)) == 0 && memcmp(&a.y0, &b.y0, sizeof(float)) == 0 &&
+           memcmp(&a.inv_h, &b.inv_h, sizeof(float)) == 0 && a.nx == b.nx && a.ny == b.ny &&
+           a.cell_start == b.cell_start && a.items == b.items && a.outside == b.outside && a.n_outside == b.n_outside;
+}
+
+// The iterations of cp_plan from p->iteration as one CUDA graph launch, recorded on first
+// use and again whenever the start iteration, the count, the scene records or the end
+// points (kernel arguments of the recorded launches) differ from the recorded ones.
+int run_plan_graph(cp_planner *p, int iters)
+{
+    const bool same = p->plan_exec && p->plan_start == p->iteration && p->plan_iters == iters &&
+                      same_scene(p->plan_sdev, p->sdev) && same_grid(p->plan_gdev, p->gdev) &&
+                      memcmp(&p->plan_q0, &p->q0f, sizeof(float4)) == 0 &&
+                      memcmp(&p->plan_qd, &p->qdf, sizeof(float4)) == 0;
+    const int start = p->iteration;
+    if (!same) {
+        if (p->plan_exec) {
+            cudaGraphExecDestroy(p->plan_exec);
+            p->plan_exec = nullptr;
+        }
+        const int64_t launches_before = g_launches.load();
+        const cudaError_t e_begin = cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal);
+        if (e_begin != cudaSuccess) {
+            cudaGetLastError();   // clear it, so that later launch checks do not see it
+            return cuda_fail(e_begin, "cudaStreamBeginCapture");
+        }
+        int rc = CP_OK;
+        for (int it = 0; it < iters && rc == CP_OK; ++it) {
+            rc = run_sample(p, p->iteration, p->xi);
+            if (rc == CP_OK) rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr);
+            if (rc == CP_OK) rc = run_update(p, p->J, p->xi);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(p->st, &graph);
+        p->iteration = start;
+        p->plan_nodes = g_launches.load() - launches_before;   // recorded, not run
+        g_launches.fetch_sub(p->plan_nodes);
+        if (rc != CP_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e_end != cudaSuccess) return cuda_fail(e_end, "cudaStreamEndCapture");
+        const cudaError_t e_inst = cudaGraphInstantiate(&p->plan_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e_inst != cudaSuccess) {
+            p->plan_exec = nullptr;
+            return cuda_fail(e_inst, "cudaGraphInstantiate");
+        }
+        p->plan_start = start;
+        p->plan_iters = iters;
+        p->plan_sdev = p->sdev;
+        p->plan_gdev = p->gdev;
+        p->plan_q0 = p->q0f;
+        p->plan_qd = p->qdf;
+    }
+    CP_CUDA(cudaGraphLaunch(p->plan_exec, p->st));
+    g_launches.fetch_add(p->plan_nodes, std::memory_order_relaxed);
+    p->iteration = start + iters;
+    return CP_OK;
+}
+
 int cp_plan(cp_planner *p, int32_t iters, double *h_ctrl, cp_plan_stats *stats)
 {
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     if (iters < 0) return set_error("iters must be >= 0"), CP_ERR_ARG;
     if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
     int rc;
-    for (int it = 0; it < iters; ++it) {
-        if ((rc = run_sample(p, p->iteration, p->xi)) != CP_OK) return rc;
-        if ((rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr)) != CP_OK) return rc;
-        if ((rc = run_update(p, p->J, p->xi)) != CP_OK) return rc;
+    // graphs are recorded from a stream of the caller's; the legacy default stream cannot
+    // be captured, so plans on it (and timed plans, whose stage events sit between the
+    // kernels) launch kernel by kernel
+    const bool capturable = p->st != nullptr && p->st != cudaStreamLegacy && p->st != cudaStreamPerThread;
+    if (p->timer.on || iters == 0 || !capturable) {
+        for (int it = 0; it < iters; ++it) {
+            if ((rc = run_sample(p, p->iteration, p->xi)) != CP_OK) return rc;
+            if ((rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr)) != CP_OK) return rc;
+            if ((rc = run_update(p, p->J, p->xi)) != CP_OK) return rc;
+        }
+    } else if ((rc = run_plan_graph(p, iters)) != CP_OK) {
+        return rc;
     }
     if ((rc = launch_mean_to_candidate(p->mu, p->D, p->mean_xi, p->st)) != CP_OK) return rc;
     if ((rc = run_eval(p, p->mean_xi, 1, p->mean_J, p->mean_flag, p->mean_terms, nullptr, nullptr)) != CP_OK)

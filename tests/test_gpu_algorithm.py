@@ -271,3 +271,38 @@ def test_plan_deterministic_and_resumable(lib, crane):
         assert st2["iteration"] == 20
     finally:
         s.close()
+
+
+def test_plan_graph_equals_stream_launches(lib, crane):
+    """On a stream of the caller's, cp_plan replays its iterations as a recorded CUDA graph;
+    the plans equal those launched kernel by kernel on the default stream, bit for bit,
+    also after new end points, a new iteration count and a new scene re-record the graph."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("single_small")
+    scene = workloads.make_scene(workloads.WORKLOADS["single_small"])
+    params = lib.make_params(256, 8, 32, seed=5)
+    ref = lib.Planner(crane, scene, params)
+    side = torch.cuda.Stream()
+    g = lib.Planner(crane, scene, params, stream=side)
+    try:
+        def both(iters, a, b, sc=None):
+            out = []
+            for pl in (ref, g):
+                if sc is not None:
+                    lib.cp_set_scene(pl.handle, lib.HostScene.from_scene(sc))
+                lib.cp_set_endpoints(pl.handle, a, b)
+                out.append(lib.cp_plan(pl.handle, iters, K=8))
+            np.testing.assert_array_equal(out[0][0], out[1][0])
+            assert out[0][1]["J"] == out[1][1]["J"]
+        n0 = lib.cp_launch_count()
+        both(12, q0, qd)
+        both(12, q0, qd)             # replayed
+        assert lib.cp_launch_count() > n0
+        both(12, qd, q0)             # new end points
+        both(7, q0, qd)              # new count
+        sc2 = workloads.Scene(scene.cylinders[:10].copy(), scene.boxes)
+        both(7, q0, qd, sc=sc2)      # new scene
+    finally:
+        ref.close()
+        g.close()
