@@ -133,8 +133,12 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
             crane_fk_polar<NSPH>(m, q, X, Z, s1, c1);
             // broad phase of the chunk: the box of its spheres in the slew frame, dilated by
             // the softplus range m + cut beta beyond the obstacles' contact reach
-            const UnitFrame fr = unit_frame<NSPH>(s1, c1, X);
+            // spheres farther below or above every obstacle than the softplus range reaches
+            // (r_max + m + cut beta) add nothing: left out of the box and of the filter
             const float extra = a.margin + kSmoothCut * a.beta;
+            const float zreach = m.r_max + extra + kZGate;
+            const float zlo = sc.z_lo_all - zreach, zhi = sc.z_hi_all + zreach;
+            const UnitFrame fr = unit_frame_band<NSPH>(s1, c1, X, Z, zlo, zhi);
 #pragma unroll
             for (int s = 0; s < NSPH; ++s) {
                 const float h = X[s];
@@ -151,7 +155,8 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
             // and softplus code serves every sphere (unrolled it outgrows the instruction
             // cache) without per-thread local arrays.
 #pragma unroll
-            for (int s = 0; s < NSPH; ++s) T[s] = kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]);
+            for (int s = 0; s < NSPH; ++s)
+                T[s] = Z[s] > zlo && Z[s] < zhi ? kFilterMargin - fmaf(X[s], X[s], Y[s] * Y[s]) : -1e30f;
             float2 X2[NSPH / 2], Y2[NSPH / 2];
 #pragma unroll
             for (int p = 0; p < NSPH / 2; ++p) {
@@ -189,8 +194,9 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                         const float h = s_h[s * 32];
                         const float cx = __fmul_rn(c1, h), cy = __fmul_rn(s1, h);
                         const float cw = kFilterMargin - fmaf(cx, cx, cy * cy);
-                        if (fmaf(-2.f * cx, f.x, fmaf(-2.f * cy, f.y, f.z)) < cw) {
-                            const float cz = s_z[s * 32];
+                        const float cz = s_z[s * 32];
+                        if (fmaf(-2.f * cx, f.x, fmaf(-2.f * cy, f.y, f.z)) < cw && cz > e.y - zreach &&
+                            cz < e.z + zreach) {
                             const float sd = sdf_cylinder(cx, cy, cz, f.x, f.y, e) - m.sph[s].radius;
                             const float3 gr = GRAD ? sdf_cylinder_grad(cx, cy, cz, f.x, f.y, e)
                                                    : make_float3(0.f, 0.f, 0.f);
