@@ -11,6 +11,7 @@ written here with numpy, one function per step, in the paper's order and notatio
                      control points, Sec. 4.1) and initial covariance C
   factor             L with L L^T = sigma^2 C (numpy Cholesky), for step (1)
   sample             step (1): xi_i = mu + L z_i, z_i from Philox + Box-Muller
+  sample_elites      step (1) from the last update's elites, no factor (same distribution)
   evaluate           step (2): J(xi_i) through the C oracle
   rank               step (3): stable ascending sort of J (NaN sorts last)
   log_rank_weights   step (4): w_j = (ln(nu + 1/2) - ln j) / sum_k (ln(nu + 1/2) - ln k)
@@ -341,6 +342,23 @@ def sample(mu: np.ndarray, L: np.ndarray, seed: int, t: int, query: int, N: int,
     """Step (1): xi_i = mu + L z_i ~ N(mu, sigma^2 C), i = 0..N-1; returns [N][K][4]."""
     z = normals(seed, t, query, N, K)
     return (mu[None, :] + z @ L.T).reshape(N, K, 4)
+
+
+def sample_elites(mu: np.ndarray, elites: np.ndarray, w: np.ndarray, sigma: float, eps: float,
+                  seed: int, t: int, query: int, N: int, K: int):
+    """Step (1) drawn from the elites of the last update, with no factor. With
+    C = sum_j w_j (x_(j) - mu)(x_(j) - mu)^T + eps I (steps (5)-(6), mu the new mean),
+        xi_i = mu + sigma (sum_j sqrt(w_j) (x_(j) - mu) g_ij + sqrt(eps) g'_i)
+    is normal with mean mu and covariance sigma^2 C exactly. g_i are the first nu standard
+    normals of candidate i's Philox stream at iteration t (blocks of four as in `normals`),
+    g'_i the next D. Returns [N][K][4]."""
+    D = 4 * K
+    nu = len(w)
+    X = _c64(elites).reshape(nu, D)
+    z = normals(seed, t, query, N, (nu + D + 3) // 4)
+    Y = np.sqrt(_c64(w))[:, None] * (X - _c64(mu)[None, :])
+    xi = _c64(mu)[None, :] + sigma * (z[:, :nu] @ Y + math.sqrt(eps) * z[:, nu:nu + D])
+    return xi.reshape(N, K, 4)
 
 
 def rank(J: np.ndarray) -> np.ndarray:
