@@ -220,6 +220,18 @@ def flush_l2(buf):
     buf.add_(1.0)   # a write of a buffer larger than the 129 MB L2
 
 
+def resolve_sampler(args, wl):
+    """Step (1): the FP64 Cholesky factor, or the factor-free draw from the last update's
+    elites (the same distribution; paper rule only). "auto" takes the elites where their
+    N x nu x D FP32 product is cheaper than the FP64 moments and factor it replaces."""
+    if args.sampler != "auto":
+        return args.sampler
+    if args.update_rule != "paper":
+        return "factor"
+    N, D = wl.n_candidates, 4 * wl.n_waypoints
+    return "elites" if N * (N // 2) * D <= 2 ** 31 else "factor"
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -238,9 +250,11 @@ def run_ours(args):
     iters = args.iterations or wl.iterations
     crane = workloads.forestry_crane()
     scene = workloads.make_scene(wl)
+    sampler = resolve_sampler(args, wl)
     params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank,
                             grid_cell=wl.grid_cell, eval_exhaustive=int(args.exhaustive),
-                            update_rule=cp.CP_UPDATE_CMAES if args.update_rule == "cmaes" else cp.CP_UPDATE_PAPER)
+                            update_rule=cp.CP_UPDATE_CMAES if args.update_rule == "cmaes" else cp.CP_UPDATE_PAPER,
+                            sampler=cp.CP_SAMPLE_ELITES if sampler == "elites" else cp.CP_SAMPLE_FACTOR)
     planner = cp.Planner(crane, scene, params)
     h = planner.handle
     q0, qd, ok = select_endpoints_gpu(cp, planner, crane, wl.seed, rank)
@@ -339,7 +353,7 @@ def run_ours(args):
                                       scene.n_cyl, iters),
                        "step": "one plan", "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "flushed between steps (256 MB write)",
-                       "endpoints_ok": bool(ok), "update_rule": args.update_rule},
+                       "endpoints_ok": bool(ok), "update_rule": args.update_rule, "sampler": sampler},
             "ms_per_plan": ms,
             "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "ms_per_plan": ms_e2e,
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
@@ -867,6 +881,8 @@ def main():
     ap.add_argument("--iterations", type=int, default=0, help="override iterations per plan")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sampler", default="auto", choices=["auto", "factor", "elites"],
+                    help="step (1) from the Cholesky factor or from the last update's elites")
     ap.add_argument("--update-rule", default="paper", choices=["paper", "cmaes"],
                     help="steps (5)-(6) as Algorithm 1 prints them, or the CMA-ES update")
     ap.add_argument("--exhaustive", action="store_true",

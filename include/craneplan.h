@@ -140,10 +140,20 @@ typedef struct cp_params {
                                on: a cumulated step-size path adapts sigma, and C takes a
                                rank-one (evolution path) and a rank-mu (elites about the OLD
                                mean) update with the default learning rates; no eps. */
+    int32_t sampler;        /* step (1): CP_SAMPLE_FACTOR (0) draws xi = mu + L z with L the
+                               FP64 Cholesky factor of sigma^2 C; CP_SAMPLE_ELITES (1), with
+                               CP_UPDATE_PAPER only, draws the same N(mu, sigma^2 C) from the
+                               last update's elites without forming C or its factor:
+                               xi = mu + sigma (sum_j sqrt(w_j)(x_(j) - mu) g_j + sqrt(eps) g').
+                               The first sample after cp_set_endpoints or
+                               cp_set_distribution uses the factor. C and L are formed only
+                               when cp_get_distribution or cp_get_factor asks for them. */
 } cp_params;
 
 #define CP_UPDATE_PAPER 0
 #define CP_UPDATE_CMAES 1
+#define CP_SAMPLE_FACTOR 0
+#define CP_SAMPLE_ELITES 1
 
 /* Cost terms of the final mean path and the state of a finished plan. */
 typedef struct cp_plan_stats {

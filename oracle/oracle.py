@@ -480,23 +480,30 @@ class PlanResult:
 
 
 def plan(problem: Problem, sp: SearchParams, q0, qd, iterations: int,
-         callback=None, rule: str = "paper") -> PlanResult:
+         callback=None, rule: str = "paper", sampler: str = "factor") -> PlanResult:
     """Algorithm 1 for a fixed number of iterations, starting from init_distribution;
-    rule "cmaes" takes update_cmaes (sigma adapted) in place of steps (5)-(6)."""
+    rule "cmaes" takes update_cmaes (sigma adapted) in place of steps (5)-(6); sampler
+    "elites" (paper rule) draws every sample after the first with sample_elites."""
     q0, qd = _c64(q0), _c64(qd)
     m = problem.model_py
     mu, C = init_distribution(q0, qd, sp.K, m.q_min, m.q_max, sp.init_std_frac)
     st = cma_init(mu, C, sp.sigma)
     best, mean_J = [], []
+    last = None   # (mean, elites in rank order, weights) of the last paper-rule update
     for t in range(iterations):
-        L = factor(st.C if rule == "cmaes" else C, st.sigma if rule == "cmaes" else sp.sigma)
-        xi = sample(st.mu if rule == "cmaes" else mu, L, sp.seed, t, sp.query, sp.N, sp.K)
+        if sampler == "elites" and last is not None:
+            xi = sample_elites(last[0], last[1], last[2], sp.sigma, sp.eps, sp.seed, t, sp.query, sp.N, sp.K)
+        else:
+            L = factor(st.C if rule == "cmaes" else C, st.sigma if rule == "cmaes" else sp.sigma)
+            xi = sample(st.mu if rule == "cmaes" else mu, L, sp.seed, t, sp.query, sp.N, sp.K)
         J = evaluate(problem, xi, q0, qd).J
         if rule == "cmaes":
             st = update_cmaes(st, xi, J, sp.n_elites)
             mu, C = st.mu, st.C
         else:
             mu, C = update(xi, J, sp.n_elites, sp.eps)
+            X = _c64(xi).reshape(sp.N, -1)
+            last = (mu, X[rank(J)[:sp.n_elites]], log_rank_weights(sp.n_elites))
         best.append(float(np.nanmin(J)))
         if callback is not None:
             callback(t, mu, C, J)

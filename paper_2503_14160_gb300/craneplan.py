@@ -65,11 +65,13 @@ class cp_params(ctypes.Structure):
                 ("max_grid_items", ctypes.c_int64), ("smooth_margin", ctypes.c_double),
                 ("smooth_beta", ctypes.c_double), ("eval_ctas_per_sm", ctypes.c_int32),
                 ("debug_withhold_staging", ctypes.c_int32), ("eval_exhaustive", ctypes.c_int32),
-                ("update_rule", ctypes.c_int32)]
+                ("update_rule", ctypes.c_int32), ("sampler", ctypes.c_int32)]
 
 
 CP_UPDATE_PAPER = 0
 CP_UPDATE_CMAES = 1
+CP_SAMPLE_FACTOR = 0
+CP_SAMPLE_ELITES = 1
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -251,11 +253,12 @@ def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 grid_half_extent: float = 0.0, max_grid_items: int = 0,
                 smooth_margin: float = 0.05, smooth_beta: float = 0.01,
                 eval_ctas_per_sm: int = 0, debug_withhold_staging: int = 0,
-                eval_exhaustive: int = 0, update_rule: int = CP_UPDATE_PAPER) -> cp_params:
+                eval_exhaustive: int = 0, update_rule: int = CP_UPDATE_PAPER,
+                sampler: int = CP_SAMPLE_FACTOR) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
                      query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
                      max_grid_items, smooth_margin, smooth_beta, eval_ctas_per_sm,
-                     debug_withhold_staging, eval_exhaustive, update_rule)
+                     debug_withhold_staging, eval_exhaustive, update_rule, sampler)
 
 
 # --------------------------------------------------------------------------- entry points

@@ -155,6 +155,11 @@ struct cp_planner {
     double *cma = nullptr;      // CMA-ES rule: {sigma, sigma before the update, h_sigma, |p_sigma|}
     double *p_sigma = nullptr, *p_c = nullptr, *mu_prev = nullptr;
     CmaConsts cmak{};
+    // factor-free sampler: scaled elite deviations Y [nu][D], the mean in FP32, the slice
+    // partials [slices][N][D]; elites_ready when the last step was such an update
+    float *elite_Y = nullptr, *mu_f = nullptr, *sample_part = nullptr;
+    int elite_slices = 1;
+    bool elites_ready = false;
     float *smooth_part_g = nullptr;   // partial gradients when few candidates share the GPU
     double *smooth_part_J = nullptr;
     int smem_optin = 0;
@@ -175,6 +180,7 @@ struct cp_planner {
     float4 plan_q0{}, plan_qd{};
     SceneDev plan_sdev{};
     GridDev plan_gdev{};
+    bool plan_ready_before = false, plan_ready_after = false;
     int64_t plan_nodes = 0;   // kernels in the recorded graph
 };
 
@@ -300,6 +306,11 @@ int validate_params(const cp_params *p)
         return set_error("eval_exhaustive must be 0 or 1"), CP_ERR_ARG;
     if (p->update_rule != CP_UPDATE_PAPER && p->update_rule != CP_UPDATE_CMAES)
         return set_error("update_rule must be CP_UPDATE_PAPER or CP_UPDATE_CMAES"), CP_ERR_ARG;
+    if (p->sampler != CP_SAMPLE_FACTOR && p->sampler != CP_SAMPLE_ELITES)
+        return set_error("sampler must be CP_SAMPLE_FACTOR or CP_SAMPLE_ELITES"), CP_ERR_ARG;
+    if (p->sampler == CP_SAMPLE_ELITES && p->update_rule != CP_UPDATE_PAPER)
+        return set_error("CP_SAMPLE_ELITES draws the covariance of the paper's update; it needs CP_UPDATE_PAPER"),
+               CP_ERR_ARG;
     if (!(p->grid_cell >= 0.0) || !is_finite(p->grid_cell) || !(p->grid_half_extent >= 0.0) ||
         !is_finite(p->grid_half_extent) || p->max_grid_items < 0 || !(p->smooth_margin >= 0.0) ||
         !is_finite(p->smooth_margin) || !(p->smooth_beta >= 0.0) || !is_finite(p->smooth_beta))
@@ -441,8 +452,13 @@ int run_sample(cp_planner *p, int iter, float *d_xi)
 {
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
-    rc = launch_sample(p->mu, p->Lt, p->N, p->K, p->prm.seed, (uint32_t)iter, p->prm.query, d_xi,
-                       p->st);
+    if (p->elites_ready)
+        rc = launch_sample_elites(p->elite_Y, p->mu_f, p->N, p->K, p->nu, p->elite_slices, p->prm.sigma,
+                                  p->prm.eps, p->prm.seed, (uint32_t)iter, p->prm.query, p->sample_part, d_xi,
+                                  p->st);
+    else
+        rc = launch_sample(p->mu, p->Lt, p->N, p->K, p->prm.seed, (uint32_t)iter, p->prm.query, d_xi,
+                           p->st);
     if (rc != CP_OK) return rc;
     return p->timer.end(ST_SAMPLE, p->st);
 }
@@ -471,6 +487,15 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
                                     p->cov_part, p->mean_part, p->mu, p->C, p->p_sigma, p->p_c, p->cma,
                                     p->st)) != CP_OK)
             return rc;
+    } else if (p->prm.sampler == CP_SAMPLE_ELITES) {
+        // the next draw comes from these elites: the mean and the scaled deviations, no C
+        if ((rc = launch_elite_mean(p->elites, p->w, p->nu, p->D, p->prm.sigma, p->mu, p->mu_f, p->elite_Y,
+                                    p->st)) != CP_OK)
+            return rc;
+        if ((rc = p->timer.end(ST_UPDATE, p->st)) != CP_OK) return rc;
+        p->elites_ready = true;
+        p->iteration += 1;
+        return CP_OK;
     } else if ((rc = launch_moments(p->elites, p->w, p->nu, p->D, p->prm.eps, p->cov_part, p->mean_part,
                                     p->mu, p->C, p->st)) != CP_OK) {
         return rc;
@@ -479,6 +504,19 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
     if ((rc = run_factor(p)) != CP_OK) return rc;
     p->iteration += 1;
     return CP_OK;
+}
+
+// With the factor-free sampler after an update, C (and its factor) exist only on request:
+// the moments of the current elites, with the mean written to scratch so that the mean the
+// sampler uses keeps its bits.
+int materialise_distribution(const cp_planner *p)
+{
+    if (!p->elites_ready) return CP_OK;
+    cp_planner *q = const_cast<cp_planner *>(p);
+    int rc = launch_moments(q->elites, q->w, q->nu, q->D, q->prm.eps, q->cov_part, q->mean_part, q->mu_prev, q->C,
+                            q->st);
+    if (rc != CP_OK) return rc;
+    return launch_factor(q->C, q->prm.sigma * q->prm.sigma, nullptr, q->D, q->L, q->Lt, q->status, q->st);
 }
 
 int check_status(cp_planner *p)
@@ -634,6 +672,11 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_psig = L.take<double>(D);
     const size_t o_pc = L.take<double>(D);
     const size_t o_mu_prev = L.take<double>(D);
+    const bool elite_sampler = p->prm.sampler == CP_SAMPLE_ELITES;
+    p->elite_slices = elite_sampler ? elite_slices(p->N, p->D, p->nu, p->num_sms) : 1;
+    const size_t o_elite_Y = L.take<float>(elite_sampler ? nu * D : 1);
+    const size_t o_mu_f = L.take<float>(D);
+    const size_t o_sample_part = L.take<float>(elite_sampler ? (size_t)p->elite_slices * N * D : 1);
     const bool radix = p->N >= kRadixMinN;
     const size_t o_rka = L.take<unsigned long long>(radix ? N : 1);
     const size_t o_rkb = L.take<unsigned long long>(radix ? N : 1);
@@ -682,6 +725,9 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->p_sigma = (double *)(b + o_psig);
     p->p_c = (double *)(b + o_pc);
     p->mu_prev = (double *)(b + o_mu_prev);
+    p->elite_Y = (float *)(b + o_elite_Y);
+    p->mu_f = (float *)(b + o_mu_f);
+    p->sample_part = (float *)(b + o_sample_part);
     p->cmak = cma_consts(p->D, p->nu);
     p->rkey_a = (unsigned long long *)(b + o_rka);
     p->rkey_b = (unsigned long long *)(b + o_rkb);
@@ -758,6 +804,7 @@ int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4])
     if (rc != CP_OK) return rc;
     if ((rc = launch_cma_reset(p->prm.sigma, p->D, p->cma, p->p_sigma, p->p_c, p->st)) != CP_OK) return rc;
     p->iteration = 0;
+    p->elites_ready = false;
     p->have_endpoints = true;
     return run_factor(p);
 }
@@ -808,10 +855,12 @@ bool same_grid(const GridDev &a, const GridDev &b)
 int run_plan_graph(cp_planner *p, int iters)
 {
     const bool same = p->plan_exec && p->plan_start == p->iteration && p->plan_iters == iters &&
+                      p->plan_ready_before == p->elites_ready &&
                       same_scene(p->plan_sdev, p->sdev) && same_grid(p->plan_gdev, p->gdev) &&
                       memcmp(&p->plan_q0, &p->q0f, sizeof(float4)) == 0 &&
                       memcmp(&p->plan_qd, &p->qdf, sizeof(float4)) == 0;
     const int start = p->iteration;
+    const bool ready_before = p->elites_ready;
     if (!same) {
         if (p->plan_exec) {
             cudaGraphExecDestroy(p->plan_exec);
@@ -832,6 +881,9 @@ int run_plan_graph(cp_planner *p, int iters)
         cudaGraph_t graph = nullptr;
         const cudaError_t e_end = cudaStreamEndCapture(p->st, &graph);
         p->iteration = start;
+        p->plan_ready_before = ready_before;
+        p->plan_ready_after = p->elites_ready;
+        p->elites_ready = ready_before;
         p->plan_nodes = g_launches.load() - launches_before;   // recorded, not run
         g_launches.fetch_sub(p->plan_nodes);
         if (rc != CP_OK) {
@@ -855,6 +907,7 @@ int run_plan_graph(cp_planner *p, int iters)
     CP_CUDA(cudaGraphLaunch(p->plan_exec, p->st));
     g_launches.fetch_add(p->plan_nodes, std::memory_order_relaxed);
     p->iteration = start + iters;
+    p->elites_ready = p->plan_ready_after;
     return CP_OK;
 }
 
@@ -991,6 +1044,10 @@ int cp_ik(cp_planner *p, const float *d_targets, int32_t n, const cp_ik_params *
 int cp_get_distribution(const cp_planner *p, double *d_mu, double *d_C)
 {
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (d_C) {
+        const int rc = materialise_distribution(p);
+        if (rc != CP_OK) return rc;
+    }
     if (d_mu) CP_CUDA(cudaMemcpyAsync(d_mu, p->mu, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
     if (d_C)
         CP_CUDA(cudaMemcpyAsync(d_C, p->C, sizeof(double) * p->D * p->D, cudaMemcpyDeviceToDevice, p->st));
@@ -1005,12 +1062,15 @@ int cp_set_distribution(cp_planner *p, const double *d_mu, const double *d_C, in
     CP_CUDA(cudaMemcpyAsync(p->mu, d_mu, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
     CP_CUDA(cudaMemcpyAsync(p->C, d_C, sizeof(double) * p->D * p->D, cudaMemcpyDeviceToDevice, p->st));
     p->iteration = iter;
+    p->elites_ready = false;
     return run_factor(p);
 }
 
 int cp_get_factor(const cp_planner *p, double *d_L)
 {
     if (!p || !d_L) return set_error("NULL argument"), CP_ERR_ARG;
+    const int rc = materialise_distribution(p);
+    if (rc != CP_OK) return rc;
     CP_CUDA(cudaMemcpyAsync(d_L, p->L, sizeof(double) * p->D * p->D, cudaMemcpyDeviceToDevice, p->st));
     return CP_OK;
 }
@@ -1133,6 +1193,7 @@ int record_plan(cp_planner *p, int iters, const double *h_in, double *h_out, uin
         return rc;
     if ((rc = launch_cma_reset(p->prm.sigma, p->D, p->cma, p->p_sigma, p->p_c, p->st)) != CP_OK) return rc;
     p->iteration = 0;
+    p->elites_ready = false;
     if ((rc = run_factor(p)) != CP_OK) return rc;
     for (int t = 0; t < iters; ++t) {
         if ((rc = run_sample(p, t, p->xi)) != CP_OK) return rc;

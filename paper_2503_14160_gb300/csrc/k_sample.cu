@@ -9,18 +9,6 @@
 namespace cp {
 namespace {
 
-// Box-Muller on the top 24 bits of two words: u1 in (0, 1], u2 in [0, 1), both exact.
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
-{
-    const float u1 = (float)((a >> 8) + 1u) * 0x1p-24f;
-    const float u2 = (float)(b >> 8) * 0x1p-24f;
-    const float r = sqrtf(-2.f * logf(u1));
-    float s, c;
-    sincospif(2.f * u2, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
-}
-
 __global__ void k_philox(const uint4 *__restrict__ ctr, uint32_t k0, uint32_t k1, int64_t n,
                          uint4 *out)
 {

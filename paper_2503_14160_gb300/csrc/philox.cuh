@@ -1,5 +1,5 @@
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the counter-based generator of the
-// sampling step and of the IK starting points: ten rounds, each multiplying words 0 and 2
+// sampling step and of the IK starting points, and the Box-Muller transform of its words: ten rounds, each multiplying words 0 and 2
 // by the round constants, xor-ing the high halves with the other words and the round key,
 // the key bumped by the Weyl constants between rounds.
 #pragma once
@@ -22,6 +22,18 @@ static __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint
         k1 += kWeyl1;
     }
     return c;
+}
+
+// Box-Muller on the top 24 bits of two words: u1 in (0, 1], u2 in [0, 1), both exact.
+static __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    const float u1 = (float)((a >> 8) + 1u) * 0x1p-24f;
+    const float u2 = (float)(b >> 8) * 0x1p-24f;
+    const float r = sqrtf(-2.f * logf(u1));
+    float s, c;
+    sincospif(2.f * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
 }
 
 }  // namespace cp
