@@ -265,6 +265,28 @@ int cp_signed_distance(cp_planner *p, const float *d_q, int32_t n, float *d_d);
  * the planner's stream. Errors: CP_ERR_ARG (n < 0, NULL or misaligned d_q). */
 int cp_forward_kinematics(cp_planner *p, const float *d_q, int32_t n, float *d_centres, float *d_tip);
 
+/* Convex-hull collision checking of Sec. 3.1 (the crane's links as convex hulls against the
+ * obstacles by the separating axis theorem), batched. The paper's crane meshes are not
+ * available; synthetic hulls stand in: the boom, the jib and the telescope as oriented boxes
+ * along their axes (axes e, n, e x n with n the normal of the crane's vertical plane; half
+ * extents (length/2 + pad, w, h); the telescope spans max(q4, 0)), the grapple as an upright
+ * box of half width grapple_w and height grapple_len below the tip. Obstacles: the boxes, and
+ * each cylinder as the regular octagonal prism circumscribing it (side normals at multiples
+ * of 45 degrees). For each configuration d_pen receives the largest penetration depth over
+ * links and obstacles (the shortest translation that separates the pair; 0 when every pair
+ * is disjoint). FP32. Arguments: d_q float[n][4] (device, 16-byte aligned), hulls (host, or
+ * NULL for the defaults w = h = (0.2, 0.2, 0.15) m, pad 0.2 m, grapple 0.25 x 1.0 m), d_pen
+ * float[n] (device). Asynchronous on the planner's stream. Errors: CP_ERR_ARG. */
+typedef struct cp_hull_model {
+    double w[3];          /* half extents across the crane plane: boom, jib, telescope (m) */
+    double h[3];          /* half extents in the plane, across the link */
+    double pad;           /* added to each arm box's half length (m) */
+    double grapple_w;     /* half width of the grapple box (m) */
+    double grapple_len;   /* height of the grapple box below the tip (m) */
+} cp_hull_model;
+
+int cp_hull_penetration(cp_planner *p, const float *d_q, int32_t n, const cp_hull_model *hulls, float *d_pen);
+
 /* Collision-free inverse kinematics of Sec. 3.2 (Eq. IK opt), batched: for each target
  * pose (x, y, z, psi) the configuration q that minimises |r(q)|^2 with
  *   r[0..2] = p_g(q) - (x, y, z)      p_g = the grapple centre, grapple_len below the tip

@@ -100,6 +100,11 @@ class cp_timing(ctypes.Structure):
                 ("eval_pair_tests", ctypes.c_int64)]
 
 
+class cp_hull_model(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_double * 3), ("h", ctypes.c_double * 3), ("pad", ctypes.c_double),
+                ("grapple_w", ctypes.c_double), ("grapple_len", ctypes.c_double)]
+
+
 class cp_ik_params(ctypes.Structure):
     _fields_ = [("lambda_q", ctypes.c_double), ("lambda_c", ctypes.c_double),
                 ("grapple_len", ctypes.c_double), ("mu0", ctypes.c_double),
@@ -128,6 +133,7 @@ _SIGS = {
                                ctypes.POINTER(cp_plan_stats)]),
     "cp_signed_distance": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "cp_forward_kinematics": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
+    "cp_hull_penetration": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(cp_hull_model), _P]),
     "cp_ik": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(cp_ik_params), _P, _P, _P,
                              _P, _P]),
     "cp_get_distribution": (ctypes.c_int, [_P, _P, _P]),
@@ -328,6 +334,16 @@ def cp_signed_distance(p: int, q, n: int, d) -> None:
 
 def cp_forward_kinematics(p: int, q, n: int, centres=None, tip=None) -> None:
     _check(load().cp_forward_kinematics(p, _ptr(q), int(n), _ptr(centres), _ptr(tip)))
+
+
+def make_hull_model(w=(0.2, 0.2, 0.15), h=(0.2, 0.2, 0.15), pad: float = 0.2, grapple_w: float = 0.25,
+                    grapple_len: float = 1.0) -> cp_hull_model:
+    return cp_hull_model((ctypes.c_double * 3)(*w), (ctypes.c_double * 3)(*h), pad, grapple_w, grapple_len)
+
+
+def cp_hull_penetration(p: int, q, n: int, pen, hulls: Optional[cp_hull_model] = None) -> None:
+    _check(load().cp_hull_penetration(p, _ptr(q), int(n), ctypes.byref(hulls) if hulls is not None else None,
+                                      _ptr(pen)))
 
 
 def make_ik_params(lambda_q: float = 1.0, lambda_c: float = 1.0, grapple_len: float = 1.0,

@@ -1023,6 +1023,27 @@ int cp_forward_kinematics(cp_planner *p, const float *d_q, int32_t n, float *d_c
     return launch_forward_kinematics(p->mdev, d_q, n, d_centres, d_tip, p->st);
 }
 
+int cp_hull_penetration(cp_planner *p, const float *d_q, int32_t n, const cp_hull_model *hulls, float *d_pen)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (n < 0 || (n > 0 && (!d_q || !d_pen))) return set_error("invalid arguments"), CP_ERR_ARG;
+    if ((uintptr_t)d_q & 15u) return set_error("d_q must be 16-byte aligned"), CP_ERR_ARG;
+    const cp_hull_model def = {{0.2, 0.2, 0.15}, {0.2, 0.2, 0.15}, 0.2, 0.25, 1.0};
+    const cp_hull_model &h = hulls ? *hulls : def;
+    float w[3], hh[3];
+    for (int k = 0; k < 3; ++k) {
+        if (!(h.w[k] > 0.0) || !(h.h[k] > 0.0) || !is_finite(h.w[k]) || !is_finite(h.h[k]))
+            return set_error("hull half extents must be finite and > 0"), CP_ERR_ARG;
+        w[k] = (float)h.w[k];
+        hh[k] = (float)h.h[k];
+    }
+    if (!(h.pad >= 0.0) || !(h.grapple_w > 0.0) || !(h.grapple_len > 0.0) || !is_finite(h.pad) ||
+        !is_finite(h.grapple_w) || !is_finite(h.grapple_len))
+        return set_error("hull pad must be >= 0 and the grapple box > 0"), CP_ERR_ARG;
+    return launch_hull_penetration(p->mdev, p->sdev, d_q, n, w, hh, (float)h.pad, (float)h.grapple_w,
+                                   (float)h.grapple_len, d_pen, p->st);
+}
+
 int cp_ik(cp_planner *p, const float *d_targets, int32_t n, const cp_ik_params *ik,
           const float *d_q_init, float *d_q, float *d_f, int32_t *d_restart, float *d_r)
 {
