@@ -679,6 +679,120 @@ def run_ik(args):
     planner.close()
 
 
+HULL_CONFIGS = 1 << 20
+
+
+def hull_config(scene):
+    return {"workload": "hulls: %d configurations uniform in the joint limits against the single-large "
+                        "forest (%d trees as circumscribed octagonal prisms), 4 link boxes each"
+                        % (HULL_CONFIGS, scene.n_cyl),
+            "step": "one cp_hull_penetration launch over all configurations",
+            "l2": "flushed between steps (256 MB write)"}
+
+
+def hull_oracle_sample(crane, scene, q, seconds):
+    """The FP64 oracle's hull penetration on configurations in turn until `seconds` have
+    passed (numpy, one thread)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import hulls
+    import oracle
+    pb = oracle.Problem(crane, scene, oracle.CostParams(K=1, S=1))
+    done, t0 = 0, time.perf_counter()
+    while True:
+        hulls.penetration(pb, q[done % len(q)])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": "configurations/s", "cores": 1, "kind": "oracle", "seconds": el,
+            "sample": "%d FP64 hull checks (4 link boxes vs %d prisms, numpy over obstacles), one thread"
+                      % (done, scene.n_cyl)}
+
+
+def run_hulls(args):
+    """Convex-hull collision checking (Sec. 3.1): configurations checked per second."""
+    import torch
+    from paper_2503_14160_gb300 import build, craneplan as cp, workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    cp.load()
+    crane = workloads.forestry_crane()
+    scene = workloads.make_scene(workloads.WORKLOADS["single_large"])
+    planner = cp.Planner(crane, scene, cp.make_params(64, 2, 2))
+    h = planner.handle
+    n = HULL_CONFIGS
+    q_np = workloads.uniform_configurations(crane, workloads.rng(rank, workloads.STREAM_TEST, 9), n)
+    q = torch.from_numpy(q_np.astype(np.float32)).cuda()
+    pen = torch.zeros(n, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        cp.cp_hull_penetration(h, q, n, pen)
+    torch.cuda.synchronize()
+    times = []
+    l0 = cp.cp_launch_count()
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush_l2(flush)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cp.cp_hull_penetration(h, q, n, pen)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+    launches = cp.cp_launch_count() - l0
+    ms = float(np.mean(times))
+    colliding = float((pen > 0).float().mean().item())
+    host_q = q.cpu().pin_memory()
+    host_p = torch.empty_like(pen, device="cpu").pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.copy_(host_q, non_blocking=True)
+        cp.cp_hull_penetration(h, q, n, pen)
+        host_p.copy_(pen, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    line = {"metric": "convex-hull collision checks/sec (configurations, Sec. 3.1)",
+            "value": n / (ms / 1e3), "unit": "configurations/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded configurations in the crane-and-forest scene; paper meshes unavailable)",
+            "config": hull_config(scene), "colliding_fraction": colliding,
+            "e2e": {"value": n / (float(np.mean(e2e)) / 1e3), "unit": "configurations/s",
+                    "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": n * 4},
+            "gpu_launches": launches, "clocks": clocks.summary()}
+    if not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = hull_oracle_sample(crane, scene, q_np[:4096], args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    planner.close()
+
+
+def run_hulls_reference(args):
+    from paper_2503_14160_gb300 import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    crane = workloads.forestry_crane()
+    scene = workloads.make_scene(workloads.WORKLOADS["single_large"])
+    q = workloads.uniform_configurations(crane, workloads.rng(0, workloads.STREAM_TEST, 9), 4096)
+    per = [hull_oracle_sample(crane, scene, q, args.cpu_seconds / 4) for _ in range(args.warmup + args.steps)]
+    per = per[args.warmup:]
+    value = float(np.mean([r["value"] for r in per]))
+    line = {"metric": "convex-hull collision checks/sec (configurations, Sec. 3.1)", "value": value,
+            "unit": "configurations/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean([r["seconds"] for r in per])) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded configurations in the crane-and-forest scene; paper meshes unavailable)",
+            "impl": "reference", "config": hull_config(scene),
+            "cpu_baseline": {"value": value, "unit": "configurations/s", "cores": 1, "kind": "oracle",
+                             "sample": per[0]["sample"]},
+            "e2e": {"value": value, "unit": "configurations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_ik_reference(args):
     from paper_2503_14160_gb300 import workloads
     ws, rank, _ = dist_env()
@@ -890,10 +1004,14 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference" and args.workload == "ik":
         run_ik_reference(args)
+    elif args.impl == "reference" and args.workload == "hulls":
+        run_hulls_reference(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "ik":
         run_ik(args)
+    elif args.workload == "hulls":
+        run_hulls(args)
     elif args.workload == "differentiable":
         run_differentiable(args)
     elif args.workload == "batch":
