@@ -12,11 +12,13 @@
 // Every configuration's result is the largest depth over links and obstacles (0 when
 // collision-free).
 //
-// One thread per configuration. All threads scan the obstacles in the same order (the
-// loads are warp-wide broadcasts); an obstacle whose horizontal reach stays farther from
-// the crane's vertical plane than the widest hull is skipped, and so is a pair whose
-// bounding spheres (the link box's and the obstacle's) do not meet. A pair's axes are
-// tried with the cheap obstacle axes first and stop at the first separating one.
+// One thread per configuration scans the obstacles (all threads in the same order, so the
+// loads are warp-wide broadcasts); an obstacle whose horizontal reach stays farther from the
+// crane's vertical plane than the widest hull, or beyond the arm's extent along it, is
+// skipped. The pairs left go through a queue per warp and are worked 32 at a time, one per
+// lane; a pair whose bounding spheres (the link box's and the obstacle's) do not meet is
+// skipped, and a pair's axes are tried with the cheap obstacle axes first and stop at the
+// first separating one.
 #include <math_constants.h>
 
 #include "cp_internal.cuh"
@@ -139,21 +141,91 @@ struct HullArgs {
     float *pen;
 };
 
-__device__ __forceinline__ void make_box(Obb &b, float3 c, float3 e, float3 n, float hl, float w, float h)
+constexpr int kHullWarps = kHullThreads / 32;
+constexpr int kBoxFloats = 16;   // centre, three axes, half extents, bounding radius
+
+__device__ __forceinline__ void store_box(float *r, float3 c, float3 e, float3 n, float hl, float w, float h)
 {
-    b.c = c;
-    b.u[0] = e;
-    b.u[1] = n;
-    b.u[2] = cross3(e, n);
-    b.h[0] = hl;
-    b.h[1] = w;
-    b.h[2] = h;
-    b.rb = sqrtf(fmaf(hl, hl, fmaf(w, w, h * h)));
+    const float3 u2 = cross3(e, n);
+    const float v[kBoxFloats] = {c.x, c.y, c.z, e.x, e.y, e.z, n.x, n.y, n.z, u2.x, u2.y, u2.z, hl, w, h,
+                                 sqrtf(fmaf(hl, hl, fmaf(w, w, h * h)))};
+#pragma unroll
+    for (int k = 0; k < kBoxFloats; ++k) r[k] = v[k];
 }
 
+__device__ __forceinline__ Obb load_box(const float *r)
+{
+    Obb b;
+    b.c = make_float3(r[0], r[1], r[2]);
+    b.u[0] = make_float3(r[3], r[4], r[5]);
+    b.u[1] = make_float3(r[6], r[7], r[8]);
+    b.u[2] = make_float3(r[9], r[10], r[11]);
+    b.h[0] = r[12];
+    b.h[1] = r[13];
+    b.h[2] = r[14];
+    b.rb = r[15];
+    return b;
+}
+
+// Depth of the four link boxes of one configuration against obstacle `ob` (cylinders
+// first, then boxes), 0 when disjoint.
+__device__ __forceinline__ float pair_depth(const SceneDev &sc, const float *boxes, int ob)
+{
+    float pen = 0.f;
+    if (ob < sc.n_cyl) {
+        const float4 f = __ldg(sc.cyl_filt + ob), e = __ldg(sc.cyl_exact + ob);
+        const float rc = e.x / kOctCos, hz = 0.5f * (e.z - e.y);
+        const float3 pc = make_float3(f.x, f.y, 0.5f * (e.y + e.z));
+        const float rbo = sqrtf(fmaf(rc, rc, hz * hz));
+#pragma unroll 1
+        for (int l = 0; l < 4; ++l) {
+            const Obb b = load_box(boxes + l * kBoxFloats);
+            const float3 d = make_float3(pc.x - b.c.x, pc.y - b.c.y, pc.z - b.c.z);
+            const float rr = b.rb + rbo;
+            if (dot3(d, d) > rr * rr) continue;   // bounding spheres apart
+            pen = fmaxf(pen, sat_prism(b, pc, rc, hz));
+        }
+    } else {
+        const int bi = ob - sc.n_cyl;
+        const float4 c = __ldg(sc.box_c + bi), h = __ldg(sc.box_h + bi);
+        const float rbo = sqrtf(fmaf(h.x, h.x, fmaf(h.y, h.y, h.z * h.z)));
+#pragma unroll 1
+        for (int l = 0; l < 4; ++l) {
+            const Obb b = load_box(boxes + l * kBoxFloats);
+            const float3 d = make_float3(c.x - b.c.x, c.y - b.c.y, c.z - b.c.z);
+            const float rr = b.rb + rbo;
+            if (dot3(d, d) > rr * rr) continue;
+            pen = fmaxf(pen, sat_box(b, make_float3(c.x, c.y, c.z), make_float3(h.x, h.y, h.z)));
+        }
+    }
+    return pen;
+}
+
+// Entries 0..count-1 of the warp's queue, one per lane: (configuration lane, obstacle); the
+// depth goes to the owning lane's running maximum (non-negative floats order as their bits).
+__device__ __forceinline__ void run_queue(const SceneDev &sc, const float *s_boxes, const int *queue, int count,
+                                          int *s_pen, int lane)
+{
+    if (lane < count) {
+        const int e = queue[lane];
+        const int owner = e & 31, ob = e >> 5;
+        const float pen = pair_depth(sc, s_boxes + owner * 4 * kBoxFloats, ob);
+        if (pen > 0.f) atomicMax(s_pen + owner, __float_as_int(pen));
+    }
+    __syncwarp();
+}
+
+// One thread per configuration for the kinematics and the obstacle scan; the (configuration,
+// obstacle) pairs that pass the scan's plane and range tests join a queue per warp, and the
+// warp works through them 32 at a time, one pair per lane, so that the separating-axis work
+// runs on full warps whatever pairs each configuration has.
 __global__ void __launch_bounds__(kHullThreads)
 k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
 {
+    __shared__ float s_box[kHullWarps][32 * 4 * kBoxFloats];
+    __shared__ int s_pen[kHullWarps][32];
+    __shared__ int s_queue[kHullWarps][64];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < a.n;
     const float4 q = a.q[live ? i : 0];
@@ -163,57 +235,65 @@ k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
     sincosf(q.y + q.z, &s23, &c23);
     const float3 eb = make_float3(c2 * c1, c2 * s1, s2), ej = make_float3(c23 * c1, c23 * s1, s23);
     const float3 n = make_float3(-s1, c1, 0.f);
-    const float3 O = make_float3(0.f, 0.f, m.base_z);
-    const float3 J = make_float3(fmaf(m.boom_len, eb.x, O.x), fmaf(m.boom_len, eb.y, O.y), fmaf(m.boom_len, eb.z, O.z));
+    const float3 J = make_float3(m.boom_len * eb.x, m.boom_len * eb.y, fmaf(m.boom_len, eb.z, m.base_z));
     const float tl = m.jib_len + q.w;
     const float3 T = make_float3(fmaf(tl, ej.x, J.x), fmaf(tl, ej.y, J.y), fmaf(tl, ej.z, J.z));
     const float q4p = fmaxf(q.w, 0.f);
-    Obb box[4];
-    make_box(box[0], make_float3(fmaf(0.5f * m.boom_len, eb.x, O.x), fmaf(0.5f * m.boom_len, eb.y, O.y),
-                                 fmaf(0.5f * m.boom_len, eb.z, O.z)),
-             eb, n, 0.5f * m.boom_len + a.pad, a.w[0], a.hh[0]);
-    make_box(box[1], make_float3(fmaf(0.5f * m.jib_len, ej.x, J.x), fmaf(0.5f * m.jib_len, ej.y, J.y),
-                                 fmaf(0.5f * m.jib_len, ej.z, J.z)),
-             ej, n, 0.5f * m.jib_len + a.pad, a.w[1], a.hh[1]);
-    const float tc = fmaf(0.5f, q4p, m.jib_len);
-    make_box(box[2], make_float3(fmaf(tc, ej.x, J.x), fmaf(tc, ej.y, J.y), fmaf(tc, ej.z, J.z)), ej, n,
-             fmaf(0.5f, q4p, a.pad), a.w[2], a.hh[2]);
-    make_box(box[3], make_float3(T.x, T.y, T.z - 0.5f * a.glen), make_float3(c1, s1, 0.f), n, a.gw, a.gw,
-             0.5f * a.glen);
-    // every hull point lies within wmax of the crane's vertical plane
+    float *mine = s_box[wib] + lane * 4 * kBoxFloats;
+    const float hb = 0.5f * m.boom_len, hj = 0.5f * m.jib_len, tc = fmaf(0.5f, q4p, m.jib_len);
+    store_box(mine, make_float3(hb * eb.x, hb * eb.y, fmaf(hb, eb.z, m.base_z)), eb, n, hb + a.pad, a.w[0],
+              a.hh[0]);
+    store_box(mine + kBoxFloats, make_float3(fmaf(hj, ej.x, J.x), fmaf(hj, ej.y, J.y), fmaf(hj, ej.z, J.z)), ej, n,
+              hj + a.pad, a.w[1], a.hh[1]);
+    store_box(mine + 2 * kBoxFloats, make_float3(fmaf(tc, ej.x, J.x), fmaf(tc, ej.y, J.y), fmaf(tc, ej.z, J.z)), ej,
+              n, fmaf(0.5f, q4p, a.pad), a.w[2], a.hh[2]);
+    store_box(mine + 3 * kBoxFloats, make_float3(T.x, T.y, T.z - 0.5f * a.glen), make_float3(c1, s1, 0.f), n, a.gw,
+              a.gw, 0.5f * a.glen);
+    s_pen[wib][lane] = 0;
+    // every hull point lies within wmax of the crane's vertical plane, and its coordinate
+    // along the slew direction within [h_lo, h_hi]: the arm's joints O, J, the jib's end and
+    // T, widened by an arm box's end pad plus its in-plane half extent, or the grapple's
+    // half width
     const float wmax = fmaxf(fmaxf(a.w[0], a.w[1]), fmaxf(a.w[2], a.gw));
-    float pen = 0.f;
-    for (int o = 0; o < sc.n_cyl; ++o) {
-        const float4 f = __ldg(sc.cyl_filt + o), e = __ldg(sc.cyl_exact + o);
-        const float rc = e.x / kOctCos;
-        const float v = fmaf(-s1, f.x, c1 * f.y);
-        if (fabsf(v) > rc + wmax + 1e-3f) continue;
-        const float3 pc = make_float3(f.x, f.y, 0.5f * (e.y + e.z));
-        const float hz = 0.5f * (e.z - e.y);
-        const float rbo = sqrtf(fmaf(rc, rc, hz * hz));
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const float3 d = make_float3(pc.x - box[l].c.x, pc.y - box[l].c.y, pc.z - box[l].c.z);
-            const float rr = box[l].rb + rbo;
-            if (dot3(d, d) > rr * rr) continue;   // bounding spheres apart
-            pen = fmaxf(pen, sat_prism(box[l], pc, rc, hz));
+    const float ext = fmaxf(a.pad + fmaxf(fmaxf(a.hh[0], a.hh[1]), a.hh[2]), a.gw);
+    const float hJ = m.boom_len * c2, hT = fmaf(tl, c23, hJ), hE = fmaf(m.jib_len, c23, hJ);
+    const float h_lo = fminf(fminf(0.f, hJ), fminf(hT, hE)) - ext, h_hi = fmaxf(fmaxf(0.f, hJ), fmaxf(hT, hE)) + ext;
+    __syncwarp();
+    int *queue = s_queue[wib];
+    int count = 0;
+    const int n_obs = sc.n_cyl + sc.n_box;
+    for (int o = 0; o < n_obs; ++o) {
+        float cx, cy, reach;
+        if (o < sc.n_cyl) {
+            const float4 f = __ldg(sc.cyl_filt + o);
+            cx = f.x;
+            cy = f.y;
+            reach = __ldg(&sc.cyl_exact[o].x) / kOctCos;
+        } else {
+            const float4 c = __ldg(sc.box_c + o - sc.n_cyl), h = __ldg(sc.box_h + o - sc.n_cyl);
+            cx = c.x;
+            cy = c.y;
+            reach = sqrtf(fmaf(h.x, h.x, h.y * h.y));
+        }
+        const float v = fmaf(-s1, cx, c1 * cy), u = fmaf(c1, cx, s1 * cy);
+        const bool pass = live && fabsf(v) <= reach + wmax + 1e-3f && u >= h_lo - reach - 1e-3f &&
+                          u <= h_hi + reach + 1e-3f;
+        const uint32_t mask = __ballot_sync(0xffffffffu, pass);
+        if (pass) queue[count + __popc(mask & ((1u << lane) - 1u))] = lane | (o << 5);
+        count += __popc(mask);
+        __syncwarp();
+        if (count >= 32) {
+            run_queue(sc, s_box[wib], queue, 32, s_pen[wib], lane);
+            const int rest = count - 32;
+            const int moved = lane < rest ? queue[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) queue[lane] = moved;
+            count = rest;
+            __syncwarp();
         }
     }
-    for (int b = 0; b < sc.n_box; ++b) {
-        const float4 c = __ldg(sc.box_c + b), h = __ldg(sc.box_h + b);
-        const float reach = sqrtf(fmaf(h.x, h.x, h.y * h.y));
-        const float v = fmaf(-s1, c.x, c1 * c.y);
-        if (fabsf(v) > reach + wmax + 1e-3f) continue;
-        const float rbo = sqrtf(fmaf(h.x, h.x, fmaf(h.y, h.y, h.z * h.z)));
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const float3 d = make_float3(c.x - box[l].c.x, c.y - box[l].c.y, c.z - box[l].c.z);
-            const float rr = box[l].rb + rbo;
-            if (dot3(d, d) > rr * rr) continue;
-            pen = fmaxf(pen, sat_box(box[l], make_float3(c.x, c.y, c.z), make_float3(h.x, h.y, h.z)));
-        }
-    }
-    if (live) a.pen[i] = pen;
+    if (count > 0) run_queue(sc, s_box[wib], queue, count, s_pen[wib], lane);
+    if (live) a.pen[i] = __int_as_float(s_pen[wib][lane]);
 }
 
 }  // namespace
