@@ -140,6 +140,13 @@ typedef struct cp_params {
                                on: a cumulated step-size path adapts sigma, and C takes a
                                rank-one (evolution path) and a rank-mu (elites about the OLD
                                mean) update with the default learning rates; no eps. */
+    int32_t collision_model;/* d(q) of Sec. 3.1 in the path cost: CP_COLLISION_SPHERES (0), the
+                               link spheres of cp_model against the obstacles (the exact,
+                               exhaustive, broad-phase and grid forms), or CP_COLLISION_HULLS
+                               (1), the link boxes of cp_set_hull_model against boxes and
+                               octagonal prisms by separating axes (cp_hull_penetration's model;
+                               no grid: every obstacle is scanned per checkpoint). Only the
+                               penetration depth enters J_c and the flags. */
     int32_t sampler;        /* step (1): CP_SAMPLE_FACTOR (0) draws xi = mu + L z with L the
                                FP64 Cholesky factor of sigma^2 C; CP_SAMPLE_ELITES (1), with
                                CP_UPDATE_PAPER only, draws the same N(mu, sigma^2 C) from the
@@ -154,6 +161,8 @@ typedef struct cp_params {
 #define CP_UPDATE_CMAES 1
 #define CP_SAMPLE_FACTOR 0
 #define CP_SAMPLE_ELITES 1
+#define CP_COLLISION_SPHERES 0
+#define CP_COLLISION_HULLS 1
 
 /* Cost terms of the final mean path and the state of a finished plan. */
 typedef struct cp_plan_stats {
@@ -286,6 +295,10 @@ typedef struct cp_hull_model {
 } cp_hull_model;
 
 int cp_hull_penetration(cp_planner *p, const float *d_q, int32_t n, const cp_hull_model *hulls, float *d_pen);
+
+/* The hull model the planner's path cost uses under CP_COLLISION_HULLS (host struct, copied;
+ * NULL restores the defaults of cp_hull_penetration). Errors: CP_ERR_ARG. */
+int cp_set_hull_model(cp_planner *p, const cp_hull_model *hulls);
 
 /* Collision-free inverse kinematics of Sec. 3.2 (Eq. IK opt), batched: for each target
  * pose (x, y, z, psi) the configuration q that minimises |r(q)|^2 with

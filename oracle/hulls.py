@@ -159,6 +159,29 @@ def min_overlap_axis(centre, axes, half, verts_b, axes_b):
     return float(o[k]), axes_b[k] * (1.0 if d[k] >= 0.0 else -1.0)
 
 
+def checkpoint_configurations(problem, xi, q0, qd):
+    """q(s_k), k = 1..n_s, of one candidate xi[K][4] (the spline of the oracle's cost:
+    control points q0 x4, xi, qd x4, tau(s) = 4 + (K + 3) s, s_k = k / n_s)."""
+    K, S = problem.cost.K, problem.cost.S
+    n_s = (K + 3) * S
+    P = np.concatenate([np.tile(_o._c64(q0), (4, 1)), np.asarray(xi, dtype=np.float64).reshape(K, 4),
+                        np.tile(_o._c64(qd), (4, 1))])
+    return np.array([_o.bspline(P, 4.0 + (K + 3) * k / n_s) for k in range(1, n_s + 1)])
+
+
+def evaluate_hulls(problem, xi, q0, qd, hulls: Hulls = Hulls()):
+    """Eq. path opt with the hull model's collision term: (J, Jc, pen[n][n_s]) for candidates
+    xi[n][K][4]. J_p and J_l are the model-free terms of the oracle's cost;
+    J_c = lambda_c sum_k pen(q(s_k)) with pen the hull penetration."""
+    c = problem.cost
+    base = _o.evaluate(problem, xi, q0, qd)
+    xi = np.asarray(xi, dtype=np.float64).reshape(-1, c.K, 4)
+    pen = np.array([penetration_batch(problem, checkpoint_configurations(problem, x, q0, qd), hulls) for x in xi])
+    Jc = c.lambda_c * pen.sum(axis=1)
+    J = base.Jp + c.w_c * Jc + c.w_l * base.Jl
+    return J, Jc, pen
+
+
 # ---------------------------------------------------------------- geometry used by the pins
 
 def box_vertices(centre, axes, half):

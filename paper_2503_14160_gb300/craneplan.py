@@ -65,13 +65,16 @@ class cp_params(ctypes.Structure):
                 ("max_grid_items", ctypes.c_int64), ("smooth_margin", ctypes.c_double),
                 ("smooth_beta", ctypes.c_double), ("eval_ctas_per_sm", ctypes.c_int32),
                 ("debug_withhold_staging", ctypes.c_int32), ("eval_exhaustive", ctypes.c_int32),
-                ("update_rule", ctypes.c_int32), ("sampler", ctypes.c_int32)]
+                ("update_rule", ctypes.c_int32), ("collision_model", ctypes.c_int32),
+                ("sampler", ctypes.c_int32)]
 
 
 CP_UPDATE_PAPER = 0
 CP_UPDATE_CMAES = 1
 CP_SAMPLE_FACTOR = 0
 CP_SAMPLE_ELITES = 1
+CP_COLLISION_SPHERES = 0
+CP_COLLISION_HULLS = 1
 
 
 class cp_plan_stats(ctypes.Structure):
@@ -134,6 +137,7 @@ _SIGS = {
     "cp_signed_distance": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "cp_forward_kinematics": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
     "cp_hull_penetration": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(cp_hull_model), _P]),
+    "cp_set_hull_model": (ctypes.c_int, [_P, ctypes.POINTER(cp_hull_model)]),
     "cp_ik": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(cp_ik_params), _P, _P, _P,
                              _P, _P]),
     "cp_get_distribution": (ctypes.c_int, [_P, _P, _P]),
@@ -260,11 +264,11 @@ def make_params(N: int, K: int, S: int, n_elites: int = 0, w_c: float = 100.0,
                 smooth_margin: float = 0.05, smooth_beta: float = 0.01,
                 eval_ctas_per_sm: int = 0, debug_withhold_staging: int = 0,
                 eval_exhaustive: int = 0, update_rule: int = CP_UPDATE_PAPER,
-                sampler: int = CP_SAMPLE_FACTOR) -> cp_params:
+                sampler: int = CP_SAMPLE_FACTOR, collision_model: int = CP_COLLISION_SPHERES) -> cp_params:
     return cp_params(N, K, S, n_elites, w_c, w_l, lambda_c, sigma, eps, init_std_frac, seed,
                      query, max_cylinders, max_boxes, grid_cell, grid_half_extent,
                      max_grid_items, smooth_margin, smooth_beta, eval_ctas_per_sm,
-                     debug_withhold_staging, eval_exhaustive, update_rule, sampler)
+                     debug_withhold_staging, eval_exhaustive, update_rule, collision_model, sampler)
 
 
 # --------------------------------------------------------------------------- entry points
@@ -344,6 +348,10 @@ def make_hull_model(w=(0.2, 0.2, 0.15), h=(0.2, 0.2, 0.15), pad: float = 0.2, gr
 def cp_hull_penetration(p: int, q, n: int, pen, hulls: Optional[cp_hull_model] = None) -> None:
     _check(load().cp_hull_penetration(p, _ptr(q), int(n), ctypes.byref(hulls) if hulls is not None else None,
                                       _ptr(pen)))
+
+
+def cp_set_hull_model(p: int, hulls: Optional[cp_hull_model] = None) -> None:
+    _check(load().cp_set_hull_model(p, ctypes.byref(hulls) if hulls is not None else None))
 
 
 def make_ik_params(lambda_q: float = 1.0, lambda_c: float = 1.0, grapple_len: float = 1.0,

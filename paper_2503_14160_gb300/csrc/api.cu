@@ -160,6 +160,7 @@ struct cp_planner {
     float *elite_Y = nullptr, *mu_f = nullptr, *sample_part = nullptr;
     int elite_slices = 1;
     bool elites_ready = false;
+    HullDims hulls{{0.2f, 0.2f, 0.15f}, {0.2f, 0.2f, 0.15f}, 0.2f, 0.25f, 1.0f};   // CP_COLLISION_HULLS
     float *smooth_part_g = nullptr;   // partial gradients when few candidates share the GPU
     double *smooth_part_J = nullptr;
     int smem_optin = 0;
@@ -306,6 +307,8 @@ int validate_params(const cp_params *p)
         return set_error("eval_exhaustive must be 0 or 1"), CP_ERR_ARG;
     if (p->update_rule != CP_UPDATE_PAPER && p->update_rule != CP_UPDATE_CMAES)
         return set_error("update_rule must be CP_UPDATE_PAPER or CP_UPDATE_CMAES"), CP_ERR_ARG;
+    if (p->collision_model != CP_COLLISION_SPHERES && p->collision_model != CP_COLLISION_HULLS)
+        return set_error("collision_model must be CP_COLLISION_SPHERES or CP_COLLISION_HULLS"), CP_ERR_ARG;
     if (p->sampler != CP_SAMPLE_FACTOR && p->sampler != CP_SAMPLE_ELITES)
         return set_error("sampler must be CP_SAMPLE_FACTOR or CP_SAMPLE_ELITES"), CP_ERR_ARG;
     if (p->sampler == CP_SAMPLE_ELITES && p->update_rule != CP_UPDATE_PAPER)
@@ -429,8 +432,11 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.pen_out = d_pen;
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
-    rc = p->use_grid ? launch_eval_grid(p->mdev, p->sdev, p->gdev, a, p->num_sms, p->st)
-                     : launch_eval(p->mdev, p->sdev, a, p->num_sms, p->st);
+    if (p->prm.collision_model == CP_COLLISION_HULLS)
+        rc = launch_eval_hulls(p->mdev, p->sdev, p->hulls, a, p->num_sms, p->st);
+    else
+        rc = p->use_grid ? launch_eval_grid(p->mdev, p->sdev, p->gdev, a, p->num_sms, p->st)
+                         : launch_eval(p->mdev, p->sdev, a, p->num_sms, p->st);
     if (rc != CP_OK) return rc;
     rc = p->timer.end(ST_EVAL, p->st);
     if (rc != CP_OK) return rc;
@@ -1023,25 +1029,52 @@ int cp_forward_kinematics(cp_planner *p, const float *d_q, int32_t n, float *d_c
     return launch_forward_kinematics(p->mdev, d_q, n, d_centres, d_tip, p->st);
 }
 
+namespace {
+
+int hull_dims(const cp_hull_model *hulls, HullDims &d)
+{
+    const cp_hull_model def = {{0.2, 0.2, 0.15}, {0.2, 0.2, 0.15}, 0.2, 0.25, 1.0};
+    const cp_hull_model &h = hulls ? *hulls : def;
+    for (int k = 0; k < 3; ++k) {
+        if (!(h.w[k] > 0.0) || !(h.h[k] > 0.0) || !is_finite(h.w[k]) || !is_finite(h.h[k]))
+            return set_error("hull half extents must be finite and > 0"), CP_ERR_ARG;
+        d.w[k] = (float)h.w[k];
+        d.hh[k] = (float)h.h[k];
+    }
+    if (!(h.pad >= 0.0) || !(h.grapple_w > 0.0) || !(h.grapple_len > 0.0) || !is_finite(h.pad) ||
+        !is_finite(h.grapple_w) || !is_finite(h.grapple_len))
+        return set_error("hull pad must be >= 0 and the grapple box > 0"), CP_ERR_ARG;
+    d.pad = (float)h.pad;
+    d.gw = (float)h.grapple_w;
+    d.glen = (float)h.grapple_len;
+    return CP_OK;
+}
+
+}  // namespace
+
 int cp_hull_penetration(cp_planner *p, const float *d_q, int32_t n, const cp_hull_model *hulls, float *d_pen)
 {
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     if (n < 0 || (n > 0 && (!d_q || !d_pen))) return set_error("invalid arguments"), CP_ERR_ARG;
     if ((uintptr_t)d_q & 15u) return set_error("d_q must be 16-byte aligned"), CP_ERR_ARG;
-    const cp_hull_model def = {{0.2, 0.2, 0.15}, {0.2, 0.2, 0.15}, 0.2, 0.25, 1.0};
-    const cp_hull_model &h = hulls ? *hulls : def;
-    float w[3], hh[3];
-    for (int k = 0; k < 3; ++k) {
-        if (!(h.w[k] > 0.0) || !(h.h[k] > 0.0) || !is_finite(h.w[k]) || !is_finite(h.h[k]))
-            return set_error("hull half extents must be finite and > 0"), CP_ERR_ARG;
-        w[k] = (float)h.w[k];
-        hh[k] = (float)h.h[k];
+    HullDims d{};
+    const int rc = hull_dims(hulls, d);
+    if (rc != CP_OK) return rc;
+    return launch_hull_penetration(p->mdev, p->sdev, d, d_q, n, d_pen, p->st);
+}
+
+int cp_set_hull_model(cp_planner *p, const cp_hull_model *hulls)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    HullDims d{};
+    const int rc = hull_dims(hulls, d);
+    if (rc != CP_OK) return rc;
+    p->hulls = d;
+    if (p->plan_exec) {   // the recorded plan holds the old model as a kernel argument
+        cudaGraphExecDestroy(p->plan_exec);
+        p->plan_exec = nullptr;
     }
-    if (!(h.pad >= 0.0) || !(h.grapple_w > 0.0) || !(h.grapple_len > 0.0) || !is_finite(h.pad) ||
-        !is_finite(h.grapple_w) || !is_finite(h.grapple_len))
-        return set_error("hull pad must be >= 0 and the grapple box > 0"), CP_ERR_ARG;
-    return launch_hull_penetration(p->mdev, p->sdev, d_q, n, w, hh, (float)h.pad, (float)h.grapple_w,
-                                   (float)h.grapple_len, d_pen, p->st);
+    return CP_OK;
 }
 
 int cp_ik(cp_planner *p, const float *d_targets, int32_t n, const cp_ik_params *ik,

@@ -138,8 +138,15 @@ int launch_ik(const ModelDev &m, const SceneDev &sc, const float *targets, const
               cudaStream_t st);
 int launch_forward_kinematics(const ModelDev &m, const float *q, int n, float *centres, float *tip,
                               cudaStream_t st);
-int launch_hull_penetration(const ModelDev &m, const SceneDev &sc, const float *q, int n, const float w[3],
-                            const float hh[3], float pad, float gw, float glen, float *pen, cudaStream_t st);
+// Link boxes of the convex-hull collision model (half extents across the plane w and in it
+// hh for boom, jib, telescope; end pad; grapple half width and height).
+struct HullDims {
+    float w[3], hh[3], pad, gw, glen;
+};
+int launch_hull_penetration(const ModelDev &m, const SceneDev &sc, const HullDims &d, const float *q, int n, float *pen,
+                            cudaStream_t st);
+int launch_eval_hulls(const ModelDev &m, const SceneDev &sc, const HullDims &d, const EvalArgs &a, int num_sms,
+                      cudaStream_t st);
 size_t eval_smem_bytes(int n_cyl, int n_box, int S);
 int eval_configure(size_t smem_bytes);
 int eval_ensure_smem(size_t smem_bytes);

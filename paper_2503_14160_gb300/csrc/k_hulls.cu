@@ -19,9 +19,7 @@
 // lane; a pair whose bounding spheres (the link box's and the obstacle's) do not meet is
 // skipped, and a pair's axes are tried with the cheap obstacle axes first and stop at the
 // first separating one.
-#include <math_constants.h>
-
-#include "cp_internal.cuh"
+#include "eval_common.cuh"
 
 namespace cp {
 namespace {
@@ -137,7 +135,7 @@ __device__ __forceinline__ float sat_box(const Obb &a, float3 bc, float3 bh)
 struct HullArgs {
     const float4 *q;
     int n;
-    float w[3], hh[3], pad, gw, glen;
+    HullDims d;
     float *pen;
 };
 
@@ -215,20 +213,15 @@ __device__ __forceinline__ void run_queue(const SceneDev &sc, const float *s_box
     __syncwarp();
 }
 
-// One thread per configuration for the kinematics and the obstacle scan; the (configuration,
-// obstacle) pairs that pass the scan's plane and range tests join a queue per warp, and the
+// The hull penetration of configuration q on this lane, the warp working together: one
+// lane per configuration for the kinematics and the obstacle scan; the (configuration,
+// obstacle) pairs that pass the scan's plane and range tests join the warp's queue, and the
 // warp works through them 32 at a time, one pair per lane, so that the separating-axis work
-// runs on full warps whatever pairs each configuration has.
-__global__ void __launch_bounds__(kHullThreads)
-k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
+// runs on full warps whatever pairs each configuration has. s_box (32 x 4 boxes), s_pen (32)
+// and queue (64) are the warp's shared memory. Every lane of the warp must call it.
+__device__ __forceinline__ float hull_pen_warp(const ModelDev &m, const SceneDev &sc, const HullDims &hd, float4 q,
+                                               bool live, float *s_box, int *s_pen, int *queue, int lane)
 {
-    __shared__ float s_box[kHullWarps][32 * 4 * kBoxFloats];
-    __shared__ int s_pen[kHullWarps][32];
-    __shared__ int s_queue[kHullWarps][64];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < a.n;
-    const float4 q = a.q[live ? i : 0];
     float s1, c1, s2, c2, s23, c23;
     sincosf(q.x, &s1, &c1);
     sincosf(q.y, &s2, &c2);
@@ -239,27 +232,26 @@ k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
     const float tl = m.jib_len + q.w;
     const float3 T = make_float3(fmaf(tl, ej.x, J.x), fmaf(tl, ej.y, J.y), fmaf(tl, ej.z, J.z));
     const float q4p = fmaxf(q.w, 0.f);
-    float *mine = s_box[wib] + lane * 4 * kBoxFloats;
+    float *mine = s_box + lane * 4 * kBoxFloats;
     const float hb = 0.5f * m.boom_len, hj = 0.5f * m.jib_len, tc = fmaf(0.5f, q4p, m.jib_len);
-    store_box(mine, make_float3(hb * eb.x, hb * eb.y, fmaf(hb, eb.z, m.base_z)), eb, n, hb + a.pad, a.w[0],
-              a.hh[0]);
+    store_box(mine, make_float3(hb * eb.x, hb * eb.y, fmaf(hb, eb.z, m.base_z)), eb, n, hb + hd.pad, hd.w[0],
+              hd.hh[0]);
     store_box(mine + kBoxFloats, make_float3(fmaf(hj, ej.x, J.x), fmaf(hj, ej.y, J.y), fmaf(hj, ej.z, J.z)), ej, n,
-              hj + a.pad, a.w[1], a.hh[1]);
+              hj + hd.pad, hd.w[1], hd.hh[1]);
     store_box(mine + 2 * kBoxFloats, make_float3(fmaf(tc, ej.x, J.x), fmaf(tc, ej.y, J.y), fmaf(tc, ej.z, J.z)), ej,
-              n, fmaf(0.5f, q4p, a.pad), a.w[2], a.hh[2]);
-    store_box(mine + 3 * kBoxFloats, make_float3(T.x, T.y, T.z - 0.5f * a.glen), make_float3(c1, s1, 0.f), n, a.gw,
-              a.gw, 0.5f * a.glen);
-    s_pen[wib][lane] = 0;
+              n, fmaf(0.5f, q4p, hd.pad), hd.w[2], hd.hh[2]);
+    store_box(mine + 3 * kBoxFloats, make_float3(T.x, T.y, T.z - 0.5f * hd.glen), make_float3(c1, s1, 0.f), n,
+              hd.gw, hd.gw, 0.5f * hd.glen);
+    s_pen[lane] = 0;
     // every hull point lies within wmax of the crane's vertical plane, and its coordinate
     // along the slew direction within [h_lo, h_hi]: the arm's joints O, J, the jib's end and
     // T, widened by an arm box's end pad plus its in-plane half extent, or the grapple's
     // half width
-    const float wmax = fmaxf(fmaxf(a.w[0], a.w[1]), fmaxf(a.w[2], a.gw));
-    const float ext = fmaxf(a.pad + fmaxf(fmaxf(a.hh[0], a.hh[1]), a.hh[2]), a.gw);
+    const float wmax = fmaxf(fmaxf(hd.w[0], hd.w[1]), fmaxf(hd.w[2], hd.gw));
+    const float ext = fmaxf(hd.pad + fmaxf(fmaxf(hd.hh[0], hd.hh[1]), hd.hh[2]), hd.gw);
     const float hJ = m.boom_len * c2, hT = fmaf(tl, c23, hJ), hE = fmaf(m.jib_len, c23, hJ);
     const float h_lo = fminf(fminf(0.f, hJ), fminf(hT, hE)) - ext, h_hi = fmaxf(fmaxf(0.f, hJ), fmaxf(hT, hE)) + ext;
     __syncwarp();
-    int *queue = s_queue[wib];
     int count = 0;
     const int n_obs = sc.n_cyl + sc.n_box;
     for (int o = 0; o < n_obs; ++o) {
@@ -283,7 +275,7 @@ k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
         count += __popc(mask);
         __syncwarp();
         if (count >= 32) {
-            run_queue(sc, s_box[wib], queue, 32, s_pen[wib], lane);
+            run_queue(sc, s_box, queue, 32, s_pen, lane);
             const int rest = count - 32;
             const int moved = lane < rest ? queue[32 + lane] : 0;
             __syncwarp();
@@ -292,29 +284,77 @@ k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
             __syncwarp();
         }
     }
-    if (count > 0) run_queue(sc, s_box[wib], queue, count, s_pen[wib], lane);
-    if (live) a.pen[i] = __int_as_float(s_pen[wib][lane]);
+    if (count > 0) run_queue(sc, s_box, queue, count, s_pen, lane);
+    return __int_as_float(s_pen[lane]);
+}
+
+__global__ void __launch_bounds__(kHullThreads)
+k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
+{
+    __shared__ float s_box[kHullWarps][32 * 4 * kBoxFloats];
+    __shared__ int s_pen[kHullWarps][32];
+    __shared__ int s_queue[kHullWarps][64];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < a.n;
+    const float pen = hull_pen_warp(m, sc, a.d, a.q[live ? i : 0], live, s_box[wib], s_pen[wib], s_queue[wib], lane);
+    if (live) a.pen[i] = pen;
+}
+
+// The path evaluation with the hull model: a warp per (candidate, 32 checkpoints), the
+// checkpoint's configuration and costs as in the sphere forms, its collision term the hull
+// penetration (d = -depth where the hulls meet an obstacle, +inf elsewhere: only the
+// penetration enters J_c and the flags).
+__global__ void __launch_bounds__(kHullThreads)
+k_eval_hulls(const ModelDev m, const SceneDev sc, const HullDims hd, const EvalArgs a)
+{
+    extern __shared__ __align__(16) float4 s_basis[];
+    __shared__ float s_box[kHullWarps][32 * 4 * kBoxFloats];
+    __shared__ int s_pen[kHullWarps][32];
+    __shared__ int s_queue[kHullWarps][64];
+    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x) s_basis[i] = a.basis[i];
+    __syncthreads();
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int u = warp; u < a.n * a.chunks; u += n_warps) {
+        const int cand = u / a.chunks, chunk = u - cand * a.chunks;
+        const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
+        const float pen = hull_pen_warp(m, sc, hd, c.q, true, s_box[wib], s_pen[wib], s_queue[wib], lane);
+        __syncwarp();
+        unit_epilogue(a, c, pen > 0.f ? -pen : CUDART_INF_F, cand, chunk, lane);
+    }
 }
 
 }  // namespace
 
-int launch_hull_penetration(const ModelDev &m, const SceneDev &sc, const float *q, int n, const float w[3],
-                            const float hh[3], float pad, float gw, float glen, float *pen, cudaStream_t st)
+int launch_hull_penetration(const ModelDev &m, const SceneDev &sc, const HullDims &d, const float *q, int n, float *pen,
+                            cudaStream_t st)
 {
     if (n == 0) return CP_OK;
     HullArgs a{};
     a.q = (const float4 *)q;
     a.n = n;
-    for (int k = 0; k < 3; ++k) {
-        a.w[k] = w[k];
-        a.hh[k] = hh[k];
-    }
-    a.pad = pad;
-    a.gw = gw;
-    a.glen = glen;
+    a.d = d;
     a.pen = pen;
     k_hull_penetration<<<(n + kHullThreads - 1) / kHullThreads, kHullThreads, 0, st>>>(m, sc, a);
     CP_LAUNCHED("k_hull_penetration");
+    return CP_OK;
+}
+
+int launch_eval_hulls(const ModelDev &m, const SceneDev &sc, const HullDims &d, const EvalArgs &a, int num_sms,
+                      cudaStream_t st)
+{
+    const size_t smem = sizeof(float4) * 2 * (size_t)a.S;
+    CP_CUDA(cudaFuncSetAttribute(k_eval_hulls, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_hulls, kHullThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const long long units = (long long)a.n * a.chunks;
+    long long blocks = (units + kHullWarps - 1) / kHullWarps;
+    if (blocks > (long long)num_sms * per_sm) blocks = (long long)num_sms * per_sm;
+    k_eval_hulls<<<(unsigned)blocks, kHullThreads, smem, st>>>(m, sc, d, a);
+    CP_LAUNCHED("k_eval_hulls");
     return CP_OK;
 }
 

@@ -128,3 +128,20 @@ def test_prism_contains_its_cylinder(hl):
         assert not separated(p[None, :] + 1e-12, vb)
         # and on the prism's faces at most at the apothem
         assert np.max(np.abs((p[:2] - cyl[:2]) @ hl.OCT_DIRS[:, :2].T)) <= cyl[2] + 1e-12
+
+
+def test_checkpoint_configurations_are_the_costs(hl, oracle, crane):
+    """The checkpoints of the hull-form cost are those of the oracle's path cost: the sphere
+    model's penetration summed over them is the oracle's J_c."""
+    from paper_2503_14160_gb300 import workloads
+    scene = workloads.make_scene(workloads.WORKLOADS["single_small"])
+    pb = oracle.Problem(crane, scene, oracle.CostParams(K=3, S=5))
+    q0, qd = np.array([0.3, 0.2, -1.0, 0.4]), np.array([-2.0, 0.9, -0.6, 1.8])
+    xi = workloads.random_candidates(q0, qd, 3, 6, seed=2)
+    base = oracle.evaluate(pb, xi, q0, qd)
+    for i in range(6):
+        qs = hl.checkpoint_configurations(pb, xi[i], q0, qd)
+        assert len(qs) == (3 + 3) * 5
+        np.testing.assert_allclose(qs[-1], qd, atol=1e-12)
+        pen = np.maximum(0.0, -oracle.signed_distance(pb, qs))
+        assert pb.cost.lambda_c * pen.sum() == pytest.approx(base.Jc[i], rel=1e-12, abs=1e-12)
