@@ -254,7 +254,8 @@ def run_ours(args):
     params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank,
                             grid_cell=wl.grid_cell, eval_exhaustive=int(args.exhaustive),
                             update_rule=cp.CP_UPDATE_CMAES if args.update_rule == "cmaes" else cp.CP_UPDATE_PAPER,
-                            sampler=cp.CP_SAMPLE_ELITES if sampler == "elites" else cp.CP_SAMPLE_FACTOR)
+                            sampler=cp.CP_SAMPLE_ELITES if sampler == "elites" else cp.CP_SAMPLE_FACTOR,
+                            collision_model=cp.CP_COLLISION_HULLS if args.collision == "hulls" else cp.CP_COLLISION_SPHERES)
     planner = cp.Planner(crane, scene, params)
     h = planner.handle
     q0, qd, ok = select_endpoints_gpu(cp, planner, crane, wl.seed, rank)
@@ -327,15 +328,22 @@ def run_ours(args):
     roofline_exhaustive = None
     peaks_fp64 = None
     form = "grid" if wl.grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
-    roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
-                             candidates, form, clk.get("sm_mhz"))
-    if roofline is not None:
+    if args.collision == "hulls":
+        # the hull form's work per checkpoint depends on the pairs its scan keeps; its line
+        # reports the launch time only
+        roofline = {"bound": "alu", "kernel": "k_eval_hulls", "achieved": None, "peak": None, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None,
+                    "eval_ms_per_launch": timing["eval_ms"] / max(timing["eval_launches"], 1)}
+    else:
+        roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
+                                 candidates, form, clk.get("sm_mhz"))
+    if roofline is not None and roofline.get("achieved") is not None:
         roofline["traffic"] = traffic_per_launch() if form == "broad" else None
         peaks = cp.cp_alu_peaks()
         peaks_fp64 = peaks["fp64_tflops"]
         roofline["measured_fma_peaks"] = peaks
         roofline["frac_of_measured_fp32"] = roofline["achieved"] / peaks["fp32_tflops"]
-    if wl.grid_cell <= 0:
+    if wl.grid_cell <= 0 and args.collision == "spheres":
         if not args.exhaustive:
             roofline_exhaustive = exhaustive_roofline(cp, crane, scene, wl, q0, qd,
                                                       clk.get("sm_mhz"))
@@ -353,15 +361,16 @@ def run_ours(args):
                                       scene.n_cyl, iters),
                        "step": "one plan", "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "flushed between steps (256 MB write)",
-                       "endpoints_ok": bool(ok), "update_rule": args.update_rule, "sampler": sampler},
+                       "endpoints_ok": bool(ok), "update_rule": args.update_rule, "sampler": sampler,
+                       "collision_model": args.collision},
             "ms_per_plan": ms,
             "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "ms_per_plan": ms_e2e,
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
             "gpu_launches": launches,
             "roofline": roofline,
             "roofline_exhaustive": roofline_exhaustive,
-            "eval_kernel": {"name": {"broad": "k_eval_broad", "exhaustive": "k_eval",
-                                     "grid": "k_eval_grid"}[form],
+            "eval_kernel": {"name": "k_eval_hulls" if args.collision == "hulls" else
+                            {"broad": "k_eval_broad", "exhaustive": "k_eval", "grid": "k_eval_grid"}[form],
                             "ms_per_launch": eval_ms, "launches": timing["eval_launches"]},
             "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
                                   for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},
@@ -995,6 +1004,8 @@ def main():
     ap.add_argument("--iterations", type=int, default=0, help="override iterations per plan")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--collision", default="spheres", choices=["spheres", "hulls"],
+                    help="d(q) from link spheres, or from link boxes by separating axes")
     ap.add_argument("--sampler", default="auto", choices=["auto", "factor", "elites"],
                     help="step (1) from the Cholesky factor or from the last update's elites")
     ap.add_argument("--update-rule", default="paper", choices=["paper", "cmaes"],

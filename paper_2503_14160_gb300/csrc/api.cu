@@ -160,7 +160,8 @@ struct cp_planner {
     float *elite_Y = nullptr, *mu_f = nullptr, *sample_part = nullptr;
     int elite_slices = 1;
     bool elites_ready = false;
-    HullDims hulls{{0.2f, 0.2f, 0.15f}, {0.2f, 0.2f, 0.15f}, 0.2f, 0.25f, 1.0f};   // CP_COLLISION_HULLS
+    HullDims hulls{{0.2f, 0.2f, 0.15f}, {0.2f, 0.2f, 0.15f}, 0.2f, 0.25f, 1.0f, 0.f};   // CP_COLLISION_HULLS
+    float hull_reach_extra = 0.f;   // per scene: prism reach beyond the records' sphere reach
     float *smooth_part_g = nullptr;   // partial gradients when few candidates share the GPU
     double *smooth_part_J = nullptr;
     int smem_optin = 0;
@@ -391,6 +392,11 @@ int stage_scene(cp_planner *p, const cp_scene *sc)
     }
     p->sdev.z_lo_all = (float)zlo;
     p->sdev.z_hi_all = (float)zhi;
+    // the octagonal prism of a cylinder reaches R / cos(pi/8); the records' reach is at least
+    // R + r_max, so the hull form dilates the broad phase by the difference where positive
+    double rmax_cyl = 0.0;
+    for (int i = 0; i < sc->n_cyl; ++i) rmax_cyl = std::max(rmax_cyl, sc->cyl[i].radius);
+    p->hull_reach_extra = (float)(std::max(0.0, rmax_cyl / std::cos(M_PI / 8.0) - rmax_cyl - (double)p->mdev.r_max) + 1e-3);
     if (p->use_grid) {
         const int64_t need = grid_items_bound(sc, p->mdev.r_max, p->prm.grid_cell);
         if (need > p->grid_cap)
@@ -432,8 +438,11 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.pen_out = d_pen;
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
-    if (p->prm.collision_model == CP_COLLISION_HULLS)
-        rc = launch_eval_hulls(p->mdev, p->sdev, p->hulls, a, p->num_sms, p->st);
+    if (p->prm.collision_model == CP_COLLISION_HULLS) {
+        HullDims d = p->hulls;
+        d.reach_extra = p->hull_reach_extra;
+        rc = launch_eval_hulls(p->mdev, p->sdev, d, a, p->num_sms, p->st);
+    }
     else
         rc = p->use_grid ? launch_eval_grid(p->mdev, p->sdev, p->gdev, a, p->num_sms, p->st)
                          : launch_eval(p->mdev, p->sdev, a, p->num_sms, p->st);

@@ -142,6 +142,8 @@ int launch_forward_kinematics(const ModelDev &m, const float *q, int n, float *c
 // hh for boom, jib, telescope; end pad; grapple half width and height).
 struct HullDims {
     float w[3], hh[3], pad, gw, glen;
+    float reach_extra;   // how far an obstacle's octagonal prism can reach beyond the
+                         // sphere forms' record reach (set per scene by the planner)
 };
 int launch_hull_penetration(const ModelDev &m, const SceneDev &sc, const HullDims &d, const float *q, int n, float *pen,
                             cudaStream_t st);

@@ -218,7 +218,13 @@ __device__ __forceinline__ void run_queue(const SceneDev &sc, const float *s_box
 // obstacle) pairs that pass the scan's plane and range tests join the warp's queue, and the
 // warp works through them 32 at a time, one pair per lane, so that the separating-axis work
 // runs on full warps whatever pairs each configuration has. s_box (32 x 4 boxes), s_pen (32)
-// and queue (64) are the warp's shared memory. Every lane of the warp must call it.
+// and queue (64) are the warp's shared memory. Every lane of the warp must call it. With
+// BROAD (the lanes' configurations are neighbours on a path), the obstacles first go
+// through the broad phase of the sphere forms: the box, in the slew frame of lane 16, that
+// holds every lane's arm extent [h_lo, h_hi] on its plane, against the Morton-ordered groups
+// of eight cylinders and then their members, dilated by the hulls' half width and by how
+// far a prism reaches beyond the records' sphere reach.
+template <bool BROAD>
 __device__ __forceinline__ float hull_pen_warp(const ModelDev &m, const SceneDev &sc, const HullDims &hd, float4 q,
                                                bool live, float *s_box, int *s_pen, int *queue, int lane)
 {
@@ -253,8 +259,9 @@ __device__ __forceinline__ float hull_pen_warp(const ModelDev &m, const SceneDev
     const float h_lo = fminf(fminf(0.f, hJ), fminf(hT, hE)) - ext, h_hi = fmaxf(fmaxf(0.f, hJ), fmaxf(hT, hE)) + ext;
     __syncwarp();
     int count = 0;
-    const int n_obs = sc.n_cyl + sc.n_box;
-    for (int o = 0; o < n_obs; ++o) {
+    // one obstacle for every lane: its plane and range test, the queue, and a full round of
+    // pairs whenever 32 are waiting (warp-uniform)
+    auto scan_one = [&](int o) {
         float cx, cy, reach;
         if (o < sc.n_cyl) {
             const float4 f = __ldg(sc.cyl_filt + o);
@@ -283,6 +290,36 @@ __device__ __forceinline__ float hull_pen_warp(const ModelDev &m, const SceneDev
             count = rest;
             __syncwarp();
         }
+    };
+    if (BROAD) {
+        const float hbnd[2] = {h_lo, h_hi};
+        const UnitFrame fr = unit_frame<2>(s1, c1, hbnd);
+        const float extra = wmax + hd.reach_extra + 1e-3f;
+        const int n_grp = n_groups(sc.n_cyl);
+        for (int gbase = 0; gbase < n_grp; gbase += 32) {
+            uint32_t gmask = __ballot_sync(0xffffffffu, gbase + lane < n_grp &&
+                                                            unit_near(fr, __ldg(sc.cyl_group + gbase + lane), extra));
+            while (gmask) {
+                // lane l takes member l % 8 of the (l / 8)-th remaining group
+                uint32_t g = gmask;
+                const int slot = lane >> 3;
+                g = slot >= 1 ? g & (g - 1) : g;
+                g = slot >= 2 ? g & (g - 1) : g;
+                g = slot >= 3 ? g & (g - 1) : g;
+                const int o = g ? (gbase + __ffs(g) - 1) * kGroup + (lane & (kGroup - 1)) : sc.n_cyl;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) gmask &= gmask - 1;
+                uint32_t mmask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, __ldg(sc.cyl_filt + o), extra));
+                while (mmask) {
+                    const int ob = __shfl_sync(0xffffffffu, o, __ffs(mmask) - 1);
+                    mmask &= mmask - 1;
+                    scan_one(ob);
+                }
+            }
+        }
+        for (int b = 0; b < sc.n_box; ++b) scan_one(sc.n_cyl + b);
+    } else {
+        for (int o = 0; o < sc.n_cyl + sc.n_box; ++o) scan_one(o);
     }
     if (count > 0) run_queue(sc, s_box, queue, count, s_pen, lane);
     return __int_as_float(s_pen[lane]);
@@ -297,7 +334,8 @@ k_hull_penetration(const ModelDev m, const SceneDev sc, const HullArgs a)
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < a.n;
-    const float pen = hull_pen_warp(m, sc, a.d, a.q[live ? i : 0], live, s_box[wib], s_pen[wib], s_queue[wib], lane);
+    const float pen =
+        hull_pen_warp<false>(m, sc, a.d, a.q[live ? i : 0], live, s_box[wib], s_pen[wib], s_queue[wib], lane);
     if (live) a.pen[i] = pen;
 }
 
@@ -320,7 +358,7 @@ k_eval_hulls(const ModelDev m, const SceneDev sc, const HullDims hd, const EvalA
     for (int u = warp; u < a.n * a.chunks; u += n_warps) {
         const int cand = u / a.chunks, chunk = u - cand * a.chunks;
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
-        const float pen = hull_pen_warp(m, sc, hd, c.q, true, s_box[wib], s_pen[wib], s_queue[wib], lane);
+        const float pen = hull_pen_warp<true>(m, sc, hd, c.q, true, s_box[wib], s_pen[wib], s_queue[wib], lane);
         __syncwarp();
         unit_epilogue(a, c, pen > 0.f ? -pen : CUDART_INF_F, cand, chunk, lane);
     }
