@@ -22,7 +22,7 @@ constexpr int kEvalThreads = 256;
 #endif
 constexpr int kEvalMinBlocks = CP_EVAL_MIN_BLOCKS;
 #ifndef CP_EVAL_BROAD_MIN_BLOCKS
-#define CP_EVAL_BROAD_MIN_BLOCKS 4   // broad-phase form: at most 64 registers
+#define CP_EVAL_BROAD_MIN_BLOCKS 3   // broad-phase form: at most 80 registers
 #endif
 constexpr int kEvalBroadMinBlocks = CP_EVAL_BROAD_MIN_BLOCKS;
 constexpr int kObstaclesPerBranch = 2;   // obstacles tested between two branches
