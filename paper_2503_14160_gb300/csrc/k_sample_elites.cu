@@ -10,7 +10,7 @@
 //   k_sample_elites  partial products over a slice of the elites: a CTA takes 64 candidates
 //                    x 64 coordinates, stages 32 elites of Y and the matching 32 x 64
 //                    normals (Philox blocks generated in place) in shared memory, each
-//                    thread accumulating 4 x 4 outputs
+//                    thread accumulating 8 x 4 outputs
 //   k_sample_reduce  xi = mu + sum of the slices (fixed order) + sigma sqrt(eps) g'
 // Normals: candidate i at iteration t has the stream of Philox blocks (b, i, t, query), four
 // standard normals per block (Box-Muller on words 0-1 and 2-3); g_ij is normal j, g'_id
@@ -24,7 +24,7 @@ namespace {
 constexpr int kTileC = 64;     // candidates per CTA tile
 constexpr int kTileD = 64;     // coordinates per CTA tile
 constexpr int kChunkE = 32;    // elites per staged chunk
-constexpr int kSEThreads = 256;
+constexpr int kSEThreads = 128;   // 8 candidates x 4 coordinates a thread
 
 // Normal number j of candidate i (a block of four per Philox call).
 __device__ __forceinline__ float normal_at(uint32_t i, uint32_t j, uint32_t iter, uint32_t query, uint32_t k0,
@@ -85,8 +85,8 @@ k_sample_elites(const float *__restrict__ Y, int N, int D, int nu, int per_slice
     __shared__ __align__(16) float s_y[kChunkE][kTileD];   // Y chunk [elite][coordinate]
     const int c0 = blockIdx.x * kTileC, d0 = blockIdx.y * kTileD, slice = blockIdx.z;
     const int j_begin = slice * per_slice, j_end = min(nu, j_begin + per_slice);
-    const int tid = threadIdx.x, tc = tid & 15, td = tid >> 4;   // 4 candidates x 4 coordinates
-    float acc[4][4] = {};
+    const int tid = threadIdx.x, tc = tid & 7, td = tid >> 3;   // 8 candidates x 4 coordinates
+    float acc[8][4] = {};
     for (int j0 = j_begin; j0 < j_end; j0 += kChunkE) {
         __syncthreads();
         // normals: 64 candidates x 8 Philox blocks of 4
@@ -113,19 +113,20 @@ k_sample_elites(const float *__restrict__ Y, int N, int D, int nu, int per_slice
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < kChunkE; ++k) {
-            const float4 g = *reinterpret_cast<const float4 *>(&s_g[k][4 * tc]);
+            const float4 g0 = *reinterpret_cast<const float4 *>(&s_g[k][8 * tc]);
+            const float4 g1 = *reinterpret_cast<const float4 *>(&s_g[k][8 * tc + 4]);
             const float4 y = *reinterpret_cast<const float4 *>(&s_y[k][4 * td]);
-            const float gv[4] = {g.x, g.y, g.z, g.w}, yv[4] = {y.x, y.y, y.z, y.w};
+            const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w}, yv[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 8; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(gv[a], yv[b], acc[a][b]);
         }
     }
     float *out = P + (size_t)slice * N * D;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = c0 + 4 * tc + a;
+    for (int a = 0; a < 8; ++a) {
+        const int i = c0 + 8 * tc + a;
         if (i >= N) continue;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -151,12 +152,13 @@ __global__ void k_sample_reduce(const float *__restrict__ P, int slices, const f
 
 }  // namespace
 
-// Slices of the elites for N candidates and D coordinates: about six CTAs per SM, so that
-// the last wave is a small part of the launch (at most 32 slices, at least one chunk each).
+// Slices of the elites for N candidates and D coordinates: about twelve CTAs per SM, so
+// that the last wave is a small part of the launch (at most 32 slices, at least one chunk
+// each).
 int elite_slices(int N, int D, int nu, int num_sms)
 {
     const int tiles = ((N + kTileC - 1) / kTileC) * ((D + kTileD - 1) / kTileD);
-    int s = (6 * num_sms + tiles - 1) / tiles;
+    int s = (12 * num_sms + tiles - 1) / tiles;
     const int max_s = (nu + kChunkE - 1) / kChunkE;
     if (s > max_s) s = max_s;
     if (s > 32) s = 32;
