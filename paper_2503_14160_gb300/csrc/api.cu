@@ -158,6 +158,7 @@ struct cp_planner {
     // factor-free sampler: scaled elite deviations Y [nu][D], the mean in FP32, the slice
     // partials [slices][N][D]; elites_ready when the last step was such an update
     float *elite_Y = nullptr, *mu_f = nullptr, *sample_part = nullptr;
+    double *elite_sw = nullptr;   // sigma sqrt(w_j)
     int elite_slices = 1;
     bool elites_ready = false;
     HullDims hulls{{0.2f, 0.2f, 0.15f}, {0.2f, 0.2f, 0.15f}, 0.2f, 0.25f, 1.0f, 0.f};   // CP_COLLISION_HULLS
@@ -504,7 +505,7 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
             return rc;
     } else if (p->prm.sampler == CP_SAMPLE_ELITES) {
         // the next draw comes from these elites: the mean and the scaled deviations, no C
-        if ((rc = launch_elite_mean(p->elites, p->w, p->nu, p->D, p->prm.sigma, p->mu, p->mu_f, p->elite_Y,
+        if ((rc = launch_elite_mean(p->elites, p->w, p->elite_sw, p->nu, p->D, p->mu, p->mu_f, p->elite_Y,
                                     p->st)) != CP_OK)
             return rc;
         if ((rc = p->timer.end(ST_UPDATE, p->st)) != CP_OK) return rc;
@@ -691,6 +692,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->elite_slices = elite_sampler ? elite_slices(p->N, p->D, p->nu, p->num_sms) : 1;
     const size_t o_elite_Y = L.take<float>(elite_sampler ? nu * D : 1);
     const size_t o_mu_f = L.take<float>(D);
+    const size_t o_elite_sw = L.take<double>(elite_sampler ? nu : 1);
     const size_t o_sample_part = L.take<float>(elite_sampler ? (size_t)p->elite_slices * N * D : 1);
     const bool radix = p->N >= kRadixMinN;
     const size_t o_rka = L.take<unsigned long long>(radix ? N : 1);
@@ -742,6 +744,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mu_prev = (double *)(b + o_mu_prev);
     p->elite_Y = (float *)(b + o_elite_Y);
     p->mu_f = (float *)(b + o_mu_f);
+    p->elite_sw = (double *)(b + o_elite_sw);
     p->sample_part = (float *)(b + o_sample_part);
     p->cmak = cma_consts(p->D, p->nu);
     p->rkey_a = (unsigned long long *)(b + o_rka);
@@ -779,6 +782,9 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     if ((rc = stage_scene(p, scene)) != CP_OK) return fail(rc);
     if ((rc = launch_basis_table(p->S, p->basis, p->st)) != CP_OK) return fail(rc);
     if ((rc = launch_weights(p->nu, p->w, p->st)) != CP_OK) return fail(rc);
+    if (p->prm.sampler == CP_SAMPLE_ELITES &&
+        (rc = launch_elite_weights(p->w, p->nu, p->prm.sigma, p->elite_sw, p->st)) != CP_OK)
+        return fail(rc);
     e = cudaStreamSynchronize(p->st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamSynchronize(init)"));
     *out = p;

@@ -5,6 +5,7 @@
 // is normal with mean mu and covariance sigma^2 C exactly, so the FP64 moments and the FP64
 // Cholesky factor (whose dependent chains are slow on this part) leave the iteration; the
 // draw is an FP32 product of N x nu normals and the nu x D scaled elite deviations.
+//   k_elite_weights  sigma sqrt(w_j), once per planner
 //   k_elite_mean     mu (FP64, about the best elite, fixed order) and Y[j][d] =
 //                    sigma sqrt(w_j) (x_(j)d - mu_d) in FP32
 //   k_sample_elites  partial products over a slice of the elites: a CTA takes 64 candidates
@@ -42,9 +43,15 @@ __device__ __forceinline__ float normal_at(uint32_t i, uint32_t j, uint32_t iter
 // One block per coordinate d: mu_d = x_(1)d + sum_j w_j (x_(j)d - x_(1)d), then the column d
 // of Y. The sum runs over the elites in a fixed partition (thread t takes j = t, t + 256, ...)
 // and a fixed reduction tree.
+__global__ void k_elite_weights(const double *__restrict__ w, int nu, double sigma, double *sw)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nu) sw[k] = sigma * sqrt(w[k]);
+}
+
 __global__ void __launch_bounds__(256)
-k_elite_mean(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D, double sigma,
-             double *mu, float *mu_f, float *Y)
+k_elite_mean(const float *__restrict__ elites, const double *__restrict__ w, const double *__restrict__ sw,
+             int nu, int D, double *mu, float *mu_f, float *Y)
 {
     __shared__ double s_part[8];
     __shared__ double s_mu;
@@ -72,7 +79,7 @@ k_elite_mean(const float *__restrict__ elites, const double *__restrict__ w, int
     __syncthreads();
     const double m = s_mu;
     for (int k = tid; k < nu; k += 256)
-        Y[(size_t)k * D + d] = (float)(sigma * sqrt(w[k]) * ((double)elites[(size_t)k * D + d] - m));
+        Y[(size_t)k * D + d] = (float)(sw[k] * ((double)elites[(size_t)k * D + d] - m));
 }
 
 // Slice s of the elites [j_begin, j_end) for the tile (candidates c0.., coordinates d0..):
@@ -165,10 +172,17 @@ int elite_slices(int N, int D, int nu, int num_sms)
     return s < 1 ? 1 : s;
 }
 
-int launch_elite_mean(const float *elites, const double *w, int nu, int D, double sigma, double *mu, float *mu_f,
+int launch_elite_weights(const double *w, int nu, double sigma, double *sw, cudaStream_t st)
+{
+    k_elite_weights<<<(nu + 255) / 256, 256, 0, st>>>(w, nu, sigma, sw);
+    CP_LAUNCHED("k_elite_weights");
+    return CP_OK;
+}
+
+int launch_elite_mean(const float *elites, const double *w, const double *sw, int nu, int D, double *mu, float *mu_f,
                       float *Y, cudaStream_t st)
 {
-    k_elite_mean<<<D, 256, 0, st>>>(elites, w, nu, D, sigma, mu, mu_f, Y);
+    k_elite_mean<<<D, 256, 0, st>>>(elites, w, sw, nu, D, mu, mu_f, Y);
     CP_LAUNCHED("k_elite_mean");
     return CP_OK;
 }
