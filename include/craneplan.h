@@ -228,7 +228,10 @@ int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4]);
 /* Algorithm 1 step (1): d_xi[i] = mu + L z_i for i < N, L L^T = sigma^2 C, z_i the D
  * standard normals of Philox4x32-10 at counter (block j, candidate i, iteration `iter`,
  * query) under key seed, through Box-Muller (block j gives z[4j..4j+3]). d_xi is
- * float[N][K][4] on the device. Errors: CP_ERR_STATE (no end points), CP_ERR_ARG. */
+ * float[N][K][4] on the device. Every candidate array of this API (d_xi here and in
+ * cp_evaluate, cp_update, cp_smooth_cost, cp_smooth_cost_grad, cp_polish) is read and
+ * written one control point (16 bytes) at a time and must be 16-byte aligned; an
+ * unaligned pointer is CP_ERR_ARG. Errors: CP_ERR_STATE (no end points), CP_ERR_ARG. */
 int cp_sample(cp_planner *p, int32_t iter, float *d_xi);
 
 /* Algorithm 1 step (2): the cost of Eq. path opt for n candidates d_xi (float[n][K][4],

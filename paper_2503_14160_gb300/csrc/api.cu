@@ -112,6 +112,9 @@ struct Layout {
 
 bool is_finite(double v) { return std::isfinite(v); }
 
+// Candidate arrays are read and written one control point (four floats) at a time.
+bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
 }  // namespace
 
 struct cp_planner {
@@ -155,8 +158,9 @@ struct cp_planner {
     double *cma = nullptr;      // CMA-ES rule: {sigma, sigma before the update, h_sigma, |p_sigma|}
     double *p_sigma = nullptr, *p_c = nullptr, *mu_prev = nullptr;
     CmaConsts cmak{};
-    // factor-free sampler: scaled elite deviations Y [nu][D], the mean in FP32, the slice
-    // partials [slices][N][D]; elites_ready when the last step was such an update
+    // factor-free sampler: scaled elite deviations Y (TF32 pair, packed in the tensor-core
+    // operand layout), the mean in FP32, the slice partials [slices][N][D]; elites_ready
+    // when the last step was such an update
     float *elite_Y = nullptr, *mu_f = nullptr, *sample_part = nullptr;
     double *elite_sw = nullptr;   // sigma sqrt(w_j)
     int elite_slices = 1;
@@ -471,7 +475,7 @@ int run_sample(cp_planner *p, int iter, float *d_xi)
     if (p->elites_ready)
         rc = launch_sample_elites(p->elite_Y, p->mu_f, p->N, p->K, p->nu, p->elite_slices, p->prm.sigma,
                                   p->prm.eps, p->prm.seed, (uint32_t)iter, p->prm.query, p->sample_part, d_xi,
-                                  p->st);
+                                  p->status, p->st);
     else
         rc = launch_sample(p->mu, p->Lt, p->N, p->K, p->prm.seed, (uint32_t)iter, p->prm.query, d_xi,
                            p->st);
@@ -690,7 +694,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_mu_prev = L.take<double>(D);
     const bool elite_sampler = p->prm.sampler == CP_SAMPLE_ELITES;
     p->elite_slices = elite_sampler ? elite_slices(p->N, p->D, p->nu, p->num_sms) : 1;
-    const size_t o_elite_Y = L.take<float>(elite_sampler ? nu * D : 1);
+    const size_t o_elite_Y = L.take<float>(elite_sampler ? elite_operand_floats(p->nu, p->D) : 1);
     const size_t o_mu_f = L.take<float>(D);
     const size_t o_elite_sw = L.take<double>(elite_sampler ? nu : 1);
     const size_t o_sample_part = L.take<float>(elite_sampler ? (size_t)p->elite_slices * N * D : 1);
@@ -833,6 +837,7 @@ int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4])
 int cp_sample(cp_planner *p, int32_t iter, float *d_xi)
 {
     if (!p || !d_xi) return set_error("NULL argument"), CP_ERR_ARG;
+    if (!aligned16(d_xi)) return set_error("d_xi is not 16-byte aligned"), CP_ERR_ARG;
     if (iter < 0) return set_error("iteration must be >= 0"), CP_ERR_ARG;
     if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
     return run_sample(p, iter, d_xi);
@@ -844,6 +849,7 @@ int cp_evaluate(cp_planner *p, const float *d_xi, int32_t n, double *d_J, uint8_
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     if (n < 0 || n > p->N) return set_error("n = %d outside 0..N = %d", n, p->N), CP_ERR_ARG;
     if (n > 0 && (!d_xi || !d_J)) return set_error("d_xi and d_J are required"), CP_ERR_ARG;
+    if (!aligned16(d_xi)) return set_error("d_xi is not 16-byte aligned"), CP_ERR_ARG;
     if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
     if (n == 0) return CP_OK;
     return run_eval(p, d_xi, n, d_J, d_flag, d_terms, d_substep_flags, d_pen);
@@ -852,6 +858,7 @@ int cp_evaluate(cp_planner *p, const float *d_xi, int32_t n, double *d_J, uint8_
 int cp_update(cp_planner *p, const double *d_J, const float *d_xi)
 {
     if (!p || !d_J || !d_xi) return set_error("NULL argument"), CP_ERR_ARG;
+    if (!aligned16(d_xi)) return set_error("d_xi is not 16-byte aligned"), CP_ERR_ARG;
     if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
     return run_update(p, d_J, d_xi);
 }
@@ -984,6 +991,7 @@ static int smooth_check(cp_planner *p, int n, const void *xi)
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     if (n < 0 || n > p->N) return set_error("n = %d outside 0..N = %d", n, p->N), CP_ERR_ARG;
     if (n > 0 && !xi) return set_error("d_xi is NULL"), CP_ERR_ARG;
+    if (!aligned16(xi)) return set_error("d_xi is not 16-byte aligned"), CP_ERR_ARG;
     if (!p->have_endpoints) return set_error("set the end points first"), CP_ERR_STATE;
     const size_t smem = smooth_smem_bytes(p->sdev.n_cyl, p->sdev.n_box, p->S, p->K);
     if (smem > (size_t)p->smem_optin)

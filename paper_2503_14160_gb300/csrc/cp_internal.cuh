@@ -205,12 +205,13 @@ int launch_cma_update(const float *elites, const double *w, int nu, int D, const
                       const double *L, const CmaConsts &k, int t, double *s2p, double *s1p, double *mu,
                       double *C, double *p_sigma, double *p_c, double *cma, cudaStream_t st);
 int elite_slices(int N, int D, int nu, int num_sms);
+size_t elite_operand_floats(int nu, int D);   // packed Y_hi / Y_lo of the tensor-core sampler
 int launch_elite_weights(const double *w, int nu, double sigma, double *sw, cudaStream_t st);
 int launch_elite_mean(const float *elites, const double *w, const double *sw, int nu, int D, double *mu, float *mu_f,
-                      float *Y, cudaStream_t st);
-int launch_sample_elites(const float *Y, const float *mu_f, int N, int K, int nu, int slices, double sigma,
+                      float *Yp, cudaStream_t st);
+int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int nu, int slices, double sigma,
                          double eps, uint64_t seed, uint32_t iter, uint32_t query, float *P, float *xi,
-                         cudaStream_t st);
+                         uint32_t *status, cudaStream_t st);
 int update_chunks(int nu);
 int radix_tiles(int N);
 int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,

@@ -65,6 +65,7 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     if ((n_cyl > 0 && !d_cyl) || (n_box > 0 && !d_box) || (n > 0 && (!d_xi || !d_J)) ||
         !h_q0 || !h_qd)
         return set_error("NULL argument"), CP_ERR_ARG;
+    if (((uintptr_t)d_xi & 15u) != 0) return set_error("d_xi is not 16-byte aligned"), CP_ERR_ARG;
     if (!(w_c >= 0.0) || !(w_l >= 0.0) || !(lambda_c >= 0.0))
         return set_error("cost weights must be >= 0"), CP_ERR_ARG;
     if (n == 0) return CP_OK;
