@@ -161,8 +161,10 @@ struct cp_planner {
     // factor-free sampler: scaled elite deviations Y (TF32 pair, packed in the tensor-core
     // operand layout), the mean in FP32, the slice partials [slices][N][D]; elites_ready
     // when the last step was such an update
-    float *elite_Y = nullptr, *mu_f = nullptr, *sample_part = nullptr;
-    double *elite_sw = nullptr;   // sigma sqrt(w_j)
+    float *elite_Y = nullptr, *mu_f = nullptr, *mu_lo = nullptr, *sample_part = nullptr;
+    float *elite_sw = nullptr;        // sigma sqrt(w_j)
+    double *elite_mean_part = nullptr;   // per-block partial sums of the mean
+    unsigned int *elite_bar = nullptr;   // grid barrier of the elite update (count, generation)
     int elite_slices = 1;
     bool elites_ready = false;
     HullDims hulls{{0.2f, 0.2f, 0.15f}, {0.2f, 0.2f, 0.15f}, 0.2f, 0.25f, 1.0f, 0.f};   // CP_COLLISION_HULLS
@@ -495,7 +497,6 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
                                        p->st)) != CP_OK)
             return rc;
     } else {
-        CP_CUDA(cudaMemsetAsync(p->rank, 0, sizeof(int) * p->N, p->st));
         if ((rc = launch_rank(d_J, p->N, p->nu, p->rank, p->st)) != CP_OK) return rc;
         if ((rc = launch_scatter(p->rank, d_J, d_xi, p->N, p->nu, p->D, p->elite, p->elites, p->best,
                                  p->st)) != CP_OK)
@@ -509,8 +510,10 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
             return rc;
     } else if (p->prm.sampler == CP_SAMPLE_ELITES) {
         // the next draw comes from these elites: the mean and the scaled deviations, no C
-        if ((rc = launch_elite_mean(p->elites, p->w, p->elite_sw, p->nu, p->D, p->mu, p->mu_f, p->elite_Y,
-                                    p->st)) != CP_OK)
+        if ((rc = launch_elite_update(p->elites, p->w, p->elite_sw, p->nu, p->D,
+                                      elite_update_blocks(p->nu, p->num_sms), p->elite_mean_part,
+                                      p->elite_bar, p->mu, p->mu_f, p->mu_lo, p->elite_Y, p->status,
+                                      p->st)) != CP_OK)
             return rc;
         if ((rc = p->timer.end(ST_UPDATE, p->st)) != CP_OK) return rc;
         p->elites_ready = true;
@@ -696,7 +699,11 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->elite_slices = elite_sampler ? elite_slices(p->N, p->D, p->nu, p->num_sms) : 1;
     const size_t o_elite_Y = L.take<float>(elite_sampler ? elite_operand_floats(p->nu, p->D) : 1);
     const size_t o_mu_f = L.take<float>(D);
-    const size_t o_elite_sw = L.take<double>(elite_sampler ? nu : 1);
+    const size_t o_mu_lo = L.take<float>(D);
+    const size_t o_elite_sw = L.take<float>(elite_sampler ? nu : 1);
+    const size_t o_elite_mp =
+        L.take<double>(elite_sampler ? (size_t)elite_update_blocks(p->nu, p->num_sms) * D : 1);
+    const size_t o_elite_bar = L.take<unsigned int>(2);
     const size_t o_sample_part = L.take<float>(elite_sampler ? (size_t)p->elite_slices * N * D : 1);
     const bool radix = p->N >= kRadixMinN;
     const size_t o_rka = L.take<unsigned long long>(radix ? N : 1);
@@ -748,7 +755,10 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->mu_prev = (double *)(b + o_mu_prev);
     p->elite_Y = (float *)(b + o_elite_Y);
     p->mu_f = (float *)(b + o_mu_f);
-    p->elite_sw = (double *)(b + o_elite_sw);
+    p->mu_lo = (float *)(b + o_mu_lo);
+    p->elite_sw = (float *)(b + o_elite_sw);
+    p->elite_mean_part = (double *)(b + o_elite_mp);
+    p->elite_bar = (unsigned int *)(b + o_elite_bar);
     p->sample_part = (float *)(b + o_sample_part);
     p->cmak = cma_consts(p->D, p->nu);
     p->rkey_a = (unsigned long long *)(b + o_rka);
@@ -822,6 +832,8 @@ int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4])
     memcpy(ends, h_q0, 4 * sizeof(double));
     memcpy(ends + 4, h_qd, 4 * sizeof(double));
     CP_CUDA(cudaMemcpyAsync(p->consts, ends, sizeof ends, cudaMemcpyHostToDevice, p->st));
+    // the rank counters are zero between updates; a reset restores that after any failure
+    CP_CUDA(cudaMemsetAsync(p->rank, 0, sizeof(int) * p->N, p->st));
     p->q0f = make_float4((float)h_q0[0], (float)h_q0[1], (float)h_q0[2], (float)h_q0[3]);
     p->qdf = make_float4((float)h_qd[0], (float)h_qd[1], (float)h_qd[2], (float)h_qd[3]);
     int rc = launch_init_distribution(p->consts, p->consts + 4, p->consts + 8, p->consts + 12, p->K,

@@ -189,7 +189,7 @@ int sample_configure();
 
 int launch_weights(int nu, double *w, cudaStream_t st);
 int launch_rank(const double *J, int N, int nu, int *rank, cudaStream_t st);
-int launch_scatter(const int *rank, const double *J, const float *xi, int N, int nu, int D,
+int launch_scatter(int *rank, const double *J, const float *xi, int N, int nu, int D,
                    int *elite, float *elites, double *best_J, cudaStream_t st);
 int launch_moments(const float *elites, const double *w, int nu, int D, double eps,
                    double *s2p, double *s1p, double *mu, double *C, cudaStream_t st);
@@ -206,9 +206,11 @@ int launch_cma_update(const float *elites, const double *w, int nu, int D, const
                       double *C, double *p_sigma, double *p_c, double *cma, cudaStream_t st);
 int elite_slices(int N, int D, int nu, int num_sms);
 size_t elite_operand_floats(int nu, int D);   // packed Y_hi / Y_lo of the tensor-core sampler
-int launch_elite_weights(const double *w, int nu, double sigma, double *sw, cudaStream_t st);
-int launch_elite_mean(const float *elites, const double *w, const double *sw, int nu, int D, double *mu, float *mu_f,
-                      float *Yp, cudaStream_t st);
+int launch_elite_weights(const double *w, int nu, double sigma, float *sw, cudaStream_t st);
+int elite_update_blocks(int nu, int num_sms);
+int launch_elite_update(const float *elites, const double *w, const float *sw, int nu, int D, int blocks,
+                        double *part, unsigned int *bar, double *mu, float *mu_f, float *mu_lo, float *Yp,
+                        uint32_t *status, cudaStream_t st);
 int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int nu, int slices, double sigma,
                          double eps, uint64_t seed, uint32_t iter, uint32_t query, float *P, float *xi,
                          uint32_t *status, cudaStream_t st);

@@ -328,55 +328,6 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
 }
 
 
-// Four lanes per candidate: lane g of the group sums the candidate's chunks g, g + 4, ...
-// in FP64, and two shuffle steps combine the four (a fixed order, so results are
-// deterministic). The group's lanes read neighbouring chunk records of one row.
-constexpr int kFinalizeLanes = 4;
-
-__global__ void k_eval_finalize(const float4 *__restrict__ partial,
-                                const uint32_t *__restrict__ flagword, int n, int chunks,
-                                double w_c, double w_l, double lambda_c, double *J,
-                                uint8_t *flag, double *terms, uint32_t *substep_flags)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / kFinalizeLanes, g = t % kFinalizeLanes;
-    const bool active = i < n;
-    double jp = 0.0, jc = 0.0, jl = 0.0, len = 0.0;
-    int n_flagged = 0;
-    if (active) {
-        for (int c = g; c < chunks; c += kFinalizeLanes) {
-            const float4 v = partial[(size_t)i * chunks + c];
-            const uint32_t w = flagword[(size_t)i * chunks + c];
-            jp += (double)v.x;
-            jc += (double)v.y;
-            jl += (double)v.z;
-            len += (double)v.w;
-            n_flagged += __popc(w);
-            if (substep_flags != nullptr) substep_flags[(size_t)i * chunks + c] = w;
-        }
-    }
-#pragma unroll
-    for (int off = 1; off < kFinalizeLanes; off <<= 1) {   // every lane of the warp takes part
-        jp += __shfl_xor_sync(0xffffffffu, jp, off);
-        jc += __shfl_xor_sync(0xffffffffu, jc, off);
-        jl += __shfl_xor_sync(0xffffffffu, jl, off);
-        len += __shfl_xor_sync(0xffffffffu, len, off);
-        n_flagged += __shfl_xor_sync(0xffffffffu, n_flagged, off);
-    }
-    if (!active || g != 0) return;
-    jc *= lambda_c;
-    J[i] = jp + w_c * jc + w_l * jl;
-    if (flag != nullptr) flag[i] = n_flagged > 0 ? 1 : 0;
-    if (terms != nullptr) {
-        double *tm = terms + (size_t)i * 5;
-        tm[0] = jp;
-        tm[1] = jc;
-        tm[2] = jl;
-        tm[3] = len;
-        tm[4] = (double)n_flagged;
-    }
-}
-
 // d(q) for single configurations: every pair, exact distances (no filter).
 template <int NSPH>
 __global__ void k_signed_distance(const ModelDev m, const SceneDev sc, const float *q, int n,
@@ -466,18 +417,6 @@ int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int nu
             k_eval<16><<<eval_grid(k_eval<16>, smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);
     }
     CP_LAUNCHED("k_eval");
-    return CP_OK;
-}
-
-int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n, int chunks,
-                         double w_c, double w_l, double lambda_c, double *J, uint8_t *flag,
-                         double *terms, uint32_t *substep_flags, cudaStream_t st)
-{
-    if (n == 0) return CP_OK;
-    const int threads = 256;
-    k_eval_finalize<<<(n * kFinalizeLanes + threads - 1) / threads, threads, 0, st>>>(
-        partial, flagword, n, chunks, w_c, w_l, lambda_c, J, flag, terms, substep_flags);
-    CP_LAUNCHED("k_eval_finalize");
     return CP_OK;
 }
 

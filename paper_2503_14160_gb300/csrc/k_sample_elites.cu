@@ -6,16 +6,18 @@
 // Cholesky factor (whose dependent chains are slow on this part) leave the iteration; the
 // draw is the product G Y of N x nu normals and the nu x D scaled elite deviations, a dense
 // contraction that runs on the tensor cores.
-//   k_elite_weights  sigma sqrt(w_j), once per planner
-//   k_elite_mean     mu (FP64, about the best elite, fixed order) and Y[j][d] =
-//                    sigma sqrt(w_j) (x_(j)d - mu_d), rounded to FP32 and split into two TF32
-//                    parts Y = Y_hi + Y_lo, written in the tensor cores' operand layout
+//   k_elite_weights  sigma sqrt(w_j) in FP32, once per planner
+//   k_elite_update   one cooperative launch: mu = sum_j w_j x_(j) in FP64 (block partials,
+//                    a grid barrier, a fixed-order sum), mu as an FP32 pair mu_f + mu_lo,
+//                    and Y[j][d] = sigma sqrt(w_j) (x_(j)d - mu_d) in FP32 (within 4 ulp),
+//                    split into two TF32 parts Y = Y_hi + Y_lo, written in the tensor cores'
+//                    operand layout
 //   k_sample_elites  partial products over a slice of the elites on the tensor cores
-//                    (tcgen05, kind::tf32): a CTA takes 128 candidates and all D coordinates,
-//                    its 256 threads generate the normals of 16 elites per pipeline stage
+//                    (tcgen05, kind::tf32): a CTA takes 128 candidates and all D coordinates;
+//                    eight warps generate the normals of 16 elites per pipeline stage
 //                    (Philox blocks in place, split G = G_hi + G_lo) into shared memory
-//                    while the previous stage's MMAs run; the accumulator lives in tensor
-//                    memory. G Y is formed as G_hi Y_hi + G_hi Y_lo + G_lo Y_hi ("3xTF32":
+//                    while a ninth warp feeds the tensor cores the previous stage; the
+//                    accumulator lives in tensor memory. G Y is formed as G_hi Y_hi + G_hi Y_lo + G_lo Y_hi ("3xTF32":
 //                    each product within 3 * 2^-22 of the FP32 product, FP32 accumulation)
 //   k_sample_reduce  xi = mu + sum of the slices (fixed order) + sigma sqrt(eps) g'
 // Normals: candidate i at iteration t has the stream of Philox blocks (b, i, t, query), four
@@ -62,70 +64,165 @@ uint32_t tmem_columns(int Dp)
     return c;
 }
 
-__global__ void k_elite_weights(const double *__restrict__ w, int nu, double sigma, double *sw)
+__global__ void k_elite_weights(const double *__restrict__ w, int nu, double sigma, float *sw)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nu) sw[k] = sigma * sqrt(w[k]);
+    if (k < nu) sw[k] = (float)(sigma * sqrt(w[k]));
 }
 
-// One block per coordinate d: mu_d = x_(1)d + sum_j w_j (x_(j)d - x_(1)d), then the row d of
-// the packed operand (Y_hi, Y_lo per chunk of 16 elites). The sum runs over the elites in a
-// fixed partition (thread t takes j = t, t + 256, ...) and a fixed reduction tree. Rows
-// d >= D and elites past nu of the packed operand stay zero (the buffer is cleared once).
-__global__ void __launch_bounds__(256)
-k_elite_mean(const float *__restrict__ elites, const double *__restrict__ w, const double *__restrict__ sw,
-             int nu, int D, double *mu, float *mu_f, float *Yp)
+constexpr int kEUThreads = 256;
+constexpr int kSumBatch = 16;  // partials loaded before they are added
+
+// All blocks of a launch wait here until every block has arrived. bar[0] counts arrivals,
+// bar[1] is the generation; both start at zero and the last arrival resets the count, so
+// the pair is ready for the next launch. The wait is bounded: false when it ran out. Only
+// for cooperative launches, whose blocks are all resident at once.
+__device__ bool grid_barrier(unsigned int *bar, unsigned int nblocks, long long limit)
 {
-    __shared__ double s_part[8];
-    __shared__ double s_mu;
-    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
-    const double x1 = (double)elites[d];
-    double a0 = 0.0, a1 = 0.0;
-    int j = tid;
-    for (; j + 256 < nu; j += 512) {
-        a0 = fma(w[j], (double)elites[(size_t)j * D + d] - x1, a0);
-        a1 = fma(w[j + 256], (double)elites[(size_t)(j + 256) * D + d] - x1, a1);
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = bar + 1;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > limit) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
     }
-    if (j < nu) a0 = fma(w[j], (double)elites[(size_t)j * D + d] - x1, a0);
-    double v = a0 + a1;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Steps (5) and the operand of the next draw, in one cooperative launch of nb blocks (one
+// SM each at most) over the chunks of 16 elites (block b takes chunks b, b + nb, ...):
+//  1. mu = sum_j w_j x_(j) (FP64): thread (g, d), g < G = 256 / D' (D' = D rounded up to
+//     32), takes elites g, g + G, ... of the block's chunks; the groups are added in order
+//     into part[b][d].
+//  2. after a grid barrier every block adds part[0..nb)[d] in the same fixed order (so the
+//     result is deterministic and identical in every block); block 0 writes mu, its FP32
+//     rounding mu_f and the rest mu_lo = mu - mu_f rounded to FP32.
+//  3. Y[j][d] = sigma sqrt(w_j) (x_(j)d - mu_d) in FP32 against mu_f + mu_lo: x - mu_f is
+//     exact when both lie within a factor of two of each other (Sterbenz) and otherwise
+//     rounded once with mu_lo far below it, so with the second difference, the FP32
+//     sigma sqrt(w_j) and the product, Y is within 4 ulp of its FP64 value; then the TF32
+//     split Y = Y_hi + Y_lo into the tensor cores' layout. Rows d >= D and elites past nu
+//     of the packed operand stay zero (the buffer is cleared once).
+// FP64 work is one FMA per element and a short fixed sum per coordinate: FP64 throughput is
+// a small fraction of FP32 on this part. A barrier that runs out records DEV_ERR_TIMEOUT.
+__global__ void __launch_bounds__(kEUThreads)
+k_elite_update(const float *__restrict__ elites, const double *__restrict__ w, const float *__restrict__ sw,
+               int nu, int D, double *part, unsigned int *bar, double *mu, float *mu_f, float *mu_lo, float *Yp,
+               uint32_t *status)
+{
+    __shared__ double s_acc[kEUThreads];
+    __shared__ float s_hi[4 * CP_MAX_WAYPOINTS], s_lo[4 * CP_MAX_WAYPOINTS];
+    const int Dr = (D + 31) & ~31, G = kEUThreads / Dr, Dp = padded_d(D);
+    const int tid = threadIdx.x, g = tid / Dr, d = tid - g * Dr;
+    const bool on = g < G && d < D;
+    const int nb = (int)gridDim.x, chunks = (nu + kChunkE - 1) / kChunkE;
+
+    double a = 0.0;
+    if (on)
+        for (int c = blockIdx.x; c < chunks; c += nb) {   // at most 8 elites of a chunk per thread
+            const int e0 = c * kChunkE, ne = min(kChunkE, nu - e0);
+            double wv[8];
+            float xv[8];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) s_part[tid >> 5] = v;
+            for (int m = 0; m < 8; ++m) {   // loads first, all in flight together
+                const int k = g + m * G;
+                wv[m] = k < ne ? w[e0 + k] : 0.0;
+                xv[m] = k < ne ? elites[(size_t)(e0 + k) * D + d] : 0.f;
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) a = fma(wv[m], (double)xv[m], a);
+        }
+    s_acc[tid] = a;
     __syncthreads();
-    if (tid == 0) {
-        double sum = 0.0;
-        for (int k = 0; k < 8; ++k) sum += s_part[k];
-        s_mu = x1 + sum;
-        mu[d] = s_mu;
-        mu_f[d] = (float)s_mu;
+    if (tid < D) {
+        double v = s_acc[tid];
+        for (int q = 1; q < G; ++q) v += s_acc[q * Dr + tid];
+        part[(size_t)blockIdx.x * D + tid] = v;
+    }
+    __threadfence();
+    const bool ok = grid_barrier(bar, (unsigned int)nb, kWaitCycles);
+
+    double v = 0.0;
+    if (on)
+        for (int b0 = g; b0 < nb; b0 += kSumBatch * G) {
+            double t[kSumBatch];
+#pragma unroll
+            for (int q = 0; q < kSumBatch; ++q) {
+                const int b = b0 + q * G;
+                t[q] = b < nb ? __ldcg(part + (size_t)b * D + d) : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kSumBatch; ++q) v += t[q];
+        }
+    s_acc[tid] = v;
+    __syncthreads();
+    if (tid < D) {
+        double m = s_acc[tid];
+        for (int q = 1; q < G; ++q) m += s_acc[q * Dr + tid];
+        const float hi = (float)m, lo = (float)(m - (double)hi);
+        s_hi[tid] = hi;
+        s_lo[tid] = lo;
+        if (blockIdx.x == 0) {
+            mu[tid] = m;
+            mu_f[tid] = hi;
+            mu_lo[tid] = lo;
+        }
     }
     __syncthreads();
-    const double m = s_mu;
-    const int Dp = padded_d(D);
-    for (int k = tid; k < nu; k += 256) {
-        const float y = (float)(sw[k] * ((double)elites[(size_t)k * D + d] - m));
-        const float hi = tc::to_tf32(y), lo = tc::to_tf32(y - hi);
-        float *chunk = Yp + (size_t)(k / kChunkE) * chunk_floats(Dp);
-        const int idx = core_index(d, k % kChunkE);
-        chunk[idx] = hi;
-        chunk[Dp * kChunkE + idx] = lo;
+
+    for (int c = blockIdx.x; c < chunks; c += nb) {
+        float *chunk = Yp + (size_t)c * chunk_floats(Dp);
+        const int ne = min(kChunkE, nu - c * kChunkE);
+        for (int e = tid; e < ne * D; e += kEUThreads) {
+            const int k = e / D, dd = e - k * D;
+            const int j = c * kChunkE + k;
+            const float dev = __fsub_rn(__fsub_rn(elites[(size_t)j * D + dd], s_hi[dd]), s_lo[dd]);
+            const float y = __fmul_rn(sw[j], dev);
+            const float hi = tc::to_tf32(y), lo = tc::to_tf32(__fsub_rn(y, hi));
+            const int idx = core_index(dd, k);
+            chunk[idx] = hi;
+            chunk[Dp * kChunkE + idx] = lo;
+        }
     }
+    if (!ok && tid == 0 && status != nullptr) atomicOr(status, DEV_ERR_TIMEOUT);
 }
 
 // Slice blockIdx.y of the elite chunks, for candidates 128 blockIdx.x ...:
 // P[slice][i][d] = sum over the slice's elites j of g_ij Y[j][d].
-// Per stage (16 elites): thread 0 brings the packed Y chunk in with one bulk copy, every
-// thread writes 8 normals of its candidate row (G_hi, G_lo) into the stage, and after a
-// barrier thread 0 issues 6 MMAs of 128 x Dp x 8 and commits them to the stage's barrier;
-// a stage is refilled once that barrier reports its MMAs done. Every wait is bounded: when
-// one runs out the CTA records DEV_ERR_TIMEOUT, goes on (results are then meaningless) and
-// still releases its tensor memory.
-__global__ void __launch_bounds__(kTcThreads)
+// Warp-specialised pipeline over stages of 16 elites (two stages in shared memory):
+//  - warps 0-7 (256 threads, two per candidate row) write the stage's normals (G_hi, G_lo,
+//    8 per thread), make them visible to the tensor cores (proxy fence) and arrive on the
+//    stage's a_full barrier, one arrival per warp; before refilling a stage they wait for
+//    its done barrier (the MMAs that read it have completed), never for each other;
+//  - warp 8 (one elected lane) brings each packed Y chunk in with a bulk copy (b_full),
+//    waits for a_full and b_full, issues the stage's 6 MMAs of 128 x Dp x 8 and commits
+//    them to done.
+// Every wait is bounded: when one runs out the CTA records DEV_ERR_TIMEOUT, goes on
+// (results are then meaningless) and still releases its tensor memory.
+__global__ void __launch_bounds__(kTcThreads + 32)
 k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int slices, uint32_t tmem_cols,
                 uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *P, uint32_t *status)
 {
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t full[kStages], done[kStages];
+    __shared__ __align__(8) uint64_t a_full[kStages], b_full[kStages], done[kStages];
     __shared__ uint32_t s_tmem;
     const int Dp = padded_d(D);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -138,7 +235,8 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&a_full[s], kTcThreads / 32);
+            tc::mbar_init(&b_full[s], 1);
             tc::mbar_init(&done[s], 1);
         }
         tc::mbar_init_fence();
@@ -148,77 +246,101 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-
-    const int r = tid & (kTcM - 1), half = tid >> 7;   // candidate row; Philox blocks 2 half, 2 half + 1
-    const bool row_ok = m0 + r < N;
-    const uint32_t idesc = tc::idesc_tf32(kTcM, Dp);
     bool late = false;
-    for (int it = 0; it < n; ++it) {
-        const int s = it % kStages;
-        float *a_hi = smem + s * stage_floats, *a_lo = a_hi + a_floats, *b_hi = a_lo + a_floats;
-        if (it >= kStages && !tc::mbar_wait(&done[s], ((it - kStages) / kStages) & 1, kWaitCycles)) late = true;
-        const int c = c_begin + it;
-        if (tid == 0) {
-            tc::mbar_expect_tx(&full[s], b_bytes);
-            tc::bulk_g2s(b_hi, Yp + (size_t)c * b_floats, b_bytes, &full[s]);
+
+    if (warp == kTcThreads / 32) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(kTcM, Dp);
+            for (int it = 0; it < kStages && it < n; ++it) {
+                float *b_hi = smem + it * stage_floats + 2 * a_floats;
+                tc::mbar_expect_tx(&b_full[it], b_bytes);
+                tc::bulk_g2s(b_hi, Yp + (size_t)(c_begin + it) * b_floats, b_bytes, &b_full[it]);
+            }
+            for (int it = 0; it < n; ++it) {
+                const int s = it % kStages;
+                float *a_hi = smem + s * stage_floats, *a_lo = a_hi + a_floats, *b_hi = a_lo + a_floats;
+                if (!tc::mbar_wait(&a_full[s], (it / kStages) & 1, kWaitCycles)) late = true;
+                if (!tc::mbar_wait(&b_full[s], (it / kStages) & 1, kWaitCycles)) late = true;
+                tc::fence_after_sync();
+                const uint32_t sa_hi = tc::smem_addr(a_hi), sa_lo = tc::smem_addr(a_lo);
+                const uint32_t sb_hi = tc::smem_addr(b_hi), sb_lo = sb_hi + 4u * (uint32_t)(Dp * kChunkE);
+#pragma unroll
+                for (int ks = 0; ks < kChunkE / 8; ++ks) {
+                    const uint32_t o = 2 * kCoreLbo * (uint32_t)ks;   // 8 elements of K: two core matrices
+                    const uint64_t ah = tc::desc_kmajor(sa_hi + o, kCoreLbo, kCoreSbo);
+                    const uint64_t al = tc::desc_kmajor(sa_lo + o, kCoreLbo, kCoreSbo);
+                    const uint64_t bh = tc::desc_kmajor(sb_hi + o, kCoreLbo, kCoreSbo);
+                    const uint64_t bl = tc::desc_kmajor(sb_lo + o, kCoreLbo, kCoreSbo);
+                    tc::mma_tf32(tmem, ah, bh, idesc, it > 0 || ks > 0);
+                    tc::mma_tf32(tmem, ah, bl, idesc, true);
+                    tc::mma_tf32(tmem, al, bh, idesc, true);
+                }
+                tc::mma_commit(&done[s]);
+                // the chunk two stages on goes where the previous stage's MMAs read
+                const int nx = it + 1, sx = nx % kStages;
+                if (it >= 1 && nx < n) {
+                    if (!tc::mbar_wait(&done[sx], ((nx - kStages) / kStages) & 1, kWaitCycles)) late = true;
+                    float *bx = smem + sx * stage_floats + 2 * a_floats;
+                    tc::mbar_expect_tx(&b_full[sx], b_bytes);
+                    tc::bulk_g2s(bx, Yp + (size_t)(c_begin + nx) * b_floats, b_bytes, &b_full[sx]);
+                }
+            }
         }
+        __syncwarp();
+    } else {
+        const int r = tid & (kTcM - 1), half = tid >> 7;   // candidate row; Philox blocks 2 half, 2 half + 1
+        const bool row_ok = m0 + r < N;
+        for (int it = 0; it < n; ++it) {
+            const int s = it % kStages;
+            float *a_hi = smem + s * stage_floats, *a_lo = a_hi + a_floats;
+            const int c = c_begin + it;
+            float h[kChunkE / 8][4], l[kChunkE / 8][4];
 #pragma unroll
-        for (int q = 0; q < kChunkE / 8; ++q) {
-            const int blk = (kChunkE / 8) * half + q;   // elites 4 blk .. 4 blk + 3 of the chunk
-            float z[4] = {0.f, 0.f, 0.f, 0.f};
-            if (row_ok) {
-                const uint4 x = philox4x32_10(
-                    make_uint4((uint32_t)(c * (kChunkE / 4) + blk), (uint32_t)(m0 + r), iter, query), k0, k1);
-                box_muller(x.x, x.y, z[0], z[1]);
-                box_muller(x.z, x.w, z[2], z[3]);
-            }
-            float h[4], l[4];
+            for (int q = 0; q < kChunkE / 8; ++q) {   // the normals before the wait for the stage
+                const int blk = (kChunkE / 8) * half + q;   // elites 4 blk .. 4 blk + 3 of the chunk
+                float z[4] = {0.f, 0.f, 0.f, 0.f};
+                if (row_ok) {
+                    const uint4 x = philox4x32_10(
+                        make_uint4((uint32_t)(c * (kChunkE / 4) + blk), (uint32_t)(m0 + r), iter, query), k0, k1);
+                    box_muller(x.x, x.y, z[0], z[1]);
+                    box_muller(x.z, x.w, z[2], z[3]);
+                }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                h[e] = tc::to_tf32(z[e]);
-                l[e] = tc::to_tf32(z[e] - h[e]);
+                for (int e = 0; e < 4; ++e) {
+                    h[q][e] = tc::to_tf32(z[e]);
+                    l[q][e] = tc::to_tf32(z[e] - h[q][e]);
+                }
             }
-            const int off = core_index(r, 4 * blk);
-            *reinterpret_cast<float4 *>(a_hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4 *>(a_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
-        }
-        tc::fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            if (!tc::mbar_wait(&full[s], (it / kStages) & 1, kWaitCycles)) late = true;
-            tc::fence_after_sync();
-            const uint32_t sa_hi = tc::smem_addr(a_hi), sa_lo = tc::smem_addr(a_lo);
-            const uint32_t sb_hi = tc::smem_addr(b_hi), sb_lo = sb_hi + 4u * (uint32_t)(Dp * kChunkE);
+            if (it >= kStages && !tc::mbar_wait(&done[s], ((it - kStages) / kStages) & 1, kWaitCycles)) late = true;
 #pragma unroll
-            for (int ks = 0; ks < kChunkE / 8; ++ks) {
-                const uint32_t o = 2 * kCoreLbo * (uint32_t)ks;   // 8 elements of K: two core matrices
-                const uint64_t ah = tc::desc_kmajor(sa_hi + o, kCoreLbo, kCoreSbo);
-                const uint64_t al = tc::desc_kmajor(sa_lo + o, kCoreLbo, kCoreSbo);
-                const uint64_t bh = tc::desc_kmajor(sb_hi + o, kCoreLbo, kCoreSbo);
-                const uint64_t bl = tc::desc_kmajor(sb_lo + o, kCoreLbo, kCoreSbo);
-                tc::mma_tf32(tmem, ah, bh, idesc, it > 0 || ks > 0);
-                tc::mma_tf32(tmem, ah, bl, idesc, true);
-                tc::mma_tf32(tmem, al, bh, idesc, true);
+            for (int q = 0; q < kChunkE / 8; ++q) {
+                const int off = core_index(r, 4 * ((kChunkE / 8) * half + q));
+                *reinterpret_cast<float4 *>(a_hi + off) = make_float4(h[q][0], h[q][1], h[q][2], h[q][3]);
+                *reinterpret_cast<float4 *>(a_lo + off) = make_float4(l[q][0], l[q][1], l[q][2], l[q][3]);
             }
-            tc::mma_commit(&done[s]);
+            tc::fence_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&a_full[s]);
         }
     }
     // the last commit covers every MMA of the CTA
     if (!tc::mbar_wait(&done[(n - 1) % kStages], ((n - 1) / kStages) & 1, kWaitCycles)) late = true;
     tc::fence_after_sync();
-    // warp w reads lanes 32 (w % 4) .. of tensor memory, columns 16 (w / 4) + 32 k
-    const int quarter = warp & 3, cgroup = warp >> 2;
-    const int i = m0 + 32 * quarter + lane;
-    float *out = P + ((size_t)slice * N + (size_t)(i < N ? i : 0)) * D;
-    for (int c0 = 16 * cgroup; c0 < Dp; c0 += 32) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
-        if (i < N) {
+    if (warp < kTcThreads / 32) {
+        // warp w reads lanes 32 (w % 4) .. of tensor memory, columns 16 (w / 4) + 32 k
+        const int quarter = warp & 3, cgroup = warp >> 2;
+        const int i = m0 + 32 * quarter + lane;
+        float *out = P + ((size_t)slice * N + (size_t)(i < N ? i : 0)) * D;
+        for (int c0 = 16 * cgroup; c0 < Dp; c0 += 32) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
+            if (i < N) {
 #pragma unroll
-            for (int g = 0; g < 4; ++g)
-                if (c0 + 4 * g < D)
-                    *reinterpret_cast<float4 *>(out + c0 + 4 * g) =
-                        make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                for (int g = 0; g < 4; ++g)
+                    if (c0 + 4 * g < D)
+                        *reinterpret_cast<float4 *>(out + c0 + 4 * g) =
+                            make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+            }
         }
     }
     if (late && status != nullptr) atomicOr(status, DEV_ERR_TIMEOUT);
@@ -278,7 +400,8 @@ size_t elite_operand_floats(int nu, int D)
 // Slices of the elite chunks for N candidates: as many CTAs as are resident on the GPU at
 // once (the normals dominate the work, so one wave of equal CTAs), at most 32 slices and at
 // least one chunk each. Residency follows from the shared memory of a CTA (dynamic, static
-// and the driver's reserve) against the SM's, its threads and its tensor-memory columns.
+// and the driver's reserve) against the SM's, its threads, registers and tensor-memory
+// columns.
 int elite_slices(int N, int D, int nu, int num_sms)
 {
     const int Dp = padded_d(D);
@@ -295,7 +418,10 @@ int elite_slices(int N, int D, int nu, int num_sms)
         cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess &&
         cudaFuncGetAttributes(&fa, k_sample_elites) == cudaSuccess) {
         per_sm = (int)((size_t)sm_smem / (smem + fa.sharedSizeBytes + (size_t)reserved));
-        per_sm = std::min(per_sm, sm_threads / kTcThreads);
+        per_sm = std::min(per_sm, sm_threads / (kTcThreads + 32));
+        const int warps = (kTcThreads + 32) / 32;   // registers: allocated per warp in units of 256
+        const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+        if (regs_per_warp > 0) per_sm = std::min(per_sm, 65536 / (regs_per_warp * warps));
         per_sm = std::min(per_sm, (int)(512u / tmem_columns(Dp)));
         if (per_sm < 1) per_sm = 1;
     } else {
@@ -309,18 +435,38 @@ int elite_slices(int N, int D, int nu, int num_sms)
     return s < 1 ? 1 : s;
 }
 
-int launch_elite_weights(const double *w, int nu, double sigma, double *sw, cudaStream_t st)
+int launch_elite_weights(const double *w, int nu, double sigma, float *sw, cudaStream_t st)
 {
     k_elite_weights<<<(nu + 255) / 256, 256, 0, st>>>(w, nu, sigma, sw);
     CP_LAUNCHED("k_elite_weights");
     return CP_OK;
 }
 
-int launch_elite_mean(const float *elites, const double *w, const double *sw, int nu, int D, double *mu, float *mu_f,
-                      float *Yp, cudaStream_t st)
+// Blocks of k_elite_update: one per chunk of 16 elites, at most one per two SMs (fewer
+// partials to add after the barrier), so that all are resident at once.
+int elite_update_blocks(int nu, int num_sms)
 {
-    k_elite_mean<<<D, 256, 0, st>>>(elites, w, sw, nu, D, mu, mu_f, Yp);
-    CP_LAUNCHED("k_elite_mean");
+    const int chunks = (nu + kChunkE - 1) / kChunkE;
+    const int cap = num_sms / 2 > 0 ? num_sms / 2 : 1;
+    return chunks < cap ? chunks : cap;
+}
+
+int launch_elite_update(const float *elites, const double *w, const float *sw, int nu, int D, int blocks,
+                        double *part, unsigned int *bar, double *mu, float *mu_f, float *mu_lo, float *Yp,
+                        uint32_t *status, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kEUThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CP_CUDA(cudaLaunchKernelEx(&cfg, k_elite_update, elites, w, sw, nu, D, part, bar, mu, mu_f, mu_lo, Yp, status));
+    CP_LAUNCHED("k_elite_update");
     return CP_OK;
 }
 
@@ -333,7 +479,7 @@ int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int n
     if (slices > chunks) slices = chunks;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     dim3 grid((N + kTcM - 1) / kTcM, slices);
-    k_sample_elites<<<grid, kTcThreads, tc_smem_bytes(Dp), st>>>(Yp, N, D, chunks, slices, tmem_columns(Dp), k0,
+    k_sample_elites<<<grid, kTcThreads + 32, tc_smem_bytes(Dp), st>>>(Yp, N, D, chunks, slices, tmem_columns(Dp), k0,
                                                                   k1, iter, query, P, status);
     CP_LAUNCHED("k_sample_elites");
     const int64_t total = (int64_t)N * (D / 4);

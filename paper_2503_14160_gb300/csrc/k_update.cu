@@ -3,7 +3,8 @@
 //   k_rank_count     rank of every candidate = number of candidates before it in the order
 //                    (J ascending, NaN as +inf, ties by index): an all-pairs count, split
 //                    over the grid's y dimension and summed with integer atomics
-//   k_scatter        elite list in rank order, the elite rows gathered contiguously
+//   k_scatter        elite list in rank order, the elite rows gathered contiguously; the
+//                    rank counters are cleared for the next ranking
 //   k_radix_*        for large N instead: a stable LSD radix sort of the keys (8 x 8 bits)
 //   k_moments_partial / k_moments_combine   mu = sum_j w_j xi_(j) and
 //                    C = sum_j w_j (xi_(j) - mu)(xi_(j) - mu)^T + eps I (about the new
@@ -17,7 +18,7 @@ namespace {
 constexpr int kChunk = 32;          // elites staged at a time
 constexpr int kMaxChunks = 512;     // bound on the partial buffers
 constexpr int kRankThreads = 256;
-constexpr int kRankSplit = 256;     // j-range per grid row of k_rank_count
+constexpr int kRankPer = 128;       // j-range per grid row of k_rank_count
 
 // Order-preserving map of a double to uint64 (NaN -> +inf, -0 -> +0).
 __device__ __forceinline__ unsigned long long order_key(double v)
@@ -44,32 +45,33 @@ __global__ void k_weights(int nu, double *w)
     for (int j = threadIdx.x; j < nu; j += blockDim.x) w[j] = (top - log((double)(j + 1))) / total;
 }
 
+// Block (x, y): candidates i of block x against the candidates j of the y-th range of
+// kRankPer. Candidate j precedes i when k_j < k_i, or k_j == k_i and j < i; for j < i that
+// is k_j < k_i + 1 (the key of a real cost stays below 2^64 - 1), for j >= i k_j < k_i, so
+// each comparison is one 64-bit compare against a threshold that changes once per range.
 __global__ void __launch_bounds__(kRankThreads)
 k_rank_count(const double *__restrict__ J, int N, int *rank)
 {
-    __shared__ unsigned long long s_key[kRankThreads];
+    __shared__ unsigned long long s_key[kRankPer];
     const int i = blockIdx.x * kRankThreads + threadIdx.x;
-    const unsigned long long ki = i < N ? order_key(J[i]) : ~0ull;
-    const int j_begin = blockIdx.y * kRankSplit;
-    const int j_end = min(N, j_begin + kRankSplit);
+    const unsigned long long ki = i < N ? order_key(J[i]) : 0ull;
+    const int j0 = blockIdx.y * kRankPer;
+    const int len = min(kRankPer, N - j0);
+    for (int t = threadIdx.x; t < len; t += kRankThreads) s_key[t] = order_key(J[j0 + t]);
+    __syncthreads();
+    const int split = min(max(i - j0, 0), len);   // j0 + split: the first j >= i
+    const unsigned long long ki1 = ki + 1;
     int cnt = 0;
-    for (int base = j_begin; base < j_end; base += kRankThreads) {
-        __syncthreads();
-        const int j = base + threadIdx.x;
-        s_key[threadIdx.x] = j < j_end ? order_key(J[j]) : ~0ull;
-        __syncthreads();
-        const int lim = min(kRankThreads, j_end - base);
-        for (int t = 0; t < lim; ++t) {
-            const unsigned long long kj = s_key[t];
-            cnt += (kj < ki) || (kj == ki && base + t < i);
-        }
-    }
+    for (int t = 0; t < split; ++t) cnt += s_key[t] < ki1;
+#pragma unroll 4
+    for (int t = split; t < len; ++t) cnt += s_key[t] < ki;
     if (i < N && cnt > 0) atomicAdd(rank + i, cnt);
 }
 
 // One warp per candidate: a candidate of rank r < nu writes its index to elite[r] and its
-// row to elites[r][:]; rank 0 also records its cost.
-__global__ void k_scatter(const int *__restrict__ rank, const double *__restrict__ J,
+// row to elites[r][:]; rank 0 also records its cost. The rank counter goes back to zero for
+// the next ranking.
+__global__ void k_scatter(int *__restrict__ rank, const double *__restrict__ J,
                           const float *__restrict__ xi, int N, int nu, int D, int *elite,
                           float *elites, double *best_J)
 {
@@ -77,6 +79,8 @@ __global__ void k_scatter(const int *__restrict__ rank, const double *__restrict
     const int lane = threadIdx.x & 31;
     if (warp >= N) return;
     const int r = rank[warp];
+    __syncwarp();
+    if (lane == 0) rank[warp] = 0;
     if (r >= nu) return;
     if (lane == 0) {
         elite[r] = warp;
@@ -487,17 +491,17 @@ int launch_weights(int nu, double *w, cudaStream_t st)
     return CP_OK;
 }
 
-// rank must be zeroed by the caller; elite, elites and best_J are written.
+// rank must be zero on entry (the workspace starts cleared and k_scatter clears it again).
 int launch_rank(const double *J, int N, int nu, int *rank, cudaStream_t st)
 {
-    dim3 grid((N + kRankThreads - 1) / kRankThreads, (N + kRankSplit - 1) / kRankSplit);
+    dim3 grid((N + kRankThreads - 1) / kRankThreads, (N + kRankPer - 1) / kRankPer);
     k_rank_count<<<grid, kRankThreads, 0, st>>>(J, N, rank);
     CP_LAUNCHED("k_rank_count");
     (void)nu;
     return CP_OK;
 }
 
-int launch_scatter(const int *rank, const double *J, const float *xi, int N, int nu, int D,
+int launch_scatter(int *rank, const double *J, const float *xi, int N, int nu, int D,
                    int *elite, float *elites, double *best_J, cudaStream_t st)
 {
     const int threads = 256;

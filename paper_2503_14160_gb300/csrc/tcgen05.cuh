@@ -50,6 +50,13 @@ static __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t par
     return ok != 0;
 }
 
+// One arrival on the barrier (release: this thread's earlier shared-memory writes are
+// visible to whoever waits for the phase).
+static __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(bar)) : "memory");
+}
+
 // Waits until the phase of the given parity has completed, for at most `limit` clock
 // cycles; false when the wait ran out.
 static __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit)

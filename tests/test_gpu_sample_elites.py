@@ -3,15 +3,16 @@ oracle's sample_elites, on identical updates: the mean to FP64 rounding, the sam
 the error bound of the tensor-core product, the covariance formed on request equal to the
 paper's update, plans against the oracle's plan with the same sampler, and determinism.
 
-Bound per sample coordinate (u = 2^-24). The product sum_j g_ij Y_jd runs on the tensor
+Bound per sample coordinate (u = 2^-24). Y is formed in FP32 against the mean as an FP32
+pair, within 4 ulp (8 u) of its FP64 value. The product sum_j g_ij Y_jd runs on the tensor
 cores as G_hi Y_hi + G_hi Y_lo + G_lo Y_hi with G = G_hi + G_lo (+ a rest below 2^-22 |G|)
-and the same split of Y rounded to FP32: each product is within (12 + 1) u of g_ij Y_jd.
-The 3 nu products are accumulated in FP32 (at most one ulp, 2 u, per addition even when
-the hardware truncates) and the slices added in FP32, so the sum is within
-(13 + 6 nu + slices + 16) u sum_j |g_ij||Y_jd| in the worst case; the float Box-Muller
+and the same split of Y: each product is within (12 + 8) u of g_ij Y_jd. The 3 nu products
+are accumulated in FP32 (at most one ulp, 2 u, per addition even when the hardware
+truncates) and the slices added in FP32, so the sum is within
+(20 + 6 nu + slices + 16) u sum_j |g_ij||Y_jd| in the worst case; the float Box-Muller
 normals add a few ulp each, the result's rounding u |xi|. Typical errors are far smaller:
 independent rounding errors grow like sqrt(3 nu), and the RMS over all coordinates must
-stay within (13 + 2 sqrt(3 nu)) u of the same scale.
+stay within (20 + 2 sqrt(3 nu)) u of the same scale.
 """
 import numpy as np
 import pytest
@@ -66,12 +67,12 @@ def test_sample_matches_oracle(lib, crane, N, K, nu, it):
         z = s.oracle.normals(21, it, 2, N, (nu_ + D + 3) // 4)
         Y = np.sqrt(w)[:, None] * (X - mu_o[None, :]) * 0.8
         scale = np.abs(z[:, :nu_]) @ np.abs(Y)
-        bound = (EPS32 * np.abs(want) + (13 + 6 * nu_ + 32 + 16) * EPS32 * scale
+        bound = (EPS32 * np.abs(want) + (20 + 6 * nu_ + 32 + 16) * EPS32 * scale
                  + 8 * EPS32 * 0.8e-3 * np.abs(z[:, nu_:nu_ + D]) + 1e-30)
         err = np.abs(got - want)
         assert np.all(err <= bound), np.max(err / bound)
         rms = np.sqrt(np.mean((err / (scale + 1e-30)) ** 2))
-        assert rms <= (13 + 2 * np.sqrt(3 * nu_)) * EPS32, rms / EPS32
+        assert rms <= (20 + 2 * np.sqrt(3 * nu_)) * EPS32, rms / EPS32
     finally:
         s.close()
 
