@@ -127,8 +127,10 @@ typedef struct cp_params {
     int32_t eval_ctas_per_sm; /* launch shape of the evaluation kernel: CTAs per SM of its
                                  persistent grid (0: as many as fit) */
     int32_t debug_withhold_staging; /* test hook, 0 in use: 1 makes the brute-force
-                                 evaluation issue no shared-memory staging copy, so that its
-                                 bounded wait runs out and CP_ERR_TIMEOUT is reported */
+                                 evaluation issue no shared-memory staging copy, 2 makes the
+                                 tensor-core elite sampler issue no copy of its operand
+                                 chunks, so that the bounded wait runs out and
+                                 CP_ERR_TIMEOUT is reported */
     int32_t eval_exhaustive; /* 1: test every sphere against every obstacle; 0 (default): a
                                 broad phase first drops, per 32 checkpoints of a candidate,
                                 the obstacles out of reach of all their spheres. Both give

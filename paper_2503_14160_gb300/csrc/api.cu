@@ -300,6 +300,8 @@ int validate_params(const cp_params *p)
         return set_error("n_waypoints %d outside 1..%d", p->n_waypoints, CP_MAX_WAYPOINTS), CP_ERR_ARG;
     if (p->substeps < 1 || p->substeps > 4096)
         return set_error("substeps %d outside 1..4096", p->substeps), CP_ERR_ARG;
+    if (p->debug_withhold_staging < 0 || p->debug_withhold_staging > 2)
+        return set_error("debug_withhold_staging %d outside 0..2", p->debug_withhold_staging), CP_ERR_ARG;
     if (p->n_elites < 0 || p->n_elites > p->n_candidates)
         return set_error("n_elites %d outside 0..n_candidates", p->n_elites), CP_ERR_ARG;
     if (!(p->sigma > 0.0) || !is_finite(p->sigma)) return set_error("sigma must be > 0"), CP_ERR_ARG;
@@ -426,11 +428,13 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.S = p->S;
     a.n_s = p->n_s;
     a.chunks = p->chunks;
+    a.div_S = fast_div((uint32_t)p->S);
+    a.div_chunks = fast_div((uint32_t)p->chunks);
     a.q0 = p->q0f;
     a.qd = p->qdf;
     a.ends = p->ends_f;
     a.ctas_per_sm = p->prm.eval_ctas_per_sm;
-    a.withhold_staging = p->prm.debug_withhold_staging;
+    a.withhold_staging = p->prm.debug_withhold_staging == 1;
     a.broadphase = p->prm.eval_exhaustive ? 0 : 1;
     a.work = p->timer.on ? p->work : nullptr;
     if (p->timer.on) {
@@ -477,7 +481,7 @@ int run_sample(cp_planner *p, int iter, float *d_xi)
     if (p->elites_ready)
         rc = launch_sample_elites(p->elite_Y, p->mu_f, p->N, p->K, p->nu, p->elite_slices, p->prm.sigma,
                                   p->prm.eps, p->prm.seed, (uint32_t)iter, p->prm.query, p->sample_part, d_xi,
-                                  p->status, p->st);
+                                  p->status, p->prm.debug_withhold_staging == 2, p->st);
     else
         rc = launch_sample(p->mu, p->Lt, p->N, p->K, p->prm.seed, (uint32_t)iter, p->prm.query, d_xi,
                            p->st);

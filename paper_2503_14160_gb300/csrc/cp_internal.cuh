@@ -33,6 +33,36 @@ enum : uint32_t {
     DEV_ERR_NOT_PD = 2u,       // Cholesky met a non-positive pivot
 };
 
+// ------------------------------------------------------------------ division by an invariant
+
+// Unsigned division by a divisor d >= 1 fixed for a launch, as a multiply-high and shifts
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", PLDI
+// 1994, Fig. 4.1 with N = 32): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// sh1 = min(l, 1), sh2 = max(l - 1, 0); then n / d = (t + ((n - t) >> sh1)) >> sh2 with
+// t = mulhi(m, n), exact for every 32-bit n.
+struct FastDiv {
+    uint32_t m, sh1, sh2;
+};
+
+inline FastDiv fast_div(uint32_t d)
+{
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.sh1 = l < 1 ? l : 1;
+    f.sh2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+#ifdef __CUDACC__
+static __device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f)
+{
+    const uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.sh1)) >> f.sh2;
+}
+#endif
+
 // ------------------------------------------------------------------ geometry records
 
 // Sphere placement in the linear form used by the kernels:
@@ -112,6 +142,7 @@ ModelDev make_model(const cp_model *m);
 struct EvalArgs {
     const float4 *xi;           // [n][K]
     int n, K, S, n_s, chunks;   // chunks = ceil(n_s / 32)
+    FastDiv div_S, div_chunks;  // division by S and by chunks
     float4 q0, qd;              // end points, used when `ends` is null
     const float4 *ends;         // optional device copy {q0, qd}, read at run time
     int ctas_per_sm;            // persistent-grid CTAs per SM (0: as many as fit)
@@ -213,7 +244,7 @@ int launch_elite_update(const float *elites, const double *w, const float *sw, i
                         uint32_t *status, cudaStream_t st);
 int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int nu, int slices, double sigma,
                          double eps, uint64_t seed, uint32_t iter, uint32_t query, float *P, float *xi,
-                         uint32_t *status, cudaStream_t st);
+                         uint32_t *status, bool withhold, cudaStream_t st);
 int update_chunks(int nu);
 int radix_tiles(int N);
 int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,

@@ -174,6 +174,22 @@ static __device__ __forceinline__ uint32_t any_below(const float2 *g, const floa
 // An obstacle whose centre lies farther than its reach (the `w` of its record) from that
 // box cannot pass the per-sphere filter for any lane; the reach carries 1 cm of slack over
 // the filter's own bound, far above the FP32 rounding of either test.
+// Minimum and maximum of a float over the full warp in one warp-wide reduction (the
+// hardware's float min / max reduce, NaN ignored as by fminf / fmaxf).
+static __device__ __forceinline__ float warp_min(float v)
+{
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+static __device__ __forceinline__ float warp_max(float v)
+{
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 struct UnitFrame {
     float c0, s0;     // frame axes
     float uc, uh;     // box centre and half extent along the slew direction
@@ -193,15 +209,8 @@ static __device__ __forceinline__ UnitFrame unit_frame(float s1, float c1, const
         hmax = fmaxf(hmax, H[s]);
     }
     const float cd = fmaf(f.c0, c1, f.s0 * s1), sd = fmaf(f.c0, s1, -f.s0 * c1);
-    float umin = fminf(hmin * cd, hmax * cd), umax = fmaxf(hmin * cd, hmax * cd);
-    float vmin = fminf(hmin * sd, hmax * sd), vmax = fmaxf(hmin * sd, hmax * sd);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, off));
-        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, off));
-        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, off));
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
-    }
+    const float umin = warp_min(fminf(hmin * cd, hmax * cd)), umax = warp_max(fmaxf(hmin * cd, hmax * cd));
+    const float vmin = warp_min(fminf(hmin * sd, hmax * sd)), vmax = warp_max(fmaxf(hmin * sd, hmax * sd));
     f.uc = 0.5f * (umin + umax);
     f.uh = 0.5f * (umax - umin);
     f.vc = 0.5f * (vmin + vmax);
@@ -257,7 +266,7 @@ static __device__ __forceinline__ Checkpoint checkpoint_setup(const ModelDev &m,
     c.k = chunk * 32 + lane + 1;
     c.valid = c.k <= a.n_s;
     const int kc = c.valid ? c.k : a.n_s;
-    const int span = (kc - 1) / a.S;              // moving span - 1, 0..K+2
+    const int span = (int)fdiv((uint32_t)(kc - 1), a.div_S);   // moving span - 1, 0..K+2
     const int mstep = kc - span * a.S;            // 1..S within the span
     // control points P_{span+1..span+4} of [q0 x4, xi (K), qd x4]
     const float4 *xi = a.xi + (size_t)cand * a.K;

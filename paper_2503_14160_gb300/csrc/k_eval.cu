@@ -164,7 +164,7 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
     const float zero[NSPH] = {};
 
     for (int u = warp; u < units; u += n_warps) {
-        const int cand = u / a.chunks;
+        const int cand = (int)fdiv((uint32_t)u, a.div_chunks);
         const int chunk = u - cand * a.chunks;
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
         float H[NSPH], Z[NSPH], s1, c1;
@@ -258,7 +258,7 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
     const int units = a.n * a.chunks;
 
     for (int u = warp; u < units; u += n_warps) {
-        const int cand = u / a.chunks;
+        const int cand = (int)fdiv((uint32_t)u, a.div_chunks);
         const int chunk = u - cand * a.chunks;
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
 

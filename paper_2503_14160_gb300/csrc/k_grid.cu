@@ -155,7 +155,7 @@ k_eval_grid(const ModelDev m, const SceneDev sc, const GridDev g, const EvalArgs
     const int units = a.n * a.chunks;
     uint32_t tested = 0;   // cell entries this lane visited
     for (int u = warp; u < units; u += n_warps) {
-        const int cand = u / a.chunks;
+        const int cand = (int)fdiv((uint32_t)u, a.div_chunks);
         const int chunk = u - cand * a.chunks;
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
         float H[NSPH], Z[NSPH], s1, c1;

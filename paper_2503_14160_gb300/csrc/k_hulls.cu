@@ -356,7 +356,7 @@ k_eval_hulls(const ModelDev m, const SceneDev sc, const HullDims hd, const EvalA
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     for (int u = warp; u < a.n * a.chunks; u += n_warps) {
-        const int cand = u / a.chunks, chunk = u - cand * a.chunks;
+        const int cand = (int)fdiv((uint32_t)u, a.div_chunks), chunk = u - cand * a.chunks;
         const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
         const float pen = hull_pen_warp<true>(m, sc, hd, c.q, true, s_box[wib], s_pen[wib], s_queue[wib], lane);
         __syncwarp();

@@ -118,6 +118,8 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     a.S = S;
     a.n_s = n_s;
     a.chunks = chunks;
+    a.div_S = fast_div((uint32_t)S);
+    a.div_chunks = fast_div((uint32_t)chunks);
     a.q0 = make_float4((float)h_q0[0], (float)h_q0[1], (float)h_q0[2], (float)h_q0[3]);
     a.qd = make_float4((float)h_qd[0], (float)h_qd[1], (float)h_qd[2], (float)h_qd[3]);
     a.broadphase = 1;

@@ -216,10 +216,11 @@ k_elite_update(const float *__restrict__ elites, const double *__restrict__ w, c
 //    waits for a_full and b_full, issues the stage's 6 MMAs of 128 x Dp x 8 and commits
 //    them to done.
 // Every wait is bounded: when one runs out the CTA records DEV_ERR_TIMEOUT, goes on
-// (results are then meaningless) and still releases its tensor memory.
+// (results are then meaningless) and still releases its tensor memory. `withhold` issues
+// no operand copy, so that the wait for it runs out on purpose (the test of this path).
 __global__ void __launch_bounds__(kTcThreads + 32)
 k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int slices, uint32_t tmem_cols,
-                uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *P, uint32_t *status)
+                uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *P, uint32_t *status, int withhold)
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t a_full[kStages], b_full[kStages], done[kStages];
@@ -251,7 +252,7 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
     if (warp == kTcThreads / 32) {
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_tf32(kTcM, Dp);
-            for (int it = 0; it < kStages && it < n; ++it) {
+            for (int it = 0; it < kStages && it < n && !withhold; ++it) {
                 float *b_hi = smem + it * stage_floats + 2 * a_floats;
                 tc::mbar_expect_tx(&b_full[it], b_bytes);
                 tc::bulk_g2s(b_hi, Yp + (size_t)(c_begin + it) * b_floats, b_bytes, &b_full[it]);
@@ -278,7 +279,7 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
                 tc::mma_commit(&done[s]);
                 // the chunk two stages on goes where the previous stage's MMAs read
                 const int nx = it + 1, sx = nx % kStages;
-                if (it >= 1 && nx < n) {
+                if (it >= 1 && nx < n && !withhold) {
                     if (!tc::mbar_wait(&done[sx], ((nx - kStages) / kStages) & 1, kWaitCycles)) late = true;
                     float *bx = smem + sx * stage_floats + 2 * a_floats;
                     tc::mbar_expect_tx(&b_full[sx], b_bytes);
@@ -472,7 +473,7 @@ int launch_elite_update(const float *elites, const double *w, const float *sw, i
 
 int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int nu, int slices, double sigma,
                          double eps, uint64_t seed, uint32_t iter, uint32_t query, float *P, float *xi,
-                         uint32_t *status, cudaStream_t st)
+                         uint32_t *status, bool withhold, cudaStream_t st)
 {
     const int D = 4 * K, Dp = padded_d(D);
     const int chunks = (nu + kChunkE - 1) / kChunkE;
@@ -480,7 +481,7 @@ int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int n
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     dim3 grid((N + kTcM - 1) / kTcM, slices);
     k_sample_elites<<<grid, kTcThreads + 32, tc_smem_bytes(Dp), st>>>(Yp, N, D, chunks, slices, tmem_columns(Dp), k0,
-                                                                  k1, iter, query, P, status);
+                                                                  k1, iter, query, P, status, withhold ? 1 : 0);
     CP_LAUNCHED("k_sample_elites");
     const int64_t total = (int64_t)N * (D / 4);
     k_sample_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, slices, mu_f, N, D, nu,

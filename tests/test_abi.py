@@ -77,6 +77,7 @@ def _crane():
     (lambda m, p: setattr(p, "sigma", 0.0), "sigma"),
     (lambda m, p: setattr(p, "eps", -1.0), "eps"),
     (lambda m, p: setattr(p, "w_c", float("nan")), "weights"),
+    (lambda m, p: setattr(p, "debug_withhold_staging", 3), "debug_withhold_staging"),
 ])
 def test_init_rejects_bad_arguments(cp, mutate, needle):
     from paper_2503_14160_gb300 import workloads

@@ -178,3 +178,47 @@ def test_unaligned_candidates_are_rejected(lib, crane):
         lib.cp_synchronize(pl.handle)
     finally:
         pl.close()
+
+
+def test_operand_wait_runs_out_and_is_reported(lib, crane):
+    """With the operand copy withheld (test hook 2) the MMA warp's bounded wait for it runs
+    out: the launch still finishes and releases its tensor memory, CP_ERR_TIMEOUT is
+    reported at the next synchronisation, and the device keeps working."""
+    import time
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    N, K = 64, 2
+    bad = lib.Planner(crane, workloads.empty_scene(),
+                      lib.make_params(N, K, 2, sampler=lib.CP_SAMPLE_ELITES, debug_withhold_staging=2))
+    try:
+        g = np.random.default_rng(5)
+        xi = torch.from_numpy((g.normal(size=(N, K, 4)) * 0.3).astype(np.float32)).cuda()
+        J = torch.from_numpy(g.random(N)).cuda()
+        lib.cp_set_endpoints(bad.handle, np.zeros(4), np.ones(4))
+        lib.cp_update(bad.handle, J, xi)
+        lib.cp_synchronize(bad.handle)
+        out = torch.zeros(N, K, 4, device="cuda")
+        t0 = time.perf_counter()
+        lib.cp_sample(bad.handle, 1, out)
+        with pytest.raises(lib.CranePlanError) as e:
+            lib.cp_synchronize(bad.handle)
+        assert e.value.status == -3
+        assert time.perf_counter() - t0 < 30.0
+        lib.cp_synchronize(bad.handle)          # the report is cleared once read
+    finally:
+        bad.close()
+    s = Setup(crane, workloads.empty_scene(), N=N, K=K, S=2, seed=21, sigma=0.8, eps=1e-6)
+    s.planner.close()
+    s.planner = lib.Planner(crane, workloads.empty_scene(),
+                            lib.make_params(N, K, 2, seed=21, sigma=0.8, eps=1e-6, sampler=lib.CP_SAMPLE_ELITES))
+    try:                                         # the device keeps working: a clean draw
+        lib.cp_set_endpoints(s.h, np.zeros(4), np.ones(4))
+        g = np.random.default_rng(6)
+        xi = torch.from_numpy((g.normal(size=(N, K, 4)) * 0.3).astype(np.float32)).cuda()
+        lib.cp_update(s.h, torch.from_numpy(g.random(N)).cuda(), xi)
+        out = torch.zeros(N, K, 4, device="cuda")
+        lib.cp_sample(s.h, 1, out)
+        lib.cp_synchronize(s.h)
+        assert torch.isfinite(out).all()
+    finally:
+        s.close()
