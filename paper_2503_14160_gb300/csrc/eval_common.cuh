@@ -289,27 +289,30 @@ static __device__ __forceinline__ Checkpoint checkpoint_setup(const ModelDev &m,
     return c;
 }
 
-// Warp-shuffle sums (FP32) of the unit's lanes and the ballot of collision flags, written
-// by lane 0 ([candidate][chunk]); the per-checkpoint penalty goes to pen_out when asked.
+// FP32 sums of the unit's lanes of four values and the ballot of collision flags, written
+// ([candidate][chunk]); the per-checkpoint penalty goes to pen_out when asked. The four
+// sums share one transposing butterfly: across lanes 16 apart each lane keeps two of the
+// values and hands the other two to its partner, across lanes 8 apart one of the two, and
+// three more steps finish the sum of that one value, so lane 8 k ends with the sum of
+// value k (6 shuffles instead of 20).
 static __device__ __forceinline__ void unit_epilogue(const EvalArgs &a, const Checkpoint &c, float dmin,
                                                      int cand, int chunk, int lane)
 {
     const float pen = fmaxf(0.f, -dmin);
     const bool hit = c.valid && (dmin < 0.f);
-    float v0 = c.valid ? c.jp : 0.f, v1 = c.valid ? pen : 0.f;
-    float v2 = c.valid ? c.jl : 0.f, v3 = c.valid ? c.len : 0.f;
+    const float v0 = c.valid ? c.jp : 0.f, v1 = c.valid ? pen : 0.f;
+    const float v2 = c.valid ? c.jl : 0.f, v3 = c.valid ? c.len : 0.f;
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    const float r0 = __shfl_xor_sync(0xffffffffu, hi16 ? v0 : v2, 16);
+    const float r1 = __shfl_xor_sync(0xffffffffu, hi16 ? v1 : v3, 16);
+    const float w0 = (hi16 ? v2 : v0) + r0, w1 = (hi16 ? v3 : v1) + r1;   // values 2 hi16, 2 hi16 + 1
+    float x = (hi8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, hi8 ? w0 : w1, 8);   // value 2 hi16 + hi8
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, off);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-        v3 += __shfl_xor_sync(0xffffffffu, v3, off);
-    }
+    for (int off = 4; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
     const uint32_t word = __ballot_sync(0xffffffffu, hit);
-    if (lane == 0) {   // candidate-major: the finalize warp of a candidate reads its row
-        a.partial[(size_t)cand * a.chunks + chunk] = make_float4(v0, v1, v2, v3);
-        a.flagword[(size_t)cand * a.chunks + chunk] = word;
-    }
+    const size_t slot = (size_t)cand * a.chunks + chunk;   // candidate-major: the finalize reads rows
+    if ((lane & 7) == 0) reinterpret_cast<float *>(a.partial + slot)[lane >> 3] = x;
+    if (lane == 0) a.flagword[slot] = word;
     if (a.pen_out != nullptr && c.valid) a.pen_out[(size_t)cand * a.n_s + (c.k - 1)] = pen;
 }
 
