@@ -17,8 +17,9 @@
 //                    eight warps generate the normals of 16 elites per pipeline stage
 //                    (Philox blocks in place, split G = G_hi + G_lo) into shared memory
 //                    while a ninth warp feeds the tensor cores the previous stage; the
-//                    accumulator lives in tensor memory. G Y is formed as G_hi Y_hi + G_hi Y_lo + G_lo Y_hi ("3xTF32":
-//                    each product within 3 * 2^-22 of the FP32 product, FP32 accumulation)
+//                    accumulator lives in tensor memory. G Y is formed as
+//                    G_hi Y_hi + G_hi Y_lo + G_lo Y_hi ("3xTF32": each product within
+//                    3 * 2^-22 of the FP32 product, FP32 accumulation)
 //   k_sample_reduce  xi = mu + sum of the slices (fixed order) + sigma sqrt(eps) g'
 // Normals: candidate i at iteration t has the stream of Philox blocks (b, i, t, query), four
 // standard normals per block (Box-Muller on words 0-1 and 2-3); g_ij is normal j, g'_id
@@ -34,7 +35,7 @@ namespace {
 
 constexpr int kTcM = 128;          // candidates per CTA: the MMA's M, one tensor-memory lane each
 constexpr int kChunkE = 16;        // elites per pipeline stage: two MMA K steps of 8
-constexpr int kTcThreads = 256;    // two threads per candidate row
+constexpr int kTcThreads = 256;    // generator threads, two per candidate row (+ one MMA warp)
 constexpr int kStages = 2;
 constexpr long long kWaitCycles = 2000000000ll;   // about one second at 2 GHz
 
