@@ -221,7 +221,7 @@ k_elite_update(const float *__restrict__ elites, const double *__restrict__ w, c
 // no operand copy, so that the wait for it runs out on purpose (the test of this path).
 __global__ void __launch_bounds__(kTcThreads + 32)
 k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int slices, uint32_t tmem_cols,
-                uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *P, uint32_t *status, int withhold)
+                const PhiloxKeys key, uint32_t iter, uint32_t query, float *P, uint32_t *status, int withhold)
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t a_full[kStages], b_full[kStages], done[kStages];
@@ -303,7 +303,7 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
                 float z[4] = {0.f, 0.f, 0.f, 0.f};
                 if (row_ok) {
                     const uint4 x = philox4x32_10(
-                        make_uint4((uint32_t)(c * (kChunkE / 4) + blk), (uint32_t)(m0 + r), iter, query), k0, k1);
+                        make_uint4((uint32_t)(c * (kChunkE / 4) + blk), (uint32_t)(m0 + r), iter, query), key);
                     box_muller(x.x, x.y, z[0], z[1]);
                     box_muller(x.z, x.w, z[2], z[3]);
                 }
@@ -355,7 +355,7 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
 // coordinates per thread: their normals nu + d .. nu + d + 3 come from one Philox block, or
 // two when nu is not a multiple of four.
 __global__ void k_sample_reduce(const float *__restrict__ P, int slices, const float *__restrict__ mu_f, int N,
-                                int D, int nu, float eps_scale, uint32_t k0, uint32_t k1, uint32_t iter,
+                                int D, int nu, float eps_scale, const PhiloxKeys key, uint32_t iter,
                                 uint32_t query, float *xi)
 {
     const int D4 = D >> 2;
@@ -372,11 +372,11 @@ __global__ void k_sample_reduce(const float *__restrict__ P, int slices, const f
     }
     const uint32_t j0 = (uint32_t)(nu + d), b0 = j0 >> 2, sh = j0 & 3u;
     float g[8];
-    uint4 x = philox4x32_10(make_uint4(b0, (uint32_t)i, iter, query), k0, k1);
+    uint4 x = philox4x32_10(make_uint4(b0, (uint32_t)i, iter, query), key);
     box_muller(x.x, x.y, g[0], g[1]);
     box_muller(x.z, x.w, g[2], g[3]);
     if (sh != 0) {
-        x = philox4x32_10(make_uint4(b0 + 1, (uint32_t)i, iter, query), k0, k1);
+        x = philox4x32_10(make_uint4(b0 + 1, (uint32_t)i, iter, query), key);
         box_muller(x.x, x.y, g[4], g[5]);
         box_muller(x.z, x.w, g[6], g[7]);
     }
@@ -479,14 +479,14 @@ int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int n
     const int D = 4 * K, Dp = padded_d(D);
     const int chunks = (nu + kChunkE - 1) / kChunkE;
     if (slices > chunks) slices = chunks;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const PhiloxKeys key = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));
     dim3 grid((N + kTcM - 1) / kTcM, slices);
-    k_sample_elites<<<grid, kTcThreads + 32, tc_smem_bytes(Dp), st>>>(Yp, N, D, chunks, slices, tmem_columns(Dp), k0,
-                                                                  k1, iter, query, P, status, withhold ? 1 : 0);
+    k_sample_elites<<<grid, kTcThreads + 32, tc_smem_bytes(Dp), st>>>(Yp, N, D, chunks, slices, tmem_columns(Dp), key,
+                                                                  iter, query, P, status, withhold ? 1 : 0);
     CP_LAUNCHED("k_sample_elites");
     const int64_t total = (int64_t)N * (D / 4);
     k_sample_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, slices, mu_f, N, D, nu,
-                                                                     (float)(sigma * sqrt(eps)), k0, k1, iter,
+                                                                     (float)(sigma * sqrt(eps)), key, iter,
                                                                      query, xi);
     CP_LAUNCHED("k_sample_reduce");
     return CP_OK;
