@@ -38,6 +38,9 @@ constexpr int kChunkE = 16;        // elites per pipeline stage: two MMA K steps
 constexpr int kTcThreads = 256;    // generator threads, two per candidate row (+ one MMA warp)
 constexpr int kStages = 2;
 constexpr long long kWaitCycles = 2000000000ll;   // about one second at 2 GHz
+#ifndef CP_ELITE_MAX_SLICES
+#define CP_ELITE_MAX_SLICES 32   // elite slices of the tensor-core product (partials to add)
+#endif
 
 // D padded to the MMA's N granularity (16 for M = 128).
 __host__ __device__ inline int padded_d(int D) { return (D + 15) & ~15; }
@@ -433,7 +436,7 @@ int elite_slices(int N, int D, int nu, int num_sms)
     const int chunks = (nu + kChunkE - 1) / kChunkE;
     int s = per_sm * num_sms / tiles;
     if (s > chunks) s = chunks;
-    if (s > 32) s = 32;
+    if (s > CP_ELITE_MAX_SLICES) s = CP_ELITE_MAX_SLICES;
     return s < 1 ? 1 : s;
 }
 
