@@ -154,9 +154,12 @@ typedef struct cp_params {
                                CP_UPDATE_PAPER only, draws the same N(mu, sigma^2 C) from the
                                last update's elites without forming C or its factor:
                                xi = mu + sigma (sum_j sqrt(w_j)(x_(j) - mu) g_j + sqrt(eps) g').
-                               The first sample after cp_set_endpoints or
-                               cp_set_distribution uses the factor. C and L are formed only
-                               when cp_get_distribution or cp_get_factor asks for them. */
+                               The product of the N x nu normals g and the scaled elite
+                               deviations runs on the tensor cores in TF32 with a hi/lo split of
+                               both operands (FP32 accuracy; FP32 accumulation). The first
+                               sample after cp_set_endpoints or cp_set_distribution uses the
+                               factor. C and L are formed only when cp_get_distribution or
+                               cp_get_factor asks for them. */
 } cp_params;
 
 #define CP_UPDATE_PAPER 0
