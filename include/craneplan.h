@@ -209,6 +209,11 @@ int32_t cp_version(void);
  * batch graph counts the kernels recorded in it. */
 int64_t cp_launch_count(void);
 
+/* Test hook: the next n planner workspace allocations (cp_plan_init's one device
+ * allocation) fail as if the device were out of memory, so that cp_plan_init returns
+ * CP_ERR_OOM after releasing what it holds. n = 0 turns it off; no other effect. */
+void cp_debug_fail_allocations(int32_t n);
+
 /* Create a planner on the current CUDA device: validates the model, scene and parameters,
  * allocates the device workspace for N candidates, stages the scene (host -> device) and
  * tabulates the spline basis. End points must be set with cp_set_endpoints before

@@ -122,6 +122,7 @@ _SIGS = {
     "cp_last_error": (ctypes.c_char_p, []),
     "cp_version": (ctypes.c_int32, []),
     "cp_launch_count": (ctypes.c_int64, []),
+    "cp_debug_fail_allocations": (None, [ctypes.c_int32]),
     "cp_plan_init": (ctypes.c_int, [ctypes.POINTER(cp_model), ctypes.POINTER(cp_scene),
                                     ctypes.POINTER(cp_params), _P, ctypes.POINTER(_P)]),
     "cp_destroy": (None, [_P]),
@@ -283,6 +284,10 @@ def cp_version() -> int:
 
 def cp_launch_count() -> int:
     return int(load().cp_launch_count())
+
+
+def cp_debug_fail_allocations(n: int) -> None:
+    load().cp_debug_fail_allocations(int(n))
 
 
 def cp_plan_init(model: cp_model, scene: HostScene, params: cp_params, stream=None) -> int:

@@ -18,6 +18,7 @@ namespace cp {
 namespace {
 thread_local char g_err[512] = "";
 std::atomic<int64_t> g_launches{0};
+std::atomic<int32_t> g_fail_allocs{0};   // test hook: workspace allocations still to fail
 }  // namespace
 
 void set_error(const char *fmt, ...)
@@ -572,6 +573,8 @@ int32_t cp_version(void) { return CP_VERSION; }
 
 int64_t cp_launch_count(void) { return g_launches.load(); }
 
+void cp_debug_fail_allocations(int32_t n) { g_fail_allocs.store(n > 0 ? n : 0); }
+
 int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *params,
                  void *stream, cp_planner **out)
 {
@@ -715,7 +718,10 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_rva = L.take<int>(radix ? N : 1);
     const size_t o_rvb = L.take<int>(radix ? N : 1);
     const size_t o_rh = L.take<int>(radix ? 256 * (size_t)radix_tiles(p->N) : 1);
-    e = cudaMalloc((void **)&p->base, L.bytes);
+    int32_t left = g_fail_allocs.load();
+    while (left > 0 && !g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+    }
+    e = left > 0 ? cudaErrorMemoryAllocation : cudaMalloc((void **)&p->base, L.bytes);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(workspace)"));
     char *b = p->base;
     p->cyl_in = (cp_cylinder *)(b + o_cyl_in);

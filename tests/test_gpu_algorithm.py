@@ -306,3 +306,22 @@ def test_plan_graph_equals_stream_launches(lib, crane):
     finally:
         ref.close()
         g.close()
+
+
+def test_workspace_allocation_failure_is_reported(lib, crane):
+    """An out-of-memory workspace allocation (forced by the test hook) makes cp_plan_init
+    return CP_ERR_OOM after releasing what it holds; the next planner is created as usual."""
+    from paper_2503_14160_gb300 import workloads
+    lib.cp_debug_fail_allocations(1)
+    try:
+        with pytest.raises(lib.CranePlanError) as e:
+            lib.Planner(crane, workloads.empty_scene(), lib.make_params(64, 2, 2))
+        assert e.value.status == -5
+    finally:
+        lib.cp_debug_fail_allocations(0)
+    pl = lib.Planner(crane, workloads.empty_scene(), lib.make_params(64, 2, 2))
+    try:
+        lib.cp_set_endpoints(pl.handle, np.zeros(4), np.ones(4))
+        lib.cp_synchronize(pl.handle)
+    finally:
+        pl.close()
