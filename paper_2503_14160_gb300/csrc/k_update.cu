@@ -184,7 +184,7 @@ __global__ void k_moments_combine(const double *__restrict__ s2p, const double *
 // Stable ascending sort of (key, index) by the order-preserving 64-bit keys: eight passes of
 // 8-bit digits; tiles of kRadixTile consecutive elements; per pass a tile histogram, an
 // exclusive scan in (digit, tile) order, and a stable scatter (ranks inside a warp from
-// __match_any_sync, across warps and rounds from per-digit prefixes).
+// __match_any_sync, across warps and passes from per-digit prefixes).
 constexpr int kRadixTile = 1024;
 constexpr int kRadixThreads = 256;
 
@@ -240,8 +240,8 @@ k_radix_scatter(const unsigned long long *__restrict__ key_in, const int *__rest
                 int shift, int tiles, const int *__restrict__ offsets, unsigned long long *key_out,
                 int *val_out)
 {
-    __shared__ int run[256];            // elements of each digit placed by earlier rounds
-    __shared__ int wcount[8][256];      // per-warp digit counts of the current round
+    __shared__ int run[256];            // elements of each digit placed by earlier passes
+    __shared__ int wcount[8][256];      // per-warp digit counts of the current pass
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     run[threadIdx.x] = offsets[threadIdx.x * tiles + blockIdx.x];
     const int b = blockIdx.x * kRadixTile, e = min(N, b + kRadixTile);
@@ -262,7 +262,7 @@ k_radix_scatter(const unsigned long long *__restrict__ key_in, const int *__rest
         const int in_warp = __popc(peers & lt);
         if (valid && in_warp == 0) wcount[warp][d] = __popc(peers);
         __syncthreads();
-        int before = 0;                 // same digit in earlier warps of this round
+        int before = 0;                 // same digit in earlier warps of this pass
         if (valid)
             for (int w = 0; w < warp; ++w) before += wcount[w][d];
         if (valid) {
