@@ -2,8 +2,11 @@
 
 A step is one whole plan: the T iterations of Algorithm 1 (sample, evaluate, rank,
 update; arXiv 2503.14160 Sec. 4.1) for one query, then the evaluation of the mean path.
-Workload: the single large query (N = 4096 candidates, K = 16 waypoints, S = 64 checkpoints
-per span, 500 trees in a 2-10 m annulus, 100 iterations), synthetic and seeded.
+Default workload: the dense forest (N = 65536 candidates, K = 32 waypoints, S = 128
+checkpoints per span, 5000 trees at >= 0.8 m spacing in a 2-50 m annulus plus 50 boxes,
+through a 0.5 m obstacle grid, 200 iterations), synthetic and seeded; --workload
+single_large runs the single large query (N = 4096, K = 16, S = 64, 500 trees, 100
+iterations).
 
 Metric: candidate paths evaluated per second = N * T / (time per plan), plus ms per plan.
   value  device time of the plan on the planner's stream (CUDA events), inputs resident
@@ -32,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "candidate paths evaluated/sec & ms per plan on 1 GB300 vs FP64 CPU oracle"
 UNIT = "candidate paths/s"
-WORKLOAD = "single_large"
+WORKLOAD = "dense_forest"
 PEAK_SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FLOPS_PER_PAIR = 5          # 2 sub, 1 mul, 1 fma per sphere-obstacle pair
@@ -162,41 +165,43 @@ def steps_for_clocks(steps, run_once, min_seconds=1.0):
     return max(steps, int(math.ceil(min_seconds / max(dt, 1e-6))))
 
 
-EVAL_SOURCES = [os.path.join(ROOT, "paper_2503_14160_gb300", "csrc", f)
-                for f in ("k_eval.cu", "eval_common.cuh", "cp_internal.cuh")]
-EVAL_PROFILE = os.path.join(ROOT, "profiles", "k_eval_broad_single_large.md")
+KERNEL_SOURCES = {
+    "k_eval_broad": ("k_eval.cu", "eval_common.cuh", "cp_internal.cuh"),
+    "k_eval_grid": ("k_grid.cu", "eval_common.cuh", "cp_internal.cuh"),
+}
+
+# DRAM bytes (read + write) per launch of an evaluation kernel from one ncu capture of the
+# workload's launch (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the SHA-1 of the
+# kernel's sources at the time of the capture: reported only while the sources still hash
+# to it, None once the kernel has changed.
+PROFILED_TRAFFIC = {
+    "k_eval_broad": {"sha1": "ad26a635ca0cb88579d455974d6ff7926d689a2f", "bytes": 1113344.0,
+                     "workload": "single_large"},
+}
 
 
-def eval_source_sha1():
-    """SHA-1 over the sources of the evaluation kernel (the key of its committed profile):
-    k_eval.cu and eval_common.cuh whole, and cp_internal.cuh up to its first launcher
-    declaration (the device records the kernel reads; the host-side declarations after it
-    do not change the kernel)."""
+def kernel_source_sha1(kernel):
+    """SHA-1 over the sources of an evaluation kernel: its .cu file and eval_common.cuh whole,
+    and cp_internal.cuh up to its first launcher declaration (the device records the kernel
+    reads; the host-side declarations after it do not change the kernel)."""
     import hashlib
     h = hashlib.sha1()
-    for path in EVAL_SOURCES:
-        with open(path, "rb") as f:
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2503_14160_gb300", "csrc", name), "rb") as f:
             data = f.read()
-        if path.endswith("cp_internal.cuh"):
+        if name == "cp_internal.cuh":
             data = data[:data.index(b"int launch_eval(")]
         h.update(data)
     return h.hexdigest()
 
 
-def traffic_per_launch():
-    """DRAM bytes (read + write) per launch of the evaluation kernel from the committed ncu
-    summary, or None when that summary was taken from a different kernel source."""
-    try:
-        text = open(EVAL_PROFILE).read()
-    except OSError:
+def traffic_per_launch(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from its last ncu capture, or None
+    when there is none for this workload or the kernel's sources have changed since."""
+    rec = PROFILED_TRAFFIC.get(kernel)
+    if rec is None or rec["workload"] != workload or rec["sha1"] != kernel_source_sha1(kernel):
         return None
-    sha, traffic = None, None
-    for line in text.splitlines():
-        if line.startswith("source sha1:"):
-            sha = line.split(":", 1)[1].strip()
-        if line.startswith("dram bytes per launch:"):
-            traffic = float(line.split(":", 1)[1].split()[0])
-    return traffic if sha == eval_source_sha1() else None
+    return rec["bytes"]
 
 
 def select_endpoints_gpu(cp, planner, crane, seed, query):
@@ -310,8 +315,10 @@ def run_ours(args):
 
     # the same plans again with per-stage events and the work counters on (outside the
     # timed region: the stage events add a little device time of their own)
+    # (at most 3 and 5 plans: the dense forest's plans take seconds each)
     cp.cp_set_timing(h, True)
-    for _ in range(args.steps):
+    n_timing = min(args.steps, 3)
+    for _ in range(n_timing):
         flush_l2(flush)
         cp.cp_set_endpoints(h, q0, qd)
         cp.cp_plan(h, iters, K=None)
@@ -320,7 +327,7 @@ def run_ours(args):
 
     # end-to-end through the C ABI with host buffers, wall clock
     e2e_times = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 5)):
         flush_l2(flush)
         torch.cuda.synchronize()
         barrier()
@@ -340,7 +347,7 @@ def run_ours(args):
     n_s = wl.n_checkpoints
     eval_ms = timing["eval_ms"] / max(timing["eval_launches"], 1)
     clk = clocks.summary()
-    candidates = args.steps * (wl.n_candidates * iters + 1)
+    candidates = n_timing * (wl.n_candidates * iters + 1)
     roofline_exhaustive = None
     peaks_fp64 = None
     form = "grid" if wl.grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
@@ -354,7 +361,7 @@ def run_ours(args):
         roofline = eval_roofline(timing, len(crane.spheres), scene.n_cyl + scene.n_box, n_s,
                                  candidates, form, clk.get("sm_mhz"))
     if roofline is not None and roofline.get("achieved") is not None:
-        roofline["traffic"] = traffic_per_launch() if form == "broad" else None
+        roofline["traffic"] = traffic_per_launch(roofline["kernel"], wl.name)
         peaks = cp.cp_alu_peaks()
         peaks_fp64 = peaks["fp64_tflops"]
         roofline["measured_fma_peaks"] = peaks
@@ -388,7 +395,7 @@ def run_ours(args):
             "eval_kernel": {"name": "k_eval_hulls" if args.collision == "hulls" else
                             {"broad": "k_eval_broad", "exhaustive": "k_eval", "grid": "k_eval_grid"}[form],
                             "ms_per_launch": eval_ms, "launches": timing["eval_launches"]},
-            "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / args.steps
+            "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / n_timing
                                   for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},
             "fp64_stages": fp64_stages(timing, wl, peaks_fp64, sampler),
             "sampler_stage": sampler_stage(timing, wl, sampler),
@@ -396,7 +403,12 @@ def run_ours(args):
             "clocks": clk,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl, crane, scene, q0, qd, args.cpu_seconds)
+            # the CPU-baseline leg: the oracle timed on the host cores, and the error of the
+            # results above against it
+            ctrl_last, st_last = cp.cp_plan(h, 0, K=wl.n_waypoints)   # the plan's mean path, again
+            line["oracle_error"] = oracle_errors(cp, h, wl, crane, scene, q0, qd, ctrl_last, st_last, iters)
+            line["cpu_baseline"] = cpu_baseline(wl, crane, scene, q0, qd, args.cpu_seconds,
+                                                single_core_seconds=args.cpu_seconds / 4)
         print(json.dumps(line), flush=True)
     planner.close()
     if ws > 1:
@@ -975,31 +987,103 @@ def batch_cpu_baseline(crane, queries, q0s, qds, seed, S, seconds):
                       "the batch, each with its own scene and sizes" % (done, picked)}
 
 
-def cpu_baseline(wl, crane, scene, q0, qd, seconds, max_batches=None):
+def _oracle_eval(oracle, problem, wl, xi, q0, qd, with_distances=False):
+    """Step (2) by the oracle: brute force, or through its uniform grid (the same costs and
+    flags, pinned equal to the brute force) on the grid workloads."""
+    if wl.grid_cell > 0:
+        return oracle.evaluate_grid(problem, xi, q0, qd, wl.grid_cell, with_distances=with_distances)
+    return oracle.evaluate(problem, xi, q0, qd, with_distances=with_distances)
+
+
+def cpu_baseline(wl, crane, scene, q0, qd, seconds, max_batches=None, single_core_seconds=None):
     """The FP64 oracle as it stands, on all host cores, on a bounded sample: candidate
     evaluations (step (2), which dominates a plan) of the same workload, in batches until
-    `seconds` have passed; value in candidate paths per second."""
+    `seconds` have passed; value in candidate paths per second. On the grid workloads the
+    oracle takes d(q) through its own uniform grid (equal to its brute force in every cost
+    and flag). With single_core_seconds the same is also timed on one core."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle
     from paper_2503_14160_gb300 import workloads
     cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
     problem = oracle.Problem(crane, scene, oracle.CostParams(K=wl.n_waypoints, S=wl.substeps))
-    batch = 4 * cores
-    xi = workloads.random_candidates(q0, qd, wl.n_waypoints, batch, seed=123).astype(np.float64)
-    done, t0, batches = 0, time.perf_counter(), 0
-    while True:
-        oracle.evaluate(problem, xi, q0, qd)
-        done += batch
-        batches += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or (max_batches and batches >= max_batches):
-            break
-    return {"value": done / el, "unit": UNIT, "cores": int(oracle.get_threads()),
-            "kind": "oracle", "seconds": el,
-            "sample": "%d candidate evaluations (K=%d, S=%d, %d cylinders, FP64, OpenMP over "
-                      "candidates) of the %s workload" % (done, wl.n_waypoints, wl.substeps,
-                                                          scene.n_cyl, wl.name)}
+    form = "grid of %.2f m cells" % wl.grid_cell if wl.grid_cell > 0 else "brute force"
+
+    def timed(threads, budget, batch, limit):
+        oracle.set_threads(threads)
+        xi = workloads.random_candidates(q0, qd, wl.n_waypoints, batch, seed=123).astype(np.float64)
+        done, t0, batches = 0, time.perf_counter(), 0
+        while True:
+            _oracle_eval(oracle, problem, wl, xi, q0, qd)
+            done += batch
+            batches += 1
+            el = time.perf_counter() - t0
+            if el >= budget or (limit and batches >= limit):
+                return done, el, int(oracle.get_threads())
+
+    done, el, used = timed(cores, seconds, 4 * cores * (8 if wl.grid_cell > 0 else 1), max_batches)
+    out = {"value": done / el, "unit": UNIT, "cores": used, "kind": "oracle", "seconds": el,
+           "sample": "%d candidate evaluations (K=%d, S=%d, %d cylinders + %d boxes, FP64, d(q) by %s, "
+                     "OpenMP over candidates) of the %s workload" % (done, wl.n_waypoints, wl.substeps,
+                                                                  scene.n_cyl, scene.n_box, form, wl.name)}
+    if single_core_seconds:
+        d1, e1, _ = timed(1, single_core_seconds, 8 if wl.grid_cell > 0 else 1, None)
+        out["single_core"] = {"value": d1 / e1, "unit": UNIT, "cores": 1, "seconds": e1,
+                              "sample": "%d candidate evaluations, same form" % d1}
+    oracle.set_threads(cores)
+    return out
+
+
+def oracle_errors(cp, h, wl, crane, scene, q0, qd, ctrl, stats, iters, n_sample=256):
+    """The error of the benchmarked results against the FP64 oracle (run in the CPU-baseline
+    leg): the plan's mean path (the float32 waypoints the GPU evaluated) by brute force, its
+    J, length and flags; and n_sample candidates drawn from the final distribution, the
+    GPU's J, penalties and flags against the oracle's on the same float32 candidates."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    K, n_s = wl.n_waypoints, wl.n_checkpoints
+    problem = oracle.Problem(crane, scene, oracle.CostParams(K=K, S=wl.substeps))
+    mean_xi = np.asarray(ctrl)[4:4 + K].astype(np.float32).astype(np.float64)[None]
+    o = oracle.evaluate(problem, mean_xi, q0, qd)
+    plan = {"J_gpu": stats["J"], "J_oracle": float(o.J[0]),
+            "J_rel_err": abs(stats["J"] - float(o.J[0])) / max(abs(float(o.J[0])), 1e-300),
+            "length_gpu": stats["length"], "length_oracle": float(o.length[0]),
+            "length_rel_err": abs(stats["length"] - float(o.length[0])) / max(float(o.length[0]), 1e-300),
+            "flag_gpu": int(stats["flag"]), "flag_oracle": int(o.flag[0]),
+            "n_flagged_gpu": int(stats["n_flagged"]), "n_flagged_oracle": int(o.n_flagged[0]),
+            "oracle_form": "brute force"}
+    n = min(n_sample, wl.n_candidates)
+    xi = torch.zeros(n if n == wl.n_candidates else wl.n_candidates, K, 4, device="cuda")
+    cp.cp_sample(h, iters, xi)
+    J = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flag = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    terms = torch.zeros(n, 5, dtype=torch.float64, device="cuda")
+    W = (n_s + 31) // 32
+    words = torch.zeros(n, W, dtype=torch.int32, device="cuda")
+    pen = torch.zeros(n, n_s, dtype=torch.float32, device="cuda")
+    cp.cp_evaluate(h, xi, n, J, flag, terms, words, pen)
+    torch.cuda.synchronize()
+    xs = xi[:n].cpu().numpy().astype(np.float64)
+    c = _oracle_eval(oracle, problem, wl, xs, q0, qd, with_distances=True)
+    d = c.d[:, 1:]
+    Jg = J.cpu().numpy()
+    rel = np.abs(Jg - c.J) / np.maximum(np.abs(c.J), 1e-300)
+    w = words.cpu().numpy().view(np.uint32)
+    bits = ((w[:, :, None] >> np.arange(32, dtype=np.uint32)[None, None, :]) & 1).astype(bool)
+    flags = bits.reshape(n, -1)[:, :n_s]
+    band = np.abs(d) > 1e-4
+    near = (d < 2e-5).sum(axis=1)
+    tol = 1e-4 * np.abs(c.J) + 100.0 * 2e-5 * near + 1e-9
+    cand = {"candidates": n, "drawn_from": "the final distribution (iteration %d)" % iters,
+            "oracle_form": "grid (equal to brute force)" if wl.grid_cell > 0 else "brute force",
+            "J_rel_err_max": float(rel.max()), "J_rel_err_median": float(np.median(rel)),
+            "frac_J_within_1e-4_rel": float(np.mean(rel <= 1e-4)),
+            "frac_J_within_tolerance": float(np.mean(np.abs(Jg - c.J) <= tol)),
+            "contact_checkpoints_per_candidate": float(near.mean()),
+            "pen_abs_err_max_m": float(np.abs(pen.cpu().numpy() - np.maximum(0.0, -d)).max()),
+            "flag_mismatches_outside_1e-4_m": int((flags[band] != (d < 0)[band]).sum()),
+            "checkpoints_compared": int(n * n_s)}
+    return {"plan": plan, "candidates": cand}
 
 
 def run_reference(args):

@@ -450,28 +450,38 @@ void cp_batch_destroy(cp_batch *b);
 /* Size of the fixed device scratch behind cp_evaluate_static (bytes, per GPU). */
 #define CP_STATIC_SCRATCH_BYTES (32u << 20)
 
-/* The evaluation of cp_evaluate (Algorithm 1 step (2), without the per-checkpoint outputs)
- * for callers that may not allocate device memory: it calls no cudaMalloc, cudaFree or
- * other allocating routine and needs no planner. The paper has no counterpart; this entry
- * point exists for callers such as a real-time control loop, where cudaMalloc may stall the
- * device for an unbounded time, or a plug-in whose host application owns all device memory.
- * All scratch (obstacle records, spline table, partial sums: about 20 bytes per candidate
- * per 32 checkpoints plus 32 bytes per obstacle and per checkpoint of a span) lives in one
- * fixed array of CP_STATIC_SCRATCH_BYTES that every GPU loading the library keeps until
- * the process exits; larger requests fail with CP_ERR_ARG and say how much they need.
- * Inputs, all on the current device except model, h_q0 and h_qd (host): d_cyl[n_cyl] and
- * d_box[n_box] in the cp_cylinder / cp_box layout, the candidates d_xi (float[n][K][4]).
+/* Candidate costs as cp_evaluate computes them with the link-sphere collision model (the
+ * broad-phase form; the convex-hull model and the grid are not available here), for callers
+ * that may not allocate device memory: it calls no cudaMalloc, cudaFree or other allocating
+ * routine and needs no planner. The paper has no counterpart; this entry point exists for
+ * callers such as a real-time control loop, where cudaMalloc may stall the device for an
+ * unbounded time, or a plug-in whose host application owns all device memory.
+ * All scratch (a status word, obstacle records, spline table, partial sums: about 20 bytes
+ * per candidate per 32 checkpoints plus 32 bytes per obstacle and per checkpoint of a span)
+ * lives in one fixed array of CP_STATIC_SCRATCH_BYTES that every GPU loading the library
+ * keeps until the process exits; larger requests fail with CP_ERR_ARG and say how much they
+ * need. Inputs, all on the current device except model, h_q0 and h_qd (host): d_cyl[n_cyl]
+ * and d_box[n_box] in the cp_cylinder / cp_box layout, the candidates d_xi (float[n][K][4]).
  * Outputs as in cp_evaluate: d_J (required), d_flag and d_terms (may be NULL). Work is
- * ordered on `stream`. The first call on a device looks up the scratch array's device
- * address (make that first call before any stream capture). Every call reuses the same
- * scratch and overwrites all of it that it reads, so two calls that overlap on the GPU
- * (different streams, or different host threads) race with each other: serialise them. */
+ * ordered on `stream`; the call returns before it completes. If the bounded wait for the
+ * obstacle staging gives up on the device, every d_J of the call is NaN, every d_flag is 1
+ * and the d_terms are NaN (the failure is visible without a synchronisation).
+ * The first call on a device looks up the scratch array's device address (make that first
+ * call before any stream capture); the address is kept, so do not call this after a
+ * cudaDeviceReset of the host application. Every call reuses the same scratch and
+ * overwrites all of it that it reads, so two calls that overlap on the GPU (different
+ * streams, or different host threads) race with each other: serialise them. */
 int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cyl, int32_t n_cyl,
                        const cp_box *d_box, int32_t n_box, int32_t n_waypoints,
                        int32_t substeps, double w_c, double w_l, double lambda_c,
                        const double h_q0[4], const double h_qd[4], const float *d_xi,
                        int32_t n, double *d_J, uint8_t *d_flag, double *d_terms,
                        void *stream);
+
+/* Test hook: while on (1), cp_evaluate_static issues no staging copy, so that its bounded
+ * wait runs out on the device (about one second) and the call's results read as failed.
+ * 0 turns it off; no other effect. */
+void cp_debug_static_withhold_staging(int32_t on);
 
 /* Turn per-stage timing on (1) or off (0); turning it on clears the accumulators. */
 int cp_set_timing(cp_planner *p, int32_t on);

@@ -21,6 +21,8 @@
  *   o_bspline           q(s) = sum_i P_i N_i^3(s), Cox-de Boor on a uniform knot vector (Sec. 4.1)
  *   o_path_cost         J = J_p + w_c J_c + w_l J_l (Eq. path opt, all three sums)
  *   o_path_cost_batch   the same for N candidates (Algorithm 1 step (2)); OpenMP over candidates
+ *   o_path_cost_batch_grid  the same with d(q) through a uniform obstacle grid (equal to
+ *                       the brute force in every cost term and flag; for timing large scenes)
  *   o_smooth_cost       the softplus-penalty variant of J used by the differentiable form
  *   o_smooth_grad       its analytic gradient with respect to the K free control points
  *   o_ik_residual       residual and Jacobian of the collision-free IK (Sec. 3.2, Eq. IK opt)
@@ -305,10 +307,21 @@ typedef struct {
     int32_t n_flagged;     /* how many checkpoints are in collision */
 } o_cost;
 
-/* Eq. path opt for one candidate. d_out (optional, [n_s + 1]) receives d(q(s_k)). */
-void o_path_cost(const o_model *m, const o_scene *sc, const o_cost_params *cp,
-                 const double *xi /* [K][4] */, const double q0[4], const double qd[4],
-                 o_cost *out, double *d_out)
+/* A distance function d(q) for the path cost: the brute-force o_signed_distance, or the
+ * grid form below (equal wherever d < 0, which is all the cost uses). */
+typedef double (*o_distance_fn)(const o_model *m, const o_scene *sc, const void *ctx, const double q[4]);
+
+static double brute_distance(const o_model *m, const o_scene *sc, const void *ctx, const double q[4])
+{
+    (void)ctx;
+    return o_signed_distance(m, sc, q);
+}
+
+/* Eq. path opt for one candidate with the distance function `dist`. d_out (optional,
+ * [n_s + 1]) receives d(q(s_k)). */
+static void path_cost_with(const o_model *m, const o_scene *sc, o_distance_fn dist, const void *ctx,
+                           const o_cost_params *cp, const double *xi /* [K][4] */, const double q0[4],
+                           const double qd[4], o_cost *out, double *d_out)
 {
     const int32_t K = cp->K, n_c = K + 8;
     const int64_t n_s = (int64_t)(K + 3) * cp->S;
@@ -316,7 +329,7 @@ void o_path_cost(const o_model *m, const o_scene *sc, const o_cost_params *cp,
     assemble_control_points(K, xi, q0, qd, P);
     double q_prev[4];
     o_bspline(P, n_c, checkpoint_tau(K, cp->S, 0), q_prev);
-    if (d_out) d_out[0] = o_signed_distance(m, sc, q_prev);
+    if (d_out) d_out[0] = dist(m, sc, ctx, q_prev);
     double Jp = 0.0, Jc = 0.0, Jl = 0.0, len = 0.0;
     int32_t flag = 0, n_flagged = 0;
     for (int64_t k = 1; k <= n_s; ++k) {
@@ -326,7 +339,7 @@ void o_path_cost(const o_model *m, const o_scene *sc, const o_cost_params *cp,
         for (int c = 0; c < 4; ++c) step2 += (q[c] - q_prev[c]) * (q[c] - q_prev[c]);
         Jp += step2;
         len += sqrt(step2);
-        const double d = o_signed_distance(m, sc, q);
+        const double d = dist(m, sc, ctx, q);
         if (d_out) d_out[k] = d;
         Jc += cp->lambda_c * fmax(0.0, -d);
         if (d < 0.0) {
@@ -349,6 +362,14 @@ void o_path_cost(const o_model *m, const o_scene *sc, const o_cost_params *cp,
     out->n_flagged = n_flagged;
 }
 
+/* Eq. path opt for one candidate, d(q) by brute force over every pair. */
+void o_path_cost(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                 const double *xi /* [K][4] */, const double q0[4], const double qd[4],
+                 o_cost *out, double *d_out)
+{
+    path_cost_with(m, sc, brute_distance, NULL, cp, xi, q0, qd, out, d_out);
+}
+
 /* Algorithm 1 step (2) for n candidates xi[n][K][4]. d_out (optional) is [n][n_s+1]. */
 void o_path_cost_batch(const o_model *m, const o_scene *sc, const o_cost_params *cp,
                        const double *xi, int64_t n, const double q0[4], const double qd[4],
@@ -359,6 +380,155 @@ void o_path_cost_batch(const o_model *m, const o_scene *sc, const o_cost_params 
     for (int64_t i = 0; i < n; ++i)
         o_path_cost(m, sc, cp, xi + i * 4 * cp->K, q0, qd, out + i,
                     d_out ? d_out + i * (n_s + 1) : NULL);
+}
+
+/* ------------------------------------------------------------------ grid form (timing) */
+
+/* A uniform 2-D grid of the obstacles, for timing the oracle on large scenes only (the
+ * parity tests use the brute-force d(q)). Cells of side h cover the bounding box of every
+ * obstacle's footprint dilated by the largest sphere radius (plus 1 mm); each obstacle is
+ * listed in every cell its dilated footprint overlaps. A sphere that penetrates an obstacle
+ * has its centre inside that footprint, so the obstacles listed in the cell of the centre
+ * include every one the sphere penetrates, and the minimum over them equals the brute-force
+ * d(q) wherever that is negative; elsewhere it is non-negative (or +inf), so the penalty
+ * max(0, -d) and the collision flags of Eq. path opt are those of the brute force. */
+typedef struct {
+    double x0, y0, h;
+    int32_t nx, ny;
+    int32_t *start;   /* [nx ny + 1] */
+    int32_t *items;   /* obstacle ids: cylinders 0..n_cyl-1, then boxes */
+} o_grid;
+
+static void footprint(const o_scene *sc, double r, int id, double f[4] /* x0, x1, y0, y1 */)
+{
+    if (id < sc->n_cyl) {
+        const double *c = sc->cyl + 5 * id;
+        const double reach = c[2] + r;
+        f[0] = c[0] - reach;
+        f[1] = c[0] + reach;
+        f[2] = c[1] - reach;
+        f[3] = c[1] + reach;
+    } else {
+        const double *b = sc->box + 6 * (id - sc->n_cyl);
+        f[0] = b[0] - r;
+        f[1] = b[3] + r;
+        f[2] = b[1] - r;
+        f[3] = b[4] + r;
+    }
+}
+
+static void cell_span(const o_grid *g, const double f[4], int c[4] /* ix0, ix1, iy0, iy1 */)
+{
+    c[0] = (int)floor((f[0] - g->x0) / g->h);
+    c[1] = (int)floor((f[1] - g->x0) / g->h);
+    c[2] = (int)floor((f[2] - g->y0) / g->h);
+    c[3] = (int)floor((f[3] - g->y0) / g->h);
+    if (c[0] < 0) c[0] = 0;
+    if (c[2] < 0) c[2] = 0;
+    if (c[1] > g->nx - 1) c[1] = g->nx - 1;
+    if (c[3] > g->ny - 1) c[3] = g->ny - 1;
+}
+
+/* Build the grid (returns 0, or -1 when memory runs out); free with o_grid_free. */
+static int grid_build(const o_model *m, const o_scene *sc, double h, o_grid *g)
+{
+    double r = 0.0;
+    for (int s = 0; s < m->n_spheres; ++s) r = fmax(r, m->radius[s]);
+    r += 1e-3;
+    const int n_obs = sc->n_cyl + sc->n_box;
+    double lo_x = 0.0, hi_x = 0.0, lo_y = 0.0, hi_y = 0.0;
+    for (int id = 0; id < n_obs; ++id) {
+        double f[4];
+        footprint(sc, r, id, f);
+        if (id == 0 || f[0] < lo_x) lo_x = f[0];
+        if (id == 0 || f[1] > hi_x) hi_x = f[1];
+        if (id == 0 || f[2] < lo_y) lo_y = f[2];
+        if (id == 0 || f[3] > hi_y) hi_y = f[3];
+    }
+    g->h = h;
+    g->x0 = lo_x;
+    g->y0 = lo_y;
+    g->nx = (int)floor((hi_x - lo_x) / h) + 1;
+    g->ny = (int)floor((hi_y - lo_y) / h) + 1;
+    const int64_t cells = (int64_t)g->nx * g->ny;
+    g->start = calloc((size_t)cells + 1, sizeof(int32_t));
+    int32_t *fill = calloc((size_t)cells, sizeof(int32_t));
+    if (!g->start || !fill) {
+        free(g->start);
+        free(fill);
+        return -1;
+    }
+    for (int pass = 0; pass < 2; ++pass) {   /* count, then fill */
+        for (int id = 0; id < n_obs; ++id) {
+            double f[4];
+            int c[4];
+            footprint(sc, r, id, f);
+            cell_span(g, f, c);
+            for (int iy = c[2]; iy <= c[3]; ++iy)
+                for (int ix = c[0]; ix <= c[1]; ++ix) {
+                    const int64_t cell = (int64_t)iy * g->nx + ix;
+                    if (pass == 0) g->start[cell + 1] += 1;
+                    else g->items[g->start[cell] + fill[cell]++] = id;
+                }
+        }
+        if (pass == 0) {
+            for (int64_t cell = 0; cell < cells; ++cell) g->start[cell + 1] += g->start[cell];
+            g->items = malloc(sizeof(int32_t) * (size_t)(g->start[cells] > 0 ? g->start[cells] : 1));
+            if (!g->items) {
+                free(g->start);
+                free(fill);
+                return -1;
+            }
+        }
+    }
+    free(fill);
+    return 0;
+}
+
+static void grid_free(o_grid *g)
+{
+    free(g->start);
+    free(g->items);
+}
+
+/* d(q) over the obstacles listed in the cells of the sphere centres (see above). */
+static double grid_distance(const o_model *m, const o_scene *sc, const void *ctx, const double q[4])
+{
+    const o_grid *g = (const o_grid *)ctx;
+    double centres[3 * O_MAX_SPHERES];
+    o_fk(m, q, centres, NULL, NULL);
+    double d = HUGE_VAL;
+    for (int s = 0; s < m->n_spheres; ++s) {
+        const double *p = centres + 3 * s;
+        const double fx = floor((p[0] - g->x0) / g->h), fy = floor((p[1] - g->y0) / g->h);
+        if (!(fx >= 0.0 && fy >= 0.0 && fx < (double)g->nx && fy < (double)g->ny)) continue;
+        const int64_t cell = (int64_t)fy * g->nx + (int64_t)fx;
+        for (int32_t it = g->start[cell]; it < g->start[cell + 1]; ++it) {
+            const int id = g->items[it];
+            if (id < sc->n_cyl) d = fmin(d, o_sdf_cylinder(p, sc->cyl + 5 * id) - m->radius[s]);
+            else d = fmin(d, o_sdf_box(p, sc->box + 6 * (id - sc->n_cyl)) - m->radius[s]);
+        }
+    }
+    return d;
+}
+
+/* o_path_cost_batch with d(q) through a uniform grid of cell side h (m): the same J, terms,
+ * flags and collision counts as the brute force (see above). Returns 0, or -1 when the
+ * grid could not be allocated. d_out, when given, holds the grid distances (equal to the
+ * brute force's where negative). */
+int32_t o_path_cost_batch_grid(const o_model *m, const o_scene *sc, const o_cost_params *cp,
+                               const double *xi, int64_t n, const double q0[4], const double qd[4],
+                               double h, o_cost *out, double *d_out)
+{
+    o_grid g;
+    if (!(h > 0.0) || grid_build(m, sc, h, &g) != 0) return -1;
+    const int64_t n_s = (int64_t)(cp->K + 3) * cp->S;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i)
+        path_cost_with(m, sc, grid_distance, &g, cp, xi + i * 4 * cp->K, q0, qd, out + i,
+                       d_out ? d_out + i * (n_s + 1) : NULL);
+    grid_free(&g);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ smooth form */

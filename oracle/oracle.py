@@ -13,6 +13,7 @@ written here with numpy, one function per step, in the paper's order and notatio
   sample             step (1): xi_i = mu + L z_i, z_i from Philox + Box-Muller
   sample_elites      step (1) from the last update's elites, no factor (same distribution)
   evaluate           step (2): J(xi_i) through the C oracle
+  evaluate_grid      the same with d(q) through a uniform obstacle grid (timing only)
   rank               step (3): stable ascending sort of J (NaN sorts last)
   log_rank_weights   step (4): w_j = (ln(nu + 1/2) - ln j) / sum_k (ln(nu + 1/2) - ln k)
   update             steps (5) and (6): mu <- sum_j w_j x_(j);
@@ -101,6 +102,10 @@ def lib():
         L.o_path_cost_batch.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Scene),
                                         ctypes.POINTER(_CostParams), dp, ctypes.c_int64,
                                         dp, dp, ctypes.POINTER(_Cost), dp]
+        L.o_path_cost_batch_grid.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Scene),
+                                             ctypes.POINTER(_CostParams), dp, ctypes.c_int64,
+                                             dp, dp, ctypes.c_double, ctypes.POINTER(_Cost), dp]
+        L.o_path_cost_batch_grid.restype = ctypes.c_int32
         L.o_smooth_cost_batch.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Scene),
                                           ctypes.POINTER(_CostParams), dp, ctypes.c_int64,
                                           dp, dp, dp]
@@ -267,6 +272,25 @@ def evaluate(problem: Problem, xi, q0, qd, with_distances: bool = False) -> Cost
     lib().o_path_cost_batch(ctypes.byref(problem.model), ctypes.byref(problem.scene),
                             ctypes.byref(problem.cp), _dp(xi), n, _dp(_c64(q0)), _dp(_c64(qd)),
                             out, _dp(d) if d is not None else None)
+    arr = np.ctypeslib.as_array(out)[:n]
+    return Costs(arr["J"].copy(), arr["Jp"].copy(), arr["Jc"].copy(), arr["Jl"].copy(),
+                 arr["length"].copy(), arr["flag"].copy(), arr["n_flagged"].copy(), d)
+
+
+def evaluate_grid(problem: Problem, xi, q0, qd, cell: float, with_distances: bool = False) -> Costs:
+    """evaluate() with d(q) through a uniform obstacle grid of cell side `cell` (m): the same
+    costs and flags as the brute force (only negative distances enter them), much faster on
+    large scenes. For timing the oracle on the dense forest; the parity tests use evaluate()."""
+    K = problem.cost.K
+    xi = _c64(xi).reshape(-1, K, 4)
+    n = xi.shape[0]
+    out = (_Cost * max(n, 1))()
+    d = np.zeros((n, problem.cost.n_checkpoints + 1)) if with_distances else None
+    rc = lib().o_path_cost_batch_grid(ctypes.byref(problem.model), ctypes.byref(problem.scene),
+                                      ctypes.byref(problem.cp), _dp(xi), n, _dp(_c64(q0)), _dp(_c64(qd)),
+                                      ctypes.c_double(cell), out, _dp(d) if d is not None else None)
+    if rc != 0:
+        raise MemoryError("oracle grid of cell %g could not be built" % cell)
     arr = np.ctypeslib.as_array(out)[:n]
     return Costs(arr["J"].copy(), arr["Jp"].copy(), arr["Jc"].copy(), arr["Jl"].copy(),
                  arr["length"].copy(), arr["flag"].copy(), arr["n_flagged"].copy(), d)

@@ -123,6 +123,7 @@ _SIGS = {
     "cp_version": (ctypes.c_int32, []),
     "cp_launch_count": (ctypes.c_int64, []),
     "cp_debug_fail_allocations": (None, [ctypes.c_int32]),
+    "cp_debug_static_withhold_staging": (None, [ctypes.c_int32]),
     "cp_plan_init": (ctypes.c_int, [ctypes.POINTER(cp_model), ctypes.POINTER(cp_scene),
                                     ctypes.POINTER(cp_params), _P, ctypes.POINTER(_P)]),
     "cp_destroy": (None, [_P]),
@@ -288,6 +289,10 @@ def cp_launch_count() -> int:
 
 def cp_debug_fail_allocations(n: int) -> None:
     load().cp_debug_fail_allocations(int(n))
+
+
+def cp_debug_static_withhold_staging(on: bool) -> None:
+    load().cp_debug_static_withhold_staging(1 if on else 0)
 
 
 def cp_plan_init(model: cp_model, scene: HostScene, params: cp_params, stream=None) -> int:

@@ -160,7 +160,8 @@ int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int nu
                 cudaStream_t st);
 int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n, int chunks,
                          double w_c, double w_l, double lambda_c, double *J, uint8_t *flag,
-                         double *terms, uint32_t *substep_flags, cudaStream_t st);
+                         double *terms, uint32_t *substep_flags, cudaStream_t st,
+                         const uint32_t *status = nullptr);   // nonzero *status: NaN J, flagged
 int launch_signed_distance(const ModelDev &m, const SceneDev &sc, const float *q, int n,
                            float *d, cudaStream_t st);
 int launch_ik(const ModelDev &m, const SceneDev &sc, const float *targets, const float *q_init, int n,

@@ -18,7 +18,7 @@ constexpr int kFinalizeBatch = 4;   // unit records loaded before they are added
 __global__ void __launch_bounds__(256)
 k_eval_finalize(const float4 *__restrict__ partial, const uint32_t *__restrict__ flagword, int n, int chunks,
                 double w_c, double w_l, double lambda_c, double *J, uint8_t *flag, double *terms,
-                uint32_t *substep_flags)
+                uint32_t *substep_flags, const uint32_t *status)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / kFinalizeLanes, g = t % kFinalizeLanes;
@@ -61,6 +61,14 @@ k_eval_finalize(const float4 *__restrict__ partial, const uint32_t *__restrict__
     jc *= lambda_c;
     J[i] = jp + w_c * jc + w_l * jl;
     if (flag != nullptr) flag[i] = n_flagged > 0 ? 1 : 0;
+    if (status != nullptr && *status != 0u) {
+        // the evaluation gave up on a bounded wait: some partials are stale, so no result
+        // of this call is valid (NaN cost, flagged)
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        jp = jc = jl = len = nan;
+        J[i] = nan;
+        if (flag != nullptr) flag[i] = 1;
+    }
     if (terms != nullptr) {
         double *tm = terms + (size_t)i * 5;
         tm[0] = jp;
@@ -75,13 +83,14 @@ k_eval_finalize(const float4 *__restrict__ partial, const uint32_t *__restrict__
 
 int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n, int chunks,
                          double w_c, double w_l, double lambda_c, double *J, uint8_t *flag,
-                         double *terms, uint32_t *substep_flags, cudaStream_t st)
+                         double *terms, uint32_t *substep_flags, cudaStream_t st,
+                         const uint32_t *status)
 {
     if (n == 0) return CP_OK;
     const int threads = 256;
     const int64_t total = (int64_t)n * kFinalizeLanes;
     k_eval_finalize<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
-        partial, flagword, n, chunks, w_c, w_l, lambda_c, J, flag, terms, substep_flags);
+        partial, flagword, n, chunks, w_c, w_l, lambda_c, J, flag, terms, substep_flags, status);
     CP_LAUNCHED("k_eval_finalize");
     return CP_OK;
 }

@@ -19,9 +19,14 @@ constexpr size_t kStaticScratchBytes = (size_t)CP_STATIC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_eval_scratch[kStaticScratchBytes];
 
 // Device address of g_eval_scratch per device (the host-side symbol is only a stand-in).
+// Looked up once per device; a device reset by the host application (cudaDeviceReset)
+// would leave it stale, so the entry point must not be called after one.
 constexpr int kMaxDevices = 64;
 std::atomic<unsigned char *> g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mutex;
+
+// Test hook: issue no staging copy, so that the evaluation's bounded wait runs out.
+std::atomic<int> g_withhold_staging{0};
 
 int scratch_address(unsigned char **out)
 {
@@ -73,8 +78,9 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     const int K = n_waypoints, S = substeps;
     const int n_s = (K + 3) * S;
     const int chunks = (n_s + 31) / 32;
-    // scratch layout: cylinder records, box records, basis table, partials, words
-    const size_t o_filt = 0;
+    // scratch layout: status word, cylinder records, box records, basis table, partials, words
+    const size_t o_status = 0;
+    const size_t o_filt = o_status + 256;
     const size_t o_exact = o_filt + align256(sizeof(float4) * (size_t)n_cyl);
     const size_t o_group = o_exact + align256(sizeof(float4) * (size_t)n_cyl);
     const size_t o_bc = o_group + align256(sizeof(float4) * (size_t)n_groups(n_cyl));
@@ -103,7 +109,9 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     float4 *group = (float4 *)(base + o_group);
     float4 *bc = (float4 *)(base + o_bc), *bh = (float4 *)(base + o_bh);
     float4 *basis = (float4 *)(base + o_basis);
+    uint32_t *status = (uint32_t *)(base + o_status);
     const cudaStream_t st = (cudaStream_t)stream;
+    CP_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
 
     const ModelDev m = make_model(model);
     if ((rc = launch_prepare_scene(d_cyl, n_cyl, d_box, n_box, m.r_max, filt, exact, group, bc, bh, st)) !=
@@ -123,11 +131,15 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     a.q0 = make_float4((float)h_q0[0], (float)h_q0[1], (float)h_q0[2], (float)h_q0[3]);
     a.qd = make_float4((float)h_qd[0], (float)h_qd[1], (float)h_qd[2], (float)h_qd[3]);
     a.broadphase = 1;
+    a.withhold_staging = g_withhold_staging.load() != 0;
+    a.status = status;   // a staging wait that runs out: the finalize writes NaN J, flag 1
     a.basis = basis;
     a.partial = (float4 *)(base + o_partial);
     a.flagword = (uint32_t *)(base + o_words);
     a.pen_out = nullptr;
     if ((rc = launch_eval(m, sc, a, num_sms, st)) != CP_OK) return rc;
     return launch_eval_finalize(a.partial, a.flagword, n, chunks, w_c, w_l, lambda_c, d_J, d_flag,
-                                d_terms, nullptr, st);
+                                d_terms, nullptr, st, status);
 }
+
+extern "C" void cp_debug_static_withhold_staging(int32_t on) { g_withhold_staging.store(on != 0); }

@@ -255,17 +255,28 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
 
     if (warp == kTcThreads / 32) {
         if (lane == 0) {
+            // Once a wait has run out (`late`), the results of the launch are void: the
+            // remaining waits are skipped and no further copy is issued, so a failed launch
+            // ends after one wait budget instead of one per stage. Copies already issued and
+            // not yet seen complete (`pending`, with their phase parity) are waited for,
+            // bounded, before the CTA leaves.
+            uint32_t pending = 0, pending_par = 0;
             const uint32_t idesc = tc::idesc_tf32(kTcM, Dp);
             for (int it = 0; it < kStages && it < n && !withhold; ++it) {
                 float *b_hi = smem + it * stage_floats + 2 * a_floats;
                 tc::mbar_expect_tx(&b_full[it], b_bytes);
                 tc::bulk_g2s(b_hi, Yp + (size_t)(c_begin + it) * b_floats, b_bytes, &b_full[it]);
+                pending |= 1u << it;   // phase parity 0
             }
             for (int it = 0; it < n; ++it) {
                 const int s = it % kStages;
+                const uint32_t par = (uint32_t)(it / kStages) & 1u;
                 float *a_hi = smem + s * stage_floats, *a_lo = a_hi + a_floats, *b_hi = a_lo + a_floats;
-                if (!tc::mbar_wait(&a_full[s], (it / kStages) & 1, kWaitCycles)) late = true;
-                if (!tc::mbar_wait(&b_full[s], (it / kStages) & 1, kWaitCycles)) late = true;
+                if (!late && !tc::mbar_wait(&a_full[s], par, kWaitCycles)) late = true;
+                if (!late) {
+                    if (tc::mbar_wait(&b_full[s], par, kWaitCycles)) pending &= ~(1u << s);
+                    else late = true;
+                }
                 tc::fence_after_sync();
                 const uint32_t sa_hi = tc::smem_addr(a_hi), sa_lo = tc::smem_addr(a_lo);
                 const uint32_t sb_hi = tc::smem_addr(b_hi), sb_lo = sb_hi + 4u * (uint32_t)(Dp * kChunkE);
@@ -283,13 +294,20 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
                 tc::mma_commit(&done[s]);
                 // the chunk two stages on goes where the previous stage's MMAs read
                 const int nx = it + 1, sx = nx % kStages;
-                if (it >= 1 && nx < n && !withhold) {
-                    if (!tc::mbar_wait(&done[sx], ((nx - kStages) / kStages) & 1, kWaitCycles)) late = true;
-                    float *bx = smem + sx * stage_floats + 2 * a_floats;
-                    tc::mbar_expect_tx(&b_full[sx], b_bytes);
-                    tc::bulk_g2s(bx, Yp + (size_t)(c_begin + nx) * b_floats, b_bytes, &b_full[sx]);
+                if (it >= 1 && nx < n && !withhold && !late) {
+                    if (!tc::mbar_wait(&done[sx], ((nx - kStages) / kStages) & 1, kWaitCycles)) {
+                        late = true;
+                    } else {
+                        float *bx = smem + sx * stage_floats + 2 * a_floats;
+                        tc::mbar_expect_tx(&b_full[sx], b_bytes);
+                        tc::bulk_g2s(bx, Yp + (size_t)(c_begin + nx) * b_floats, b_bytes, &b_full[sx]);
+                        pending |= 1u << sx;
+                        pending_par = (pending_par & ~(1u << sx)) | ((uint32_t)((nx / kStages) & 1) << sx);
+                    }
                 }
             }
+            for (int s = 0; s < kStages; ++s)   // copies in flight land before the CTA leaves
+                if (pending & (1u << s)) tc::mbar_wait(&b_full[s], (pending_par >> s) & 1u, kWaitCycles);
         }
         __syncwarp();
     } else {
@@ -316,7 +334,8 @@ k_sample_elites(const float *__restrict__ Yp, int N, int D, int n_chunks, int sl
                     l[q][e] = tc::to_tf32(z[e] - h[q][e]);
                 }
             }
-            if (it >= kStages && !tc::mbar_wait(&done[s], ((it - kStages) / kStages) & 1, kWaitCycles)) late = true;
+            if (it >= kStages && !late && !tc::mbar_wait(&done[s], ((it - kStages) / kStages) & 1, kWaitCycles))
+                late = true;
 #pragma unroll
             for (int q = 0; q < kChunkE / 8; ++q) {
                 const int off = core_index(r, 4 * ((kChunkE / 8) * half + q));
