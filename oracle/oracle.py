@@ -504,10 +504,14 @@ class PlanResult:
 
 
 def plan(problem: Problem, sp: SearchParams, q0, qd, iterations: int,
-         callback=None, rule: str = "paper", sampler: str = "factor") -> PlanResult:
+         callback=None, rule: str = "paper", sampler: str = "factor",
+         cost_noise: Optional[tuple] = None) -> PlanResult:
     """Algorithm 1 for a fixed number of iterations, starting from init_distribution;
     rule "cmaes" takes update_cmaes (sigma adapted) in place of steps (5)-(6); sampler
-    "elites" (paper rule) draws every sample after the first with sample_elites."""
+    "elites" (paper rule) draws every sample after the first with sample_elites.
+    cost_noise = (rel, seed), for sensitivity studies only: every cost the ranking sees is
+    multiplied by (1 + rel g), g standard normal from numpy's generator under `seed`, which
+    stands for evaluation errors of relative size rel (None: exact FP64 costs)."""
     q0, qd = _c64(q0), _c64(qd)
     m = problem.model_py
     mu, C = init_distribution(q0, qd, sp.K, m.q_min, m.q_max, sp.init_std_frac)
@@ -521,6 +525,10 @@ def plan(problem: Problem, sp: SearchParams, q0, qd, iterations: int,
             L = factor(st.C if rule == "cmaes" else C, st.sigma if rule == "cmaes" else sp.sigma)
             xi = sample(st.mu if rule == "cmaes" else mu, L, sp.seed, t, sp.query, sp.N, sp.K)
         J = evaluate(problem, xi, q0, qd).J
+        if cost_noise is not None:
+            if t == 0:
+                noise = np.random.default_rng(cost_noise[1])
+            J = J * (1.0 + cost_noise[0] * noise.standard_normal(J.shape))
         if rule == "cmaes":
             st = update_cmaes(st, xi, J, sp.n_elites)
             mu, C = st.mu, st.C

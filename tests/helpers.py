@@ -48,7 +48,7 @@ class Setup:
 
     def __init__(self, crane, scene, N, K, S, seed=0, n_elites=0, w_c=100.0, w_l=100.0,
                  lambda_c=1.0, eps=1e-8, sigma=1.0, grid_cell=0.0, grid_half_extent=0.0,
-                 exhaustive=0, update_rule=0):
+                 exhaustive=0, update_rule=0, sampler=0):
         import torch
         import oracle
         from paper_2503_14160_gb300 import craneplan as cp
@@ -60,7 +60,7 @@ class Setup:
         params = cp.make_params(N, K, S, n_elites=n_elites, w_c=w_c, w_l=w_l,
                                 lambda_c=lambda_c, eps=eps, sigma=sigma, seed=seed,
                                 grid_cell=grid_cell, grid_half_extent=grid_half_extent,
-                                eval_exhaustive=exhaustive, update_rule=update_rule)
+                                eval_exhaustive=exhaustive, update_rule=update_rule, sampler=sampler)
         self.planner = cp.Planner(crane, scene, params)
         self.nu = self.planner.nu
         self.problem = oracle.Problem(crane, scene, oracle.CostParams(K=K, S=S, w_c=w_c, w_l=w_l,
@@ -90,3 +90,25 @@ class Setup:
 
     def close(self):
         self.planner.close()
+
+
+EPS32 = 2.0 ** -24
+
+
+def factor_sample_bound(want, z, L):
+    """Float32 bound of a draw mu + L z against its FP64 value: the result's rounding and a
+    D-term float32 dot product of L and z."""
+    D = L.shape[0]
+    return EPS32 * np.abs(want) + (D + 8) * EPS32 * (np.abs(z[:, :D]) @ np.abs(L).T) + 1e-30
+
+
+def elite_sample_bound(want, z, X, mu, w, sigma, eps, slices=32):
+    """Worst-case bound of the tensor-core elite draw (3xTF32 products accumulated in FP32)
+    against the oracle's FP64 sample_elites, per coordinate; also returns the scale
+    sum_j |g_ij||Y_jd| used by the RMS check (see test_gpu_sample_elites)."""
+    nu, D = X.shape
+    Y = np.sqrt(w)[:, None] * (X - mu[None, :]) * sigma
+    scale = np.abs(z[:, :nu]) @ np.abs(Y)
+    bound = (EPS32 * np.abs(want) + (20 + 6 * nu + slices + 16) * EPS32 * scale
+             + 8 * EPS32 * sigma * np.sqrt(eps) * np.abs(z[:, nu:nu + D]) + 1e-30)
+    return bound, scale
