@@ -4,7 +4,7 @@ A step is one whole plan: the T iterations of Algorithm 1 (sample, evaluate, ran
 update; arXiv 2503.14160 Sec. 4.1) for one query, then the evaluation of the mean path.
 Default workload: the dense forest (N = 65536 candidates, K = 32 waypoints, S = 128
 checkpoints per span, 5000 trees at >= 0.8 m spacing in a 2-50 m annulus plus 50 boxes,
-through a 0.5 m obstacle grid, 200 iterations), synthetic and seeded; --workload
+through a polar obstacle index with 0.5 m rings, 200 iterations), synthetic and seeded; --workload
 single_large runs the single large query (N = 4096, K = 16, S = 64, 500 trees, 100
 iterations).
 
@@ -42,7 +42,7 @@ FLOPS_PER_PAIR = 5          # 2 sub, 1 mul, 1 fma per sphere-obstacle pair
 FLOPS_PER_CHECKPOINT = 140  # spline 32, kinematics ~80, length 12, limits 16
 FLOPS_FRAME_PER_SPHERE = 6  # broad phase: the sphere centre in the unit's frame (2 mul, 2 fma)
 FLOPS_PER_BROAD_TEST = 10   # broad phase: one obstacle against a unit's box
-FLOPS_GRID_PER_SPHERE = 4   # grid: the cell of a sphere centre (2 sub, 2 mul)
+FLOPS_PER_INDEX_TEST = 10   # polar index: one listed obstacle against a unit's box
 FP32_PEAK_TFLOPS = PEAK_SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
 
 
@@ -53,8 +53,9 @@ def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, form, sm_mhz)
     obstacle whose pair test runs FLOPS_PER_PAIR. form "exhaustive": every obstacle of every
     unit is tested. "broad": every (unit, obstacle) takes one box test, each checkpoint
     places its spheres in the unit frame, and only the counted survivors take pair tests.
-    "grid": each sphere finds its cell (FLOPS_GRID_PER_SPHERE) and the counted cell entries
-    take pair tests."""
+    "polar": each checkpoint places its spheres in the unit frame, the obstacles listed in
+    the unit's cells of the polar index take one box test each (counted on the device), and
+    the counted survivors take pair tests."""
     units = timing["eval_units"]
     pairs = timing["eval_pair_tests"]
     if units <= 0 or pairs < 0 or timing["eval_ms"] <= 0:
@@ -63,10 +64,11 @@ def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, form, sm_mhz)
     if form == "broad":
         flops += candidates * n_s * n_spheres * FLOPS_FRAME_PER_SPHERE
         flops += units * n_obstacles * FLOPS_PER_BROAD_TEST
-    elif form == "grid":
-        flops += candidates * n_s * n_spheres * FLOPS_GRID_PER_SPHERE
+    elif form == "polar":
+        flops += candidates * n_s * n_spheres * FLOPS_FRAME_PER_SPHERE
+        flops += max(timing.get("eval_box_tests", 0), 0) * FLOPS_PER_INDEX_TEST
     achieved = flops / (timing["eval_ms"] / 1e3) / 1e12
-    kernel = {"broad": "k_eval_broad", "exhaustive": "k_eval", "grid": "k_eval_grid"}[form]
+    kernel = {"broad": "k_eval_broad", "exhaustive": "k_eval", "polar": "k_eval_polar"}[form]
     return {"bound": "alu", "kernel": kernel,
             "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
@@ -76,6 +78,8 @@ def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, form, sm_mhz)
             "eval_ms_per_launch": timing["eval_ms"] / max(timing["eval_launches"], 1),
             "eval_launches": timing["eval_launches"],
             "pair_tests_per_checkpoint": pairs / max(candidates * n_s, 1),
+            "box_tests_per_unit": (timing["eval_box_tests"] / units
+                                   if timing.get("eval_box_tests", -1) >= 0 else None),
             "pair_tests_exhaustive_per_checkpoint": n_spheres * n_obstacles}
 
 
@@ -167,7 +171,7 @@ def steps_for_clocks(steps, run_once, min_seconds=1.0):
 
 KERNEL_SOURCES = {
     "k_eval_broad": ("k_eval.cu", "eval_common.cuh", "cp_internal.cuh"),
-    "k_eval_grid": ("k_grid.cu", "eval_common.cuh", "cp_internal.cuh"),
+    "k_eval_polar": ("k_grid.cu", "eval_common.cuh", "cp_internal.cuh"),
 }
 
 # DRAM bytes (read + write) per launch of an evaluation kernel from one ncu capture of the
@@ -350,7 +354,7 @@ def run_ours(args):
     candidates = n_timing * (wl.n_candidates * iters + 1)
     roofline_exhaustive = None
     peaks_fp64 = None
-    form = "grid" if wl.grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
+    form = "polar" if wl.grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
     if args.collision == "hulls":
         # the hull form's work per checkpoint depends on the pairs its scan keeps; its line
         # reports the launch time only
@@ -393,7 +397,7 @@ def run_ours(args):
             "roofline": roofline,
             "roofline_exhaustive": roofline_exhaustive,
             "eval_kernel": {"name": "k_eval_hulls" if args.collision == "hulls" else
-                            {"broad": "k_eval_broad", "exhaustive": "k_eval", "grid": "k_eval_grid"}[form],
+                            {"broad": "k_eval_broad", "exhaustive": "k_eval", "polar": "k_eval_polar"}[form],
                             "ms_per_launch": eval_ms, "launches": timing["eval_launches"]},
             "stage_ms_per_plan": {k.replace("_ms", ""): timing[k] / n_timing
                                   for k in ("eval_ms", "sample_ms", "factor_ms", "update_ms")},

@@ -117,11 +117,17 @@ typedef struct cp_params {
     uint32_t query;         /* fourth Philox counter word (query id) */
     int32_t max_cylinders;  /* capacity of the scene buffers (cp_set_scene); 0 = scene's */
     int32_t max_boxes;
-    double grid_cell;       /* > 0: evaluate through a uniform 2-D obstacle grid with cells of
-                               this side (m); 0: every sphere against every obstacle */
-    double grid_half_extent;/* half side of the square grid window centred on the base (m);
-                               0 = boom_len + jib_len + max|q4 limit| + 4 */
-    int64_t max_grid_items; /* capacity of the cell lists; 0 = bound of the initial scene */
+    double grid_cell;       /* > 0: evaluate through a polar index of the obstacles about the
+                               slew axis (256 angular bins, rings of this width in m), which
+                               finds the obstacles near each 32 checkpoints of a candidate
+                               without scanning the scene (for large scenes); 0: scan every
+                               obstacle (broad phase or exhaustive). The results are the same
+                               bit for bit. */
+    double grid_half_extent;/* outer radius of the index's last closed ring (m); obstacles
+                               beyond it share one open ring. 0 = boom_len + jib_len +
+                               max|q4 limit| + 4 */
+    int64_t max_grid_items; /* capacity of the index's cell lists; 0 = bound of the initial
+                               scene */
     double smooth_margin;   /* differentiable form: softplus margin m (m); 0 selects 0.05 */
     double smooth_beta;     /* differentiable form: softplus width beta (m); 0 selects 0.01 */
     int32_t eval_ctas_per_sm; /* launch shape of the evaluation kernel: CTAs per SM of its
@@ -193,8 +199,9 @@ typedef struct cp_timing {
                                      unit in the exhaustive form (counted on the device
                                      for the broad phase; -1 for the grid form) */
     int64_t eval_pair_tests;      /* (checkpoint lane, sphere, obstacle) filter tests run:
-                                     counted on the device for the grid form (cell entries
-                                     visited), 32 x spheres x eval_obstacle_tests otherwise */
+                                     32 x spheres x eval_obstacle_tests */
+    int64_t eval_box_tests;       /* (unit, obstacle) box tests run by the polar-index form
+                                     (counted on the device; -1 for the other forms) */
 } cp_timing;
 
 typedef struct cp_planner cp_planner;

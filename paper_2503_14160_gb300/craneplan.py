@@ -100,7 +100,7 @@ class cp_timing(ctypes.Structure):
                 ("factor_ms", ctypes.c_double), ("factor_launches", ctypes.c_int64),
                 ("update_ms", ctypes.c_double), ("update_launches", ctypes.c_int64),
                 ("eval_units", ctypes.c_int64), ("eval_obstacle_tests", ctypes.c_int64),
-                ("eval_pair_tests", ctypes.c_int64)]
+                ("eval_pair_tests", ctypes.c_int64), ("eval_box_tests", ctypes.c_int64)]
 
 
 class cp_hull_model(ctypes.Structure):

@@ -116,6 +116,8 @@ bool is_finite(double v) { return std::isfinite(v); }
 // Candidate arrays are read and written one control point (four floats) at a time.
 bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
+constexpr int kPolarBins = 256;   // angular bins of the polar obstacle index
+
 }  // namespace
 
 struct cp_planner {
@@ -140,8 +142,8 @@ struct cp_planner {
     float *xi = nullptr;
     double *J = nullptr, *terms = nullptr;
     uint8_t *flag = nullptr;
-    float4 *partial = nullptr;
-    uint32_t *flagword = nullptr;
+    double *item_sum = nullptr;     // [N][P][4] FP64 sums of the evaluation's work items
+    uint32_t *item_count = nullptr; // [N][P]
     int *rank = nullptr, *elite = nullptr;
     float *elites = nullptr;
     double *w = nullptr, *mean_part = nullptr, *cov_part = nullptr;
@@ -153,7 +155,7 @@ struct cp_planner {
     uint8_t *mean_flag = nullptr;
     float *grad = nullptr;      // [N][D] gradient buffer for polish
     float4 *ends_f = nullptr;   // [2] {q0, qd} in float, written with the end points
-    unsigned long long *work = nullptr;   // broad-phase survivor count while timing
+    unsigned long long *work = nullptr;   // [2] broad-phase survivors and box tests while timing
     unsigned long long *rkey_a = nullptr, *rkey_b = nullptr;   // radix sort scratch
     int *rval_a = nullptr, *rval_b = nullptr, *rhist = nullptr;
     double *cma = nullptr;      // CMA-ES rule: {sigma, sigma before the update, h_sigma, |p_sigma|}
@@ -174,11 +176,10 @@ struct cp_planner {
     double *smooth_part_J = nullptr;
     int smem_optin = 0;
     bool use_grid = false;
-    GridDev gdev{};
+    PolarDev gdev{};                  // polar obstacle index (grid_cell > 0)
     int64_t grid_cap = 0;
     int *grid_count = nullptr, *grid_cursor = nullptr, *grid_start = nullptr;
-    float4 *grid_items = nullptr, *grid_outside = nullptr;
-    int *grid_counters = nullptr;
+    float4 *grid_items = nullptr;
     bool have_endpoints = false;
     float4 q0f{}, qdf{};
     int iteration = 0;
@@ -189,7 +190,7 @@ struct cp_planner {
     int plan_start = -1, plan_iters = -1;
     float4 plan_q0{}, plan_qd{};
     SceneDev plan_sdev{};
-    GridDev plan_gdev{};
+    PolarDev plan_gdev{};
     bool plan_ready_before = false, plan_ready_after = false;
     int64_t plan_nodes = 0;   // kernels in the recorded graph
 };
@@ -408,12 +409,12 @@ int stage_scene(cp_planner *p, const cp_scene *sc)
     for (int i = 0; i < sc->n_cyl; ++i) rmax_cyl = std::max(rmax_cyl, sc->cyl[i].radius);
     p->hull_reach_extra = (float)(std::max(0.0, rmax_cyl / std::cos(M_PI / 8.0) - rmax_cyl - (double)p->mdev.r_max) + 1e-3);
     if (p->use_grid) {
-        const int64_t need = grid_items_bound(sc, p->mdev.r_max, p->prm.grid_cell);
+        const int64_t need = polar_items_bound(sc, p->mdev.r_max, p->gdev.n_ang, p->gdev.n_ring, p->prm.grid_cell);
         if (need > p->grid_cap)
-            return set_error("scene may need %lld grid entries; capacity %lld (max_grid_items)",
+            return set_error("scene may need %lld index entries; capacity %lld (max_grid_items)",
                              (long long)need, (long long)p->grid_cap), CP_ERR_ARG;
-        rc = launch_grid_build(p->sdev, p->gdev, p->mdev.r_max, p->grid_count, p->grid_cursor,
-                               p->grid_start, p->grid_items, p->grid_outside, p->grid_counters, p->st);
+        rc = launch_polar_build(p->sdev, p->gdev, p->grid_count, p->grid_cursor, p->grid_start, p->grid_items,
+                                p->status, p->st);
         if (rc != CP_OK) return rc;
     }
     return CP_OK;
@@ -429,8 +430,10 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.S = p->S;
     a.n_s = p->n_s;
     a.chunks = p->chunks;
+    a.G = eval_units_per_item(n, p->chunks);
+    a.P = (p->chunks + a.G - 1) / a.G;
     a.div_S = fast_div((uint32_t)p->S);
-    a.div_chunks = fast_div((uint32_t)p->chunks);
+    a.div_P = fast_div((uint32_t)a.P);
     a.q0 = p->q0f;
     a.qd = p->qdf;
     a.ends = p->ends_f;
@@ -445,8 +448,9 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     }
     a.status = p->status;
     a.basis = p->basis;
-    a.partial = p->partial;
-    a.flagword = p->flagword;
+    a.item_sum = p->item_sum;
+    a.item_count = p->item_count;
+    a.words_out = d_words;
     a.pen_out = d_pen;
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
@@ -456,13 +460,13 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
         rc = launch_eval_hulls(p->mdev, p->sdev, d, a, p->num_sms, p->st);
     }
     else
-        rc = p->use_grid ? launch_eval_grid(p->mdev, p->sdev, p->gdev, a, p->num_sms, p->st)
+        rc = p->use_grid ? launch_eval_polar(p->mdev, p->sdev, p->gdev, a, p->num_sms, p->st)
                          : launch_eval(p->mdev, p->sdev, a, p->num_sms, p->st);
     if (rc != CP_OK) return rc;
     rc = p->timer.end(ST_EVAL, p->st);
     if (rc != CP_OK) return rc;
-    return launch_eval_finalize(p->partial, p->flagword, n, p->chunks, p->prm.w_c, p->prm.w_l,
-                                p->prm.lambda_c, d_J, d_flag, d_terms, d_words, p->st);
+    return launch_eval_finalize(p->item_sum, p->item_count, n, a.P, p->prm.w_c, p->prm.w_l, p->prm.lambda_c,
+                                d_J, d_flag, d_terms, p->st);
 }
 
 int run_factor(cp_planner *p)
@@ -560,6 +564,10 @@ int check_status(cp_planner *p)
         CP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(uint32_t), p->st));
         return set_error("a bounded device wait gave up"), CP_ERR_TIMEOUT;
     }
+    if (s & DEV_ERR_OVERFLOW) {
+        CP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(uint32_t), p->st));
+        return set_error("the obstacle index met more entries than its capacity (max_grid_items)"), CP_ERR_ARG;
+    }
     return CP_OK;
 }
 
@@ -621,24 +629,26 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->use_grid = params->grid_cell > 0.0;
     int64_t cells = 0;
     if (p->use_grid) {
+        // polar index: kPolarBins angular bins, rings of width grid_cell out to the window's
+        // half extent (the last ring open outwards)
         const double h = params->grid_cell;
         double W = params->grid_half_extent;
         if (W <= 0.0)
             W = model->boom_len + model->jib_len +
                 std::fmax(std::fabs(model->q_min[3]), std::fabs(model->q_max[3])) + 4.0;
-        const int64_t n_axis = (int64_t)std::ceil(2.0 * W / h);
-        if (n_axis < 1 || n_axis * n_axis > (1 << 22)) {
-            set_error("grid of %lld x %lld cells is outside 1..2^22 cells", (long long)n_axis,
-                      (long long)n_axis);
+        const int64_t n_ring = (int64_t)std::ceil(W / h);
+        if (n_ring < 1 || n_ring * kPolarBins > (1 << 22)) {
+            set_error("polar index of %d x %lld cells is outside 1..2^22 cells", kPolarBins, (long long)n_ring);
             return fail(CP_ERR_ARG);
         }
-        cells = n_axis * n_axis;
-        p->gdev.x0 = (float)(-0.5 * n_axis * h);
-        p->gdev.y0 = p->gdev.x0;
-        p->gdev.inv_h = (float)(1.0 / h);
-        p->gdev.nx = p->gdev.ny = (int)n_axis;
-        p->grid_cap = params->max_grid_items > 0 ? params->max_grid_items
-                                                 : grid_items_bound(scene, p->mdev.r_max, h);
+        cells = n_ring * kPolarBins;
+        p->gdev.n_ang = kPolarBins;
+        p->gdev.n_ring = (int)n_ring;
+        p->gdev.inv_da = (float)(kPolarBins / (2.0 * M_PI));
+        p->gdev.inv_dr = (float)(1.0 / h);
+        p->grid_cap = params->max_grid_items > 0
+                          ? params->max_grid_items
+                          : polar_items_bound(scene, p->mdev.r_max, kPolarBins, (int)n_ring, h);
         if (p->grid_cap < 1) p->grid_cap = 1;
     }
     const size_t eval_smem = p->use_grid ? 0 : eval_smem_bytes(p->cap_cyl, p->cap_box, p->S);
@@ -671,8 +681,10 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_J = L.take<double>(N);
     const size_t o_terms = L.take<double>(N * 5);
     const size_t o_flag = L.take<uint8_t>(N);
-    const size_t o_partial = L.take<float4>(N * ch);
-    const size_t o_flagword = L.take<uint32_t>(N * ch);
+    // work items of an evaluation of n <= N candidates: n P(n) <= min(n chunks, 2^18 + n)
+    const size_t item_cap = std::min(N * ch, (size_t)(1 << 18) + N);
+    const size_t o_item_sum = L.take<double>(item_cap * 4);
+    const size_t o_item_count = L.take<uint32_t>(item_cap);
     const size_t o_rank = L.take<int>(N);
     const size_t o_elite = L.take<int>(nu);
     const size_t o_elites = L.take<float>(nu * D);
@@ -690,14 +702,12 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_grid_cursor = L.take<int>((size_t)cells + 1);
     const size_t o_grid_start = L.take<int>((size_t)cells + 1);
     const size_t o_grid_items = L.take<float4>(p->use_grid ? (size_t)p->grid_cap : 1);
-    const size_t o_grid_outside = L.take<float4>((size_t)p->cap_cyl + p->cap_box + 1);
-    const size_t o_grid_counters = L.take<int>(2);
     const size_t o_grad = L.take<float>(N * D);
     const size_t o_ends_f = L.take<float4>(2);
     const size_t units_max = (size_t)smooth_partial_units(p->num_sms);
     const size_t o_sp_g = L.take<float>(units_max * D);
     const size_t o_sp_J = L.take<double>(units_max);
-    const size_t o_work = L.take<unsigned long long>(1);
+    const size_t o_work = L.take<unsigned long long>(2);
     const size_t o_cma = L.take<double>(4);
     const size_t o_psig = L.take<double>(D);
     const size_t o_pc = L.take<double>(D);
@@ -741,8 +751,8 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->J = (double *)(b + o_J);
     p->terms = (double *)(b + o_terms);
     p->flag = (uint8_t *)(b + o_flag);
-    p->partial = (float4 *)(b + o_partial);
-    p->flagword = (uint32_t *)(b + o_flagword);
+    p->item_sum = (double *)(b + o_item_sum);
+    p->item_count = (uint32_t *)(b + o_item_count);
     p->rank = (int *)(b + o_rank);
     p->elite = (int *)(b + o_elite);
     p->elites = (float *)(b + o_elites);
@@ -782,12 +792,9 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->grid_cursor = (int *)(b + o_grid_cursor);
     p->grid_start = (int *)(b + o_grid_start);
     p->grid_items = (float4 *)(b + o_grid_items);
-    p->grid_outside = (float4 *)(b + o_grid_outside);
-    p->grid_counters = (int *)(b + o_grid_counters);
     p->gdev.cell_start = p->grid_start;
     p->gdev.items = p->grid_items;
-    p->gdev.outside = p->grid_outside;
-    p->gdev.n_outside = p->grid_counters;
+    p->gdev.capacity = (int)std::min<int64_t>(p->grid_cap, 0x7FFFFFFF);
     p->sdev.cyl_filt = p->cyl_filt;
     p->sdev.cyl_group = p->cyl_group;
     p->sdev.cyl_exact = p->cyl_exact;
@@ -892,11 +899,11 @@ bool same_scene(const SceneDev &a, const SceneDev &b)
            memcmp(&a.z_lo_all, &b.z_lo_all, sizeof(float)) == 0 && memcmp(&a.z_hi_all, &b.z_hi_all, sizeof(float)) == 0;
 }
 
-bool same_grid(const GridDev &a, const GridDev &b)
+bool same_grid(const PolarDev &a, const PolarDev &b)
 {
-    return memcmp(&a.x0, &b.x0, sizeof(float)) == 0 && memcmp(&a.y0, &b.y0, sizeof(float)) == 0 &&
-           memcmp(&a.inv_h, &b.inv_h, sizeof(float)) == 0 && a.nx == b.nx && a.ny == b.ny &&
-           a.cell_start == b.cell_start && a.items == b.items && a.outside == b.outside && a.n_outside == b.n_outside;
+    return a.n_ang == b.n_ang && a.n_ring == b.n_ring && memcmp(&a.inv_da, &b.inv_da, sizeof(float)) == 0 &&
+           memcmp(&a.inv_dr, &b.inv_dr, sizeof(float)) == 0 && a.cell_start == b.cell_start && a.items == b.items &&
+           a.capacity == b.capacity;
 }
 
 // The iterations of cp_plan from p->iteration as one CUDA graph launch, recorded on first
@@ -1239,14 +1246,14 @@ int cp_get_timing(cp_planner *p, cp_timing *out)
     out->factor_launches = cnt[ST_FACTOR];
     out->update_ms = ms[ST_UPDATE];
     out->update_launches = cnt[ST_UPDATE];
-    unsigned long long survivors = 0;
-    CP_CUDA(cudaMemcpy(&survivors, p->work, sizeof(survivors), cudaMemcpyDeviceToHost));
+    unsigned long long work[2] = {0, 0};
+    CP_CUDA(cudaMemcpy(work, p->work, sizeof(work), cudaMemcpyDeviceToHost));
     out->eval_units = p->timer.units;
-    out->eval_obstacle_tests = p->timer.grid ? -1 : p->timer.tests + (int64_t)survivors;
-    out->eval_pair_tests = p->timer.grid ? (int64_t)survivors
-                                         : out->eval_obstacle_tests * 32 * p->mdev.n_spheres;
+    out->eval_obstacle_tests = p->timer.tests + (int64_t)work[0];
+    out->eval_pair_tests = out->eval_obstacle_tests * 32 * p->mdev.n_spheres;
+    out->eval_box_tests = p->timer.grid ? (int64_t)work[1] : -1;
     p->timer.clear();
-    CP_CUDA(cudaMemsetAsync(p->work, 0, sizeof(unsigned long long), p->st));
+    CP_CUDA(cudaMemsetAsync(p->work, 0, 2 * sizeof(unsigned long long), p->st));
     CP_CUDA(cudaStreamSynchronize(p->st));
     return CP_OK;
 }

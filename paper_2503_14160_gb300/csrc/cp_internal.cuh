@@ -31,6 +31,7 @@ void count_launch();
 enum : uint32_t {
     DEV_ERR_TIMEOUT = 1u,      // a bounded wait gave up
     DEV_ERR_NOT_PD = 2u,       // Cholesky met a non-positive pivot
+    DEV_ERR_OVERFLOW = 4u,     // an index build met more entries than its capacity
 };
 
 // ------------------------------------------------------------------ division by an invariant
@@ -107,15 +108,19 @@ constexpr float kZGate = 1e-3f;
 constexpr int kGroup = 8;    // cylinders per broad-phase group
 __host__ __device__ inline int n_groups(int n_cyl) { return (n_cyl + kGroup - 1) / kGroup; }
 
-// Uniform grid of obstacle ids over a square window (cells h x h, nx x ny).
-struct GridDev {
-    float x0, y0;            // window corner
-    float inv_h;
-    int nx, ny;
-    const int *cell_start;   // [nx ny + 1]
-    const float4 *items;     // records {cx, cy, W, id}; id < n_cyl cylinder, else box n_cyl + b
-    const float4 *outside;   // records of obstacles whose dilated footprint leaves the window
-    const int *n_outside;    // [1]
+// Polar index of the obstacles for large scenes. The plane around the slew axis is cut into
+// n_ang angular bins over [-pi, pi) and n_ring rings of width dr about the axis (the last ring
+// open outwards). Every obstacle is listed in each cell (bin, ring) that its reach disk (the
+// centre and the broad-phase reach of its record) overlaps, so that a sphere centre within
+// reach of an obstacle lies in a cell that lists it. Cells are stored bin-major: the rings
+// r0..r1 of one bin are one contiguous range of entries.
+struct PolarDev {
+    int n_ang, n_ring;
+    float inv_da;            // n_ang / (2 pi)
+    float inv_dr;            // 1 / dr
+    const int *cell_start;   // [n_ang n_ring + 1]
+    const float4 *items;     // {cx, cy, id (int bits), reach}; id < n_cyl a cylinder, else box id - n_cyl
+    int capacity;            // entries allocated: the build writes and the query reads no more
 };
 
 // Margin of the fast 2-D cylinder filter, in m^2: a pair reaches the exact distance test
@@ -139,28 +144,47 @@ ModelDev make_model(const cp_model *m);
 
 // ------------------------------------------------------------------ launchers
 
+// Work of an evaluation launch: unit = (candidate, 32 consecutive checkpoints), one per
+// lane; item = (candidate, G consecutive units), taken by one warp, which adds its units'
+// sums in FP64 in unit order. G depends only on the launch's size (eval_units_per_item), so
+// every evaluation form sums in the same order.
 struct EvalArgs {
     const float4 *xi;           // [n][K]
-    int n, K, S, n_s, chunks;   // chunks = ceil(n_s / 32)
-    FastDiv div_S, div_chunks;  // division by S and by chunks
+    int n, K, S, n_s, chunks;   // chunks = ceil(n_s / 32) units per candidate
+    int G, P;                   // units per item, items per candidate (P = ceil(chunks / G))
+    FastDiv div_S, div_P;       // division by S and by P
     float4 q0, qd;              // end points, used when `ends` is null
     const float4 *ends;         // optional device copy {q0, qd}, read at run time
     int ctas_per_sm;            // persistent-grid CTAs per SM (0: as many as fit)
     int withhold_staging;       // test hook: issue no staging copy, so its wait runs out
     int broadphase;             // 1: per-unit broad phase before the per-sphere filter
-    unsigned long long *work;   // optional: += obstacle tests that passed the broad phase
+    unsigned long long *work;   // optional [2]: += obstacles that passed the unit box test,
+                                // += (unit, obstacle) box tests run (polar index form)
     uint32_t *status;           // device status word (DEV_ERR_*) or null
     const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
-    float4 *partial;            // [n][chunks] {J_p, sum pen, J_l, length} (float)
-    uint32_t *flagword;         // [n][chunks]
+    double *item_sum;           // [n][P][4] {J_p, sum pen, J_l, length}
+    uint32_t *item_count;       // [n][P] checkpoints in collision
+    uint32_t *words_out;        // optional [n][chunks]: ballot word of checkpoints in collision
     float *pen_out;             // optional [n][n_s]
 };
 
+// Units per item for n candidates of `chunks` units: about 2^17 items per launch at most
+// (enough to keep every warp of the GPU busy to the end), a whole number of units each.
+// The items of a launch, n ceil(chunks / G), are then at most min(n chunks, 2^18 + n).
+inline int eval_units_per_item(int n, int chunks)
+{
+    const long long units = (long long)n * chunks;
+    long long g = units >> 17;
+    if (g < 1) g = 1;
+    if (g > chunks) g = chunks;
+    return (int)g;
+}
+
 int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
                 cudaStream_t st);
-int launch_eval_finalize(const float4 *partial, const uint32_t *flagword, int n, int chunks,
+int launch_eval_finalize(const double *item_sum, const uint32_t *item_count, int n, int P,
                          double w_c, double w_l, double lambda_c, double *J, uint8_t *flag,
-                         double *terms, uint32_t *substep_flags, cudaStream_t st,
+                         double *terms, cudaStream_t st,
                          const uint32_t *status = nullptr);   // nonzero *status: NaN J, flagged
 int launch_signed_distance(const ModelDev &m, const SceneDev &sc, const float *q, int n,
                            float *d, cudaStream_t st);
@@ -185,11 +209,11 @@ size_t eval_smem_bytes(int n_cyl, int n_box, int S);
 int eval_configure(size_t smem_bytes);
 int eval_ensure_smem(size_t smem_bytes);
 
-int64_t grid_items_bound(const cp_scene *sc, double r_max, double h);
-int launch_grid_build(const SceneDev &sc, const GridDev &g, float r_max, int *count, int *cursor,
-                      int *start, float4 *items, float4 *outside, int *counters, cudaStream_t st);
-int launch_eval_grid(const ModelDev &m, const SceneDev &sc, const GridDev &g, const EvalArgs &a,
-                     int num_sms, cudaStream_t st);
+int64_t polar_items_bound(const cp_scene *sc, double r_max, int n_ang, int n_ring, double dr);
+int launch_polar_build(const SceneDev &sc, const PolarDev &g, int *count, int *cursor, int *start,
+                       float4 *items, uint32_t *status, cudaStream_t st);
+int launch_eval_polar(const ModelDev &m, const SceneDev &sc, const PolarDev &g, const EvalArgs &a,
+                      int num_sms, cudaStream_t st);
 
 size_t smooth_smem_bytes(int n_cyl, int n_box, int S, int K);
 int launch_smooth(const ModelDev &m, const SceneDev &sc, const float *xi, int n, int K, int S,

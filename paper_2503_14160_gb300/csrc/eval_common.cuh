@@ -1,5 +1,6 @@
-// Device code shared by the evaluation kernels (brute-force and grid): signed distances,
-// crane kinematics, the spline at one checkpoint and the per-unit reduction.
+// Device code shared by the evaluation kernels (exhaustive, broad phase, polar index, hulls):
+// signed distances, crane kinematics, the spline at one checkpoint, the unit box of the
+// broad phase and the per-unit reduction into a work item's sums.
 #pragma once
 
 #include <math_constants.h>
@@ -221,17 +222,28 @@ static __device__ __forceinline__ UnitFrame unit_frame(float s1, float c1, const
 // The unit box of unit_frame over the spheres whose centre height lies in (zlo, zhi), the
 // band in which some obstacle can be penetrated at all; a lane with no such sphere adds
 // its first sphere (a larger box is still a bound).
+// The extent [hmin, hmax] of h over this lane's spheres whose centre height lies in
+// (zlo, zhi); hmin > hmax when there is none.
 template <int NSPH>
-static __device__ __forceinline__ UnitFrame unit_frame_band(float s1, float c1, const float *H, const float *Z,
-                                                            float zlo, float zhi)
+static __device__ __forceinline__ void band_extent(const float *H, const float *Z, float zlo, float zhi,
+                                                   float &hmin, float &hmax)
 {
-    float hmin = CUDART_INF_F, hmax = -CUDART_INF_F;
+    hmin = CUDART_INF_F;
+    hmax = -CUDART_INF_F;
 #pragma unroll
     for (int s = 0; s < NSPH; ++s) {
         const bool in = Z[s] > zlo && Z[s] < zhi;
         hmin = in ? fminf(hmin, H[s]) : hmin;
         hmax = in ? fmaxf(hmax, H[s]) : hmax;
     }
+}
+
+template <int NSPH>
+static __device__ __forceinline__ UnitFrame unit_frame_band(float s1, float c1, const float *H, const float *Z,
+                                                            float zlo, float zhi)
+{
+    float hmin, hmax;
+    band_extent<NSPH>(H, Z, zlo, zhi, hmin, hmax);
     if (hmin > hmax) hmin = hmax = H[0];
     const float hb[2] = {hmin, hmax};
     return unit_frame<2>(s1, c1, hb);
@@ -247,10 +259,10 @@ static __device__ __forceinline__ bool unit_near(const UnitFrame &f, float4 r, f
     return (fabsf(u - f.uc) <= f.uh + w) & (fabsf(v - f.vc) <= f.vh + w);
 }
 
-// Per lane: the checkpoint k = 32 chunk + lane + 1 of candidate `cand`, its configuration
-// q(s_k), the squared and plain length of the increment q(s_k) - q(s_{k-1}) and the
-// joint-limit excess (Eq. path opt). Lanes past n_s evaluate the last checkpoint and are
-// marked invalid.
+// Per lane: the checkpoint k = 32 chunk + lane + 1 of a candidate whose control points
+// [q0 x4, xi (K), qd x4] are staged in s_ctrl, its configuration q(s_k), the squared and plain
+// length of the increment q(s_k) - q(s_{k-1}) and the joint-limit excess (Eq. path opt).
+// Lanes past n_s evaluate the last checkpoint and are marked invalid.
 struct Checkpoint {
     float4 q;
     float jp, len, jl;
@@ -258,30 +270,34 @@ struct Checkpoint {
     bool valid;
 };
 
-static __device__ __forceinline__ Checkpoint checkpoint_setup(const ModelDev &m, const EvalArgs &a,
-                                                              const float4 *s_basis, int cand,
-                                                              int chunk, int lane)
+// The control points of candidate `cand` into this warp's s_ctrl[K + 8]. The warp syncs
+// before (the previous item's reads are done) and after (every lane sees them).
+static __device__ __forceinline__ void stage_controls(float4 *s_ctrl, const EvalArgs &a, int cand, int lane)
+{
+    __syncwarp();
+    const float4 q0 = a.ends != nullptr ? __ldg(a.ends) : a.q0;
+    const float4 qd = a.ends != nullptr ? __ldg(a.ends + 1) : a.qd;
+    const float4 *xi = a.xi + (size_t)cand * a.K;
+    for (int i = lane; i < a.K + 8; i += 32) s_ctrl[i] = i < 4 ? q0 : (i >= a.K + 4 ? qd : __ldg(xi + (i - 4)));
+    __syncwarp();
+}
+
+static __device__ __forceinline__ Checkpoint checkpoint_at(const ModelDev &m, const EvalArgs &a,
+                                                           const float4 *s_basis, const float4 *s_ctrl,
+                                                           int chunk, int lane)
 {
     Checkpoint c;
     c.k = chunk * 32 + lane + 1;
     c.valid = c.k <= a.n_s;
     const int kc = c.valid ? c.k : a.n_s;
     const int span = (int)fdiv((uint32_t)(kc - 1), a.div_S);   // moving span - 1, 0..K+2
-    const int mstep = kc - span * a.S;            // 1..S within the span
-    // control points P_{span+1..span+4} of [q0 x4, xi (K), qd x4]
-    const float4 *xi = a.xi + (size_t)cand * a.K;
-    const float4 q0 = a.ends != nullptr ? __ldg(a.ends) : a.q0;
-    const float4 qd = a.ends != nullptr ? __ldg(a.ends + 1) : a.qd;
-    float4 P[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int g = span + 1 + i;
-        P[i] = g < 4 ? q0 : (g >= a.K + 4 ? qd : __ldg(xi + (g - 4)));
-    }
+    const int mstep = kc - span * a.S;                           // 1..S within the span
+    const float4 *P = s_ctrl + span + 1;                         // P_{span+1..span+4}
+    const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3];
     const float4 bw = s_basis[2 * (mstep - 1)];
     const float4 dbw = s_basis[2 * (mstep - 1) + 1];
-    c.q = combine4(bw, P[0], P[1], P[2], P[3]);
-    const float4 dq = combine4(dbw, P[0], P[1], P[2], P[3]);   // q(s_k) - q(s_{k-1})
+    c.q = combine4(bw, P0, P1, P2, P3);
+    const float4 dq = combine4(dbw, P0, P1, P2, P3);   // q(s_k) - q(s_{k-1})
     c.jp = fmaf(dq.x, dq.x, fmaf(dq.y, dq.y, fmaf(dq.z, dq.z, dq.w * dq.w)));
     c.len = sqrtf(c.jp);
     c.jl = limit_excess(c.q.x, m.q_min[0], m.q_max[0]) + limit_excess(c.q.y, m.q_min[1], m.q_max[1]) +
@@ -289,14 +305,30 @@ static __device__ __forceinline__ Checkpoint checkpoint_setup(const ModelDev &m,
     return c;
 }
 
-// FP32 sums of the unit's lanes of four values and the ballot of collision flags, written
-// ([candidate][chunk]); the per-checkpoint penalty goes to pen_out when asked. The four
-// sums share one transposing butterfly: across lanes 16 apart each lane keeps two of the
-// values and hands the other two to its partner, across lanes 8 apart one of the two, and
-// three more steps finish the sum of that one value, so lane 8 k ends with the sum of
-// value k (6 shuffles instead of 20).
-static __device__ __forceinline__ void unit_epilogue(const EvalArgs &a, const Checkpoint &c, float dmin,
-                                                     int cand, int chunk, int lane)
+// Candidate and unit range [c0, c1) of work item `item`.
+struct ItemRange {
+    int cand, c0, c1;
+};
+
+static __device__ __forceinline__ ItemRange item_range(const EvalArgs &a, int item)
+{
+    ItemRange r;
+    r.cand = (int)fdiv((uint32_t)item, a.div_P);
+    r.c0 = (item - r.cand * a.P) * a.G;
+    r.c1 = min(a.chunks, r.c0 + a.G);
+    return r;
+}
+
+// The unit's four sums (J_p, penetration, J_l, length) in FP32 over its lanes, added to the
+// item's FP64 sums, and its collision count. The four sums share one transposing butterfly:
+// across lanes 16 apart each lane keeps two of the values and hands the other two to its
+// partner, across lanes 8 apart one of the two, and three more steps finish the sum of that
+// one value, so lane 8 j ends with the sum of value j (6 shuffles instead of 20); lane 8 j
+// keeps the item's FP64 sum of value j. The ballot word of checkpoints in collision and the
+// per-checkpoint penalty are written when asked for.
+static __device__ __forceinline__ void unit_accumulate(const EvalArgs &a, const Checkpoint &c, float dmin,
+                                                       int cand, int chunk, int lane, double &acc,
+                                                       uint32_t &count)
 {
     const float pen = fmaxf(0.f, -dmin);
     const bool hit = c.valid && (dmin < 0.f);
@@ -309,11 +341,18 @@ static __device__ __forceinline__ void unit_epilogue(const EvalArgs &a, const Ch
     float x = (hi8 ? w1 : w0) + __shfl_xor_sync(0xffffffffu, hi8 ? w0 : w1, 8);   // value 2 hi16 + hi8
 #pragma unroll
     for (int off = 4; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    acc += (double)x;
     const uint32_t word = __ballot_sync(0xffffffffu, hit);
-    const size_t slot = (size_t)cand * a.chunks + chunk;   // candidate-major: the finalize reads rows
-    if ((lane & 7) == 0) reinterpret_cast<float *>(a.partial + slot)[lane >> 3] = x;
-    if (lane == 0) a.flagword[slot] = word;
+    count += (uint32_t)__popc(word);
+    if (a.words_out != nullptr && lane == 0) a.words_out[(size_t)cand * a.chunks + chunk] = word;
     if (a.pen_out != nullptr && c.valid) a.pen_out[(size_t)cand * a.n_s + (c.k - 1)] = pen;
+}
+
+static __device__ __forceinline__ void item_flush(const EvalArgs &a, int item, double acc, uint32_t count,
+                                                  int lane)
+{
+    if ((lane & 7) == 0) a.item_sum[(size_t)item * 4 + (lane >> 3)] = acc;
+    if (lane == 0) a.item_count[item] = count;
 }
 
 }  // namespace cp

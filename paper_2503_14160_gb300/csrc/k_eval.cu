@@ -2,15 +2,15 @@
 // n_s checkpoints, the crane kinematics, the link-sphere vs obstacle signed distance and
 // the three cost terms of Eq. path opt (arXiv 2503.14160, Sec. 4.1; d(q) of Sec. 3.1).
 //
-// Work decomposition: a work unit is (candidate, chunk of 32 consecutive checkpoints); a
-// warp takes one unit at a time, one checkpoint per lane, so the 32 lanes of a warp read
-// the same one or two spline spans (float4 control points, broadcast loads). All
-// obstacles are staged once per CTA in shared memory by bulk copies (TMA, no multicast)
-// completing on an mbarrier with a bounded wait. Per checkpoint and link sphere the
-// obstacle loop is a 2-FMA power test against every cylinder; only pairs that pass it
-// (sphere within reach of the cylinder) take the exact capped-cylinder distance. Per
-// unit, lane values are reduced with warp shuffles (FP32) into one partial per unit; a
-// second kernel sums each candidate's partials in a fixed order in FP64.
+// Work decomposition: a work unit is (candidate, chunk of 32 consecutive checkpoints), one
+// checkpoint per lane; a warp takes one work item (candidate, G consecutive units) at a time,
+// stages the candidate's control points in its slice of shared memory, and adds the units'
+// FP32 lane sums (warp shuffles) into FP64 sums in unit order. All obstacles are staged once
+// per CTA in shared memory by bulk copies (TMA, no multicast) completing on an mbarrier with
+// a bounded wait. Per checkpoint and link sphere the obstacle loop is a 2-FMA power test
+// against every cylinder; only pairs that pass it (sphere within reach of the cylinder) take
+// the exact capped-cylinder distance. A second kernel adds each candidate's item sums in a
+// fixed order in FP64.
 #include "eval_common.cuh"
 
 namespace cp {
@@ -27,6 +27,7 @@ constexpr int kEvalMinBlocks = CP_EVAL_MIN_BLOCKS;
 constexpr int kEvalBroadMinBlocks = CP_EVAL_BROAD_MIN_BLOCKS;
 constexpr int kObstaclesPerBranch = 2;   // obstacles tested between two branches
 constexpr long long kStagingWaitCycles = 2000000000ll;   // about one second at 2 GHz
+constexpr int kCtrlSlots = CP_MAX_WAYPOINTS + 8;         // control points per warp, float4
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -135,6 +136,41 @@ __device__ __forceinline__ float exact_polar(const ModelDev &m, const float *H, 
     return d;
 }
 
+// A surviving cylinder (filter record f = {cx, cy, W, reach}, exact record e = {R, z_lo,
+// z_hi, (R + r_max)^2 + margin}) against the unit's spheres at one lane: its centre at p
+// along the lane's plane and q across it; sphere s passes the polar filter when
+// (h_s - p)^2 < e.w - q^2 (two packed FP32x2 operations per sphere pair, H2 holding the
+// in-band h and 1e30 for the others), and the passing spheres take the exact distance.
+template <int NSPH>
+__device__ __forceinline__ float survivor_cylinder(const ModelDev &m, const float *H, const float *Z,
+                                                   const float2 *H2, float c1, float s1, float4 f, float4 e,
+                                                   const float *zero)
+{
+    const float p = fmaf(c1, f.x, s1 * f.y);
+    const float q = fmaf(c1, f.y, -(s1 * f.x));
+    const float rhs = fmaf(-q, q, e.w);
+    const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
+    float2 t[NSPH / 2];
+#pragma unroll
+    for (int k = 0; k < NSPH / 2; ++k) {
+        const float2 dh = __fadd2_rn(H2[k], mp2);
+        t[k] = __ffma2_rn(dh, dh, mr2);
+    }
+    return any_below<NSPH>(t, zero) ? exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e) : CUDART_INF_F;
+}
+
+// A surviving box (centre c, half extent hb) against every sphere of the lane.
+template <int NSPH>
+__device__ __forceinline__ float survivor_box(const ModelDev &m, const float *H, const float *Z, float c1,
+                                              float s1, float4 c, float4 hb)
+{
+    float d = CUDART_INF_F;
+#pragma unroll
+    for (int s = 0; s < NSPH; ++s)
+        d = fminf(d, sdf_box(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], c, hb) - m.sph[s].radius);
+    return d;
+}
+
 // The evaluation with the broad phase (the default form). Per unit: the checkpoints and
 // the kinematics in polar form, the unit box, then rounds of 32 obstacles: each lane tests
 // one obstacle against the box, and the warp takes the survivors one by one (a uniform
@@ -153,84 +189,74 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
     float4 *s_bh = s_bc + sc.n_box;
     float4 *s_basis = s_bh + sc.n_box;
     float4 *s_group = s_basis + 2 * a.S;
+    float4 *s_ctrl = s_group + n_groups(sc.n_cyl) + (threadIdx.x >> 5) * kCtrlSlots;
     __shared__ __align__(8) uint64_t staging_bar;
     if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, s_group, sc, a)) return;
 
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-    const int units = a.n * a.chunks;
+    const int items = a.n * a.P;
     uint32_t tested = 0;   // broad-phase survivors of this warp's units
     const float zero[NSPH] = {};
+    const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
 
-    for (int u = warp; u < units; u += n_warps) {
-        const int cand = (int)fdiv((uint32_t)u, a.div_chunks);
-        const int chunk = u - cand * a.chunks;
-        const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
-        float H[NSPH], Z[NSPH], s1, c1;
-        crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
-        // Spheres above or below every obstacle by more than r_max (the vertical gate over
-        // the whole scene) can penetrate nothing: they leave the unit box, and their packed
-        // h is pushed far away so that no polar filter passes them.
-        const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
-        const UnitFrame fr = unit_frame_band<NSPH>(s1, c1, H, Z, zlo, zhi);
-        float2 H2[NSPH / 2];
+    for (int it = warp; it < items; it += n_warps) {
+        const ItemRange ir = item_range(a, it);
+        stage_controls(s_ctrl, a, ir.cand, lane);
+        double acc = 0.0;
+        uint32_t count = 0;
+        for (int chunk = ir.c0; chunk < ir.c1; ++chunk) {
+            const Checkpoint c = checkpoint_at(m, a, s_basis, s_ctrl, chunk, lane);
+            float H[NSPH], Z[NSPH], s1, c1;
+            crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
+            // Spheres above or below every obstacle by more than r_max (the vertical gate over
+            // the whole scene) can penetrate nothing: they leave the unit box, and their packed
+            // h is pushed far away so that no polar filter passes them.
+            const UnitFrame fr = unit_frame_band<NSPH>(s1, c1, H, Z, zlo, zhi);
+            float2 H2[NSPH / 2];
 #pragma unroll
-        for (int q = 0; q < NSPH / 2; ++q)
-            H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
-                                Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
+            for (int q = 0; q < NSPH / 2; ++q)
+                H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
+                                    Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
 
-        float dmin = CUDART_INF_F;
-        const int n_grp = n_groups(sc.n_cyl);
-        for (int gbase = 0; gbase < n_grp; gbase += 32) {
-            // groups whose circle meets the unit box, then their members four groups at a
-            // time: lane l takes member l % 8 of the (l / 8)-th remaining group
-            uint32_t gmask = __ballot_sync(0xffffffffu, gbase + lane < n_grp && unit_near(fr, s_group[gbase + lane]));
-            while (gmask) {
-                uint32_t g = gmask;
-                const int slot = lane >> 3;
-                g = slot >= 1 ? g & (g - 1) : g;
-                g = slot >= 2 ? g & (g - 1) : g;
-                g = slot >= 3 ? g & (g - 1) : g;
-                const int o = g ? (gbase + __ffs(g) - 1) * kGroup + (lane & (kGroup - 1)) : sc.n_cyl;
+            float dmin = CUDART_INF_F;
+            const int n_grp = n_groups(sc.n_cyl);
+            for (int gbase = 0; gbase < n_grp; gbase += 32) {
+                // groups whose circle meets the unit box, then their members four groups at a
+                // time: lane l takes member l % 8 of the (l / 8)-th remaining group
+                uint32_t gmask = __ballot_sync(0xffffffffu, gbase + lane < n_grp && unit_near(fr, s_group[gbase + lane]));
+                while (gmask) {
+                    uint32_t g = gmask;
+                    const int slot = lane >> 3;
+                    g = slot >= 1 ? g & (g - 1) : g;
+                    g = slot >= 2 ? g & (g - 1) : g;
+                    g = slot >= 3 ? g & (g - 1) : g;
+                    const int o = g ? (gbase + __ffs(g) - 1) * kGroup + (lane & (kGroup - 1)) : sc.n_cyl;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) gmask &= gmask - 1;
-                uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, s_filt[o]));
-            tested += __popc(mask);
-            while (mask) {
-                const int ob = __shfl_sync(0xffffffffu, o, __ffs(mask) - 1);
-                mask &= mask - 1;
-                const float4 f = s_filt[ob], e = s_exact[ob];
-                const float p = fmaf(c1, f.x, s1 * f.y);
-                const float q = fmaf(c1, f.y, -(s1 * f.x));
-                const float rhs = fmaf(-q, q, e.w);
-                const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
-                float2 t[NSPH / 2];
-#pragma unroll
-                for (int k = 0; k < NSPH / 2; ++k) {
-                    const float2 dh = __fadd2_rn(H2[k], mp2);
-                    t[k] = __ffma2_rn(dh, dh, mr2);
+                    for (int k = 0; k < 4; ++k) gmask &= gmask - 1;
+                    uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_cyl && unit_near(fr, s_filt[o]));
+                    tested += __popc(mask);
+                    while (mask) {
+                        const int ob = __shfl_sync(0xffffffffu, o, __ffs(mask) - 1);
+                        mask &= mask - 1;
+                        dmin = fminf(dmin, survivor_cylinder<NSPH>(m, H, Z, H2, c1, s1, s_filt[ob], s_exact[ob], zero));
+                    }
                 }
-                if (any_below<NSPH>(t, zero))
-                    dmin = fminf(dmin, exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e));
             }
+            for (int base = 0; base < sc.n_box; base += 32) {
+                const int o = base + lane;
+                uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_box && unit_near(fr, s_bc[o]));
+                tested += __popc(mask);
+                while (mask) {
+                    const int ob = base + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    dmin = fminf(dmin, survivor_box<NSPH>(m, H, Z, c1, s1, s_bc[ob], s_bh[ob]));
+                }
             }
+            unit_accumulate(a, c, dmin, ir.cand, chunk, lane, acc, count);
         }
-        for (int base = 0; base < sc.n_box; base += 32) {
-            const int o = base + lane;
-            uint32_t mask = __ballot_sync(0xffffffffu, o < sc.n_box && unit_near(fr, s_bc[o]));
-            tested += __popc(mask);
-            while (mask) {
-                const int ob = base + __ffs(mask) - 1;
-                mask &= mask - 1;
-                const float4 bc = s_bc[ob], bh = s_bh[ob];
-#pragma unroll
-                for (int s = 0; s < NSPH; ++s)
-                    dmin = fminf(dmin, sdf_box(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], bc, bh) -
-                                           m.sph[s].radius);
-            }
-        }
-        unit_epilogue(a, c, dmin, cand, chunk, lane);
+        item_flush(a, it, acc, count, lane);
     }
     if (a.work != nullptr && lane == 0 && tested != 0) atomicAdd(a.work, (unsigned long long)tested);
 }
@@ -252,15 +278,19 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
     __shared__ __align__(8) uint64_t staging_bar;
     if (!stage_bulk(&staging_bar, s_filt, s_exact, s_bc, s_bh, s_basis, s_group, sc, a)) return;
 
+    float4 *s_ctrl = s_group + n_groups(sc.n_cyl) + (threadIdx.x >> 5) * kCtrlSlots;
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-    const int units = a.n * a.chunks;
+    const int items = a.n * a.P;
 
-    for (int u = warp; u < units; u += n_warps) {
-        const int cand = (int)fdiv((uint32_t)u, a.div_chunks);
-        const int chunk = u - cand * a.chunks;
-        const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
+    for (int it = warp; it < items; it += n_warps) {
+      const ItemRange ir = item_range(a, it);
+      stage_controls(s_ctrl, a, ir.cand, lane);
+      double acc = 0.0;
+      uint32_t count = 0;
+      for (int chunk = ir.c0; chunk < ir.c1; ++chunk) {
+        const Checkpoint c = checkpoint_at(m, a, s_basis, s_ctrl, chunk, lane);
 
         // Sphere centres; per sphere the filter threshold T = margin - (x^2 + y^2) and the
         // scaled coordinates (-2x, -2y), kept in pairs for packed FP32x2 FMAs.
@@ -323,7 +353,9 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
                                        m.sph[s].radius);
         }
 
-        unit_epilogue(a, c, dmin, cand, chunk, lane);
+        unit_accumulate(a, c, dmin, ir.cand, chunk, lane, acc, count);
+      }
+      item_flush(a, it, acc, count, lane);
     }
 }
 
@@ -373,7 +405,7 @@ int eval_grid(F *kernel, size_t smem, int num_sms, int units, int ctas_per_sm)
 size_t eval_smem_bytes(int n_cyl, int n_box, int S)
 {
     return sizeof(float4) * (2 * (size_t)n_cyl + 2 * (size_t)n_box + 2 * (size_t)S +
-                             (size_t)n_groups(n_cyl));
+                             (size_t)n_groups(n_cyl) + (size_t)(kEvalThreads / 32) * kCtrlSlots);
 }
 
 template <typename F>
@@ -401,7 +433,7 @@ int eval_ensure_smem(size_t smem_bytes)
 int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
                 cudaStream_t st)
 {
-    const int units = a.n * a.chunks;
+    const int units = a.n * a.P;   // work items
     if (units == 0) return CP_OK;
     const size_t smem = eval_smem_bytes(sc.n_cyl, sc.n_box, a.S);
     const int cpsm = a.ctas_per_sm;

@@ -350,17 +350,25 @@ k_eval_hulls(const ModelDev m, const SceneDev sc, const HullDims hd, const EvalA
     __shared__ float s_box[kHullWarps][32 * 4 * kBoxFloats];
     __shared__ int s_pen[kHullWarps][32];
     __shared__ int s_queue[kHullWarps][64];
+    __shared__ float4 s_ctrl_all[kHullWarps][CP_MAX_WAYPOINTS + 8];
     for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x) s_basis[i] = a.basis[i];
     __syncthreads();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int u = warp; u < a.n * a.chunks; u += n_warps) {
-        const int cand = (int)fdiv((uint32_t)u, a.div_chunks), chunk = u - cand * a.chunks;
-        const Checkpoint c = checkpoint_setup(m, a, s_basis, cand, chunk, lane);
-        const float pen = hull_pen_warp<true>(m, sc, hd, c.q, true, s_box[wib], s_pen[wib], s_queue[wib], lane);
-        __syncwarp();
-        unit_epilogue(a, c, pen > 0.f ? -pen : CUDART_INF_F, cand, chunk, lane);
+    float4 *s_ctrl = s_ctrl_all[wib];
+    for (int it = warp; it < a.n * a.P; it += n_warps) {
+        const ItemRange ir = item_range(a, it);
+        stage_controls(s_ctrl, a, ir.cand, lane);
+        double acc = 0.0;
+        uint32_t count = 0;
+        for (int chunk = ir.c0; chunk < ir.c1; ++chunk) {
+            const Checkpoint c = checkpoint_at(m, a, s_basis, s_ctrl, chunk, lane);
+            const float pen = hull_pen_warp<true>(m, sc, hd, c.q, true, s_box[wib], s_pen[wib], s_queue[wib], lane);
+            __syncwarp();
+            unit_accumulate(a, c, pen > 0.f ? -pen : CUDART_INF_F, ir.cand, chunk, lane, acc, count);
+        }
+        item_flush(a, it, acc, count, lane);
     }
 }
 
@@ -388,8 +396,8 @@ int launch_eval_hulls(const ModelDev &m, const SceneDev &sc, const HullDims &d, 
     int per_sm = 0;
     CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_hulls, kHullThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    const long long units = (long long)a.n * a.chunks;
-    long long blocks = (units + kHullWarps - 1) / kHullWarps;
+    const long long items = (long long)a.n * a.P;
+    long long blocks = (items + kHullWarps - 1) / kHullWarps;
     if (blocks > (long long)num_sms * per_sm) blocks = (long long)num_sms * per_sm;
     k_eval_hulls<<<(unsigned)blocks, kHullThreads, smem, st>>>(m, sc, d, a);
     CP_LAUNCHED("k_eval_hulls");

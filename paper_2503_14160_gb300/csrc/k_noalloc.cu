@@ -78,7 +78,9 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     const int K = n_waypoints, S = substeps;
     const int n_s = (K + 3) * S;
     const int chunks = (n_s + 31) / 32;
-    // scratch layout: status word, cylinder records, box records, basis table, partials, words
+    const int G = eval_units_per_item(n, chunks);
+    const int P = (chunks + G - 1) / G;
+    // scratch layout: status word, cylinder records, box records, basis table, item sums
     const size_t o_status = 0;
     const size_t o_filt = o_status + 256;
     const size_t o_exact = o_filt + align256(sizeof(float4) * (size_t)n_cyl);
@@ -86,9 +88,9 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     const size_t o_bc = o_group + align256(sizeof(float4) * (size_t)n_groups(n_cyl));
     const size_t o_bh = o_bc + align256(sizeof(float4) * (size_t)n_box);
     const size_t o_basis = o_bh + align256(sizeof(float4) * (size_t)n_box);
-    const size_t o_partial = o_basis + align256(sizeof(float4) * 2 * (size_t)S);
-    const size_t o_words = o_partial + align256(sizeof(float4) * (size_t)chunks * n);
-    const size_t need = o_words + align256(sizeof(uint32_t) * (size_t)chunks * n);
+    const size_t o_sum = o_basis + align256(sizeof(float4) * 2 * (size_t)S);
+    const size_t o_count = o_sum + align256(sizeof(double) * 4 * (size_t)P * n);
+    const size_t need = o_count + align256(sizeof(uint32_t) * (size_t)P * n);
     if (need > kStaticScratchBytes)
         return set_error("cp_evaluate_static needs %zu bytes of scratch for n = %d, n_s = %d and "
                          "%d + %d obstacles; its fixed scratch holds %zu bytes", need, n, n_s,
@@ -126,20 +128,23 @@ extern "C" int cp_evaluate_static(const cp_model *model, const cp_cylinder *d_cy
     a.S = S;
     a.n_s = n_s;
     a.chunks = chunks;
+    a.G = G;
+    a.P = P;
     a.div_S = fast_div((uint32_t)S);
-    a.div_chunks = fast_div((uint32_t)chunks);
+    a.div_P = fast_div((uint32_t)P);
     a.q0 = make_float4((float)h_q0[0], (float)h_q0[1], (float)h_q0[2], (float)h_q0[3]);
     a.qd = make_float4((float)h_qd[0], (float)h_qd[1], (float)h_qd[2], (float)h_qd[3]);
     a.broadphase = 1;
     a.withhold_staging = g_withhold_staging.load() != 0;
     a.status = status;   // a staging wait that runs out: the finalize writes NaN J, flag 1
     a.basis = basis;
-    a.partial = (float4 *)(base + o_partial);
-    a.flagword = (uint32_t *)(base + o_words);
+    a.item_sum = (double *)(base + o_sum);
+    a.item_count = (uint32_t *)(base + o_count);
+    a.words_out = nullptr;
     a.pen_out = nullptr;
     if ((rc = launch_eval(m, sc, a, num_sms, st)) != CP_OK) return rc;
-    return launch_eval_finalize(a.partial, a.flagword, n, chunks, w_c, w_l, lambda_c, d_J, d_flag,
-                                d_terms, nullptr, st, status);
+    return launch_eval_finalize(a.item_sum, a.item_count, n, P, w_c, w_l, lambda_c, d_J, d_flag, d_terms, st,
+                                status);
 }
 
 extern "C" void cp_debug_static_withhold_staging(int32_t on) { g_withhold_staging.store(on != 0); }

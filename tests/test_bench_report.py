@@ -44,6 +44,23 @@ def test_eval_roofline_broad_counts_every_part(bench):
     assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
 
 
+def test_eval_roofline_polar_counts_the_index_tests(bench):
+    t = _timing(eval_box_tests=5000)
+    r = bench.eval_roofline(t, n_spheres=12, n_obstacles=5050, n_s=4480, candidates=3, form="polar",
+                            sm_mhz=2070.0)
+    flops = (3 * 4480 * bench.FLOPS_PER_CHECKPOINT + 2000 * bench.FLOPS_PER_PAIR
+             + 3 * 4480 * 12 * bench.FLOPS_FRAME_PER_SPHERE + 5000 * bench.FLOPS_PER_INDEX_TEST)
+    assert r["achieved"] == pytest.approx(flops / 10e-3 / 1e12)
+    assert r["kernel"] == "k_eval_polar" and r["box_tests_per_unit"] == pytest.approx(5.0)
+
+
+def test_traffic_is_reported_only_for_the_profiled_sources(bench):
+    rec = bench.PROFILED_TRAFFIC["k_eval_broad"]
+    want = rec["bytes"] if bench.kernel_source_sha1("k_eval_broad") == rec["sha1"] else None
+    assert bench.traffic_per_launch("k_eval_broad", rec["workload"]) == want
+    assert bench.traffic_per_launch("k_eval_broad", "no such workload") is None
+
+
 def test_eval_roofline_refuses_empty_timings(bench):
     assert bench.eval_roofline(_timing(eval_units=0), 12, 500, 1216, 3, "broad", None) is None
 

@@ -157,9 +157,9 @@ def test_evaluate_single_large_full_size(lib, crane):
 
 @pytest.mark.parametrize("half,cell", [(0.0, 0.5), (5.0, 0.5), (0.0, 0.23)])
 def test_evaluate_grid_dense_forest(lib, crane, half, cell):
-    """The uniform-grid evaluation on the dense forest (5000 cylinders + 50 boxes) against
-    the oracle's brute force: default window, a 10 m window (spheres beyond it use the list
-    of obstacles that leave the window) and an odd cell size."""
+    """The polar-index evaluation on the dense forest (5000 cylinders + 50 boxes) against the
+    oracle's brute force: the default rings, closed rings only to 5 m (spheres beyond it
+    query the open last ring that holds every farther obstacle) and an odd ring width."""
     from paper_2503_14160_gb300 import workloads
     q0, qd = endpoints("dense_forest")
     s = Setup(crane, workloads.make_scene(workloads.WORKLOADS["dense_forest"]), N=64, K=6,
@@ -195,23 +195,24 @@ def test_evaluate_grid_dense_forest_full_size(lib, crane):
     ("dense_forest", None, 6, 16, 40, (0.6, 0.3, 0.4, 0.5)),    # 5000 cylinders, no grid
 ])
 def test_broadphase_matches_exhaustive_bitwise(lib, crane, name, n_cyl, K, S, n, spread):
-    """The broad phase only drops obstacles that no sphere of the 32 checkpoints can reach,
-    and it takes the same exact distances, so the default evaluation and the exhaustive one
-    (every sphere against every obstacle) give the same penalties, flags, terms and costs
-    bit for bit."""
+    """The broad phase and the polar index only drop obstacles that no sphere of the 32
+    checkpoints can reach, and they take the same exact distances, so the default
+    evaluation, the polar-index one (two ring widths) and the exhaustive one (every sphere
+    against every obstacle) give the same penalties, flags, terms and costs bit for bit."""
     from paper_2503_14160_gb300 import workloads
     q0, qd = endpoints(name)
     scene = _scene(name, n_cyl=n_cyl)
     xi = workloads.random_candidates(q0, qd, K, n, seed=K * 7 + n, spread=spread)
     out = []
-    for exhaustive in (0, 1):
-        s = Setup(crane, scene, N=n, K=K, S=S, exhaustive=exhaustive)
+    for exhaustive, cell in ((0, 0.0), (1, 0.0), (0, 0.5), (0, 1.7)):
+        s = Setup(crane, scene, N=n, K=K, S=S, exhaustive=exhaustive, grid_cell=cell)
         try:
             out.append(s.evaluate(xi, q0, qd))
         finally:
             s.close()
-    for key in ("J", "flag", "terms", "words", "pen"):
-        np.testing.assert_array_equal(out[0][key], out[1][key], err_msg=key)
+    for other in out[1:]:
+        for key in ("J", "flag", "terms", "words", "pen"):
+            np.testing.assert_array_equal(out[0][key], other[key], err_msg=key)
     assert out[0]["flag"].any()
 
 
@@ -259,10 +260,12 @@ def test_work_counters(lib, crane):
             s.close()
         assert t["eval_launches"] == 2 and t["eval_units"] == 2 * n * chunks
         assert t["eval_pair_tests"] == 32 * 12 * t["eval_obstacle_tests"]
+        assert t["eval_box_tests"] == -1
         got.append(t["eval_obstacle_tests"])
     assert got[0] == 2 * n * chunks * scene.n_cyl
     assert 0 < got[1] < got[0] // 10
-    # grid form: cell entries visited, a small fraction of the exhaustive pair tests
+    # polar-index form: the box tests of the listed obstacles (a small fraction of the
+    # obstacles of every unit) and their survivors
     s = Setup(crane, scene, N=n, K=K, S=S, grid_cell=0.5)
     try:
         lib.cp_set_endpoints(s.h, q0, qd)
@@ -272,8 +275,9 @@ def test_work_counters(lib, crane):
         lib.cp_set_timing(s.h, False)
     finally:
         s.close()
-    assert t["eval_obstacle_tests"] == -1
-    assert 0 < t["eval_pair_tests"] < 32 * 12 * got[0] // 20
+    assert t["eval_units"] == n * chunks
+    assert 0 < t["eval_obstacle_tests"] <= t["eval_box_tests"] < n * chunks * scene.n_cyl // 5
+    assert t["eval_pair_tests"] == 32 * 12 * t["eval_obstacle_tests"]
 
 
 def test_exhaustive_matches_oracle(lib, crane):
