@@ -146,12 +146,15 @@ def test_static_evaluation_staging_timeout_shows_in_results(lib):
 
 
 def test_static_evaluation_rejects_oversize(lib):
+    """A call whose work-item sums would not fit the fixed scratch is refused before any
+    launch, with a message that says how much it needs. The buffers passed are of the full
+    size, so that no path of the call could read or write outside them."""
     import torch
     from paper_2503_14160_gb300 import workloads
     model = lib.make_model(workloads.forestry_crane())
-    n, K, S = 200000, 32, 128             # partial sums alone would need ~2.5 GB
-    xi = torch.zeros(1, K, 4, device="cuda")
-    J = torch.zeros(1, dtype=torch.float64, device="cuda")
+    n, K, S = 1_200_000, 32, 128          # 1.2M items of 36 bytes: about 43 MB of item sums
+    xi = torch.zeros(n, K, 4, device="cuda")
+    J = torch.zeros(n, dtype=torch.float64, device="cuda")
     empty = torch.zeros(0, 5, dtype=torch.float64, device="cuda")
     with pytest.raises(lib.CranePlanError) as e:
         lib.cp_evaluate_static(model, empty, 0, empty, 0, K, S, 100.0, 100.0, 1.0,
