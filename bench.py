@@ -42,7 +42,8 @@ FLOPS_PER_PAIR = 5          # 2 sub, 1 mul, 1 fma per sphere-obstacle pair
 FLOPS_PER_CHECKPOINT = 140  # spline 32, kinematics ~80, length 12, limits 16
 FLOPS_FRAME_PER_SPHERE = 6  # broad phase: the sphere centre in the unit's frame (2 mul, 2 fma)
 FLOPS_PER_BROAD_TEST = 10   # broad phase: one obstacle against a unit's box
-FLOPS_PER_INDEX_TEST = 10   # polar index: one listed obstacle against a unit's box
+FLOPS_PER_INDEX_TEST = 8    # polar index: a listed obstacle in a lane's plane (p, q, bound)
+FLOPS_PER_PACKED_PAIR = 3   # polar index: one sphere's filter in the packed test (FP32x2 add + fma)
 FP32_PEAK_TFLOPS = PEAK_SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
 
 
@@ -53,19 +54,19 @@ def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, form, sm_mhz)
     obstacle whose pair test runs FLOPS_PER_PAIR. form "exhaustive": every obstacle of every
     unit is tested. "broad": every (unit, obstacle) takes one box test, each checkpoint
     places its spheres in the unit frame, and only the counted survivors take pair tests.
-    "polar": each checkpoint places its spheres in the unit frame, the obstacles listed in
-    the unit's cells of the polar index take one box test each (counted on the device), and
-    the counted survivors take pair tests."""
+    "polar": every obstacle listed for a checkpoint's slew angle and reach (counted on the
+    device) is placed in the checkpoint's plane and takes the filter for each sphere; pair
+    tests are those sphere filters."""
     units = timing["eval_units"]
     pairs = timing["eval_pair_tests"]
     if units <= 0 or pairs < 0 or timing["eval_ms"] <= 0:
         return None
-    flops = candidates * n_s * FLOPS_PER_CHECKPOINT + pairs * FLOPS_PER_PAIR
+    flops = candidates * n_s * FLOPS_PER_CHECKPOINT
+    flops += pairs * (FLOPS_PER_PACKED_PAIR if form == "polar" else FLOPS_PER_PAIR)
     if form == "broad":
         flops += candidates * n_s * n_spheres * FLOPS_FRAME_PER_SPHERE
         flops += units * n_obstacles * FLOPS_PER_BROAD_TEST
     elif form == "polar":
-        flops += candidates * n_s * n_spheres * FLOPS_FRAME_PER_SPHERE
         flops += max(timing.get("eval_box_tests", 0), 0) * FLOPS_PER_INDEX_TEST
     achieved = flops / (timing["eval_ms"] / 1e3) / 1e12
     kernel = {"broad": "k_eval_broad", "exhaustive": "k_eval", "polar": "k_eval_polar"}[form]
@@ -78,8 +79,8 @@ def eval_roofline(timing, n_spheres, n_obstacles, n_s, candidates, form, sm_mhz)
             "eval_ms_per_launch": timing["eval_ms"] / max(timing["eval_launches"], 1),
             "eval_launches": timing["eval_launches"],
             "pair_tests_per_checkpoint": pairs / max(candidates * n_s, 1),
-            "box_tests_per_unit": (timing["eval_box_tests"] / units
-                                   if timing.get("eval_box_tests", -1) >= 0 else None),
+            "listed_obstacles_per_checkpoint": (timing["eval_box_tests"] / max(candidates * n_s, 1)
+                                                if timing.get("eval_box_tests", -1) >= 0 else None),
             "pair_tests_exhaustive_per_checkpoint": n_spheres * n_obstacles}
 
 

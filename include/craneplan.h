@@ -118,11 +118,11 @@ typedef struct cp_params {
     int32_t max_cylinders;  /* capacity of the scene buffers (cp_set_scene); 0 = scene's */
     int32_t max_boxes;
     double grid_cell;       /* > 0: evaluate through a polar index of the obstacles about the
-                               slew axis (256 angular bins, rings of this width in m), which
-                               finds the obstacles near each 32 checkpoints of a candidate
-                               without scanning the scene (for large scenes); 0: scan every
-                               obstacle (broad phase or exhaustive). The results are the same
-                               bit for bit. */
+                               slew axis (256 angular bins, rings of this width in m), from
+                               which every checkpoint takes the obstacles near the vertical
+                               plane of its slew angle without scanning the scene (for large
+                               scenes); 0: scan every obstacle (broad phase or exhaustive). The
+                               results are the same bit for bit. */
     double grid_half_extent;/* outer radius of the index's last closed ring (m); obstacles
                                beyond it share one open ring. 0 = boom_len + jib_len +
                                max|q4 limit| + 4 */
@@ -194,13 +194,15 @@ typedef struct cp_timing {
     double factor_ms; int64_t factor_launches;
     double update_ms; int64_t update_launches;  /* rank, weights, mean, covariance */
     int64_t eval_units;           /* work units evaluated: candidates x ceil(n_s / 32) */
-    int64_t eval_obstacle_tests;  /* (unit, obstacle) pairs whose per-sphere test ran:
-                                     the broad-phase survivors, or every obstacle of every
-                                     unit in the exhaustive form (counted on the device
-                                     for the broad phase; -1 for the grid form) */
-    int64_t eval_pair_tests;      /* (checkpoint lane, sphere, obstacle) filter tests run:
-                                     32 x spheres x eval_obstacle_tests */
-    int64_t eval_box_tests;       /* (unit, obstacle) box tests run by the polar-index form
+    int64_t eval_obstacle_tests;  /* obstacles whose per-sphere filter passed somewhere: in the
+                                     broad-phase form the (unit, obstacle) survivors of the unit
+                                     box, in the exhaustive form every obstacle of every unit
+                                     (both per 32 lanes), in the polar-index form the (lane,
+                                     obstacle) pairs that passed (counted on the device) */
+    int64_t eval_pair_tests;      /* (checkpoint, sphere, obstacle) filter tests run: 32 x
+                                     spheres x eval_obstacle_tests, or, in the polar-index form,
+                                     spheres x eval_box_tests */
+    int64_t eval_box_tests;       /* (lane, listed obstacle) tests of the polar-index form
                                      (counted on the device; -1 for the other forms) */
 } cp_timing;
 

@@ -409,10 +409,11 @@ int stage_scene(cp_planner *p, const cp_scene *sc)
     for (int i = 0; i < sc->n_cyl; ++i) rmax_cyl = std::max(rmax_cyl, sc->cyl[i].radius);
     p->hull_reach_extra = (float)(std::max(0.0, rmax_cyl / std::cos(M_PI / 8.0) - rmax_cyl - (double)p->mdev.r_max) + 1e-3);
     if (p->use_grid) {
-        const int64_t need = polar_items_bound(sc, p->mdev.r_max, p->gdev.n_ang, p->gdev.n_ring, p->prm.grid_cell);
+        const int64_t need = polar_items_bound(sc, p->mdev.r_max, p->gdev.n_ang);
         if (need > p->grid_cap)
             return set_error("scene may need %lld index entries; capacity %lld (max_grid_items)",
                              (long long)need, (long long)p->grid_cap), CP_ERR_ARG;
+        p->gdev.w_max = polar_reach_max(sc, p->mdev.r_max);
         rc = launch_polar_build(p->sdev, p->gdev, p->grid_count, p->grid_cursor, p->grid_start, p->grid_items,
                                 p->status, p->st);
         if (rc != CP_OK) return rc;
@@ -629,8 +630,8 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->use_grid = params->grid_cell > 0.0;
     int64_t cells = 0;
     if (p->use_grid) {
-        // polar index: kPolarBins angular bins, rings of width grid_cell out to the window's
-        // half extent (the last ring open outwards)
+        // polar index: kPolarBins angular bins, rings of width grid_cell out to
+        // grid_half_extent (the last ring open outwards)
         const double h = params->grid_cell;
         double W = params->grid_half_extent;
         if (W <= 0.0)
@@ -648,7 +649,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
         p->gdev.inv_dr = (float)(1.0 / h);
         p->grid_cap = params->max_grid_items > 0
                           ? params->max_grid_items
-                          : polar_items_bound(scene, p->mdev.r_max, kPolarBins, (int)n_ring, h);
+                          : polar_items_bound(scene, p->mdev.r_max, kPolarBins);
         if (p->grid_cap < 1) p->grid_cap = 1;
     }
     const size_t eval_smem = p->use_grid ? 0 : eval_smem_bytes(p->cap_cyl, p->cap_box, p->S);
@@ -902,8 +903,8 @@ bool same_scene(const SceneDev &a, const SceneDev &b)
 bool same_grid(const PolarDev &a, const PolarDev &b)
 {
     return a.n_ang == b.n_ang && a.n_ring == b.n_ring && memcmp(&a.inv_da, &b.inv_da, sizeof(float)) == 0 &&
-           memcmp(&a.inv_dr, &b.inv_dr, sizeof(float)) == 0 && a.cell_start == b.cell_start && a.items == b.items &&
-           a.capacity == b.capacity;
+           memcmp(&a.inv_dr, &b.inv_dr, sizeof(float)) == 0 && memcmp(&a.w_max, &b.w_max, sizeof(float)) == 0 &&
+           a.cell_start == b.cell_start && a.items == b.items && a.capacity == b.capacity;
 }
 
 // The iterations of cp_plan from p->iteration as one CUDA graph launch, recorded on first
@@ -1250,8 +1251,11 @@ int cp_get_timing(cp_planner *p, cp_timing *out)
     CP_CUDA(cudaMemcpy(work, p->work, sizeof(work), cudaMemcpyDeviceToHost));
     out->eval_units = p->timer.units;
     out->eval_obstacle_tests = p->timer.tests + (int64_t)work[0];
-    out->eval_pair_tests = out->eval_obstacle_tests * 32 * p->mdev.n_spheres;
     out->eval_box_tests = p->timer.grid ? (int64_t)work[1] : -1;
+    // per-unit forms: every survivor takes the filter for 32 lanes x the spheres; the polar
+    // form: every listed obstacle of a lane takes it for the lane's spheres
+    out->eval_pair_tests = p->timer.grid ? out->eval_box_tests * p->mdev.n_spheres
+                                         : out->eval_obstacle_tests * 32 * p->mdev.n_spheres;
     p->timer.clear();
     CP_CUDA(cudaMemsetAsync(p->work, 0, 2 * sizeof(unsigned long long), p->st));
     CP_CUDA(cudaStreamSynchronize(p->st));

@@ -109,17 +109,22 @@ constexpr int kGroup = 8;    // cylinders per broad-phase group
 __host__ __device__ inline int n_groups(int n_cyl) { return (n_cyl + kGroup - 1) / kGroup; }
 
 // Polar index of the obstacles for large scenes. The plane around the slew axis is cut into
-// n_ang angular bins over [-pi, pi) and n_ring rings of width dr about the axis (the last ring
-// open outwards). Every obstacle is listed in each cell (bin, ring) that its reach disk (the
-// centre and the broad-phase reach of its record) overlaps, so that a sphere centre within
-// reach of an obstacle lies in a cell that lists it. Cells are stored bin-major: the rings
-// r0..r1 of one bin are one contiguous range of entries.
+// n_ang angular bins over [-pi, pi) and rings of width dr about the axis (the last ring open
+// outwards). Every obstacle is listed in each angular bin that its reach disk (the centre
+// and the broad-phase reach of its record) overlaps, in the ring of its centre; cells are
+// stored bin-major, so the rings r0..r1 of one bin are one contiguous range of entries. A
+// sphere at distance |h| from the axis can only reach obstacles of the bin of its angle whose
+// centre lies within w_max (the largest reach) of |h|.
 struct PolarDev {
     int n_ang, n_ring;
     float inv_da;            // n_ang / (2 pi)
     float inv_dr;            // 1 / dr
+    float w_max;             // largest reach of any obstacle record of the scene (m)
     const int *cell_start;   // [n_ang n_ring + 1]
-    const float4 *items;     // {cx, cy, id (int bits), reach}; id < n_cyl a cylinder, else box id - n_cyl
+    const float4 *items;     // {cx, cy, bound, id (int bits)}: bound = the square of the radius
+                             // within which a sphere centre can touch it ((R + r_max)^2 + margin
+                             // for a cylinder, (half diagonal + r_max + slack)^2 for a box);
+                             // id < n_cyl a cylinder, else box id - n_cyl
     int capacity;            // entries allocated: the build writes and the query reads no more
 };
 
@@ -209,7 +214,8 @@ size_t eval_smem_bytes(int n_cyl, int n_box, int S);
 int eval_configure(size_t smem_bytes);
 int eval_ensure_smem(size_t smem_bytes);
 
-int64_t polar_items_bound(const cp_scene *sc, double r_max, int n_ang, int n_ring, double dr);
+int64_t polar_items_bound(const cp_scene *sc, double r_max, int n_ang);
+float polar_reach_max(const cp_scene *sc, double r_max);
 int launch_polar_build(const SceneDev &sc, const PolarDev &g, int *count, int *cursor, int *start,
                        float4 *items, uint32_t *status, cudaStream_t st);
 int launch_eval_polar(const ModelDev &m, const SceneDev &sc, const PolarDev &g, const EvalArgs &a,

@@ -2,17 +2,18 @@
 // (Algorithm 1 step (2), d(q) of Sec. 3.1, arXiv 2503.14160).
 //
 // Every sphere of a configuration lies on the vertical plane at its slew angle, at signed
-// horizontal distance h from the slew axis; so the obstacles a work unit (32 checkpoints of
-// one candidate) can reach are those near the few slew angles and the range of |h| that its
-// spheres cover. The index cuts the plane into angular bins about the slew axis and rings
-// of width dr, and lists each obstacle in every (bin, ring) cell its reach disk (centre and
-// broad-phase reach) overlaps, bin-major, so that the rings r0..r1 of one bin are one
-// contiguous range. A unit takes the bins of its lanes' slew angles (and of the opposite
-// direction when some h is negative) and the rings of its in-band |h|, tests the listed
-// obstacles against its box in the slew frame (as the broad-phase form does), and takes
-// the survivors through the same per-sphere filter and exact distances. Every obstacle a
-// sphere can penetrate lies in a queried cell, passes the box test and the filter, so the
-// results equal the exhaustive form's bit for bit.
+// horizontal distance h from the slew axis. So the obstacles a checkpoint can touch are
+// those within reach of one half-line from the axis (two when some h is negative), over the
+// range of |h| its spheres cover. The index cuts the plane into angular bins about the slew
+// axis and lists each obstacle in every bin its reach disk overlaps, ordered by the ring
+// (of width dr) that holds its centre. A lane takes the bin of its slew angle and the rings
+// within the largest reach of its in-band |h|, and tests each listed obstacle against all
+// its spheres at once: the obstacle centre at p along the plane and q across it, sphere s
+// passes when (h_s - p)^2 + q^2 is below the obstacle's bound (two packed FP32x2 operations
+// per sphere pair); passing spheres take the exact distance. Every obstacle a sphere can
+// penetrate is listed in the bin of the sphere's angle, within the rings the lane takes, and
+// passes the test, and the exact distances are those of the exhaustive form, so the results
+// equal the exhaustive form's bit for bit.
 //
 // The index is built by kernels (count, exclusive scan, fill); the order inside a cell does
 // not matter because the kernel takes a minimum of exactly computed distances.
@@ -28,20 +29,20 @@ constexpr int kPolarThreads = 256;
 #define CP_POLAR_MIN_BLOCKS 3   // CTAs of 8 warps resident per SM (at most 80 registers)
 #endif
 constexpr int kCtrlSlots = CP_MAX_WAYPOINTS + 8;   // control points per warp, float4
-constexpr float kPolarPadR = 1e-3f;                // m: rounding of rho and of the ring index
+constexpr float kPolarPadR = 1e-3f;                // m: rounding of rho, |h| and the ring index
 constexpr float kPolarPadA = 1e-4f;                // rad: rounding of the angles and bin index
-constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTwoPiHi = 6.28318548202514648f;   // 2 pi = kTwoPiHi + kTwoPiLo (Cody-Waite)
+constexpr float kTwoPiLo = -1.7484555e-7f;
 
-// Cells of an obstacle record r = {cx, cy, ., reach}: bins a0 .. a0 + na - 1 (mod n_ang) and
-// rings r0 .. r1. A point within `reach` of the centre has |rho_p - rho| <= reach and, when
-// rho > reach, an angle within asin(reach / rho) of the centre's.
-__device__ __forceinline__ void polar_cells(const PolarDev &g, float4 r, int &a0, int &na, int &r0, int &r1)
+// Bins of an obstacle record r = {cx, cy, ., reach}: a0 .. a0 + na - 1 (mod n_ang), and the
+// ring of its centre. A point within `reach` of the centre has, when rho > reach, an angle
+// within asin(reach / rho) of the centre's; when rho <= reach every angle is possible.
+__device__ __forceinline__ void polar_cells(const PolarDev &g, float4 r, int &a0, int &na, int &ring)
 {
     const float rho = sqrtf(fmaf(r.x, r.x, r.y * r.y));
     const float w = r.w + kPolarPadR;
-    r0 = min(max((int)floorf((rho - w) * g.inv_dr), 0), g.n_ring - 1);
-    r1 = min(max((int)floorf((rho + w) * g.inv_dr), 0), g.n_ring - 1);
+    ring = min(max((int)floorf(rho * g.inv_dr), 0), g.n_ring - 1);
     if (rho <= w + kPolarPadR) {
         a0 = 0;
         na = g.n_ang;
@@ -60,23 +61,30 @@ __device__ __forceinline__ void polar_cells(const PolarDev &g, float4 r, int &a0
     }
 }
 
-// Record of obstacle id (cylinders first, then boxes): centre, id, broad-phase reach.
-__device__ __forceinline__ float4 polar_record(const SceneDev &sc, int id)
+// Entry of obstacle id (cylinders first, then boxes): centre, squared bound, id; and its
+// record for the cells (the centre and the broad-phase reach).
+__device__ __forceinline__ void polar_entry(const SceneDev &sc, int id, float4 &entry, float4 &cell_rec)
 {
-    const float4 f = id < sc.n_cyl ? sc.cyl_filt[id] : sc.box_c[id - sc.n_cyl];
-    return make_float4(f.x, f.y, __int_as_float(id), f.w);
+    if (id < sc.n_cyl) {
+        const float4 f = sc.cyl_filt[id], e = sc.cyl_exact[id];
+        entry = make_float4(f.x, f.y, e.w, __int_as_float(id));
+        cell_rec = f;
+    } else {
+        const float4 c = sc.box_c[id - sc.n_cyl];   // w: half diagonal + r_max + 1 cm
+        entry = make_float4(c.x, c.y, c.w * c.w, __int_as_float(id));
+        cell_rec = c;
+    }
 }
 
 __global__ void k_polar_count(const SceneDev sc, const PolarDev g, int *count)
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= sc.n_cyl + sc.n_box) return;
-    int a0, na, r0, r1;
-    polar_cells(g, polar_record(sc, id), a0, na, r0, r1);
-    for (int k = 0; k < na; ++k) {
-        const int a = (a0 + k) % g.n_ang;
-        for (int r = r0; r <= r1; ++r) atomicAdd(count + a * g.n_ring + r, 1);
-    }
+    float4 entry, rec;
+    polar_entry(sc, id, entry, rec);
+    int a0, na, ring;
+    polar_cells(g, rec, a0, na, ring);
+    for (int k = 0; k < na; ++k) atomicAdd(count + ((a0 + k) % g.n_ang) * g.n_ring + ring, 1);
 }
 
 // Exclusive scan of count[0..n) into start[0..n] (start[n] = total) in one CTA; cursor
@@ -110,40 +118,55 @@ __global__ void k_polar_fill(const SceneDev sc, const PolarDev g, int *cursor, f
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= sc.n_cyl + sc.n_box) return;
-    const float4 rec = polar_record(sc, id);
-    int a0, na, r0, r1;
-    polar_cells(g, rec, a0, na, r0, r1);
+    float4 entry, rec;
+    polar_entry(sc, id, entry, rec);
+    int a0, na, ring;
+    polar_cells(g, rec, a0, na, ring);
     for (int k = 0; k < na; ++k) {
-        const int a = (a0 + k) % g.n_ang;
-        for (int r = r0; r <= r1; ++r) {
-            const int at = atomicAdd(cursor + a * g.n_ring + r, 1);
-            if (at < g.capacity) items[at] = rec;
-            else if (status != nullptr) atomicOr(status, DEV_ERR_OVERFLOW);   // the host's bound was short
-        }
+        const int at = atomicAdd(cursor + ((a0 + k) % g.n_ang) * g.n_ring + ring, 1);
+        if (at < g.capacity) items[at] = entry;
+        else if (status != nullptr) atomicOr(status, DEV_ERR_OVERFLOW);   // the host's bound was short
     }
 }
 
-// A surviving cylinder (filter record f = {cx, cy, W, reach}, exact record e = {R, z_lo,
-// z_hi, (R + r_max)^2 + margin}) against the lane's spheres: with its centre at p along the
-// lane's plane and q across it, sphere s passes when (h_s - p)^2 < e.w - q^2 and its centre
-// lies within the cylinder's height range widened by r_max and the gate (so spheres outside
-// the scene's band never pass); the passing spheres take the exact distance from their
-// Cartesian centres, the same rounded products as every other form.
-template <int NSPH>
-__device__ __forceinline__ float polar_cylinder(const ModelDev &m, const float *H, const float *Z, float c1,
-                                                float s1, float4 f, float4 e)
+// Slew angle wrapped to [-pi, pi]: Cody-Waite reduction by 2 pi in two parts (accurate to a
+// few 1e-7 rad for |phi| below 2^14 rad), in FP64 beyond.
+__device__ __forceinline__ float wrap_angle(float phi)
 {
-    const float p = fmaf(c1, f.x, s1 * f.y);
-    const float q = fmaf(c1, f.y, -(s1 * f.x));
-    const float rhs = fmaf(-q, q, e.w);
-    const float zlo = e.y - m.r_max - kZGate, zhi = e.z + m.r_max + kZGate;
+    if (fabsf(phi) < 16384.f) {
+        const float k = rintf(phi * 0.159154943091895336f);
+        return fmaf(-k, kTwoPiLo, fmaf(-k, kTwoPiHi, phi));
+    }
+    const double d = (double)phi;
+    return (float)(d - 6.283185307179586477 * rint(d * 0.15915494309189533577));
+}
+
+// The exact distance of every sphere whose filter passes against listed obstacle `id` (the
+// spheres' Cartesian centres from the same rounded products as every other form; for a
+// cylinder only within its height range widened by r_max and the gate).
+template <int NSPH>
+__device__ __forceinline__ float polar_exact(const ModelDev &m, const SceneDev &sc, const float *H,
+                                             const float *Z, float c1, float s1, float p, float rhs, int id)
+{
     float d = CUDART_INF_F;
+    if (id < sc.n_cyl) {
+        const float4 f = __ldg(sc.cyl_filt + id), e = __ldg(sc.cyl_exact + id);
+        const float zlo = e.y - m.r_max - kZGate, zhi = e.z + m.r_max + kZGate;
 #pragma unroll
-    for (int s = 0; s < NSPH; ++s) {
-        const float dh = H[s] - p;
-        if (fmaf(dh, dh, -rhs) < 0.f && Z[s] > zlo && Z[s] < zhi)
-            d = fminf(d, sdf_cylinder(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], f.x, f.y, e) -
-                             m.sph[s].radius);
+        for (int s = 0; s < NSPH; ++s) {
+            const float dh = H[s] - p;
+            if (fmaf(dh, dh, -rhs) < 0.f && Z[s] > zlo && Z[s] < zhi)
+                d = fminf(d, sdf_cylinder(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], f.x, f.y, e) -
+                                 m.sph[s].radius);
+        }
+    } else {
+        const float4 bc = __ldg(sc.box_c + id - sc.n_cyl), bh = __ldg(sc.box_h + id - sc.n_cyl);
+#pragma unroll
+        for (int s = 0; s < NSPH; ++s) {
+            const float dh = H[s] - p;
+            if (fmaf(dh, dh, -rhs) < 0.f)
+                d = fminf(d, sdf_box(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s], bc, bh) - m.sph[s].radius);
+        }
     }
     return d;
 }
@@ -162,7 +185,8 @@ k_eval_polar(const ModelDev m, const SceneDev sc, const PolarDev g, const EvalAr
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     const int items = a.n * a.P;
     const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
-    uint32_t survivors = 0, tests = 0;
+    const float zero[NSPH] = {};
+    uint32_t survivors = 0, tests = 0;   // (lane, obstacle) pairs passing the packed filter; tested
 
     for (int it = warp; it < items; it += n_warps) {
         const ItemRange ir = item_range(a, it);
@@ -174,77 +198,62 @@ k_eval_polar(const ModelDev m, const SceneDev sc, const PolarDev g, const EvalAr
             float H[NSPH], Z[NSPH], s1, c1;
             crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
             // in-band extent of h at this lane; spheres outside the scene's height band (widened
-            // by r_max) can penetrate nothing and take no part
+            // by r_max) can penetrate nothing: they take no part (1e30 in the packed h)
             float hmin, hmax;
             band_extent<NSPH>(H, Z, zlo, zhi, hmin, hmax);
-            const bool any_in = hmin <= hmax;
             float dmin = CUDART_INF_F;
-            if (__any_sync(0xffffffffu, any_in)) {
-                // the unit box (a lane with no in-band sphere adds its first sphere: a larger box
-                // is still a bound)
-                const float hb[2] = {any_in ? hmin : H[0], any_in ? hmax : H[0]};
-                const UnitFrame fr = unit_frame<2>(s1, c1, hb);
-                // radial extents on each side of the slew axis, and the spread of slew angles
-                const float p_lo = warp_min(any_in && hmax >= 0.f ? fmaxf(hmin, 0.f) : CUDART_INF_F);
-                const float p_hi = warp_max(any_in && hmax >= 0.f ? hmax : -CUDART_INF_F);
-                const float n_lo = warp_min(any_in && hmin < 0.f ? fmaxf(-hmax, 0.f) : CUDART_INF_F);
-                const float n_hi = warp_max(any_in && hmin < 0.f ? -hmin : -CUDART_INF_F);
-                const float phi16 = __shfl_sync(0xffffffffu, c.q.x, 16);
-                const float dphi = warp_max(any_in ? fabsf(c.q.x - phi16) : 0.f);
-                const float phi0 = phi16 - kTwoPi * rintf(phi16 * (1.f / kTwoPi));   // in [-pi, pi]
-                const float pad = kPolarPadA + 4e-7f * fabsf(phi16);
+            if (hmin <= hmax) {
+                float2 H2[NSPH / 2];
+#pragma unroll
+                for (int q = 0; q < NSPH / 2; ++q)
+                    H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
+                                        Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
+                const float phi0 = wrap_angle(c.q.x);
 #pragma unroll 1
                 for (int side = 0; side < 2; ++side) {
-                    const float r_lo = side ? n_lo : p_lo, r_hi = side ? n_hi : p_hi;
+                    // spheres with h >= 0 lie on the half-line at the slew angle, those with h < 0
+                    // on the opposite one, at distance |h| from the axis
+                    const float r_lo = side ? fmaxf(-hmax, 0.f) : fmaxf(hmin, 0.f);
+                    const float r_hi = side ? -hmin : hmax;
                     if (!(r_lo <= r_hi)) continue;
-                    const float centre = side ? (phi0 >= 0.f ? phi0 - kPi : phi0 + kPi) : phi0;
-                    int a0 = (int)floorf((centre - dphi - pad + kPi) * g.inv_da);
-                    int na = (int)floorf((centre + dphi + pad + kPi) * g.inv_da) - a0 + 1;
-                    if (dphi + pad >= kPi || na >= g.n_ang) {
-                        a0 = 0;
-                        na = g.n_ang;
-                    }
-                    a0 = ((a0 % g.n_ang) + g.n_ang) % g.n_ang;
-                    const int r0 = min(max((int)floorf((r_lo - kPolarPadR) * g.inv_dr), 0), g.n_ring - 1);
-                    const int r1 = min(max((int)floorf((r_hi + kPolarPadR) * g.inv_dr), 0), g.n_ring - 1);
-#pragma unroll 1
-                    for (int k = 0; k < na; ++k) {
-                        const int cell = ((a0 + k) % g.n_ang) * g.n_ring;
-                        const int beg = __ldg(g.cell_start + cell + r0);
-                        const int end = min(__ldg(g.cell_start + cell + r1 + 1), g.capacity);
-                        for (int e0 = beg; e0 < end; e0 += 32) {
-                            const int e = e0 + lane;
-                            const float4 rec = e < end ? __ldg(g.items + e) : make_float4(0.f, 0.f, 0.f, -1.f);
-                            uint32_t mask = __ballot_sync(0xffffffffu, e < end && unit_near(fr, rec));
-                            tests += (uint32_t)min(32, end - e0);
-                            survivors += __popc(mask);
-                            while (mask) {
-                                const int id = __shfl_sync(0xffffffffu, __float_as_int(rec.z), __ffs(mask) - 1);
-                                mask &= mask - 1;
-                                if (id < sc.n_cyl) {
-                                    dmin = fminf(dmin, polar_cylinder<NSPH>(m, H, Z, c1, s1,
-                                                                            __ldg(sc.cyl_filt + id),
-                                                                            __ldg(sc.cyl_exact + id)));
-                                } else {
-                                    const float4 bc = __ldg(sc.box_c + id - sc.n_cyl);
-                                    const float4 bh = __ldg(sc.box_h + id - sc.n_cyl);
+                    const float ang = side ? (phi0 >= 0.f ? phi0 - kPi : phi0 + kPi) : phi0;
+                    const int bin = min(max((int)floorf((ang + kPi) * g.inv_da), 0), g.n_ang - 1);
+                    const float reach = g.w_max + kPolarPadR;
+                    const int r0 = min(max((int)floorf((r_lo - reach) * g.inv_dr), 0), g.n_ring - 1);
+                    const int r1 = min(max((int)floorf((r_hi + reach) * g.inv_dr), 0), g.n_ring - 1);
+                    const int cell = bin * g.n_ring;
+                    const int beg = __ldg(g.cell_start + cell + r0);
+                    const int end = min(__ldg(g.cell_start + cell + r1 + 1), g.capacity);
+                    tests += (uint32_t)max(end - beg, 0);
+                    for (int e = beg; e < end; ++e) {
+                        const float4 rec = __ldg(g.items + e);   // {cx, cy, bound, id}
+                        const float p = fmaf(c1, rec.x, s1 * rec.y);
+                        const float q = fmaf(c1, rec.y, -(s1 * rec.x));
+                        const float rhs = fmaf(-q, q, rec.z);
+                        const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
+                        float2 t[NSPH / 2];
 #pragma unroll
-                                    for (int s = 0; s < NSPH; ++s)
-                                        dmin = fminf(dmin, sdf_box(__fmul_rn(c1, H[s]), __fmul_rn(s1, H[s]), Z[s],
-                                                                   bc, bh) - m.sph[s].radius);
-                                }
-                            }
+                        for (int k = 0; k < NSPH / 2; ++k) {
+                            const float2 dh = __fadd2_rn(H2[k], mp2);
+                            t[k] = __ffma2_rn(dh, dh, mr2);
+                        }
+                        if (any_below<NSPH>(t, zero)) {
+                            ++survivors;
+                            dmin = fminf(dmin, polar_exact<NSPH>(m, sc, H, Z, c1, s1, p, rhs, __float_as_int(rec.w)));
                         }
                     }
                 }
             }
+            __syncwarp();
             unit_accumulate(a, c, dmin, ir.cand, chunk, lane, acc, count);
         }
         item_flush(a, it, acc, count, lane);
     }
-    if (a.work != nullptr && lane == 0) {
-        if (survivors != 0) atomicAdd(a.work, (unsigned long long)survivors);
-        if (tests != 0) atomicAdd(a.work + 1, (unsigned long long)tests);
+    if (a.work != nullptr) {
+        const uint32_t ws = __reduce_add_sync(0xffffffffu, survivors);
+        const uint32_t wt = __reduce_add_sync(0xffffffffu, tests);
+        if (lane == 0 && ws != 0) atomicAdd(a.work, (unsigned long long)ws);
+        if (lane == 0 && wt != 0) atomicAdd(a.work + 1, (unsigned long long)wt);
     }
 }
 
@@ -259,39 +268,51 @@ cudaError_t raise_polar_smem(F *fn, size_t smem)
     return e;
 }
 
+// Broad-phase reach of the device records (k_prepare_scene), in FP64.
+double cylinder_reach(const cp_cylinder &c, double r_max)
+{
+    const double reach = c.radius + r_max;
+    return std::sqrt(reach * reach + 0.01) + 0.01;
+}
+
+double box_reach(const cp_box &b, double r_max)
+{
+    const double hx = 0.5 * (b.hi[0] - b.lo[0]), hy = 0.5 * (b.hi[1] - b.lo[1]);
+    return std::sqrt(hx * hx + hy * hy) + r_max + 0.01;
+}
+
 }  // namespace
 
 // Upper bound on the entries of the index for a scene: per obstacle the bins of its angular
-// half width asin(reach / rho) (all bins when it covers the axis) times the rings of its
-// radial extent, each rounded up by two for the rounding of the device's cell ranges.
-int64_t polar_items_bound(const cp_scene *sc, double r_max, int n_ang, int n_ring, double dr)
+// half width asin(reach / rho) (all bins when it covers the axis), rounded up by three for
+// the padding and the rounding of the device's bin range.
+int64_t polar_items_bound(const cp_scene *sc, double r_max, int n_ang)
 {
     const double da = 2.0 * M_PI / n_ang;
-    auto cells = [&](double cx, double cy, double reach) -> int64_t {
+    auto bins = [&](double cx, double cy, double reach) -> int64_t {
         const double rho = std::sqrt(cx * cx + cy * cy);
         const double w = reach + 2.0 * (double)kPolarPadR + 0.02;
-        int64_t rings = (int64_t)std::floor(2.0 * w / dr) + 3;
-        if (rings > n_ring) rings = n_ring;
-        int64_t bins = n_ang;
-        if (rho > w + 0.01) {
-            const double alpha = std::asin(std::min(1.0, w / (rho - 0.01))) * 1.001 + 2e-4;
-            bins = std::min<int64_t>(n_ang, (int64_t)std::floor(2.0 * alpha / da) + 3);
-        }
-        return rings * bins;
+        if (rho <= w + 0.01) return n_ang;
+        const double alpha = std::asin(std::min(1.0, w / (rho - 0.01))) * 1.001 + 2e-4;
+        return std::min<int64_t>(n_ang, (int64_t)std::floor(2.0 * alpha / da) + 3);
     };
     int64_t total = 0;
-    for (int i = 0; i < sc->n_cyl; ++i) {
-        const cp_cylinder &c = sc->cyl[i];
-        const double reach = std::sqrt((c.radius + r_max) * (c.radius + r_max) + 0.01) + 0.01;
-        total += cells(c.cx, c.cy, reach);
-    }
+    for (int i = 0; i < sc->n_cyl; ++i) total += bins(sc->cyl[i].cx, sc->cyl[i].cy, cylinder_reach(sc->cyl[i], r_max));
     for (int i = 0; i < sc->n_box; ++i) {
         const cp_box &b = sc->box[i];
-        const double hx = 0.5 * (b.hi[0] - b.lo[0]), hy = 0.5 * (b.hi[1] - b.lo[1]);
-        const double reach = std::sqrt(hx * hx + hy * hy) + r_max + 0.01;
-        total += cells(0.5 * (b.lo[0] + b.hi[0]), 0.5 * (b.lo[1] + b.hi[1]), reach);
+        total += bins(0.5 * (b.lo[0] + b.hi[0]), 0.5 * (b.lo[1] + b.hi[1]), box_reach(b, r_max));
     }
     return total;
+}
+
+// The largest broad-phase reach of the scene's records, rounded up past the FP32 rounding
+// of the records themselves.
+float polar_reach_max(const cp_scene *sc, double r_max)
+{
+    double w = 0.0;
+    for (int i = 0; i < sc->n_cyl; ++i) w = std::max(w, cylinder_reach(sc->cyl[i], r_max));
+    for (int i = 0; i < sc->n_box; ++i) w = std::max(w, box_reach(sc->box[i], r_max));
+    return (float)(w * (1.0 + 1e-5) + 1e-4);
 }
 
 int launch_polar_build(const SceneDev &sc, const PolarDev &g, int *count, int *cursor, int *start,

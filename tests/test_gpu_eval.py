@@ -264,8 +264,8 @@ def test_work_counters(lib, crane):
         got.append(t["eval_obstacle_tests"])
     assert got[0] == 2 * n * chunks * scene.n_cyl
     assert 0 < got[1] < got[0] // 10
-    # polar-index form: the box tests of the listed obstacles (a small fraction of the
-    # obstacles of every unit) and their survivors
+    # polar-index form: the obstacles listed for each checkpoint (a small fraction of the
+    # scene) and those whose filter passed
     s = Setup(crane, scene, N=n, K=K, S=S, grid_cell=0.5)
     try:
         lib.cp_set_endpoints(s.h, q0, qd)
@@ -275,9 +275,10 @@ def test_work_counters(lib, crane):
         lib.cp_set_timing(s.h, False)
     finally:
         s.close()
+    n_s = (K + 3) * S
     assert t["eval_units"] == n * chunks
-    assert 0 < t["eval_obstacle_tests"] <= t["eval_box_tests"] < n * chunks * scene.n_cyl // 5
-    assert t["eval_pair_tests"] == 32 * 12 * t["eval_obstacle_tests"]
+    assert 0 < t["eval_obstacle_tests"] <= t["eval_box_tests"] < n * n_s * scene.n_cyl // 20
+    assert t["eval_pair_tests"] == 12 * t["eval_box_tests"]
 
 
 def test_exhaustive_matches_oracle(lib, crane):
