@@ -77,17 +77,41 @@ static __device__ __forceinline__ float3 sdf_box_grad(float x, float y, float z,
     return make_float3(0.f, 0.f, sz);
 }
 
+// Sine and cosine of an angle for the kinematics: the angle reduced to [-pi, pi] by 2 pi in
+// two parts (Cody and Waite's additive reduction; 2 pi = 6.28318548202514648 - 1.7484555e-7,
+// both parts exact in FP32, so the reduced angle is within a few 1e-7 rad of the true one for
+// |x| < 2^14, far beyond any joint angle the search draws), then the hardware sine and cosine,
+// whose absolute error on [-pi, pi] is below 2^-21.4 (3.6e-7). Over the crane's levers (at
+// most about 10.5 m) that moves a sphere centre by under 1e-5 m, within the 2e-5 m to which
+// the distances are checked against the FP64 oracle; the accurate library sincosf costs
+// several times the instructions on this hottest path.
+static __device__ __forceinline__ void sincos_reduced(float x, float *s, float *c)
+{
+    const float k = rintf(x * 0.159154943091895336f);
+    const float r = fmaf(k, 1.7484555e-7f, fmaf(-k, 6.28318548202514648f, x));
+    __sincosf(r, s, c);
+}
+
 // Sphere centres at configuration q (chain of Sec. 2 in the linear placement form), in
 // polar form: every centre is (c1 h, s1 h, z) with (c1, s1) the cosine and sine of the slew
 // angle and h the signed horizontal distance from the slew axis.
-template <int NSPH>
+// kFastTrig: the reduced hardware sine and cosine above (the evaluation forms, which must all
+// agree bit for bit); otherwise the accurate library sincosf (the forward-kinematics entry
+// point and the smooth cost, whose softplus penalty is checked to 1e-4 relative).
+template <int NSPH, bool kFastTrig = true>
 static __device__ __forceinline__ void crane_fk_polar(const ModelDev &m, float4 q, float *h, float *z,
                                                float &s1, float &c1)
 {
     float s2, c2, s23, c23;
-    sincosf(q.x, &s1, &c1);
-    sincosf(q.y, &s2, &c2);
-    sincosf(q.y + q.z, &s23, &c23);
+    if (kFastTrig) {
+        sincos_reduced(q.x, &s1, &c1);
+        sincos_reduced(q.y, &s2, &c2);
+        sincos_reduced(q.y + q.z, &s23, &c23);
+    } else {
+        sincosf(q.x, &s1, &c1);
+        sincosf(q.y, &s2, &c2);
+        sincosf(q.y + q.z, &s23, &c23);
+    }
 #pragma unroll
     for (int s = 0; s < NSPH; ++s) {
         const SphereLin sp = m.sph[s];
@@ -98,12 +122,12 @@ static __device__ __forceinline__ void crane_fk_polar(const ModelDev &m, float4 
 }
 
 // The same centres in Cartesian form, x = c1 h and y = s1 h.
-template <int NSPH>
+template <int NSPH, bool kFastTrig = true>
 static __device__ __forceinline__ void crane_fk(const ModelDev &m, float4 q, float *x, float *y,
                                          float *z)
 {
     float s1, c1;
-    crane_fk_polar<NSPH>(m, q, x, z, s1, c1);
+    crane_fk_polar<NSPH, kFastTrig>(m, q, x, z, s1, c1);
 #pragma unroll
     for (int s = 0; s < NSPH; ++s) {
         const float h = x[s];

@@ -372,7 +372,7 @@ __global__ void k_forward_kinematics(const ModelDev m, const float4 *__restrict_
     if (i >= n) return;
     const float4 qi = q[i];
     float x[NSPH], y[NSPH], z[NSPH];
-    crane_fk<NSPH>(m, qi, x, y, z);
+    crane_fk<NSPH, false>(m, qi, x, y, z);
     if (centres != nullptr) {
         float *c = centres + (size_t)i * m.n_spheres * 3;
 #pragma unroll

@@ -130,7 +130,7 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
                              limit_excess(q.z, m.q_min[2], m.q_max[2]) + limit_excess(q.w, m.q_min[3], m.q_max[3]);
 
             float X[NSPH], Y[NSPH], Z[NSPH], T[NSPH], s1, c1;
-            crane_fk_polar<NSPH>(m, q, X, Z, s1, c1);
+            crane_fk_polar<NSPH, false>(m, q, X, Z, s1, c1);
             // broad phase of the chunk: the box of its spheres in the slew frame, dilated by
             // the softplus range m + cut beta beyond the obstacles' contact reach
             // spheres farther below or above every obstacle than the softplus range reaches
