@@ -217,9 +217,10 @@ SENSITIVITY_NOISE = ((4e-6, 101), (1e-6, 202))
 STABLE = 1e-4
 
 
-def test_free_running_every_seed_elites(lib, crane):
+@pytest.mark.parametrize("sampler", ["factor", "elites"])
+def test_free_running_every_seed(lib, crane, sampler):
     """The plain single query (N=256, K=8, S=32, 20 trees, 50 iterations) free-running with
-    the factor-free sampler, on every seed 0..11. The search is sensitive to its rank
+    the factor sampler and with the factor-free one, on every seed 0..11. The search is sensitive to its rank
     decisions: the oracle's own plan, with its costs perturbed by the size of an FP32
     evaluation error, often ends elsewhere (a different local optimum). So, per seed: the
     oracle's sensitivity is measured (its plan under the perturbations of SENSITIVITY_NOISE);
@@ -234,14 +235,14 @@ def test_free_running_every_seed_elites(lib, crane):
     scene = workloads.make_scene(workloads.WORKLOADS["single_small"])
     rows = []
     for seed in range(12):
-        s = Setup(crane, scene, N=256, K=8, S=32, seed=seed, sampler=1)
+        s = Setup(crane, scene, N=256, K=8, S=32, seed=seed, sampler=int(sampler == "elites"))
         o = s.oracle
         try:
             lib.cp_set_endpoints(s.h, q0, qd)
             ctrl, st = lib.cp_plan(s.h, 50, K=8)
-            res = o.plan(s.problem, s.sp, q0, qd, 50, sampler="elites")
+            res = o.plan(s.problem, s.sp, q0, qd, 50, sampler=sampler)
             L_o = res.final.length[0]
-            sens = max(abs(o.plan(s.problem, s.sp, q0, qd, 50, sampler="elites",
+            sens = max(abs(o.plan(s.problem, s.sp, q0, qd, 50, sampler=sampler,
                                   cost_noise=noise).final.length[0] - L_o) / L_o
                        for noise in SENSITIVITY_NOISE)
             mean_g = ctrl[4:12].astype(np.float32).astype(np.float64)[None]
@@ -256,7 +257,7 @@ def test_free_running_every_seed_elites(lib, crane):
                 assert st["flag"] == res.final.flag[0], seed
         finally:
             s.close()
-    print("seed, |L_gpu - L_oracle| / L, oracle sensitivity, flag gpu, flag oracle")
+    print(sampler, "sampler: seed, |L_gpu - L_oracle| / L, oracle sensitivity, flag gpu, flag oracle")
     for r in rows:
         print("%2d  %.2e  %.2e  %d %d" % r)
     dev, sens = np.array([r[1] for r in rows]), np.array([r[2] for r in rows])
