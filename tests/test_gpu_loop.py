@@ -211,9 +211,11 @@ def test_teacher_forced_dense_forest(lib, crane):
         s.close()
 
 
-# Relative cost errors of the oracle's sensitivity runs: the GPU's FP32 costs differ from the
-# FP64 ones by a few 1e-6 relative (median 4e-6 on the dense forest's candidates).
-SENSITIVITY_NOISE = ((4e-6, 101), (1e-6, 202))
+# Relative cost errors of the oracle's sensitivity runs. The GPU's FP32 costs differ from the
+# FP64 ones by a few 1e-6 relative away from contact (median 4e-6 on the dense forest's
+# candidates) and by up to w_c x the FP32 distance error per checkpoint in contact, which is
+# up to 1e-4 relative on these costs; one run at each scale.
+SENSITIVITY_NOISE = ((4e-6, 101), (3e-5, 202), (1e-4, 303))
 STABLE = 1e-4
 
 
