@@ -180,8 +180,10 @@ KERNEL_SOURCES = {
 # kernel's sources at the time of the capture: reported only while the sources still hash
 # to it, None once the kernel has changed.
 PROFILED_TRAFFIC = {
-    "k_eval_broad": {"sha1": "ad26a635ca0cb88579d455974d6ff7926d689a2f", "bytes": 1113344.0,
+    "k_eval_broad": {"sha1": "457bb6563f6b94b1372e94ddf7a49e9cbb97fa18", "bytes": 1104384.0,
                      "workload": "single_large"},
+    "k_eval_polar": {"sha1": "51a7865ac840a7f71b7e762bd4de651257b30453", "bytes": 33661440.0,
+                     "workload": "dense_forest"},
 }
 
 
