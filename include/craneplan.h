@@ -456,6 +456,76 @@ cp_planner *cp_batch_planner(cp_batch *b, int32_t q);
 /* Release the batch, its planners, streams and graph. NULL is ignored. */
 void cp_batch_destroy(cp_batch *b);
 
+/* ------------------------------------------------------------------ trajectory step */
+
+/* Trajectory tracking optimisation of Sec. 4.2 (Eq. discrete), batched: each planned path
+ * q*(s) becomes a near-time-optimal trajectory by trapezoidal direct collocation on N
+ * intervals,
+ *   min  t_F + omega_s sum_{k=1..N} u_k^T R u_k + omega_t sum_{k=1..N} |q_a,k - q*(k/N)|^2
+ *   s.t. x_{k+1} - x_k = h/2 (f(x_k, u_k) + f(x_{k+1}, u_{k+1})),  h = t_F / N,
+ *        x_0 = (q*(0), 0), x_N = (q*(1), 0),  x_min <= x_k <= x_max.
+ * The model f has the structure of Sec. 2.1 with synthetic parameters (the paper gives none):
+ * x = (q1..q4, alpha, beta, dq1..dq4, dalpha, dbeta), u = (ddq1..ddq4): the actuated joints
+ * driven through their accelerations (subordinate velocity controllers), and the grapple's
+ * two passive swing angles, a point mass on a rigid link of length grapple_len under the tip
+ * (plumb at alpha = beta = 0, direction (sin a, cos a sin b, -cos a cos b)), whose
+ * accelerations follow from the pendulum's Euler-Lagrange equations with the tip's
+ * acceleration. Bounds: the cp_model joint limits, |dq_j| <= dq_max[j], |alpha|, |beta| <=
+ * swing_max. Solver (the paper uses IPOPT): augmented Lagrangian on the equalities
+ * (multipliers updated `outer` times, lambda += rho c), quadratic penalty rho_b on the bounds,
+ * `inner` Levenberg-Marquardt steps (J^T J + mu (diag J^T J + 1e-9)) dz = -(e_t + J^T r) per
+ * update, a step kept when t_F + 1/2 |r|^2 decreases (mu / 3, else mu * 4, from mu0). FP64.
+ * The variables of one trajectory are z = (t_F, w_0, ..., w_N), w_k = (x_k, u_k): 1 + 16 (N+1)
+ * doubles. */
+typedef struct cp_traj_params {
+    int32_t N;            /* collocation intervals, 2..255 */
+    double omega_s;       /* effort weight */
+    double omega_t;       /* tracking weight */
+    double R[4];          /* diagonal of R (>= 0) */
+    double dq_max[4];     /* velocity limits of q1..q4 (> 0; rad/s, m/s) */
+    double swing_max;     /* bound of the swing angles (rad, 0 < swing_max < 1.5) */
+    double grapple_len;   /* link length of the grapple pendulum (m, > 0) */
+    double rho;           /* augmented-Lagrangian weight (> 0) */
+    double rho_b;         /* bound-penalty weight (>= 0) */
+    int32_t outer;        /* multiplier updates */
+    int32_t inner;        /* Levenberg-Marquardt steps per update */
+    double mu0;           /* initial damping (> 0) */
+} cp_traj_params;
+
+typedef struct cp_traj cp_traj;
+
+/* Create a batched trajectory solver on the current device for up to max_paths trajectories:
+ * validates, allocates its workspace (about 5 KB per grid point per trajectory) and keeps the
+ * stream. Errors: CP_ERR_ARG, CP_ERR_CUDA. */
+int cp_traj_init(const cp_model *model, const cp_traj_params *tp, int32_t max_paths, void *stream,
+                 cp_traj **out);
+
+/* Release the solver (synchronises its stream first). NULL is ignored. */
+void cp_traj_destroy(cp_traj *t);
+
+/* The targets q*(k / N), k = 0..N, of n planned paths given by their control points d_ctrl
+ * (double[n][K+8][4], the layout cp_plan returns): the cubic B-spline of Sec. 4.1 on the K + 3
+ * moving spans. d_q_star receives double[n][N+1][4]. Errors: CP_ERR_ARG. */
+int cp_traj_targets(cp_traj *t, const double *d_ctrl, int32_t K, int32_t n, double *d_q_star);
+
+/* The solver's starting point from the targets: q_a = q*_k, velocities by central differences
+ * and inputs by second differences over t_F, the swing at rest, t_F = 1.5 x the largest
+ * (total variation of a joint over its velocity limit). d_z receives double[n][1 + 16 (N+1)].
+ * Errors: CP_ERR_ARG. */
+int cp_traj_initial_guess(cp_traj *t, const double *d_q_star, int32_t n, double *d_z);
+
+/* One Levenberg-Marquardt step dz (double[n][1 + 16 (N+1)]) at z with multipliers d_lam
+ * (double[n][12 (N+2)]: the N defects, then the start and end states) and damping mu, without
+ * acceptance (for tests and diagnostics). Errors: CP_ERR_ARG. */
+int cp_traj_step(cp_traj *t, const double *d_q_star, int32_t n, const double *d_z, const double *d_lam,
+                 double mu, double *d_dz);
+
+/* Solve the n trajectories from their starting points d_z (updated in place to the result).
+ * d_stats receives double[n][4]: t_F, the final objective t_F + 1/2 |r|^2, the largest
+ * equality-constraint error and the largest bound violation. Asynchronous on the solver's
+ * stream. Errors: CP_ERR_ARG. */
+int cp_traj_solve(cp_traj *t, const double *d_q_star, int32_t n, double *d_z, double *d_stats);
+
 /* Size of the fixed device scratch behind cp_evaluate_static (bytes, per GPU). */
 #define CP_STATIC_SCRATCH_BYTES (32u << 20)
 

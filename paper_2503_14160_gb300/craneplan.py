@@ -108,6 +108,22 @@ class cp_hull_model(ctypes.Structure):
                 ("grapple_w", ctypes.c_double), ("grapple_len", ctypes.c_double)]
 
 
+class cp_traj_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("omega_s", ctypes.c_double), ("omega_t", ctypes.c_double),
+                ("R", ctypes.c_double * 4), ("dq_max", ctypes.c_double * 4), ("swing_max", ctypes.c_double),
+                ("grapple_len", ctypes.c_double), ("rho", ctypes.c_double), ("rho_b", ctypes.c_double),
+                ("outer", ctypes.c_int32), ("inner", ctypes.c_int32), ("mu0", ctypes.c_double)]
+
+
+def make_traj_params(N: int = 100, omega_s: float = 1e-2, omega_t: float = 1e2, R=(1.0, 1.0, 1.0, 1.0),
+                     dq_max=(0.6, 0.3, 0.3, 0.5), swing_max: float = 0.6, grapple_len: float = 1.0,
+                     rho: float = 3e3, rho_b: float = 1e5, outer: int = 8, inner: int = 10,
+                     mu0: float = 1e-3) -> "cp_traj_params":
+    return cp_traj_params(int(N), float(omega_s), float(omega_t), (ctypes.c_double * 4)(*R),
+                          (ctypes.c_double * 4)(*dq_max), float(swing_max), float(grapple_len), float(rho),
+                          float(rho_b), int(outer), int(inner), float(mu0))
+
+
 class cp_ik_params(ctypes.Structure):
     _fields_ = [("lambda_q", ctypes.c_double), ("lambda_c", ctypes.c_double),
                 ("grapple_len", ctypes.c_double), ("mu0", ctypes.c_double),
@@ -168,6 +184,13 @@ _SIGS = {
     "cp_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cp_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(cp_timing)]),
     "cp_alu_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "cp_traj_init": (ctypes.c_int, [ctypes.POINTER(cp_model), ctypes.POINTER(cp_traj_params), ctypes.c_int32, _P,
+                                    ctypes.POINTER(_P)]),
+    "cp_traj_destroy": (None, [_P]),
+    "cp_traj_targets": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "cp_traj_initial_guess": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "cp_traj_step": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, ctypes.c_double, _P]),
+    "cp_traj_solve": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P]),
 }
 
 _lib = None
@@ -476,6 +499,34 @@ def cp_get_timing(p: int) -> dict:
     t = cp_timing()
     _check(load().cp_get_timing(p, ctypes.byref(t)))
     return {f: getattr(t, f) for f, _ in cp_timing._fields_}
+
+
+def cp_traj_init(model: cp_model, tp: cp_traj_params, max_paths: int, stream=None) -> int:
+    """Returns the trajectory solver handle (an opaque pointer as int)."""
+    out = _P()
+    _check(load().cp_traj_init(ctypes.byref(model), ctypes.byref(tp), int(max_paths), _stream(stream),
+                               ctypes.byref(out)))
+    return out.value
+
+
+def cp_traj_destroy(t: int) -> None:
+    load().cp_traj_destroy(t)
+
+
+def cp_traj_targets(t: int, ctrl, K: int, n: int, q_star) -> None:
+    _check(load().cp_traj_targets(t, _ptr(ctrl), int(K), int(n), _ptr(q_star)))
+
+
+def cp_traj_initial_guess(t: int, q_star, n: int, z) -> None:
+    _check(load().cp_traj_initial_guess(t, _ptr(q_star), int(n), _ptr(z)))
+
+
+def cp_traj_step(t: int, q_star, n: int, z, lam, mu: float, dz) -> None:
+    _check(load().cp_traj_step(t, _ptr(q_star), int(n), _ptr(z), _ptr(lam), float(mu), _ptr(dz)))
+
+
+def cp_traj_solve(t: int, q_star, n: int, z, stats) -> None:
+    _check(load().cp_traj_solve(t, _ptr(q_star), int(n), _ptr(z), _ptr(stats)))
 
 
 def cp_alu_peaks() -> dict:

@@ -1,0 +1,219 @@
+"""GPU parity of the trajectory tracking optimisation (Sec. 4.2, Eq. discrete) with the FP64
+oracle (oracle/trajopt.py): the path targets from control points, the starting point, one
+Levenberg-Marquardt step from the same state (teacher-forced: the GPU's block-tridiagonal
+solve against the oracle's dense solve with complex-step Jacobians), and whole solves; at the
+paper's grid size (N = 100) one step against the oracle and the feasibility of whole solves."""
+import numpy as np
+import pytest
+
+from helpers import endpoints
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2503_14160_gb300 import build, craneplan
+    build.build()
+    craneplan.load()
+    return craneplan
+
+
+@pytest.fixture(scope="module")
+def crane():
+    from paper_2503_14160_gb300 import workloads
+    return workloads.forestry_crane()
+
+
+def _paths(n, K, seed):
+    """Control points [n][K+8][4] of paths between drawn end points (not collision-checked:
+    the trajectory step only tracks them)."""
+    g = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        q0 = np.array([g.uniform(-2, 2), g.uniform(0.0, 1.0), g.uniform(-2.0, -0.6), g.uniform(0.3, 2.0)])
+        qd = np.array([g.uniform(-2, 2), g.uniform(0.0, 1.0), g.uniform(-2.0, -0.6), g.uniform(0.3, 2.0)])
+        f = (np.arange(1, K + 1) / (K + 1))[:, None]
+        mid = q0[None] + f * (qd - q0)[None] + g.normal(size=(K, 4)) * np.array([0.2, 0.05, 0.05, 0.1])
+        out.append(np.concatenate([np.tile(q0, (4, 1)), mid, np.tile(qd, (4, 1))]))
+    return np.stack(out)
+
+
+class _Solver:
+    def __init__(self, lib, crane, N, n, **kw):
+        import trajopt
+        self.lib, self.N, self.n = lib, N, n
+        self.tp_o = trajopt.TrajParams(N=N, **kw)
+        self.h = lib.cp_traj_init(lib.make_model(crane), lib.make_traj_params(N=N, **kw), n)
+        self.n_var = 1 + 16 * (N + 1)
+        self.n_eq = 12 * (N + 2)
+
+    def targets(self, ctrl, K):
+        import torch
+        c = torch.from_numpy(np.ascontiguousarray(ctrl)).cuda()
+        q = torch.zeros(ctrl.shape[0], self.N + 1, 4, dtype=torch.float64, device="cuda")
+        self.lib.cp_traj_targets(self.h, c, K, ctrl.shape[0], q)
+        return q
+
+    def close(self):
+        self.lib.cp_traj_destroy(self.h)
+
+
+def test_targets_and_start_match_oracle(lib, crane):
+    import torch
+    import trajopt
+    K, n, N = 8, 3, 20
+    ctrl = _paths(n, K, seed=1)
+    s = _Solver(lib, crane, N, n)
+    try:
+        q = s.targets(ctrl, K)
+        z = torch.zeros(n, s.n_var, dtype=torch.float64, device="cuda")
+        lib.cp_traj_initial_guess(s.h, q, n, z)
+        torch.cuda.synchronize()
+        q, z = q.cpu().numpy(), z.cpu().numpy()
+        for p in range(n):
+            want = trajopt.path_targets(ctrl[p], N)
+            np.testing.assert_allclose(q[p], want, rtol=0, atol=1e-13)
+            np.testing.assert_allclose(q[p][0], ctrl[p][0], atol=1e-14)
+            np.testing.assert_allclose(q[p][-1], ctrl[p][-1], atol=1e-14)
+            prob = trajopt.TrajProblem(crane, s.tp_o, q[p], q[p][0], q[p][-1])
+            np.testing.assert_allclose(z[p], prob.initial_guess(), rtol=1e-13, atol=1e-13)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("N,mu,perturb", [(10, 1e-3, 0.0), (10, 0.0, 0.3), (24, 1e-2, 0.1)])
+def test_one_step_matches_oracle(lib, crane, N, mu, perturb):
+    """One damped Gauss-Newton step from the same (z, lambda, mu): the oracle's dense solve of
+    (J^T J + mu (diag + 1e-9)) dz = -(e_t + J^T r) with complex-step J against the GPU's
+    block-tridiagonal solve with forward-mode Jacobians. `perturb` moves the start off the
+    path (and past some velocity bounds), so that active bounds and swing terms take part."""
+    import torch
+    import trajopt
+    K, n = 6, 2
+    ctrl = _paths(n, K, seed=N + 3)
+    s = _Solver(lib, crane, N, n)
+    try:
+        q = s.targets(ctrl, K)
+        z = torch.zeros(n, s.n_var, dtype=torch.float64, device="cuda")
+        lib.cp_traj_initial_guess(s.h, q, n, z)
+        torch.cuda.synchronize()
+        g = np.random.default_rng(N)
+        zh = z.cpu().numpy() + perturb * g.normal(size=(n, s.n_var)) * (np.arange(s.n_var) > 0)
+        lam = g.normal(size=(n, s.n_eq)) * 0.1
+        dz = torch.zeros_like(z)
+        lib.cp_traj_step(s.h, q, n, torch.from_numpy(zh).cuda(), torch.from_numpy(lam).cuda(), mu, dz)
+        torch.cuda.synchronize()
+        dz, qh = dz.cpu().numpy(), q.cpu().numpy()
+        for p in range(n):
+            prob = trajopt.TrajProblem(crane, s.tp_o, qh[p], qh[p][0], qh[p][-1])
+            want = prob.lm_step(zh[p], lam[p], mu)
+            scale = np.max(np.abs(want))
+            np.testing.assert_allclose(dz[p], want, rtol=0, atol=1e-7 * scale)
+            if perturb > 0:
+                assert np.any(np.abs(prob.violation(zh[p])) > 0)
+    finally:
+        s.close()
+
+
+def test_solve_matches_oracle(lib, crane):
+    """Whole solves (8 multiplier updates x 10 steps) from the same start: the GPU follows the
+    oracle's steps, so the results agree to rounding."""
+    import torch
+    import trajopt
+    K, n, N = 6, 2, 10
+    ctrl = _paths(n, K, seed=7)
+    s = _Solver(lib, crane, N, n)
+    try:
+        q = s.targets(ctrl, K)
+        z = torch.zeros(n, s.n_var, dtype=torch.float64, device="cuda")
+        stats = torch.zeros(n, 4, dtype=torch.float64, device="cuda")
+        lib.cp_traj_initial_guess(s.h, q, n, z)
+        lib.cp_traj_solve(s.h, q, n, z, stats)
+        torch.cuda.synchronize()
+        z, st, qh = z.cpu().numpy(), stats.cpu().numpy(), q.cpu().numpy()
+        for p in range(n):
+            prob = trajopt.TrajProblem(crane, s.tp_o, qh[p], qh[p][0], qh[p][-1])
+            zo, lam_o, _ = prob.solve(prob.initial_guess())
+            np.testing.assert_allclose(z[p], zo, rtol=0, atol=1e-6 * np.max(np.abs(zo)))
+            assert st[p, 0] == pytest.approx(zo[0], rel=1e-8)
+            assert st[p, 2] == pytest.approx(np.max(np.abs(prob.constraints(zo))), rel=1e-3, abs=1e-12)
+            assert st[p, 2] < 2e-4 and st[p, 3] < 1e-4
+    finally:
+        s.close()
+
+
+def test_paper_grid_step_and_feasible_solves(lib, crane):
+    """N = 100 grid points (the paper's n_s): one step against the oracle, and whole solves of
+    eight paths that end feasible (constraint error below 2e-4, bounds within 1e-4) and no
+    faster than the velocity limits allow."""
+    import torch
+    import trajopt
+    K, n, N = 8, 8, 100
+    ctrl = _paths(n, K, seed=11)
+    s = _Solver(lib, crane, N, n)
+    try:
+        q = s.targets(ctrl, K)
+        z = torch.zeros(n, s.n_var, dtype=torch.float64, device="cuda")
+        lib.cp_traj_initial_guess(s.h, q, n, z)
+        lam = torch.zeros(n, s.n_eq, dtype=torch.float64, device="cuda")
+        dz = torch.zeros_like(z)
+        lib.cp_traj_step(s.h, q, n, z, lam, 1e-3, dz)
+        torch.cuda.synchronize()
+        qh, zh, dzh = q.cpu().numpy(), z.cpu().numpy(), dz.cpu().numpy()
+        prob = trajopt.TrajProblem(crane, s.tp_o, qh[0], qh[0][0], qh[0][-1])
+        want = prob.lm_step(zh[0], np.zeros(s.n_eq), 1e-3)
+        np.testing.assert_allclose(dzh[0], want, rtol=0, atol=1e-7 * np.max(np.abs(want)))
+        stats = torch.zeros(n, 4, dtype=torch.float64, device="cuda")
+        lib.cp_traj_solve(s.h, q, n, z, stats)
+        torch.cuda.synchronize()
+        st = stats.cpu().numpy()
+        assert np.all(st[:, 2] < 2e-4) and np.all(st[:, 3] < 1e-4)
+        t_min = np.max(np.abs(qh[:, -1] - qh[:, 0]) / np.array([0.6, 0.3, 0.3, 0.5]), axis=1)
+        assert np.all(st[:, 0] > t_min * (1 - 1e-3))
+    finally:
+        s.close()
+
+
+def test_trajectory_of_a_plan(lib, crane):
+    """The two steps chained: a plan of the 20-tree query (control points from cp_plan), its
+    targets on the GPU and a feasible trajectory."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    q0, qd = endpoints("single_small")
+    pl = lib.Planner(crane, workloads.make_scene(workloads.WORKLOADS["single_small"]), lib.make_params(256, 8, 32))
+    try:
+        lib.cp_set_endpoints(pl.handle, q0, qd)
+        ctrl, _ = lib.cp_plan(pl.handle, 50, K=8)
+    finally:
+        pl.close()
+    s = _Solver(lib, crane, 100, 1)
+    try:
+        q = s.targets(ctrl[None], 8)
+        z = torch.zeros(1, s.n_var, dtype=torch.float64, device="cuda")
+        stats = torch.zeros(1, 4, dtype=torch.float64, device="cuda")
+        lib.cp_traj_initial_guess(s.h, q, 1, z)
+        lib.cp_traj_solve(s.h, q, 1, z, stats)
+        torch.cuda.synchronize()
+        st = stats.cpu().numpy()[0]
+        assert st[2] < 2e-4 and st[3] < 1e-4 and st[0] > 0
+        zz = z.cpu().numpy()[0, 1:].reshape(101, 16)
+        np.testing.assert_allclose(zz[0, :4], q0, atol=2e-4)
+        np.testing.assert_allclose(zz[-1, :4], qd, atol=2e-4)
+    finally:
+        s.close()
+
+
+def test_argument_errors(lib, crane):
+    with pytest.raises(lib.CranePlanError):
+        lib.cp_traj_init(lib.make_model(crane), lib.make_traj_params(N=1), 1)
+    with pytest.raises(lib.CranePlanError):
+        lib.cp_traj_init(lib.make_model(crane), lib.make_traj_params(N=10, swing_max=2.0), 1)
+    s = _Solver(lib, crane, 10, 2)
+    try:
+        import torch
+        z = torch.zeros(3, s.n_var, dtype=torch.float64, device="cuda")
+        with pytest.raises(lib.CranePlanError):
+            lib.cp_traj_initial_guess(s.h, z, 3, z)      # more paths than the solver holds
+    finally:
+        s.close()
