@@ -44,7 +44,9 @@ Readings where the paper is silent:
              damped Gauss-Newton (Levenberg-Marquardt) step
                  (J^T J + mu (diag(J^T J) + 1e-9)) dz = -(e_t + J^T r),
              accepted when F decreases (mu / 3, floor 1e-12), else mu * 4 (cap 1e12); after
-             `inner` steps the multipliers move, lambda <- lambda + rho c. The Jacobian J is
+             `inner` steps the multipliers move, lambda <- lambda + rho c (12 x 10 steps by
+             default; a fixed schedule, so the constraints hold to what it reaches, reported
+             per solve). The Jacobian J is
              taken by complex-step differentiation of r (exact to rounding), dense.
 """
 from __future__ import annotations
@@ -70,7 +72,7 @@ class TrajParams:
     grapple_len: float = 1.0
     rho: float = 3e3
     rho_b: float = 1e5
-    outer: int = 8
+    outer: int = 12
     inner: int = 10
     mu0: float = 1e-3
 

@@ -117,7 +117,7 @@ class cp_traj_params(ctypes.Structure):
 
 def make_traj_params(N: int = 100, omega_s: float = 1e-2, omega_t: float = 1e2, R=(1.0, 1.0, 1.0, 1.0),
                      dq_max=(0.6, 0.3, 0.3, 0.5), swing_max: float = 0.6, grapple_len: float = 1.0,
-                     rho: float = 3e3, rho_b: float = 1e5, outer: int = 8, inner: int = 10,
+                     rho: float = 3e3, rho_b: float = 1e5, outer: int = 12, inner: int = 10,
                      mu0: float = 1e-3) -> "cp_traj_params":
     return cp_traj_params(int(N), float(omega_s), float(omega_t), (ctypes.c_double * 4)(*R),
                           (ctypes.c_double * 4)(*dq_max), float(swing_max), float(grapple_len), float(rho),
