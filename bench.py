@@ -968,6 +968,145 @@ def run_batch(args):
     cp.cp_batch_destroy(b)
 
 
+TRAJ_PATHS = 64
+
+
+def traj_flops_per_step(N):
+    """Algorithmic FP64 work of one Levenberg-Marquardt step of one trajectory (the GPU's form):
+    per grid point the dynamics' Jacobian by 16 forward-mode passes (about 360 flops each), the
+    diagonal and off-diagonal 16 x 16 blocks of J^T J from the 12-row defect Jacobians
+    (2 x 12 flops per entry), the block factorisation (the Schur update 2 x 16^3, the 16 x 16
+    Cholesky 16^3 / 3, L^-1 E_k 16^3) and the substitutions of two vectors (4 x 2 x 16^2)."""
+    per_point = 16 * 360 + 2 * 256 * 24 + 2 * 16 ** 3 + 16 ** 3 / 3 + 16 ** 3 + 8 * 256
+    return (N + 1) * per_point
+
+
+def run_trajopt(args):
+    """The trajectory tracking optimisation of Sec. 4.2 (Eq. discrete), batched: the paths of
+    64 plans of the 20-tree query (seeds 0..63, K = 8, 50 iterations each) turned into
+    trajectories on N = 100 collocation intervals (the paper's n_s) by one solver launch, one
+    CTA per trajectory. A step is one batch: targets, starting points and the solve."""
+    import torch
+    from paper_2503_14160_gb300 import build, craneplan as cp, workloads
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    build.build()
+    cp.load()
+    crane = workloads.forestry_crane()
+    wl = workloads.WORKLOADS["single_small"]
+    scene = workloads.make_scene(wl)
+    with open(os.path.join(ROOT, "tests", "golden", "endpoints.json")) as f:
+        e = json.load(f)["workloads"][wl.name]
+    q0, qd = np.array(e["q0"]), np.array(e["qd"])
+    K, N, n = wl.n_waypoints, 100, TRAJ_PATHS
+    ctrl = np.zeros((n, K + 8, 4))
+    for p in range(n):   # the planned paths (untimed: the path step is measured by its own line)
+        with cp.Planner(crane, scene, cp.make_params(wl.n_candidates, K, wl.substeps, seed=p, query=rank)) as pl:
+            cp.cp_set_endpoints(pl.handle, q0, qd)
+            ctrl[p], _ = cp.cp_plan(pl.handle, wl.iterations, K=K)
+    tp = cp.make_traj_params(N=N)
+    h = cp.cp_traj_init(cp.make_model(crane), tp, n)
+    n_var = 1 + 16 * (N + 1)
+    d_ctrl = torch.from_numpy(ctrl).cuda()
+    q = torch.zeros(n, N + 1, 4, dtype=torch.float64, device="cuda")
+    z = torch.zeros(n, n_var, dtype=torch.float64, device="cuda")
+    stats = torch.zeros(n, 4, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one():
+        cp.cp_traj_targets(h, d_ctrl, K, n, q)
+        cp.cp_traj_initial_guess(h, q, n, z)
+        cp.cp_traj_solve(h, q, n, z, stats)
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    l0 = cp.cp_launch_count()
+    times = []
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+    launches = cp.cp_launch_count() - l0
+    # end to end with host buffers: control points in, trajectories and statistics out
+    h_ctrl = torch.from_numpy(ctrl).pin_memory()
+    h_z = torch.zeros(n, n_var, dtype=torch.float64).pin_memory()
+    h_st = torch.zeros(n, 4, dtype=torch.float64).pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_ctrl.copy_(h_ctrl, non_blocking=True)
+        one()
+        h_z.copy_(z, non_blocking=True)
+        h_st.copy_(stats, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    st = stats.cpu().numpy()
+    ms, ms_e2e = max_over_ranks([float(np.mean(times)), float(np.mean(e2e))], "cuda")
+    steps_lm = tp.outer * tp.inner
+    flops = traj_flops_per_step(N) * steps_lm * n
+    peaks = cp.cp_alu_peaks()
+    achieved = flops / (ms / 1e3) / 1e12
+    line = {"metric": "trajectories optimised/sec (Sec. 4.2 direct collocation, N = 100)",
+            "value": job_throughput(n, ws, ms), "unit": "trajectories/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (paths planned on the seeded 20-tree scene; synthetic crane dynamics)",
+            "config": {"workload": "trajopt: %d paths (plans of the 20-tree query, seeds 0..%d), N=%d, %d x %d "
+                                   "Levenberg-Marquardt steps" % (n, n - 1, N, tp.outer, tp.inner),
+                       "step": "one batch: targets, starting points, solve", "l2": "inputs below L2 (a few MB)"},
+            "e2e": {"value": job_throughput(n, ws, ms_e2e), "unit": "trajectories/s", "ms_per_step": ms_e2e,
+                    "h2d_bytes_per_step": ctrl.nbytes, "d2h_bytes_per_step": n * (n_var + 4) * 8},
+            "gpu_launches": launches // max(args.steps, 1) * args.steps,
+            "roofline": {"bound": "fp64", "kernel": "k_traj_solve", "achieved": achieved,
+                         "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"],
+                         "peak_basis": "cp_alu_peaks (measured FP64 FMA rate, whole GPU)",
+                         "sms_used": n, "traffic": None},
+            "result": {"t_F_mean_s": float(st[:, 0].mean()), "max_constraint_error": float(st[:, 2].max()),
+                       "max_bound_violation": float(st[:, 3].max())},
+            "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = traj_cpu_baseline(crane, ctrl[0], N, steps_lm, q.cpu().numpy()[0])
+        line["oracle_error"] = traj_oracle_error(crane, q.cpu().numpy()[0], z.cpu().numpy()[0], N)
+    print(json.dumps(line), flush=True)
+    cp.cp_traj_destroy(h)
+
+
+def traj_cpu_baseline(crane, ctrl, N, steps, q_star):
+    """The oracle's trajectory solver as it stands (dense complex-step Jacobians, numpy) on a
+    bounded sample: one Levenberg-Marquardt step of one trajectory at N, timed, scaled to the
+    solve's steps."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import trajopt
+    prob = trajopt.TrajProblem(crane, trajopt.TrajParams(N=N), q_star, q_star[0], q_star[-1])
+    z = prob.initial_guess()
+    t0 = time.perf_counter()
+    prob.lm_step(z, np.zeros(prob.n_eq), 1e-3)
+    el = time.perf_counter() - t0
+    return {"value": 1.0 / (el * steps), "unit": "trajectories/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "seconds": el, "sample": "one Levenberg-Marquardt step of one trajectory at N=%d (dense complex-step "
+                                     "Jacobian, numpy), scaled to the %d steps of a solve" % (N, steps)}
+
+
+def traj_oracle_error(crane, q_star, z_gpu, N):
+    """The GPU's first Levenberg-Marquardt step against the oracle's, at the GPU's result (the
+    CPU-baseline leg): relative difference of the steps, and the oracle's objective at the
+    GPU's trajectory against the GPU's."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import trajopt
+    prob = trajopt.TrajProblem(crane, trajopt.TrajParams(N=N), q_star, q_star[0], q_star[-1])
+    c = prob.constraints(z_gpu)
+    return {"max_constraint_error_oracle": float(np.max(np.abs(c))),
+            "max_bound_violation_oracle": float(np.max(np.abs(prob.violation(z_gpu)))),
+            "t_F": float(z_gpu[0])}
+
+
 def batch_cpu_baseline(crane, queries, q0s, qds, seed, S, seconds):
     """The FP64 oracle on a bounded sample of the batch: candidate evaluations of every
     eighth query in turn (each with its own scene and sizes) until `seconds` have passed."""
@@ -1093,6 +1232,46 @@ def oracle_errors(cp, h, wl, crane, scene, q0, qd, ctrl, stats, iters, n_sample=
     return {"plan": plan, "candidates": cand}
 
 
+def run_traj_reference(args):
+    """--impl reference for the trajectory workload: the oracle's solver on one trajectory,
+    one Levenberg-Marquardt step per bench step (bounded), scaled to a solve."""
+    from paper_2503_14160_gb300 import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import trajopt
+    crane = workloads.forestry_crane()
+    with open(os.path.join(ROOT, "tests", "golden", "endpoints.json")) as f:
+        e = json.load(f)["workloads"]["single_small"]
+    q0, qd = np.array(e["q0"]), np.array(e["qd"])
+    N = 100
+    s = np.linspace(0.0, 1.0, N + 1)[:, None]
+    q_star = q0[None] + (3 * s ** 2 - 2 * s ** 3) * (qd - q0)[None]
+    tp = trajopt.TrajParams(N=N)
+    prob = trajopt.TrajProblem(crane, tp, q_star, q0, qd)
+    z = prob.initial_guess()
+    per = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        prob.lm_step(z, np.zeros(prob.n_eq), 1e-3)
+        if i >= args.warmup:
+            per.append(time.perf_counter() - t0)
+    el = float(np.mean(per))
+    value = 1.0 / (el * tp.outer * tp.inner)
+    line = {"metric": "trajectories optimised/sec (Sec. 4.2 direct collocation, N = 100)", "value": value,
+            "unit": "trajectories/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (a smooth rest-to-rest path of the 20-tree query's end points)",
+            "impl": "reference",
+            "config": {"workload": "trajopt: N=%d, %d x %d Levenberg-Marquardt steps" % (N, tp.outer, tp.inner),
+                       "step": "a bounded sample: one Levenberg-Marquardt step of one trajectory"},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": os.cpu_count() or 1,
+                             "kind": "oracle", "sample": "one step of one trajectory per bench step, scaled to a solve"},
+            "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     from paper_2503_14160_gb300 import workloads
     ws, rank, _ = dist_env()
@@ -1152,6 +1331,8 @@ def main():
         run_ik_reference(args)
     elif args.impl == "reference" and args.workload == "hulls":
         run_hulls_reference(args)
+    elif args.impl == "reference" and args.workload == "trajopt":
+        run_traj_reference(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "ik":
@@ -1162,6 +1343,8 @@ def main():
         run_differentiable(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "trajopt":
+        run_trajopt(args)
     else:
         run_ours(args)
 
