@@ -386,6 +386,11 @@ int cp_get_factor(const cp_planner *p, double *d_L);
 /* Copy the candidate indices of the last update in rank order (int32[nu]). */
 int cp_get_elites(const cp_planner *p, int32_t *d_idx);
 
+/* Copy the population of the last iteration of cp_plan (or of a batch run) and its costs:
+ * d_xi float[N][K][4], d_J double[N] (either may be NULL). Only the planner's own draws
+ * are kept here; cp_sample and cp_evaluate write the caller's buffers. */
+int cp_get_population(const cp_planner *p, float *d_xi, double *d_J);
+
 /* Philox4x32-10 (Salmon et al., SC'11) of n counters d_ctr (uint32[n][4], device) under
  * key = (uint32)seed, (uint32)(seed >> 32); d_out is uint32[n][4]. `stream` as above. */
 int cp_philox4x32_10(const uint32_t *d_ctr, uint64_t key, int64_t n, uint32_t *d_out,
@@ -432,12 +437,21 @@ typedef struct cp_batch_result {
 
 typedef struct cp_batch cp_batch;
 
-/* Batched serving form of Algorithm 1: nq independent queries planned concurrently for
- * `iters` iterations each. Creates one planner and one stream per query, then records every
- * query's whole plan (end points in, initial distribution, the iterations, the mean path's
- * evaluation, results out) as one CUDA graph whose branches run concurrently, so that small
- * queries fill the GPU around large ones. Allocation happens here only. Errors: as
- * cp_plan_init (for the first query that fails), CP_ERR_CUDA. */
+/* Batched serving form of Algorithm 1 (Sec. 4.1; the many-query setting of Sec. 5.1):
+ * nq independent queries planned together for `iters` iterations each, every stage of an
+ * iteration one launch for all queries. The evaluation of step (2) is one persistent launch
+ * per iteration: CTAs take tiles of (query, consecutive work items) from a device counter
+ * and restage the query's obstacle index and spline table when the query of their tile
+ * changes. Sampling (step 1), costs, the stable ranking (steps 3-4; a radix sort of all
+ * queries' costs followed by passes on the query), the elites' moments (steps 5-6) and the
+ * factors are segmented by query through block tables. Each query keeps its own planner
+ * workspace, and its results equal those of its planner planning alone with cp_plan bit
+ * for bit. The whole run (end points in, initial distributions, the iterations, the mean
+ * paths' evaluation, results out) is recorded once as one CUDA graph. Every query must use
+ * the polar obstacle index (grid_cell > 0), the paper's update rule, the factor sampler and
+ * the sphere collision model, with one crane model for all. Allocation happens here only.
+ * Errors: CP_ERR_ARG (a query outside that form; the message names it), as cp_plan_init
+ * (for the first query that fails), CP_ERR_CUDA. */
 int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, int32_t iters,
                   cp_batch **out);
 
@@ -446,14 +460,44 @@ int cp_batch_set_endpoints(cp_batch *b, int32_t q, const double h_q0[4], const d
 
 /* Run every query once: one launch of the recorded graph, then wait for it. results (host,
  * nq entries, may be NULL) receives each query's result. Errors: CP_ERR_NUMERIC when a
- * query's covariance lost positive definiteness, CP_ERR_CUDA. */
+ * query's covariance lost positive definiteness, CP_ERR_ARG when a query's obstacle index
+ * overflowed, CP_ERR_CUDA. */
 int cp_batch_run(cp_batch *b, cp_batch_result *results);
 
-/* The planner behind query q (owned by the batch), e.g. to plan that query alone with
- * cp_plan; do not use it while cp_batch_run is running. NULL when q is out of range. */
+/* Launch shape of the batched evaluation (picked by the autotuner). Results do not depend
+ * on it: an item's arithmetic and the order of its sums are fixed by the query alone. */
+typedef struct cp_batch_shape {
+    int32_t threads;          /* CTA size: 128, 256 or 512 */
+    int32_t ctas_per_sm;      /* resident CTAs per SM (0: as many as fit) */
+    int32_t items_per_warp;   /* work items per warp in a tile (1..64): a tile holds
+                                 threads / 32 * items_per_warp consecutive items */
+} cp_batch_shape;
+
+/* Set the launch shape (default {256, 0, 2}) and record the graph again. Errors:
+ * CP_ERR_ARG (a field outside its range), CP_ERR_CUDA. */
+int cp_batch_set_shape(cp_batch *b, const cp_batch_shape *shape);
+
+/* Time the batched evaluation alone: `reps` launches over every query's current population
+ * (whatever the last run left), CUDA events around each launch; *ms = the mean duration.
+ * Errors: CP_ERR_ARG, CP_ERR_CUDA. */
+int cp_batch_evaluate(cp_batch *b, int32_t reps, double *ms);
+
+typedef struct cp_batch_info {
+    int64_t kernel_nodes;     /* kernels recorded in the graph (one cp_batch_run) */
+    int64_t eval_tiles;       /* tiles of one iteration's evaluation */
+    int32_t eval_ctas;        /* CTAs of the persistent evaluation launch */
+    int32_t eval_launches;    /* persistent evaluation launches per run (iterations + 1) */
+    int64_t candidates;       /* sum of the queries' N */
+} cp_batch_info;
+
+int cp_batch_get_info(const cp_batch *b, cp_batch_info *out);
+
+/* The planner behind query q (owned by the batch): it holds the query's state after a run
+ * (cp_get_distribution, cp_get_elites), and can plan the query alone with cp_plan; do not
+ * use it while cp_batch_run is running. NULL when q is out of range. */
 cp_planner *cp_batch_planner(cp_batch *b, int32_t q);
 
-/* Release the batch, its planners, streams and graph. NULL is ignored. */
+/* Release the batch, its planners, stream and graph. NULL is ignored. */
 void cp_batch_destroy(cp_batch *b);
 
 /* ------------------------------------------------------------------ trajectory step */

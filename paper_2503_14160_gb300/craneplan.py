@@ -90,6 +90,17 @@ class cp_query(ctypes.Structure):
                 ("qd", ctypes.c_double * 4)]
 
 
+class cp_batch_shape(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("items_per_warp", ctypes.c_int32)]
+
+
+class cp_batch_info(ctypes.Structure):
+    _fields_ = [("kernel_nodes", ctypes.c_int64), ("eval_tiles", ctypes.c_int64),
+                ("eval_ctas", ctypes.c_int32), ("eval_launches", ctypes.c_int32),
+                ("candidates", ctypes.c_int64)]
+
+
 class cp_batch_result(ctypes.Structure):
     _fields_ = [("stats", cp_plan_stats), ("ctrl", ctypes.c_double * ((CP_MAX_WAYPOINTS + 8) * 4))]
 
@@ -164,6 +175,7 @@ _SIGS = {
     "cp_get_cma_state": (ctypes.c_int, [_P, _P]),
     "cp_set_cma_state": (ctypes.c_int, [_P, _P]),
     "cp_get_elites": (ctypes.c_int, [_P, _P]),
+    "cp_get_population": (ctypes.c_int, [_P, _P, _P]),
     "cp_philox4x32_10": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P]),
     "cp_evaluate_static": (ctypes.c_int, [ctypes.POINTER(cp_model), _P, ctypes.c_int32, _P,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -180,6 +192,9 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_double)]),
     "cp_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(cp_batch_result)]),
     "cp_batch_planner": (_P, [_P, ctypes.c_int32]),
+    "cp_batch_set_shape": (ctypes.c_int, [_P, ctypes.POINTER(cp_batch_shape)]),
+    "cp_batch_evaluate": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "cp_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(cp_batch_info)]),
     "cp_batch_destroy": (None, [_P]),
     "cp_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cp_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(cp_timing)]),
@@ -423,6 +438,11 @@ def cp_get_elites(p: int, idx) -> None:
     _check(load().cp_get_elites(p, _ptr(idx)))
 
 
+def cp_get_population(p: int, xi=None, J=None) -> None:
+    _check(load().cp_get_population(p, _ptr(xi) if xi is not None else None,
+                                    _ptr(J) if J is not None else None))
+
+
 def cp_philox4x32_10(ctr, key: int, n: int, out, stream=None) -> None:
     _check(load().cp_philox4x32_10(_ptr(ctr), int(key), int(n), _ptr(out), _stream(stream)))
 
@@ -485,6 +505,24 @@ def cp_batch_run(b: int, nq: int, K=None):
 
 def cp_batch_planner(b: int, q: int) -> int:
     return load().cp_batch_planner(b, int(q))
+
+
+def cp_batch_set_shape(b: int, threads: int = 256, ctas_per_sm: int = 0, items_per_warp: int = 2) -> None:
+    sh = cp_batch_shape(int(threads), int(ctas_per_sm), int(items_per_warp))
+    _check(load().cp_batch_set_shape(b, ctypes.byref(sh)))
+
+
+def cp_batch_evaluate(b: int, reps: int = 3) -> float:
+    """Mean duration (ms) of the batched evaluation launch over the current populations."""
+    ms = ctypes.c_double()
+    _check(load().cp_batch_evaluate(b, int(reps), ctypes.byref(ms)))
+    return ms.value
+
+
+def cp_batch_get_info(b: int) -> dict:
+    info = cp_batch_info()
+    _check(load().cp_batch_get_info(b, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in cp_batch_info._fields_}
 
 
 def cp_batch_destroy(b: int) -> None:

@@ -1208,6 +1208,16 @@ int cp_get_elites(const cp_planner *p, int32_t *d_idx)
     return CP_OK;
 }
 
+int cp_get_population(const cp_planner *p, float *d_xi, double *d_J)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    if (d_xi && !aligned16(d_xi)) return set_error("d_xi must be 16-byte aligned"), CP_ERR_ARG;
+    if (d_xi)
+        CP_CUDA(cudaMemcpyAsync(d_xi, p->xi, sizeof(float) * (size_t)p->N * p->D, cudaMemcpyDeviceToDevice, p->st));
+    if (d_J) CP_CUDA(cudaMemcpyAsync(d_J, p->J, sizeof(double) * (size_t)p->N, cudaMemcpyDeviceToDevice, p->st));
+    return CP_OK;
+}
+
 int cp_philox4x32_10(const uint32_t *d_ctr, uint64_t key, int64_t n, uint32_t *d_out, void *stream)
 {
     if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return set_error("invalid arguments"), CP_ERR_ARG;
@@ -1274,69 +1284,177 @@ int cp_synchronize(cp_planner *p)
 
 struct cp_batch {
     int nq = 0, iters = 0;
-    cudaStream_t origin = nullptr;
+    cudaStream_t st = nullptr;
     std::vector<cp_planner *> planners;
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> joins;
-    cudaEvent_t fork = nullptr;
-    double *h_in = nullptr;       // pinned [nq][8]: q0, qd
-    double *h_out = nullptr;      // pinned [nq][kOutStride]
-    uint32_t *h_status = nullptr; // pinned [nq]
-    cudaGraph_t graph = nullptr;
+    ModelDev mdev{};
+    int num_sms = 1, max_K = 0, max_S = 0, max_D = 0;
+    int64_t total = 0;                 // sum of N
+    double *h_in = nullptr;            // pinned [nq][8]: q0, qd
+    double *h_out = nullptr;           // pinned [nq][kOutStride]
+    char *base = nullptr;              // device memory of the batch
+    double *d_in = nullptr, *d_out = nullptr;
+    BatchQueryDev *qdev = nullptr;
+    BatchEvalDev *ev_pop = nullptr, *ev_mean = nullptr;
+    int2 *tab_init = nullptr, *tab_sample = nullptr, *tab_cand = nullptr, *tab_gather = nullptr;
+    int2 *tab_mpart = nullptr, *tab_mcomb = nullptr;
+    int n_init = 0, n_sample = 0, n_cand = 0, n_gather = 0, n_mpart = 0, n_mcomb = 0;
+    int4 *tiles_pop = nullptr, *tiles_mean = nullptr;
+    int64_t tiles_cap = 0;
+    int n_tiles_pop = 0, n_tiles_mean = 0;
+    int *queue = nullptr;              // [iters + 2] tile counters (the last one for cp_batch_evaluate)
+    uint16_t *qid = nullptr;           // [total] query of each ranking position
+    unsigned long long *key_a = nullptr, *key_b = nullptr;
+    int *val_a = nullptr, *val_b = nullptr, *hist = nullptr;
+    std::vector<int> order;            // queries by decreasing work per item (tile order)
+    std::vector<int> items_pop, items_mean;
+    cp_batch_shape shape{256, 0, 2};
+    int eval_blocks = 0;
     cudaGraphExec_t exec = nullptr;
-    int64_t kernel_nodes = 0;     // kernels recorded into the graph
+    int64_t kernel_nodes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace {
 
-constexpr int kOutStride = 8 + (CP_MAX_WAYPOINTS + 8) * 4;   // J, terms[5], best, pad, ctrl
+constexpr int kOutStride = 8 + (CP_MAX_WAYPOINTS + 8) * 4;   // J, terms[5], best, status, ctrl
 
-// The device work of one query's plan on its planner's stream, with host inputs and outputs
-// in pinned memory (recorded into the batch graph).
-int record_plan(cp_planner *p, int iters, const double *h_in, double *h_out, uint32_t *h_status)
+// The form the batched kernels implement, for query q.
+int batch_query_ok(const cp_query &qr, int q, const cp_model *model)
+{
+    const cp_params &p = qr.params;
+    if (!(p.grid_cell > 0.0))
+        return set_error("query %d: the batched form evaluates with the polar obstacle index (grid_cell > 0)", q),
+               CP_ERR_ARG;
+    if (p.update_rule != CP_UPDATE_PAPER || p.sampler != CP_SAMPLE_FACTOR || p.collision_model != CP_COLLISION_SPHERES)
+        return set_error("query %d: the batched form runs the paper's update rule, the factor sampler and the "
+                         "sphere collision model", q),
+               CP_ERR_ARG;
+    if (p.debug_withhold_staging != 0) return set_error("query %d: no test hooks in the batched form", q), CP_ERR_ARG;
+    (void)model;
+    return CP_OK;
+}
+
+// Tiles of consecutive items of each query, queries in the given order.
+void build_tiles(const std::vector<int> &order, const std::vector<int> &items, int per_tile, std::vector<int4> &out)
+{
+    out.clear();
+    for (int q : order)
+        for (int b = 0; b < items[q]; b += per_tile) out.push_back(make_int4(q, b, std::min(items[q], b + per_tile), 0));
+}
+
+int batch_upload_tiles(cp_batch *b)
+{
+    const int per_tile = b->shape.threads / 32 * b->shape.items_per_warp;
+    std::vector<int4> pop, mean;
+    build_tiles(b->order, b->items_pop, per_tile, pop);
+    build_tiles(b->order, b->items_mean, per_tile, mean);
+    if ((int64_t)pop.size() > b->tiles_cap || (int64_t)mean.size() > b->tiles_cap)
+        return set_error("batched evaluation: %zu tiles exceed the %lld allocated", pop.size(), (long long)b->tiles_cap),
+               CP_ERR_ARG;
+    CP_CUDA(cudaMemcpyAsync(b->tiles_pop, pop.data(), sizeof(int4) * pop.size(), cudaMemcpyHostToDevice, b->st));
+    CP_CUDA(cudaMemcpyAsync(b->tiles_mean, mean.data(), sizeof(int4) * mean.size(), cudaMemcpyHostToDevice, b->st));
+    CP_CUDA(cudaStreamSynchronize(b->st));
+    b->n_tiles_pop = (int)pop.size();
+    b->n_tiles_mean = (int)mean.size();
+    const int max_blocks = batch_eval_max_blocks(b->mdev, b->shape.threads, b->max_S, b->num_sms);
+    if (max_blocks < 0) return CP_ERR_ARG;
+    int blocks = max_blocks;
+    if (b->shape.ctas_per_sm > 0) blocks = std::min(blocks, b->shape.ctas_per_sm * b->num_sms);
+    b->eval_blocks = std::max(1, std::min(blocks, b->n_tiles_pop));
+    return CP_OK;
+}
+
+// One run of the batch as stream work (recorded into the graph).
+int record_batch(cp_batch *b)
 {
     int rc;
-    CP_CUDA(cudaMemsetAsync(p->status, 0, sizeof(uint32_t), p->st));
-    CP_CUDA(cudaMemcpyAsync(p->consts, h_in, 8 * sizeof(double), cudaMemcpyHostToDevice, p->st));
-    if ((rc = launch_init_distribution(p->consts, p->consts + 4, p->consts + 8, p->consts + 12, p->K,
-                                       p->prm.init_std_frac, p->mu, p->C, p->ends_f, p->st)) != CP_OK)
-        return rc;
-    if ((rc = launch_cma_reset(p->prm.sigma, p->D, p->cma, p->p_sigma, p->p_c, p->st)) != CP_OK) return rc;
-    p->iteration = 0;
-    p->elites_ready = false;
-    if ((rc = run_factor(p)) != CP_OK) return rc;
-    for (int t = 0; t < iters; ++t) {
-        if ((rc = run_sample(p, t, p->xi)) != CP_OK) return rc;
-        if ((rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr)) != CP_OK) return rc;
-        if ((rc = run_update(p, p->J, p->xi)) != CP_OK) return rc;
+    CP_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int) * (size_t)(b->iters + 2), b->st));
+    CP_CUDA(cudaMemcpyAsync(b->d_in, b->h_in, sizeof(double) * 8 * b->nq, cudaMemcpyHostToDevice, b->st));
+    if ((rc = launch_batch_init(b->qdev, b->tab_init, b->n_init, b->d_in, b->st)) != CP_OK) return rc;
+    if ((rc = launch_batch_factor(b->qdev, b->nq, b->max_D, b->st)) != CP_OK) return rc;
+    for (int t = 0; t < b->iters; ++t) {
+        if ((rc = launch_batch_sample(b->qdev, b->tab_sample, b->n_sample, b->max_K, (uint32_t)t, b->st)) != CP_OK)
+            return rc;
+        if ((rc = launch_batch_eval_polar(b->mdev, b->ev_pop, b->tiles_pop, b->n_tiles_pop, b->queue + t, b->max_S,
+                                          b->shape.threads, b->eval_blocks, b->st)) != CP_OK)
+            return rc;
+        if ((rc = launch_batch_finalize(b->qdev, b->tab_cand, b->n_cand, nullptr, b->st)) != CP_OK) return rc;
+        int *sorted = nullptr;
+        if ((rc = launch_batch_radix_rank(b->qdev, b->tab_cand, b->n_cand, (int)b->total, b->nq, b->qid, b->key_a,
+                                          b->key_b, b->val_a, b->val_b, b->hist, &sorted, b->st)) != CP_OK)
+            return rc;
+        if ((rc = launch_batch_gather(b->qdev, b->tab_gather, b->n_gather, sorted, b->st)) != CP_OK) return rc;
+        if ((rc = launch_batch_moments(b->qdev, b->tab_mpart, b->n_mpart, b->tab_mcomb, b->n_mcomb, b->st)) != CP_OK)
+            return rc;
+        if ((rc = launch_batch_factor(b->qdev, b->nq, b->max_D, b->st)) != CP_OK) return rc;
     }
-    if ((rc = launch_mean_to_candidate(p->mu, p->D, p->mean_xi, p->st)) != CP_OK) return rc;
-    if ((rc = run_eval(p, p->mean_xi, 1, p->mean_J, p->mean_flag, p->mean_terms, nullptr, nullptr)) != CP_OK)
+    if ((rc = launch_batch_outputs(b->qdev, b->nq, true, nullptr, 0, b->st)) != CP_OK) return rc;
+    const int mean_blocks = std::max(1, std::min(b->eval_blocks, b->n_tiles_mean));
+    if ((rc = launch_batch_eval_polar(b->mdev, b->ev_mean, b->tiles_mean, b->n_tiles_mean, b->queue + b->iters,
+                                      b->max_S, b->shape.threads, mean_blocks, b->st)) != CP_OK)
         return rc;
-    if ((rc = launch_control_points(p->consts, p->consts + 4, p->mu, p->K, p->ctrl, p->st)) != CP_OK)
+    if ((rc = launch_batch_finalize(b->qdev, nullptr, b->nq, b->ev_mean, b->st)) != CP_OK) return rc;
+    if ((rc = launch_batch_outputs(b->qdev, b->nq, false, b->d_out, kOutStride, b->st)) != CP_OK) return rc;
+    CP_CUDA(cudaMemcpyAsync(b->h_out, b->d_out, sizeof(double) * kOutStride * b->nq, cudaMemcpyDeviceToHost, b->st));
+    return CP_OK;
+}
+
+int batch_record_graph(cp_batch *b)
+{
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    CP_CUDA(cudaStreamSynchronize(b->st));
+    const int64_t launches_before = g_launches.load();
+    const cudaError_t e_begin = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e_begin != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e_begin, "cudaStreamBeginCapture");
+    }
+    const int rc = record_batch(b);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(b->st, &graph);
+    b->kernel_nodes = g_launches.load() - launches_before;   // recorded, not run
+    g_launches.fetch_sub(b->kernel_nodes);
+    if (rc != CP_OK) {
+        if (graph) cudaGraphDestroy(graph);
         return rc;
-    CP_CUDA(cudaMemcpyAsync(h_out, p->mean_J, sizeof(double), cudaMemcpyDeviceToHost, p->st));
-    CP_CUDA(cudaMemcpyAsync(h_out + 1, p->mean_terms, 5 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
-    CP_CUDA(cudaMemcpyAsync(h_out + 6, p->best, sizeof(double), cudaMemcpyDeviceToHost, p->st));
-    CP_CUDA(cudaMemcpyAsync(h_out + 8, p->ctrl, sizeof(double) * 4 * (p->K + 8), cudaMemcpyDeviceToHost, p->st));
-    CP_CUDA(cudaMemcpyAsync(h_status, p->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, p->st));
+    }
+    if (e_end != cudaSuccess) return cuda_fail(e_end, "cudaStreamEndCapture");
+    const cudaError_t e_inst = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e_inst != cudaSuccess) {
+        b->exec = nullptr;
+        return cuda_fail(e_inst, "cudaGraphInstantiate");
+    }
     return CP_OK;
 }
 
 void batch_free(cp_batch *b)
 {
     if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
     for (auto *p : b->planners) cp_destroy(p);
-    for (auto e : b->joins) cudaEventDestroy(e);
-    if (b->fork) cudaEventDestroy(b->fork);
-    for (auto s : b->streams) cudaStreamDestroy(s);
-    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->base) cudaFree(b->base);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->st) cudaStreamDestroy(b->st);
     if (b->h_in) cudaFreeHost(b->h_in);
     if (b->h_out) cudaFreeHost(b->h_out);
-    if (b->h_status) cudaFreeHost(b->h_status);
     delete b;
+}
+
+// Block table: for each query, `count(q)` entries {q, 0..count(q)-1}.
+template <typename F>
+void block_table(int nq, F count, std::vector<int2> &out)
+{
+    out.clear();
+    for (int q = 0; q < nq; ++q) {
+        const int c = count(q);
+        for (int i = 0; i < c; ++i) out.push_back(make_int2(q, i));
+    }
 }
 
 }  // namespace
@@ -1351,10 +1469,14 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     *out = nullptr;
     if (!queries || nq < 1 || nq > 4096) return set_error("nq = %d outside 1..4096", nq), CP_ERR_ARG;
     if (iters < 0) return set_error("iters must be >= 0"), CP_ERR_ARG;
-    for (int q = 0; q < nq; ++q)
+    int rc;
+    if ((rc = validate_model(model)) != CP_OK) return rc;
+    for (int q = 0; q < nq; ++q) {
         for (int j = 0; j < 4; ++j)
             if (!is_finite(queries[q].q0[j]) || !is_finite(queries[q].qd[j]))
                 return set_error("query %d: end points must be finite", q), CP_ERR_ARG;
+        if ((rc = batch_query_ok(queries[q], q, model)) != CP_OK) return rc;
+    }
     cp_batch *b = new (std::nothrow) cp_batch();
     if (!b) return set_error("host allocation failed"), CP_ERR_OOM;
     b->nq = nq;
@@ -1364,25 +1486,16 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
         return code;
     };
     cudaError_t e;
-    if ((e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking)) != cudaSuccess)
+    if ((e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
-    if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess)
+    if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess || (e = cudaEventCreate(&b->ev1)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaEventCreate"));
     if ((e = cudaMallocHost((void **)&b->h_in, sizeof(double) * 8 * nq)) != cudaSuccess ||
-        (e = cudaMallocHost((void **)&b->h_out, sizeof(double) * kOutStride * nq)) != cudaSuccess ||
-        (e = cudaMallocHost((void **)&b->h_status, sizeof(uint32_t) * nq)) != cudaSuccess)
+        (e = cudaMallocHost((void **)&b->h_out, sizeof(double) * kOutStride * nq)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaMallocHost"));
     for (int q = 0; q < nq; ++q) {
-        cudaStream_t st;
-        cudaEvent_t ev;
-        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
-            return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
-        b->streams.push_back(st);
-        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
-            return fail(cuda_fail(e, "cudaEventCreate"));
-        b->joins.push_back(ev);
         cp_planner *p = nullptr;
-        const int rc = cp_plan_init(model, &queries[q].scene, &queries[q].params, st, &p);
+        rc = cp_plan_init(model, &queries[q].scene, &queries[q].params, b->st, &p);
         if (rc != CP_OK) {
             char msg[512];
             snprintf(msg, sizeof msg, "query %d: %s", q, g_err);
@@ -1394,30 +1507,180 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
         memcpy(b->h_in + 8 * q, queries[q].q0, 4 * sizeof(double));
         memcpy(b->h_in + 8 * q + 4, queries[q].qd, 4 * sizeof(double));
     }
-    // record every query's plan as one graph with a branch per query
-    if ((e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return fail(cuda_fail(e, "cudaStreamBeginCapture"));
-    int rc = CP_OK;
-    const int64_t launches_before = g_launches.load();
-    e = cudaEventRecord(b->fork, b->origin);
-    for (int q = 0; q < nq && e == cudaSuccess && rc == CP_OK; ++q) {
-        if ((e = cudaStreamWaitEvent(b->streams[q], b->fork, 0)) != cudaSuccess) break;
-        rc = record_plan(b->planners[q], iters, b->h_in + 8 * q, b->h_out + kOutStride * q,
-                         b->h_status + q);
-        if (rc != CP_OK) break;
-        if ((e = cudaEventRecord(b->joins[q], b->streams[q])) != cudaSuccess) break;
-        e = cudaStreamWaitEvent(b->origin, b->joins[q], 0);
+    b->mdev = b->planners[0]->mdev;
+    b->num_sms = b->planners[0]->num_sms;
+    std::vector<BatchQueryDev> qh(nq);
+    std::vector<BatchEvalDev> eh(nq), mh(nq);
+    std::vector<int> G(nq);
+    b->items_pop.resize(nq);
+    b->items_mean.resize(nq);
+    int64_t off = 0;
+    for (int q = 0; q < nq; ++q) {
+        cp_planner *p = b->planners[q];
+        b->max_K = std::max(b->max_K, p->K);
+        b->max_S = std::max(b->max_S, p->S);
+        b->max_D = std::max(b->max_D, p->D);
+        BatchQueryDev &d = qh[q];
+        d.N = p->N;
+        d.K = p->K;
+        d.D = p->D;
+        d.nu = p->nu;
+        d.J = p->J;
+        d.flag = p->flag;
+        d.item_sum = p->item_sum;
+        d.item_count = p->item_count;
+        d.w_c = p->prm.w_c;
+        d.w_l = p->prm.w_l;
+        d.lambda_c = p->prm.lambda_c;
+        d.xi = p->xi;
+        d.mu = p->mu;
+        d.C = p->C;
+        d.L = p->L;
+        d.Lt = p->Lt;
+        d.seed_lo = (uint32_t)p->prm.seed;
+        d.seed_hi = (uint32_t)(p->prm.seed >> 32);
+        d.query = p->prm.query;
+        d.sigma2 = p->prm.sigma * p->prm.sigma;
+        d.elite = p->elite;
+        d.elites = p->elites;
+        d.w = p->w;
+        d.best = p->best;
+        d.s2p = p->cov_part;
+        d.s1p = p->mean_part;
+        d.eps = p->prm.eps;
+        d.n_chunks = moments_chunking(p->nu, &d.per);
+        d.cand_off = (int)off;
+        d.status = p->status;
+        d.consts = p->consts;
+        d.init_std_frac = p->prm.init_std_frac;
+        d.ends = p->ends_f;
+        d.mean_xi = p->mean_xi;
+        d.mean_J = p->mean_J;
+        d.mean_terms = p->mean_terms;
+        d.mean_flag = p->mean_flag;
+        d.ctrl = p->ctrl;
+        // the evaluation arguments of cp_plan's launches (run_eval) for the population and
+        // the mean candidate
+        for (int m = 0; m < 2; ++m) {
+            EvalArgs a{};
+            const int n = m == 0 ? p->N : 1;
+            a.xi = (const float4 *)(m == 0 ? p->xi : p->mean_xi);
+            a.n = n;
+            a.K = p->K;
+            a.S = p->S;
+            a.n_s = p->n_s;
+            a.chunks = p->chunks;
+            a.G = eval_units_per_item(n, p->chunks);
+            a.P = (p->chunks + a.G - 1) / a.G;
+            a.div_S = fast_div((uint32_t)p->S);
+            a.div_P = fast_div((uint32_t)a.P);
+            a.ends = p->ends_f;
+            a.broadphase = 1;
+            a.status = p->status;
+            a.basis = p->basis;
+            a.item_sum = p->item_sum;
+            a.item_count = p->item_count;
+            BatchEvalDev &ev = m == 0 ? eh[q] : mh[q];
+            ev.a = a;
+            ev.sc = p->sdev;
+            ev.g = p->gdev;
+            (m == 0 ? b->items_pop : b->items_mean)[q] = n * a.P;
+            if (m == 0) {
+                d.P = a.P;
+                G[q] = a.G;
+            }
+        }
+        off += p->N;
     }
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e_end = cudaStreamEndCapture(b->origin, &graph);
-    b->graph = graph;
-    b->kernel_nodes = g_launches.load() - launches_before;   // recorded, not run
-    g_launches.fetch_sub(b->kernel_nodes);
-    if (rc != CP_OK) return fail(rc);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "recording the batch graph"));
-    if (e_end != cudaSuccess) return fail(cuda_fail(e_end, "cudaStreamEndCapture"));
-    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
-        return fail(cuda_fail(e, "cudaGraphInstantiate"));
+    b->total = off;
+    if (b->total > (1ll << 30)) return fail((set_error("the batch holds %lld candidates; at most 2^30", (long long)off), CP_ERR_ARG));
+    b->order.resize(nq);
+    for (int q = 0; q < nq; ++q) b->order[q] = q;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return G[x] > G[y]; });
+
+    std::vector<int2> t_init, t_sample, t_cand, t_gather, t_mpart, t_mcomb;
+    block_table(nq, [&](int q) { return (qh[q].D * qh[q].D + 255) / 256; }, t_init);
+    block_table(nq, [&](int q) { return (qh[q].N + kBatchSampleCands - 1) / kBatchSampleCands; }, t_sample);
+    block_table(nq, [&](int q) { return (qh[q].N + 255) / 256; }, t_cand);
+    block_table(nq, [&](int q) { return (qh[q].nu + 7) / 8; }, t_gather);
+    block_table(nq, [&](int q) {
+        const int nt = (qh[q].D + 15) / 16;
+        return nt * (nt + 1) / 2 * qh[q].n_chunks;
+    }, t_mpart);
+    block_table(nq, [&](int q) { return (qh[q].D * (qh[q].D + 1) / 2 + 7) / 8; }, t_mcomb);
+    int64_t max_tiles = 0;
+    for (int q = 0; q < nq; ++q) max_tiles += std::max(b->items_pop[q], b->items_mean[q]);   // tiles of >= 1 item
+    b->tiles_cap = max_tiles;
+    const int64_t tiles_radix = radix_tiles((int)b->total);
+
+    Layout L;
+    const size_t o_in = L.take<double>(8 * (size_t)nq);
+    const size_t o_out = L.take<double>((size_t)kOutStride * nq);
+    const size_t o_q = L.take<BatchQueryDev>(nq);
+    const size_t o_ep = L.take<BatchEvalDev>(nq);
+    const size_t o_em = L.take<BatchEvalDev>(nq);
+    const size_t o_ti = L.take<int2>(t_init.size());
+    const size_t o_ts = L.take<int2>(t_sample.size());
+    const size_t o_tc = L.take<int2>(t_cand.size());
+    const size_t o_tg = L.take<int2>(t_gather.size());
+    const size_t o_tp = L.take<int2>(t_mpart.size());
+    const size_t o_tm = L.take<int2>(t_mcomb.size());
+    const size_t o_tilp = L.take<int4>((size_t)max_tiles);
+    const size_t o_tilm = L.take<int4>((size_t)max_tiles);
+    const size_t o_queue = L.take<int>((size_t)iters + 2);
+    const size_t o_qid = L.take<uint16_t>((size_t)b->total);
+    const size_t o_ka = L.take<unsigned long long>((size_t)b->total);
+    const size_t o_kb = L.take<unsigned long long>((size_t)b->total);
+    const size_t o_va = L.take<int>((size_t)b->total);
+    const size_t o_vb = L.take<int>((size_t)b->total);
+    const size_t o_h = L.take<int>(256 * (size_t)tiles_radix);
+    if ((e = cudaMalloc((void **)&b->base, L.bytes)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(batch)"));
+    char *base = b->base;
+    b->d_in = (double *)(base + o_in);
+    b->d_out = (double *)(base + o_out);
+    b->qdev = (BatchQueryDev *)(base + o_q);
+    b->ev_pop = (BatchEvalDev *)(base + o_ep);
+    b->ev_mean = (BatchEvalDev *)(base + o_em);
+    b->tab_init = (int2 *)(base + o_ti);
+    b->tab_sample = (int2 *)(base + o_ts);
+    b->tab_cand = (int2 *)(base + o_tc);
+    b->tab_gather = (int2 *)(base + o_tg);
+    b->tab_mpart = (int2 *)(base + o_tp);
+    b->tab_mcomb = (int2 *)(base + o_tm);
+    b->tiles_pop = (int4 *)(base + o_tilp);
+    b->tiles_mean = (int4 *)(base + o_tilm);
+    b->queue = (int *)(base + o_queue);
+    b->qid = (uint16_t *)(base + o_qid);
+    b->key_a = (unsigned long long *)(base + o_ka);
+    b->key_b = (unsigned long long *)(base + o_kb);
+    b->val_a = (int *)(base + o_va);
+    b->val_b = (int *)(base + o_vb);
+    b->hist = (int *)(base + o_h);
+    b->n_init = (int)t_init.size();
+    b->n_sample = (int)t_sample.size();
+    b->n_cand = (int)t_cand.size();
+    b->n_gather = (int)t_gather.size();
+    b->n_mpart = (int)t_mpart.size();
+    b->n_mcomb = (int)t_mcomb.size();
+    std::vector<uint16_t> qid((size_t)b->total);
+    for (int q = 0; q < nq; ++q)
+        std::fill(qid.begin() + qh[q].cand_off, qid.begin() + qh[q].cand_off + qh[q].N, (uint16_t)q);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->st);
+    };
+    if ((e = up(b->qdev, qh.data(), sizeof(BatchQueryDev) * nq)) != cudaSuccess ||
+        (e = up(b->ev_pop, eh.data(), sizeof(BatchEvalDev) * nq)) != cudaSuccess ||
+        (e = up(b->ev_mean, mh.data(), sizeof(BatchEvalDev) * nq)) != cudaSuccess ||
+        (e = up(b->tab_init, t_init.data(), sizeof(int2) * t_init.size())) != cudaSuccess ||
+        (e = up(b->tab_sample, t_sample.data(), sizeof(int2) * t_sample.size())) != cudaSuccess ||
+        (e = up(b->tab_cand, t_cand.data(), sizeof(int2) * t_cand.size())) != cudaSuccess ||
+        (e = up(b->tab_gather, t_gather.data(), sizeof(int2) * t_gather.size())) != cudaSuccess ||
+        (e = up(b->tab_mpart, t_mpart.data(), sizeof(int2) * t_mpart.size())) != cudaSuccess ||
+        (e = up(b->tab_mcomb, t_mcomb.data(), sizeof(int2) * t_mcomb.size())) != cudaSuccess ||
+        (e = up(b->qid, qid.data(), sizeof(uint16_t) * qid.size())) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaMemcpyAsync(batch tables)"));
+    if ((rc = batch_upload_tiles(b)) != CP_OK) return fail(rc);   // synchronises
+    if ((rc = batch_record_graph(b)) != CP_OK) return fail(rc);
     *out = b;
     return CP_OK;
 }
@@ -1427,7 +1690,7 @@ int cp_batch_set_endpoints(cp_batch *b, int32_t q, const double h_q0[4], const d
     if (!b || !h_q0 || !h_qd || q < 0 || q >= b->nq) return set_error("invalid arguments"), CP_ERR_ARG;
     for (int j = 0; j < 4; ++j)
         if (!is_finite(h_q0[j]) || !is_finite(h_qd[j])) return set_error("end points must be finite"), CP_ERR_ARG;
-    CP_CUDA(cudaStreamSynchronize(b->origin));   // the graph may be reading the inputs
+    CP_CUDA(cudaStreamSynchronize(b->st));   // the graph may be reading the inputs
     memcpy(b->h_in + 8 * q, h_q0, 4 * sizeof(double));
     memcpy(b->h_in + 8 * q + 4, h_qd, 4 * sizeof(double));
     return CP_OK;
@@ -1436,12 +1699,19 @@ int cp_batch_set_endpoints(cp_batch *b, int32_t q, const double h_q0[4], const d
 int cp_batch_run(cp_batch *b, cp_batch_result *results)
 {
     if (!b) return set_error("batch is NULL"), CP_ERR_ARG;
-    CP_CUDA(cudaGraphLaunch(b->exec, b->origin));
+    CP_CUDA(cudaGraphLaunch(b->exec, b->st));
     g_launches.fetch_add(b->kernel_nodes, std::memory_order_relaxed);
-    CP_CUDA(cudaStreamSynchronize(b->origin));
+    CP_CUDA(cudaStreamSynchronize(b->st));
     int rc = CP_OK;
     for (int q = 0; q < b->nq; ++q) {
         const double *o = b->h_out + kOutStride * q;
+        cp_planner *p = b->planners[q];
+        // the query's planner now holds the state after `iters` iterations from the start
+        p->iteration = b->iters;
+        p->elites_ready = false;
+        const double *in = b->h_in + 8 * q;
+        p->q0f = make_float4((float)in[0], (float)in[1], (float)in[2], (float)in[3]);
+        p->qdf = make_float4((float)in[4], (float)in[5], (float)in[6], (float)in[7]);
         if (results) {
             cp_batch_result &r = results[q];
             memset(&r, 0, sizeof r);
@@ -1455,14 +1725,75 @@ int cp_batch_run(cp_batch *b, cp_batch_result *results)
             r.stats.iterations = b->iters;
             r.stats.iteration = b->iters;
             r.stats.best_J = o[6];
-            memcpy(r.ctrl, o + 8, sizeof(double) * 4 * (b->planners[q]->K + 8));
+            memcpy(r.ctrl, o + 8, sizeof(double) * 4 * (p->K + 8));
         }
-        if (b->h_status[q] != 0 && rc == CP_OK) {
-            set_error("query %d: the covariance is not positive definite", q);
-            rc = CP_ERR_NUMERIC;
+        const uint32_t status = (uint32_t)o[7];
+        if (status != 0 && rc == CP_OK) {
+            if (status & DEV_ERR_NOT_PD) {
+                set_error("query %d: the covariance is not positive definite", q);
+                rc = CP_ERR_NUMERIC;
+            } else {
+                set_error("query %d: the obstacle index met more entries than its capacity, or the ranking "
+                          "placed a foreign candidate in the query's range (status %u)", q, status);
+                rc = CP_ERR_ARG;
+            }
         }
     }
     return rc;
+}
+
+int cp_batch_set_shape(cp_batch *b, const cp_batch_shape *shape)
+{
+    if (!b || !shape) return set_error("invalid arguments"), CP_ERR_ARG;
+    if (shape->threads != 128 && shape->threads != 256 && shape->threads != 512)
+        return set_error("threads = %d is not 128, 256 or 512", shape->threads), CP_ERR_ARG;
+    if (shape->ctas_per_sm < 0 || shape->ctas_per_sm > 32)
+        return set_error("ctas_per_sm = %d outside 0..32", shape->ctas_per_sm), CP_ERR_ARG;
+    if (shape->items_per_warp < 1 || shape->items_per_warp > 64)
+        return set_error("items_per_warp = %d outside 1..64", shape->items_per_warp), CP_ERR_ARG;
+    CP_CUDA(cudaStreamSynchronize(b->st));
+    const cp_batch_shape old = b->shape;
+    b->shape = *shape;
+    int rc = batch_upload_tiles(b);
+    if (rc == CP_OK) rc = batch_record_graph(b);
+    if (rc != CP_OK) {
+        b->shape = old;
+        batch_upload_tiles(b);
+        batch_record_graph(b);
+    }
+    return rc;
+}
+
+int cp_batch_evaluate(cp_batch *b, int32_t reps, double *ms)
+{
+    if (!b || !ms || reps < 1) return set_error("invalid arguments"), CP_ERR_ARG;
+    int *counter = b->queue + b->iters + 1;
+    double total = 0.0;
+    for (int r = 0; r < reps; ++r) {
+        CP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), b->st));
+        CP_CUDA(cudaEventRecord(b->ev0, b->st));
+        int rc = launch_batch_eval_polar(b->mdev, b->ev_pop, b->tiles_pop, b->n_tiles_pop, counter, b->max_S,
+                                         b->shape.threads, b->eval_blocks, b->st);
+        if (rc != CP_OK) return rc;
+        CP_CUDA(cudaEventRecord(b->ev1, b->st));
+        CP_CUDA(cudaEventSynchronize(b->ev1));
+        float t = 0.f;
+        CP_CUDA(cudaEventElapsedTime(&t, b->ev0, b->ev1));
+        total += t;
+    }
+    *ms = total / reps;
+    return CP_OK;
+}
+
+int cp_batch_get_info(const cp_batch *b, cp_batch_info *out)
+{
+    if (!b || !out) return set_error("invalid arguments"), CP_ERR_ARG;
+    out->kernel_nodes = b->kernel_nodes;
+    out->eval_tiles = b->n_tiles_pop;
+    out->eval_ctas = b->eval_blocks;
+    out->eval_launches = b->iters + 1;
+    out->candidates = b->total;
+    return CP_OK;
 }
 
 cp_planner *cp_batch_planner(cp_batch *b, int32_t q)
@@ -1474,7 +1805,6 @@ cp_planner *cp_batch_planner(cp_batch *b, int32_t q)
 void cp_batch_destroy(cp_batch *b)
 {
     if (!b) return;
-    if (b->origin) cudaStreamSynchronize(b->origin);
     batch_free(b);
 }
 

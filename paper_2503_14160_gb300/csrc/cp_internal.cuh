@@ -285,4 +285,70 @@ int launch_gather_elites(const int *sorted, const double *J, const float *xi, in
 constexpr int kRadixMinN = 8193;   // the radix sort ranks populations above 8192
 int update_configure();
 
+// ------------------------------------------------------------------ batched form
+// One launch of each stage serves every query of a batch. Each query keeps its own planner
+// workspace; the batched kernels reach it through this per-query view, and a block finds its
+// query in a table of {query, block within the query} built once per batch, so that every
+// query's arithmetic is that of its planner run alone.
+struct BatchEvalDev {          // what the evaluation of one query reads (restaged per query)
+    EvalArgs a;
+    SceneDev sc;
+    PolarDev g;
+};
+
+struct BatchQueryDev {
+    int N, K, D, nu;
+    double *J;                       // [N] costs of the population
+    uint8_t *flag;                   // [N]
+    const double *item_sum;          // [N][P][4] of the population's evaluation
+    const uint32_t *item_count;
+    int P;                           // items per candidate of the population's evaluation
+    double w_c, w_l, lambda_c;
+    float *xi;                       // [N][D] population
+    double *mu, *C, *L;
+    float *Lt;
+    uint32_t seed_lo, seed_hi, query;
+    double sigma2;                   // sigma^2 of the factor
+    int *elite;                      // [nu] elite indices in rank order
+    float *elites;                   // [nu][D]
+    const double *w;                 // [nu] elite weights
+    double *best;                    // cost of the best candidate
+    double *s2p, *s1p;               // moment partials
+    double eps;
+    int per, n_chunks;               // elites per moment chunk, chunks
+    int cand_off;                    // first position of the query in the concatenated ranking
+    uint32_t *status;
+    double *consts;                  // q0[4], qd[4], q_min[4], q_max[4]
+    double init_std_frac;
+    float4 *ends;                    // {q0, qd} in float
+    float *mean_xi;
+    double *mean_J, *mean_terms;
+    uint8_t *mean_flag;
+    double *ctrl;                    // [K + 8][4]
+};
+
+// Block-to-query tables: entry b = {query, block index within the query}.
+int launch_batch_init(const BatchQueryDev *qd, const int2 *tab, int blocks, const double *inputs, cudaStream_t st);
+int launch_batch_factor(const BatchQueryDev *qd, int nq, int max_D, cudaStream_t st);
+int launch_batch_sample(const BatchQueryDev *qd, const int2 *tab, int blocks, int max_K, uint32_t iter,
+                        cudaStream_t st);
+constexpr int kBatchSampleCands = 128;   // candidates per block of the batched sampler
+int batch_eval_configure();
+int launch_batch_eval_polar(const ModelDev &m, const BatchEvalDev *qd, const int4 *tiles, int n_tiles, int *queue,
+                            int max_S, int threads, int blocks, cudaStream_t st);
+int batch_eval_max_blocks(const ModelDev &m, int threads, int max_S, int num_sms);
+// tab non-null: the populations (blocks of 256 candidates); null: the mean candidates of
+// `blocks` queries, whose evaluation is described by mean_ev.
+int launch_batch_finalize(const BatchQueryDev *qd, const int2 *tab, int blocks, const BatchEvalDev *mean_ev,
+                          cudaStream_t st);
+int launch_batch_radix_rank(const BatchQueryDev *qd, const int2 *tab, int blocks, int total, int nq,
+                            const uint16_t *qid, unsigned long long *key_a, unsigned long long *key_b,
+                            int *val_a, int *val_b, int *hist, int **sorted, cudaStream_t st);
+int launch_batch_gather(const BatchQueryDev *qd, const int2 *tab, int blocks, const int *sorted, cudaStream_t st);
+int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_partial, int blocks_partial,
+                         const int2 *tab_combine, int blocks_combine, cudaStream_t st);
+int moments_chunking(int nu, int *per);   // chunks of the moment partials and elites per chunk
+int launch_batch_outputs(const BatchQueryDev *qd, int nq, bool mean_candidate, double *out, int out_stride,
+                         cudaStream_t st);
+
 }  // namespace cp

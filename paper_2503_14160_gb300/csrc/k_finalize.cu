@@ -8,12 +8,11 @@
 namespace cp {
 namespace {
 
-__global__ void __launch_bounds__(256)
-k_eval_finalize(const double *__restrict__ item_sum, const uint32_t *__restrict__ item_count, int n, int P,
-                double w_c, double w_l, double lambda_c, double *J, uint8_t *flag, double *terms,
-                const uint32_t *status)
+__device__ __forceinline__ void finalize_body(const double *__restrict__ item_sum,
+                                              const uint32_t *__restrict__ item_count, int n, int P, double w_c,
+                                              double w_l, double lambda_c, double *J, uint8_t *flag, double *terms,
+                                              const uint32_t *status, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double *row = item_sum + (size_t)i * P * 4;
     const uint32_t *crow = item_count + (size_t)i * P;
@@ -48,6 +47,33 @@ k_eval_finalize(const double *__restrict__ item_sum, const uint32_t *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(256)
+k_eval_finalize(const double *__restrict__ item_sum, const uint32_t *__restrict__ item_count, int n, int P,
+                double w_c, double w_l, double lambda_c, double *J, uint8_t *flag, double *terms,
+                const uint32_t *status)
+{
+    finalize_body(item_sum, item_count, n, P, w_c, w_l, lambda_c, J, flag, terms, status,
+                  blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Every query's costs in one launch: block b of query q takes its candidates 256 b ..; the
+// mean form takes the single mean candidate of query blockIdx.x (with the terms).
+__global__ void __launch_bounds__(256)
+k_batch_finalize(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab, const BatchEvalDev *ev)
+{
+    if (tab != nullptr) {
+        const int2 e = tab[blockIdx.x];
+        const BatchQueryDev &q = qd[e.x];
+        finalize_body(q.item_sum, q.item_count, q.N, q.P, q.w_c, q.w_l, q.lambda_c, q.J, q.flag, nullptr, nullptr,
+                      e.y * 256 + (int)threadIdx.x);
+    } else {
+        const BatchQueryDev &q = qd[blockIdx.x];
+        const EvalArgs &a = ev[blockIdx.x].a;
+        finalize_body(a.item_sum, a.item_count, 1, a.P, q.w_c, q.w_l, q.lambda_c, q.mean_J, q.mean_flag,
+                      q.mean_terms, nullptr, (int)threadIdx.x);
+    }
+}
+
 }  // namespace
 
 int launch_eval_finalize(const double *item_sum, const uint32_t *item_count, int n, int P,
@@ -59,6 +85,19 @@ int launch_eval_finalize(const double *item_sum, const uint32_t *item_count, int
     k_eval_finalize<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
         item_sum, item_count, n, P, w_c, w_l, lambda_c, J, flag, terms, status);
     CP_LAUNCHED("k_eval_finalize");
+    return CP_OK;
+}
+
+}  // namespace cp
+
+namespace cp {
+
+int launch_batch_finalize(const BatchQueryDev *qd, const int2 *tab, int blocks, const BatchEvalDev *mean_ev,
+                          cudaStream_t st)
+{
+    if (blocks == 0) return CP_OK;
+    k_batch_finalize<<<blocks, tab != nullptr ? 256 : 32, 0, st>>>(qd, tab, mean_ev);
+    CP_LAUNCHED("k_batch_finalize");
     return CP_OK;
 }
 

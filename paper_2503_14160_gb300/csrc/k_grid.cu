@@ -171,6 +171,78 @@ __device__ __forceinline__ float polar_exact(const ModelDev &m, const SceneDev &
     return d;
 }
 
+// One work item (candidate, G consecutive units) of the polar form on one warp: per lane a
+// checkpoint, its spheres' in-band extent of h, the one or two angular bins and the ring
+// range that can hold an obstacle within reach, the packed filter over the listed entries
+// and the exact distance of those that pass.
+template <int NSPH>
+static __device__ __forceinline__ void polar_item(const ModelDev &m, const SceneDev &sc, const PolarDev &g,
+                                                  const EvalArgs &a, const float4 *s_basis, float4 *s_ctrl,
+                                                  int it, int lane, uint32_t &survivors, uint32_t &tests)
+{
+    const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
+    const float zero[NSPH] = {};
+    const ItemRange ir = item_range(a, it);
+    stage_controls(s_ctrl, a, ir.cand, lane);
+    double acc = 0.0;
+    uint32_t count = 0;
+    for (int chunk = ir.c0; chunk < ir.c1; ++chunk) {
+        const Checkpoint c = checkpoint_at(m, a, s_basis, s_ctrl, chunk, lane);
+        float H[NSPH], Z[NSPH], s1, c1;
+        crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
+        // in-band extent of h at this lane; spheres outside the scene's height band (widened
+        // by r_max) can penetrate nothing: they take no part (1e30 in the packed h)
+        float hmin, hmax;
+        band_extent<NSPH>(H, Z, zlo, zhi, hmin, hmax);
+        float dmin = CUDART_INF_F;
+        if (hmin <= hmax) {
+            float2 H2[NSPH / 2];
+#pragma unroll
+            for (int q = 0; q < NSPH / 2; ++q)
+                H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
+                                    Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
+            const float phi0 = wrap_angle(c.q.x);
+#pragma unroll 1
+            for (int side = 0; side < 2; ++side) {
+                // spheres with h >= 0 lie on the half-line at the slew angle, those with h < 0
+                // on the opposite one, at distance |h| from the axis
+                const float r_lo = side ? fmaxf(-hmax, 0.f) : fmaxf(hmin, 0.f);
+                const float r_hi = side ? -hmin : hmax;
+                if (!(r_lo <= r_hi)) continue;
+                const float ang = side ? (phi0 >= 0.f ? phi0 - kPi : phi0 + kPi) : phi0;
+                const int bin = min(max((int)floorf((ang + kPi) * g.inv_da), 0), g.n_ang - 1);
+                const float reach = g.w_max + kPolarPadR;
+                const int r0 = min(max((int)floorf((r_lo - reach) * g.inv_dr), 0), g.n_ring - 1);
+                const int r1 = min(max((int)floorf((r_hi + reach) * g.inv_dr), 0), g.n_ring - 1);
+                const int cell = bin * g.n_ring;
+                const int beg = __ldg(g.cell_start + cell + r0);
+                const int end = min(__ldg(g.cell_start + cell + r1 + 1), g.capacity);
+                tests += (uint32_t)max(end - beg, 0);
+                for (int e = beg; e < end; ++e) {
+                    const float4 rec = __ldg(g.items + e);   // {cx, cy, bound, id}
+                    const float p = fmaf(c1, rec.x, s1 * rec.y);
+                    const float q = fmaf(c1, rec.y, -(s1 * rec.x));
+                    const float rhs = fmaf(-q, q, rec.z);
+                    const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
+                    float2 t[NSPH / 2];
+#pragma unroll
+                    for (int k = 0; k < NSPH / 2; ++k) {
+                        const float2 dh = __fadd2_rn(H2[k], mp2);
+                        t[k] = __ffma2_rn(dh, dh, mr2);
+                    }
+                    if (any_below<NSPH>(t, zero)) {
+                        ++survivors;
+                        dmin = fminf(dmin, polar_exact<NSPH>(m, sc, H, Z, c1, s1, p, rhs, __float_as_int(rec.w)));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        unit_accumulate(a, c, dmin, ir.cand, chunk, lane, acc, count);
+    }
+    item_flush(a, it, acc, count, lane);
+}
+
 template <int NSPH>
 __global__ void __launch_bounds__(kPolarThreads, CP_POLAR_MIN_BLOCKS)
 k_eval_polar(const ModelDev m, const SceneDev sc, const PolarDev g, const EvalArgs a)
@@ -184,76 +256,54 @@ k_eval_polar(const ModelDev m, const SceneDev sc, const PolarDev g, const EvalAr
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     const int items = a.n * a.P;
-    const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
-    const float zero[NSPH] = {};
     uint32_t survivors = 0, tests = 0;   // (lane, obstacle) pairs passing the packed filter; tested
-
-    for (int it = warp; it < items; it += n_warps) {
-        const ItemRange ir = item_range(a, it);
-        stage_controls(s_ctrl, a, ir.cand, lane);
-        double acc = 0.0;
-        uint32_t count = 0;
-        for (int chunk = ir.c0; chunk < ir.c1; ++chunk) {
-            const Checkpoint c = checkpoint_at(m, a, s_basis, s_ctrl, chunk, lane);
-            float H[NSPH], Z[NSPH], s1, c1;
-            crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
-            // in-band extent of h at this lane; spheres outside the scene's height band (widened
-            // by r_max) can penetrate nothing: they take no part (1e30 in the packed h)
-            float hmin, hmax;
-            band_extent<NSPH>(H, Z, zlo, zhi, hmin, hmax);
-            float dmin = CUDART_INF_F;
-            if (hmin <= hmax) {
-                float2 H2[NSPH / 2];
-#pragma unroll
-                for (int q = 0; q < NSPH / 2; ++q)
-                    H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
-                                        Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
-                const float phi0 = wrap_angle(c.q.x);
-#pragma unroll 1
-                for (int side = 0; side < 2; ++side) {
-                    // spheres with h >= 0 lie on the half-line at the slew angle, those with h < 0
-                    // on the opposite one, at distance |h| from the axis
-                    const float r_lo = side ? fmaxf(-hmax, 0.f) : fmaxf(hmin, 0.f);
-                    const float r_hi = side ? -hmin : hmax;
-                    if (!(r_lo <= r_hi)) continue;
-                    const float ang = side ? (phi0 >= 0.f ? phi0 - kPi : phi0 + kPi) : phi0;
-                    const int bin = min(max((int)floorf((ang + kPi) * g.inv_da), 0), g.n_ang - 1);
-                    const float reach = g.w_max + kPolarPadR;
-                    const int r0 = min(max((int)floorf((r_lo - reach) * g.inv_dr), 0), g.n_ring - 1);
-                    const int r1 = min(max((int)floorf((r_hi + reach) * g.inv_dr), 0), g.n_ring - 1);
-                    const int cell = bin * g.n_ring;
-                    const int beg = __ldg(g.cell_start + cell + r0);
-                    const int end = min(__ldg(g.cell_start + cell + r1 + 1), g.capacity);
-                    tests += (uint32_t)max(end - beg, 0);
-                    for (int e = beg; e < end; ++e) {
-                        const float4 rec = __ldg(g.items + e);   // {cx, cy, bound, id}
-                        const float p = fmaf(c1, rec.x, s1 * rec.y);
-                        const float q = fmaf(c1, rec.y, -(s1 * rec.x));
-                        const float rhs = fmaf(-q, q, rec.z);
-                        const float2 mp2 = make_float2(-p, -p), mr2 = make_float2(-rhs, -rhs);
-                        float2 t[NSPH / 2];
-#pragma unroll
-                        for (int k = 0; k < NSPH / 2; ++k) {
-                            const float2 dh = __fadd2_rn(H2[k], mp2);
-                            t[k] = __ffma2_rn(dh, dh, mr2);
-                        }
-                        if (any_below<NSPH>(t, zero)) {
-                            ++survivors;
-                            dmin = fminf(dmin, polar_exact<NSPH>(m, sc, H, Z, c1, s1, p, rhs, __float_as_int(rec.w)));
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            unit_accumulate(a, c, dmin, ir.cand, chunk, lane, acc, count);
-        }
-        item_flush(a, it, acc, count, lane);
-    }
+    for (int it = warp; it < items; it += n_warps) polar_item<NSPH>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
     if (a.work != nullptr) {
         const uint32_t ws = __reduce_add_sync(0xffffffffu, survivors);
         const uint32_t wt = __reduce_add_sync(0xffffffffu, tests);
         if (lane == 0 && ws != 0) atomicAdd(a.work, (unsigned long long)ws);
         if (lane == 0 && wt != 0) atomicAdd(a.work + 1, (unsigned long long)wt);
+    }
+}
+
+// The evaluations of every query of a batch in one persistent launch. The work is a list of
+// tiles {query, first item, end item} (a tile is one query's consecutive work items); each
+// CTA takes the next tile from a device counter (an atomic add: no CTA ever waits on
+// another) until the list is exhausted. When the query of its tile differs from the one it
+// holds, the CTA restages: it copies the query's view (its evaluation arguments, obstacle
+// records and polar index) and the query's spline table into shared memory. The warps then
+// take the tile's items in turn; an item's arithmetic is that of the single-query launch.
+template <int NSPH, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_batch_eval_polar(const ModelDev m, const BatchEvalDev *__restrict__ qd, const int4 *__restrict__ tiles,
+                   int n_tiles, int *queue, int max_S)
+{
+    extern __shared__ __align__(16) float4 s_basis[];
+    __shared__ __align__(16) BatchEvalDev s_q;
+    __shared__ int s_tile;
+    constexpr int W = THREADS / 32;
+    float4 *s_ctrl = s_basis + 2 * max_S + (threadIdx.x >> 5) * kCtrlSlots;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int held = -1;
+    uint32_t survivors = 0, tests = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= n_tiles) break;
+        const int4 tile = __ldg(tiles + t);
+        if (tile.x != held) {
+            held = tile.x;
+            const int *src = reinterpret_cast<const int *>(qd + held);
+            int *dst = reinterpret_cast<int *>(&s_q);
+            for (int i = threadIdx.x; i < (int)(sizeof(BatchEvalDev) / sizeof(int)); i += THREADS) dst[i] = __ldg(src + i);
+            __syncthreads();
+            for (int i = threadIdx.x; i < 2 * s_q.a.S; i += THREADS) s_basis[i] = __ldg(s_q.a.basis + i);
+            __syncthreads();
+        }
+        for (int it = tile.y + wib; it < tile.z; it += W)
+            polar_item<NSPH>(m, s_q.sc, s_q.g, s_q.a, s_basis, s_ctrl, it, lane, survivors, tests);
+        __syncthreads();   // the tile's items are done before s_tile and s_q change
     }
 }
 
@@ -358,6 +408,56 @@ int launch_eval_polar(const ModelDev &m, const SceneDev &sc, const PolarDev &g, 
     else
         k_eval_polar<16><<<grid, kPolarThreads, smem, st>>>(m, sc, g, a);
     CP_LAUNCHED("k_eval_polar");
+    return CP_OK;
+}
+
+// Batched form: CTAs of 128, 256 or 512 threads (block shape picked by the autotuner).
+template <int NSPH, int THREADS>
+static auto batch_eval_kernel()
+{
+    constexpr int MINB = THREADS == 128 ? 2 * CP_POLAR_MIN_BLOCKS : (THREADS == 256 ? CP_POLAR_MIN_BLOCKS : 1);
+    return k_batch_eval_polar<NSPH, THREADS, MINB>;
+}
+
+template <int NSPH>
+static void *batch_eval_fn(int threads)
+{
+    if (threads == 128) return (void *)batch_eval_kernel<NSPH, 128>();
+    if (threads == 256) return (void *)batch_eval_kernel<NSPH, 256>();
+    if (threads == 512) return (void *)batch_eval_kernel<NSPH, 512>();
+    return nullptr;
+}
+
+static size_t batch_eval_smem(int threads, int max_S)
+{
+    return sizeof(float4) * (2 * (size_t)max_S + (size_t)(threads / 32) * kCtrlSlots);
+}
+
+int batch_eval_max_blocks(const ModelDev &m, int threads, int max_S, int num_sms)
+{
+    void *fn = m.n_spheres == 12 ? batch_eval_fn<12>(threads) : batch_eval_fn<16>(threads);
+    if (fn == nullptr) return set_error("batched evaluation: %d threads per CTA is not 128, 256 or 512", threads), -1;
+    const size_t smem = batch_eval_smem(threads, max_S);
+    cudaFuncAttributes at{};
+    CP_CUDA(cudaFuncGetAttributes(&at, fn));
+    if ((size_t)at.maxDynamicSharedSizeBytes < smem)
+        CP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    return (per_sm < 1 ? 1 : per_sm) * num_sms;
+}
+
+int launch_batch_eval_polar(const ModelDev &m, const BatchEvalDev *qd, const int4 *tiles, int n_tiles, int *queue,
+                            int max_S, int threads, int blocks, cudaStream_t st)
+{
+    if (n_tiles == 0) return CP_OK;
+    void *fn = m.n_spheres == 12 ? batch_eval_fn<12>(threads) : batch_eval_fn<16>(threads);
+    if (fn == nullptr) return set_error("batched evaluation: %d threads per CTA is not 128, 256 or 512", threads), CP_ERR_ARG;
+    const size_t smem = batch_eval_smem(threads, max_S);
+    ModelDev mm = m;
+    void *args[] = {(void *)&mm, (void *)&qd, (void *)&tiles, (void *)&n_tiles, (void *)&queue, (void *)&max_S};
+    CP_CUDA(cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, st));
+    CP_LAUNCHED("k_batch_eval_polar");
     return CP_OK;
 }
 

@@ -88,30 +88,57 @@ __global__ void k_basis_table(int S, float4 *basis)
 }
 
 // mu[4f + c] = q0[c] + (f+1)/(K+1) (qd[c] - q0[c]); C = diag((frac (q_max - q_min))^2).
+__device__ __forceinline__ void init_entry(int idx, const double *q0, const double *qd, const double *q_min,
+                                           const double *q_max, int K, double frac, double *mu, double *C)
+{
+    const int D = 4 * K;
+    const int r = idx / D, c = idx - r * D;
+    double v = 0.0;
+    if (r == c) {
+        const int j = r & 3;
+        const double sd = frac * (q_max[j] - q_min[j]);
+        v = sd * sd;
+    }
+    C[idx] = v;
+    if (idx < D) {
+        const int f = idx >> 2, j = idx & 3;
+        mu[idx] = q0[j] + (double)(f + 1) / (double)(K + 1) * (qd[j] - q0[j]);
+    }
+}
+
+__device__ __forceinline__ void ends_to_float(const double *q0, const double *qd, float4 *ends_f)
+{
+    ends_f[0] = make_float4((float)q0[0], (float)q0[1], (float)q0[2], (float)q0[3]);
+    ends_f[1] = make_float4((float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]);
+}
+
 __global__ void k_init_distribution(const double *q0, const double *qd, const double *q_min,
                                     const double *q_max, int K, double frac, double *mu,
                                     double *C, float4 *ends_f)
 {
     const int D = 4 * K;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && ends_f != nullptr) {
-        ends_f[0] = make_float4((float)q0[0], (float)q0[1], (float)q0[2], (float)q0[3]);
-        ends_f[1] = make_float4((float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]);
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ends_f != nullptr) ends_to_float(q0, qd, ends_f);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < D * D;
-         idx += gridDim.x * blockDim.x) {
-        const int r = idx / D, c = idx - r * D;
-        double v = 0.0;
-        if (r == c) {
-            const int j = r & 3;
-            const double sd = frac * (q_max[j] - q_min[j]);
-            v = sd * sd;
-        }
-        C[idx] = v;
-        if (idx < D) {
-            const int f = idx >> 2, j = idx & 3;
-            mu[idx] = q0[j] + (double)(f + 1) / (double)(K + 1) * (qd[j] - q0[j]);
-        }
+         idx += gridDim.x * blockDim.x)
+        init_entry(idx, q0, qd, q_min, q_max, K, frac, mu, C);
+}
+
+// The start of every query of a batch: end points from inputs[q][8] = {q0, qd} into the
+// query's constants and float copy, its status cleared, and its initial distribution (block
+// b of query q: entries 256 b .. of C).
+__global__ void __launch_bounds__(256)
+k_batch_init(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab, const double *__restrict__ inputs)
+{
+    const int2 e = tab[blockIdx.x];
+    const BatchQueryDev &q = qd[e.x];
+    const double *in = inputs + 8 * e.x;
+    if (e.y == 0 && threadIdx.x < 8) q.consts[threadIdx.x] = in[threadIdx.x];
+    if (e.y == 0 && threadIdx.x == 0) {
+        ends_to_float(in, in + 4, q.ends);
+        *q.status = 0u;
     }
+    const int idx = e.y * 256 + (int)threadIdx.x;
+    if (idx < q.D * q.D) init_entry(idx, in, in + 4, q.consts + 8, q.consts + 12, q.K, q.init_std_frac, q.mu, q.C);
 }
 
 __global__ void k_mean_to_candidate(const double *mu, int D, float *xi)
@@ -120,13 +147,44 @@ __global__ void k_mean_to_candidate(const double *mu, int D, float *xi)
     if (r < D) xi[r] = (float)mu[r];
 }
 
+__device__ __forceinline__ double control_point(const double *q0, const double *qd, const double *mu, int K,
+                                                int idx)
+{
+    const int point = idx >> 2, j = idx & 3;
+    return point < 4 ? q0[j] : (point >= K + 4 ? qd[j] : mu[4 * (point - 4) + j]);
+}
+
 __global__ void k_control_points(const double *q0, const double *qd, const double *mu, int K,
                                  double *ctrl)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // 0 .. 4(K+8)-1
     if (idx >= 4 * (K + 8)) return;
-    const int point = idx >> 2, j = idx & 3;
-    ctrl[idx] = point < 4 ? q0[j] : (point >= K + 4 ? qd[j] : mu[4 * (point - 4) + j]);
+    ctrl[idx] = control_point(q0, qd, mu, K, idx);
+}
+
+// One block per query. mean_candidate: the mean as an FP32 candidate. Otherwise the
+// query's results into out[q][stride]: the mean's cost and terms[5], the best cost, the
+// status word, then the control points of the mean path (also kept in the query's ctrl).
+__global__ void __launch_bounds__(256)
+k_batch_outputs(const BatchQueryDev *__restrict__ qd, int mean_candidate, double *out, int stride)
+{
+    const BatchQueryDev &q = qd[blockIdx.x];
+    if (mean_candidate) {
+        for (int r = threadIdx.x; r < q.D; r += blockDim.x) q.mean_xi[r] = (float)q.mu[r];
+        return;
+    }
+    double *o = out + (size_t)stride * blockIdx.x;
+    for (int idx = threadIdx.x; idx < 4 * (q.K + 8); idx += blockDim.x) {
+        const double v = control_point(q.consts, q.consts + 4, q.mu, q.K, idx);
+        q.ctrl[idx] = v;
+        o[8 + idx] = v;
+    }
+    if (threadIdx.x == 0) {
+        o[0] = *q.mean_J;
+        for (int t = 0; t < 5; ++t) o[1 + t] = q.mean_terms[t];
+        o[6] = *q.best;
+        o[7] = (double)*q.status;
+    }
 }
 
 }  // namespace
@@ -180,6 +238,21 @@ int launch_control_points(const double *q0, const double *qd, const double *mu, 
     const int n = 4 * (K + 8);
     k_control_points<<<(n + 127) / 128, 128, 0, st>>>(q0, qd, mu, K, ctrl);
     CP_LAUNCHED("k_control_points");
+    return CP_OK;
+}
+
+int launch_batch_init(const BatchQueryDev *qd, const int2 *tab, int blocks, const double *inputs, cudaStream_t st)
+{
+    k_batch_init<<<blocks, 256, 0, st>>>(qd, tab, inputs);
+    CP_LAUNCHED("k_batch_init");
+    return CP_OK;
+}
+
+int launch_batch_outputs(const BatchQueryDev *qd, int nq, bool mean_candidate, double *out, int out_stride,
+                         cudaStream_t st)
+{
+    k_batch_outputs<<<nq, 256, 0, st>>>(qd, mean_candidate ? 1 : 0, out, out_stride);
+    CP_LAUNCHED("k_batch_outputs");
     return CP_OK;
 }
 

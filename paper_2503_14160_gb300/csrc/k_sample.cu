@@ -55,12 +55,9 @@ __device__ __forceinline__ double rsqrt_newton(double a)
 // roots taken together. Outputs L (double, row-major, upper part zero) and its FP32
 // transpose Lt[c][r] = L[r][c] for the sampler. A pivot that is not positive raises
 // DEV_ERR_NOT_PD (and is replaced by 1 so that the kernel finishes).
-__global__ void __launch_bounds__(kFactorThreads)
-k_factor(const double *__restrict__ C, double sigma2, const double *__restrict__ sigma_dev, int D, double *L,
-         float *Lt, uint32_t *status)
+__device__ __forceinline__ void factor_body(const double *__restrict__ C, double sigma2, int D, double *L,
+                                            float *Lt, uint32_t *status, double *A)
 {
-    if (sigma_dev != nullptr) sigma2 = sigma_dev[0] * sigma_dev[0];   // the step size kept on the device
-    extern __shared__ double A[];
     __shared__ double s_d[2];
     __shared__ double s_t[kFactorMaxD];
     __shared__ int bad;
@@ -124,24 +121,39 @@ k_factor(const double *__restrict__ C, double sigma2, const double *__restrict__
     if (tid == 0 && bad) atomicOr(status, DEV_ERR_NOT_PD);
 }
 
+__global__ void __launch_bounds__(kFactorThreads)
+k_factor(const double *__restrict__ C, double sigma2, const double *__restrict__ sigma_dev, int D, double *L,
+         float *Lt, uint32_t *status)
+{
+    if (sigma_dev != nullptr) sigma2 = sigma_dev[0] * sigma_dev[0];   // the step size kept on the device
+    extern __shared__ double A[];
+    factor_body(C, sigma2, D, L, Lt, status, A);
+}
+
+// The factors of every query of a batch, one CTA per query.
+__global__ void __launch_bounds__(kFactorThreads) k_batch_factor(const BatchQueryDev *__restrict__ qd)
+{
+    extern __shared__ double A[];
+    const BatchQueryDev &q = qd[blockIdx.x];
+    factor_body(q.C, q.sigma2, q.D, q.L, q.Lt, q.status, A);
+}
+
 constexpr int kSampleThreads = 256;
 
 // One candidate per warp at a time; Lt (FP32, column-major) in shared memory, the D
 // normals of the candidate in a per-warp shared buffer; lane l writes rows l, l+32, ...
-__global__ void __launch_bounds__(kSampleThreads)
-k_sample(const double *__restrict__ mu, const float *__restrict__ Lt, int N, int K,
-         uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *xi)
+// Candidates warp, warp + n_warps, ... below N (i_end) of one query.
+__device__ __forceinline__ void sample_body(const double *__restrict__ mu, const float *__restrict__ Lt, int N,
+                                            int K, uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query,
+                                            float *xi, int warp, int n_warps, int i_end, float *sm)
 {
-    extern __shared__ float sm[];
     const int D = 4 * K;
     float *sL = sm;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *sZ = sm + D * D + wib * D;
     for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) sL[idx] = Lt[idx];
     __syncthreads();
-    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int i = warp; i < N; i += n_warps) {
+    for (int i = warp; i < i_end; i += n_warps) {
         for (int j = lane; j < K; j += 32) {
             const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)i, iter, query), k0, k1);
             float z0, z1, z2, z3;
@@ -160,6 +172,32 @@ k_sample(const double *__restrict__ mu, const float *__restrict__ Lt, int N, int
         }
         __syncwarp();
     }
+    (void)N;
+}
+
+__global__ void __launch_bounds__(kSampleThreads)
+k_sample(const double *__restrict__ mu, const float *__restrict__ Lt, int N, int K,
+         uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *xi)
+{
+    extern __shared__ float sm[];
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
+    sample_body(mu, Lt, N, K, k0, k1, iter, query, xi, warp, n_warps, N, sm);
+}
+
+// Every query's draw in one launch: block b of query q takes the kBatchSampleCands
+// candidates from b kBatchSampleCands, one per warp at a time. A candidate's normals and
+// arithmetic do not depend on which warp draws it, so each query's xi equals its plain draw.
+__global__ void __launch_bounds__(kSampleThreads)
+k_batch_sample(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab, uint32_t iter)
+{
+    extern __shared__ float sm[];
+    const int2 e = tab[blockIdx.x];
+    const BatchQueryDev &q = qd[e.x];
+    const int b = e.y * kBatchSampleCands;
+    const int warps = kSampleThreads / 32;
+    sample_body(q.mu, q.Lt, q.N, q.K, q.seed_lo, q.seed_hi, iter, q.query, q.xi, b + (int)(threadIdx.x >> 5), warps,
+                min(q.N, b + kBatchSampleCands), sm);
 }
 
 size_t sample_smem(int K) { return sizeof(float) * ((size_t)16 * K * K + (kSampleThreads / 32) * 4 * K); }
@@ -198,6 +236,28 @@ int sample_configure()
 {
     CP_CUDA(cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sample_smem(CP_MAX_WAYPOINTS)));
+    CP_CUDA(cudaFuncSetAttribute(k_batch_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sample_smem(CP_MAX_WAYPOINTS)));
+    const int Dm = 4 * CP_MAX_WAYPOINTS;
+    CP_CUDA(cudaFuncSetAttribute(k_batch_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double) * Dm * (Dm + 1))));
+    return CP_OK;
+}
+
+int launch_batch_factor(const BatchQueryDev *qd, int nq, int max_D, cudaStream_t st)
+{
+    const size_t smem = sizeof(double) * (size_t)max_D * (max_D + 1);
+    k_batch_factor<<<nq, kFactorThreads, smem, st>>>(qd);
+    CP_LAUNCHED("k_batch_factor");
+    return CP_OK;
+}
+
+int launch_batch_sample(const BatchQueryDev *qd, const int2 *tab, int blocks, int max_K, uint32_t iter,
+                        cudaStream_t st)
+{
+    if (blocks == 0) return CP_OK;
+    k_batch_sample<<<blocks, kSampleThreads, sample_smem(max_K), st>>>(qd, tab, iter);
+    CP_LAUNCHED("k_batch_sample");
     return CP_OK;
 }
 

@@ -99,19 +99,18 @@ __global__ void k_scatter(int *__restrict__ rank, const double *__restrict__ J,
 // Block (tile t of the lower triangle of 16x16 tiles, chunk p of kChunk-row groups): one
 // S2 entry per thread, and S1 of the tile's rows on diagonal tiles. Partials are stored
 // entry-major ([entry][chunk]) so that the combine reads them with coalesced loads.
-__global__ void __launch_bounds__(256)
-k_moments_partial(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D,
-                  int per, int n_chunks, double *s2p, double *s1p)
+__device__ __forceinline__ void moments_partial_body(const float *__restrict__ elites, const double *__restrict__ w,
+                                                    int nu, int D, int per, int n_chunks, double *s2p, double *s1p,
+                                                    int t, int p)
 {
     __shared__ double wyr[kChunk][17];
     __shared__ double yc[kChunk][17];
-    int t = blockIdx.x, tr = 0;   // tile index -> (tile row tr >= tile col tc)
+    int tr = 0;   // tile index -> (tile row tr >= tile col tc)
     while (t > tr) {
         t -= tr + 1;
         ++tr;
     }
     const int tc = t;
-    const int p = blockIdx.y;
     const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
     const bool diag = tr == tc;
     const int j_end = min(nu, (p + 1) * per);
@@ -145,6 +144,24 @@ k_moments_partial(const float *__restrict__ elites, const double *__restrict__ w
     if (diag && b == 0 && r < D) s1p[(size_t)r * n_chunks + p] = acc1;
 }
 
+__global__ void __launch_bounds__(256)
+k_moments_partial(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D,
+                  int per, int n_chunks, double *s2p, double *s1p)
+{
+    moments_partial_body(elites, w, nu, D, per, n_chunks, s2p, s1p, blockIdx.x, blockIdx.y);
+}
+
+// Every query's partials in one launch: block b of query q is tile b % tiles, chunk b / tiles
+// of that query (tiles = its lower-triangle tile count).
+__global__ void __launch_bounds__(256)
+k_batch_moments_partial(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab)
+{
+    const int2 e = tab[blockIdx.x];
+    const BatchQueryDev &q = qd[e.x];
+    const int nt = (q.D + 15) / 16, tiles = nt * (nt + 1) / 2;
+    moments_partial_body(q.elites, q.w, q.nu, q.D, q.per, q.n_chunks, q.s2p, q.s1p, e.y % tiles, e.y / tiles);
+}
+
 // Sum of n values at stride 1, lane-strided and then by a fixed shuffle tree (every lane
 // gets the same result; the order does not depend on scheduling).
 __device__ __forceinline__ double warp_sum(const double *__restrict__ v, int n, int lane)
@@ -158,11 +175,10 @@ __device__ __forceinline__ double warp_sum(const double *__restrict__ v, int n, 
 
 // One warp per lower-triangle entry (r >= c): C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c];
 // on the diagonal also mu_r = m0_r + S1_r.
-__global__ void k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1p,
-                                  int n_chunks, int D, double eps, const float *__restrict__ elites,
-                                  double *mu, double *C)
+__device__ __forceinline__ void moments_combine_body(const double *__restrict__ s2p, const double *__restrict__ s1p,
+                                                    int n_chunks, int D, double eps,
+                                                    const float *__restrict__ elites, double *mu, double *C, int e)
 {
-    const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= D * (D + 1) / 2) return;
     int r, c;
@@ -178,6 +194,24 @@ __global__ void k_moments_combine(const double *__restrict__ s2p, const double *
     }
     C[(size_t)r * D + c] = v;
     C[(size_t)c * D + r] = v;
+}
+
+__global__ void k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1p,
+                                  int n_chunks, int D, double eps, const float *__restrict__ elites,
+                                  double *mu, double *C)
+{
+    moments_combine_body(s2p, s1p, n_chunks, D, eps, elites, mu, C,
+                         (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5));
+}
+
+// Block b of query q combines the entries 8 b .. 8 b + 7 of that query (one warp each).
+__global__ void __launch_bounds__(256)
+k_batch_moments_combine(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab)
+{
+    const int2 e = tab[blockIdx.x];
+    const BatchQueryDev &q = qd[e.x];
+    moments_combine_body(q.s2p, q.s1p, q.n_chunks, q.D, q.eps, q.elites, q.mu, q.C,
+                         e.y * 8 + (int)(threadIdx.x >> 5));
 }
 
 // ---------------------------------------------------------------- LSD radix sort (large N)
@@ -197,15 +231,26 @@ __global__ void k_radix_init(const double *__restrict__ J, int N, unsigned long 
     }
 }
 
+// The digit of a pass: 8 bits of the key, or (kByQuery) 8 bits of the query of the element's
+// value (qid[value]), for the last passes of the batched ranking.
+template <bool kByQuery>
+__device__ __forceinline__ int radix_digit(unsigned long long k, int v, int shift, const uint16_t *__restrict__ qid)
+{
+    if (kByQuery) return (int)((qid[v] >> shift) & 255u);
+    return (int)((k >> shift) & 255ull);
+}
+
+template <bool kByQuery = false>
 __global__ void __launch_bounds__(kRadixThreads)
-k_radix_hist(const unsigned long long *__restrict__ key, int N, int shift, int tiles, int *hist)
+k_radix_hist(const unsigned long long *__restrict__ key, int N, int shift, int tiles, int *hist,
+             const int *__restrict__ val = nullptr, const uint16_t *__restrict__ qid = nullptr)
 {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     const int b = blockIdx.x * kRadixTile, e = min(N, b + kRadixTile);
     for (int i = b + threadIdx.x; i < e; i += kRadixThreads)
-        atomicAdd(&h[(int)((key[i] >> shift) & 255ull)], 1);
+        atomicAdd(&h[radix_digit<kByQuery>(kByQuery ? 0ull : key[i], kByQuery ? val[i] : 0, shift, qid)], 1);
     __syncthreads();
     hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];   // digit-major
 }
@@ -235,10 +280,11 @@ __global__ void __launch_bounds__(1024) k_radix_scan(int *a, int n)
     }
 }
 
+template <bool kByQuery = false>
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_scatter(const unsigned long long *__restrict__ key_in, const int *__restrict__ val_in, int N,
                 int shift, int tiles, const int *__restrict__ offsets, unsigned long long *key_out,
-                int *val_out)
+                int *val_out, const uint16_t *__restrict__ qid = nullptr)
 {
     __shared__ int run[256];            // elements of each digit placed by earlier passes
     __shared__ int wcount[8][256];      // per-warp digit counts of the current pass
@@ -256,7 +302,7 @@ k_radix_scatter(const unsigned long long *__restrict__ key_in, const int *__rest
         if (valid) {
             k = key_in[i];
             v = val_in[i];
-            d = (int)((k >> shift) & 255ull);
+            d = radix_digit<kByQuery>(k, v, shift, qid);
         }
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int in_warp = __popc(peers & lt);
@@ -279,19 +325,54 @@ k_radix_scatter(const unsigned long long *__restrict__ key_in, const int *__rest
 }
 
 // Elite list and rows from the sorted indices; rank 0 also records its cost.
-__global__ void k_gather_elites(const int *__restrict__ sorted, const double *__restrict__ J,
-                                const float *__restrict__ xi, int nu, int D, int *elite,
-                                float *elites, double *best_J)
+__device__ __forceinline__ void gather_body(const int *__restrict__ sorted, int base, const double *__restrict__ J,
+                                            const float *__restrict__ xi, int nu, int D, int *elite, float *elites,
+                                            double *best_J, int r, int n_valid = 0x7FFFFFFF,
+                                            uint32_t *status = nullptr)
 {
-    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= nu) return;
-    const int i = sorted[r];
+    const int i = sorted[r] - base;
+    if (i < 0 || i >= n_valid) {   // not one of this query's candidates: report, touch nothing
+        if (lane == 0 && status != nullptr) atomicOr(status, DEV_ERR_OVERFLOW);
+        return;
+    }
     if (lane == 0) {
         elite[r] = i;
         if (r == 0 && best_J != nullptr) *best_J = J[i];
     }
     for (int c = lane; c < D; c += 32) elites[(size_t)r * D + c] = xi[(size_t)i * D + c];
+}
+
+__global__ void k_gather_elites(const int *__restrict__ sorted, const double *__restrict__ J,
+                                const float *__restrict__ xi, int nu, int D, int *elite,
+                                float *elites, double *best_J)
+{
+    gather_body(sorted, 0, J, xi, nu, D, elite, elites, best_J, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5));
+}
+
+// The batched ranking: key and value of every query's candidates at the query's offset in
+// the concatenated arrays (value = that position), and the query of each position.
+__global__ void k_batch_radix_init(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab,
+                                   unsigned long long *key, int *val)
+{
+    const int2 e = tab[blockIdx.x];
+    const BatchQueryDev &q = qd[e.x];
+    const int i = e.y * 256 + (int)threadIdx.x;
+    if (i < q.N) {
+        key[q.cand_off + i] = order_key(q.J[i]);
+        val[q.cand_off + i] = q.cand_off + i;
+    }
+}
+
+// Elites of every query from its sorted range (block b of query q: ranks 8 b .. 8 b + 7).
+__global__ void __launch_bounds__(256)
+k_batch_gather(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab, const int *__restrict__ sorted)
+{
+    const int2 e = tab[blockIdx.x];
+    const BatchQueryDev &q = qd[e.x];
+    gather_body(sorted + q.cand_off, q.cand_off, q.J, q.xi, q.nu, q.D, q.elite, q.elites, q.best,
+                e.y * 8 + (int)(threadIdx.x >> 5), q.N, q.status);
 }
 
 // ---------------------------------------------------------------- CMA-ES update rule
@@ -436,11 +517,11 @@ int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigne
     CP_LAUNCHED("k_radix_init");
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 8 * pass;
-        k_radix_hist<<<tiles, kRadixThreads, 0, st>>>(key_a, N, shift, tiles, hist);
+        k_radix_hist<false><<<tiles, kRadixThreads, 0, st>>>(key_a, N, shift, tiles, hist);
         CP_LAUNCHED("k_radix_hist");
         k_radix_scan<<<1, 1024, 0, st>>>(hist, 256 * tiles);
         CP_LAUNCHED("k_radix_scan");
-        k_radix_scatter<<<tiles, kRadixThreads, 0, st>>>(key_a, val_a, N, shift, tiles, hist, key_b, val_b);
+        k_radix_scatter<false><<<tiles, kRadixThreads, 0, st>>>(key_a, val_a, N, shift, tiles, hist, key_b, val_b);
         CP_LAUNCHED("k_radix_scatter");
         unsigned long long *tk = key_a;
         key_a = key_b;
@@ -537,6 +618,70 @@ int launch_cma_update(const float *elites, const double *w, int nu, int D, const
     k_cma_cov<<<(entries * 32 + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, elites, mu_prev, p_c, cma,
                                                           k, C);
     CP_LAUNCHED("k_cma_cov");
+    return CP_OK;
+}
+
+int moments_chunking(int nu, int *per)
+{
+    *per = per_chunk(nu);
+    return (nu + *per - 1) / *per;
+}
+
+// Stable LSD ranking of every query's candidates at once: the eight key passes order all
+// positions by (J, position); the query passes then move each query's candidates, in that
+// order, to its own range (a query's positions are contiguous and increase with the index,
+// so ties keep the index order of the plain ranking).
+int launch_batch_radix_rank(const BatchQueryDev *qd, const int2 *tab, int blocks, int total, int nq,
+                            const uint16_t *qid, unsigned long long *key_a, unsigned long long *key_b,
+                            int *val_a, int *val_b, int *hist, int **sorted, cudaStream_t st)
+{
+    const int tiles = radix_tiles(total);
+    k_batch_radix_init<<<blocks, 256, 0, st>>>(qd, tab, key_a, val_a);
+    CP_LAUNCHED("k_batch_radix_init");
+    const int q_passes = nq > 256 ? 2 : (nq > 1 ? 1 : 0);
+    for (int pass = 0; pass < 8 + q_passes; ++pass) {
+        const bool byq = pass >= 8;
+        const int shift = byq ? 8 * (pass - 8) : 8 * pass;
+        if (byq)
+            k_radix_hist<true><<<tiles, kRadixThreads, 0, st>>>(key_a, total, shift, tiles, hist, val_a, qid);
+        else
+            k_radix_hist<false><<<tiles, kRadixThreads, 0, st>>>(key_a, total, shift, tiles, hist);
+        CP_LAUNCHED("k_radix_hist");
+        k_radix_scan<<<1, 1024, 0, st>>>(hist, 256 * tiles);
+        CP_LAUNCHED("k_radix_scan");
+        if (byq)
+            k_radix_scatter<true><<<tiles, kRadixThreads, 0, st>>>(key_a, val_a, total, shift, tiles, hist, key_b,
+                                                                   val_b, qid);
+        else
+            k_radix_scatter<false><<<tiles, kRadixThreads, 0, st>>>(key_a, val_a, total, shift, tiles, hist, key_b,
+                                                                    val_b);
+        CP_LAUNCHED("k_radix_scatter");
+        unsigned long long *tk = key_a;
+        key_a = key_b;
+        key_b = tk;
+        int *tv = val_a;
+        val_a = val_b;
+        val_b = tv;
+    }
+    *sorted = val_a;
+    return CP_OK;
+}
+
+int launch_batch_gather(const BatchQueryDev *qd, const int2 *tab, int blocks, const int *sorted, cudaStream_t st)
+{
+    if (blocks == 0) return CP_OK;
+    k_batch_gather<<<blocks, 256, 0, st>>>(qd, tab, sorted);
+    CP_LAUNCHED("k_batch_gather");
+    return CP_OK;
+}
+
+int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_partial, int blocks_partial,
+                         const int2 *tab_combine, int blocks_combine, cudaStream_t st)
+{
+    k_batch_moments_partial<<<blocks_partial, 256, 0, st>>>(qd, tab_partial);
+    CP_LAUNCHED("k_batch_moments_partial");
+    k_batch_moments_combine<<<blocks_combine, 256, 0, st>>>(qd, tab_combine);
+    CP_LAUNCHED("k_batch_moments_combine");
     return CP_OK;
 }
 
