@@ -895,9 +895,11 @@ def run_ik_reference(args):
 
 def run_batch(args):
     """The batched serving form: 64 queries of uneven size (N ~ U[1024, 16384], K ~ U[8, 32],
-    M ~ U[50, 3000] cylinders, S = 64, 100 iterations) planned by one graph launch, against the
-    same queries planned one after another with cp_plan. Launch shapes per size bucket come
-    from the autotuner."""
+    M ~ U[50, 3000] cylinders, S = 64, 100 iterations), every stage of an iteration one launch
+    for all queries (the evaluation one persistent launch over a device queue of tiles), the
+    whole run one CUDA graph; against the same queries planned one after another with cp_plan.
+    The polar index's ring width per size bucket and the batched evaluation's block and tile
+    shape come from the autotuner."""
     import torch
     from paper_2503_14160_gb300 import autotune, build, craneplan as cp, workloads
     ws, rank, local = dist_env()
@@ -906,17 +908,18 @@ def run_batch(args):
     cp.load()
     crane = workloads.forestry_crane()
     model = cp.make_model(crane)
-    S, T = 64, args.iterations or 100
-    queries = workloads.batch_queries(64, seed=rank)
+    S, T, nq = 64, args.iterations or 100, 64
+    queries = workloads.batch_queries(nq, seed=rank)
     tuner = autotune.Autotuner()
     t_tune = time.perf_counter()
-    cfgs = [tuner.best(crane, bq.n_candidates, bq.n_waypoints, S, bq.n_cyl) for bq in queries]
+    cfgs = [tuner.best_polar(crane, bq.n_candidates, bq.n_waypoints, S, bq.n_cyl) for bq in queries]
     t_tune = time.perf_counter() - t_tune
-    scenes, params, q0s, qds = [], [], [], []
+    scenes, params, q0s, qds, raw = [], [], [], [], []
     for q, (bq, cfg) in enumerate(zip(queries, cfgs)):
         sc = workloads.batch_scene(bq, seed=rank, q=q)
         with cp.Planner(crane, sc, cp.make_params(64, bq.n_waypoints, S)) as tmp:
             q0, qd, _ = select_endpoints_gpu(cp, tmp, crane, rank, q)
+        raw.append(sc)
         scenes.append(cp.HostScene.from_scene(sc))
         params.append(cp.make_params(bq.n_candidates, bq.n_waypoints, S, seed=rank, query=q, **cfg))
         q0s.append(q0)
@@ -924,48 +927,92 @@ def run_batch(args):
     t0 = time.perf_counter()
     b = cp.cp_batch_init(model, scenes, params, q0s, qds, T)
     t_init = time.perf_counter() - t0
-    units = sum(bq.n_candidates for bq in queries) * T
-    for _ in range(args.warmup):
-        cp.cp_batch_run(b, 64)
-    batch_ms = []
+    Ks = [bq.n_waypoints for bq in queries]
+    cp.cp_batch_run(b, nq)                      # populations for the shape search
+    t1 = time.perf_counter()
+    tuned = tuner.tune_batch(b, "nq%d|seed%d|S%d" % (nq, rank, S))
+    t_tune += time.perf_counter() - t1
+    info = cp.cp_batch_get_info(b)
+    units = info["candidates"] * T
+    for _ in range(max(args.warmup, 3)):
+        cp.cp_batch_run(b, nq)
+    dev_ms, host_ms = [], []
     l0 = cp.cp_launch_count()
     with ClockSampler(local) as clocks:
         for _ in range(args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = cp.cp_batch_run(b, 64)
-            batch_ms.append((time.perf_counter() - t0) * 1e3)
+            res = cp.cp_batch_run(b, nq, K=Ks)
+            host_ms.append((time.perf_counter() - t0) * 1e3)
+            dev_ms.append(cp.cp_batch_get_info(b)["last_run_ms"])
     launches = cp.cp_launch_count() - l0
-    seq_ms = []
-    for _ in range(args.steps):
+    eval_ms = cp.cp_batch_evaluate(b, 5)
+    checkpoints = sum(bq.n_candidates * (bq.n_waypoints + 3) * S for bq in queries)
+    # the same queries planned one after another in the plain form (each planner's own graph,
+    # recorded in an untimed pass first)
+    seq = []
+    for rep in range(1 + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for q in range(64):
+        for q in range(nq):
             p = cp.cp_batch_planner(b, q)
             cp.cp_set_endpoints(p, q0s[q], qds[q])
             cp.cp_plan(p, T)
-        seq_ms.append((time.perf_counter() - t0) * 1e3)
-    ms, ms_seq = float(np.mean(batch_ms)), float(np.mean(seq_ms))
-    grid_q = sum(1 for c in cfgs if c["grid_cell"] > 0)
-    line = {"metric": "candidate paths evaluated/sec, 64-query batch (one CUDA graph) vs sequential",
+        if rep > 0:
+            seq.append((time.perf_counter() - t0) * 1e3)
+    ms, ms_host, ms_seq = float(np.mean(dev_ms)), float(np.mean(host_ms)), float(np.mean(seq))
+    line = {"metric": "candidate paths evaluated/sec, 64-query batch (one graph, one launch per stage) "
+                      "vs sequential plain plans",
             "value": units / (ms / 1e3), "unit": "candidate paths/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded crane-and-forest scenes)",
-            "config": {"workload": "64 queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
-                                   "S=64, %d iterations" % T, "step": "one batch (all queries)"},
-            "sequential": {"value": units / (ms_seq / 1e3), "ms_per_batch": ms_seq},
+            "config": {"workload": "batch: 64 queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
+                                   "S=64, %d iterations" % T, "step": "one batch run (all queries)",
+                       "l2": "working set above L2 (%d candidates x up to 128 floats, plus scenes)"
+                             % info["candidates"]},
+            "sequential": {"value": units / (ms_seq / 1e3), "ms_per_batch": ms_seq,
+                           "form": "cp_plan per query (its own graph), one after another"},
             "speedup_vs_sequential": ms_seq / ms,
-            "graph_record_and_instantiate_s": t_init, "autotune_s": t_tune,
-            "queries_on_grid": grid_q,
+            "graph": {"kernel_nodes": info["kernel_nodes"], "persistent_eval_launches": info["eval_launches"],
+                      "eval_tiles_per_launch": info["eval_tiles"], "eval_ctas": info["eval_ctas"]},
+            "eval_kernel": {"name": "k_batch_eval_polar", "ms_per_launch": eval_ms,
+                            "share_of_run": eval_ms * T / ms,
+                            "checkpoints_per_s": checkpoints / (eval_ms / 1e3)},
+            "autotune": {"shape": tuned["shape"], "shape_ms": dict(zip(
+                             ["%d/%d/%d" % tuple(sh) for sh in tuned["shapes"]], tuned["ms"])),
+                         "ring_widths": sorted({c["grid_cell"] for c in cfgs}), "seconds": t_tune},
+            "graph_record_and_instantiate_s": t_init,
             "collision_free": sum(1 for _, st in res if st["flag"] == 0),
             "gpu_launches": launches, "clocks": clocks.summary(),
-            "e2e": {"value": units / (ms / 1e3), "unit": "candidate paths/s",
-                    "h2d_bytes_per_step": 64 * 64, "d2h_bytes_per_step": 64 * 8 * 168}}
+            "e2e": {"value": units / (ms_host / 1e3), "unit": "candidate paths/s", "ms_per_batch": ms_host,
+                    "h2d_bytes_per_step": nq * 8 * 8, "d2h_bytes_per_step": nq * 168 * 8}}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = batch_cpu_baseline(crane, queries, q0s, qds, rank, S, args.cpu_seconds)
+        line["oracle_error"] = batch_oracle_errors(crane, queries, raw, q0s, qds, res, S)
     print(json.dumps(line), flush=True)
     cp.cp_batch_destroy(b)
+
+
+def batch_oracle_errors(crane, queries, scenes, q0s, qds, res, S):
+    """Error of the batch's results against the FP64 oracle (brute force): the returned mean
+    path of every eighth query, its J, length and flag."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    rows = []
+    for q in range(0, len(queries), 8):
+        K = queries[q].n_waypoints
+        ctrl, st = res[q]
+        problem = oracle.Problem(crane, scenes[q], oracle.CostParams(K=K, S=S))
+        x = np.asarray(ctrl)[4:4 + K].astype(np.float32).astype(np.float64)[None]
+        o = oracle.evaluate(problem, x, q0s[q], qds[q])
+        rows.append({"query": q, "J_rel_err": abs(st["J"] - float(o.J[0])) / max(abs(float(o.J[0])), 1e-300),
+                     "length_rel_err": abs(st["length"] - float(o.length[0])) / float(o.length[0]),
+                     "flag_gpu": int(st["flag"]), "flag_oracle": int(o.flag[0])})
+    return {"queries": rows, "J_rel_err_max": max(r["J_rel_err"] for r in rows),
+            "length_rel_err_max": max(r["length_rel_err"] for r in rows),
+            "flag_agreement": sum(r["flag_gpu"] == r["flag_oracle"] for r in rows) / len(rows),
+            "oracle_form": "brute force"}
 
 
 TRAJ_PATHS = 64
@@ -1308,6 +1355,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch_reference(args):
+    """--impl reference for the batch workload: the FP64 oracle evaluating candidates of every
+    eighth query of the same 64-query batch (each with its own scene and sizes), one bounded
+    sample per step, scaled to candidate paths per second."""
+    from paper_2503_14160_gb300 import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    crane = workloads.forestry_crane()
+    S, T = 64, args.iterations or 100
+    queries = workloads.batch_queries(64, seed=rank)
+    q0s, qds = [None] * 64, [None] * 64
+    for q in range(0, 64, 8):
+        bq = queries[q]
+        pb = oracle.Problem(crane, workloads.batch_scene(bq, seed=rank, q=q), oracle.CostParams(K=bq.n_waypoints, S=S))
+        q0s[q], qds[q], _, _ = workloads.select_endpoints(crane, lambda x: oracle.signed_distance(pb, x),
+                                                          seed=rank, batch=4096, query=q)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        r = batch_cpu_baseline(crane, queries, q0s, qds, rank, S, args.cpu_seconds / 4)
+        if i >= args.warmup:
+            per_step.append(r)
+    value = float(np.mean([r["value"] for r in per_step]))
+    line = {"metric": "candidate paths evaluated/sec, 64-query batch (one graph, one launch per stage) "
+                      "vs sequential plain plans",
+            "value": value, "unit": "candidate paths/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean([r["seconds"] for r in per_step])) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded crane-and-forest scenes)", "impl": "reference",
+            "config": {"workload": "batch: 64 queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
+                                   "S=64, %d iterations" % T,
+                       "step": "a bounded sample: candidate evaluations of every eighth query"},
+            "cpu_baseline": {"value": value, "unit": "candidate paths/s", "cores": per_step[0]["cores"],
+                             "kind": "oracle", "sample": per_step[0]["sample"]},
+            "e2e": {"value": value, "unit": "candidate paths/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1333,6 +1421,8 @@ def main():
         run_hulls_reference(args)
     elif args.impl == "reference" and args.workload == "trajopt":
         run_traj_reference(args)
+    elif args.impl == "reference" and args.workload == "batch":
+        run_batch_reference(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "ik":

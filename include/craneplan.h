@@ -488,6 +488,8 @@ typedef struct cp_batch_info {
     int32_t eval_ctas;        /* CTAs of the persistent evaluation launch */
     int32_t eval_launches;    /* persistent evaluation launches per run (iterations + 1) */
     int64_t candidates;       /* sum of the queries' N */
+    double last_run_ms;       /* device time of the last cp_batch_run (CUDA events around the
+                                 graph launch: input copy to result copy), 0 before the first */
 } cp_batch_info;
 
 int cp_batch_get_info(const cp_batch *b, cp_batch_info *out);

@@ -98,7 +98,7 @@ class cp_batch_shape(ctypes.Structure):
 class cp_batch_info(ctypes.Structure):
     _fields_ = [("kernel_nodes", ctypes.c_int64), ("eval_tiles", ctypes.c_int64),
                 ("eval_ctas", ctypes.c_int32), ("eval_launches", ctypes.c_int32),
-                ("candidates", ctypes.c_int64)]
+                ("candidates", ctypes.c_int64), ("last_run_ms", ctypes.c_double)]
 
 
 class cp_batch_result(ctypes.Structure):

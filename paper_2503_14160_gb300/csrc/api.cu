@@ -147,6 +147,7 @@ struct cp_planner {
     int *rank = nullptr, *elite = nullptr;
     float *elites = nullptr;
     double *w = nullptr, *mean_part = nullptr, *cov_part = nullptr;
+    double *mom_y = nullptr;    // [2][nu][D] FP64 deviations of the elites for the moments
     double *best = nullptr;
     uint32_t *status = nullptr;
     double *ctrl = nullptr;
@@ -515,7 +516,7 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
     if (p->prm.update_rule == CP_UPDATE_CMAES) {
         CP_CUDA(cudaMemcpyAsync(p->mu_prev, p->mu, sizeof(double) * p->D, cudaMemcpyDeviceToDevice, p->st));
         if ((rc = launch_cma_update(p->elites, p->w, p->nu, p->D, p->mu_prev, p->L, p->cmak, p->iteration,
-                                    p->cov_part, p->mean_part, p->mu, p->C, p->p_sigma, p->p_c, p->cma,
+                                    p->mom_y, p->cov_part, p->mean_part, p->mu, p->C, p->p_sigma, p->p_c, p->cma,
                                     p->st)) != CP_OK)
             return rc;
     } else if (p->prm.sampler == CP_SAMPLE_ELITES) {
@@ -529,7 +530,7 @@ int run_update(cp_planner *p, const double *d_J, const float *d_xi)
         p->elites_ready = true;
         p->iteration += 1;
         return CP_OK;
-    } else if ((rc = launch_moments(p->elites, p->w, p->nu, p->D, p->prm.eps, p->cov_part, p->mean_part,
+    } else if ((rc = launch_moments(p->elites, p->w, p->nu, p->D, p->prm.eps, p->mom_y, p->cov_part, p->mean_part,
                                     p->mu, p->C, p->st)) != CP_OK) {
         return rc;
     }
@@ -546,7 +547,7 @@ int materialise_distribution(const cp_planner *p)
 {
     if (!p->elites_ready) return CP_OK;
     cp_planner *q = const_cast<cp_planner *>(p);
-    int rc = launch_moments(q->elites, q->w, q->nu, q->D, q->prm.eps, q->cov_part, q->mean_part, q->mu_prev, q->C,
+    int rc = launch_moments(q->elites, q->w, q->nu, q->D, q->prm.eps, q->mom_y, q->cov_part, q->mean_part, q->mu_prev, q->C,
                             q->st);
     if (rc != CP_OK) return rc;
     return launch_factor(q->C, q->prm.sigma * q->prm.sigma, nullptr, q->D, q->L, q->Lt, q->status, q->st);
@@ -609,7 +610,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->chunks = (p->n_s + 31) / 32;
     p->nu = params->n_elites > 0 ? params->n_elites : p->N / 2;
     if (p->nu < 1) p->nu = 1;
-    p->n_mean_chunks = update_chunks(p->nu);
+    p->n_mean_chunks = update_chunks(p->nu, p->D);
     p->cap_cyl = params->max_cylinders > scene->n_cyl ? params->max_cylinders : scene->n_cyl;
     p->cap_box = params->max_boxes > scene->n_box ? params->max_boxes : scene->n_box;
     p->mdev = make_model(model);
@@ -692,6 +693,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_w = L.take<double>(nu);
     const size_t o_mean_part = L.take<double>(mc * D);
     const size_t o_cov_part = L.take<double>(mc * D * D);
+    const size_t o_mom_y = L.take<double>(2 * nu * D);
     const size_t o_best = L.take<double>(1);
     const size_t o_status = L.take<uint32_t>(1);
     const size_t o_ctrl = L.take<double>(4 * ((size_t)p->K + 8));
@@ -760,6 +762,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->w = (double *)(b + o_w);
     p->mean_part = (double *)(b + o_mean_part);
     p->cov_part = (double *)(b + o_cov_part);
+    p->mom_y = (double *)(b + o_mom_y);
     p->best = (double *)(b + o_best);
     p->status = (uint32_t *)(b + o_status);
     p->ctrl = (double *)(b + o_ctrl);
@@ -1296,8 +1299,8 @@ struct cp_batch {
     BatchQueryDev *qdev = nullptr;
     BatchEvalDev *ev_pop = nullptr, *ev_mean = nullptr;
     int2 *tab_init = nullptr, *tab_sample = nullptr, *tab_cand = nullptr, *tab_gather = nullptr;
-    int2 *tab_mpart = nullptr, *tab_mcomb = nullptr;
-    int n_init = 0, n_sample = 0, n_cand = 0, n_gather = 0, n_mpart = 0, n_mcomb = 0;
+    int2 *tab_mprep = nullptr, *tab_mpart = nullptr, *tab_mcomb = nullptr;
+    int n_init = 0, n_sample = 0, n_cand = 0, n_gather = 0, n_mprep = 0, n_mpart = 0, n_mcomb = 0;
     int4 *tiles_pop = nullptr, *tiles_mean = nullptr;
     int64_t tiles_cap = 0;
     int n_tiles_pop = 0, n_tiles_mean = 0;
@@ -1312,6 +1315,7 @@ struct cp_batch {
     cudaGraphExec_t exec = nullptr;
     int64_t kernel_nodes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_run_ms = 0.0;          // device time of the last cp_batch_run
 };
 
 namespace {
@@ -1384,7 +1388,8 @@ int record_batch(cp_batch *b)
                                           b->key_b, b->val_a, b->val_b, b->hist, &sorted, b->st)) != CP_OK)
             return rc;
         if ((rc = launch_batch_gather(b->qdev, b->tab_gather, b->n_gather, sorted, b->st)) != CP_OK) return rc;
-        if ((rc = launch_batch_moments(b->qdev, b->tab_mpart, b->n_mpart, b->tab_mcomb, b->n_mcomb, b->st)) != CP_OK)
+        if ((rc = launch_batch_moments(b->qdev, b->tab_mprep, b->n_mprep, b->tab_mpart, b->n_mpart, b->tab_mcomb,
+                                       b->n_mcomb, b->st)) != CP_OK)
             return rc;
         if ((rc = launch_batch_factor(b->qdev, b->nq, b->max_D, b->st)) != CP_OK) return rc;
     }
@@ -1548,7 +1553,8 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
         d.s2p = p->cov_part;
         d.s1p = p->mean_part;
         d.eps = p->prm.eps;
-        d.n_chunks = moments_chunking(p->nu, &d.per);
+        d.n_chunks = moments_chunking(p->nu, p->D, &d.per);
+        d.mom_y = p->mom_y;
         d.cand_off = (int)off;
         d.status = p->status;
         d.consts = p->consts;
@@ -1598,11 +1604,12 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     for (int q = 0; q < nq; ++q) b->order[q] = q;
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return G[x] > G[y]; });
 
-    std::vector<int2> t_init, t_sample, t_cand, t_gather, t_mpart, t_mcomb;
+    std::vector<int2> t_init, t_sample, t_cand, t_gather, t_mprep, t_mpart, t_mcomb;
     block_table(nq, [&](int q) { return (qh[q].D * qh[q].D + 255) / 256; }, t_init);
     block_table(nq, [&](int q) { return (qh[q].N + kBatchSampleCands - 1) / kBatchSampleCands; }, t_sample);
     block_table(nq, [&](int q) { return (qh[q].N + 255) / 256; }, t_cand);
     block_table(nq, [&](int q) { return (qh[q].nu + 7) / 8; }, t_gather);
+    block_table(nq, [&](int q) { return (qh[q].nu * qh[q].D + 255) / 256; }, t_mprep);
     block_table(nq, [&](int q) {
         const int nt = (qh[q].D + 15) / 16;
         return nt * (nt + 1) / 2 * qh[q].n_chunks;
@@ -1623,6 +1630,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     const size_t o_ts = L.take<int2>(t_sample.size());
     const size_t o_tc = L.take<int2>(t_cand.size());
     const size_t o_tg = L.take<int2>(t_gather.size());
+    const size_t o_tq = L.take<int2>(t_mprep.size());
     const size_t o_tp = L.take<int2>(t_mpart.size());
     const size_t o_tm = L.take<int2>(t_mcomb.size());
     const size_t o_tilp = L.take<int4>((size_t)max_tiles);
@@ -1645,6 +1653,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     b->tab_sample = (int2 *)(base + o_ts);
     b->tab_cand = (int2 *)(base + o_tc);
     b->tab_gather = (int2 *)(base + o_tg);
+    b->tab_mprep = (int2 *)(base + o_tq);
     b->tab_mpart = (int2 *)(base + o_tp);
     b->tab_mcomb = (int2 *)(base + o_tm);
     b->tiles_pop = (int4 *)(base + o_tilp);
@@ -1660,6 +1669,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     b->n_sample = (int)t_sample.size();
     b->n_cand = (int)t_cand.size();
     b->n_gather = (int)t_gather.size();
+    b->n_mprep = (int)t_mprep.size();
     b->n_mpart = (int)t_mpart.size();
     b->n_mcomb = (int)t_mcomb.size();
     std::vector<uint16_t> qid((size_t)b->total);
@@ -1675,6 +1685,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
         (e = up(b->tab_sample, t_sample.data(), sizeof(int2) * t_sample.size())) != cudaSuccess ||
         (e = up(b->tab_cand, t_cand.data(), sizeof(int2) * t_cand.size())) != cudaSuccess ||
         (e = up(b->tab_gather, t_gather.data(), sizeof(int2) * t_gather.size())) != cudaSuccess ||
+        (e = up(b->tab_mprep, t_mprep.data(), sizeof(int2) * t_mprep.size())) != cudaSuccess ||
         (e = up(b->tab_mpart, t_mpart.data(), sizeof(int2) * t_mpart.size())) != cudaSuccess ||
         (e = up(b->tab_mcomb, t_mcomb.data(), sizeof(int2) * t_mcomb.size())) != cudaSuccess ||
         (e = up(b->qid, qid.data(), sizeof(uint16_t) * qid.size())) != cudaSuccess)
@@ -1699,9 +1710,14 @@ int cp_batch_set_endpoints(cp_batch *b, int32_t q, const double h_q0[4], const d
 int cp_batch_run(cp_batch *b, cp_batch_result *results)
 {
     if (!b) return set_error("batch is NULL"), CP_ERR_ARG;
+    CP_CUDA(cudaEventRecord(b->ev0, b->st));
     CP_CUDA(cudaGraphLaunch(b->exec, b->st));
     g_launches.fetch_add(b->kernel_nodes, std::memory_order_relaxed);
+    CP_CUDA(cudaEventRecord(b->ev1, b->st));
     CP_CUDA(cudaStreamSynchronize(b->st));
+    float run_ms = 0.f;
+    CP_CUDA(cudaEventElapsedTime(&run_ms, b->ev0, b->ev1));
+    b->last_run_ms = run_ms;
     int rc = CP_OK;
     for (int q = 0; q < b->nq; ++q) {
         const double *o = b->h_out + kOutStride * q;
@@ -1793,6 +1809,7 @@ int cp_batch_get_info(const cp_batch *b, cp_batch_info *out)
     out->eval_ctas = b->eval_blocks;
     out->eval_launches = b->iters + 1;
     out->candidates = b->total;
+    out->last_run_ms = b->last_run_ms;
     return CP_OK;
 }
 

@@ -253,7 +253,8 @@ int launch_weights(int nu, double *w, cudaStream_t st);
 int launch_rank(const double *J, int N, int nu, int *rank, cudaStream_t st);
 int launch_scatter(int *rank, const double *J, const float *xi, int N, int nu, int D,
                    int *elite, float *elites, double *best_J, cudaStream_t st);
-int launch_moments(const float *elites, const double *w, int nu, int D, double eps,
+// yw: scratch of 2 nu D doubles (the elites' FP64 deviations and their weighted copies).
+int launch_moments(const float *elites, const double *w, int nu, int D, double eps, double *yw,
                    double *s2p, double *s1p, double *mu, double *C, cudaStream_t st);
 
 // Learning rates of the CMA-ES update (Hansen, "The CMA Evolution Strategy: A Tutorial",
@@ -264,7 +265,7 @@ struct CmaConsts {
 CmaConsts cma_consts(int D, int nu);
 int launch_cma_reset(double sigma0, int D, double *cma, double *p_sigma, double *p_c, cudaStream_t st);
 int launch_cma_update(const float *elites, const double *w, int nu, int D, const double *mu_prev,
-                      const double *L, const CmaConsts &k, int t, double *s2p, double *s1p, double *mu,
+                      const double *L, const CmaConsts &k, int t, double *yw, double *s2p, double *s1p, double *mu,
                       double *C, double *p_sigma, double *p_c, double *cma, cudaStream_t st);
 int elite_slices(int N, int D, int nu, int num_sms);
 size_t elite_operand_floats(int nu, int D);   // packed Y_hi / Y_lo of the tensor-core sampler
@@ -276,7 +277,7 @@ int launch_elite_update(const float *elites, const double *w, const float *sw, i
 int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int nu, int slices, double sigma,
                          double eps, uint64_t seed, uint32_t iter, uint32_t query, float *P, float *xi,
                          uint32_t *status, bool withhold, cudaStream_t st);
-int update_chunks(int nu);
+int update_chunks(int nu, int D);
 int radix_tiles(int N);
 int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,
                       int *val_a, int *val_b, int *hist, cudaStream_t st);
@@ -314,6 +315,7 @@ struct BatchQueryDev {
     const double *w;                 // [nu] elite weights
     double *best;                    // cost of the best candidate
     double *s2p, *s1p;               // moment partials
+    double *mom_y;                   // [2][nu][D] the elites' FP64 deviations, then weighted
     double eps;
     int per, n_chunks;               // elites per moment chunk, chunks
     int cand_off;                    // first position of the query in the concatenated ranking
@@ -332,7 +334,7 @@ int launch_batch_init(const BatchQueryDev *qd, const int2 *tab, int blocks, cons
 int launch_batch_factor(const BatchQueryDev *qd, int nq, int max_D, cudaStream_t st);
 int launch_batch_sample(const BatchQueryDev *qd, const int2 *tab, int blocks, int max_K, uint32_t iter,
                         cudaStream_t st);
-constexpr int kBatchSampleCands = 128;   // candidates per block of the batched sampler
+constexpr int kBatchSampleCands = 64;    // candidates per block of the batched sampler
 int batch_eval_configure();
 int launch_batch_eval_polar(const ModelDev &m, const BatchEvalDev *qd, const int4 *tiles, int n_tiles, int *queue,
                             int max_S, int threads, int blocks, cudaStream_t st);
@@ -345,9 +347,9 @@ int launch_batch_radix_rank(const BatchQueryDev *qd, const int2 *tab, int blocks
                             const uint16_t *qid, unsigned long long *key_a, unsigned long long *key_b,
                             int *val_a, int *val_b, int *hist, int **sorted, cudaStream_t st);
 int launch_batch_gather(const BatchQueryDev *qd, const int2 *tab, int blocks, const int *sorted, cudaStream_t st);
-int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_partial, int blocks_partial,
-                         const int2 *tab_combine, int blocks_combine, cudaStream_t st);
-int moments_chunking(int nu, int *per);   // chunks of the moment partials and elites per chunk
+int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_prep, int blocks_prep, const int2 *tab_partial,
+                         int blocks_partial, const int2 *tab_combine, int blocks_combine, cudaStream_t st);
+int moments_chunking(int nu, int D, int *per);   // chunks of the moment partials and elites per chunk
 int launch_batch_outputs(const BatchQueryDev *qd, int nq, bool mean_candidate, double *out, int out_stride,
                          cudaStream_t st);
 

@@ -138,69 +138,106 @@ __global__ void __launch_bounds__(kFactorThreads) k_batch_factor(const BatchQuer
     factor_body(q.C, q.sigma2, q.D, q.L, q.Lt, q.status, A);
 }
 
-constexpr int kSampleThreads = 256;
+constexpr int kSampleWarps = 8;
+constexpr int kSampleThreads = 32 * kSampleWarps;
+constexpr int kSampleCands = 8;   // candidates a warp draws at a time
 
-// One candidate per warp at a time; Lt (FP32, column-major) in shared memory, the D
-// normals of the candidate in a per-warp shared buffer; lane l writes rows l, l+32, ...
-// Candidates warp, warp + n_warps, ... below N (i_end) of one query.
-__device__ __forceinline__ void sample_body(const double *__restrict__ mu, const float *__restrict__ Lt, int N,
-                                            int K, uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query,
-                                            float *xi, int warp, int n_warps, int i_end, float *sm)
+// Shared memory of the sampler: L^T (FP32, column-major, D x D, plus a pad of 32 floats read
+// by the lanes past the last row) and per warp the normals of its kSampleCands candidates
+// ([D][kSampleCands], candidate fastest).
+size_t sample_smem(int K)
+{
+    const size_t D = 4 * (size_t)K;
+    return sizeof(float) * (D * D + 32 + (size_t)kSampleWarps * kSampleCands * D);
+}
+
+// Warp w draws the candidates g .. g + 7 of the groups g = g0 + 8 w, g0 + 8 w + g_stride, ...
+// below i_end: their normals (Philox counter (j, i, iter, query) for z[4j..4j+3], spread over
+// the lanes) go to the warp's buffer; then, 32 rows at a time, lane l holds row r = r0 + l of
+// all eight and forms acc = sum_c L[r][c] z[c] over ascending c with one FMA per term (L read
+// once for the eight), and writes xi_r = mu_r + acc (added in FP64, rounded once to FP32).
+// Columns past the block's last row hold zeros of L for every row of the block and are
+// skipped; adding 0 z leaves a nonzero sum unchanged, so each row equals the full D-term sum.
+__device__ __forceinline__ void sample_body(const double *__restrict__ mu, const float *__restrict__ Lt, int K,
+                                            uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query,
+                                            float *xi, int g0, int g_stride, int i_end, float *sm)
 {
     const int D = 4 * K;
     float *sL = sm;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *sZ = sm + D * D + wib * D;
+    float *sZ = sm + D * D + 32 + wib * kSampleCands * D;
     for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) sL[idx] = Lt[idx];
+    if (threadIdx.x < 32) sL[D * D + threadIdx.x] = 0.f;
     __syncthreads();
-    for (int i = warp; i < i_end; i += n_warps) {
-        for (int j = lane; j < K; j += 32) {
-            const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)i, iter, query), k0, k1);
-            float z0, z1, z2, z3;
-            box_muller(x.x, x.y, z0, z1);
-            box_muller(x.z, x.w, z2, z3);
-            sZ[4 * j + 0] = z0;
-            sZ[4 * j + 1] = z1;
-            sZ[4 * j + 2] = z2;
-            sZ[4 * j + 3] = z3;
+    for (int g = g0 + kSampleCands * wib; g < i_end; g += g_stride) {
+        for (int pq = lane; pq < kSampleCands * K; pq += 32) {
+            const int cnd = pq % kSampleCands, j = pq / kSampleCands;
+            const int i = g + cnd;
+            float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+            if (i < i_end) {
+                const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)i, iter, query), k0, k1);
+                box_muller(x.x, x.y, z0, z1);
+                box_muller(x.z, x.w, z2, z3);
+            }
+            sZ[(4 * j + 0) * kSampleCands + cnd] = z0;
+            sZ[(4 * j + 1) * kSampleCands + cnd] = z1;
+            sZ[(4 * j + 2) * kSampleCands + cnd] = z2;
+            sZ[(4 * j + 3) * kSampleCands + cnd] = z3;
         }
         __syncwarp();
-        for (int r = lane; r < D; r += 32) {
-            float acc = 0.f;
-            for (int c = 0; c < D; ++c) acc = fmaf(sL[c * D + r], sZ[c], acc);
-            xi[(size_t)i * D + r] = (float)(mu[r] + (double)acc);
+        for (int r0 = 0; r0 < D; r0 += 32) {
+            const int r = r0 + lane;
+            float acc[kSampleCands];
+#pragma unroll
+            for (int q = 0; q < kSampleCands; ++q) acc[q] = 0.f;
+            const int c_last = min(D, r0 + 32);
+            for (int c = 0; c < c_last; ++c) {
+                const float l = sL[c * D + r];
+                const float4 za = *reinterpret_cast<const float4 *>(sZ + c * kSampleCands);
+                const float4 zb = *reinterpret_cast<const float4 *>(sZ + c * kSampleCands + 4);
+                acc[0] = fmaf(l, za.x, acc[0]);
+                acc[1] = fmaf(l, za.y, acc[1]);
+                acc[2] = fmaf(l, za.z, acc[2]);
+                acc[3] = fmaf(l, za.w, acc[3]);
+                acc[4] = fmaf(l, zb.x, acc[4]);
+                acc[5] = fmaf(l, zb.y, acc[5]);
+                acc[6] = fmaf(l, zb.z, acc[6]);
+                acc[7] = fmaf(l, zb.w, acc[7]);
+            }
+            if (r < D) {
+                const double m = mu[r];
+#pragma unroll
+                for (int q = 0; q < kSampleCands; ++q)
+                    if (g + q < i_end) xi[(size_t)(g + q) * D + r] = (float)(m + (double)acc[q]);
+            }
         }
         __syncwarp();
     }
-    (void)N;
 }
 
 __global__ void __launch_bounds__(kSampleThreads)
 k_sample(const double *__restrict__ mu, const float *__restrict__ Lt, int N, int K,
          uint32_t k0, uint32_t k1, uint32_t iter, uint32_t query, float *xi)
 {
-    extern __shared__ float sm[];
-    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
-    sample_body(mu, Lt, N, K, k0, k1, iter, query, xi, warp, n_warps, N, sm);
+    extern __shared__ __align__(16) float sm[];
+    const int per_block = kSampleWarps * kSampleCands;
+    sample_body(mu, Lt, K, k0, k1, iter, query, xi, blockIdx.x * per_block, gridDim.x * per_block, N, sm);
 }
 
 // Every query's draw in one launch: block b of query q takes the kBatchSampleCands
-// candidates from b kBatchSampleCands, one per warp at a time. A candidate's normals and
-// arithmetic do not depend on which warp draws it, so each query's xi equals its plain draw.
+// candidates from b kBatchSampleCands. A candidate's normals and arithmetic do not depend on
+// which warp draws it, so each query's xi equals its plain draw.
 __global__ void __launch_bounds__(kSampleThreads)
 k_batch_sample(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab, uint32_t iter)
 {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     const int2 e = tab[blockIdx.x];
     const BatchQueryDev &q = qd[e.x];
     const int b = e.y * kBatchSampleCands;
-    const int warps = kSampleThreads / 32;
-    sample_body(q.mu, q.Lt, q.N, q.K, q.seed_lo, q.seed_hi, iter, q.query, q.xi, b + (int)(threadIdx.x >> 5), warps,
+    static_assert(kBatchSampleCands == kSampleWarps * kSampleCands, "one group of candidates per warp");
+    sample_body(q.mu, q.Lt, q.K, q.seed_lo, q.seed_hi, iter, q.query, q.xi, b, kBatchSampleCands,
                 min(q.N, b + kBatchSampleCands), sm);
 }
-
-size_t sample_smem(int K) { return sizeof(float) * ((size_t)16 * K * K + (kSampleThreads / 32) * 4 * K); }
 
 }  // namespace
 
@@ -270,8 +307,7 @@ int launch_sample(const double *mu, const float *Lt_f, int N, int K, uint64_t se
     const size_t smem = sample_smem(K);
     CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample, kSampleThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    const int warps = kSampleThreads / 32;
-    int blocks = (N + warps - 1) / warps;
+    int blocks = (N + kSampleWarps * kSampleCands - 1) / (kSampleWarps * kSampleCands);
     if (blocks > sms * per_sm) blocks = sms * per_sm;
     k_sample<<<blocks, kSampleThreads, smem, st>>>(mu, Lt_f, N, K, (uint32_t)seed,
                                                    (uint32_t)(seed >> 32), iter, query, xi);

@@ -99,7 +99,7 @@ __global__ void k_scatter(int *__restrict__ rank, const double *__restrict__ J,
 // Block (tile t of the lower triangle of 16x16 tiles, chunk p of kChunk-row groups): one
 // S2 entry per thread, and S1 of the tile's rows on diagonal tiles. Partials are stored
 // entry-major ([entry][chunk]) so that the combine reads them with coalesced loads.
-__device__ __forceinline__ void moments_partial_body(const float *__restrict__ elites, const double *__restrict__ w,
+__device__ __forceinline__ void moments_partial_body(const double *__restrict__ Y, const double *__restrict__ WY,
                                                     int nu, int D, int per, int n_chunks, double *s2p, double *s1p,
                                                     int t, int p)
 {
@@ -111,8 +111,12 @@ __device__ __forceinline__ void moments_partial_body(const float *__restrict__ e
         ++tr;
     }
     const int tc = t;
-    const int a = threadIdx.x >> 4, b = threadIdx.x & 15;
     const bool diag = tr == tc;
+    // the thread's entry (a, b) of the tile: all 256 of an off-diagonal tile; the 136 with
+    // b <= a of a diagonal tile (warps 5-7 idle there)
+    int a = threadIdx.x >> 4, b = threadIdx.x & 15;
+    const bool active = !diag || threadIdx.x < 136;
+    if (diag && active) tri_index(threadIdx.x, a, b);
     const int j_end = min(nu, (p + 1) * per);
     // four interleaved accumulators: a dependent FP64 FMA waits tens of cycles, so one
     // running sum would leave the FP64 pipe idle between its steps
@@ -123,32 +127,61 @@ __device__ __forceinline__ void moments_partial_body(const float *__restrict__ e
         for (int idx = threadIdx.x; idx < cnt * 16; idx += blockDim.x) {
             const int j = idx >> 4, k = idx & 15;
             const int r = tr * 16 + k, c = tc * 16 + k;
-            const float *row = elites + (size_t)(j0 + j) * D;
-            wyr[j][k] = r < D ? w[j0 + j] * ((double)row[r] - (double)elites[r]) : 0.0;
-            yc[j][k] = c < D ? (double)row[c] - (double)elites[c] : 0.0;
+            const size_t row = (size_t)(j0 + j) * D;
+            wyr[j][k] = r < D ? WY[row + r] : 0.0;
+            yc[j][k] = c < D ? Y[row + c] : 0.0;
         }
         __syncthreads();
-        int j = 0;
-        for (; j + 3 < cnt; j += 4) {
-            a0 = fma(wyr[j][a], yc[j][b], a0);
-            a1 = fma(wyr[j + 1][a], yc[j + 1][b], a1);
-            a2 = fma(wyr[j + 2][a], yc[j + 2][b], a2);
-            a3 = fma(wyr[j + 3][a], yc[j + 3][b], a3);
+        if (active) {
+            int j = 0;
+            for (; j + 3 < cnt; j += 4) {
+                a0 = fma(wyr[j][a], yc[j][b], a0);
+                a1 = fma(wyr[j + 1][a], yc[j + 1][b], a1);
+                a2 = fma(wyr[j + 2][a], yc[j + 2][b], a2);
+                a3 = fma(wyr[j + 3][a], yc[j + 3][b], a3);
+            }
+            for (; j < cnt; ++j) a0 = fma(wyr[j][a], yc[j][b], a0);
+            if (diag && b == 0)
+                for (int j = 0; j < cnt; ++j) acc1 += wyr[j][a];
         }
-        for (; j < cnt; ++j) a0 = fma(wyr[j][a], yc[j][b], a0);
-        if (diag && b == 0)
-            for (int j = 0; j < cnt; ++j) acc1 += wyr[j][a];
     }
     const int r = tr * 16 + a, c = tc * 16 + b;
-    if (r < D && c <= r) s2p[((size_t)r * D + c) * n_chunks + p] = (a0 + a1) + (a2 + a3);
-    if (diag && b == 0 && r < D) s1p[(size_t)r * n_chunks + p] = acc1;
+    if (active && r < D && c <= r) s2p[((size_t)r * D + c) * n_chunks + p] = (a0 + a1) + (a2 + a3);
+    if (active && diag && b == 0 && r < D) s1p[(size_t)r * n_chunks + p] = acc1;
+}
+
+// The elites' deviations from the best elite in FP64, y_j = x_(j) - x_(1) (exact: both are
+// FP32), and w_j y_j, once per update for every tile of the moments.
+__device__ __forceinline__ void moments_prep_body(const float *__restrict__ elites, const double *__restrict__ w,
+                                                 int nu, int D, double *Y, double *WY, int idx)
+{
+    if (idx >= nu * D) return;
+    const int j = idx / D, r = idx - j * D;
+    const double y = (double)elites[idx] - (double)elites[r];
+    Y[idx] = y;
+    WY[idx] = w[j] * y;
+}
+
+__global__ void k_moments_prep(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D,
+                               double *Y, double *WY)
+{
+    moments_prep_body(elites, w, nu, D, Y, WY, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(256)
-k_moments_partial(const float *__restrict__ elites, const double *__restrict__ w, int nu, int D,
+k_moments_partial(const double *__restrict__ Y, const double *__restrict__ WY, int nu, int D,
                   int per, int n_chunks, double *s2p, double *s1p)
 {
-    moments_partial_body(elites, w, nu, D, per, n_chunks, s2p, s1p, blockIdx.x, blockIdx.y);
+    moments_partial_body(Y, WY, nu, D, per, n_chunks, s2p, s1p, blockIdx.x, blockIdx.y);
+}
+
+// Every query's deviations in one launch (block b of query q: entries 256 b ..).
+__global__ void __launch_bounds__(256)
+k_batch_moments_prep(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab)
+{
+    const int2 e = tab[blockIdx.x];
+    const BatchQueryDev &q = qd[e.x];
+    moments_prep_body(q.elites, q.w, q.nu, q.D, q.mom_y, q.mom_y + (size_t)q.nu * q.D, e.y * 256 + (int)threadIdx.x);
 }
 
 // Every query's partials in one launch: block b of query q is tile b % tiles, chunk b / tiles
@@ -159,7 +192,8 @@ k_batch_moments_partial(const BatchQueryDev *__restrict__ qd, const int2 *__rest
     const int2 e = tab[blockIdx.x];
     const BatchQueryDev &q = qd[e.x];
     const int nt = (q.D + 15) / 16, tiles = nt * (nt + 1) / 2;
-    moments_partial_body(q.elites, q.w, q.nu, q.D, q.per, q.n_chunks, q.s2p, q.s1p, e.y % tiles, e.y / tiles);
+    moments_partial_body(q.mom_y, q.mom_y + (size_t)q.nu * q.D, q.nu, q.D, q.per, q.n_chunks, q.s2p, q.s1p,
+                         e.y % tiles, e.y / tiles);
 }
 
 // Sum of n values at stride 1, lane-strided and then by a fixed shuffle tree (every lane
@@ -255,28 +289,61 @@ k_radix_hist(const unsigned long long *__restrict__ key, int N, int shift, int t
     hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];   // digit-major
 }
 
-// Exclusive scan of n = 256 * tiles counts in place (one CTA).
+// Exclusive scan of n = 256 * tiles counts in place (one CTA; n is a multiple of 8 and a is
+// 16-byte aligned): 8192 counts at a time, eight consecutive ones per thread (two 16-byte
+// loads), the threads' totals scanned by warp shuffles and the warp totals by warp 0, and
+// the running total carried to the next 8192.
 __global__ void __launch_bounds__(1024) k_radix_scan(int *a, int n)
 {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
-    const int per = (n + 1023) / 1024;
-    const int b = t * per, e = min(n, b + per);
-    int acc = 0;
-    for (int i = b; i < e; ++i) acc += a[i];
-    part[t] = acc;
+    __shared__ int warp_tot[32];
+    __shared__ int carry_s;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) carry_s = 0;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int v = t >= off ? part[t - off] : 0;
+    for (int base = 0; base < n; base += 8192) {
+        const int i = base + 8 * t;
+        int4 u = make_int4(0, 0, 0, 0), w = make_int4(0, 0, 0, 0);
+        if (i < n) {
+            u = *reinterpret_cast<const int4 *>(a + i);
+            w = *reinterpret_cast<const int4 *>(a + i + 4);
+        }
+        const int sum = u.x + u.y + u.z + u.w + w.x + w.y + w.z + w.w;
+        int x = sum;   // inclusive scan of the thread totals within the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
         __syncthreads();
-        part[t] += v;
+        if (warp == 0) {
+            int v = warp_tot[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, off);
+                if (lane >= off) v += y;
+            }
+            warp_tot[lane] = v;   // inclusive over warps
+        }
         __syncthreads();
-    }
-    int run = t > 0 ? part[t - 1] : 0;
-    for (int i = b; i < e; ++i) {
-        const int c = a[i];
-        a[i] = run;
-        run += c;
+        const int carry = carry_s;
+        int run = carry + (warp > 0 ? warp_tot[warp - 1] : 0) + x - sum;
+        if (i < n) {
+            int4 o, q;
+            o.x = run; run += u.x;
+            o.y = run; run += u.y;
+            o.z = run; run += u.z;
+            o.w = run; run += u.w;
+            q.x = run; run += w.x;
+            q.y = run; run += w.y;
+            q.z = run; run += w.z;
+            q.w = run;
+            *reinterpret_cast<int4 *>(a + i) = o;
+            *reinterpret_cast<int4 *>(a + i + 4) = q;
+        }
+        __syncthreads();
+        if (t == 1023) carry_s = carry + warp_tot[31];
+        __syncthreads();
     }
 }
 
@@ -543,16 +610,22 @@ int launch_gather_elites(const int *sorted, const double *J, const float *xi, in
     return CP_OK;
 }
 
-// Number of partials (chunks of elites) the update uses for nu elites, and elites per chunk.
-int update_chunks(int nu)
+// Number of partials (chunks of elites) the update uses for nu elites of dimension D, and
+// elites per chunk: chunks of 32 elites, doubled (up to 256) while the partial launch would
+// have more than 1024 blocks, at most kMaxChunks chunks. A function of (nu, D) alone, so the
+// order of the sums does not depend on the device.
+int update_chunks(int nu, int D)
 {
-    const int n = (nu + kChunk - 1) / kChunk;
+    const int nt = (D + 15) / 16, tiles = nt * (nt + 1) / 2;
+    int e = kChunk;
+    while (e < 256 && (long long)((nu + e - 1) / e) * tiles > 1024) e *= 2;
+    const int n = (nu + e - 1) / e;
     return n < kMaxChunks ? n : kMaxChunks;
 }
 
-static int per_chunk(int nu)
+static int per_chunk(int nu, int D)
 {
-    const int n = update_chunks(nu);
+    const int n = update_chunks(nu, D);
     const int per = (nu + n - 1) / n;
     return (per + kChunk - 1) / kChunk * kChunk;
 }
@@ -601,16 +674,29 @@ int launch_cma_reset(double sigma0, int D, double *cma, double *p_sigma, double 
 
 // CMA-ES update: mu_prev must hold the mean before the update; mu, C, p_sigma, p_c and cma
 // are updated in place (L is the factor of sigma^2 C before the update).
-int launch_cma_update(const float *elites, const double *w, int nu, int D, const double *mu_prev,
-                      const double *L, const CmaConsts &k, int t, double *s2p, double *s1p, double *mu,
-                      double *C, double *p_sigma, double *p_c, double *cma, cudaStream_t st)
+static int launch_moments_partial(const float *elites, const double *w, int nu, int D, double *yw, double *s2p,
+                                  double *s1p, int *n_chunks_out, cudaStream_t st)
 {
-    const int per = per_chunk(nu);
+    const int per = per_chunk(nu, D);
     const int n_chunks = (nu + per - 1) / per;
     const int tiles = (D + 15) / 16;
+    double *Y = yw, *WY = yw + (size_t)nu * D;
+    k_moments_prep<<<(nu * D + 255) / 256, 256, 0, st>>>(elites, w, nu, D, Y, WY);
+    CP_LAUNCHED("k_moments_prep");
     dim3 grid(tiles * (tiles + 1) / 2, n_chunks);
-    k_moments_partial<<<grid, 256, 0, st>>>(elites, w, nu, D, per, n_chunks, s2p, s1p);
+    k_moments_partial<<<grid, 256, 0, st>>>(Y, WY, nu, D, per, n_chunks, s2p, s1p);
     CP_LAUNCHED("k_moments_partial");
+    *n_chunks_out = n_chunks;
+    return CP_OK;
+}
+
+int launch_cma_update(const float *elites, const double *w, int nu, int D, const double *mu_prev,
+                      const double *L, const CmaConsts &k, int t, double *yw, double *s2p, double *s1p, double *mu,
+                      double *C, double *p_sigma, double *p_c, double *cma, cudaStream_t st)
+{
+    int n_chunks = 0;
+    int rc = launch_moments_partial(elites, w, nu, D, yw, s2p, s1p, &n_chunks, st);
+    if (rc != CP_OK) return rc;
     const size_t smem = sizeof(double) * (size_t)D * (D + 1);
     k_cma_paths<<<1, kCmaThreads, smem, st>>>(s1p, n_chunks, D, elites, mu_prev, L, k, t, mu, p_sigma, p_c, cma);
     CP_LAUNCHED("k_cma_paths");
@@ -621,9 +707,9 @@ int launch_cma_update(const float *elites, const double *w, int nu, int D, const
     return CP_OK;
 }
 
-int moments_chunking(int nu, int *per)
+int moments_chunking(int nu, int D, int *per)
 {
-    *per = per_chunk(nu);
+    *per = per_chunk(nu, D);
     return (nu + *per - 1) / *per;
 }
 
@@ -675,9 +761,11 @@ int launch_batch_gather(const BatchQueryDev *qd, const int2 *tab, int blocks, co
     return CP_OK;
 }
 
-int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_partial, int blocks_partial,
-                         const int2 *tab_combine, int blocks_combine, cudaStream_t st)
+int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_prep, int blocks_prep, const int2 *tab_partial,
+                         int blocks_partial, const int2 *tab_combine, int blocks_combine, cudaStream_t st)
 {
+    k_batch_moments_prep<<<blocks_prep, 256, 0, st>>>(qd, tab_prep);
+    CP_LAUNCHED("k_batch_moments_prep");
     k_batch_moments_partial<<<blocks_partial, 256, 0, st>>>(qd, tab_partial);
     CP_LAUNCHED("k_batch_moments_partial");
     k_batch_moments_combine<<<blocks_combine, 256, 0, st>>>(qd, tab_combine);
@@ -685,15 +773,12 @@ int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_partial, int b
     return CP_OK;
 }
 
-int launch_moments(const float *elites, const double *w, int nu, int D, double eps,
+int launch_moments(const float *elites, const double *w, int nu, int D, double eps, double *yw,
                    double *s2p, double *s1p, double *mu, double *C, cudaStream_t st)
 {
-    const int per = per_chunk(nu);
-    const int n_chunks = (nu + per - 1) / per;
-    const int tiles = (D + 15) / 16;
-    dim3 grid(tiles * (tiles + 1) / 2, n_chunks);
-    k_moments_partial<<<grid, 256, 0, st>>>(elites, w, nu, D, per, n_chunks, s2p, s1p);
-    CP_LAUNCHED("k_moments_partial");
+    int n_chunks = 0;
+    int rc = launch_moments_partial(elites, w, nu, D, yw, s2p, s1p, &n_chunks, st);
+    if (rc != CP_OK) return rc;
     const int entries = D * (D + 1) / 2;
     k_moments_combine<<<(entries * 32 + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, eps, elites,
                                                                   mu, C);

@@ -40,10 +40,12 @@ def test_every_declared_symbol_is_exported(cp):
 def test_struct_layout_matches_header(cp, tmp_path):
     src = tmp_path / "probe.c"
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "craneplan.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                    'sizeof(cp_model), sizeof(cp_params), sizeof(cp_plan_stats),'
                    'sizeof(cp_timing), sizeof(cp_scene), sizeof(cp_cylinder), sizeof(cp_box),'
-                   'offsetof(cp_params, seed), offsetof(cp_model, spheres));return 0;}\n')
+                   'offsetof(cp_params, seed), offsetof(cp_model, spheres), sizeof(cp_batch_shape),'
+                   'sizeof(cp_batch_info), offsetof(cp_batch_info, last_run_ms), sizeof(cp_traj_params));'
+                   'return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
@@ -52,7 +54,9 @@ def test_struct_layout_matches_header(cp, tmp_path):
     want = [ctypes.sizeof(cp.cp_model), ctypes.sizeof(cp.cp_params),
             ctypes.sizeof(cp.cp_plan_stats), ctypes.sizeof(cp.cp_timing),
             ctypes.sizeof(cp.cp_scene), ctypes.sizeof(cp.cp_cylinder),
-            ctypes.sizeof(cp.cp_box), cp.cp_params.seed.offset, cp.cp_model.spheres.offset]
+            ctypes.sizeof(cp.cp_box), cp.cp_params.seed.offset, cp.cp_model.spheres.offset,
+            ctypes.sizeof(cp.cp_batch_shape), ctypes.sizeof(cp.cp_batch_info),
+            cp.cp_batch_info.last_run_ms.offset, ctypes.sizeof(cp.cp_traj_params)]
     assert got == want
 
 
