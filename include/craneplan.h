@@ -386,6 +386,18 @@ int cp_get_factor(const cp_planner *p, double *d_L);
 /* Copy the candidate indices of the last update in rank order (int32[nu]). */
 int cp_get_elites(const cp_planner *p, int32_t *d_idx);
 
+/* Per-iteration metrics of cp_plan (off by default; on costs one small kernel per
+ * iteration). Each iteration of cp_plan while on writes one row {iteration, best J of the
+ * population, mean J of the population, tr C of the updated distribution, fraction of the
+ * population without a checkpoint in collision} (tr C of the factor-free sampler's
+ * distribution is taken from the elites: sum_j w_j |x_(j) - mu|^2 + D eps) into a device ring
+ * of the last 256 iterations. cp_set_endpoints restarts the record. */
+int cp_set_metrics(cp_planner *p, int32_t on);
+
+/* Copy up to max_rows of the most recent metric rows (host double[rows][5], oldest first)
+ * and their count to *n_rows (synchronises the planner's stream). Errors: CP_ERR_ARG. */
+int cp_get_metrics(cp_planner *p, double *h_rows, int32_t max_rows, int32_t *n_rows);
+
 /* Copy the population of the last iteration of cp_plan (or of a batch run) and its costs:
  * d_xi float[N][K][4], d_J double[N] (either may be NULL). Only the planner's own draws
  * are kept here; cp_sample and cp_evaluate write the caller's buffers. */

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcraneplan.so")
 SOURCES = ["api.cu", "k_eval.cu", "k_init.cu", "k_sample.cu", "k_update.cu", "k_noalloc.cu", "k_grid.cu", "k_smooth.cu",
-           "k_peaks.cu", "k_ik.cu", "k_sample_elites.cu", "k_hulls.cu", "k_finalize.cu", "k_traj.cu"]
+           "k_peaks.cu", "k_ik.cu", "k_sample_elites.cu", "k_hulls.cu", "k_finalize.cu", "k_traj.cu", "k_metrics.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -176,6 +176,9 @@ _SIGS = {
     "cp_set_cma_state": (ctypes.c_int, [_P, _P]),
     "cp_get_elites": (ctypes.c_int, [_P, _P]),
     "cp_get_population": (ctypes.c_int, [_P, _P, _P]),
+    "cp_set_metrics": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cp_get_metrics": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32)]),
     "cp_philox4x32_10": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P]),
     "cp_evaluate_static": (ctypes.c_int, [ctypes.POINTER(cp_model), _P, ctypes.c_int32, _P,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -436,6 +439,19 @@ def cp_set_cma_state(p: int, state) -> None:
 
 def cp_get_elites(p: int, idx) -> None:
     _check(load().cp_get_elites(p, _ptr(idx)))
+
+
+def cp_set_metrics(p: int, on: bool) -> None:
+    _check(load().cp_set_metrics(p, 1 if on else 0))
+
+
+def cp_get_metrics(p: int, max_rows: int = 256) -> np.ndarray:
+    """Rows {iteration, best J, mean J, tr C, collision-free fraction}, oldest first."""
+    buf = np.zeros((max(max_rows, 1), 5), dtype=np.float64)
+    n = ctypes.c_int32()
+    _check(load().cp_get_metrics(p, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(max_rows),
+                                 ctypes.byref(n)))
+    return buf[: n.value].copy()
 
 
 def cp_get_population(p: int, xi=None, J=None) -> None:

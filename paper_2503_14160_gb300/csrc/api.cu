@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cp_internal.cuh"
 
 namespace cp {
@@ -118,6 +120,15 @@ bool aligned16(const void *ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 constexpr int kPolarBins = 256;   // angular bins of the polar obstacle index
 
+// An NVTX range over a scope (host side: it brackets the enqueue of a stage's launches; a
+// profiler attributes the kernels launched inside it to the range). No-ops without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 }  // namespace
 
 struct cp_planner {
@@ -193,7 +204,12 @@ struct cp_planner {
     SceneDev plan_sdev{};
     PolarDev plan_gdev{};
     bool plan_ready_before = false, plan_ready_after = false;
+    bool plan_metrics = false;
     int64_t plan_nodes = 0;   // kernels in the recorded graph
+    // per-iteration metrics of cp_plan: ring of kMetricsRing rows (slot = iteration mod ring)
+    bool metrics_on = false;
+    double *metrics = nullptr;
+    int64_t metrics_count = 0;   // rows written since the end points were set
 };
 
 namespace cp {
@@ -425,6 +441,7 @@ int stage_scene(cp_planner *p, const cp_scene *sc)
 int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_flag,
              double *d_terms, uint32_t *d_words, float *d_pen)
 {
+    NvtxRange range("craneplan:evaluate");
     EvalArgs a{};
     a.xi = (const float4 *)d_xi;
     a.n = n;
@@ -473,6 +490,7 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
 
 int run_factor(cp_planner *p)
 {
+    NvtxRange range("craneplan:factor");
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
     rc = launch_factor(p->C, p->prm.sigma * p->prm.sigma, p->prm.update_rule == CP_UPDATE_CMAES ? p->cma : nullptr,
@@ -483,6 +501,7 @@ int run_factor(cp_planner *p)
 
 int run_sample(cp_planner *p, int iter, float *d_xi)
 {
+    NvtxRange range("craneplan:sample");
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
     if (p->elites_ready)
@@ -498,6 +517,7 @@ int run_sample(cp_planner *p, int iter, float *d_xi)
 
 int run_update(cp_planner *p, const double *d_J, const float *d_xi)
 {
+    NvtxRange range("craneplan:update");
     int rc = p->timer.begin(p->st);
     if (rc != CP_OK) return rc;
     if (p->N >= kRadixMinN) {
@@ -551,6 +571,27 @@ int materialise_distribution(const cp_planner *p)
                             q->st);
     if (rc != CP_OK) return rc;
     return launch_factor(q->C, q->prm.sigma * q->prm.sigma, nullptr, q->D, q->L, q->Lt, q->status, q->st);
+}
+
+// The metrics row of the iteration just completed by cp_plan (after run_update).
+int record_metrics(cp_planner *p)
+{
+    if (!p->metrics_on) return CP_OK;
+    const int it = p->iteration - 1;
+    double *row = p->metrics + (size_t)(it % kMetricsRing) * kMetricsCols;
+    const bool no_C = p->elites_ready;   // the factor-free sampler's update forms no C
+    return launch_iter_metrics(p->J, p->flag, p->N, p->best, no_C ? nullptr : p->C, p->elites, p->w, p->mu, p->nu,
+                               p->D, p->prm.eps, it, row, p->st);
+}
+
+// One iteration of cp_plan: steps (1)-(6) and the metrics row when on.
+int run_iteration(cp_planner *p)
+{
+    int rc;
+    if ((rc = run_sample(p, p->iteration, p->xi)) != CP_OK) return rc;
+    if ((rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr)) != CP_OK) return rc;
+    if ((rc = run_update(p, p->J, p->xi)) != CP_OK) return rc;
+    return record_metrics(p);
 }
 
 int check_status(cp_planner *p)
@@ -711,6 +752,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_sp_g = L.take<float>(units_max * D);
     const size_t o_sp_J = L.take<double>(units_max);
     const size_t o_work = L.take<unsigned long long>(2);
+    const size_t o_metrics = L.take<double>((size_t)kMetricsRing * kMetricsCols);
     const size_t o_cma = L.take<double>(4);
     const size_t o_psig = L.take<double>(D);
     const size_t o_pc = L.take<double>(D);
@@ -773,6 +815,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->grad = (float *)(b + o_grad);
     p->ends_f = (float4 *)(b + o_ends_f);
     p->work = (unsigned long long *)(b + o_work);
+    p->metrics = (double *)(b + o_metrics);
     p->cma = (double *)(b + o_cma);
     p->p_sigma = (double *)(b + o_psig);
     p->p_c = (double *)(b + o_pc);
@@ -864,6 +907,7 @@ int cp_set_endpoints(cp_planner *p, const double h_q0[4], const double h_qd[4])
     p->iteration = 0;
     p->elites_ready = false;
     p->have_endpoints = true;
+    p->metrics_count = 0;
     return run_factor(p);
 }
 
@@ -916,7 +960,7 @@ bool same_grid(const PolarDev &a, const PolarDev &b)
 int run_plan_graph(cp_planner *p, int iters)
 {
     const bool same = p->plan_exec && p->plan_start == p->iteration && p->plan_iters == iters &&
-                      p->plan_ready_before == p->elites_ready &&
+                      p->plan_ready_before == p->elites_ready && p->plan_metrics == p->metrics_on &&
                       same_scene(p->plan_sdev, p->sdev) && same_grid(p->plan_gdev, p->gdev) &&
                       memcmp(&p->plan_q0, &p->q0f, sizeof(float4)) == 0 &&
                       memcmp(&p->plan_qd, &p->qdf, sizeof(float4)) == 0;
@@ -934,11 +978,7 @@ int run_plan_graph(cp_planner *p, int iters)
             return cuda_fail(e_begin, "cudaStreamBeginCapture");
         }
         int rc = CP_OK;
-        for (int it = 0; it < iters && rc == CP_OK; ++it) {
-            rc = run_sample(p, p->iteration, p->xi);
-            if (rc == CP_OK) rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr);
-            if (rc == CP_OK) rc = run_update(p, p->J, p->xi);
-        }
+        for (int it = 0; it < iters && rc == CP_OK; ++it) rc = run_iteration(p);
         cudaGraph_t graph = nullptr;
         const cudaError_t e_end = cudaStreamEndCapture(p->st, &graph);
         p->iteration = start;
@@ -960,6 +1000,7 @@ int run_plan_graph(cp_planner *p, int iters)
         }
         p->plan_start = start;
         p->plan_iters = iters;
+        p->plan_metrics = p->metrics_on;
         p->plan_sdev = p->sdev;
         p->plan_gdev = p->gdev;
         p->plan_q0 = p->q0f;
@@ -968,6 +1009,7 @@ int run_plan_graph(cp_planner *p, int iters)
     CP_CUDA(cudaGraphLaunch(p->plan_exec, p->st));
     g_launches.fetch_add(p->plan_nodes, std::memory_order_relaxed);
     p->iteration = start + iters;
+    if (p->plan_metrics) p->metrics_count += iters;
     p->elites_ready = p->plan_ready_after;
     return CP_OK;
 }
@@ -982,11 +1024,11 @@ int cp_plan(cp_planner *p, int32_t iters, double *h_ctrl, cp_plan_stats *stats)
     // be captured, so plans on it (and timed plans, whose stage events sit between the
     // kernels) launch kernel by kernel
     const bool capturable = p->st != nullptr && p->st != cudaStreamLegacy && p->st != cudaStreamPerThread;
+    NvtxRange range("craneplan:plan");
     if (p->timer.on || iters == 0 || !capturable) {
         for (int it = 0; it < iters; ++it) {
-            if ((rc = run_sample(p, p->iteration, p->xi)) != CP_OK) return rc;
-            if ((rc = run_eval(p, p->xi, p->N, p->J, p->flag, nullptr, nullptr, nullptr)) != CP_OK) return rc;
-            if ((rc = run_update(p, p->J, p->xi)) != CP_OK) return rc;
+            if ((rc = run_iteration(p)) != CP_OK) return rc;
+            if (p->metrics_on) p->metrics_count += 1;
         }
     } else if ((rc = run_plan_graph(p, iters)) != CP_OK) {
         return rc;
@@ -1052,6 +1094,7 @@ int cp_smooth_cost(cp_planner *p, const float *d_xi, int32_t n, double *d_J)
 int cp_smooth_cost_grad(cp_planner *p, const float *d_xi, int32_t n, const double *d_gJ,
                         double *d_J, float *d_dxi)
 {
+    NvtxRange range("craneplan:smooth_cost_grad");
     int rc = smooth_check(p, n, d_xi);
     if (rc != CP_OK) return rc;
     if (n > 0 && !d_dxi) return set_error("d_dxi is NULL"), CP_ERR_ARG;
@@ -1060,6 +1103,7 @@ int cp_smooth_cost_grad(cp_planner *p, const float *d_xi, int32_t n, const doubl
 
 int cp_polish(cp_planner *p, float *d_xi, int32_t n, int32_t steps, double alpha)
 {
+    NvtxRange range("craneplan:polish");
     int rc = smooth_check(p, n, d_xi);
     if (rc != CP_OK) return rc;
     if (steps < 0 || !is_finite(alpha)) return set_error("steps >= 0 and finite alpha"), CP_ERR_ARG;
@@ -1072,6 +1116,7 @@ int cp_polish(cp_planner *p, float *d_xi, int32_t n, int32_t steps, double alpha
 
 int cp_signed_distance(cp_planner *p, const float *d_q, int32_t n, float *d_d)
 {
+    NvtxRange range("craneplan:signed_distance");
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     if (n < 0 || (n > 0 && (!d_q || !d_d))) return set_error("invalid arguments"), CP_ERR_ARG;
     return launch_signed_distance(p->mdev, p->sdev, d_q, n, d_d, p->st);
@@ -1110,6 +1155,7 @@ int hull_dims(const cp_hull_model *hulls, HullDims &d)
 
 int cp_hull_penetration(cp_planner *p, const float *d_q, int32_t n, const cp_hull_model *hulls, float *d_pen)
 {
+    NvtxRange range("craneplan:hull_penetration");
     if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
     if (n < 0 || (n > 0 && (!d_q || !d_pen))) return set_error("invalid arguments"), CP_ERR_ARG;
     if ((uintptr_t)d_q & 15u) return set_error("d_q must be 16-byte aligned"), CP_ERR_ARG;
@@ -1136,6 +1182,7 @@ int cp_set_hull_model(cp_planner *p, const cp_hull_model *hulls)
 int cp_ik(cp_planner *p, const float *d_targets, int32_t n, const cp_ik_params *ik,
           const float *d_q_init, float *d_q, float *d_f, int32_t *d_restart, float *d_r)
 {
+    NvtxRange range("craneplan:ik");
     if (!p || !ik) return set_error("NULL argument"), CP_ERR_ARG;
     if (n < 0 || (n > 0 && (!d_targets || !d_q || !d_f))) return set_error("invalid arguments"), CP_ERR_ARG;
     if (ik->restarts < 1 || ik->restarts > CP_IK_MAX_RESTARTS)
@@ -1218,6 +1265,31 @@ int cp_get_population(const cp_planner *p, float *d_xi, double *d_J)
     if (d_xi)
         CP_CUDA(cudaMemcpyAsync(d_xi, p->xi, sizeof(float) * (size_t)p->N * p->D, cudaMemcpyDeviceToDevice, p->st));
     if (d_J) CP_CUDA(cudaMemcpyAsync(d_J, p->J, sizeof(double) * (size_t)p->N, cudaMemcpyDeviceToDevice, p->st));
+    return CP_OK;
+}
+
+int cp_set_metrics(cp_planner *p, int32_t on)
+{
+    if (!p) return set_error("planner is NULL"), CP_ERR_ARG;
+    p->metrics_on = on != 0;
+    return CP_OK;
+}
+
+int cp_get_metrics(cp_planner *p, double *h_rows, int32_t max_rows, int32_t *n_rows)
+{
+    if (!p || !n_rows || max_rows < 0 || (max_rows > 0 && !h_rows)) return set_error("invalid arguments"), CP_ERR_ARG;
+    int64_t n = std::min<int64_t>(p->metrics_count, kMetricsRing);
+    n = std::min<int64_t>(n, max_rows);
+    n = std::min<int64_t>(n, p->iteration);
+    *n_rows = (int32_t)n;
+    if (n == 0) return CP_OK;
+    double ring[kMetricsRing * kMetricsCols];
+    CP_CUDA(cudaMemcpyAsync(ring, p->metrics, sizeof ring, cudaMemcpyDeviceToHost, p->st));
+    CP_CUDA(cudaStreamSynchronize(p->st));
+    const int first = p->iteration - (int)n;   // oldest iteration returned
+    for (int64_t r = 0; r < n; ++r)
+        memcpy(h_rows + r * kMetricsCols, ring + (size_t)((first + r) % kMetricsRing) * kMetricsCols,
+               sizeof(double) * kMetricsCols);
     return CP_OK;
 }
 
@@ -1710,6 +1782,7 @@ int cp_batch_set_endpoints(cp_batch *b, int32_t q, const double h_q0[4], const d
 int cp_batch_run(cp_batch *b, cp_batch_result *results)
 {
     if (!b) return set_error("batch is NULL"), CP_ERR_ARG;
+    NvtxRange range("craneplan:batch_run");
     CP_CUDA(cudaEventRecord(b->ev0, b->st));
     CP_CUDA(cudaGraphLaunch(b->exec, b->st));
     g_launches.fetch_add(b->kernel_nodes, std::memory_order_relaxed);

@@ -286,6 +286,14 @@ int launch_gather_elites(const int *sorted, const double *J, const float *xi, in
 constexpr int kRadixMinN = 8193;   // the radix sort ranks populations above 8192
 int update_configure();
 
+// Per-iteration metrics row {iteration, best J, mean J, tr C, collision-free fraction}; C
+// null: tr C from the elites about mu (factor-free sampler).
+constexpr int kMetricsCols = 5;
+constexpr int kMetricsRing = 256;   // rows kept (the last kMetricsRing iterations)
+int launch_iter_metrics(const double *J, const uint8_t *flag, int N, const double *best, const double *C,
+                        const float *elites, const double *w, const double *mu, int nu, int D, double eps,
+                        int iteration, double *row, cudaStream_t st);
+
 // ------------------------------------------------------------------ batched form
 // One launch of each stage serves every query of a batch. Each query keeps its own planner
 // workspace; the batched kernels reach it through this per-query view, and a block finds its

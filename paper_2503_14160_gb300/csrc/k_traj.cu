@@ -24,7 +24,15 @@
 #include <cmath>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cp_internal.cuh"
+
+// An NVTX range over a scope (no-op without a profiling tool).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+};
 
 namespace cp {
 namespace {
@@ -731,6 +739,7 @@ int cp_traj_initial_guess(cp_traj *t, const double *d_q_star, int32_t n, double 
 int cp_traj_step(cp_traj *t, const double *d_q_star, int32_t n, const double *d_z, const double *d_lam, double mu,
                  double *d_dz)
 {
+    const NvtxScope range("craneplan:traj_step");
     if (!t) return set_error("solver is NULL"), CP_ERR_ARG;
     if (n < 0 || n > t->max_paths) return set_error("n = %d outside 0..%d", n, t->max_paths), CP_ERR_ARG;
     if (n > 0 && (!d_q_star || !d_z || !d_lam || !d_dz)) return set_error("NULL argument"), CP_ERR_ARG;
@@ -744,6 +753,7 @@ int cp_traj_step(cp_traj *t, const double *d_q_star, int32_t n, const double *d_
 
 int cp_traj_solve(cp_traj *t, const double *d_q_star, int32_t n, double *d_z, double *d_stats)
 {
+    const NvtxScope range("craneplan:traj_solve");
     if (!t) return set_error("solver is NULL"), CP_ERR_ARG;
     if (n < 0 || n > t->max_paths) return set_error("n = %d outside 0..%d", n, t->max_paths), CP_ERR_ARG;
     if (n > 0 && (!d_q_star || !d_z || !d_stats)) return set_error("NULL argument"), CP_ERR_ARG;
