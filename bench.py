@@ -331,6 +331,15 @@ def run_ours(args):
         cp.cp_plan(h, iters, K=None)
     timing = cp.cp_get_timing(h)
     cp.cp_set_timing(h, False)
+    # one more plan with the per-iteration metrics on (outside the timed region)
+    cp.cp_set_metrics(h, True)
+    cp.cp_set_endpoints(h, q0, qd)
+    cp.cp_plan(h, iters, K=None)
+    metric_rows = cp.cp_get_metrics(h)
+    cp.cp_set_metrics(h, False)
+    picks = sorted({0, len(metric_rows) // 4, len(metric_rows) // 2, 3 * len(metric_rows) // 4, len(metric_rows) - 1})
+    iteration_metrics = {"columns": ["iteration", "best_J", "mean_J", "trace_C", "collision_free_fraction"],
+                         "rows": [[float(v) for v in metric_rows[i]] for i in picks if 0 <= i < len(metric_rows)]}
 
     # end-to-end through the C ABI with host buffers, wall clock
     e2e_times = []
@@ -407,6 +416,7 @@ def run_ours(args):
             "fp64_stages": fp64_stages(timing, wl, peaks_fp64, sampler),
             "sampler_stage": sampler_stage(timing, wl, sampler),
             "plan_result": {"J": stats["J"], "length": stats["length"], "flag": stats["flag"]},
+            "iteration_metrics": iteration_metrics,
             "clocks": clk,
         }
         if not args.no_cpu_baseline:
@@ -908,7 +918,7 @@ def run_batch(args):
     cp.load()
     crane = workloads.forestry_crane()
     model = cp.make_model(crane)
-    S, T, nq = 64, args.iterations or 100, 64
+    S, T, nq = 64, args.iterations or 100, args.queries
     queries = workloads.batch_queries(nq, seed=rank)
     tuner = autotune.Autotuner()
     t_tune = time.perf_counter()
@@ -928,10 +938,16 @@ def run_batch(args):
     b = cp.cp_batch_init(model, scenes, params, q0s, qds, T)
     t_init = time.perf_counter() - t0
     Ks = [bq.n_waypoints for bq in queries]
-    cp.cp_batch_run(b, nq)                      # populations for the shape search
-    t1 = time.perf_counter()
-    tuned = tuner.tune_batch(b, "nq%d|seed%d|S%d" % (nq, rank, S))
-    t_tune += time.perf_counter() - t1
+    if args.batch_shape:
+        # a fixed launch shape (profiling runs): no shape search
+        shape = [int(v) for v in args.batch_shape.split(",")]
+        cp.cp_batch_set_shape(b, *shape)
+        tuned = {"shape": shape, "ms": [], "shapes": [], "fixed": True}
+    else:
+        cp.cp_batch_run(b, nq)                      # populations for the shape search
+        t1 = time.perf_counter()
+        tuned = tuner.tune_batch(b, "nq%d|seed%d|S%d" % (nq, rank, S))
+        t_tune += time.perf_counter() - t1
     info = cp.cp_batch_get_info(b)
     units = info["candidates"] * T
     for _ in range(max(args.warmup, 3)):
@@ -961,14 +977,14 @@ def run_batch(args):
         if rep > 0:
             seq.append((time.perf_counter() - t0) * 1e3)
     ms, ms_host, ms_seq = float(np.mean(dev_ms)), float(np.mean(host_ms)), float(np.mean(seq))
-    line = {"metric": "candidate paths evaluated/sec, 64-query batch (one graph, one launch per stage) "
-                      "vs sequential plain plans",
+    line = {"metric": "candidate paths evaluated/sec, %d-query batch (one graph, one launch per stage) "
+                      "vs sequential plain plans" % nq,
             "value": units / (ms / 1e3), "unit": "candidate paths/s", "n_gpus": ws,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded crane-and-forest scenes)",
-            "config": {"workload": "batch: 64 queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
-                                   "S=64, %d iterations" % T, "step": "one batch run (all queries)",
+            "config": {"workload": "batch: %d queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
+                                   "S=64, %d iterations" % (nq, T), "step": "one batch run (all queries)",
                        "l2": "working set above L2 (%d candidates x up to 128 floats, plus scenes)"
                              % info["candidates"]},
             "sequential": {"value": units / (ms_seq / 1e3), "ms_per_batch": ms_seq,
@@ -1367,9 +1383,10 @@ def run_batch_reference(args):
     import oracle
     crane = workloads.forestry_crane()
     S, T = 64, args.iterations or 100
-    queries = workloads.batch_queries(64, seed=rank)
-    q0s, qds = [None] * 64, [None] * 64
-    for q in range(0, 64, 8):
+    nq = args.queries
+    queries = workloads.batch_queries(nq, seed=rank)
+    q0s, qds = [None] * nq, [None] * nq
+    for q in range(0, nq, 8):
         bq = queries[q]
         pb = oracle.Problem(crane, workloads.batch_scene(bq, seed=rank, q=q), oracle.CostParams(K=bq.n_waypoints, S=S))
         q0s[q], qds[q], _, _ = workloads.select_endpoints(crane, lambda x: oracle.signed_distance(pb, x),
@@ -1380,14 +1397,14 @@ def run_batch_reference(args):
         if i >= args.warmup:
             per_step.append(r)
     value = float(np.mean([r["value"] for r in per_step]))
-    line = {"metric": "candidate paths evaluated/sec, 64-query batch (one graph, one launch per stage) "
-                      "vs sequential plain plans",
+    line = {"metric": "candidate paths evaluated/sec, %d-query batch (one graph, one launch per stage) "
+                      "vs sequential plain plans" % nq,
             "value": value, "unit": "candidate paths/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean([r["seconds"] for r in per_step])) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded crane-and-forest scenes)", "impl": "reference",
-            "config": {"workload": "batch: 64 queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
-                                   "S=64, %d iterations" % T,
+            "config": {"workload": "batch: %d queries, N U[1024,16384], K U[8,32], cylinders U[50,3000], "
+                                   "S=64, %d iterations" % (nq, T),
                        "step": "a bounded sample: candidate evaluations of every eighth query"},
             "cpu_baseline": {"value": value, "unit": "candidate paths/s", "cores": per_step[0]["cores"],
                              "kind": "oracle", "sample": per_step[0]["sample"]},
@@ -1414,6 +1431,10 @@ def main():
                     help="steps (5)-(6) as Algorithm 1 prints them, or the CMA-ES update")
     ap.add_argument("--exhaustive", action="store_true",
                     help="evaluate every sphere against every obstacle (no broad phase)")
+    ap.add_argument("--queries", type=int, default=64, help="batch workload: number of queries")
+    ap.add_argument("--batch-shape", default="",
+                    help="batch workload: fixed evaluation shape 'threads,ctas_per_sm,items_per_warp' "
+                         "(skips the autotuner)")
     args = ap.parse_args()
     if args.impl == "reference" and args.workload == "ik":
         run_ik_reference(args)
