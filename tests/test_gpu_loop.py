@@ -160,7 +160,7 @@ def test_teacher_forced_single_large_elites(lib, crane):
 
 def test_teacher_forced_dense_forest(lib, crane):
     """The dense forest at its full size (N=65536, K=32, S=128, 5000 trees + 50 boxes through
-    the 0.5 m grid), one iteration with the factor sampler the benchmark uses there: the
+    the polar index with 0.5 m rings), one iteration with the factor sampler the benchmark uses there: the
     draw (4096 sampled rows against the FP64 draw), J of 256 sampled candidates against the
     oracle's grid form and 8 against its brute force checkpoint by checkpoint, the rank and
     update (radix path) on the GPU's own J of all 65536 candidates against the oracle's
