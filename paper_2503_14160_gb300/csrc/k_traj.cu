@@ -62,6 +62,21 @@ template <typename T> __device__ __forceinline__ T lift(double v);
 template <> __device__ __forceinline__ double lift<double>(double v) { return v; }
 template <> __device__ __forceinline__ Dual lift<Dual>(double v) { return {v, 0.0}; }
 
+// 1 / sqrt(a) in FP64 for the pivots of the block factorisation: an FP32 seed and two
+// Newton steps (quadratic convergence: about 22 -> 44 -> 88 bits), a short dependent chain
+// where FP64 operations wait tens of cycles each. Arguments outside FP32's normal range take
+// the IEEE operations (a non-positive pivot gives NaN, as sqrt would).
+__device__ __forceinline__ double rsqrt_pivot(double a)
+{
+    const float af = (float)a;
+    if (!(af > 1e-30f && af < 1e30f)) return 1.0 / sqrt(a);
+    double y = (double)rsqrtf(af);
+    const double hh = 0.5 * a;
+    y = y * fma(-hh * y, y, 1.5);
+    y = y * fma(-hh * y, y, 1.5);
+    return y;
+}
+
 struct TrajDev {
     double base_z, boom_len, jib_len, ell;
     double omega_s, omega_t, R[4];
@@ -232,14 +247,29 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
                lam[(size_t)k * NX + r] / rho;
     };
     auto eres = [&](int k, int r) -> double { return -(ws.f[(size_t)k * NX + r] + ws.f[(size_t)(k + 1) * NX + r]) / (2.0 * N); };
-    // diagonal blocks and their damping, off-diagonal blocks
+    // Diagonal blocks (lower triangles) and off-diagonal blocks from F_k = df/dw at grid
+    // point k (c = h/2, I' = [I 0] of 12 x 16): A_k = -(I' + c F_k), B_k = I' - c F_{k+1}, so
+    //   A_k^T A_k = I'^T I' + c (I'^T F_k + F_k^T I') + c^2 F_k^T F_k,
+    //   B_{k-1}^T B_{k-1} = I'^T I' - c (I'^T F_k + F_k^T I') + c^2 F_k^T F_k
+    // (interior points take both, whose first-order terms cancel) and
+    //   A_k^T B_k = -(I'^T I' - c I'^T F_{k+1} + c F_k^T I' - c^2 F_k^T F_{k+1}).
+    const double c = 0.5 * h;
+    auto Fjv = [&](int k, int r, int i) -> double { return ws.Fj[((size_t)k * NX + r) * NW + i]; };
     for (int e = t; e < (N + 1) * NW * NW; e += blockDim.x) {
         const int k = e / (NW * NW), ij = e - k * NW * NW, i = ij / NW, j = ij - i * NW;
-        double v = 0.0;
-        if (k < N)
-            for (int r = 0; r < NX; ++r) v += Aent(k, r, i) * Aent(k, r, j);
-        if (k > 0)
-            for (int r = 0; r < NX; ++r) v += Bent(k - 1, r, i) * Bent(k - 1, r, j);
+        if (j > i) continue;   // the factorisation reads the lower triangle only
+        double f0 = 0.0, f1 = 0.0;
+        for (int r = 0; r < NX; r += 2) {
+            f0 = fma(Fjv(k, r, i), Fjv(k, r, j), f0);
+            f1 = fma(Fjv(k, r + 1, i), Fjv(k, r + 1, j), f1);
+        }
+        const double ff = f0 + f1;
+        const double cross = (i < NX ? Fjv(k, i, j) : 0.0) + (j < NX ? Fjv(k, j, i) : 0.0);
+        const double id = (i == j && i < NX) ? 1.0 : 0.0;
+        double v;
+        if (k == 0) v = id + c * cross + c * c * ff;
+        else if (k == N) v = id - c * cross + c * c * ff;
+        else v = 2.0 * id + 2.0 * c * c * ff;
         v *= rho;
         if (i == j) {
             if ((k == 0 || k == N) && i < NX) v += rho;                      // end states
@@ -256,9 +286,15 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     }
     for (int e = t; e < N * NW * NW; e += blockDim.x) {
         const int k = e / (NW * NW), ij = e - k * NW * NW, i = ij / NW, j = ij - i * NW;
-        double v = 0.0;
-        for (int r = 0; r < NX; ++r) v += Aent(k, r, i) * Bent(k, r, j);
-        ws.E[e] = rho * v;
+        double p0 = 0.0, p1 = 0.0;
+        for (int r = 0; r < NX; r += 2) {
+            p0 = fma(Fjv(k, r, i), Fjv(k + 1, r, j), p0);
+            p1 = fma(Fjv(k, r + 1, i), Fjv(k + 1, r + 1, j), p1);
+        }
+        const double id = (i == j && i < NX) ? 1.0 : 0.0;
+        const double v = id - c * (i < NX ? Fjv(k + 1, i, j) : 0.0) + c * (j < NX ? Fjv(k, j, i) : 0.0) -
+                         c * c * (p0 + p1);
+        ws.E[e] = -rho * v;
     }
     // border column, gradient
     for (int e = t; e < (N + 1) * NW; e += blockDim.x) {
@@ -305,95 +341,115 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     __syncthreads();
     // 3. block Cholesky of the tridiagonal part, forward substitution of the border column
     //    (y) and the negated gradient (v): for k = 0..N
-    //      D_k -= M_{k-1}^T M_{k-1};  L_k L_k^T = D_k;  M_k = L_k^-1 E_k;
+    //      S_k = D_k - M_{k-1}^T M_{k-1};  L_k L_k^T = S_k;  M_k = L_k^-1 E_k;
     //      y_k = L_k^-1 (b_k - M_{k-1}^T y_{k-1});  v_k = L_k^-1 (-g_k - M_{k-1}^T v_{k-1}).
-    double *L = s_blk;   // 16 x 16 working block
+    //    The chain of the sweep is long dependent FP64 work, so every step keeps it short: the
+    //    16 x 16 factor runs on one warp in registers (lane i holds row i; the pivot's
+    //    reciprocal square root by rsqrt_pivot, the column scaled by it, the trailing rows
+    //    updated from shuffled column entries), and the triangular solves go column by
+    //    column with one lane per right-hand side. The stored factor keeps 1 / L_pp on its
+    //    diagonal for the back substitution.
+    double *Ls = s_blk;           // the current block: S_k, then its factor
+    double *s_vec = s_red + 8;    // [2][NW] right-hand sides of y_k and v_k
+    const unsigned full = 0xffffffffu;
     for (int k = 0; k <= N; ++k) {
         double *Dk = ws.D + (size_t)k * NW * NW;
+        const double *Mp = ws.E + (size_t)(k > 0 ? k - 1 : 0) * NW * NW;   // M_{k-1}
         for (int ij = t; ij < NW * NW; ij += blockDim.x) {
             const int i = ij / NW, j = ij - i * NW;
-            double v = Dk[ij];
-            if (k > 0) {
-                const double *M = ws.E + (size_t)(k - 1) * NW * NW;
-                for (int r = 0; r < NW; ++r) v -= M[r * NW + i] * M[r * NW + j];
-            }
-            L[ij] = v;
-        }
-        if (t < NW) {
-            double yv = ws.bb[(size_t)k * NW + t], vv = -ws.g[(size_t)k * NW + t];
-            if (k > 0) {
-                const double *M = ws.E + (size_t)(k - 1) * NW * NW;
-                for (int r = 0; r < NW; ++r) {
-                    yv -= M[r * NW + t] * ws.bb[(size_t)(k - 1) * NW + r];
-                    vv -= M[r * NW + t] * ws.g[(size_t)(k - 1) * NW + r];
+            if (j > i) continue;
+            double v0 = Dk[ij], v1 = 0.0;
+            if (k > 0)
+                for (int r = 0; r < NW; r += 2) {
+                    v0 = fma(-Mp[r * NW + i], Mp[r * NW + j], v0);
+                    v1 = fma(-Mp[(r + 1) * NW + i], Mp[(r + 1) * NW + j], v1);
                 }
-            }
-            s_red[8 + t] = yv;
-            s_red[8 + NW + t] = vv;
+            Ls[ij] = v0 + v1;
+        }
+        if (t >= 32 && t < 64) {   // warp 1: the right-hand sides (lanes 0-15 y, 16-31 v)
+            const int r = t & 15, which = (t - 32) >> 4;
+            const double *prev = (which ? ws.g : ws.bb) + (size_t)(k > 0 ? k - 1 : 0) * NW;
+            double v = which ? -ws.g[(size_t)k * NW + r] : ws.bb[(size_t)k * NW + r];
+            if (k > 0)
+                for (int q = 0; q < NW; ++q) v = fma(-Mp[q * NW + r], prev[q], v);
+            s_vec[which * NW + r] = v;
         }
         __syncthreads();
-        // Cholesky of L in place (lower), column by column
-        for (int p = 0; p < NW; ++p) {
-            if (t == 0) L[p * NW + p] = sqrt(L[p * NW + p]);
-            __syncthreads();
-            const double piv = L[p * NW + p];
-            if (t > p && t < NW) L[t * NW + p] /= piv;
-            __syncthreads();
-            for (int ij = t; ij < NW * NW; ij += blockDim.x) {
-                const int i = ij / NW, j = ij - i * NW;
-                if (i > p && j > p && j <= i) L[ij] -= L[i * NW + p] * L[j * NW + p];
-            }
-            __syncthreads();
-        }
-        // forward substitutions: the two vectors (threads 0, 1) and M_k = L^-1 E_k (columns)
-        if (k < N) {
-            const double *Ek = ws.E + (size_t)k * NW * NW;
-            double *Mk = ws.E + (size_t)k * NW * NW;
-            if (t < NW) {   // column t of E_k
-                double col[NW];
-                for (int r = 0; r < NW; ++r) col[r] = Ek[r * NW + t];
-                for (int r = 0; r < NW; ++r) {
-                    double v = col[r];
-                    for (int q = 0; q < r; ++q) v -= L[r * NW + q] * col[q];
-                    col[r] = v / L[r * NW + r];
+        if (t < 32) {   // warp 0: the factor
+            const int i = t & (NW - 1);
+            double a[NW], rin[NW];
+#pragma unroll
+            for (int j = 0; j < NW; ++j) a[j] = j <= i ? Ls[i * NW + j] : 0.0;
+#pragma unroll
+            for (int p = 0; p < NW; ++p) {
+                const double d = __shfl_sync(full, a[p], p);   // the pivot, from lane p
+                const double r = rsqrt_pivot(d);
+                rin[p] = r;
+                const double l = i > p ? a[p] * r : (i == p ? d * r : 0.0);   // L[i][p]
+                a[p] = l;
+#pragma unroll
+                for (int j = p + 1; j < NW; ++j) {
+                    const double lj = __shfl_sync(full, l, j);                // L[j][p]
+                    if (j <= i) a[j] = fma(-l, lj, a[j]);
                 }
-                __syncwarp(0xffffu);
-                for (int r = 0; r < NW; ++r) Mk[r * NW + t] = col[r];
+            }
+            if (t < NW) {
+#pragma unroll
+                for (int j = 0; j < NW; ++j) Ls[i * NW + j] = j < i ? a[j] : (j == i ? rin[i] : 0.0);
+            }
+            __syncwarp();
+            // M_k = L^-1 E_k (lanes 0-15, one column each) and the two vectors (lanes 16, 17)
+            const bool col = t < NW && k < N, vec = t == 16 || t == 17;
+            if (col || vec) {
+                const double *Ek = ws.E + (size_t)k * NW * NW;
+                double x[NW];
+#pragma unroll
+                for (int r = 0; r < NW; ++r) x[r] = col ? Ek[r * NW + t] : s_vec[(t - 16) * NW + r];
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    x[q] *= Ls[q * NW + q];
+#pragma unroll
+                    for (int r = q + 1; r < NW; ++r) x[r] = fma(-Ls[r * NW + q], x[q], x[r]);
+                }
+                double *dst = col ? ws.E + (size_t)k * NW * NW : (t == 16 ? ws.bb : ws.g) + (size_t)k * NW;
+#pragma unroll
+                for (int r = 0; r < NW; ++r) dst[col ? r * NW + t : r] = x[r];
             }
         }
-        if (t == 32 || t == 33) {
-            const double *src = s_red + 8 + (t == 32 ? 0 : NW);
-            double *dst = (t == 32 ? ws.bb : ws.g) + (size_t)k * NW;
-            double v[NW];
-            for (int r = 0; r < NW; ++r) {
-                double s = src[r];
-                for (int q = 0; q < r; ++q) s -= L[r * NW + q] * v[q];
-                v[r] = s / L[r * NW + r];
-            }
-            for (int r = 0; r < NW; ++r) dst[r] = v[r];
-        }
-        for (int ij = t; ij < NW * NW; ij += blockDim.x) Dk[ij] = L[ij];
         __syncthreads();
+        for (int ij = t; ij < NW * NW; ij += blockDim.x) Dk[ij] = Ls[ij];
     }
-    // back substitution: y_k = L_k^-T (y_k - M_k y_{k+1}), the same for v
+    __syncthreads();
+    // back substitution: y_k = L_k^-T (y_k - M_k y_{k+1}), the same for v (warp 0: lanes 0-15
+    // y, 16-31 v, one row each; L_k^T x = rhs solved from the last row up, column by column)
     for (int k = N; k >= 0; --k) {
-        if (t == 0 || t == 1) {
-            double *vec = (t == 0 ? ws.bb : ws.g) + (size_t)k * NW;
+        if (t < 32) {
+            const int r = t & (NW - 1), which = t >> 4;
+            double *vec = (which ? ws.g : ws.bb) + (size_t)k * NW;
             const double *Lk = ws.D + (size_t)k * NW * NW;
-            double v[NW];
-            for (int r = 0; r < NW; ++r) v[r] = vec[r];
+            double x = vec[r];
             if (k < N) {
                 const double *M = ws.E + (size_t)k * NW * NW;
-                const double *nxt = (t == 0 ? ws.bb : ws.g) + (size_t)(k + 1) * NW;
-                for (int r = 0; r < NW; ++r)
-                    for (int c = 0; c < NW; ++c) v[r] -= M[r * NW + c] * nxt[c];
+                const double *nxt = (which ? ws.g : ws.bb) + (size_t)(k + 1) * NW;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                for (int q = 0; q < NW; q += 4) {
+                    s0 = fma(M[r * NW + q], nxt[q], s0);
+                    s1 = fma(M[r * NW + q + 1], nxt[q + 1], s1);
+                    s2 = fma(M[r * NW + q + 2], nxt[q + 2], s2);
+                    s3 = fma(M[r * NW + q + 3], nxt[q + 3], s3);
+                }
+                x -= (s0 + s1) + (s2 + s3);
             }
-            for (int r = NW - 1; r >= 0; --r) {
-                double s = v[r];
-                for (int q = r + 1; q < NW; ++q) s -= Lk[q * NW + r] * v[q];
-                v[r] = s / Lk[r * NW + r];
+#pragma unroll
+            for (int rr = NW - 1; rr >= 0; --rr) {
+                const double lrr = Lk[rr * NW + rr];     // 1 / L_rr
+                const double lrq = Lk[rr * NW + r];      // L[rr][r] (r < rr)
+                const double xr = __shfl_sync(full, x * lrr, rr + NW * which);
+                if (r == rr) x = xr;
+                else if (r < rr) x = fma(-lrq, xr, x);
             }
-            for (int r = 0; r < NW; ++r) vec[r] = v[r];
+            __syncwarp();
+            vec[r] = x;
         }
         __syncthreads();
     }
