@@ -182,7 +182,7 @@ KERNEL_SOURCES = {
 PROFILED_TRAFFIC = {
     "k_eval_broad": {"sha1": "457bb6563f6b94b1372e94ddf7a49e9cbb97fa18", "bytes": 1104384.0,
                      "workload": "single_large"},
-    "k_eval_polar": {"sha1": "51a7865ac840a7f71b7e762bd4de651257b30453", "bytes": 33661440.0,
+    "k_eval_polar": {"sha1": "7a5def19126e736b95509050d8b2505429db5c16", "bytes": 33659904.0,
                      "workload": "dense_forest"},
 }
 
