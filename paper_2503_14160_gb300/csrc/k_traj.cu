@@ -37,7 +37,8 @@ struct NvtxScope {
 namespace cp {
 namespace {
 
-constexpr int kTrajThreads = 256;
+constexpr int kTrajThreads = 512;
+constexpr int kRedDoubles = 64;   // block reductions: [0, 32) and [32, 64) (one slot per warp)
 constexpr int NX = 12, NU = 4, NW = 16;
 constexpr double kGravity = 9.81;
 
@@ -129,6 +130,7 @@ struct TrajWs {
     double *E;     // [N][16][16] off-diagonal blocks, then L_k^-1 E_k
     double *bb;    // [N+1][16] border column, then the forward/back solves
     double *g;     // [N+1][16] gradient, then the forward/back solves
+    double *P;     // [N+1][16][16] L_k^-1 T[k][left neighbour] of the eliminated blocks
 };
 
 __device__ __forceinline__ TrajWs ws_of(double *base, int N)
@@ -140,6 +142,7 @@ __device__ __forceinline__ TrajWs ws_of(double *base, int N)
     w.E = w.D + (size_t)(N + 1) * NW * NW;
     w.bb = w.E + (size_t)N * NW * NW;
     w.g = w.bb + (size_t)(N + 1) * NW;
+    w.P = w.g + (size_t)(N + 1) * NW;
     return w;
 }
 
@@ -211,6 +214,98 @@ __device__ double merit(const TrajDev &td, const double *z, const double *lam, c
         }
     }
     return z[0] + block_sum(acc, s_red);
+}
+
+// Cholesky factor of a 16 x 16 SPD block on one warp (all 32 lanes call; lanes 0-15 hold a
+// row each in registers): the lower triangle of A in, F = the factor's strict lower triangle
+// with 1 / L_pp on its diagonal out (shared memory of the warp). Each pivot's reciprocal square
+// root comes from rsqrt_pivot; the column is scaled by it and the trailing rows updated from
+// shuffled entries, so a pivot costs one short chain of dependent FP64 operations.
+__device__ __noinline__ void warp_factor16(const double *A, double *F, int lane)
+{
+    const unsigned full = 0xffffffffu;
+    const int i = lane & (NW - 1);
+    double a[NW], rin[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) a[j] = j <= i ? A[i * NW + j] : 0.0;
+#pragma unroll
+    for (int p = 0; p < NW; ++p) {
+        const double d = __shfl_sync(full, a[p], p);   // the pivot, from lane p
+        const double r = rsqrt_pivot(d);
+        rin[p] = r;
+        const double l = i > p ? a[p] * r : (i == p ? d * r : 0.0);   // L[i][p]
+        a[p] = l;
+#pragma unroll
+        for (int j = p + 1; j < NW; ++j) {
+            const double lj = __shfl_sync(full, l, j);                // L[j][p]
+            if (j <= i) a[j] = fma(-l, lj, a[j]);
+        }
+    }
+    if (lane < NW) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) F[i * NW + j] = j < i ? a[j] : (j == i ? rin[i] : 0.0);
+    }
+    __syncwarp();
+}
+
+// dst <- L^-1 src for one right-hand side of this lane (entry rr at src[rr * ss], written to
+// dst[rr * ds]), L in the form of warp_factor16: column by column, a chain of two dependent
+// operations per column.
+__device__ __noinline__ void column_solve16(const double *F, const double *src, int ss, double *dst, int ds)
+{
+    double x[NW];
+#pragma unroll
+    for (int rr = 0; rr < NW; ++rr) x[rr] = src[rr * ss];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        x[q] *= F[q * NW + q];
+#pragma unroll
+        for (int r = q + 1; r < NW; ++r) x[r] = fma(-F[r * NW + q], x[q], x[r]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < NW; ++rr) dst[rr * ds] = x[rr];
+}
+
+// x_k = L_k^-T (w_k - P_k x_l - Q_k x_r) for both vectors (lanes 0-15 y, 16-31 v, one row
+// each; P or Q absent when null): the products, then L^T x = rhs from the last row up,
+// column by column with the solved entry shuffled to the rows above it.
+__device__ __noinline__ void warp_back16(const double *Lk, const double *P, const double *xl_y, const double *xl_v,
+                            const double *Q, const double *xr_y, const double *xr_v, double *out_y, double *out_v,
+                            int lane)
+{
+    const unsigned full = 0xffffffffu;
+    const int r = lane & (NW - 1), which = lane >> 4;
+    double *out = which ? out_v : out_y;
+    double x = out[r];   // w_k
+    if (P != nullptr) {
+        const double *xl = which ? xl_v : xl_y;
+        double s0 = 0.0, s1 = 0.0;
+        for (int c = 0; c < NW; c += 2) {
+            s0 = fma(P[r * NW + c], xl[c], s0);
+            s1 = fma(P[r * NW + c + 1], xl[c + 1], s1);
+        }
+        x -= s0 + s1;
+    }
+    if (Q != nullptr) {
+        const double *xr = which ? xr_v : xr_y;
+        double s0 = 0.0, s1 = 0.0;
+        for (int c = 0; c < NW; c += 2) {
+            s0 = fma(Q[r * NW + c], xr[c], s0);
+            s1 = fma(Q[r * NW + c + 1], xr[c + 1], s1);
+        }
+        x -= s0 + s1;
+    }
+#pragma unroll
+    for (int rr = NW - 1; rr >= 0; --rr) {
+        const double lrr = Lk[rr * NW + rr];     // 1 / L_rr
+        const double lrq = Lk[rr * NW + r];      // L[rr][r] (r < rr)
+        const double xr = __shfl_sync(full, x * lrr, rr + NW * which);
+        if (r == rr) x = xr;
+        else if (r < rr) x = fma(-lrq, xr, x);
+    }
+    __syncwarp();
+    out[r] = x;
+    __syncwarp();
 }
 
 // The damped Gauss-Newton step dz at z (T6): Jacobian, assembly, block factorisation, solve.
@@ -339,117 +434,109 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     gt = 1.0 + rho * block_sum(gt, s_red);
     cc += mu * (cc + 1e-9);
     __syncthreads();
-    // 3. block Cholesky of the tridiagonal part, forward substitution of the border column
-    //    (y) and the negated gradient (v): for k = 0..N
-    //      S_k = D_k - M_{k-1}^T M_{k-1};  L_k L_k^T = S_k;  M_k = L_k^-1 E_k;
-    //      y_k = L_k^-1 (b_k - M_{k-1}^T y_{k-1});  v_k = L_k^-1 (-g_k - M_{k-1}^T v_{k-1}).
-    //    The chain of the sweep is long dependent FP64 work, so every step keeps it short: the
-    //    16 x 16 factor runs on one warp in registers (lane i holds row i; the pivot's
-    //    reciprocal square root by rsqrt_pivot, the column scaled by it, the trailing rows
-    //    updated from shuffled column entries), and the triangular solves go column by
-    //    column with one lane per right-hand side. The stored factor keeps 1 / L_pp on its
-    //    diagonal for the back substitution.
-    double *Ls = s_blk;           // the current block: S_k, then its factor
-    double *s_vec = s_red + 8;    // [2][NW] right-hand sides of y_k and v_k
-    const unsigned full = 0xffffffffu;
-    for (int k = 0; k <= N; ++k) {
-        double *Dk = ws.D + (size_t)k * NW * NW;
-        const double *Mp = ws.E + (size_t)(k > 0 ? k - 1 : 0) * NW * NW;   // M_{k-1}
-        for (int ij = t; ij < NW * NW; ij += blockDim.x) {
-            const int i = ij / NW, j = ij - i * NW;
-            if (j > i) continue;
-            double v0 = Dk[ij], v1 = 0.0;
-            if (k > 0)
-                for (int r = 0; r < NW; r += 2) {
-                    v0 = fma(-Mp[r * NW + i], Mp[r * NW + j], v0);
-                    v1 = fma(-Mp[(r + 1) * NW + i], Mp[(r + 1) * NW + j], v1);
-                }
-            Ls[ij] = v0 + v1;
-        }
-        if (t >= 32 && t < 64) {   // warp 1: the right-hand sides (lanes 0-15 y, 16-31 v)
-            const int r = t & 15, which = (t - 32) >> 4;
-            const double *prev = (which ? ws.g : ws.bb) + (size_t)(k > 0 ? k - 1 : 0) * NW;
-            double v = which ? -ws.g[(size_t)k * NW + r] : ws.bb[(size_t)k * NW + r];
-            if (k > 0)
-                for (int q = 0; q < NW; ++q) v = fma(-Mp[q * NW + r], prev[q], v);
-            s_vec[which * NW + r] = v;
+    // 3. the tridiagonal part T (diagonal blocks D_k, couplings T[k][k+1] = E_k) solved for the
+    //    two right-hand sides b (into y, ws.bb) and -g (into v, ws.g) by block cyclic reduction.
+    //    Level s = 1, 2, 4, ... eliminates the blocks k = s, 3s, 5s, ... <= N, each between
+    //    l = k - s and r = k + s (when r <= N), one warp per block:
+    //      L L^T = D_k,  P = L^-1 T[k][l],  Q = L^-1 T[k][r],  w = L^-1 f_k,
+    //    then the kept blocks j = 0, 2s, 4s, ... take D_j -= Q_(j-s)^T Q_(j-s) + P_(j+s)^T P_(j+s),
+    //    f_j -= Q_(j-s)^T w_(j-s) + P_(j+s)^T w_(j+s) and the coupling T'[j][j+2s] = -P^T Q of
+    //    block j + s. Block 0 is left and solved; the eliminated blocks then follow level by
+    //    level from the last: x_k = L^-T (w - P x_l - Q x_r). The couplings are kept in ws.E
+    //    under their left block (E_l becomes the new coupling; E_k then holds Q), P in ws.P,
+    //    the factors (1 / L_pp on the diagonal) in ws.D, w and x in ws.bb / ws.g. Each level's
+    //    blocks are independent, so the chain of dependent FP64 steps is that of about
+    //    log2(N + 1) block factors instead of N + 1.
+    const int warp = t >> 5, lane = t & 31, n_warps = (int)(blockDim.x >> 5);
+    double *Fw = s_blk + (size_t)warp * NW * NW;
+    for (int e = t; e < (N + 1) * NW; e += blockDim.x) ws.g[e] = -ws.g[e];
+    __syncthreads();
+    int s_top = 1;
+    for (int s = 1; s <= N; s <<= 1) {
+        s_top = s;
+        const int n_odd = (N / s + 1) / 2;
+        for (int m = warp; m < n_odd; m += n_warps) {   // phase A
+            const int k = (2 * m + 1) * s, l = k - s, r = k + s;
+            const bool has_r = r <= N;
+            warp_factor16(ws.D + (size_t)k * NW * NW, Fw, lane);
+            const int c = lane & (NW - 1);
+            const bool do_p = lane < NW, do_q = lane >= NW && has_r;
+            if (do_p)   // column c of T[k][l] = row c of the coupling E_l
+                column_solve16(Fw, ws.E + (size_t)l * NW * NW + c * NW, 1, ws.P + (size_t)k * NW * NW + c, NW);
+            if (do_q)   // column c of T[k][r] = E_k, solved in place
+                column_solve16(Fw, ws.E + (size_t)k * NW * NW + c, NW, ws.E + (size_t)k * NW * NW + c, NW);
+            if (lane < 2) {
+                double *f = (lane ? ws.g : ws.bb) + (size_t)k * NW;
+                column_solve16(Fw, f, 1, f, 1);
+            }
+            for (int ij = lane; ij < NW * NW; ij += 32) ws.D[(size_t)k * NW * NW + ij] = Fw[ij];
+            __syncwarp();
         }
         __syncthreads();
-        if (t < 32) {   // warp 0: the factor
-            const int i = t & (NW - 1);
-            double a[NW], rin[NW];
-#pragma unroll
-            for (int j = 0; j < NW; ++j) a[j] = j <= i ? Ls[i * NW + j] : 0.0;
-#pragma unroll
-            for (int p = 0; p < NW; ++p) {
-                const double d = __shfl_sync(full, a[p], p);   // the pivot, from lane p
-                const double r = rsqrt_pivot(d);
-                rin[p] = r;
-                const double l = i > p ? a[p] * r : (i == p ? d * r : 0.0);   // L[i][p]
-                a[p] = l;
-#pragma unroll
-                for (int j = p + 1; j < NW; ++j) {
-                    const double lj = __shfl_sync(full, l, j);                // L[j][p]
-                    if (j <= i) a[j] = fma(-l, lj, a[j]);
-                }
+        const int n_even = N / (2 * s) + 1;
+        for (int m = warp; m < n_even; m += n_warps) {   // phase B
+            const int j = 2 * m * s, iL = j - s, iR = j + s;
+            const bool hasL = m > 0, hasR = iR <= N;
+            const double *QL = ws.E + (size_t)(hasL ? iL : 0) * NW * NW;
+            const double *PR = ws.P + (size_t)(hasR ? iR : 0) * NW * NW;
+            for (int e = lane; e < NW * NW; e += 32) {
+                const int a = e >> 4, b = e & (NW - 1);
+                if (b > a) continue;
+                double v0 = ws.D[(size_t)j * NW * NW + e], v1 = 0.0;
+                if (hasL)
+                    for (int q = 0; q < NW; ++q) v0 = fma(-QL[q * NW + a], QL[q * NW + b], v0);
+                if (hasR)
+                    for (int q = 0; q < NW; ++q) v1 = fma(-PR[q * NW + a], PR[q * NW + b], v1);
+                ws.D[(size_t)j * NW * NW + e] = v0 + v1;
             }
-            if (t < NW) {
-#pragma unroll
-                for (int j = 0; j < NW; ++j) Ls[i * NW + j] = j < i ? a[j] : (j == i ? rin[i] : 0.0);
+            {
+                const int a = lane & (NW - 1), which = lane >> 4;
+                double *f = which ? ws.g : ws.bb;
+                double v = f[(size_t)j * NW + a];
+                if (hasL) {
+                    const double *w = f + (size_t)iL * NW;
+                    for (int q = 0; q < NW; ++q) v = fma(-QL[q * NW + a], w[q], v);
+                }
+                if (hasR) {
+                    const double *w = f + (size_t)iR * NW;
+                    for (int q = 0; q < NW; ++q) v = fma(-PR[q * NW + a], w[q], v);
+                }
+                f[(size_t)j * NW + a] = v;
+            }
+            if (hasR && iR + s <= N) {
+                const double *QR = ws.E + (size_t)iR * NW * NW;
+                for (int e = lane; e < NW * NW; e += 32) {
+                    const int a = e >> 4, b = e & (NW - 1);
+                    double v = 0.0;
+                    for (int q = 0; q < NW; ++q) v = fma(PR[q * NW + a], QR[q * NW + b], v);
+                    ws.E[(size_t)j * NW * NW + e] = -v;
+                }
             }
             __syncwarp();
-            // M_k = L^-1 E_k (lanes 0-15, one column each) and the two vectors (lanes 16, 17)
-            const bool col = t < NW && k < N, vec = t == 16 || t == 17;
-            if (col || vec) {
-                const double *Ek = ws.E + (size_t)k * NW * NW;
-                double x[NW];
-#pragma unroll
-                for (int r = 0; r < NW; ++r) x[r] = col ? Ek[r * NW + t] : s_vec[(t - 16) * NW + r];
-#pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    x[q] *= Ls[q * NW + q];
-#pragma unroll
-                    for (int r = q + 1; r < NW; ++r) x[r] = fma(-Ls[r * NW + q], x[q], x[r]);
-                }
-                double *dst = col ? ws.E + (size_t)k * NW * NW : (t == 16 ? ws.bb : ws.g) + (size_t)k * NW;
-#pragma unroll
-                for (int r = 0; r < NW; ++r) dst[col ? r * NW + t : r] = x[r];
-            }
         }
         __syncthreads();
-        for (int ij = t; ij < NW * NW; ij += blockDim.x) Dk[ij] = Ls[ij];
+    }
+    // block 0: D_0 x_0 = f_0
+    if (warp == 0) {
+        warp_factor16(ws.D, Fw, lane);
+        if (lane < 2) {
+            double *f = lane ? ws.g : ws.bb;
+            column_solve16(Fw, f, 1, f, 1);
+        }
+        __syncwarp();
+        warp_back16(Fw, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, ws.bb, ws.g, lane);
     }
     __syncthreads();
-    // back substitution: y_k = L_k^-T (y_k - M_k y_{k+1}), the same for v (warp 0: lanes 0-15
-    // y, 16-31 v, one row each; L_k^T x = rhs solved from the last row up, column by column)
-    for (int k = N; k >= 0; --k) {
-        if (t < 32) {
-            const int r = t & (NW - 1), which = t >> 4;
-            double *vec = (which ? ws.g : ws.bb) + (size_t)k * NW;
-            const double *Lk = ws.D + (size_t)k * NW * NW;
-            double x = vec[r];
-            if (k < N) {
-                const double *M = ws.E + (size_t)k * NW * NW;
-                const double *nxt = (which ? ws.g : ws.bb) + (size_t)(k + 1) * NW;
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                for (int q = 0; q < NW; q += 4) {
-                    s0 = fma(M[r * NW + q], nxt[q], s0);
-                    s1 = fma(M[r * NW + q + 1], nxt[q + 1], s1);
-                    s2 = fma(M[r * NW + q + 2], nxt[q + 2], s2);
-                    s3 = fma(M[r * NW + q + 3], nxt[q + 3], s3);
-                }
-                x -= (s0 + s1) + (s2 + s3);
-            }
-#pragma unroll
-            for (int rr = NW - 1; rr >= 0; --rr) {
-                const double lrr = Lk[rr * NW + rr];     // 1 / L_rr
-                const double lrq = Lk[rr * NW + r];      // L[rr][r] (r < rr)
-                const double xr = __shfl_sync(full, x * lrr, rr + NW * which);
-                if (r == rr) x = xr;
-                else if (r < rr) x = fma(-lrq, xr, x);
-            }
-            __syncwarp();
-            vec[r] = x;
+    // the eliminated blocks, from the last level to the first
+    for (int s = s_top; s >= 1; s >>= 1) {
+        const int n_odd = (N / s + 1) / 2;
+        for (int m = warp; m < n_odd; m += n_warps) {
+            const int k = (2 * m + 1) * s, l = k - s, r = k + s;
+            const bool has_r = r <= N;
+            warp_back16(ws.D + (size_t)k * NW * NW, ws.P + (size_t)k * NW * NW, ws.bb + (size_t)l * NW,
+                        ws.g + (size_t)l * NW, has_r ? ws.E + (size_t)k * NW * NW : nullptr,
+                        has_r ? ws.bb + (size_t)r * NW : nullptr, has_r ? ws.g + (size_t)r * NW : nullptr,
+                        ws.bb + (size_t)k * NW, ws.g + (size_t)k * NW, lane);
         }
         __syncthreads();
     }
@@ -486,9 +573,9 @@ k_traj_step(const TrajDev td, const double *q_star, const double *z, const doubl
     extern __shared__ double s_mem[];
     const int N = td.N, n_var = 1 + NW * (N + 1), n_eq = NX * (N + 2);
     const int p = blockIdx.x;
-    double *s_red = s_mem;                  // 8 + 2 NW
-    double *s_blk = s_red + 8 + 2 * NW;     // NW * NW
-    double *x_S = s_blk + NW * NW, *x_T = x_S + NX;
+    double *s_red = s_mem;                                      // kRedDoubles
+    double *s_blk = s_red + kRedDoubles;                        // per warp NW * NW
+    double *x_S = s_blk + (kTrajThreads / 32) * NW * NW, *x_T = x_S + NX;
     const double *qs = q_star + (size_t)p * (N + 1) * 4;
     for (int i = threadIdx.x; i < NX; i += blockDim.x) {
         x_S[i] = i < 4 ? qs[i] : 0.0;
@@ -510,8 +597,8 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
     const int N = td.N, n_var = 1 + NW * (N + 1), n_eq = NX * (N + 2);
     const int p = blockIdx.x, t = threadIdx.x;
     double *s_red = s_mem;
-    double *s_blk = s_red + 8 + 2 * NW;
-    double *x_S = s_blk + NW * NW, *x_T = x_S + NX;
+    double *s_blk = s_red + kRedDoubles;
+    double *x_S = s_blk + (kTrajThreads / 32) * NW * NW, *x_T = x_S + NX;
     double *z = x_T + NX;          // n_var
     double *zn = z + n_var;        // n_var
     double *dz = zn + n_var;       // n_var
@@ -590,14 +677,14 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
     __syncthreads();
     if ((t & 31) == 0) {
         s_red[t >> 5] = cmax;
-        s_red[8 + (t >> 5)] = vmax;
+        s_red[32 + (t >> 5)] = vmax;
     }
     __syncthreads();
     if (t == 0) {
         double c = 0.0, v = 0.0;
         for (int i = 0; i < kTrajThreads / 32; ++i) {
             c = fmax(c, s_red[i]);
-            v = fmax(v, s_red[8 + i]);
+            v = fmax(v, s_red[32 + i]);
         }
         stats[(size_t)p * 4 + 2] = c;
         stats[(size_t)p * 4 + 3] = fmax(v, 0.0);
@@ -681,12 +768,12 @@ namespace {
 
 size_t traj_ws_doubles(int N)
 {
-    return (size_t)(N + 1) * (NX + NX * NW + NW * NW + 2 * NW) + (size_t)N * NW * NW;
+    return (size_t)(N + 1) * (NX + NX * NW + 2 * NW * NW + 2 * NW) + (size_t)N * NW * NW;
 }
 
 size_t traj_smem(int N, bool solve)
 {
-    const size_t base = 8 + 2 * NW + NW * NW + 2 * NX;
+    const size_t base = kRedDoubles + (size_t)(kTrajThreads / 32) * NW * NW + 2 * NX;
     return sizeof(double) * (base + (solve ? 3 * (size_t)(1 + NW * (N + 1)) : 0));
 }
 
