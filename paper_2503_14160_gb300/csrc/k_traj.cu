@@ -39,6 +39,7 @@ namespace {
 
 constexpr int kTrajThreads = 512;
 constexpr int kRedDoubles = 64;   // block reductions: [0, 32) and [32, 64) (one slot per warp)
+constexpr int kWarpScratch = 2 * 12 * 16;   // doubles of shared memory per warp (block factor, F_k pair)
 constexpr int NX = 12, NU = 4, NW = 16;
 constexpr double kGravity = 9.81;
 
@@ -62,6 +63,37 @@ __device__ __forceinline__ double dcos(double a) { return cos(a); }
 template <typename T> __device__ __forceinline__ T lift(double v);
 template <> __device__ __forceinline__ double lift<double>(double v) { return v; }
 template <> __device__ __forceinline__ Dual lift<Dual>(double v) { return {v, 0.0}; }
+
+// Cosine and sine of an angle of the dynamics. The primal values depend on the grid point
+// only, so a cache (c, s pairs written by the value pass at that point) serves the 16
+// derivative passes; without one (or for plain doubles) they are computed here.
+__device__ __forceinline__ void trig_of(double a, const double *cache, double *cw, int idx, double &c, double &s)
+{
+    if (cache != nullptr) {
+        c = cache[2 * idx];
+        s = cache[2 * idx + 1];
+        return;
+    }
+    sincos(a, &s, &c);
+    if (cw != nullptr) {
+        cw[2 * idx] = c;
+        cw[2 * idx + 1] = s;
+    }
+}
+
+__device__ __forceinline__ void trig_of(Dual a, const double *cache, double *cw, int idx, Dual &c, Dual &s)
+{
+    double cv, sv;
+    if (cache != nullptr) {
+        cv = cache[2 * idx];
+        sv = cache[2 * idx + 1];
+    } else {
+        sincos(a.v, &sv, &cv);
+    }
+    (void)cw;
+    c = {cv, -sv * a.d};
+    s = {sv, cv * a.d};
+}
 
 // 1 / sqrt(a) in FP64 for the pivots of the block factorisation: an FP32 seed and two
 // Newton steps (quadratic convergence: about 22 -> 44 -> 88 bits), a short dependent chain
@@ -90,15 +122,20 @@ struct TrajDev {
 // the tip acceleration T'' (cylindrical coordinates of the tip) by
 //   (ddalpha, ddbeta) = -(r_a . v / l, r_b . v / (l cos^2 alpha)),  v = T'' + l w + g z,
 //   r = (sin a, cos a sin b, -cos a cos b),  w = r_aa da^2 + 2 r_ab da db + r_bb db^2.
+// cache: the cosines and sines of this grid point (A, B, q1, alpha, beta) when known; cw: where
+// the value pass stores them (either may be null).
 template <typename T>
-__device__ void traj_f(const TrajDev &td, const T *x, const T *u, T *out)
+__device__ void traj_f(const TrajDev &td, const T *x, const T *u, T *out, const double *cache = nullptr,
+                       double *cw = nullptr)
 {
     const T q1 = x[0], q2 = x[1], q3 = x[2], q4 = x[3], a = x[4], b = x[5];
     const T d1 = x[6], d2 = x[7], d3 = x[8], d4 = x[9], da = x[10], db = x[11];
     const T u1 = u[0], u2 = u[1], u3 = u[2], u4 = u[3];
     const T lam = lift<T>(td.jib_len) + q4;
     const T A = q2, B = q2 + q3, dB = d2 + d3, ddB = u2 + u3;
-    const T cA = dcos(A), sA = dsin(A), cB = dcos(B), sB = dsin(B);
+    T cA, sA, cB, sB;
+    trig_of(A, cache, cw, 0, cA, sA);
+    trig_of(B, cache, cw, 1, cB, sB);
     const T h = td.boom_len * cA + lam * cB;
     const T dh = lift<T>(0.0) - td.boom_len * sA * d2 + d4 * cB - lam * sB * dB;
     const T ddh = lift<T>(0.0) - td.boom_len * (cA * d2 * d2 + sA * u2) + u4 * cB - 2.0 * d4 * sB * dB -
@@ -106,9 +143,12 @@ __device__ void traj_f(const TrajDev &td, const T *x, const T *u, T *out)
     const T ddz = td.boom_len * (cA * u2 - sA * d2 * d2) + u4 * sB + 2.0 * d4 * cB * dB +
                   lam * (cB * ddB - sB * dB * dB);
     const T a_r = ddh - h * d1 * d1, a_t = h * u1 + 2.0 * dh * d1;
-    const T c1 = dcos(q1), s1 = dsin(q1);
+    T c1, s1;
+    trig_of(q1, cache, cw, 2, c1, s1);
     const T ax = a_r * c1 - a_t * s1, ay = a_r * s1 + a_t * c1;
-    const T ca = dcos(a), sa = dsin(a), cb = dcos(b), sb = dsin(b);
+    T ca, sa, cb, sb;
+    trig_of(a, cache, cw, 3, ca, sa);
+    trig_of(b, cache, cw, 4, cb, sb);
     // w = r_aa da^2 + 2 r_ab da db + r_bb db^2
     const T wx = lift<T>(0.0) - sa * da * da;
     const T wy = lift<T>(0.0) - ca * sb * da * da - 2.0 * sa * cb * da * db - ca * sb * db * db;
@@ -131,6 +171,7 @@ struct TrajWs {
     double *bb;    // [N+1][16] border column, then the forward/back solves
     double *g;     // [N+1][16] gradient, then the forward/back solves
     double *P;     // [N+1][16][16] L_k^-1 T[k][left neighbour] of the eliminated blocks
+    double *trig;  // [N+1][10] cosines and sines of the dynamics at the grid points of z
 };
 
 __device__ __forceinline__ TrajWs ws_of(double *base, int N)
@@ -143,6 +184,7 @@ __device__ __forceinline__ TrajWs ws_of(double *base, int N)
     w.bb = w.E + (size_t)N * NW * NW;
     w.g = w.bb + (size_t)(N + 1) * NW;
     w.P = w.g + (size_t)(N + 1) * NW;
+    w.trig = w.P + (size_t)(N + 1) * NW * NW;
     return w;
 }
 
@@ -166,11 +208,12 @@ __device__ double block_sum(double v, double *s_red)
 }
 
 // f at every grid point of z (values only) into ws.f.
-__device__ void eval_f(const TrajDev &td, const double *z, double *f)
+// trig (optional): the cosines and sines of every grid point are stored there too.
+__device__ void eval_f(const TrajDev &td, const double *z, double *f, double *trig = nullptr)
 {
     for (int k = threadIdx.x; k <= td.N; k += blockDim.x) {
         const double *w = z + 1 + (size_t)k * NW;
-        traj_f<double>(td, w, w + NX, f + (size_t)k * NX);
+        traj_f<double>(td, w, w + NX, f + (size_t)k * NX, nullptr, trig != nullptr ? trig + (size_t)k * 10 : nullptr);
     }
 }
 
@@ -316,14 +359,15 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     const int N = td.N, t = threadIdx.x;
     const double h = z[0] / N, rho = td.rho;
     // 1. f and df/dw at every grid point (16 forward-mode passes each)
-    eval_f(td, z, ws.f);
+    eval_f(td, z, ws.f, ws.trig);
+    __syncthreads();
     for (int e = t; e < (N + 1) * NW; e += blockDim.x) {
         const int k = e / NW, j = e - k * NW;
         const double *w = z + 1 + (size_t)k * NW;
         Dual x[NX], u[NU], out[NX];
         for (int i = 0; i < NX; ++i) x[i] = {w[i], i == j ? 1.0 : 0.0};
         for (int i = 0; i < NU; ++i) u[i] = {w[NX + i], NX + i == j ? 1.0 : 0.0};
-        traj_f<Dual>(td, x, u, out);
+        traj_f<Dual>(td, x, u, out, ws.trig + (size_t)k * 10);
         for (int i = 0; i < NX; ++i) ws.Fj[((size_t)k * NX + i) * NW + j] = out[i].d;
     }
     __syncthreads();
@@ -349,48 +393,62 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     // (interior points take both, whose first-order terms cancel) and
     //   A_k^T B_k = -(I'^T I' - c I'^T F_{k+1} + c F_k^T I' - c^2 F_k^T F_{k+1}).
     const double c = 0.5 * h;
-    auto Fjv = [&](int k, int r, int i) -> double { return ws.Fj[((size_t)k * NX + r) * NW + i]; };
-    for (int e = t; e < (N + 1) * NW * NW; e += blockDim.x) {
-        const int k = e / (NW * NW), ij = e - k * NW * NW, i = ij / NW, j = ij - i * NW;
-        if (j > i) continue;   // the factorisation reads the lower triangle only
-        double f0 = 0.0, f1 = 0.0;
-        for (int r = 0; r < NX; r += 2) {
-            f0 = fma(Fjv(k, r, i), Fjv(k, r, j), f0);
-            f1 = fma(Fjv(k, r + 1, i), Fjv(k, r + 1, j), f1);
-        }
-        const double ff = f0 + f1;
-        const double cross = (i < NX ? Fjv(k, i, j) : 0.0) + (j < NX ? Fjv(k, j, i) : 0.0);
-        const double id = (i == j && i < NX) ? 1.0 : 0.0;
-        double v;
-        if (k == 0) v = id + c * cross + c * c * ff;
-        else if (k == N) v = id - c * cross + c * c * ff;
-        else v = 2.0 * id + 2.0 * c * c * ff;
-        v *= rho;
-        if (i == j) {
-            if ((k == 0 || k == N) && i < NX) v += rho;                      // end states
-            if (i < NX) {
-                const double x = z[1 + (size_t)k * NW + i];
-                if (x > td.x_max[i] || x < td.x_min[i]) v += td.rho_b;        // active bound
-                if (i < 4 && k >= 1) v += 2.0 * td.omega_t;                   // tracking
-            } else if (k >= 1) {
-                v += 2.0 * td.omega_s * td.R[i - NX];                         // effort
+    // one warp per grid point k: F_k and F_{k+1} staged in the warp's shared memory, then the
+    // 136 lower entries of D_k and the 256 of E_k
+    {
+        const int warp = t >> 5, lane = t & 31, n_warps = (int)(blockDim.x >> 5);
+        double *sF = s_blk + (size_t)warp * kWarpScratch;   // [2][NX][NW]: F_k, F_{k+1}
+        const double *F0 = sF, *F1 = sF + NX * NW;
+        for (int k = warp; k <= N; k += n_warps) {
+            __syncwarp();
+            for (int q = lane; q < 2 * NX * NW; q += 32)
+                sF[q] = (q < NX * NW || k < N) ? ws.Fj[(size_t)k * NX * NW + q] : 0.0;
+            __syncwarp();
+            for (int e = lane; e < NW * (NW + 1) / 2; e += 32) {
+                int i, j;
+                tri_index(e, i, j);
+                double f0 = 0.0, f1 = 0.0;
+                for (int r = 0; r < NX; r += 2) {
+                    f0 = fma(F0[r * NW + i], F0[r * NW + j], f0);
+                    f1 = fma(F0[(r + 1) * NW + i], F0[(r + 1) * NW + j], f1);
+                }
+                const double ff = f0 + f1;
+                const double cross = (i < NX ? F0[i * NW + j] : 0.0) + (j < NX ? F0[j * NW + i] : 0.0);
+                const double id = (i == j && i < NX) ? 1.0 : 0.0;
+                double v;
+                if (k == 0) v = id + c * cross + c * c * ff;
+                else if (k == N) v = id - c * cross + c * c * ff;
+                else v = 2.0 * id + 2.0 * c * c * ff;
+                v *= rho;
+                if (i == j) {
+                    if ((k == 0 || k == N) && i < NX) v += rho;                      // end states
+                    if (i < NX) {
+                        const double x = z[1 + (size_t)k * NW + i];
+                        if (x > td.x_max[i] || x < td.x_min[i]) v += td.rho_b;        // active bound
+                        if (i < 4 && k >= 1) v += 2.0 * td.omega_t;                   // tracking
+                    } else if (k >= 1) {
+                        v += 2.0 * td.omega_s * td.R[i - NX];                         // effort
+                    }
+                    v += mu * (v + 1e-9);                                             // damping
+                }
+                ws.D[(size_t)k * NW * NW + i * NW + j] = v;
             }
-            v += mu * (v + 1e-9);                                             // damping
+            if (k < N)
+                for (int e = lane; e < NW * NW; e += 32) {
+                    const int i = e >> 4, j = e & (NW - 1);
+                    double p0 = 0.0, p1 = 0.0;
+                    for (int r = 0; r < NX; r += 2) {
+                        p0 = fma(F0[r * NW + i], F1[r * NW + j], p0);
+                        p1 = fma(F0[(r + 1) * NW + i], F1[(r + 1) * NW + j], p1);
+                    }
+                    const double id = (i == j && i < NX) ? 1.0 : 0.0;
+                    const double v = id - c * (i < NX ? F1[i * NW + j] : 0.0) + c * (j < NX ? F0[j * NW + i] : 0.0) -
+                                     c * c * (p0 + p1);
+                    ws.E[(size_t)k * NW * NW + e] = -rho * v;
+                }
         }
-        ws.D[e] = v;
     }
-    for (int e = t; e < N * NW * NW; e += blockDim.x) {
-        const int k = e / (NW * NW), ij = e - k * NW * NW, i = ij / NW, j = ij - i * NW;
-        double p0 = 0.0, p1 = 0.0;
-        for (int r = 0; r < NX; r += 2) {
-            p0 = fma(Fjv(k, r, i), Fjv(k + 1, r, j), p0);
-            p1 = fma(Fjv(k, r + 1, i), Fjv(k + 1, r + 1, j), p1);
-        }
-        const double id = (i == j && i < NX) ? 1.0 : 0.0;
-        const double v = id - c * (i < NX ? Fjv(k + 1, i, j) : 0.0) + c * (j < NX ? Fjv(k, j, i) : 0.0) -
-                         c * c * (p0 + p1);
-        ws.E[e] = -rho * v;
-    }
+    __syncthreads();
     // border column, gradient
     for (int e = t; e < (N + 1) * NW; e += blockDim.x) {
         const int k = e / NW, i = e - k * NW;
@@ -448,7 +506,7 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     //    blocks are independent, so the chain of dependent FP64 steps is that of about
     //    log2(N + 1) block factors instead of N + 1.
     const int warp = t >> 5, lane = t & 31, n_warps = (int)(blockDim.x >> 5);
-    double *Fw = s_blk + (size_t)warp * NW * NW;
+    double *Fw = s_blk + (size_t)warp * kWarpScratch;
     for (int e = t; e < (N + 1) * NW; e += blockDim.x) ws.g[e] = -ws.g[e];
     __syncthreads();
     int s_top = 1;
@@ -574,8 +632,8 @@ k_traj_step(const TrajDev td, const double *q_star, const double *z, const doubl
     const int N = td.N, n_var = 1 + NW * (N + 1), n_eq = NX * (N + 2);
     const int p = blockIdx.x;
     double *s_red = s_mem;                                      // kRedDoubles
-    double *s_blk = s_red + kRedDoubles;                        // per warp NW * NW
-    double *x_S = s_blk + (kTrajThreads / 32) * NW * NW, *x_T = x_S + NX;
+    double *s_blk = s_red + kRedDoubles;                        // per warp kWarpScratch
+    double *x_S = s_blk + (kTrajThreads / 32) * kWarpScratch, *x_T = x_S + NX;
     const double *qs = q_star + (size_t)p * (N + 1) * 4;
     for (int i = threadIdx.x; i < NX; i += blockDim.x) {
         x_S[i] = i < 4 ? qs[i] : 0.0;
@@ -598,7 +656,7 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
     const int p = blockIdx.x, t = threadIdx.x;
     double *s_red = s_mem;
     double *s_blk = s_red + kRedDoubles;
-    double *x_S = s_blk + (kTrajThreads / 32) * NW * NW, *x_T = x_S + NX;
+    double *x_S = s_blk + (kTrajThreads / 32) * kWarpScratch, *x_T = x_S + NX;
     double *z = x_T + NX;          // n_var
     double *zn = z + n_var;        // n_var
     double *dz = zn + n_var;       // n_var
@@ -768,12 +826,12 @@ namespace {
 
 size_t traj_ws_doubles(int N)
 {
-    return (size_t)(N + 1) * (NX + NX * NW + 2 * NW * NW + 2 * NW) + (size_t)N * NW * NW;
+    return (size_t)(N + 1) * (NX + NX * NW + 2 * NW * NW + 2 * NW + 10) + (size_t)N * NW * NW;
 }
 
 size_t traj_smem(int N, bool solve)
 {
-    const size_t base = kRedDoubles + (size_t)(kTrajThreads / 32) * NW * NW + 2 * NX;
+    const size_t base = kRedDoubles + (size_t)(kTrajThreads / 32) * kWarpScratch + 2 * NX;
     return sizeof(double) * (base + (solve ? 3 * (size_t)(1 + NW * (N + 1)) : 0));
 }
 
@@ -838,6 +896,8 @@ int cp_traj_init(const cp_model *model, const cp_traj_params *tp, int32_t max_pa
     e = cudaMemcpyAsync(t->dq_max, tp->dq_max, sizeof(double) * 4, cudaMemcpyHostToDevice, t->st);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_traj_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)traj_smem(tp->N, true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_traj_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)traj_smem(tp->N, false));
     if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
     if (e != cudaSuccess) {
         cudaFree(t->ws);
