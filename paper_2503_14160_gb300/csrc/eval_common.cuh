@@ -136,14 +136,22 @@ static __device__ __forceinline__ void crane_fk(const ModelDev &m, float4 q, flo
     }
 }
 
+// w.x p0 + w.y p1 + w.z p2 + w.w p3 per component, innermost product first; the (x, y) and
+// (z, w) components go through the packed FP32x2 FMA, each lane of which is the IEEE fmaf of
+// the same operands, so the result equals four scalar chains bit for bit.
 static __device__ __forceinline__ float4 combine4(float4 w, float4 p0, float4 p1, float4 p2, float4 p3)
 {
-    float4 r;
-    r.x = fmaf(w.x, p0.x, fmaf(w.y, p1.x, fmaf(w.z, p2.x, w.w * p3.x)));
-    r.y = fmaf(w.x, p0.y, fmaf(w.y, p1.y, fmaf(w.z, p2.y, w.w * p3.y)));
-    r.z = fmaf(w.x, p0.z, fmaf(w.y, p1.z, fmaf(w.z, p2.z, w.w * p3.z)));
-    r.w = fmaf(w.x, p0.w, fmaf(w.y, p1.w, fmaf(w.z, p2.w, w.w * p3.w)));
-    return r;
+    const float2 wx = make_float2(w.x, w.x), wy = make_float2(w.y, w.y);
+    const float2 wz = make_float2(w.z, w.z), ww = make_float2(w.w, w.w);
+    float2 a = __fmul2_rn(ww, make_float2(p3.x, p3.y));
+    float2 b = __fmul2_rn(ww, make_float2(p3.z, p3.w));
+    a = __ffma2_rn(wz, make_float2(p2.x, p2.y), a);
+    b = __ffma2_rn(wz, make_float2(p2.z, p2.w), b);
+    a = __ffma2_rn(wy, make_float2(p1.x, p1.y), a);
+    b = __ffma2_rn(wy, make_float2(p1.z, p1.w), b);
+    a = __ffma2_rn(wx, make_float2(p0.x, p0.y), a);
+    b = __ffma2_rn(wx, make_float2(p0.z, p0.w), b);
+    return make_float4(a.x, a.y, b.x, b.y);
 }
 
 static __device__ __forceinline__ float limit_excess(float v, float lo, float hi)
