@@ -282,6 +282,13 @@ ModelDev make_model(const cp_model *m)
     d.r_max = r_max;
     d.boom_len = (float)m->boom_len;
     d.jib_len = (float)m->jib_len;
+    for (int q = 0; q < kMaxSpheres / 2; ++q) {
+        const SphereLin &a = d.sph[2 * q], &b = d.sph[2 * q + 1];
+        d.pk_alpha[q] = make_float2(a.alpha, b.alpha);
+        d.pk_beta[q] = make_float2(a.beta, b.beta);
+        d.pk_gamma[q] = make_float2(a.gamma, b.gamma);
+        d.pk_ndelta[q] = make_float2(-a.delta, -b.delta);
+    }
     return d;
 }
 

@@ -81,6 +81,10 @@ struct ModelDev {
     float r_max;                       // largest sphere radius (filter bound)
     SphereLin sph[kMaxSpheres];
     float boom_len, jib_len;           // L_b and L_j: the tip is O + L_b e_b + (L_j + q4) e_j
+    // the same placement constants of spheres 2p and 2p + 1 side by side (alpha, beta, gamma,
+    // -delta), the operands of the kinematics' packed FP32x2 arithmetic
+    float2 pk_alpha[kMaxSpheres / 2], pk_beta[kMaxSpheres / 2], pk_gamma[kMaxSpheres / 2],
+        pk_ndelta[kMaxSpheres / 2];
 };
 
 // Cylinder records in device memory (float32):

@@ -112,12 +112,20 @@ static __device__ __forceinline__ void crane_fk_polar(const ModelDev &m, float4 
         sincosf(q.y, &s2, &c2);
         sincosf(q.y + q.z, &s23, &c23);
     }
+    // per sphere b = gamma q4 + beta, h = alpha c2 + b c23, z = base_z + (alpha s2 + (b s23 - delta)),
+    // two spheres at a time in packed FP32x2 arithmetic (each lane the same IEEE operation as
+    // the scalar form)
+    const float2 q4 = make_float2(q.w, q.w), C2 = make_float2(c2, c2), C23 = make_float2(c23, c23);
+    const float2 S2 = make_float2(s2, s2), S23 = make_float2(s23, s23), BZ = make_float2(m.base_z, m.base_z);
 #pragma unroll
-    for (int s = 0; s < NSPH; ++s) {
-        const SphereLin sp = m.sph[s];
-        const float b = fmaf(sp.gamma, q.w, sp.beta);
-        h[s] = fmaf(sp.alpha, c2, b * c23);
-        z[s] = m.base_z + fmaf(sp.alpha, s2, fmaf(b, s23, -sp.delta));
+    for (int p = 0; p < NSPH / 2; ++p) {
+        const float2 b = __ffma2_rn(m.pk_gamma[p], q4, m.pk_beta[p]);
+        const float2 hh = __ffma2_rn(m.pk_alpha[p], C2, __fmul2_rn(b, C23));
+        const float2 zz = __fadd2_rn(BZ, __ffma2_rn(m.pk_alpha[p], S2, __ffma2_rn(b, S23, m.pk_ndelta[p])));
+        h[2 * p] = hh.x;
+        h[2 * p + 1] = hh.y;
+        z[2 * p] = zz.x;
+        z[2 * p + 1] = zz.y;
     }
 }
 
