@@ -278,6 +278,39 @@ static __device__ __forceinline__ void band_extent(const float *H, const float *
     }
 }
 
+// The in-band extent [hmin, hmax] of h over the lane's spheres (hmin > hmax when there is
+// none) and their heights packed for the filter, spheres outside the band at 1e30 so that no
+// filter passes them. When every centre lies inside the band (the common case) it is one
+// min / max pass over all spheres with nothing masked, which gives the same values.
+template <int NSPH>
+static __device__ __forceinline__ void band_pack(const float *H, const float *Z, float zlo, float zhi, float &hmin,
+                                                 float &hmax, float2 *H2)
+{
+    float zmn = Z[0], zmx = Z[0];
+#pragma unroll
+    for (int s = 1; s < NSPH; ++s) {
+        zmn = fminf(zmn, Z[s]);
+        zmx = fmaxf(zmx, Z[s]);
+    }
+    if (zmn > zlo && zmx < zhi) {
+        hmin = H[0];
+        hmax = H[0];
+#pragma unroll
+        for (int s = 1; s < NSPH; ++s) {
+            hmin = fminf(hmin, H[s]);
+            hmax = fmaxf(hmax, H[s]);
+        }
+#pragma unroll
+        for (int q = 0; q < NSPH / 2; ++q) H2[q] = make_float2(H[2 * q], H[2 * q + 1]);
+    } else {
+        band_extent<NSPH>(H, Z, zlo, zhi, hmin, hmax);
+#pragma unroll
+        for (int q = 0; q < NSPH / 2; ++q)
+            H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
+                                Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
+    }
+}
+
 template <int NSPH>
 static __device__ __forceinline__ UnitFrame unit_frame_band(float s1, float c1, const float *H, const float *Z,
                                                             float zlo, float zhi)

@@ -192,35 +192,9 @@ static __device__ __forceinline__ void polar_item(const ModelDev &m, const Scene
         crane_fk_polar<NSPH>(m, c.q, H, Z, s1, c1);
         // in-band extent of h at this lane; spheres outside the scene's height band (widened
         // by r_max) can penetrate nothing: they take no part (1e30 in the packed h)
-        // when every centre of the lane lies inside the band (the common case), the extent is
-        // that of all spheres and no sphere is masked: one min / max pass instead of the
-        // per-sphere band tests, with the same results
-        float zmn = Z[0], zmx = Z[0];
-#pragma unroll
-        for (int sp = 1; sp < NSPH; ++sp) {
-            zmn = fminf(zmn, Z[sp]);
-            zmx = fmaxf(zmx, Z[sp]);
-        }
-        const bool all_in = zmn > zlo && zmx < zhi;
         float hmin, hmax;
         float2 H2[NSPH / 2];
-        if (all_in) {
-            hmin = H[0];
-            hmax = H[0];
-#pragma unroll
-            for (int sp = 1; sp < NSPH; ++sp) {
-                hmin = fminf(hmin, H[sp]);
-                hmax = fmaxf(hmax, H[sp]);
-            }
-#pragma unroll
-            for (int q = 0; q < NSPH / 2; ++q) H2[q] = make_float2(H[2 * q], H[2 * q + 1]);
-        } else {
-            band_extent<NSPH>(H, Z, zlo, zhi, hmin, hmax);
-#pragma unroll
-            for (int q = 0; q < NSPH / 2; ++q)
-                H2[q] = make_float2(Z[2 * q] > zlo && Z[2 * q] < zhi ? H[2 * q] : 1e30f,
-                                    Z[2 * q + 1] > zlo && Z[2 * q + 1] < zhi ? H[2 * q + 1] : 1e30f);
-        }
+        band_pack<NSPH>(H, Z, zlo, zhi, hmin, hmax, H2);
         float dmin = CUDART_INF_F;
         if (hmin <= hmax) {
             const float phi0 = wrap_angle(c.q.x);
