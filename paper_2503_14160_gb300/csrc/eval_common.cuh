@@ -195,6 +195,18 @@ static __device__ __forceinline__ uint32_t any_below12(const float2 *g, const fl
     return r;
 }
 
+// 1 when some value of the packed filter t (NSPH values of the form dh^2 - rhs) is below zero:
+// the OR of their sign bits. Such a value is never -0 (an exact cancellation rounds to +0) nor
+// NaN (its terms are finite or +inf), so a set sign bit means exactly t < 0.
+template <int NSPH>
+static __device__ __forceinline__ uint32_t any_negative(const float2 *t)
+{
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int q = 0; q < NSPH / 2; ++q) bits |= __float_as_uint(t[q].x) | __float_as_uint(t[q].y);
+    return bits >> 31;
+}
+
 template <int NSPH>
 static __device__ __forceinline__ uint32_t any_below(const float2 *g, const float *t)
 {

@@ -156,7 +156,7 @@ __device__ __forceinline__ float survivor_cylinder(const ModelDev &m, const floa
         const float2 dh = __fadd2_rn(H2[k], mp2);
         t[k] = __ffma2_rn(dh, dh, mr2);
     }
-    return any_below<NSPH>(t, zero) ? exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e) : CUDART_INF_F;
+    return any_negative<NSPH>(t) ? exact_polar<NSPH>(m, H, Z, c1, s1, p, rhs, f, e) : CUDART_INF_F;
 }
 
 // A surviving box (centre c, half extent hb) against every sphere of the lane.

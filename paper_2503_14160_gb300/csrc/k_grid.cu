@@ -181,7 +181,6 @@ static __device__ __forceinline__ void polar_item(const ModelDev &m, const Scene
                                                   int it, int lane, uint32_t &survivors, uint32_t &tests)
 {
     const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
-    const float zero[NSPH] = {};
     const ItemRange ir = item_range(a, it);
     stage_controls(s_ctrl, a, ir.cand, lane);
     double acc = 0.0;
@@ -226,7 +225,7 @@ static __device__ __forceinline__ void polar_item(const ModelDev &m, const Scene
                         const float2 dh = __fadd2_rn(H2[k], mp2);
                         t[k] = __ffma2_rn(dh, dh, mr2);
                     }
-                    if (any_below<NSPH>(t, zero)) {
+                    if (any_negative<NSPH>(t)) {
                         ++survivors;
                         dmin = fminf(dmin, polar_exact<NSPH>(m, sc, H, Z, c1, s1, p, rhs, __float_as_int(rec.w)));
                     }
@@ -275,7 +274,8 @@ k_batch_eval_polar(const ModelDev m, const BatchEvalDev *__restrict__ qd, const 
                    int n_tiles, int *queue, int max_S)
 {
     extern __shared__ __align__(16) float4 s_basis[];
-    __shared__ __align__(16) BatchEvalDev s_q;
+    __shared__ __align__(16) unsigned char s_q_raw[sizeof(BatchEvalDev)];   // the held query's view
+    BatchEvalDev &s_q = *reinterpret_cast<BatchEvalDev *>(s_q_raw);
     __shared__ int s_tile;
     constexpr int W = THREADS / 32;
     float4 *s_ctrl = s_basis + 2 * max_S + (threadIdx.x >> 5) * kCtrlSlots;
