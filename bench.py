@@ -180,9 +180,9 @@ KERNEL_SOURCES = {
 # kernel's sources at the time of the capture: reported only while the sources still hash
 # to it, None once the kernel has changed.
 PROFILED_TRAFFIC = {
-    "k_eval_broad": {"sha1": "457bb6563f6b94b1372e94ddf7a49e9cbb97fa18", "bytes": 1104384.0,
+    "k_eval_broad": {"sha1": "30aed9912d26c48794f6d773d37814f0157d69a0", "bytes": 1108736.0,
                      "workload": "single_large"},
-    "k_eval_polar": {"sha1": "7a5def19126e736b95509050d8b2505429db5c16", "bytes": 33659904.0,
+    "k_eval_polar": {"sha1": "d7815354b220eddb118805f21d6987b927ec3690", "bytes": 33659648.0,
                      "workload": "dense_forest"},
 }
 
