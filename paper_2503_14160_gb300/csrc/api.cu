@@ -289,6 +289,10 @@ ModelDev make_model(const cp_model *m)
         d.pk_gamma[q] = make_float2(a.gamma, b.gamma);
         d.pk_ndelta[q] = make_float2(-a.delta, -b.delta);
     }
+    for (int q = 0; q < 2; ++q) {
+        d.pk_qmin[q] = make_float2(d.q_min[2 * q], d.q_min[2 * q + 1]);
+        d.pk_nqmax[q] = make_float2(-d.q_max[2 * q], -d.q_max[2 * q + 1]);
+    }
     return d;
 }
 

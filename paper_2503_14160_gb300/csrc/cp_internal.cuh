@@ -85,6 +85,7 @@ struct ModelDev {
     // -delta), the operands of the kinematics' packed FP32x2 arithmetic
     float2 pk_alpha[kMaxSpheres / 2], pk_beta[kMaxSpheres / 2], pk_gamma[kMaxSpheres / 2],
         pk_ndelta[kMaxSpheres / 2];
+    float2 pk_qmin[2], pk_nqmax[2];   // (q_min, -q_max) of joints (1, 2) and (3, 4)
 };
 
 // Cylinder records in device memory (float32):

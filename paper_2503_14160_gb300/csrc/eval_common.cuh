@@ -385,8 +385,16 @@ static __device__ __forceinline__ Checkpoint checkpoint_at(const ModelDev &m, co
     const float4 dq = combine4(dbw, P0, P1, P2, P3);   // q(s_k) - q(s_{k-1})
     c.jp = fmaf(dq.x, dq.x, fmaf(dq.y, dq.y, fmaf(dq.z, dq.z, dq.w * dq.w)));
     c.len = sqrtf(c.jp);
-    c.jl = limit_excess(c.q.x, m.q_min[0], m.q_max[0]) + limit_excess(c.q.y, m.q_min[1], m.q_max[1]) +
-           limit_excess(c.q.z, m.q_min[2], m.q_max[2]) + limit_excess(c.q.w, m.q_min[3], m.q_max[3]);
+    // limit excess per joint: only one of v - q_max and q_min - v can be positive (q_min <
+    // q_max), so max(0, v - q_max)^2 + max(0, q_min - v)^2 is e^2 with e the larger of the two
+    // clamped at 0, the same rounding as the two-term form; the differences and squares packed
+    const float2 qa = make_float2(c.q.x, c.q.y), qb = make_float2(c.q.z, c.q.w), m1 = make_float2(-1.f, -1.f);
+    const float2 hi_a = __fadd2_rn(qa, m.pk_nqmax[0]), hi_b = __fadd2_rn(qb, m.pk_nqmax[1]);   // v - q_max
+    const float2 lo_a = __ffma2_rn(m1, qa, m.pk_qmin[0]), lo_b = __ffma2_rn(m1, qb, m.pk_qmin[1]);   // q_min - v
+    const float2 ea = make_float2(fmaxf(fmaxf(hi_a.x, lo_a.x), 0.f), fmaxf(fmaxf(hi_a.y, lo_a.y), 0.f));
+    const float2 eb = make_float2(fmaxf(fmaxf(hi_b.x, lo_b.x), 0.f), fmaxf(fmaxf(hi_b.y, lo_b.y), 0.f));
+    const float2 sa = __fmul2_rn(ea, ea), sb = __fmul2_rn(eb, eb);
+    c.jl = sa.x + sa.y + sb.x + sb.y;
     return c;
 }
 
