@@ -180,9 +180,9 @@ KERNEL_SOURCES = {
 # kernel's sources at the time of the capture: reported only while the sources still hash
 # to it, None once the kernel has changed.
 PROFILED_TRAFFIC = {
-    "k_eval_broad": {"sha1": "30aed9912d26c48794f6d773d37814f0157d69a0", "bytes": 1108736.0,
+    "k_eval_broad": {"sha1": "7115394e59c612bdd7db715ba526249759c91e33", "bytes": 1109248.0,
                      "workload": "single_large"},
-    "k_eval_polar": {"sha1": "d7815354b220eddb118805f21d6987b927ec3690", "bytes": 33659648.0,
+    "k_eval_polar": {"sha1": "c672cf73c00f408944227a9428d7ecfe5db0a6cd", "bytes": 33693952.0,
                      "workload": "dense_forest"},
 }
 
