@@ -783,7 +783,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_rkb = L.take<unsigned long long>(radix ? N : 1);
     const size_t o_rva = L.take<int>(radix ? N : 1);
     const size_t o_rvb = L.take<int>(radix ? N : 1);
-    const size_t o_rh = L.take<int>(radix ? 256 * (size_t)radix_tiles(p->N) : 1);
+    const size_t o_rh = L.take<int>(radix ? radix_hist_ints(p->N) : 1);
     int32_t left = g_fail_allocs.load();
     while (left > 0 && !g_fail_allocs.compare_exchange_weak(left, left - 1)) {
     }
@@ -1697,11 +1697,10 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
         const int nt = (qh[q].D + 15) / 16;
         return nt * (nt + 1) / 2 * qh[q].n_chunks;
     }, t_mpart);
-    block_table(nq, [&](int q) { return (qh[q].D * (qh[q].D + 1) / 2 + 7) / 8; }, t_mcomb);
+    block_table(nq, [&](int q) { return (qh[q].D * (qh[q].D + 1) / 2 + 255) / 256; }, t_mcomb);
     int64_t max_tiles = 0;
     for (int q = 0; q < nq; ++q) max_tiles += std::max(b->items_pop[q], b->items_mean[q]);   // tiles of >= 1 item
     b->tiles_cap = max_tiles;
-    const int64_t tiles_radix = radix_tiles((int)b->total);
 
     Layout L;
     const size_t o_in = L.take<double>(8 * (size_t)nq);
@@ -1724,7 +1723,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
     const size_t o_kb = L.take<unsigned long long>((size_t)b->total);
     const size_t o_va = L.take<int>((size_t)b->total);
     const size_t o_vb = L.take<int>((size_t)b->total);
-    const size_t o_h = L.take<int>(256 * (size_t)tiles_radix);
+    const size_t o_h = L.take<int>(radix_hist_ints((int)b->total));
     if ((e = cudaMalloc((void **)&b->base, L.bytes)) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(batch)"));
     char *base = b->base;
     b->d_in = (double *)(base + o_in);

@@ -284,6 +284,7 @@ int launch_sample_elites(const float *Yp, const float *mu_f, int N, int K, int n
                          uint32_t *status, bool withhold, cudaStream_t st);
 int update_chunks(int nu, int D);
 int radix_tiles(int N);
+size_t radix_hist_ints(int N);   // ints of the histogram scratch of launch_radix_rank
 int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,
                       int *val_a, int *val_b, int *hist, cudaStream_t st);
 int launch_gather_elites(const int *sorted, const double *J, const float *xi, int nu, int D,

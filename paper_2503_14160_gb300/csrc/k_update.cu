@@ -98,7 +98,9 @@ __global__ void k_scatter(int *__restrict__ rank, const double *__restrict__ J,
 //
 // Block (tile t of the lower triangle of 16x16 tiles, chunk p of kChunk-row groups): one
 // S2 entry per thread, and S1 of the tile's rows on diagonal tiles. Partials are stored
-// entry-major ([entry][chunk]) so that the combine reads them with coalesced loads.
+// chunk-major ([chunk][row][col] and [chunk][row]): a tile's writes are rows of 16
+// consecutive entries, and the combine (one thread per entry) reads one chunk of
+// consecutive entries per load.
 __device__ __forceinline__ void moments_partial_body(const double *__restrict__ Y, const double *__restrict__ WY,
                                                     int nu, int D, int per, int n_chunks, double *s2p, double *s1p,
                                                     int t, int p)
@@ -146,8 +148,8 @@ __device__ __forceinline__ void moments_partial_body(const double *__restrict__ 
         }
     }
     const int r = tr * 16 + a, c = tc * 16 + b;
-    if (active && r < D && c <= r) s2p[((size_t)r * D + c) * n_chunks + p] = (a0 + a1) + (a2 + a3);
-    if (active && diag && b == 0 && r < D) s1p[(size_t)r * n_chunks + p] = acc1;
+    if (active && r < D && c <= r) s2p[(size_t)p * D * D + (size_t)r * D + c] = (a0 + a1) + (a2 + a3);
+    if (active && diag && b == 0 && r < D) s1p[(size_t)p * D + r] = acc1;
 }
 
 // The elites' deviations from the best elite in FP64, y_j = x_(j) - x_(1) (exact: both are
@@ -196,56 +198,82 @@ k_batch_moments_partial(const BatchQueryDev *__restrict__ qd, const int2 *__rest
                          e.y % tiles, e.y / tiles);
 }
 
-// Sum of n values at stride 1, lane-strided and then by a fixed shuffle tree (every lane
-// gets the same result; the order does not depend on scheduling).
-__device__ __forceinline__ double warp_sum(const double *__restrict__ v, int n, int lane)
+// Sum of the n values v[0], v[stride], ..., v[(n - 1) stride] in a fixed order: 32 running
+// sums, sum l taking the terms q = l, l + 32, l + 64, ... in turn, then pairwise at distances
+// 16, 8, 4, 2, 1 (sum l of the first 16 plus sum l + 16, and so on down to sums 0 and 1).
+// It is the order of a warp's lane-strided sums and xor-shuffle tree, done by one thread:
+// the same additions, at a 32nd of the warp form's FP64 operations.
+__device__ __forceinline__ double tree_sum32(const double *__restrict__ v, int n, size_t stride)
 {
-    double s = 0.0;
-    for (int q = lane; q < n; q += 32) s += v[q];
+    double s[32];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    return s;
+    for (int l = 0; l < 32; ++l) s[l] = 0.0;
+    for (int q0 = 0; q0 < n; q0 += 32) {
+#pragma unroll
+        for (int l = 0; l < 32; ++l)
+            if (q0 + l < n) s[l] += v[(size_t)(q0 + l) * stride];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int l = 0; l < off; ++l) s[l] += s[l + off];
+    }
+    return s[0];
 }
 
-// One warp per lower-triangle entry (r >= c): C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c];
-// on the diagonal also mu_r = m0_r + S1_r.
+// S1 of rows 0 .. r_last into shared memory (one thread per row), for the entries of a block.
+__device__ __forceinline__ void stage_s1(const double *__restrict__ s1p, int n_chunks, int D, int r_last,
+                                         double *s_s1)
+{
+    for (int r = threadIdx.x; r <= r_last && r < D; r += blockDim.x) s_s1[r] = tree_sum32(s1p + r, n_chunks, D);
+    __syncthreads();
+}
+
+// Row of the last lower-triangle entry a block of blockDim.x threads starting at entry e0 holds.
+__device__ __forceinline__ int last_row(int e0, int D)
+{
+    int r, c;
+    tri_index(min(e0 + (int)blockDim.x, D * (D + 1) / 2) - 1, r, c);
+    return r;
+}
+
+// One thread per lower-triangle entry (r >= c) of a block of consecutive entries starting at
+// e0: C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c]; on the diagonal also
+// mu_r = m0_r + S1_r. S1 of the rows the block needs first goes to shared memory.
 __device__ __forceinline__ void moments_combine_body(const double *__restrict__ s2p, const double *__restrict__ s1p,
                                                     int n_chunks, int D, double eps,
-                                                    const float *__restrict__ elites, double *mu, double *C, int e)
+                                                    const float *__restrict__ elites, double *mu, double *C, int e0)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ double s_s1[4 * CP_MAX_WAYPOINTS];
+    stage_s1(s1p, n_chunks, D, last_row(e0, D), s_s1);
+    const int e = e0 + (int)threadIdx.x;
     if (e >= D * (D + 1) / 2) return;
     int r, c;
     tri_index(e, r, c);
-    const double s2 = warp_sum(s2p + ((size_t)r * D + c) * n_chunks, n_chunks, lane);
-    const double sr = warp_sum(s1p + (size_t)r * n_chunks, n_chunks, lane);
-    const double sc = warp_sum(s1p + (size_t)c * n_chunks, n_chunks, lane);
-    if (lane != 0) return;
-    double v = fma(-sr, sc, s2);
+    const double s2 = tree_sum32(s2p + (size_t)r * D + c, n_chunks, (size_t)D * D);
+    double v = fma(-s_s1[r], s_s1[c], s2);
     if (r == c) {
         v += eps;
-        mu[r] = (double)elites[r] + sr;
+        mu[r] = (double)elites[r] + s_s1[r];
     }
     C[(size_t)r * D + c] = v;
     C[(size_t)c * D + r] = v;
 }
 
-__global__ void k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1p,
-                                  int n_chunks, int D, double eps, const float *__restrict__ elites,
-                                  double *mu, double *C)
+__global__ void __launch_bounds__(256)
+k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1p, int n_chunks, int D, double eps,
+                  const float *__restrict__ elites, double *mu, double *C)
 {
-    moments_combine_body(s2p, s1p, n_chunks, D, eps, elites, mu, C,
-                         (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5));
+    moments_combine_body(s2p, s1p, n_chunks, D, eps, elites, mu, C, (int)(blockIdx.x * blockDim.x));
 }
 
-// Block b of query q combines the entries 8 b .. 8 b + 7 of that query (one warp each).
+// Block b of query q combines the entries 256 b .. 256 b + 255 of that query.
 __global__ void __launch_bounds__(256)
 k_batch_moments_combine(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab)
 {
     const int2 e = tab[blockIdx.x];
     const BatchQueryDev &q = qd[e.x];
-    moments_combine_body(q.s2p, q.s1p, q.n_chunks, q.D, q.eps, q.elites, q.mu, q.C,
-                         e.y * 8 + (int)(threadIdx.x >> 5));
+    moments_combine_body(q.s2p, q.s1p, q.n_chunks, q.D, q.eps, q.elites, q.mu, q.C, e.y * 256);
 }
 
 // ---------------------------------------------------------------- LSD radix sort (large N)
@@ -255,6 +283,7 @@ k_batch_moments_combine(const BatchQueryDev *__restrict__ qd, const int2 *__rest
 // __match_any_sync, across warps and passes from per-digit prefixes).
 constexpr int kRadixTile = 1024;
 constexpr int kRadixThreads = 256;
+constexpr int kRadixTotals = 10 * 256;   // per-digit totals of up to ten passes
 
 __global__ void k_radix_init(const double *__restrict__ J, int N, unsigned long long *key, int *val)
 {
@@ -274,9 +303,11 @@ __device__ __forceinline__ int radix_digit(unsigned long long k, int v, int shif
     return (int)((k >> shift) & 255ull);
 }
 
+// Tile histograms of one pass, digit-major (hist[d * tiles + tile]), and each digit's count
+// over all tiles added into totals[d] (zero before the pass).
 template <bool kByQuery = false>
 __global__ void __launch_bounds__(kRadixThreads)
-k_radix_hist(const unsigned long long *__restrict__ key, int N, int shift, int tiles, int *hist,
+k_radix_hist(const unsigned long long *__restrict__ key, int N, int shift, int tiles, int *hist, int *totals,
              const int *__restrict__ val = nullptr, const uint16_t *__restrict__ qid = nullptr)
 {
     __shared__ int h[256];
@@ -287,28 +318,33 @@ k_radix_hist(const unsigned long long *__restrict__ key, int N, int shift, int t
         atomicAdd(&h[radix_digit<kByQuery>(kByQuery ? 0ull : key[i], kByQuery ? val[i] : 0, shift, qid)], 1);
     __syncthreads();
     hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];   // digit-major
+    if (h[threadIdx.x] != 0) atomicAdd(totals + threadIdx.x, h[threadIdx.x]);
 }
 
-// Exclusive scan of n = 256 * tiles counts in place (one CTA; n is a multiple of 8 and a is
-// 16-byte aligned): 8192 counts at a time, eight consecutive ones per thread (two 16-byte
-// loads), the threads' totals scanned by warp shuffles and the warp totals by warp 0, and
-// the running total carried to the next 8192.
-__global__ void __launch_bounds__(1024) k_radix_scan(int *a, int n)
+// Exclusive scan of the digit-major histogram in place, one block per digit d: the element
+// (d, tile) becomes the count of all digits below d (from the per-digit totals) plus the
+// counts of digit d in the tiles before `tile`, 256 tiles at a time (block scan by warp
+// shuffles, the running total carried to the next 256). Integer sums: the same offsets as
+// any other order of the scan.
+__global__ void __launch_bounds__(256) k_radix_scan(int *hist, int tiles, const int *__restrict__ totals)
 {
-    __shared__ int warp_tot[32];
+    __shared__ int warp_tot[8];
     __shared__ int carry_s;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0) carry_s = 0;
+    const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int below = __reduce_add_sync(0xffffffffu, t < d ? totals[t] : 0);
+    if (lane == 0) warp_tot[warp] = below;
     __syncthreads();
-    for (int base = 0; base < n; base += 8192) {
-        const int i = base + 8 * t;
-        int4 u = make_int4(0, 0, 0, 0), w = make_int4(0, 0, 0, 0);
-        if (i < n) {
-            u = *reinterpret_cast<const int4 *>(a + i);
-            w = *reinterpret_cast<const int4 *>(a + i + 4);
-        }
-        const int sum = u.x + u.y + u.z + u.w + w.x + w.y + w.z + w.w;
-        int x = sum;   // inclusive scan of the thread totals within the warp
+    if (t == 0) {
+        int c = 0;
+        for (int w = 0; w < 8; ++w) c += warp_tot[w];
+        carry_s = c;
+    }
+    int *row = hist + (size_t)d * tiles;
+    for (int base = 0; base < tiles; base += 256) {
+        __syncthreads();   // carry_s written, warp_tot free
+        const int i = base + t;
+        const int c = i < tiles ? row[i] : 0;
+        int x = c;         // inclusive scan within the warp
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, off);
@@ -316,34 +352,11 @@ __global__ void __launch_bounds__(1024) k_radix_scan(int *a, int n)
         }
         if (lane == 31) warp_tot[warp] = x;
         __syncthreads();
-        if (warp == 0) {
-            int v = warp_tot[lane];
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, v, off);
-                if (lane >= off) v += y;
-            }
-            warp_tot[lane] = v;   // inclusive over warps
-        }
-        __syncthreads();
-        const int carry = carry_s;
-        int run = carry + (warp > 0 ? warp_tot[warp - 1] : 0) + x - sum;
-        if (i < n) {
-            int4 o, q;
-            o.x = run; run += u.x;
-            o.y = run; run += u.y;
-            o.z = run; run += u.z;
-            o.w = run; run += u.w;
-            q.x = run; run += w.x;
-            q.y = run; run += w.y;
-            q.z = run; run += w.z;
-            q.w = run;
-            *reinterpret_cast<int4 *>(a + i) = o;
-            *reinterpret_cast<int4 *>(a + i + 4) = q;
-        }
-        __syncthreads();
-        if (t == 1023) carry_s = carry + warp_tot[31];
-        __syncthreads();
+        int pre = carry_s;
+        for (int w = 0; w < warp; ++w) pre += warp_tot[w];
+        if (i < tiles) row[i] = pre + x - c;
+        __syncthreads();   // every thread has read carry_s
+        if (t == 255) carry_s = pre + x;
     }
 }
 
@@ -486,7 +499,7 @@ k_cma_paths(const double *__restrict__ s1p, int n_chunks, int D, const float *__
     double shift = 0.0;
     if (r < D) {
         double s1 = 0.0;
-        for (int c = 0; c < n_chunks; ++c) s1 += s1p[(size_t)r * n_chunks + c];
+        for (int c = 0; c < n_chunks; ++c) s1 += s1p[(size_t)c * D + r];
         const double m_new = (double)elites[r] + s1;
         shift = m_new - mu_prev[r];
         mu[r] = m_new;
@@ -543,24 +556,24 @@ k_cma_paths(const double *__restrict__ s1p, int n_chunks, int D, const float *__
     }
 }
 
-// One warp per lower-triangle entry: the elites' weighted scatter about the OLD mean m from
+// One thread per lower-triangle entry: the elites' weighted scatter about the OLD mean m from
 // the moments about x_(1) (with d = x_(1) - m and weights summing to one:
 // S2 + S1 d^T + d S1^T + d d^T), then C' = a C + c_1 p_c p_c^T + c_mu scatter / sigma^2 with
 // a = 1 + c_1 (1 - h_sigma) c_c (2 - c_c) - c_1 - c_mu.
-__global__ void k_cma_cov(const double *__restrict__ s2p, const double *__restrict__ s1p, int n_chunks,
+__global__ void __launch_bounds__(256) k_cma_cov(const double *__restrict__ s2p, const double *__restrict__ s1p, int n_chunks,
                           int D, const float *__restrict__ elites, const double *__restrict__ mu_prev,
                           const double *__restrict__ p_c, const double *__restrict__ cma, CmaConsts k,
                           double *C)
 {
-    const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+    __shared__ double s_s1[4 * CP_MAX_WAYPOINTS];
+    const int e0 = (int)(blockIdx.x * blockDim.x);
+    stage_s1(s1p, n_chunks, D, last_row(e0, D), s_s1);
+    const int e = e0 + (int)threadIdx.x;
     if (e >= D * (D + 1) / 2) return;
     int r, c;
     tri_index(e, r, c);
-    const double s2 = warp_sum(s2p + ((size_t)r * D + c) * n_chunks, n_chunks, lane);
-    const double sr = warp_sum(s1p + (size_t)r * n_chunks, n_chunks, lane);
-    const double sc = warp_sum(s1p + (size_t)c * n_chunks, n_chunks, lane);
-    if (lane != 0) return;
+    const double s2 = tree_sum32(s2p + (size_t)r * D + c, n_chunks, (size_t)D * D);
+    const double sr = s_s1[r], sc = s_s1[c];
     const double dr = (double)elites[r] - mu_prev[r], dc = (double)elites[c] - mu_prev[c];
     const double scatter = fma(dr, dc, fma(dr, sc, fma(sr, dc, s2)));
     const double sig = cma[1], h = cma[2];
@@ -574,19 +587,25 @@ __global__ void k_cma_cov(const double *__restrict__ s2p, const double *__restri
 
 int radix_tiles(int N) { return (N + kRadixTile - 1) / kRadixTile; }
 
+size_t radix_hist_ints(int N) { return 256 * (size_t)radix_tiles(N) + kRadixTotals; }
+
 // Sorted candidate order by (J, index) into `sorted` (N ints); scratch: two key buffers of
-// N, one value buffer of N, hist of 256 * radix_tiles(N) ints.
+// N, one value buffer of N, hist of radix_hist_ints(N) ints (tile histograms, then the
+// per-digit totals of every pass).
 int launch_radix_rank(const double *J, int N, unsigned long long *key_a, unsigned long long *key_b,
                       int *val_a, int *val_b, int *hist, cudaStream_t st)
 {
     const int tiles = radix_tiles(N);
+    int *totals = hist + 256 * (size_t)tiles;   // [pass][digit]
+    CP_CUDA(cudaMemsetAsync(totals, 0, sizeof(int) * kRadixTotals, st));
     k_radix_init<<<(N + 255) / 256, 256, 0, st>>>(J, N, key_a, val_a);
     CP_LAUNCHED("k_radix_init");
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 8 * pass;
-        k_radix_hist<false><<<tiles, kRadixThreads, 0, st>>>(key_a, N, shift, tiles, hist);
+        int *tot = totals + 256 * pass;
+        k_radix_hist<false><<<tiles, kRadixThreads, 0, st>>>(key_a, N, shift, tiles, hist, tot);
         CP_LAUNCHED("k_radix_hist");
-        k_radix_scan<<<1, 1024, 0, st>>>(hist, 256 * tiles);
+        k_radix_scan<<<256, 256, 0, st>>>(hist, tiles, tot);
         CP_LAUNCHED("k_radix_scan");
         k_radix_scatter<false><<<tiles, kRadixThreads, 0, st>>>(key_a, val_a, N, shift, tiles, hist, key_b, val_b);
         CP_LAUNCHED("k_radix_scatter");
@@ -701,8 +720,7 @@ int launch_cma_update(const float *elites, const double *w, int nu, int D, const
     k_cma_paths<<<1, kCmaThreads, smem, st>>>(s1p, n_chunks, D, elites, mu_prev, L, k, t, mu, p_sigma, p_c, cma);
     CP_LAUNCHED("k_cma_paths");
     const int entries = D * (D + 1) / 2;
-    k_cma_cov<<<(entries * 32 + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, elites, mu_prev, p_c, cma,
-                                                          k, C);
+    k_cma_cov<<<(entries + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, elites, mu_prev, p_c, cma, k, C);
     CP_LAUNCHED("k_cma_cov");
     return CP_OK;
 }
@@ -722,18 +740,21 @@ int launch_batch_radix_rank(const BatchQueryDev *qd, const int2 *tab, int blocks
                             int *val_a, int *val_b, int *hist, int **sorted, cudaStream_t st)
 {
     const int tiles = radix_tiles(total);
+    int *totals = hist + 256 * (size_t)tiles;   // [pass][digit]
+    CP_CUDA(cudaMemsetAsync(totals, 0, sizeof(int) * kRadixTotals, st));
     k_batch_radix_init<<<blocks, 256, 0, st>>>(qd, tab, key_a, val_a);
     CP_LAUNCHED("k_batch_radix_init");
     const int q_passes = nq > 256 ? 2 : (nq > 1 ? 1 : 0);
     for (int pass = 0; pass < 8 + q_passes; ++pass) {
         const bool byq = pass >= 8;
         const int shift = byq ? 8 * (pass - 8) : 8 * pass;
+        int *tot = totals + 256 * pass;
         if (byq)
-            k_radix_hist<true><<<tiles, kRadixThreads, 0, st>>>(key_a, total, shift, tiles, hist, val_a, qid);
+            k_radix_hist<true><<<tiles, kRadixThreads, 0, st>>>(key_a, total, shift, tiles, hist, tot, val_a, qid);
         else
-            k_radix_hist<false><<<tiles, kRadixThreads, 0, st>>>(key_a, total, shift, tiles, hist);
+            k_radix_hist<false><<<tiles, kRadixThreads, 0, st>>>(key_a, total, shift, tiles, hist, tot);
         CP_LAUNCHED("k_radix_hist");
-        k_radix_scan<<<1, 1024, 0, st>>>(hist, 256 * tiles);
+        k_radix_scan<<<256, 256, 0, st>>>(hist, tiles, tot);
         CP_LAUNCHED("k_radix_scan");
         if (byq)
             k_radix_scatter<true><<<tiles, kRadixThreads, 0, st>>>(key_a, val_a, total, shift, tiles, hist, key_b,
@@ -780,8 +801,7 @@ int launch_moments(const float *elites, const double *w, int nu, int D, double e
     int rc = launch_moments_partial(elites, w, nu, D, yw, s2p, s1p, &n_chunks, st);
     if (rc != CP_OK) return rc;
     const int entries = D * (D + 1) / 2;
-    k_moments_combine<<<(entries * 32 + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, eps, elites,
-                                                                  mu, C);
+    k_moments_combine<<<(entries + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, eps, elites, mu, C);
     CP_LAUNCHED("k_moments_combine");
     return CP_OK;
 }
