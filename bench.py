@@ -1130,7 +1130,7 @@ def run_trajopt(args):
             "roofline": {"bound": "fp64", "kernel": "k_traj_solve", "achieved": achieved,
                          "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"],
                          "peak_basis": "cp_alu_peaks (measured FP64 FMA rate, whole GPU)",
-                         "sms_used": n, "traffic": None},
+                         "sms_used": 2 * n, "ctas_per_trajectory": 2, "traffic": None},
             "result": {"t_F_mean_s": float(st[:, 0].mean()), "max_constraint_error": float(st[:, 2].max()),
                        "max_bound_violation": float(st[:, 3].max())},
             "clocks": clocks.summary()}

@@ -19,11 +19,12 @@
 // w_k = (x_k, u_k) with a border for t_F (the defects couple neighbours and t_F); it is
 // factored block by block (16 x 16 Cholesky factors L_k, L_k^-1 E_k) and the border is taken
 // through its Schur complement. The dynamics' Jacobian per grid point comes from forward-mode
-// differentiation (value and one derivative per pass, 16 passes). Everything is FP64: one
-// CTA of 256 threads per trajectory.
+// differentiation (value and one derivative per pass, 16 passes). Everything is FP64: a
+// cluster of two CTAs of 512 threads per trajectory.
 #include <cmath>
 #include <new>
 
+#include <cooperative_groups.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "cp_internal.cuh"
@@ -38,6 +39,7 @@ namespace cp {
 namespace {
 
 constexpr int kTrajThreads = 512;
+constexpr int kTrajCtas = 2;      // CTAs (one thread-block cluster) per trajectory
 constexpr int kRedDoubles = 64;   // block reductions: [0, 32) and [32, 64) (one slot per warp)
 constexpr int kWarpScratch = 2 * 12 * 16;   // doubles of shared memory per warp (block factor, F_k pair)
 constexpr int NX = 12, NU = 4, NW = 16;
@@ -56,10 +58,6 @@ __device__ __forceinline__ Dual operator/(Dual a, Dual b)
     const double q = a.v / b.v;
     return {q, (a.d - q * b.d) / b.v};
 }
-__device__ __forceinline__ Dual dsin(Dual a) { return {sin(a.v), cos(a.v) * a.d}; }
-__device__ __forceinline__ Dual dcos(Dual a) { return {cos(a.v), -sin(a.v) * a.d}; }
-__device__ __forceinline__ double dsin(double a) { return sin(a); }
-__device__ __forceinline__ double dcos(double a) { return cos(a); }
 template <typename T> __device__ __forceinline__ T lift(double v);
 template <> __device__ __forceinline__ double lift<double>(double v) { return v; }
 template <> __device__ __forceinline__ Dual lift<Dual>(double v) { return {v, 0.0}; }
@@ -188,30 +186,71 @@ __device__ __forceinline__ TrajWs ws_of(double *base, int N)
     return w;
 }
 
-// Block sum of a double over the CTA in a fixed order (deterministic).
-__device__ double block_sum(double v, double *s_red)
+// The CTAs of one trajectory: a cluster of kTrajCtas CTAs on neighbouring SMs. Grid points,
+// entries and blocks are split over the team-wide thread or warp index. Data one CTA writes to
+// the trajectory's global workspace is read by the other only after team_sync(), a cluster
+// barrier with release / acquire semantics. Every thread of both CTAs passes the same
+// sequence of them: no barrier sits under a branch whose condition the CTAs could see
+// differently (the sums below give both the same values).
+struct Team {
+    int rank;   // this CTA's rank in the cluster
+    __device__ int tid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ int nthreads() const { return kTrajCtas * (int)blockDim.x; }
+    __device__ int warp() const { return tid() >> 5; }
+    __device__ int nwarps() const { return nthreads() >> 5; }
+};
+
+__device__ __forceinline__ Team team_of_block()
+{
+    return Team{(int)cooperative_groups::this_cluster().block_rank()};
+}
+
+__device__ __forceinline__ void team_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Sums of a and b over both CTAs in a fixed order: per warp by shuffles, a CTA's warps in
+// order by its thread 0, then CTA 0's partial plus CTA 1's (read from each CTA's shared
+// memory), so every thread of both CTAs returns the same values (deterministic).
+__device__ double2 team_sum2(double a, double b, double *s_red)
 {
     const int t = threadIdx.x;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
     __syncthreads();
-    if ((t & 31) == 0) s_red[t >> 5] = v;
+    if ((t & 31) == 0) {
+        s_red[t >> 5] = a;
+        s_red[32 + (t >> 5)] = b;
+    }
     __syncthreads();
-    double s = 0.0;
-    if (t == 0)
-        for (int i = 0; i < kTrajThreads / 32; ++i) s += s_red[i];
-    __syncthreads();
-    if (t == 0) s_red[0] = s;
-    __syncthreads();
-    const double r = s_red[0];
-    __syncthreads();
+    if (t == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int i = 0; i < kTrajThreads / 32; ++i) {
+            sa += s_red[i];
+            sb += s_red[32 + i];
+        }
+        s_red[kRedDoubles - 2] = sa;
+        s_red[kRedDoubles - 1] = sb;
+    }
+    team_sync();   // both CTAs' partials are written
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    const double *p0 = cl.map_shared_rank(s_red + kRedDoubles - 2, 0);
+    const double *p1 = cl.map_shared_rank(s_red + kRedDoubles - 2, 1);
+    const double2 r = make_double2(p0[0] + p1[0], p0[1] + p1[1]);
+    team_sync();   // every thread has read them before either CTA writes s_red again
     return r;
 }
 
-// f at every grid point of z (values only) into ws.f.
+__device__ double team_sum(double v, double *s_red) { return team_sum2(v, 0.0, s_red).x; }
+
+// f at every grid point of z (values only) into ws.f, the points split over the team.
 // trig (optional): the cosines and sines of every grid point are stored there too.
-__device__ void eval_f(const TrajDev &td, const double *z, double *f, double *trig = nullptr)
+__device__ void eval_f(const Team &tm, const TrajDev &td, const double *z, double *f, double *trig = nullptr)
 {
-    for (int k = threadIdx.x; k <= td.N; k += blockDim.x) {
+    for (int k = tm.tid(); k <= td.N; k += tm.nthreads()) {
         const double *w = z + 1 + (size_t)k * NW;
         traj_f<double>(td, w, w + NX, f + (size_t)k * NX, nullptr, trig != nullptr ? trig + (size_t)k * 10 : nullptr);
     }
@@ -219,14 +258,14 @@ __device__ void eval_f(const TrajDev &td, const double *z, double *f, double *tr
 
 // The merit F(z) = t_F + 1/2 |r(z)|^2 (T6): the AL terms of the defects and end states, the
 // effort and tracking sums over k = 1..N, and the bound penalty; f must be current for z.
-__device__ double merit(const TrajDev &td, const double *z, const double *lam, const double *q_star,
+__device__ double merit(const Team &tm, const TrajDev &td, const double *z, const double *lam, const double *q_star,
                         const double *f, const double *x_S, const double *x_T, double *s_red)
 {
     const int N = td.N;
     const double h = z[0] / N;
     double acc = 0.0;
     // defects and end states: rho/2 (c + lam/rho)^2
-    for (int e = threadIdx.x; e < NX * (N + 2); e += blockDim.x) {
+    for (int e = tm.tid(); e < NX * (N + 2); e += tm.nthreads()) {
         const int k = e / NX, i = e - k * NX;
         double c;
         if (k < N) {
@@ -241,7 +280,7 @@ __device__ double merit(const TrajDev &td, const double *z, const double *lam, c
         acc += 0.5 * td.rho * t * t;
     }
     // effort, tracking and bounds per grid point
-    for (int e = threadIdx.x; e < (N + 1) * NW; e += blockDim.x) {
+    for (int e = tm.tid(); e < (N + 1) * NW; e += tm.nthreads()) {
         const int k = e / NW, i = e - k * NW;
         const double v = z[1 + e];
         if (i < NX) {
@@ -256,7 +295,7 @@ __device__ double merit(const TrajDev &td, const double *z, const double *lam, c
             acc += td.omega_s * td.R[i - NX] * v * v;
         }
     }
-    return z[0] + block_sum(acc, s_red);
+    return z[0] + team_sum(acc, s_red);
 }
 
 // Cholesky factor of a 16 x 16 SPD block on one warp (all 32 lanes call; lanes 0-15 hold a
@@ -352,16 +391,18 @@ __device__ __noinline__ void warp_back16(const double *Lk, const double *P, cons
 }
 
 // The damped Gauss-Newton step dz at z (T6): Jacobian, assembly, block factorisation, solve.
-__device__ void lm_step(const TrajDev &td, const double *z, const double *lam, const double *q_star,
-                        const double *x_S, const double *x_T, double mu, const TrajWs &ws, double *dz,
+// dz_local: dz is this CTA's shared-memory copy, which gets every entry; otherwise it is one
+// global vector whose entries the team splits.
+__device__ void lm_step(const Team &tm, const TrajDev &td, const double *z, const double *lam, const double *q_star,
+                        const double *x_S, const double *x_T, double mu, const TrajWs &ws, double *dz, bool dz_local,
                         double *s_red, double *s_blk)
 {
-    const int N = td.N, t = threadIdx.x;
+    const int N = td.N, t = tm.tid(), nt = tm.nthreads();
     const double h = z[0] / N, rho = td.rho;
     // 1. f and df/dw at every grid point (16 forward-mode passes each)
-    eval_f(td, z, ws.f, ws.trig);
-    __syncthreads();
-    for (int e = t; e < (N + 1) * NW; e += blockDim.x) {
+    eval_f(tm, td, z, ws.f, ws.trig);
+    team_sync();
+    for (int e = t; e < (N + 1) * NW; e += nt) {
         const int k = e / NW, j = e - k * NW;
         const double *w = z + 1 + (size_t)k * NW;
         Dual x[NX], u[NU], out[NX];
@@ -370,7 +411,7 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
         traj_f<Dual>(td, x, u, out, ws.trig + (size_t)k * 10);
         for (int i = 0; i < NX; ++i) ws.Fj[((size_t)k * NX + i) * NW + j] = out[i].d;
     }
-    __syncthreads();
+    team_sync();
     // 2. assembly. Defect k: d_k = x_{k+1} - x_k - h/2 (f_k + f_{k+1}), rows scaled by sqrt(rho):
     //    A_k = dd_k/dw_k = -[I 0] - h/2 Fj_k, B_k = dd_k/dw_{k+1} = [I 0] - h/2 Fj_{k+1},
     //    e_k = dd_k/dt_F = -(f_k + f_{k+1}) / (2N); residual sqrt(rho) (d_k + lam_k / rho).
@@ -396,8 +437,8 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     // one warp per grid point k: F_k and F_{k+1} staged in the warp's shared memory, then the
     // 136 lower entries of D_k and the 256 of E_k
     {
-        const int warp = t >> 5, lane = t & 31, n_warps = (int)(blockDim.x >> 5);
-        double *sF = s_blk + (size_t)warp * kWarpScratch;   // [2][NX][NW]: F_k, F_{k+1}
+        const int warp = tm.warp(), lane = threadIdx.x & 31, n_warps = tm.nwarps();
+        double *sF = s_blk + (size_t)(threadIdx.x >> 5) * kWarpScratch;   // [2][NX][NW]: F_k, F_{k+1}
         const double *F0 = sF, *F1 = sF + NX * NW;
         for (int k = warp; k <= N; k += n_warps) {
             __syncwarp();
@@ -448,9 +489,8 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
                 }
         }
     }
-    __syncthreads();
-    // border column, gradient
-    for (int e = t; e < (N + 1) * NW; e += blockDim.x) {
+    // border column, gradient (stored negated: the solves below take -g)
+    for (int e = t; e < (N + 1) * NW; e += nt) {
         const int k = e / NW, i = e - k * NW;
         double bv = 0.0, gv = 0.0;
         if (k < N)
@@ -478,20 +518,22 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
             gv += 2.0 * td.omega_s * td.R[i - NX] * x;
         }
         ws.bb[e] = bv;
-        ws.g[e] = gv;
+        ws.g[e] = -gv;
     }
     // the t_F corner and gradient
     double cc = 0.0, gt = 0.0;
-    for (int e = t; e < N * NX; e += blockDim.x) {
+    for (int e = t; e < N * NX; e += nt) {
         const int k = e / NX, r = e - k * NX;
         const double ev = eres(k, r);
         cc += ev * ev;
         gt += ev * dres(k, r);
     }
-    cc = rho * block_sum(cc, s_red);
-    gt = 1.0 + rho * block_sum(gt, s_red);
+    {
+        const double2 sums = team_sum2(cc, gt, s_red);   // also orders D, E, bb, g before the solve
+        cc = rho * sums.x;
+        gt = 1.0 + rho * sums.y;
+    }
     cc += mu * (cc + 1e-9);
-    __syncthreads();
     // 3. the tridiagonal part T (diagonal blocks D_k, couplings T[k][k+1] = E_k) solved for the
     //    two right-hand sides b (into y, ws.bb) and -g (into v, ws.g) by block cyclic reduction.
     //    Level s = 1, 2, 4, ... eliminates the blocks k = s, 3s, 5s, ... <= N, each between
@@ -505,10 +547,8 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     //    the factors (1 / L_pp on the diagonal) in ws.D, w and x in ws.bb / ws.g. Each level's
     //    blocks are independent, so the chain of dependent FP64 steps is that of about
     //    log2(N + 1) block factors instead of N + 1.
-    const int warp = t >> 5, lane = t & 31, n_warps = (int)(blockDim.x >> 5);
-    double *Fw = s_blk + (size_t)warp * kWarpScratch;
-    for (int e = t; e < (N + 1) * NW; e += blockDim.x) ws.g[e] = -ws.g[e];
-    __syncthreads();
+    const int warp = tm.warp(), lane = threadIdx.x & 31, n_warps = tm.nwarps();
+    double *Fw = s_blk + (size_t)(threadIdx.x >> 5) * kWarpScratch;
     int s_top = 1;
     for (int s = 1; s <= N; s <<= 1) {
         s_top = s;
@@ -530,7 +570,7 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
             for (int ij = lane; ij < NW * NW; ij += 32) ws.D[(size_t)k * NW * NW + ij] = Fw[ij];
             __syncwarp();
         }
-        __syncthreads();
+        team_sync();
         const int n_even = N / (2 * s) + 1;
         for (int m = warp; m < n_even; m += n_warps) {   // phase B
             const int j = 2 * m * s, iL = j - s, iR = j + s;
@@ -572,7 +612,7 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
             }
             __syncwarp();
         }
-        __syncthreads();
+        team_sync();
     }
     // block 0: D_0 x_0 = f_0
     if (warp == 0) {
@@ -584,7 +624,7 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
         __syncwarp();
         warp_back16(Fw, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, ws.bb, ws.g, lane);
     }
-    __syncthreads();
+    team_sync();
     // the eliminated blocks, from the last level to the first
     for (int s = s_top; s >= 1; s >>= 1) {
         const int n_odd = (N / s + 1) / 2;
@@ -596,7 +636,7 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
                         has_r ? ws.bb + (size_t)r * NW : nullptr, has_r ? ws.g + (size_t)r * NW : nullptr,
                         ws.bb + (size_t)k * NW, ws.g + (size_t)k * NW, lane);
         }
-        __syncthreads();
+        team_sync();
     }
     // 4. the border: dt = (-g_t - b^T v) / (c - b^T y), dw = v - y dt, with y = T^-1 b and
     //    v = T^-1 (-g_w) (b the original border column, kept in the factor-free terms above:
@@ -604,7 +644,7 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
     //    T y = b and T v = -g hold, so b^T y = sum_k b_k . y_k needs the original b: it is
     //    re-derived here from its definition.
     double by = 0.0, bv = 0.0;
-    for (int e = t; e < (N + 1) * NW; e += blockDim.x) {
+    for (int e = t; e < (N + 1) * NW; e += nt) {
         const int k = e / NW, i = e - k * NW;
         double b = 0.0;
         if (k < N)
@@ -615,22 +655,26 @@ __device__ void lm_step(const TrajDev &td, const double *z, const double *lam, c
         by += b * ws.bb[e];
         bv += b * ws.g[e];
     }
-    by = block_sum(by, s_red);
-    bv = block_sum(bv, s_red);
+    const double2 sums = team_sum2(by, bv, s_red);
+    by = sums.x;
+    bv = sums.y;
     const double dt = (-gt - bv) / (cc - by);
-    if (t == 0) dz[0] = dt;
-    for (int e = t; e < (N + 1) * NW; e += blockDim.x) dz[1 + e] = ws.g[e] - ws.bb[e] * dt;
+    const int d0 = dz_local ? (int)threadIdx.x : t, dn = dz_local ? (int)blockDim.x : nt;
+    if (d0 == 0) dz[0] = dt;
+    for (int e = d0; e < (N + 1) * NW; e += dn) dz[1 + e] = ws.g[e] - ws.bb[e] * dt;
     __syncthreads();
 }
 
-// One LM step for each trajectory (a test of the step): dz at (z, lam, mu).
-__global__ void __launch_bounds__(kTrajThreads)
+// One LM step for each trajectory (a test of the step): dz at (z, lam, mu). Cluster p of
+// kTrajCtas CTAs serves trajectory p.
+__global__ void __cluster_dims__(kTrajCtas, 1, 1) __launch_bounds__(kTrajThreads)
 k_traj_step(const TrajDev td, const double *q_star, const double *z, const double *lam, double mu, double *ws_base,
             size_t ws_stride, double *dz)
 {
     extern __shared__ double s_mem[];
     const int N = td.N, n_var = 1 + NW * (N + 1), n_eq = NX * (N + 2);
-    const int p = blockIdx.x;
+    const int p = (int)(blockIdx.x / kTrajCtas);
+    const Team tm = team_of_block();
     double *s_red = s_mem;                                      // kRedDoubles
     double *s_blk = s_red + kRedDoubles;                        // per warp kWarpScratch
     double *x_S = s_blk + (kTrajThreads / 32) * kWarpScratch, *x_T = x_S + NX;
@@ -641,19 +685,22 @@ k_traj_step(const TrajDev td, const double *q_star, const double *z, const doubl
     }
     __syncthreads();
     const TrajWs ws = ws_of(ws_base + (size_t)p * ws_stride, N);
-    lm_step(td, z + (size_t)p * n_var, lam + (size_t)p * n_eq, qs, x_S, x_T, mu, ws, dz + (size_t)p * n_var, s_red,
-            s_blk);
+    lm_step(tm, td, z + (size_t)p * n_var, lam + (size_t)p * n_eq, qs, x_S, x_T, mu, ws, dz + (size_t)p * n_var, false,
+            s_red, s_blk);
 }
 
 // The whole solve (T6) for each trajectory: z in place; stats {t_F, F, max |c|, max bound
-// violation}.
-__global__ void __launch_bounds__(kTrajThreads)
+// violation}. Cluster p of kTrajCtas CTAs serves trajectory p; each CTA keeps z, the trial
+// point and the step in its shared memory and updates all of them itself (the same values in
+// both), the multipliers and the workspace are global and split.
+__global__ void __cluster_dims__(kTrajCtas, 1, 1) __launch_bounds__(kTrajThreads)
 k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_base, size_t ws_stride, double *lam_ws,
              double *stats)
 {
     extern __shared__ double s_mem[];
     const int N = td.N, n_var = 1 + NW * (N + 1), n_eq = NX * (N + 2);
-    const int p = blockIdx.x, t = threadIdx.x;
+    const int p = (int)(blockIdx.x / kTrajCtas), t = threadIdx.x;
+    const Team tm = team_of_block();
     double *s_red = s_mem;
     double *s_blk = s_red + kRedDoubles;
     double *x_S = s_blk + (kTrajThreads / 32) * kWarpScratch, *x_T = x_S + NX;
@@ -667,21 +714,21 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
         x_T[i] = i < 4 ? qs[(size_t)N * 4 + i] : 0.0;
     }
     for (int i = t; i < n_var; i += blockDim.x) z[i] = z_io[(size_t)p * n_var + i];
-    for (int i = t; i < n_eq; i += blockDim.x) lam[i] = 0.0;
-    __syncthreads();
+    for (int i = tm.tid(); i < n_eq; i += tm.nthreads()) lam[i] = 0.0;
+    team_sync();
     const TrajWs ws = ws_of(ws_base + (size_t)p * ws_stride, N);
     double mu = td.mu0;
     for (int o = 0; o < td.outer; ++o) {
-        eval_f(td, z, ws.f);
-        __syncthreads();
-        double F = merit(td, z, lam, qs, ws.f, x_S, x_T, s_red);
+        eval_f(tm, td, z, ws.f);
+        team_sync();
+        double F = merit(tm, td, z, lam, qs, ws.f, x_S, x_T, s_red);
         for (int it = 0; it < td.inner; ++it) {
-            lm_step(td, z, lam, qs, x_S, x_T, mu, ws, dz, s_red, s_blk);
+            lm_step(tm, td, z, lam, qs, x_S, x_T, mu, ws, dz, true, s_red, s_blk);
             for (int i = t; i < n_var; i += blockDim.x) zn[i] = z[i] + dz[i];
             __syncthreads();
-            eval_f(td, zn, ws.f);
-            __syncthreads();
-            const double Fn = merit(td, zn, lam, qs, ws.f, x_S, x_T, s_red);
+            eval_f(tm, td, zn, ws.f);
+            team_sync();
+            const double Fn = merit(tm, td, zn, lam, qs, ws.f, x_S, x_T, s_red);
             if (Fn < F) {
                 for (int i = t; i < n_var; i += blockDim.x) z[i] = zn[i];
                 F = Fn;
@@ -692,10 +739,10 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
             __syncthreads();
         }
         // multipliers: lam += rho c(z)
-        eval_f(td, z, ws.f);
-        __syncthreads();
+        eval_f(tm, td, z, ws.f);
+        team_sync();
         const double h = z[0] / N;
-        for (int e = t; e < n_eq; e += blockDim.x) {
+        for (int e = tm.tid(); e < n_eq; e += tm.nthreads()) {
             const int k = e / NX, i = e - k * NX;
             double c;
             if (k < N) c = z[1 + (size_t)(k + 1) * NW + i] - z[1 + (size_t)k * NW + i] -
@@ -704,12 +751,13 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
             else c = z[1 + (size_t)N * NW + i] - x_T[i];
             lam[e] += td.rho * c;
         }
-        __syncthreads();
+        team_sync();
     }
-    // results and statistics
-    for (int i = t; i < n_var; i += blockDim.x) z_io[(size_t)p * n_var + i] = z[i];
-    eval_f(td, z, ws.f);
-    __syncthreads();
+    // results and statistics (each CTA takes every entry; CTA 0 writes them)
+    if (tm.rank == 0)
+        for (int i = t; i < n_var; i += blockDim.x) z_io[(size_t)p * n_var + i] = z[i];
+    eval_f(tm, td, z, ws.f);
+    team_sync();
     double cmax = 0.0, vmax = 0.0;
     const double h = z[0] / N;
     for (int e = t; e < n_eq; e += blockDim.x) {
@@ -738,7 +786,7 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
         s_red[32 + (t >> 5)] = vmax;
     }
     __syncthreads();
-    if (t == 0) {
+    if (t == 0 && tm.rank == 0) {
         double c = 0.0, v = 0.0;
         for (int i = 0; i < kTrajThreads / 32; ++i) {
             c = fmax(c, s_red[i]);
@@ -748,8 +796,8 @@ k_traj_solve(const TrajDev td, const double *q_star, double *z_io, double *ws_ba
         stats[(size_t)p * 4 + 3] = fmax(v, 0.0);
     }
     __syncthreads();
-    const double Fend = merit(td, z, lam, qs, ws.f, x_S, x_T, s_red);
-    if (t == 0) {
+    const double Fend = merit(tm, td, z, lam, qs, ws.f, x_S, x_T, s_red);
+    if (t == 0 && tm.rank == 0) {
         stats[(size_t)p * 4 + 0] = z[0];
         stats[(size_t)p * 4 + 1] = Fend;
     }
@@ -948,8 +996,8 @@ int cp_traj_step(cp_traj *t, const double *d_q_star, int32_t n, const double *d_
     if (n > 0 && (!d_q_star || !d_z || !d_lam || !d_dz)) return set_error("NULL argument"), CP_ERR_ARG;
     if (!(mu >= 0.0)) return set_error("mu must be >= 0"), CP_ERR_ARG;
     if (n == 0) return CP_OK;
-    k_traj_step<<<n, kTrajThreads, traj_smem(t->td.N, false), t->st>>>(t->td, d_q_star, d_z, d_lam, mu, t->ws,
-                                                                     t->ws_stride, d_dz);
+    k_traj_step<<<n * kTrajCtas, kTrajThreads, traj_smem(t->td.N, false), t->st>>>(t->td, d_q_star, d_z, d_lam, mu,
+                                                                                 t->ws, t->ws_stride, d_dz);
     CP_LAUNCHED("k_traj_step");
     return CP_OK;
 }
@@ -961,8 +1009,8 @@ int cp_traj_solve(cp_traj *t, const double *d_q_star, int32_t n, double *d_z, do
     if (n < 0 || n > t->max_paths) return set_error("n = %d outside 0..%d", n, t->max_paths), CP_ERR_ARG;
     if (n > 0 && (!d_q_star || !d_z || !d_stats)) return set_error("NULL argument"), CP_ERR_ARG;
     if (n == 0) return CP_OK;
-    k_traj_solve<<<n, kTrajThreads, traj_smem(t->td.N, true), t->st>>>(t->td, d_q_star, d_z, t->ws, t->ws_stride,
-                                                                      t->lam, d_stats);
+    k_traj_solve<<<n * kTrajCtas, kTrajThreads, traj_smem(t->td.N, true), t->st>>>(t->td, d_q_star, d_z, t->ws,
+                                                                                  t->ws_stride, t->lam, d_stats);
     CP_LAUNCHED("k_traj_solve");
     return CP_OK;
 }
