@@ -743,7 +743,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_elite = L.take<int>(nu);
     const size_t o_elites = L.take<float>(nu * D);
     const size_t o_w = L.take<double>(nu);
-    const size_t o_mean_part = L.take<double>(mc * D);
+    const size_t o_mean_part = L.take<double>((mc + 1) * D);   // chunk partials, then S1
     const size_t o_cov_part = L.take<double>(mc * D * D);
     const size_t o_mom_y = L.take<double>(2 * nu * D);
     const size_t o_best = L.take<double>(1);
@@ -1471,7 +1471,7 @@ int record_batch(cp_batch *b)
                                           b->key_b, b->val_a, b->val_b, b->hist, &sorted, b->st)) != CP_OK)
             return rc;
         if ((rc = launch_batch_gather(b->qdev, b->tab_gather, b->n_gather, sorted, b->st)) != CP_OK) return rc;
-        if ((rc = launch_batch_moments(b->qdev, b->tab_mprep, b->n_mprep, b->tab_mpart, b->n_mpart, b->tab_mcomb,
+        if ((rc = launch_batch_moments(b->qdev, b->nq, b->tab_mprep, b->n_mprep, b->tab_mpart, b->n_mpart, b->tab_mcomb,
                                        b->n_mcomb, b->st)) != CP_OK)
             return rc;
         if ((rc = launch_batch_factor(b->qdev, b->nq, b->max_D, b->st)) != CP_OK) return rc;
@@ -1697,7 +1697,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
         const int nt = (qh[q].D + 15) / 16;
         return nt * (nt + 1) / 2 * qh[q].n_chunks;
     }, t_mpart);
-    block_table(nq, [&](int q) { return (qh[q].D * (qh[q].D + 1) / 2 + 255) / 256; }, t_mcomb);
+    block_table(nq, [&](int q) { return (qh[q].D * (qh[q].D + 1) / 2 + 127) / 128; }, t_mcomb);
     int64_t max_tiles = 0;
     for (int q = 0; q < nq; ++q) max_tiles += std::max(b->items_pop[q], b->items_mean[q]);   // tiles of >= 1 item
     b->tiles_cap = max_tiles;

@@ -361,8 +361,9 @@ int launch_batch_radix_rank(const BatchQueryDev *qd, const int2 *tab, int blocks
                             const uint16_t *qid, unsigned long long *key_a, unsigned long long *key_b,
                             int *val_a, int *val_b, int *hist, int **sorted, cudaStream_t st);
 int launch_batch_gather(const BatchQueryDev *qd, const int2 *tab, int blocks, const int *sorted, cudaStream_t st);
-int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_prep, int blocks_prep, const int2 *tab_partial,
-                         int blocks_partial, const int2 *tab_combine, int blocks_combine, cudaStream_t st);
+int launch_batch_moments(const BatchQueryDev *qd, int nq, const int2 *tab_prep, int blocks_prep,
+                         const int2 *tab_partial, int blocks_partial, const int2 *tab_combine, int blocks_combine,
+                         cudaStream_t st);
 int moments_chunking(int nu, int D, int *per);   // chunks of the moment partials and elites per chunk
 int launch_batch_outputs(const BatchQueryDev *qd, int nq, bool mean_candidate, double *out, int out_stride,
                          cudaStream_t st);

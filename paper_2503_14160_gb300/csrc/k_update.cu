@@ -237,43 +237,61 @@ __device__ __forceinline__ int last_row(int e0, int D)
     return r;
 }
 
-// One thread per lower-triangle entry (r >= c) of a block of consecutive entries starting at
-// e0: C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c]; on the diagonal also
-// mu_r = m0_r + S1_r. S1 of the rows the block needs first goes to shared memory.
-__device__ __forceinline__ void moments_combine_body(const double *__restrict__ s2p, const double *__restrict__ s1p,
-                                                    int n_chunks, int D, double eps,
-                                                    const float *__restrict__ elites, double *mu, double *C, int e0)
+// S1 of row r (its chunk partials summed in the fixed order above), stored after the chunk
+// partials of s1p, and mu_r = m0_r + S1_r.
+__device__ __forceinline__ void moments_s1_body(double *s1p, int n_chunks, int D, const float *__restrict__ elites,
+                                               double *mu, int r)
 {
-    __shared__ double s_s1[4 * CP_MAX_WAYPOINTS];
-    stage_s1(s1p, n_chunks, D, last_row(e0, D), s_s1);
-    const int e = e0 + (int)threadIdx.x;
+    if (r >= D) return;
+    const double s = tree_sum32(s1p + r, n_chunks, D);
+    s1p[(size_t)n_chunks * D + r] = s;
+    mu[r] = (double)elites[r] + s;
+}
+
+// One thread per lower-triangle entry e (r >= c): C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c],
+// with S1 from moments_s1_body.
+__device__ __forceinline__ void moments_combine_body(const double *__restrict__ s2p, const double *__restrict__ s1,
+                                                    int n_chunks, int D, double eps, double *C, int e)
+{
     if (e >= D * (D + 1) / 2) return;
     int r, c;
     tri_index(e, r, c);
     const double s2 = tree_sum32(s2p + (size_t)r * D + c, n_chunks, (size_t)D * D);
-    double v = fma(-s_s1[r], s_s1[c], s2);
-    if (r == c) {
-        v += eps;
-        mu[r] = (double)elites[r] + s_s1[r];
-    }
+    double v = fma(-s1[r], s1[c], s2);
+    if (r == c) v += eps;
     C[(size_t)r * D + c] = v;
     C[(size_t)c * D + r] = v;
 }
 
-__global__ void __launch_bounds__(256)
-k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1p, int n_chunks, int D, double eps,
-                  const float *__restrict__ elites, double *mu, double *C)
+__global__ void __launch_bounds__(128)
+k_moments_s1(double *s1p, int n_chunks, int D, const float *__restrict__ elites, double *mu)
 {
-    moments_combine_body(s2p, s1p, n_chunks, D, eps, elites, mu, C, (int)(blockIdx.x * blockDim.x));
+    moments_s1_body(s1p, n_chunks, D, elites, mu, (int)threadIdx.x);
 }
 
-// Block b of query q combines the entries 256 b .. 256 b + 255 of that query.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
+k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1, int n_chunks, int D, double eps,
+                  double *C)
+{
+    moments_combine_body(s2p, s1, n_chunks, D, eps, C, (int)(blockIdx.x * blockDim.x + threadIdx.x));
+}
+
+// Block q: S1 and the mean of query q (one thread per row).
+__global__ void __launch_bounds__(128)
+k_batch_moments_s1(const BatchQueryDev *__restrict__ qd)
+{
+    const BatchQueryDev &q = qd[blockIdx.x];
+    moments_s1_body(q.s1p, q.n_chunks, q.D, q.elites, q.mu, (int)threadIdx.x);
+}
+
+// Block b of query q combines the entries 128 b .. 128 b + 127 of that query.
+__global__ void __launch_bounds__(128)
 k_batch_moments_combine(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab)
 {
     const int2 e = tab[blockIdx.x];
     const BatchQueryDev &q = qd[e.x];
-    moments_combine_body(q.s2p, q.s1p, q.n_chunks, q.D, q.eps, q.elites, q.mu, q.C, e.y * 256);
+    moments_combine_body(q.s2p, q.s1p + (size_t)q.n_chunks * q.D, q.n_chunks, q.D, q.eps, q.C,
+                         e.y * 128 + (int)threadIdx.x);
 }
 
 // ---------------------------------------------------------------- LSD radix sort (large N)
@@ -782,14 +800,17 @@ int launch_batch_gather(const BatchQueryDev *qd, const int2 *tab, int blocks, co
     return CP_OK;
 }
 
-int launch_batch_moments(const BatchQueryDev *qd, const int2 *tab_prep, int blocks_prep, const int2 *tab_partial,
-                         int blocks_partial, const int2 *tab_combine, int blocks_combine, cudaStream_t st)
+int launch_batch_moments(const BatchQueryDev *qd, int nq, const int2 *tab_prep, int blocks_prep,
+                         const int2 *tab_partial, int blocks_partial, const int2 *tab_combine, int blocks_combine,
+                         cudaStream_t st)
 {
     k_batch_moments_prep<<<blocks_prep, 256, 0, st>>>(qd, tab_prep);
     CP_LAUNCHED("k_batch_moments_prep");
     k_batch_moments_partial<<<blocks_partial, 256, 0, st>>>(qd, tab_partial);
     CP_LAUNCHED("k_batch_moments_partial");
-    k_batch_moments_combine<<<blocks_combine, 256, 0, st>>>(qd, tab_combine);
+    k_batch_moments_s1<<<nq, 128, 0, st>>>(qd);
+    CP_LAUNCHED("k_batch_moments_s1");
+    k_batch_moments_combine<<<blocks_combine, 128, 0, st>>>(qd, tab_combine);
     CP_LAUNCHED("k_batch_moments_combine");
     return CP_OK;
 }
@@ -801,7 +822,9 @@ int launch_moments(const float *elites, const double *w, int nu, int D, double e
     int rc = launch_moments_partial(elites, w, nu, D, yw, s2p, s1p, &n_chunks, st);
     if (rc != CP_OK) return rc;
     const int entries = D * (D + 1) / 2;
-    k_moments_combine<<<(entries + 255) / 256, 256, 0, st>>>(s2p, s1p, n_chunks, D, eps, elites, mu, C);
+    k_moments_s1<<<1, 128, 0, st>>>(s1p, n_chunks, D, elites, mu);
+    CP_LAUNCHED("k_moments_s1");
+    k_moments_combine<<<(entries + 127) / 128, 128, 0, st>>>(s2p, s1p + (size_t)n_chunks * D, n_chunks, D, eps, C);
     CP_LAUNCHED("k_moments_combine");
     return CP_OK;
 }

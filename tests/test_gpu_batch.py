@@ -63,8 +63,8 @@ def test_batch_matches_plain_plans(lib):
         assert info["eval_launches"] == T + 1
         assert info["candidates"] == sum(s[0] for s in SIZES)
         # per iteration: sample, evaluation, costs, ranking (init + 9 passes x 3), gather,
-        # moments (deviations, partials, combine), factor
-        assert info["kernel_nodes"] == 2 + T * (1 + 1 + 1 + 1 + 9 * 3 + 1 + 3 + 1) + 4
+        # moments (deviations, partials, first moments, combine), factor
+        assert info["kernel_nodes"] == 2 + T * (1 + 1 + 1 + 1 + 9 * 3 + 1 + 4 + 1) + 4
         res = cp.cp_batch_run(b, nq, K=Ks)
         # every launch shape gives the same bits
         for shape in [(128, 1, 1), (512, 0, 8), (256, 2, 64)]:
