@@ -1697,7 +1697,7 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
         const int nt = (qh[q].D + 15) / 16;
         return nt * (nt + 1) / 2 * qh[q].n_chunks;
     }, t_mpart);
-    block_table(nq, [&](int q) { return (qh[q].D * (qh[q].D + 1) / 2 + 127) / 128; }, t_mcomb);
+    block_table(nq, [&](int q) { return (qh[q].D * (qh[q].D + 1) / 2 + 31) / 32; }, t_mcomb);
     int64_t max_tiles = 0;
     for (int q = 0; q < nq; ++q) max_tiles += std::max(b->items_pop[q], b->items_mean[q]);   // tiles of >= 1 item
     b->tiles_cap = max_tiles;

@@ -201,31 +201,45 @@ k_batch_moments_partial(const BatchQueryDev *__restrict__ qd, const int2 *__rest
 // Sum of the n values v[0], v[stride], ..., v[(n - 1) stride] in a fixed order: 32 running
 // sums, sum l taking the terms q = l, l + 32, l + 64, ... in turn, then pairwise at distances
 // 16, 8, 4, 2, 1 (sum l of the first 16 plus sum l + 16, and so on down to sums 0 and 1).
-// It is the order of a warp's lane-strided sums and xor-shuffle tree, done by one thread:
-// the same additions, at a 32nd of the warp form's FP64 operations.
-__device__ __forceinline__ double tree_sum32(const double *__restrict__ v, int n, size_t stride)
+// It is the order of a warp's lane-strided sums and xor-shuffle tree. Here G aligned lanes
+// (sub = 0 .. G-1) share one sum: lane sub keeps the running sums sub P .. sub P + P - 1
+// (P = 32 / G), the pairings across lanes go through xor shuffles within the group and the
+// rest inside the lane, so the additions are the same and so are the bits. Every lane of the
+// warp calls it (full-warp shuffles); the total is returned on every lane of the group.
+template <int G>
+__device__ __forceinline__ double tree_sum(const double *__restrict__ v, int n, size_t stride, int sub)
 {
-    double s[32];
+    constexpr int P = 32 / G;
+    double s[P];
 #pragma unroll
-    for (int l = 0; l < 32; ++l) s[l] = 0.0;
+    for (int i = 0; i < P; ++i) s[i] = 0.0;
+    const int l0 = sub * P;
     for (int q0 = 0; q0 < n; q0 += 32) {
 #pragma unroll
-        for (int l = 0; l < 32; ++l)
-            if (q0 + l < n) s[l] += v[(size_t)(q0 + l) * stride];
+        for (int i = 0; i < P; ++i)
+            if (q0 + l0 + i < n) s[i] += v[(size_t)(q0 + l0 + i) * stride];
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 16; off >= P; off >>= 1) {   // partner lane sub + off / P holds sums l + off
 #pragma unroll
-        for (int l = 0; l < off; ++l) s[l] += s[l + off];
+        for (int i = 0; i < P; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off / P);
     }
-    return s[0];
+#pragma unroll
+    for (int off = P / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < off; ++i) s[i] += s[i + off];
+    }
+    return G > 1 ? __shfl_sync(0xffffffffu, s[0], (int)(threadIdx.x & 31) & ~(G - 1)) : s[0];
 }
+
+// Lanes per sum of the moment combine: four lanes, eight running sums each.
+constexpr int kSumLanes = 4;
 
 // S1 of rows 0 .. r_last into shared memory (one thread per row), for the entries of a block.
 __device__ __forceinline__ void stage_s1(const double *__restrict__ s1p, int n_chunks, int D, int r_last,
                                          double *s_s1)
 {
-    for (int r = threadIdx.x; r <= r_last && r < D; r += blockDim.x) s_s1[r] = tree_sum32(s1p + r, n_chunks, D);
+    for (int r = threadIdx.x; r <= r_last && r < D; r += blockDim.x) s_s1[r] = tree_sum<1>(s1p + r, n_chunks, D, 0);
     __syncthreads();
 }
 
@@ -237,61 +251,68 @@ __device__ __forceinline__ int last_row(int e0, int D)
     return r;
 }
 
-// S1 of row r (its chunk partials summed in the fixed order above), stored after the chunk
-// partials of s1p, and mu_r = m0_r + S1_r.
+// S1 of row r (its chunk partials summed in the fixed order above, kSumLanes lanes per row),
+// stored after the chunk partials of s1p, and mu_r = m0_r + S1_r. Called by whole warps.
 __device__ __forceinline__ void moments_s1_body(double *s1p, int n_chunks, int D, const float *__restrict__ elites,
-                                               double *mu, int r)
+                                               double *mu, int r, int sub)
 {
-    if (r >= D) return;
-    const double s = tree_sum32(s1p + r, n_chunks, D);
-    s1p[(size_t)n_chunks * D + r] = s;
-    mu[r] = (double)elites[r] + s;
+    const double s = tree_sum<kSumLanes>(s1p + min(r, D - 1), n_chunks, D, sub);
+    if (r < D && sub == 0) {
+        s1p[(size_t)n_chunks * D + r] = s;
+        mu[r] = (double)elites[r] + s;
+    }
 }
 
-// One thread per lower-triangle entry e (r >= c): C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c],
-// with S1 from moments_s1_body.
+// Lower-triangle entry e (r >= c), kSumLanes lanes per entry:
+// C[r][c] = C[c][r] = S2 - S1_r S1_c + eps [r = c], with S1 from moments_s1_body. Called by
+// whole warps.
 __device__ __forceinline__ void moments_combine_body(const double *__restrict__ s2p, const double *__restrict__ s1,
-                                                    int n_chunks, int D, double eps, double *C, int e)
+                                                    int n_chunks, int D, double eps, double *C, int e, int sub)
 {
-    if (e >= D * (D + 1) / 2) return;
+    const int entries = D * (D + 1) / 2;
     int r, c;
-    tri_index(e, r, c);
-    const double s2 = tree_sum32(s2p + (size_t)r * D + c, n_chunks, (size_t)D * D);
+    tri_index(min(e, entries - 1), r, c);
+    const double s2 = tree_sum<kSumLanes>(s2p + (size_t)r * D + c, n_chunks, (size_t)D * D, sub);
+    if (e >= entries || sub != 0) return;
     double v = fma(-s1[r], s1[c], s2);
     if (r == c) v += eps;
     C[(size_t)r * D + c] = v;
     C[(size_t)c * D + r] = v;
 }
 
+// Blocks of 128 threads: 32 rows (entries) per block, kSumLanes lanes each.
 __global__ void __launch_bounds__(128)
 k_moments_s1(double *s1p, int n_chunks, int D, const float *__restrict__ elites, double *mu)
 {
-    moments_s1_body(s1p, n_chunks, D, elites, mu, (int)threadIdx.x);
+    const int g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    moments_s1_body(s1p, n_chunks, D, elites, mu, g / kSumLanes, g % kSumLanes);
 }
 
 __global__ void __launch_bounds__(128)
 k_moments_combine(const double *__restrict__ s2p, const double *__restrict__ s1, int n_chunks, int D, double eps,
                   double *C)
 {
-    moments_combine_body(s2p, s1, n_chunks, D, eps, C, (int)(blockIdx.x * blockDim.x + threadIdx.x));
+    const int g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    moments_combine_body(s2p, s1, n_chunks, D, eps, C, g / kSumLanes, g % kSumLanes);
 }
 
-// Block q: S1 and the mean of query q (one thread per row).
+// Block (x, q): S1 and the mean of rows 32 x .. 32 x + 31 of query q.
 __global__ void __launch_bounds__(128)
 k_batch_moments_s1(const BatchQueryDev *__restrict__ qd)
 {
-    const BatchQueryDev &q = qd[blockIdx.x];
-    moments_s1_body(q.s1p, q.n_chunks, q.D, q.elites, q.mu, (int)threadIdx.x);
+    const BatchQueryDev &q = qd[blockIdx.y];
+    const int g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    moments_s1_body(q.s1p, q.n_chunks, q.D, q.elites, q.mu, g / kSumLanes, g % kSumLanes);
 }
 
-// Block b of query q combines the entries 128 b .. 128 b + 127 of that query.
+// Block b of query q combines the entries 32 b .. 32 b + 31 of that query.
 __global__ void __launch_bounds__(128)
 k_batch_moments_combine(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab)
 {
     const int2 e = tab[blockIdx.x];
     const BatchQueryDev &q = qd[e.x];
     moments_combine_body(q.s2p, q.s1p + (size_t)q.n_chunks * q.D, q.n_chunks, q.D, q.eps, q.C,
-                         e.y * 128 + (int)threadIdx.x);
+                         e.y * 32 + (int)threadIdx.x / kSumLanes, (int)threadIdx.x % kSumLanes);
 }
 
 // ---------------------------------------------------------------- LSD radix sort (large N)
@@ -590,7 +611,7 @@ __global__ void __launch_bounds__(256) k_cma_cov(const double *__restrict__ s2p,
     if (e >= D * (D + 1) / 2) return;
     int r, c;
     tri_index(e, r, c);
-    const double s2 = tree_sum32(s2p + (size_t)r * D + c, n_chunks, (size_t)D * D);
+    const double s2 = tree_sum<1>(s2p + (size_t)r * D + c, n_chunks, (size_t)D * D, 0);
     const double sr = s_s1[r], sc = s_s1[c];
     const double dr = (double)elites[r] - mu_prev[r], dc = (double)elites[c] - mu_prev[c];
     const double scatter = fma(dr, dc, fma(dr, sc, fma(sr, dc, s2)));
@@ -808,7 +829,7 @@ int launch_batch_moments(const BatchQueryDev *qd, int nq, const int2 *tab_prep, 
     CP_LAUNCHED("k_batch_moments_prep");
     k_batch_moments_partial<<<blocks_partial, 256, 0, st>>>(qd, tab_partial);
     CP_LAUNCHED("k_batch_moments_partial");
-    k_batch_moments_s1<<<nq, 128, 0, st>>>(qd);
+    k_batch_moments_s1<<<dim3(CP_MAX_WAYPOINTS * 4 / 32, nq), 128, 0, st>>>(qd);
     CP_LAUNCHED("k_batch_moments_s1");
     k_batch_moments_combine<<<blocks_combine, 128, 0, st>>>(qd, tab_combine);
     CP_LAUNCHED("k_batch_moments_combine");
@@ -822,9 +843,9 @@ int launch_moments(const float *elites, const double *w, int nu, int D, double e
     int rc = launch_moments_partial(elites, w, nu, D, yw, s2p, s1p, &n_chunks, st);
     if (rc != CP_OK) return rc;
     const int entries = D * (D + 1) / 2;
-    k_moments_s1<<<1, 128, 0, st>>>(s1p, n_chunks, D, elites, mu);
+    k_moments_s1<<<(D + 31) / 32, 128, 0, st>>>(s1p, n_chunks, D, elites, mu);
     CP_LAUNCHED("k_moments_s1");
-    k_moments_combine<<<(entries + 127) / 128, 128, 0, st>>>(s2p, s1p + (size_t)n_chunks * D, n_chunks, D, eps, C);
+    k_moments_combine<<<(entries + 31) / 32, 128, 0, st>>>(s2p, s1p + (size_t)n_chunks * D, n_chunks, D, eps, C);
     CP_LAUNCHED("k_moments_combine");
     return CP_OK;
 }
