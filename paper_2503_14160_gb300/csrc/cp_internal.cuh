@@ -348,7 +348,7 @@ int launch_batch_init(const BatchQueryDev *qd, const int2 *tab, int blocks, cons
 int launch_batch_factor(const BatchQueryDev *qd, int nq, int max_D, cudaStream_t st);
 int launch_batch_sample(const BatchQueryDev *qd, const int2 *tab, int blocks, int max_K, uint32_t iter,
                         cudaStream_t st);
-constexpr int kBatchSampleCands = 64;    // candidates per block of the batched sampler
+constexpr int kBatchSampleCands = 256;   // candidates per block of the batched sampler
 int batch_eval_configure();
 int launch_batch_eval_polar(const ModelDev &m, const BatchEvalDev *qd, const int4 *tiles, int n_tiles, int *queue,
                             int max_S, int threads, int blocks, cudaStream_t st);

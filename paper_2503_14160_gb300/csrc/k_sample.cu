@@ -225,8 +225,9 @@ k_sample(const double *__restrict__ mu, const float *__restrict__ Lt, int N, int
 }
 
 // Every query's draw in one launch: block b of query q takes the kBatchSampleCands
-// candidates from b kBatchSampleCands. A candidate's normals and arithmetic do not depend on
-// which warp draws it, so each query's xi equals its plain draw.
+// candidates from b kBatchSampleCands, each warp several groups of kSampleCands in turn (the
+// block stages the query's factor once for all of them). A candidate's normals and
+// arithmetic do not depend on which warp draws it, so each query's xi equals its plain draw.
 __global__ void __launch_bounds__(kSampleThreads)
 k_batch_sample(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ tab, uint32_t iter)
 {
@@ -234,8 +235,8 @@ k_batch_sample(const BatchQueryDev *__restrict__ qd, const int2 *__restrict__ ta
     const int2 e = tab[blockIdx.x];
     const BatchQueryDev &q = qd[e.x];
     const int b = e.y * kBatchSampleCands;
-    static_assert(kBatchSampleCands == kSampleWarps * kSampleCands, "one group of candidates per warp");
-    sample_body(q.mu, q.Lt, q.K, q.seed_lo, q.seed_hi, iter, q.query, q.xi, b, kBatchSampleCands,
+    static_assert(kBatchSampleCands % (kSampleWarps * kSampleCands) == 0, "whole groups of candidates per warp");
+    sample_body(q.mu, q.Lt, q.K, q.seed_lo, q.seed_hi, iter, q.query, q.xi, b, kSampleWarps * kSampleCands,
                 min(q.N, b + kBatchSampleCands), sm);
 }
 
