@@ -180,10 +180,9 @@ KERNEL_SOURCES = {
 # kernel's sources at the time of the capture: reported only while the sources still hash
 # to it, None once the kernel has changed.
 PROFILED_TRAFFIC = {
-    "k_eval_broad": {"sha1": "7115394e59c612bdd7db715ba526249759c91e33", "bytes": 1109248.0,
-                     "workload": "single_large"},
-    "k_eval_polar": {"sha1": "c672cf73c00f408944227a9428d7ecfe5db0a6cd", "bytes": 33693952.0,
-                     "workload": "dense_forest"},
+    ("k_eval_broad", "single_large"): {"sha1": "7115394e59c612bdd7db715ba526249759c91e33", "bytes": 1109248.0},
+    ("k_eval_polar", "dense_forest"): {"sha1": "c672cf73c00f408944227a9428d7ecfe5db0a6cd", "bytes": 33693952.0},
+    ("k_eval_polar", "single_large"): {"sha1": "c672cf73c00f408944227a9428d7ecfe5db0a6cd", "bytes": 1136384.0},
 }
 
 
@@ -205,8 +204,8 @@ def kernel_source_sha1(kernel):
 def traffic_per_launch(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from its last ncu capture, or None
     when there is none for this workload or the kernel's sources have changed since."""
-    rec = PROFILED_TRAFFIC.get(kernel)
-    if rec is None or rec["workload"] != workload or rec["sha1"] != kernel_source_sha1(kernel):
+    rec = PROFILED_TRAFFIC.get((kernel, workload))
+    if rec is None or rec["sha1"] != kernel_source_sha1(kernel):
         return None
     return rec["bytes"]
 
@@ -382,7 +381,7 @@ def run_ours(args):
         peaks_fp64 = peaks["fp64_tflops"]
         roofline["measured_fma_peaks"] = peaks
         roofline["frac_of_measured_fp32"] = roofline["achieved"] / peaks["fp32_tflops"]
-    if wl.grid_cell <= 0 and args.collision == "spheres":
+    if args.collision == "spheres" and scene.n_cyl + scene.n_box <= 1000:
         if not args.exhaustive:
             roofline_exhaustive = exhaustive_roofline(cp, crane, scene, wl, q0, qd,
                                                       clk.get("sm_mhz"))
@@ -481,7 +480,7 @@ def sampler_stage(timing, wl, sampler):
 
 def exhaustive_roofline(cp, crane, scene, wl, q0, qd, sm_mhz, iterations=10):
     """The exhaustive form of the evaluation (every sphere against every obstacle) timed on
-    the same query for a few iterations, for comparison with the broad phase."""
+    the same query for a few iterations, for comparison with the culled forms."""
     import torch
     params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed,
                             eval_exhaustive=1)

@@ -56,10 +56,10 @@ def test_eval_roofline_polar_counts_the_index_tests(bench):
 
 
 def test_traffic_is_reported_only_for_the_profiled_sources(bench):
-    rec = bench.PROFILED_TRAFFIC["k_eval_broad"]
-    want = rec["bytes"] if bench.kernel_source_sha1("k_eval_broad") == rec["sha1"] else None
-    assert bench.traffic_per_launch("k_eval_broad", rec["workload"]) == want
-    assert bench.traffic_per_launch("k_eval_broad", "no such workload") is None
+    for (kernel, workload), rec in bench.PROFILED_TRAFFIC.items():
+        want = rec["bytes"] if bench.kernel_source_sha1(kernel) == rec["sha1"] else None
+        assert bench.traffic_per_launch(kernel, workload) == want
+        assert bench.traffic_per_launch(kernel, "no such workload") is None
 
 
 def test_eval_roofline_refuses_empty_timings(bench):
