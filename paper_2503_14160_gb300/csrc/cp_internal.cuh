@@ -178,13 +178,15 @@ struct EvalArgs {
     float *pen_out;             // optional [n][n_s]
 };
 
-// Units per item for n candidates of `chunks` units: about 2^17 items per launch at most
-// (enough to keep every warp of the GPU busy to the end), a whole number of units each.
-// The items of a launch, n ceil(chunks / G), are then at most min(n chunks, 2^18 + n).
+// Units per item for n candidates of `chunks` units: about 2^15 items per launch at most, a
+// whole number of units each (eight or more per resident warp of the evaluation, enough to
+// keep every warp busy to the end; larger items share a candidate's control points, its
+// index neighbourhood in L1 and its item overhead over more units). The items of a launch,
+// n ceil(chunks / G), are then at most min(n chunks, 2^16 + n).
 inline int eval_units_per_item(int n, int chunks)
 {
     const long long units = (long long)n * chunks;
-    long long g = units >> 17;
+    long long g = units >> 15;
     if (g < 1) g = 1;
     if (g > chunks) g = chunks;
     return (int)g;
