@@ -180,9 +180,8 @@ KERNEL_SOURCES = {
 # kernel's sources at the time of the capture: reported only while the sources still hash
 # to it, None once the kernel has changed.
 PROFILED_TRAFFIC = {
-    ("k_eval_broad", "single_large"): {"sha1": "7115394e59c612bdd7db715ba526249759c91e33", "bytes": 1109248.0},
-    ("k_eval_polar", "dense_forest"): {"sha1": "c672cf73c00f408944227a9428d7ecfe5db0a6cd", "bytes": 33693952.0},
-    ("k_eval_polar", "single_large"): {"sha1": "c672cf73c00f408944227a9428d7ecfe5db0a6cd", "bytes": 1136384.0},
+    ("k_eval_polar", "dense_forest"): {"sha1": "721f3917bfae1f6d3a88cb16824e8a1834f45c79", "bytes": 33658880.0},
+    ("k_eval_polar", "single_large"): {"sha1": "721f3917bfae1f6d3a88cb16824e8a1834f45c79", "bytes": 1136640.0},
 }
 
 
