@@ -168,6 +168,7 @@ struct cp_planner {
     float *grad = nullptr;      // [N][D] gradient buffer for polish
     float4 *ends_f = nullptr;   // [2] {q0, qd} in float, written with the end points
     unsigned long long *work = nullptr;   // [2] broad-phase survivors and box tests while timing
+    int *eval_queue = nullptr;            // the polar evaluation's item counter
     unsigned long long *rkey_a = nullptr, *rkey_b = nullptr;   // radix sort scratch
     int *rval_a = nullptr, *rval_b = nullptr, *rhist = nullptr;
     double *cma = nullptr;      // CMA-ES rule: {sigma, sigma before the update, h_sigma, |p_sigma|}
@@ -477,6 +478,7 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
         else if (!a.broadphase) p->timer.tests += (int64_t)n * p->chunks * (p->sdev.n_cyl + p->sdev.n_box);
     }
     a.status = p->status;
+    a.queue = p->eval_queue;
     a.basis = p->basis;
     a.item_sum = p->item_sum;
     a.item_count = p->item_count;
@@ -763,6 +765,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_sp_g = L.take<float>(units_max * D);
     const size_t o_sp_J = L.take<double>(units_max);
     const size_t o_work = L.take<unsigned long long>(2);
+    const size_t o_eval_queue = L.take<int>(1);
     const size_t o_metrics = L.take<double>((size_t)kMetricsRing * kMetricsCols);
     const size_t o_cma = L.take<double>(4);
     const size_t o_psig = L.take<double>(D);
@@ -826,6 +829,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->grad = (float *)(b + o_grad);
     p->ends_f = (float4 *)(b + o_ends_f);
     p->work = (unsigned long long *)(b + o_work);
+    p->eval_queue = (int *)(b + o_eval_queue);
     p->metrics = (double *)(b + o_metrics);
     p->cma = (double *)(b + o_cma);
     p->p_sigma = (double *)(b + o_psig);

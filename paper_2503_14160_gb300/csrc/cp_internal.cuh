@@ -171,6 +171,8 @@ struct EvalArgs {
     unsigned long long *work;   // optional [2]: += obstacles that passed the unit box test,
                                 // += (unit, obstacle) box tests run (polar index form)
     uint32_t *status;           // device status word (DEV_ERR_*) or null
+    int *queue;                 // polar form: the next work item to take (zeroed before each
+                                // launch); null: items in a fixed stride over the warps
     const float4 *basis;        // [S][2]: {b0..b3}(u_m), {b0..b3}(u_m) - {b0..b3}(u_{m-1})
     double *item_sum;           // [n][P][4] {J_p, sum pen, J_l, length}
     uint32_t *item_count;       // [n][P] checkpoints in collision

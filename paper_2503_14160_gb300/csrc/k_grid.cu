@@ -252,7 +252,21 @@ k_eval_polar(const ModelDev m, const SceneDev sc, const PolarDev g, const EvalAr
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     const int items = a.n * a.P;
     uint32_t survivors = 0, tests = 0;   // (lane, obstacle) pairs passing the packed filter; tested
-    for (int it = warp; it < items; it += n_warps) polar_item<NSPH>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
+    if (a.queue != nullptr) {
+        // each warp takes the next item from the launch's counter when it is done with one, so
+        // candidates of uneven cost (those in collision take the exact distances) even out;
+        // the counter only grows, so every warp leaves once the items are handed out
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(a.queue, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= items) break;
+            polar_item<NSPH>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
+        }
+    } else {
+        for (int it = warp; it < items; it += n_warps)
+            polar_item<NSPH>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
+    }
     if (a.work != nullptr) {
         const uint32_t ws = __reduce_add_sync(0xffffffffu, survivors);
         const uint32_t wt = __reduce_add_sync(0xffffffffu, tests);
@@ -399,6 +413,7 @@ int launch_eval_polar(const ModelDev &m, const SceneDev &sc, const PolarDev &g, 
     const int needed = (items + kPolarThreads / 32 - 1) / (kPolarThreads / 32);
     int grid = num_sms * per_sm;
     if (grid > needed) grid = needed;
+    if (a.queue != nullptr) CP_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
     if (m.n_spheres == 12)
         k_eval_polar<12><<<grid, kPolarThreads, smem, st>>>(m, sc, g, a);
     else
