@@ -169,6 +169,7 @@ struct cp_planner {
     float4 *ends_f = nullptr;   // [2] {q0, qd} in float, written with the end points
     unsigned long long *work = nullptr;   // [2] broad-phase survivors and box tests while timing
     int *eval_queue = nullptr;            // the polar evaluation's item counter
+    size_t item_cap = 0;                  // work items the item_sum / item_count buffers hold
     unsigned long long *rkey_a = nullptr, *rkey_b = nullptr;   // radix sort scratch
     int *rval_a = nullptr, *rval_b = nullptr, *rhist = nullptr;
     double *cma = nullptr;      // CMA-ES rule: {sigma, sigma before the update, h_sigma, |p_sigma|}
@@ -463,6 +464,9 @@ int run_eval(cp_planner *p, const float *d_xi, int n, double *d_J, uint8_t *d_fl
     a.chunks = p->chunks;
     a.G = eval_units_per_item(n, p->chunks);
     a.P = (p->chunks + a.G - 1) / a.G;
+    if ((size_t)n * a.P > p->item_cap)   // the buffers are sized by the same rule: never expected
+        return set_error("%d candidates need %lld work items; the planner holds %lld", n,
+                         (long long)n * a.P, (long long)p->item_cap), CP_ERR_STATE;
     a.div_S = fast_div((uint32_t)p->S);
     a.div_P = fast_div((uint32_t)a.P);
     a.q0 = p->q0f;
@@ -741,6 +745,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t item_cap = std::min(N * ch, (size_t)(1 << 16) + N);
     const size_t o_item_sum = L.take<double>(item_cap * 4);
     const size_t o_item_count = L.take<uint32_t>(item_cap);
+    p->item_cap = item_cap;
     const size_t o_rank = L.take<int>(N);
     const size_t o_elite = L.take<int>(nu);
     const size_t o_elites = L.take<float>(nu * D);
@@ -1677,6 +1682,9 @@ int cp_batch_init(const cp_model *model, const cp_query *queries, int32_t nq, in
             ev.a = a;
             ev.sc = p->sdev;
             ev.g = p->gdev;
+            if ((size_t)n * a.P > p->item_cap)
+                return fail((set_error("query %d: %d candidates need more work items than its planner holds", q, n),
+                             CP_ERR_STATE));
             (m == 0 ? b->items_pop : b->items_mean)[q] = n * a.P;
             if (m == 0) {
                 d.P = a.P;
