@@ -741,8 +741,8 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_J = L.take<double>(N);
     const size_t o_terms = L.take<double>(N * 5);
     const size_t o_flag = L.take<uint8_t>(N);
-    // work items of an evaluation of n <= N candidates: n P(n) <= min(n chunks, 2^16 + n)
-    const size_t item_cap = std::min(N * ch, (size_t)(1 << 16) + N);
+    // work items of an evaluation of n <= N candidates: n P(n) <= eval_item_capacity(N, chunks)
+    const size_t item_cap = eval_item_capacity(N, ch);
     const size_t o_item_sum = L.take<double>(item_cap * 4);
     const size_t o_item_count = L.take<uint32_t>(item_cap);
     p->item_cap = item_cap;

@@ -181,17 +181,25 @@ struct EvalArgs {
 };
 
 // Units per item for n candidates of `chunks` units: about 2^15 items per launch at most, a
-// whole number of units each (eight or more per resident warp of the evaluation, enough to
-// keep every warp busy to the end; larger items share a candidate's control points, its
-// index neighbourhood in L1 and its item overhead over more units). The items of a launch,
-// n ceil(chunks / G), are then at most min(n chunks, 2^16 + n).
+// whole number of units each and at most half a candidate (rounded up). Larger items share
+// a candidate's control points, its index neighbourhood in L1 and the item overhead over more
+// units; the warps take items from a queue, and at least two items per candidate keep the
+// last ones short. The items of a launch, n ceil(chunks / G), are then at most
+// eval_item_capacity(n, chunks).
 inline int eval_units_per_item(int n, int chunks)
 {
     const long long units = (long long)n * chunks;
     long long g = units >> 15;
+    if (g > (chunks + 1) / 2) g = (chunks + 1) / 2;
     if (g < 1) g = 1;
-    if (g > chunks) g = chunks;
     return (int)g;
+}
+
+// Work items of an evaluation of at most n candidates: min(n chunks, max(2^16 + n, 2 n)).
+inline size_t eval_item_capacity(size_t n, size_t chunks)
+{
+    const size_t a = ((size_t)1 << 16) + n, b = 2 * n, c = a > b ? a : b, all = n * chunks;
+    return all < c ? all : c;
 }
 
 int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int num_sms,
