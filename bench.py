@@ -180,8 +180,8 @@ KERNEL_SOURCES = {
 # kernel's sources at the time of the capture: reported only while the sources still hash
 # to it, None once the kernel has changed.
 PROFILED_TRAFFIC = {
-    ("k_eval_polar", "dense_forest"): {"sha1": "721f3917bfae1f6d3a88cb16824e8a1834f45c79", "bytes": 33658880.0},
-    ("k_eval_polar", "single_large"): {"sha1": "721f3917bfae1f6d3a88cb16824e8a1834f45c79", "bytes": 1136640.0},
+    ("k_eval_polar", "dense_forest"): {"sha1": "4575405339bb4aa3cb380cb03f78f9cf4d2c7b82", "bytes": 33682688.0},
+    ("k_eval_polar", "single_large"): {"sha1": "4575405339bb4aa3cb380cb03f78f9cf4d2c7b82", "bytes": 1162496.0},
 }
 
 
