@@ -1099,8 +1099,8 @@ static int run_smooth(cp_planner *p, const float *xi, int n, const double *gJ, d
 {
     return launch_smooth(p->mdev, p->sdev, xi, n, p->K, p->S, p->q0f, p->qdf, p->basis,
                          p->prm.smooth_margin, p->prm.smooth_beta, p->prm.w_c * p->prm.lambda_c,
-                         p->prm.w_l, gJ, J, dxi, p->smooth_part_g, p->smooth_part_J, p->num_sms,
-                         p->st);
+                         p->prm.w_l, gJ, J, dxi, p->smooth_part_g, p->smooth_part_J, p->eval_queue,
+                         p->num_sms, p->st);
 }
 
 int cp_smooth_cost(cp_planner *p, const float *d_xi, int32_t n, double *d_J)

@@ -242,7 +242,7 @@ size_t smooth_smem_bytes(int n_cyl, int n_box, int S, int K);
 int launch_smooth(const ModelDev &m, const SceneDev &sc, const float *xi, int n, int K, int S,
                   float4 q0, float4 qd, const float4 *basis, double margin, double beta,
                   double wc_lc, double w_l, const double *gJ, double *J, float *dxi, float *part_g,
-                  double *part_J, int num_sms, cudaStream_t st);
+                  double *part_J, int *queue, int num_sms, cudaStream_t st);   // queue: item counter or null
 int64_t smooth_partial_units(int num_sms);
 int launch_axpy(float *x, const float *y, double alpha, int64_t n, cudaStream_t st);
 

@@ -30,6 +30,8 @@ struct SmoothArgs {
     int chunks_per_group;
     float *part_g;           // [n groups][4K] when groups > 1
     double *part_J;          // [n groups] when groups > 1
+    int *queue;              // the next unit to take (zeroed before the launch), or null: a
+                             // fixed stride of units over the warps
 };
 
 __device__ __forceinline__ float softplus_f(float x)
@@ -101,8 +103,16 @@ k_smooth(const ModelDev m, const SceneDev sc, const SmoothArgs a)
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     // A unit is (candidate, group of consecutive chunks); with few candidates several
-    // warps share one candidate and write partial sums that k_smooth_reduce combines.
-    for (int unit = warp; unit < a.n * a.groups; unit += n_warps) {
+    // warps share one candidate and write partial sums that k_smooth_reduce combines. A warp
+    // takes its next unit from the queue when it has one (candidates in contact cost more),
+    // else the units go round the warps in a fixed stride.
+    auto next_unit = [&](int u) {
+        if (a.queue == nullptr) return u + n_warps;
+        int v = 0;
+        if (lane == 0) v = atomicAdd(a.queue, 1);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    for (int unit = a.queue == nullptr ? warp : next_unit(0); unit < a.n * a.groups; unit = next_unit(unit)) {
         const int cand = unit / a.groups, group = unit - cand * a.groups;
         const int c_begin = group * a.chunks_per_group;
         const int c_end = min(a.chunks, c_begin + a.chunks_per_group);
@@ -370,6 +380,7 @@ int launch_smooth_t(const ModelDev &m, const SceneDev &sc, const SmoothArgs &a, 
     const int units = a.n * a.groups;
     int grid = (units + threads / 32 - 1) / (threads / 32);
     if (grid > num_sms * per_sm) grid = num_sms * per_sm;
+    if (a.queue != nullptr) CP_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
     kern<<<grid, threads, smem, st>>>(m, sc, a);
     CP_LAUNCHED("k_smooth");
     if (a.groups > 1) {
@@ -400,10 +411,11 @@ int64_t smooth_partial_units(int num_sms) { return 2 * 32 * (int64_t)num_sms; }
 int launch_smooth(const ModelDev &m, const SceneDev &sc, const float *xi, int n, int K, int S,
                   float4 q0, float4 qd, const float4 *basis, double margin, double beta,
                   double wc_lc, double w_l, const double *gJ, double *J, float *dxi, float *part_g,
-                  double *part_J, int num_sms, cudaStream_t st)
+                  double *part_J, int *queue, int num_sms, cudaStream_t st)
 {
     if (n == 0) return CP_OK;
     SmoothArgs a{};
+    a.queue = queue;
     a.xi = (const float4 *)xi;
     a.n = n;
     a.K = K;
