@@ -12,6 +12,7 @@
 // the exact capped-cylinder distance. A second kernel adds each candidate's item sums in a
 // fixed order in FP64.
 #include "eval_common.cuh"
+#include "item_queue.cuh"
 
 namespace cp {
 namespace {
@@ -201,7 +202,7 @@ k_eval_broad(const ModelDev m, const SceneDev sc, const EvalArgs a)
     const float zero[NSPH] = {};
     const float zlo = sc.z_lo_all - m.r_max - kZGate, zhi = sc.z_hi_all + m.r_max + kZGate;
 
-    for (int it = warp; it < items; it += n_warps) {
+    for (int it = queue_first(a, warp, lane); it < items; it = queue_next(a, it, n_warps, lane)) {
         const ItemRange ir = item_range(a, it);
         stage_controls(s_ctrl, a, ir.cand, lane);
         double acc = 0.0;
@@ -284,7 +285,7 @@ k_eval(const ModelDev m, const SceneDev sc, const EvalArgs a)
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     const int items = a.n * a.P;
 
-    for (int it = warp; it < items; it += n_warps) {
+    for (int it = queue_first(a, warp, lane); it < items; it = queue_next(a, it, n_warps, lane)) {
       const ItemRange ir = item_range(a, it);
       stage_controls(s_ctrl, a, ir.cand, lane);
       double acc = 0.0;
@@ -437,6 +438,7 @@ int launch_eval(const ModelDev &m, const SceneDev &sc, const EvalArgs &a, int nu
     if (units == 0) return CP_OK;
     const size_t smem = eval_smem_bytes(sc.n_cyl, sc.n_box, a.S);
     const int cpsm = a.ctas_per_sm;
+    if (a.queue != nullptr) CP_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
     if (m.n_spheres == 12) {
         if (a.broadphase)
             k_eval_broad<12><<<eval_grid(k_eval_broad<12>, smem, num_sms, units, cpsm), kEvalThreads, smem, st>>>(m, sc, a);

@@ -20,6 +20,7 @@
 // skipped, and a pair's axes are tried with the cheap obstacle axes first and stop at the
 // first separating one.
 #include "eval_common.cuh"
+#include "item_queue.cuh"
 
 namespace cp {
 namespace {
@@ -357,7 +358,7 @@ k_eval_hulls(const ModelDev m, const SceneDev sc, const HullDims hd, const EvalA
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int n_warps = (int)((gridDim.x * blockDim.x) >> 5);
     float4 *s_ctrl = s_ctrl_all[wib];
-    for (int it = warp; it < a.n * a.P; it += n_warps) {
+    for (int it = queue_first(a, warp, lane); it < a.n * a.P; it = queue_next(a, it, n_warps, lane)) {
         const ItemRange ir = item_range(a, it);
         stage_controls(s_ctrl, a, ir.cand, lane);
         double acc = 0.0;
@@ -399,6 +400,7 @@ int launch_eval_hulls(const ModelDev &m, const SceneDev &sc, const HullDims &d, 
     const long long items = (long long)a.n * a.P;
     long long blocks = (items + kHullWarps - 1) / kHullWarps;
     if (blocks > (long long)num_sms * per_sm) blocks = (long long)num_sms * per_sm;
+    if (a.queue != nullptr) CP_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
     k_eval_hulls<<<(unsigned)blocks, kHullThreads, smem, st>>>(m, sc, d, a);
     CP_LAUNCHED("k_eval_hulls");
     return CP_OK;
