@@ -211,6 +211,7 @@ struct cp_planner {
     // per-iteration metrics of cp_plan: ring of kMetricsRing rows (slot = iteration mod ring)
     bool metrics_on = false;
     double *metrics = nullptr;
+    double *metrics_part = nullptr;   // [kMetricsBlocks][3] partial sums of a row
     int64_t metrics_count = 0;   // rows written since the end points were set
 };
 
@@ -598,7 +599,7 @@ int record_metrics(cp_planner *p)
     double *row = p->metrics + (size_t)(it % kMetricsRing) * kMetricsCols;
     const bool no_C = p->elites_ready;   // the factor-free sampler's update forms no C
     return launch_iter_metrics(p->J, p->flag, p->N, p->best, no_C ? nullptr : p->C, p->elites, p->w, p->mu, p->nu,
-                               p->D, p->prm.eps, it, row, p->st);
+                               p->D, p->prm.eps, it, p->metrics_part, row, p->st);
 }
 
 // One iteration of cp_plan: steps (1)-(6) and the metrics row when on.
@@ -772,6 +773,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     const size_t o_work = L.take<unsigned long long>(2);
     const size_t o_eval_queue = L.take<int>(1);
     const size_t o_metrics = L.take<double>((size_t)kMetricsRing * kMetricsCols);
+    const size_t o_metrics_part = L.take<double>(3 * (size_t)kMetricsBlocks);
     const size_t o_cma = L.take<double>(4);
     const size_t o_psig = L.take<double>(D);
     const size_t o_pc = L.take<double>(D);
@@ -836,6 +838,7 @@ int cp_plan_init(const cp_model *model, const cp_scene *scene, const cp_params *
     p->work = (unsigned long long *)(b + o_work);
     p->eval_queue = (int *)(b + o_eval_queue);
     p->metrics = (double *)(b + o_metrics);
+    p->metrics_part = (double *)(b + o_metrics_part);
     p->cma = (double *)(b + o_cma);
     p->p_sigma = (double *)(b + o_psig);
     p->p_c = (double *)(b + o_pc);

@@ -308,9 +308,10 @@ int update_configure();
 // null: tr C from the elites about mu (factor-free sampler).
 constexpr int kMetricsCols = 5;
 constexpr int kMetricsRing = 256;   // rows kept (the last kMetricsRing iterations)
+constexpr int kMetricsBlocks = 128; // blocks of the partial sums (part holds 3 kMetricsBlocks)
 int launch_iter_metrics(const double *J, const uint8_t *flag, int N, const double *best, const double *C,
                         const float *elites, const double *w, const double *mu, int nu, int D, double eps,
-                        int iteration, double *row, cudaStream_t st);
+                        int iteration, double *part, double *row, cudaStream_t st);
 
 // ------------------------------------------------------------------ batched form
 // One launch of each stage serves every query of a batch. Each query keeps its own planner
