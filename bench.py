@@ -277,8 +277,9 @@ def run_ours(args):
     crane = workloads.forestry_crane()
     scene = workloads.make_scene(wl)
     sampler = resolve_sampler(args, wl)
+    grid_cell = 0.0 if args.exhaustive else wl.grid_cell   # the exhaustive form takes no index
     params = cp.make_params(wl.n_candidates, wl.n_waypoints, wl.substeps, seed=wl.seed, query=rank,
-                            grid_cell=wl.grid_cell, eval_exhaustive=int(args.exhaustive),
+                            grid_cell=grid_cell, eval_exhaustive=int(args.exhaustive),
                             update_rule=cp.CP_UPDATE_CMAES if args.update_rule == "cmaes" else cp.CP_UPDATE_PAPER,
                             sampler=cp.CP_SAMPLE_ELITES if sampler == "elites" else cp.CP_SAMPLE_FACTOR,
                             collision_model=cp.CP_COLLISION_HULLS if args.collision == "hulls" else cp.CP_COLLISION_SPHERES)
@@ -364,7 +365,7 @@ def run_ours(args):
     candidates = n_timing * (wl.n_candidates * iters + 1)
     roofline_exhaustive = None
     peaks_fp64 = None
-    form = "polar" if wl.grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
+    form = "polar" if grid_cell > 0 else ("exhaustive" if args.exhaustive else "broad")
     if args.collision == "hulls":
         # the hull form's work per checkpoint depends on the pairs its scan keeps; its line
         # reports the launch time only
@@ -1428,7 +1429,7 @@ def main():
     ap.add_argument("--update-rule", default="paper", choices=["paper", "cmaes"],
                     help="steps (5)-(6) as Algorithm 1 prints them, or the CMA-ES update")
     ap.add_argument("--exhaustive", action="store_true",
-                    help="evaluate every sphere against every obstacle (no broad phase)")
+                    help="evaluate every sphere against every obstacle (no broad phase, no index)")
     ap.add_argument("--queries", type=int, default=64, help="batch workload: number of queries")
     ap.add_argument("--batch-shape", default="",
                     help="batch workload: fixed evaluation shape 'threads,ctas_per_sm,items_per_warp' "
