@@ -89,6 +89,12 @@ def test_sampler_stage(bench, wl, monkeypatch):
     assert s["tensor"]["achieved"] == pytest.approx(3 * 2.0 * wl.n_candidates * nu * Dp / (us / 1e6) / 1e12)
     assert s["tensor"]["peak"] == pytest.approx(1100.0)
     assert bench.sampler_stage(_timing(), wl, "factor") is None
+    # without measured peaks the stage reports against the labelled fallback, not null
+    monkeypatch.setattr(bench, "measured_peaks", lambda: {})
+    f = bench.sampler_stage(_timing(), wl, "elites")
+    assert f["tensor"]["peak"] == pytest.approx(1700.0 * 1.1 / 2.25)
+    assert f["tensor"]["frac"] == pytest.approx(f["tensor"]["achieved"] / f["tensor"]["peak"])
+    assert "fallback" in f["tensor"]["peak_basis"]
 
 
 def test_steps_for_clocks_covers_a_second(bench, monkeypatch):

@@ -59,6 +59,43 @@ def test_sample_and_factor(lib, crane, N, K, it):
         s.close()
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e-24, 1e30])
+def test_factor_scales_and_reports_indefinite(lib, crane, scale):
+    """The FP64 factor of sigma^2 C far from unit scale (its backward error stays within a
+    few FP64 roundings of the largest diagonal entry), and a covariance with a negative
+    eigenvalue: the non-positive pivot is reported as CP_ERR_NUMERIC at the next
+    synchronisation, which also clears the report."""
+    import torch
+    from paper_2503_14160_gb300 import workloads
+    K = 8
+    D = 4 * K
+    s = Setup(crane, workloads.empty_scene(), N=64, K=K, S=4, seed=5, sigma=0.8)
+    try:
+        C, mu = _spd(D, seed=3)
+        C = C * scale
+        lib.cp_set_endpoints(s.h, np.zeros(4), np.ones(4))
+        lib.cp_set_distribution(s.h, torch.from_numpy(mu).cuda(), torch.from_numpy(C).cuda(), 0)
+        Lg = torch.zeros(D, D, dtype=torch.float64, device="cuda")
+        lib.cp_get_factor(s.h, Lg)
+        lib.cp_synchronize(s.h)
+        A = 0.8 ** 2 * C
+        Lgn = Lg.cpu().numpy()
+        assert np.all(np.triu(Lgn, 1) == 0.0)
+        # Cholesky's backward error |L L^T - A| <= gamma_(D+1) |L||L^T| entrywise, and every
+        # entry of |L||L^T| is at most the largest diagonal entry of A (Cauchy-Schwarz)
+        assert np.abs(Lgn @ Lgn.T - A).max() <= (D + 1) * 2.0 ** -52 * np.abs(np.diag(A)).max()
+        w, V = np.linalg.eigh(C)
+        w[0] = -abs(w[-1])
+        bad = (V * w) @ V.T
+        lib.cp_set_distribution(s.h, torch.from_numpy(mu).cuda(), torch.from_numpy(bad).cuda(), 0)
+        with pytest.raises(lib.CranePlanError) as e:
+            lib.cp_synchronize(s.h)
+        assert e.value.status == -6   # CP_ERR_NUMERIC
+        lib.cp_synchronize(s.h)
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("N,K,nu,ties", [(300, 4, 150, 30), (4096, 16, 0, 0), (77, 2, 1, 5),
                                          (8193, 8, 8000, 200), (65536, 32, 0, 100)])
 def test_update_matches_oracle(lib, crane, N, K, nu, ties):
