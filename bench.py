@@ -180,8 +180,8 @@ KERNEL_SOURCES = {
 # kernel's sources at the time of the capture: reported only while the sources still hash
 # to it, None once the kernel has changed.
 PROFILED_TRAFFIC = {
-    ("k_eval_polar", "dense_forest"): {"sha1": "4575405339bb4aa3cb380cb03f78f9cf4d2c7b82", "bytes": 33682688.0},
-    ("k_eval_polar", "single_large"): {"sha1": "4575405339bb4aa3cb380cb03f78f9cf4d2c7b82", "bytes": 1162496.0},
+    ("k_eval_polar", "dense_forest"): {"sha1": "b833554fe56fa708382bddf5323f7eb9611589b3", "bytes": 34001408.0},
+    ("k_eval_polar", "single_large"): {"sha1": "b833554fe56fa708382bddf5323f7eb9611589b3", "bytes": 1160192.0},
 }
 
 

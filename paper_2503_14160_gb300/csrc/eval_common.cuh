@@ -418,7 +418,9 @@ static __device__ __forceinline__ ItemRange item_range(const EvalArgs &a, int it
 // partner, across lanes 8 apart one of the two, and three more steps finish the sum of that
 // one value, so lane 8 j ends with the sum of value j (6 shuffles instead of 20); lane 8 j
 // keeps the item's FP64 sum of value j. The ballot word of checkpoints in collision and the
-// per-checkpoint penalty are written when asked for.
+// per-checkpoint penalty are written when asked for; a kernel compiled with kExtras false
+// (launched only when neither is asked for) leaves out their tests.
+template <bool kExtras = true>
 static __device__ __forceinline__ void unit_accumulate(const EvalArgs &a, const Checkpoint &c, float dmin,
                                                        int cand, int chunk, int lane, double &acc,
                                                        uint32_t &count)
@@ -437,8 +439,10 @@ static __device__ __forceinline__ void unit_accumulate(const EvalArgs &a, const 
     acc += (double)x;
     const uint32_t word = __ballot_sync(0xffffffffu, hit);
     count += (uint32_t)__popc(word);
-    if (a.words_out != nullptr && lane == 0) a.words_out[(size_t)cand * a.chunks + chunk] = word;
-    if (a.pen_out != nullptr && c.valid) a.pen_out[(size_t)cand * a.n_s + (c.k - 1)] = pen;
+    if (kExtras) {
+        if (a.words_out != nullptr && lane == 0) a.words_out[(size_t)cand * a.chunks + chunk] = word;
+        if (a.pen_out != nullptr && c.valid) a.pen_out[(size_t)cand * a.n_s + (c.k - 1)] = pen;
+    }
 }
 
 static __device__ __forceinline__ void item_flush(const EvalArgs &a, int item, double acc, uint32_t count,

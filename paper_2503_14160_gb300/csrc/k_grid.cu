@@ -174,8 +174,10 @@ __device__ __forceinline__ float polar_exact(const ModelDev &m, const SceneDev &
 // One work item (candidate, G consecutive units) of the polar form on one warp: per lane a
 // checkpoint, its spheres' in-band extent of h, the one or two angular bins and the ring
 // range that can hold an obstacle within reach, the packed filter over the listed entries
-// and the exact distance of those that pass.
-template <int NSPH>
+// and the exact distance of those that pass. kExtras false leaves out the work counters and
+// the per-checkpoint outputs (the plan's own evaluations ask for neither); the sums are the
+// same.
+template <int NSPH, bool kExtras = true>
 static __device__ __forceinline__ void polar_item(const ModelDev &m, const SceneDev &sc, const PolarDev &g,
                                                   const EvalArgs &a, const float4 *s_basis, float4 *s_ctrl,
                                                   int it, int lane, uint32_t &survivors, uint32_t &tests)
@@ -212,7 +214,7 @@ static __device__ __forceinline__ void polar_item(const ModelDev &m, const Scene
                 const int cell = bin * g.n_ring;
                 const int beg = __ldg(g.cell_start + cell + r0);
                 const int end = min(__ldg(g.cell_start + cell + r1 + 1), g.capacity);
-                tests += (uint32_t)max(end - beg, 0);
+                if (kExtras) tests += (uint32_t)max(end - beg, 0);
                 for (int e = beg; e < end; ++e) {
                     const float4 rec = __ldg(g.items + e);   // {cx, cy, bound, id}
                     const float p = fmaf(c1, rec.x, s1 * rec.y);
@@ -226,19 +228,19 @@ static __device__ __forceinline__ void polar_item(const ModelDev &m, const Scene
                         t[k] = __ffma2_rn(dh, dh, mr2);
                     }
                     if (any_negative<NSPH>(t)) {
-                        ++survivors;
+                        if (kExtras) ++survivors;
                         dmin = fminf(dmin, polar_exact<NSPH>(m, sc, H, Z, c1, s1, p, rhs, __float_as_int(rec.w)));
                     }
                 }
             }
         }
         __syncwarp();
-        unit_accumulate(a, c, dmin, ir.cand, chunk, lane, acc, count);
+        unit_accumulate<kExtras>(a, c, dmin, ir.cand, chunk, lane, acc, count);
     }
     item_flush(a, it, acc, count, lane);
 }
 
-template <int NSPH>
+template <int NSPH, bool kExtras>
 __global__ void __launch_bounds__(kPolarThreads, CP_POLAR_MIN_BLOCKS)
 k_eval_polar(const ModelDev m, const SceneDev sc, const PolarDev g, const EvalArgs a)
 {
@@ -261,13 +263,13 @@ k_eval_polar(const ModelDev m, const SceneDev sc, const PolarDev g, const EvalAr
             if (lane == 0) it = atomicAdd(a.queue, 1);
             it = __shfl_sync(0xffffffffu, it, 0);
             if (it >= items) break;
-            polar_item<NSPH>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
+            polar_item<NSPH, kExtras>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
         }
     } else {
         for (int it = warp; it < items; it += n_warps)
-            polar_item<NSPH>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
+            polar_item<NSPH, kExtras>(m, sc, g, a, s_basis, s_ctrl, it, lane, survivors, tests);
     }
-    if (a.work != nullptr) {
+    if (kExtras && a.work != nullptr) {
         const uint32_t ws = __reduce_add_sync(0xffffffffu, survivors);
         const uint32_t wt = __reduce_add_sync(0xffffffffu, tests);
         if (lane == 0 && ws != 0) atomicAdd(a.work, (unsigned long long)ws);
@@ -400,24 +402,20 @@ int launch_eval_polar(const ModelDev &m, const SceneDev &sc, const PolarDev &g, 
     const int items = a.n * a.P;
     if (items == 0) return CP_OK;
     const size_t smem = sizeof(float4) * (2 * (size_t)a.S + (size_t)(kPolarThreads / 32) * kCtrlSlots);
+    // the plain form (no work counters, no per-checkpoint outputs) drops their bookkeeping
+    const bool extras = a.work != nullptr || a.words_out != nullptr || a.pen_out != nullptr;
+    auto kern = m.n_spheres == 12 ? (extras ? k_eval_polar<12, true> : k_eval_polar<12, false>)
+                                  : (extras ? k_eval_polar<16, true> : k_eval_polar<16, false>);
     int per_sm = 0;
-    if (m.n_spheres == 12) {
-        CP_CUDA(raise_polar_smem(k_eval_polar<12>, smem));
-        CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_polar<12>, kPolarThreads, smem));
-    } else {
-        CP_CUDA(raise_polar_smem(k_eval_polar<16>, smem));
-        CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_polar<16>, kPolarThreads, smem));
-    }
+    CP_CUDA(raise_polar_smem(kern, smem));
+    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPolarThreads, smem));
     if (per_sm < 1) per_sm = 1;
     if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
     const int needed = (items + kPolarThreads / 32 - 1) / (kPolarThreads / 32);
     int grid = num_sms * per_sm;
     if (grid > needed) grid = needed;
     if (a.queue != nullptr) CP_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
-    if (m.n_spheres == 12)
-        k_eval_polar<12><<<grid, kPolarThreads, smem, st>>>(m, sc, g, a);
-    else
-        k_eval_polar<16><<<grid, kPolarThreads, smem, st>>>(m, sc, g, a);
+    kern<<<grid, kPolarThreads, smem, st>>>(m, sc, g, a);
     CP_LAUNCHED("k_eval_polar");
     return CP_OK;
 }
