@@ -313,8 +313,8 @@ k_batch_eval_polar(const ModelDev m, const BatchEvalDev *__restrict__ qd, const 
             for (int i = threadIdx.x; i < 2 * s_q.a.S; i += THREADS) s_basis[i] = __ldg(s_q.a.basis + i);
             __syncthreads();
         }
-        for (int it = tile.y + wib; it < tile.z; it += W)
-            polar_item<NSPH>(m, s_q.sc, s_q.g, s_q.a, s_basis, s_ctrl, it, lane, survivors, tests);
+        for (int it = tile.y + wib; it < tile.z; it += W)   // the batch asks for no counters or outputs
+            polar_item<NSPH, false>(m, s_q.sc, s_q.g, s_q.a, s_basis, s_ctrl, it, lane, survivors, tests);
         __syncthreads();   // the tile's items are done before s_tile and s_q change
     }
 }
