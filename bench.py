@@ -377,6 +377,11 @@ def run_ours(args):
                                  candidates, form, clk.get("sm_mhz"))
     if roofline is not None and roofline.get("achieved") is not None:
         roofline["traffic"] = traffic_per_launch(roofline["kernel"], wl.name)
+        roofline["traffic_source"] = (
+            "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (iteration 0) of this "
+            "kernel's current source on this workload, taken in a separate profiling run"
+            if roofline["traffic"] is not None else
+            "none: no ncu capture of this kernel's current source on this workload")
         peaks = cp.cp_alu_peaks()
         peaks_fp64 = peaks["fp64_tflops"]
         roofline["measured_fma_peaks"] = peaks
